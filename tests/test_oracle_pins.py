@@ -1,0 +1,290 @@
+"""Pins of the FP64 oracle against facts fixed by the paper and by the mathematics.
+
+Each test would fail under a plausible mistake in the oracle: a wrong merge order
+or misplaced conjugate in the double layer, a transposed MPO leg, a wrong frame
+rotation, a dropped environment term, a wrong QR sign, a broken stop rule.
+References are independent: brute-force state vectors, textbook site BP, dense
+MPO x MPS products, closed-form product-state values.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import _exact as X
+from oracle import blockbp as ob
+from paper_2301_05844_gb300 import inputs as I
+
+SZ, SX, SY = I.SIGMA_Z, I.SIGMA_X, I.SIGMA_Y
+
+
+def exact_values(T, Lx, Ly, terms):
+    psi = X.state_vector(T, Lx, Ly)
+    return np.array([X.exact_expect(psi, Lx * Ly, T[0].shape[0], t) for t in terms])
+
+
+# -------------------------------------------------------------------------------------
+def test_splitmix64_published_outputs():
+    """SplitMix64 outputs from state 0 (Steele et al. 2014), stored in tests/golden."""
+    path = os.path.join(os.path.dirname(__file__), "golden", "splitmix64.txt")
+    want = [int(l, 16) for l in open(path) if l.strip() and not l.startswith("#")]
+    g = 0x9E3779B97F4A7C15
+    got = ob.splitmix64(np.array([(k * g) % 2**64 for k in range(len(want))], dtype=np.uint64))
+    assert [int(v) for v in got] == want
+    u = ob.uniform_pm1(7, 3, 1000)
+    assert u.min() >= -1.0 and u.max() < 1.0 and abs(u.mean()) < 0.1
+
+
+def test_double_layer_contracts_to_norm_and_expectation():
+    """The closed double-layer network equals <psi|psi>, and with O inserted <psi|O|psi>
+    (Fig. 1(a,b)); complex tensors catch a misplaced conjugate or ket/bra swap."""
+    rng = np.random.default_rng(11)
+    Lx, Ly, d, D = 2, 2, 2, 2
+    T = []
+    for r in range(Ly):
+        for c in range(Lx):
+            shp = I.site_shape(r, c, Lx, Ly, d, D)
+            T.append(rng.standard_normal(shp) + 1j * rng.standard_normal(shp))
+    psi = X.state_vector(T, Lx, Ly)
+    O = np.array([[0.3, 1.0 - 0.5j], [0.2 + 0.7j, -1.1]])  # not Hermitian on purpose
+    for opsite in (None, 0, 3):
+        E = [ob.double_layer(T[i], O if i == opsite else None) for i in range(4)]
+        val = _closed_2x2(E)
+        if opsite is None:
+            ref = np.vdot(psi, psi)
+        else:
+            ref = X.exact_expect(psi, 4, 2, [(opsite, O)]) * np.vdot(psi, psi)
+        assert abs(val - ref) < 1e-12 * abs(np.vdot(psi, psi))
+
+
+def _closed_2x2(E):
+    """Exact contraction of a 2x2 OBC double-layer network E[u,l,d,r]."""
+    e0, e1, e2, e3 = E
+    # bonds: e0.r-e1.l (a), e0.d-e2.u (b), e1.d-e3.u (c), e2.r-e3.l (e)
+    return np.einsum("xyba,zacw,bvue,cesq->", e0, e1, e2, e3, optimize=True)
+
+
+def test_qr_lq_factors():
+    """Q orthonormal, Q^dagger M upper triangular with a real non-negative diagonal."""
+    rng = np.random.default_rng(5)
+    for cplx in (False, True):
+        M = rng.standard_normal((12, 5)) + (1j * rng.standard_normal((12, 5)) if cplx else 0)
+        Q = ob.qr_q(M)
+        R = np.conj(Q.T) @ M
+        assert np.allclose(np.conj(Q.T) @ Q, np.eye(5), atol=1e-13)
+        assert np.allclose(np.tril(R, -1), 0, atol=1e-12)
+        assert np.all(np.abs(np.diag(R).imag) < 1e-12) and np.all(np.diag(R).real > 0)
+        assert np.allclose(Q @ R, M, atol=1e-12)
+        Lq = ob.lq_q(M.T.copy())
+        L = M.T @ np.conj(Lq.T)
+        assert np.allclose(Lq @ np.conj(Lq.T), np.eye(5), atol=1e-13)
+        assert np.allclose(np.triu(L, 1), 0, atol=1e-12) and np.all(np.diag(L).real > 0)
+
+
+def _random_mpo_mps(rng, n, p, q, w, x, cplx=False):
+    def rnd(*s):
+        a = rng.standard_normal(s)
+        return a + 1j * rng.standard_normal(s) if cplx else a
+    ws = [1] + [w] * (n - 1) + [1]
+    xs = [1] + [x] * (n - 1) + [1]
+    O = [rnd(ws[i], p, q, ws[i + 1]) for i in range(n)]
+    Xs = [rnd(xs[i], p, xs[i + 1]) for i in range(n)]
+    return O, Xs
+
+
+@pytest.mark.parametrize("cplx", [False, True])
+def test_fit_full_rank_is_exact(cplx):
+    """At full bond the variational fit reproduces O|X> exactly (App. A, Eq. distance = 0)."""
+    rng = np.random.default_rng(3)
+    O, Xs = _random_mpo_mps(rng, 4, 2, 3, 2, 2, cplx)
+    dt = np.complex128 if cplx else np.float64
+    Y, hist = ob.fit_mpo_mps(O, Xs, ob.FitOpts(chi=100, tol=0.0, max_sweeps=2),
+                             lambda i, s: ob.random_site(1, i, s, dt), dt)
+    assert np.allclose(X.dense_mps(Y), X.dense_mpo_apply(O, Xs), atol=1e-10)
+
+
+@pytest.mark.parametrize("cplx", [False, True])
+def test_fit_loss_identity_and_monotone(cplx):
+    """-||Yt||^2 = ||Y - O X||^2 - <X|O^dag O|X> (App. A) and the loss never rises
+    once the environments are canonical (from the first right-to-left update on)."""
+    rng = np.random.default_rng(4)
+    O, Xs = _random_mpo_mps(rng, 5, 2, 2, 3, 3, cplx)
+    dt = np.complex128 if cplx else np.float64
+    Y, hist = ob.fit_mpo_mps(O, Xs, ob.FitOpts(chi=3, tol=0.0, max_sweeps=6),
+                             lambda i, s: ob.random_site(9, i, s, dt), dt)
+    ox = X.dense_mpo_apply(O, Xs)
+    y = X.dense_mps(Y)
+    final_loss = -np.vdot(Y[0], Y[0]).real
+    assert abs(np.linalg.norm(y - ox) ** 2 - np.linalg.norm(ox) ** 2 - final_loss) < 1e-9 * np.linalg.norm(ox) ** 2
+    flat = [l for h in hist for l in h]
+    n = len(Xs)
+    tail = flat[n - 1:]
+    assert all(b <= a + 1e-10 * abs(a) for a, b in zip(tail, tail[1:]))
+    assert final_loss <= tail[-1] + 1e-10 * abs(tail[-1])
+
+
+def test_fit_stop_rule():
+    """std/|mean| of the losses of one sweep below tol ends the fit (App. A)."""
+    rng = np.random.default_rng(8)
+    O, Xs = _random_mpo_mps(rng, 4, 2, 2, 2, 2)
+    _, hist = ob.fit_mpo_mps(O, Xs, ob.FitOpts(chi=100, tol=1e-6, max_sweeps=10),
+                             lambda i, s: ob.random_site(2, i, s, np.float64), np.float64)
+    last = np.array(hist[-1])
+    assert len(hist) < 10 and np.std(last) / abs(np.mean(last)) < 1e-6
+
+
+# -------------------------------------------------------------------------------------
+@pytest.mark.parametrize("cplx", [False, True])
+def test_single_block_equals_brute_force(cplx):
+    """One block covering the lattice: no messages, the read-out at full chi_exp is the
+    exact contraction (Fig. 1(e) with a trivial environment)."""
+    rng = np.random.default_rng(21)
+    T = I.uniform_noise_peps(4, 4, 2, 2, seed=1)
+    if cplx:
+        T = [t + 0.3j * rng.standard_normal(t.shape) for t in T]
+    terms = I.standard_terms(4, 4) + [[(5, SY), (6, SY)], [(0, SX), (9, SZ)], [(1, SX), (13, SX)]]
+    lat = ob.Lattice(4, 4, 2, 2, 4, 4, T, chi=16, chi_exp=64, fit_tol=0.0, fit_max_sweeps=2)
+    assert not lat.msgs
+    got = lat.expect(terms)
+    assert np.max(np.abs(got - exact_values(T, 4, 4, terms))) < 1e-12
+
+
+@pytest.mark.parametrize("bx,by", [(4, 1), (4, 2), (1, 4), (2, 4)])
+def test_tree_block_graph_is_exact(bx, by):
+    """Strip blocks form a chain (a tree): the BP fixed point is the exact environment
+    (Sec. "The blockBP algorithm"), so every <O> equals brute force at full chi."""
+    T = I.uniform_noise_peps(4, 4, 2, 2, seed=1)
+    terms = I.standard_terms(4, 4)
+    lat = ob.Lattice(4, 4, 2, 2, bx, by, T, chi=16, chi_exp=18, fit_tol=0.0, fit_max_sweeps=2)
+    nblk = lat.nbx * lat.nby
+    res, sweeps, _ = lat.run(n_sweeps=nblk + 1)
+    assert abs(res) < 1e-12
+    got = lat.expect(terms)
+    assert np.max(np.abs(got - exact_values(T, 4, 4, terms))) < 1e-12
+
+
+def test_product_state_D1_exact_after_one_sweep():
+    """D=1: <O>_s = t_s^dag O t_s / t_s^dag t_s after one sweep; residual 0 from sweep 2."""
+    rng = np.random.default_rng(2)
+    vecs = [rng.standard_normal(2) + 1j * rng.standard_normal(2) for _ in range(36)]
+    T = I.product_peps(6, 6, 2, 1, vecs)
+    lat = ob.Lattice(6, 6, 2, 1, 3, 2, T, chi=4, fit_tol=0.0, fit_max_sweeps=1)
+    lat.sweep()
+    assert abs(lat.sweep()) < 1e-14
+    terms = [[(s, SZ)] for s in range(36)] + [[(s, SX)] for s in range(36)]
+    got = lat.expect(terms)
+    want = [np.vdot(v, O @ v) / np.vdot(v, v) for O in (SZ, SX) for v in vecs]
+    assert np.max(np.abs(got - np.array(want))) < 1e-13
+
+
+@pytest.mark.parametrize("D,chi", [(2, 1), (2, 4), (3, 5)])
+@pytest.mark.parametrize("h_limit", ["plus", "up"])
+def test_tfim_limits_with_gauges(D, chi, h_limit):
+    """Transverse-Ising limits: |+>^N (field -> infinity) and |up>^N (field 0), embedded
+    at bond D and dressed with random bond gauges, are exact for any chi >= 1."""
+    t = np.array([1.0, 1.0]) / math.sqrt(2) if h_limit == "plus" else np.array([1.0, 0.0])
+    Lx = Ly = 4
+    T = I.gauge_dress(I.product_peps(Lx, Ly, 2, D, [t] * 16), Lx, Ly, seed=D * 10 + chi)
+    lat = ob.Lattice(Lx, Ly, 2, D, 2, 2, T, chi=chi, chi_exp=chi, fit_tol=0.0, fit_max_sweeps=2)
+    lat.run(n_sweeps=3)
+    terms = [[(5, SX)], [(5, SZ)], [(5, SZ), (6, SZ)], [(1, SZ), (2, SZ)], [(2, SX), (6, SX)]]
+    want = [1, 0, 0, 0, 1] if h_limit == "plus" else [0, 1, 1, 1, 0]
+    assert np.max(np.abs(lat.expect(terms) - np.array(want))) < 1e-10
+
+
+def test_tfim_limit_infinite_gauged():
+    """The same closed form on an infinite 2x2 unit cell with complex gauges."""
+    t = np.array([1.0, 1.0]) / math.sqrt(2)
+    T = I.gauge_dress(I.product_peps(2, 2, 2, 2, [t] * 4, boundary="infinite"), 2, 2, seed=3,
+                      boundary="infinite", complex_gauge=True)
+    lat = ob.Lattice(2, 2, 2, 2, 2, 2, T, boundary="infinite", chi=2, fit_tol=0.0, fit_max_sweeps=2)
+    lat.run(n_sweeps=3)
+    got = lat.expect([[(0, SX)], [(3, SZ)], [(0, SX), (1, SX)], [(1, SZ), (3, SZ)]])
+    assert np.max(np.abs(got - np.array([1, 0, 1, 0]))) < 1e-10
+
+
+@pytest.mark.parametrize("cplx", [False, True])
+def test_block_size_one_equals_textbook_bp(cplx):
+    """Blocks of one site reduce blockBP to plain BP (Sec. "The blockBP algorithm")."""
+    T = I.uniform_noise_peps(4, 3, 2, 2, seed=1)
+    if cplx:
+        rng = np.random.default_rng(1)
+        T = [t + 0.2j * rng.standard_normal(t.shape) for t in T]
+    terms = I.standard_terms(4, 3)
+    lat = ob.Lattice(4, 3, 2, 2, 1, 1, T, chi=4, fit_tol=0.0, fit_max_sweeps=1)
+    lat.run(n_sweeps=60)
+    got = lat.expect(terms)
+    ref = X.textbook_bp(T, 4, 3, terms)
+    assert np.max(np.abs(got - ref)) < 1e-12
+
+
+def test_messages_unit_norm_hermitian_and_converge():
+    """||m|| = 1, m(k,k') = conj m(k',k) as an operator (full rank, Hermitian init),
+    residual -> 0 at the fixed point; Im<O> ~ 0 for Hermitian O."""
+    rng = np.random.default_rng(6)
+    T = I.uniform_noise_peps(4, 4, 2, 2, seed=1)
+    T = [t + 0.3j * rng.standard_normal(t.shape) for t in T]
+    lat = ob.Lattice(4, 4, 2, 2, 2, 2, T, chi=16, fit_tol=1e-12, fit_max_sweeps=6)
+    res, sweeps, ok = lat.run(tol=1e-13, max_sweeps=15)
+    assert ok and res < 1e-13
+    for m in lat.msgs.values():
+        assert abs(ob.mps_overlap(m, m) - 1) < 1e-13
+        herm = [s.reshape(s.shape[0], 2, 2, s.shape[2]).transpose(0, 2, 1, 3).reshape(s.shape).conj() for s in m]
+        assert abs(abs(ob.mps_overlap(m, herm)) - 1) < 1e-11
+        assert abs(ob.identity_trace(m, 2).imag) < 1e-12 and ob.identity_trace(m, 2).real > 0
+    vals = lat.expect(I.standard_terms(4, 4))
+    assert np.max(np.abs(vals.imag)) < 1e-12
+
+
+def test_gauge_invariance_full_rank():
+    """Random invertible gauges on every bond leave <O> unchanged at full chi."""
+    T = I.uniform_noise_peps(4, 4, 2, 2, seed=1)
+    Tg = I.gauge_dress(T, 4, 4, seed=17)
+    terms = I.standard_terms(4, 4)
+    vals = []
+    for TT in (T, Tg):
+        lat = ob.Lattice(4, 4, 2, 2, 2, 2, TT, chi=16, fit_tol=1e-12, fit_max_sweeps=6)
+        lat.run(n_sweeps=12)
+        vals.append(lat.expect(terms))
+    assert np.max(np.abs(vals[0] - vals[1])) < 1e-10
+
+
+def test_relative_stop_rule_and_init_modes():
+    """Relative criterion r_l / r_1 < tol (App. A) stops earlier than absolute 1e-16;
+    random-MPDO init (App. A) reaches the same fixed point as the identity init."""
+    T = I.uniform_noise_peps(4, 4, 2, 2, seed=1)
+    terms = I.standard_terms(4, 4)
+    a = ob.Lattice(4, 4, 2, 2, 2, 2, T, chi=16, fit_tol=1e-12, fit_max_sweeps=6)
+    r, k, ok = a.run(tol=1e-5, max_sweeps=20, relative=True)
+    assert ok and a.residuals[-1] / a.residuals[0] < 1e-5 and k < 10
+    b = ob.Lattice(4, 4, 2, 2, 2, 2, T, chi=16, fit_tol=1e-12, fit_max_sweeps=6, init_mode=1, seed=5)
+    b.run(n_sweeps=12)
+    a.run(n_sweeps=12)
+    assert np.max(np.abs(a.expect(terms) - b.expect(terms))) < 1e-10
+
+
+def test_normalise_message_norm_and_phase():
+    """Unit 2-norm and <I|m> real positive after normalisation, for an arbitrary
+    complex MPS whose identity trace has a generic phase."""
+    rng = np.random.default_rng(12)
+    M = [rng.standard_normal(s) + 1j * rng.standard_normal(s) for s in [(1, 9, 3), (3, 9, 3), (3, 9, 1)]]
+    N = ob.normalise_message(M, 3)
+    assert abs(ob.mps_overlap(N, N) - 1) < 1e-13
+    tau = ob.identity_trace(N, 3)
+    assert abs(tau.imag) < 1e-13 * abs(tau) and tau.real > 0
+    # same state up to the phase
+    assert abs(abs(ob.mps_overlap(N, M)) ** 2 - ob.mps_overlap(M, M).real) < 1e-10 * ob.mps_overlap(M, M).real
+
+
+def test_residual_is_mean_squared_message_distance():
+    """r_l = mean over messages of ||m^l - m^{l-1}||^2 of the normalised messages
+    (the mean-square reading of the stop rule), checked with dense vectors."""
+    T = I.uniform_noise_peps(4, 4, 2, 2, seed=1)
+    lat = ob.Lattice(4, 4, 2, 2, 2, 2, T, chi=16, fit_tol=0.0, fit_max_sweeps=2)
+    lat.sweep()
+    old = {k: X.dense_mps(v) for k, v in lat.msgs.items()}
+    r = lat.sweep()
+    new = {k: X.dense_mps(v) for k, v in lat.msgs.items()}
+    want = np.mean([np.linalg.norm(new[k] - old[k]) ** 2 for k in old])
+    assert abs(r - want) < 1e-13 and r > 1e-6

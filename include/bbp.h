@@ -1,0 +1,154 @@
+/*
+ * bbp.h -- C ABI of the GB300 block belief propagation (blockBP) library.
+ *
+ * Method: Guo, Poletti & Arad, "Block belief propagation algorithm for
+ * two-dimensional tensor networks" (arXiv:2301.05844).  The library runs the
+ * data-parallel part of blockBP on one GPU: the double-layer build (Fig. 1(a,b)),
+ * the synchronous block-message update of Eq. 1 by boundary-MPS contraction with
+ * the variational zip-up fit of App. A (Eq. "update", the A/B environment
+ * recurrences, QR/LQ truncation), message normalisation and the fixed-point
+ * residual (Sec. "The blockBP algorithm", stop rule; App. A, stop rule), and the
+ * expectation-value read-out from a block and its converged incoming messages
+ * (App. A, chi = 2D^2+10 read-out; Fig. 1(f)).
+ *
+ * Conventions shared by every call
+ *   - PEPS site tensor T[p][u][l][d][r] (physical, up, left, down, right), C order.
+ *     With open boundaries the legs on the lattice edge have dimension 1
+ *     (Sec. "The blockBP algorithm": an OBC PEPS is a PBC PEPS with bond 1 on the
+ *     boundary).  Complex data is interleaved (re, im).
+ *   - Sites are numbered row-major, s = r*Lx + c (r = row, c = column).
+ *   - All functions return BBP_OK (0), a positive warning, or a negative error
+ *     code; on error bbp_last_error() holds a message for the calling thread.
+ *     No C++ exception crosses this boundary.
+ *   - Calls on one handle are not thread-safe; different handles are independent.
+ *   - Device memory is allocated by the library at bbp_create_lattice (one arena
+ *     per handle) and released by bbp_destroy; caller buffers are never retained.
+ */
+#ifndef BBP_H
+#define BBP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Return codes. */
+#define BBP_OK 0
+#define BBP_NOT_CONVERGED 1 /* max_sweeps reached; results are still valid      */
+#define BBP_ERR_INVALID (-1) /* bad argument, dimensions or term geometry         */
+#define BBP_ERR_OOM (-2)     /* device allocation failed                          */
+#define BBP_ERR_CUDA (-3)    /* a CUDA runtime call failed                        */
+#define BBP_ERR_TIMEOUT (-4) /* a device wait exceeded its bound                  */
+#define BBP_ERR_NUMERIC (-5) /* NaN/Inf or a message of zero norm                 */
+#define BBP_ERR_STATE (-6)   /* call out of order (e.g. sweep before set_tensors) */
+
+typedef struct bbp_lattice bbp_lattice; /* opaque; owned by the caller until bbp_destroy */
+
+typedef enum { BBP_OBC = 0, BBP_INFINITE = 1 } bbp_boundary;
+/* Element type of the tensors passed to bbp_set_tensors. */
+typedef enum { BBP_F64 = 0, BBP_C128 = 1, BBP_F32 = 2, BBP_C64 = 3 } bbp_dtype;
+/* Arithmetic of the contractions.  FP64: every step in FP64 on the GPU.  TF32 and
+ * BF16: the site-update contractions on tensor cores with FP32 accumulation, while
+ * the QR/LQ truncation, message normalisation, residual and read-out ratios stay FP64. */
+typedef enum { BBP_PREC_FP64 = 0, BBP_PREC_TF32 = 1, BBP_PREC_BF16 = 2 } bbp_prec;
+
+typedef struct {
+    int Lx, Ly;              /* OBC: lattice columns, rows.  INFINITE: unit cell columns, rows */
+    int boundary;            /* bbp_boundary */
+    int d, D;                /* physical and virtual bond dimension */
+    int bx, by;              /* block columns, rows.  OBC: must divide Lx, Ly.
+                                INFINITE: multiples of the unit cell (one block, Sec. "The
+                                blockBP algorithm": the block messages itself) */
+    int chi;                 /* message bond chi_m (Sec. "The blockBP algorithm", default D^2) */
+    int chi_exp;             /* read-out bond; <= 0 selects max(chi, 2 D^2 + 10) (App. A) */
+    int dtype;               /* bbp_dtype of the input tensors */
+    int prec;                /* bbp_prec */
+    double tol;              /* residual tolerance (main text: 1e-5) */
+    int max_sweeps;          /* cap on sweeps when running to tolerance (10) */
+    int stop_relative;       /* 0: residual < tol (main text); 1: r_l / r_1 < tol (App. A) */
+    double fit_tol;          /* zip-up fit: std/|mean| of -||Yt||^2 over a sweep (App. A: 1e-6) */
+    int fit_max_sweeps;      /* zip-up fit sweep cap (App. A: 10) */
+    unsigned long long seed; /* counter-based generator key (fit initial states, init_mode 1) */
+    int init_mode;           /* 0: identity-product messages; 1: random MPDO (App. A) */
+    void* stream;            /* cudaStream_t for all work; NULL = library-owned stream */
+} bbp_lattice_desc;
+
+/* Validate desc, allocate the device arena (double layer, message store, work
+ * buffers) and plan one sweep.  *out receives the handle.  Errors: INVALID, OOM, CUDA. */
+int bbp_create_lattice(const bbp_lattice_desc* desc, bbp_lattice** out);
+
+/* Upload every site tensor and build the double-layer network (Fig. 1(a,b)).
+ * data: OBC -> Lx*Ly tensors in row-major site order; INFINITE -> Lx*Ly unit-cell
+ * tensors.  Each tensor T[p][u][l][d][r] in C order with the OBC edge legs of
+ * dimension 1, element type desc->dtype, concatenated without padding.
+ * on_device != 0: data is a device pointer (read on the handle's stream).
+ * The library copies; the caller keeps ownership.  Resets the messages to their
+ * initial state.  Errors: INVALID (NULL data), CUDA. */
+int bbp_set_tensors(bbp_lattice* lat, const void* data, int on_device);
+
+/* Synchronous message sweeps, Eq. 1: every block message of sweep l+1 is computed
+ * from the messages of sweep l.  n_sweeps > 0 runs exactly that many; n_sweeps <= 0
+ * runs until the residual meets desc->tol (absolute or relative) or max_sweeps.
+ * residual_out (may be NULL): last residual, the mean over messages of
+ * ||m^l - m^{l-1}||^2 of the unit-norm, phase-fixed messages.  sweeps_done (may be
+ * NULL): sweeps run by this call.  Returns OK, NOT_CONVERGED, STATE (no tensors),
+ * NUMERIC, TIMEOUT or CUDA. */
+int bbp_sweep(bbp_lattice* lat, int n_sweeps, double* residual_out, int* sweeps_done);
+
+/* One expectation-value term: a product of nsite (1 or 2) single-site d x d
+ * operators, row-major, real and imaginary parts (op_im may be NULL).
+ * OBC sites are lattice sites; INFINITE sites index the bx x by block (row-major). */
+typedef struct {
+    int nsite;
+    int site[2];
+    const double* op_re[2];
+    const double* op_im[2];
+} bbp_term;
+
+/* <O> = N_O / N_I for each term, read from its block and the block's converged
+ * incoming messages with bond chi_exp (App. A; Fig. 1(f)).  Two sites must lie in
+ * one block, or be nearest neighbours in adjacent blocks (then read from the merged
+ * two-block region whose outer messages are joined by a bond of dimension 1), and
+ * span at most two adjacent columns of their region.  out_re/out_im: n_terms
+ * doubles each (host memory; out_im may be NULL).  Errors: INVALID, STATE, CUDA. */
+int bbp_expect(bbp_lattice* lat, const bbp_term* terms, int n_terms, double* out_re, double* out_im);
+
+/* Free the handle and its device arena.  NULL is a no-op. */
+void bbp_destroy(bbp_lattice* lat);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char* bbp_last_error(void);
+
+/* ---- inspection, checkpoint / resume ------------------------------------------- */
+
+/* Outgoing message of block `block` (row-major block index) toward direction dir
+ * (0 left, 1 right, 2 up, 3 down).  nsites/bonds (may be NULL) receive the site
+ * count and the nsites+1 bond dimensions; the message has physical dimension D^2.
+ * If out != NULL the sites are written in order, each [a][k][b] in C order, as
+ * doubles (complex interleaved).  Errors: INVALID (no such message), STATE. */
+int bbp_get_message(bbp_lattice* lat, int block, int dir, int* nsites, int* bonds, double* out);
+
+/* Replace that message (same layout as bbp_get_message); for checkpoint / resume. */
+int bbp_set_message(bbp_lattice* lat, int block, int dir, const double* in);
+
+typedef struct {
+    double flops;            /* algorithmic site-update flops executed (see DESIGN) */
+    double qr_flops;         /* FP64 QR/LQ flops executed */
+    long long kernels;       /* kernel launches issued by the library */
+    long long fit_sweeps;    /* zip-up fit sweeps executed, summed over fits */
+    long long fits;          /* zip-up fits executed */
+    int sweeps;              /* message sweeps executed since set_tensors */
+    double last_residual;
+    double first_residual;
+} bbp_stats;
+
+/* Counters since bbp_set_tensors (flops are counted on the host from the planned
+ * shapes; fit sweeps are read back from the device). */
+int bbp_get_stats(bbp_lattice* lat, bbp_stats* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BBP_H */

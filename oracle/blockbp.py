@@ -126,18 +126,30 @@ def lq_q(M: np.ndarray) -> np.ndarray:
 # Variational MPO x MPS fit (App. A, Eq. "distance" and Eq. "update", Fig. S1).
 # --------------------------------------------------------------------------------------
 def site_update(A, O, X, B):
-    """Eq. (update): Yt[y,q,y'] = sum A[y,w,x] X[x,p,x'] O[w,p,q,w'] B[y',w',x']."""
-    return np.einsum("ywx,xpX,wpqW,YWX->yqY", A, X, O, B, optimize=True)
+    """Eq. (update): Yt[y,q,y'] = sum A[y,w,x] X[x,p,x'] O[w,p,q,w'] B[y',w',x'].
+
+    Evaluated as three pairwise tensordot contractions (x, then w and p, then x' and w')."""
+    t = np.tensordot(A, X, axes=([2], [0]))              # [y, w, p, x']
+    t = np.tensordot(t, O, axes=([1, 2], [0, 1]))        # [y, x', q, w']
+    return np.tensordot(t, B, axes=([1, 3], [2, 1]))     # [y, q, y']
 
 
 def env_left(A, Y, O, X):
-    """Left-environment recurrence of App. A: A_{l+1} from A_l (conj on the fitted Y)."""
-    return np.einsum("ywx,yqY,wpqW,xpX->YWX", A, np.conj(Y), O, X, optimize=True)
+    """Left-environment recurrence of App. A: A_{l+1}[y',w',x'] =
+    sum A_l[y,w,x] conj(Y[y,q,y']) O[w,p,q,w'] X[x,p,x']."""
+    t = np.tensordot(A, X, axes=([2], [0]))              # [y, w, p, x']
+    t = np.tensordot(t, O, axes=([1, 2], [0, 1]))        # [y, x', q, w']
+    t = np.tensordot(np.conj(Y), t, axes=([0, 1], [0, 2]))  # [y', x', w']
+    return t.transpose(0, 2, 1)
 
 
 def env_right(B, Y, O, X):
-    """Right-environment recurrence of App. A: B_l from B_{l+1} (conj on the fitted Y)."""
-    return np.einsum("yqY,wpqW,xpX,YWX->ywx", np.conj(Y), O, X, B, optimize=True)
+    """Right-environment recurrence of App. A: B_l[y,w,x] =
+    sum conj(Y[y,q,y']) O[w,p,q,w'] X[x,p,x'] B_{l+1}[y',w',x']."""
+    t = np.tensordot(X, B, axes=([2], [2]))              # [x, p, y', w']
+    t = np.tensordot(t, O, axes=([1, 3], [1, 3]))        # [x, y', w, q]
+    t = np.tensordot(np.conj(Y), t, axes=([1, 2], [3, 1]))  # [y, x, w]
+    return t.transpose(0, 2, 1)
 
 
 def bond_caps(phys, chi):
@@ -212,7 +224,8 @@ def mps_overlap(M1, M2):
     """<M1|M2> for two MPS with equal physical dims (conj on M1)."""
     t = np.ones((1, 1), dtype=np.result_type(M1[0], M2[0]))
     for a, b in zip(M1, M2):
-        t = np.einsum("ab,akc,bkd->cd", t, np.conj(a), b)
+        t = np.tensordot(t, np.conj(a), axes=([0], [0]))      # [b_, k, c]
+        t = np.tensordot(t, b, axes=([0, 1], [0, 1]))         # [c, d]
     return t[0, 0]
 
 
@@ -607,14 +620,14 @@ class Lattice:
         if len(cs) == 1:
             F = np.ones((1, 1, 1), dtype=np.complex128)
             for i in range(h + 2):
-                G = np.einsum("awb,asA->wbsA", F, L[i])
-                G = np.einsum("wbsA,wsvt->bAvt", G, colops[0][i])
-                F = np.einsum("bAvt,btB->AvB", G, R[i])
+                G = np.tensordot(F, L[i], axes=([0], [0]))               # [w, b, s, A]
+                G = np.tensordot(G, colops[0][i], axes=([0, 2], [0, 1]))  # [b, A, v, t]
+                F = np.tensordot(G, R[i], axes=([0, 3], [0, 1]))          # [A, v, B]
             return F[0, 0, 0]
         F = np.ones((1, 1, 1, 1), dtype=np.complex128)
         for i in range(h + 2):
-            G = np.einsum("awzb,asA->wzbsA", F, L[i])
-            G = np.einsum("wzbsA,wsvm->zbAvm", G, colops[0][i])
-            G = np.einsum("zbAvm,zmyt->bAvyt", G, colops[1][i])
-            F = np.einsum("bAvyt,btB->AvyB", G, R[i])
+            G = np.tensordot(F, L[i], axes=([0], [0]))                   # [w, z, b, s, A]
+            G = np.tensordot(G, colops[0][i], axes=([0, 3], [0, 1]))      # [z, b, A, v, m]
+            G = np.tensordot(G, colops[1][i], axes=([0, 4], [0, 1]))      # [b, A, v, y, t]
+            F = np.tensordot(G, R[i], axes=([0, 4], [0, 1]))              # [A, v, y, B]
         return F[0, 0, 0, 0]

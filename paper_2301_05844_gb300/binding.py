@@ -1,0 +1,176 @@
+"""ctypes binding of libbbp.so (the C ABI in include/bbp.h).
+
+Argument marshalling only: every step of blockBP runs in the CUDA library.  The raw
+functions keep their C names (``lib().bbp_sweep`` ...); ``Lattice`` wraps a handle.
+``lib()`` raises if the library has not been built: there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libbbp.so")
+
+OK, NOT_CONVERGED = 0, 1
+ERR_INVALID, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_NUMERIC, ERR_STATE = -1, -2, -3, -4, -5, -6
+OBC, INFINITE = 0, 1
+F64, C128, F32, C64 = 0, 1, 2, 3
+PREC_FP64, PREC_TF32, PREC_BF16 = 0, 1, 2
+LEFT, RIGHT, UP, DOWN = 0, 1, 2, 3
+
+_NP_DTYPE = {F64: np.float64, C128: np.complex128, F32: np.float32, C64: np.complex64}
+_PREC = {"fp64": PREC_FP64, "tf32": PREC_TF32, "bf16": PREC_BF16}
+
+
+class Desc(C.Structure):
+    _fields_ = [
+        ("Lx", C.c_int), ("Ly", C.c_int), ("boundary", C.c_int), ("d", C.c_int), ("D", C.c_int),
+        ("bx", C.c_int), ("by", C.c_int), ("chi", C.c_int), ("chi_exp", C.c_int),
+        ("dtype", C.c_int), ("prec", C.c_int), ("tol", C.c_double), ("max_sweeps", C.c_int),
+        ("stop_relative", C.c_int), ("fit_tol", C.c_double), ("fit_max_sweeps", C.c_int),
+        ("seed", C.c_ulonglong), ("init_mode", C.c_int), ("stream", C.c_void_p),
+    ]
+
+
+class Term(C.Structure):
+    _fields_ = [
+        ("nsite", C.c_int), ("site", C.c_int * 2),
+        ("op_re", C.POINTER(C.c_double) * 2), ("op_im", C.POINTER(C.c_double) * 2),
+    ]
+
+
+class Stats(C.Structure):
+    _fields_ = [
+        ("flops", C.c_double), ("qr_flops", C.c_double), ("kernels", C.c_longlong),
+        ("fit_sweeps", C.c_longlong), ("fits", C.c_longlong), ("sweeps", C.c_int),
+        ("last_residual", C.c_double), ("first_residual", C.c_double),
+    ]
+
+
+_lib = None
+
+
+def lib():
+    """Load libbbp.so (raises FileNotFoundError if it was not built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise FileNotFoundError(f"{LIB_PATH} is missing: run __graft_entry__.build() first")
+    L = C.CDLL(LIB_PATH)
+    P = C.c_void_p
+    L.bbp_create_lattice.argtypes = [C.POINTER(Desc), C.POINTER(P)]
+    L.bbp_set_tensors.argtypes = [P, P, C.c_int]
+    L.bbp_sweep.argtypes = [P, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_int)]
+    L.bbp_expect.argtypes = [P, C.POINTER(Term), C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)]
+    L.bbp_destroy.argtypes = [P]
+    L.bbp_destroy.restype = None
+    L.bbp_last_error.restype = C.c_char_p
+    L.bbp_get_message.argtypes = [P, C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_double)]
+    L.bbp_set_message.argtypes = [P, C.c_int, C.c_int, C.POINTER(C.c_double)]
+    L.bbp_get_stats.argtypes = [P, C.POINTER(Stats)]
+    _lib = L
+    return L
+
+
+class BBPError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"bbp error {code}: {msg}")
+        self.code = code
+
+
+def _check(rc):
+    if rc < 0:
+        raise BBPError(rc, lib().bbp_last_error().decode())
+    return rc
+
+
+def make_desc(Lx, Ly, d, D, bx, by, chi, boundary="obc", chi_exp=0, dtype=F64, prec="fp64", tol=1e-5,
+              max_sweeps=10, stop_relative=0, fit_tol=1e-6, fit_max_sweeps=10, seed=0, init_mode=0, stream=None):
+    return Desc(Lx, Ly, OBC if boundary == "obc" else INFINITE, d, D, bx, by, chi, chi_exp, dtype,
+                _PREC[prec] if isinstance(prec, str) else prec, tol, max_sweeps, stop_relative, fit_tol,
+                fit_max_sweeps, seed, init_mode, stream)
+
+
+class Lattice:
+    """Owning wrapper of a bbp_lattice handle."""
+
+    def __init__(self, **kw):
+        self.desc = make_desc(**kw)
+        self.h = C.c_void_p()
+        _check(lib().bbp_create_lattice(C.byref(self.desc), C.byref(self.h)))
+
+    def close(self):
+        if self.h:
+            lib().bbp_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_tensors(self, tensors=None, device_ptr=None):
+        """tensors: list of numpy arrays T[p,u,l,d,r] (cast to the desc dtype), or
+        device_ptr: address of the same data already on the GPU."""
+        if device_ptr is not None:
+            return _check(lib().bbp_set_tensors(self.h, C.c_void_p(device_ptr), 1))
+        dt = _NP_DTYPE[self.desc.dtype]
+        flat = np.concatenate([np.ascontiguousarray(t, dtype=dt).reshape(-1) for t in tensors])
+        self._host = flat
+        return _check(lib().bbp_set_tensors(self.h, flat.ctypes.data_as(C.c_void_p), 0))
+
+    def sweep(self, n=0):
+        r = C.c_double()
+        k = C.c_int()
+        rc = _check(lib().bbp_sweep(self.h, n, C.byref(r), C.byref(k)))
+        return r.value, k.value, rc
+
+    def expect(self, terms):
+        """terms: list of [(site, op), ...] with d x d numpy operators."""
+        n = len(terms)
+        arr = (Term * n)()
+        keep = []
+        for i, term in enumerate(terms):
+            arr[i].nsite = len(term)
+            for k, (s, op) in enumerate(term):
+                op = np.asarray(op)
+                re = np.ascontiguousarray(op.real, dtype=np.float64)
+                im = np.ascontiguousarray(op.imag, dtype=np.float64) if np.iscomplexobj(op) else None
+                keep += [re, im]
+                arr[i].site[k] = s
+                arr[i].op_re[k] = re.ctypes.data_as(C.POINTER(C.c_double))
+                arr[i].op_im[k] = im.ctypes.data_as(C.POINTER(C.c_double)) if im is not None else None
+        out_re = np.zeros(n)
+        out_im = np.zeros(n)
+        _check(lib().bbp_expect(self.h, arr, n, out_re.ctypes.data_as(C.POINTER(C.c_double)),
+                                out_im.ctypes.data_as(C.POINTER(C.c_double))))
+        return out_re + 1j * out_im
+
+    def get_message(self, block, direction):
+        ns = C.c_int()
+        bonds = (C.c_int * 64)()
+        _check(lib().bbp_get_message(self.h, block, direction, C.byref(ns), bonds, None))
+        b = [bonds[i] for i in range(ns.value + 1)]
+        K = self.desc.D ** 2
+        cplx = self.desc.dtype in (C128, C64)
+        total = sum(b[i] * K * b[i + 1] for i in range(ns.value)) * (2 if cplx else 1)
+        buf = np.zeros(total)
+        _check(lib().bbp_get_message(self.h, block, direction, None, None, buf.ctypes.data_as(C.POINTER(C.c_double))))
+        if cplx:
+            buf = buf[0::2] + 1j * buf[1::2]
+        out, o = [], 0
+        for i in range(ns.value):
+            n = b[i] * K * b[i + 1]
+            out.append(buf[o:o + n].reshape(b[i], K, b[i + 1]))
+            o += n
+        return out
+
+    def stats(self):
+        s = Stats()
+        _check(lib().bbp_get_stats(self.h, C.byref(s)))
+        return {f: getattr(s, f) for f, _ in Stats._fields_}

@@ -1,0 +1,145 @@
+// Internal declarations shared by the blockBP CUDA kernels and the host engine.
+//
+// Every grouped kernel takes a device array of task descriptors; one launch runs
+// the same step (for example "left-to-right site update, step 2") for every
+// message being computed in the sweep, each with its own pointers and shapes.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace bbp {
+
+// Strided two-level contraction  C[m][n] (+)= sum_k op(A)[m][k] * B[k][n]
+// with m = m1*M2 + m2, n = n1*N2 + n2, k = k1*K2 + k2 and an arbitrary element
+// stride for each of the six sub-indices of A and B and four of C.  Every
+// contraction of the zip-up fit (Eq. "update", the A/B recurrences), of the MPS
+// overlaps and of the read-out closing is one of these.
+struct GTask {
+    const void* A;
+    const void* B;
+    void* C;
+    int M1, M2, N1, N2, K1, K2;
+    long long a_m1, a_m2, a_k1, a_k2;
+    long long b_k1, b_k2, b_n1, b_n2;
+    long long c_m1, c_m2, c_n1, c_n2;
+    int conjA;       // complex: use conj(A)
+    int accumulate;  // 1: C += result, 0: C = result
+    const int* active;  // task skipped when *active == 0 (nullptr: always runs)
+    int pad;
+};
+
+// Householder QR of an m x n matrix (m >= n) read with element (i, j) at
+// in[i*in_rs + j*in_cs] (conjugated if conj_io); writes the thin Q, columns scaled
+// so that diag(R) is real non-negative, to out[i*out_rs + j*out_cs] (conjugated
+// if conj_io).  conj_io with transposed strides turns this into the LQ of the
+// right-to-left half sweep.  Also writes -||in||^2 (the fit loss of App. A).
+struct QRTask {
+    const void* in;
+    void* out;
+    void* work;      // 2*m*n elements of scratch
+    double* loss;    // may be nullptr
+    const int* active;
+    int m, n;
+    long long in_rs, in_cs, out_rs, out_cs;
+    int conj_io;
+    int pad;
+};
+
+// Fill n scalars (2n doubles if complex) with the counter-based uniforms in [-1,1).
+struct RandTask {
+    void* ptr;
+    long long n;
+    unsigned long long stream;
+    int* active;  // if set, the fit's active flag is reset to 1
+};
+
+// One zip-up fit's convergence check after a sweep (App. A stop rule).
+struct CheckTask {
+    const double* losses;  // count values of this sweep
+    int* active;
+    int* counter;          // incremented for every sweep that ran (fit sweeps executed)
+    int count;
+    int pad;
+};
+
+// Scale an array by 1/||.||_F (the fitted column MPS in mixed canonical form).
+struct ScaleTask {
+    void* ptr;
+    long long n;
+};
+
+// Message assembly: sites 1..nsites of the final column MPS into the message slot,
+// the two corner scalars multiplied into the first site.
+struct AssembleTask {
+    const void* src[16];   // column MPS sites 1..nsites (contiguous [a][k][b])
+    void* dst[16];         // message sites (contiguous [a][k][b])
+    long long size[16];
+    const void* corner0;   // 1x1x1
+    const void* corner1;   // 1x1x1
+    int nsites;
+    int pad;
+};
+
+// Message normalisation and residual term: uses <m|m> and <m|m_old> from the
+// overlap chains, the identity trace tau (computed here), scales site 0 of the
+// message by conj(tau)/|tau|/||m|| and writes ||m_hat - m_old||^2.
+struct NormTask {
+    void* site0;
+    long long size0;
+    const void* sites[16];
+    int a[16], k[16], b[16];
+    int nsites, D;
+    const void* mm;      // <m|m> (1 scalar)
+    const void* mo;      // <m|m_old> (1 scalar)
+    double* resid;       // output term
+    int* status;         // set nonzero on a zero or non-finite norm
+};
+
+// Double layer E[(u u'),(l l'),(d d'),(r r')] = sum_{p,p'} O[p',p] T[p,u,l,d,r] conj(T[p',...]).
+struct DLTask {
+    const void* T;   // [d][Du][Dl][Dd][Dr]
+    void* E;         // [Du^2][Dl^2][Dd^2][Dr^2]
+    const void* O;   // d x d row-major (nullptr: identity)
+    int d, Du, Dl, Dd, Dr;
+    int pad;
+};
+
+// Two neighbouring column operators of one row fused over their shared horizontal
+// leg m (read-out of a horizontal pair):
+//   out[(u1 u2)][l1][(d1 d2)][r2] = sum_m A[u1][l1][d1][m] B[u2][m][d2][r2]
+// with A, B given as strided 4-leg views (u, l, d, r); out is contiguous.
+struct FuseTask {
+    const void* A;
+    const void* B;
+    void* out;
+    int u1, l1, d1, m, u2, d2, r2;
+    int pad;
+    long long a_u, a_l, a_d, a_r;
+    long long b_u, b_l, b_d, b_r;
+};
+
+// Launchers (kernels.cu).  cplx selects double2 (complex) over double.
+cudaError_t launch_gcontract(const GTask* d_tasks, int ntasks, int max_tiles, bool cplx, cudaStream_t s);
+cudaError_t qr_prepare(int max_m, bool cplx);  // sets the dynamic shared memory limit once
+cudaError_t launch_qr(const QRTask* d_tasks, int ntasks, int max_m, bool cplx, cudaStream_t s);
+// sweep_ctr != nullptr: the current sweep index is OR-ed into bits 36.. of each stream.
+cudaError_t launch_rand(const RandTask* d_tasks, int ntasks, unsigned long long seed, const int* sweep_ctr,
+                        bool cplx, cudaStream_t s);
+cudaError_t launch_set_int(int* p, int n, int v, cudaStream_t s);
+cudaError_t launch_add_int(int* p, int v, cudaStream_t s);
+cudaError_t launch_check(const CheckTask* d_tasks, int ntasks, double tol, cudaStream_t s);
+cudaError_t launch_scale(const ScaleTask* d_tasks, int ntasks, bool cplx, int* status, cudaStream_t s);
+cudaError_t launch_assemble(const AssembleTask* d_tasks, int ntasks, bool cplx, cudaStream_t s);
+cudaError_t launch_normalise(const NormTask* d_tasks, int ntasks, bool cplx, cudaStream_t s);
+cudaError_t launch_mean(const double* in, int n, double* out, cudaStream_t s);
+cudaError_t launch_double_layer(const DLTask* d_tasks, int ntasks, long long max_out, bool cplx, cudaStream_t s);
+cudaError_t launch_convert(const void* in, int in_dtype, void* out, long long n, bool cplx_out, cudaStream_t s);
+cudaError_t launch_copy(const void* in, void* out, long long bytes, cudaStream_t s);
+cudaError_t launch_fuse(const FuseTask* d_tasks, int ntasks, long long max_out, bool cplx, cudaStream_t s);
+
+// Host-side SplitMix64 (same definition as the device one) for host-drawn values.
+uint64_t splitmix64(uint64_t z);
+double uniform_pm1(uint64_t seed, uint64_t stream, uint64_t idx);
+
+}  // namespace bbp

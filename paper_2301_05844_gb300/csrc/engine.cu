@@ -1,0 +1,621 @@
+// Host engine of the blockBP library: geometry of blocks and frames, the lockstep
+// planner that turns every message update of a sweep into grouped launches, the
+// device arena, CUDA-graph capture of one sweep, and the C ABI of include/bbp.h.
+//
+// One sweep (Eq. 1) is planned once: every outgoing block message is an "item";
+// all items advance together through the columns of their block (App. A: bMPS
+// column by column, right to left in the rotated frame), each column being a
+// zip-up fit (App. A) whose site updates, QR/LQ steps and environment updates are
+// one grouped launch per step across all items.  The whole sweep is captured in a
+// CUDA graph and replayed.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <new>
+#include <string>
+#include <type_traits>
+#include <vector>
+
+#include "bbp.h"
+#include "bbp_internal.h"
+#include "engine.h"
+#include "plan.h"
+
+namespace bbp {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+    g_err = msg;
+    return code;
+}
+
+int bond_cap(const std::vector<int>& phys, int i, int chi) {
+    // bond between site i-1 and i of an MPS with physical dims phys
+    if (i <= 0 || i >= (int)phys.size()) return 1;
+    double left = 1, right = 1;
+    for (int j = 0; j < i; ++j) left *= phys[j];
+    for (int j = i; j < (int)phys.size(); ++j) right *= phys[j];
+    double b = std::min((double)chi, std::min(left, right));
+    return (int)b;
+}
+std::vector<int> bond_caps(const std::vector<int>& phys, int chi) {
+    std::vector<int> b(phys.size() + 1);
+    for (size_t i = 0; i <= phys.size(); ++i) b[i] = bond_cap(phys, (int)i, chi);
+    return b;
+}
+
+uint64_t stream_id(uint64_t tag, uint64_t outer, uint64_t msg, uint64_t col, uint64_t site) {
+    return (tag << 56) | (outer << 36) | (msg << 16) | (col << 8) | site;
+}
+
+// ------------------------------------------------------------------ program recording
+size_t Program::arena_alloc(size_t bytes) {
+    size_t off = (arena_used + 255) & ~(size_t)255;
+    arena_used = off + ((bytes + 15) & ~(size_t)15);
+    allocs.push_back({off, bytes});
+    return off;
+}
+
+// ------------------------------------------------------------------ host-side bounds check
+namespace {
+struct Checker {
+    const Program& pr;
+    int ss;
+    std::string err;
+    bool inside(const std::vector<std::pair<size_t, size_t>>& a, size_t lo, size_t hi) const {
+        // a is sorted by offset (allocation order)
+        size_t l = 0, r = a.size();
+        while (l < r) {
+            size_t m = (l + r) / 2;
+            if (a[m].first <= lo) l = m + 1;
+            else r = m;
+        }
+        if (l == 0) return false;
+        const auto& b = a[l - 1];
+        return lo >= b.first && hi <= b.first + b.second;
+    }
+    void range(const void* p, long long extent_elems, int elem_bytes, const char* what, size_t task) {
+        if (!err.empty() || !p) return;
+        const size_t lo = (size_t)(uintptr_t)p, hi = lo + (size_t)extent_elems * elem_bytes;
+        bool ok;
+        if (lo < pr.split || !pr.parent) ok = inside(lo < pr.split && pr.parent ? pr.parent->allocs : pr.allocs, lo, hi);
+        else ok = inside(pr.allocs, lo, hi);
+        if (!ok) err = std::string(what) + " of task " + std::to_string(task) + " leaves its buffer";
+    }
+};
+long long ext2(long long n1, long long s1, long long n2, long long s2) { return (n1 - 1) * s1 + (n2 - 1) * s2; }
+}  // namespace
+
+std::string Program::validate() const {
+    Checker c{*this, cplx ? 16 : 8, ""};
+    const int ss = c.ss;
+    for (size_t i = 0; i < gc.size(); ++i) {
+        const GTask& t = gc[i];
+        if (t.M1 < 1 || t.M2 < 1 || t.N1 < 1 || t.N2 < 1 || t.K1 < 1 || t.K2 < 1) return "empty contraction " + std::to_string(i);
+        c.range(t.A, ext2(t.M1, t.a_m1, t.M2, t.a_m2) + ext2(t.K1, t.a_k1, t.K2, t.a_k2) + 1, ss, "A", i);
+        c.range(t.B, ext2(t.K1, t.b_k1, t.K2, t.b_k2) + ext2(t.N1, t.b_n1, t.N2, t.b_n2) + 1, ss, "B", i);
+        c.range(t.C, ext2(t.M1, t.c_m1, t.M2, t.c_m2) + ext2(t.N1, t.c_n1, t.N2, t.c_n2) + 1, ss, "C", i);
+        c.range(t.active, 1, 4, "active", i);
+    }
+    for (size_t i = 0; i < qr.size(); ++i) {
+        const QRTask& t = qr[i];
+        if (t.n > 512 || t.m < t.n) return "QR shape out of range in task " + std::to_string(i);
+        c.range(t.in, ext2(t.m, t.in_rs, t.n, t.in_cs) + 1, ss, "QR in", i);
+        c.range(t.out, ext2(t.m, t.out_rs, t.n, t.out_cs) + 1, ss, "QR out", i);
+        c.range(t.work, 2LL * t.m * t.n, ss, "QR work", i);
+        c.range(t.loss, 1, 8, "QR loss", i);
+        c.range(t.active, 1, 4, "QR active", i);
+    }
+    for (size_t i = 0; i < rnd.size(); ++i) {
+        c.range(rnd[i].ptr, rnd[i].n, ss, "rand", i);
+        c.range(rnd[i].active, 1, 4, "rand active", i);
+    }
+    for (size_t i = 0; i < chk.size(); ++i) {
+        c.range(chk[i].losses, chk[i].count, 8, "losses", i);
+        c.range(chk[i].active, 1, 4, "check active", i);
+        c.range(chk[i].counter, 1, 4, "counter", i);
+    }
+    for (size_t i = 0; i < scl.size(); ++i) c.range(scl[i].ptr, scl[i].n, ss, "scale", i);
+    for (size_t i = 0; i < asmb.size(); ++i) {
+        const AssembleTask& t = asmb[i];
+        for (int s = 0; s < t.nsites; ++s) {
+            c.range(t.src[s], t.size[s], ss, "assemble src", i);
+            c.range(t.dst[s], t.size[s], ss, "assemble dst", i);
+        }
+        c.range(t.corner0, 1, ss, "corner", i);
+        c.range(t.corner1, 1, ss, "corner", i);
+    }
+    for (size_t i = 0; i < nrm.size(); ++i) {
+        const NormTask& t = nrm[i];
+        c.range(t.site0, t.size0, ss, "norm site0", i);
+        for (int s = 0; s < t.nsites; ++s) {
+            if (t.b[s] > 1024 || t.a[s] > 1024) return "message bond above 1024";
+            c.range(t.sites[s], (long long)t.a[s] * t.k[s] * t.b[s], ss, "norm site", i);
+        }
+        c.range(t.mm, 1, ss, "mm", i);
+        c.range(t.mo, 1, ss, "mo", i);
+        c.range(t.resid, 1, 8, "resid", i);
+    }
+    for (size_t i = 0; i < fus.size(); ++i) {
+        const FuseTask& t = fus[i];
+        c.range(t.A, (t.u1 - 1) * t.a_u + (t.l1 - 1) * t.a_l + (t.d1 - 1) * t.a_d + (t.m - 1) * t.a_r + 1, ss, "fuse A", i);
+        c.range(t.B, (t.u2 - 1) * t.b_u + (t.m - 1) * t.b_l + (t.d2 - 1) * t.b_d + (t.r2 - 1) * t.b_r + 1, ss, "fuse B", i);
+        c.range(t.out, (long long)t.u1 * t.u2 * t.l1 * t.d1 * t.d2 * t.r2, ss, "fuse out", i);
+    }
+    for (size_t i = 0; i < dl.size(); ++i) {
+        const DLTask& t = dl[i];
+        const long long vol = (long long)t.Du * t.Dl * t.Dd * t.Dr;
+        c.range(t.T, t.d * vol, ss, "DL T", i);
+        c.range(t.E, vol * vol, ss, "DL E", i);
+        c.range(t.O, (long long)t.d * t.d, ss, "DL O", i);
+    }
+    for (size_t i = 0; i < steps.size(); ++i) {
+        const Step& s = steps[i];
+        if (s.kind == ST_COPY) {
+            c.range(s.p0, s.n, 1, "copy src", i);
+            c.range(s.p1, s.n, 1, "copy dst", i);
+            if (s.n % 16) return "copy size not a multiple of 16 bytes";
+        }
+        if (s.kind == ST_MEAN) {
+            c.range(s.p0, s.n, 8, "mean in", i);
+            c.range(s.p1, 1, 8, "mean out", i);
+        }
+        if (s.kind == ST_INC) c.range(s.p0, 1, 4, "counter", i);
+    }
+    return c.err;
+}
+
+void Program::gc_step(std::vector<GTask>& ts) {
+    if (ts.empty()) return;
+    Step s;
+    s.kind = ST_GC;
+    s.first = gc.size();
+    s.count = (int)ts.size();
+    int mt = 1;
+    for (auto& t : ts) {
+        const long long M = (long long)t.M1 * t.M2, N = (long long)t.N1 * t.N2, K = (long long)t.K1 * t.K2;
+        const int tiles = (int)(((M + 63) / 64) * ((N + 63) / 64));
+        mt = std::max(mt, tiles);
+        const double f = 2.0 * (double)M * (double)N * (double)K * (cplx ? 4.0 : 1.0);
+        if (t.active) gated_flops += f;
+        else static_flops += f;
+        gc.push_back(t);
+    }
+    s.aux = mt;
+    steps.push_back(s);
+    ts.clear();
+}
+
+void Program::qr_step(std::vector<QRTask>& ts) {
+    if (ts.empty()) return;
+    Step s;
+    s.kind = ST_QR;
+    s.first = qr.size();
+    s.count = (int)ts.size();
+    int mm = 1;
+    for (auto& t : ts) {
+        mm = std::max(mm, t.m);
+        const double f = (4.0 * t.m * (double)t.n * t.n - 4.0 / 3.0 * (double)t.n * t.n * t.n) * (cplx ? 4.0 : 1.0);
+        if (t.active) gated_qr_flops += f;
+        else static_qr_flops += f;
+        qr.push_back(t);
+    }
+    s.aux = mm;
+    max_qr_m = std::max(max_qr_m, mm);
+    steps.push_back(s);
+    ts.clear();
+}
+
+template <typename T>
+static size_t push_all(std::vector<T>& dst, std::vector<T>& src) {
+    size_t f = dst.size();
+    dst.insert(dst.end(), src.begin(), src.end());
+    src.clear();
+    return f;
+}
+
+void Program::simple(int kind, void* p0, void* p1, long long n, int aux) {
+    Step s;
+    s.kind = kind;
+    s.p0 = p0;
+    s.p1 = p1;
+    s.n = n;
+    s.aux = aux;
+    steps.push_back(s);
+}
+
+
+// ------------------------------------------------------------------ the zip-up fit (App. A)
+// Element offsets inside the arena are converted to byte offsets with the scalar size.
+struct Emit {
+    Program& pr;
+    int ss;
+    const int* none = nullptr;
+    void* ep(size_t elem_off) const { return P(elem_off * (size_t)ss); }
+};
+
+// L->R site update at site i of fit f:  T1 = A X ; T2 = T1 O ; Yt = T2 B ; (QR) ; A' = conj(Y) T2
+static void lr_gc(const Emit& e, const FitSpec& f, int i, int stage, const int* act, std::vector<GTask>& out) {
+    const View3& X = f.X[i];
+    const View4& O = f.O[i];
+    const int y = f.ybond[i], y2 = f.ybond[i + 1];
+    const int x = X.a, x2 = X.b, p = X.k, w = O.w, w2 = O.w2, q = O.q;
+    GTask t{};
+    t.active = act;
+    if (stage == 0) {  // T1[y][w][p][x2] = sum_x A[y,w,x] X[x,p,x2]
+        t.A = e.ep(f.Aenv[i]);
+        t.B = e.ep(X.off);
+        t.C = e.ep(f.T1);
+        t.M1 = y; t.M2 = w; t.K1 = 1; t.K2 = x; t.N1 = p; t.N2 = x2;
+        t.a_m1 = (long long)w * x; t.a_m2 = x; t.a_k2 = 1;
+        t.b_k2 = X.sa; t.b_n1 = X.sk; t.b_n2 = X.sb;
+        t.c_m1 = (long long)w * p * x2; t.c_m2 = (long long)p * x2; t.c_n1 = x2; t.c_n2 = 1;
+    } else if (stage == 1) {  // T2[y][x2][q][w2] = sum_{w,p} T1[y,w,p,x2] O[w,p,q,w2]
+        t.A = e.ep(f.T1);
+        t.B = e.ep(O.off);
+        t.C = e.ep(f.T2);
+        t.M1 = y; t.M2 = x2; t.K1 = w; t.K2 = p; t.N1 = q; t.N2 = w2;
+        t.a_m1 = (long long)w * p * x2; t.a_m2 = 1; t.a_k1 = (long long)p * x2; t.a_k2 = x2;
+        t.b_k1 = O.sw; t.b_k2 = O.sp; t.b_n1 = O.sq; t.b_n2 = O.sw2;
+        t.c_m1 = (long long)x2 * q * w2; t.c_m2 = (long long)q * w2; t.c_n1 = w2; t.c_n2 = 1;
+    } else if (stage == 2) {  // Yt[y][q][y2] = sum_{x2,w2} T2[y,x2,q,w2] B[y2,w2,x2]
+        t.A = e.ep(f.T2);
+        t.B = e.ep(f.Benv[i + 1]);
+        t.C = e.ep(f.Yt);
+        t.M1 = y; t.M2 = q; t.K1 = x2; t.K2 = w2; t.N1 = 1; t.N2 = y2;
+        t.a_m1 = (long long)x2 * q * w2; t.a_m2 = w2; t.a_k1 = (long long)q * w2; t.a_k2 = 1;
+        t.b_k1 = 1; t.b_k2 = x2; t.b_n2 = (long long)w2 * x2;
+        t.c_m1 = (long long)q * y2; t.c_m2 = y2; t.c_n2 = 1;
+    } else {  // A_{i+1}[y2][w2][x2] = sum_{y,q} conj(Y[y,q,y2]) T2[y,x2,q,w2]
+        t.A = e.ep(f.Y[i]);
+        t.B = e.ep(f.T2);
+        t.C = e.ep(f.Aenv[i + 1]);
+        t.conjA = 1;
+        t.M1 = 1; t.M2 = y2; t.K1 = y; t.K2 = q; t.N1 = w2; t.N2 = x2;
+        t.a_m2 = 1; t.a_k1 = (long long)q * y2; t.a_k2 = y2;
+        t.b_k1 = (long long)x2 * q * w2; t.b_k2 = w2; t.b_n1 = 1; t.b_n2 = (long long)q * w2;
+        t.c_m2 = (long long)w2 * x2; t.c_n1 = x2; t.c_n2 = 1;
+    }
+    out.push_back(t);
+}
+
+// R->L site update at site i:  T1 = X B ; T2 = T1 O ; Yt = A T2 ; (LQ) ; B_i = conj(Y) T2
+// With Ydst != 0 the Yt of stage 2 is written there (final update of the fit).
+static void rl_gc(const Emit& e, const FitSpec& f, int i, int stage, const int* act, std::vector<GTask>& out,
+                  size_t Ydst = 0) {
+    const View3& X = f.X[i];
+    const View4& O = f.O[i];
+    const int y = f.ybond[i], y2 = f.ybond[i + 1];
+    const int x = X.a, x2 = X.b, p = X.k, w = O.w, w2 = O.w2, q = O.q;
+    GTask t{};
+    t.active = act;
+    if (stage == 0) {  // T1[x][p][y2][w2] = sum_x2 X[x,p,x2] B[y2,w2,x2]
+        t.A = e.ep(X.off);
+        t.B = e.ep(f.Benv[i + 1]);
+        t.C = e.ep(f.T1);
+        t.M1 = x; t.M2 = p; t.K1 = 1; t.K2 = x2; t.N1 = y2; t.N2 = w2;
+        t.a_m1 = X.sa; t.a_m2 = X.sk; t.a_k2 = X.sb;
+        t.b_k2 = 1; t.b_n1 = (long long)w2 * x2; t.b_n2 = x2;
+        t.c_m1 = (long long)p * y2 * w2; t.c_m2 = (long long)y2 * w2; t.c_n1 = w2; t.c_n2 = 1;
+    } else if (stage == 1) {  // T2[x][y2][w][q] = sum_{p,w2} T1[x,p,y2,w2] O[w,p,q,w2]
+        t.A = e.ep(f.T1);
+        t.B = e.ep(O.off);
+        t.C = e.ep(f.T2);
+        t.M1 = x; t.M2 = y2; t.K1 = p; t.K2 = w2; t.N1 = w; t.N2 = q;
+        t.a_m1 = (long long)p * y2 * w2; t.a_m2 = w2; t.a_k1 = (long long)y2 * w2; t.a_k2 = 1;
+        t.b_k1 = O.sp; t.b_k2 = O.sw2; t.b_n1 = O.sw; t.b_n2 = O.sq;
+        t.c_m1 = (long long)y2 * w * q; t.c_m2 = (long long)w * q; t.c_n1 = q; t.c_n2 = 1;
+    } else if (stage == 2) {  // Yt[y][q][y2] = sum_{w,x} A[y,w,x] T2[x,y2,w,q]
+        t.A = e.ep(f.Aenv[i]);
+        t.B = e.ep(f.T2);
+        t.C = e.ep(Ydst ? Ydst : f.Yt);
+        t.M1 = 1; t.M2 = y; t.K1 = w; t.K2 = x; t.N1 = q; t.N2 = y2;
+        t.a_m2 = (long long)w * x; t.a_k1 = x; t.a_k2 = 1;
+        t.b_k1 = q; t.b_k2 = (long long)y2 * w * q; t.b_n1 = 1; t.b_n2 = (long long)w * q;
+        t.c_m2 = (long long)q * y2; t.c_n1 = y2; t.c_n2 = 1;
+    } else {  // B_i[y][w][x] = sum_{q,y2} conj(Y[y,q,y2]) T2[x,y2,w,q]
+        t.A = e.ep(f.Y[i]);
+        t.B = e.ep(f.T2);
+        t.C = e.ep(f.Benv[i]);
+        t.conjA = 1;
+        t.M1 = 1; t.M2 = y; t.K1 = q; t.K2 = y2; t.N1 = w; t.N2 = x;
+        t.a_m2 = (long long)q * y2; t.a_k1 = y2; t.a_k2 = 1;
+        t.b_k1 = 1; t.b_k2 = (long long)w * q; t.b_n1 = q; t.b_n2 = (long long)y2 * w * q;
+        t.c_m2 = (long long)w * x; t.c_n1 = x; t.c_n2 = 1;
+    }
+    out.push_back(t);
+}
+
+static QRTask qr_task(const Emit& e, const FitSpec& f, int i, bool lq, size_t loss_elem, const int* act) {
+    const int y = f.ybond[i], y2 = f.ybond[i + 1], q = f.O[i].q;
+    QRTask t{};
+    t.in = e.ep(f.Yt);
+    t.out = e.ep(f.Y[i]);
+    t.work = e.ep(f.qrw);
+    t.loss = (double*)P(loss_elem);
+    t.active = act;
+    if (!lq) {
+        t.m = y * q; t.n = y2;
+        t.in_rs = y2; t.in_cs = 1; t.out_rs = y2; t.out_cs = 1; t.conj_io = 0;
+    } else {
+        t.m = q * y2; t.n = y;
+        t.in_rs = 1; t.in_cs = (long long)q * y2; t.out_rs = 1; t.out_cs = (long long)q * y2; t.conj_io = 1;
+    }
+    return t;
+}
+
+// Emit a lockstep group of fits.  losses_byte / active / counters are byte offsets
+// of per-fit arrays (losses: fit_max_sweeps * 2(n-1) doubles per fit).
+void emit_fits(Program& pr, int ss, std::vector<FitSpec*>& fits, int max_sweeps, double fit_tol,
+               const int* sweep_ctr_dev_placeholder, bool rand_uses_sweep) {
+    (void)sweep_ctr_dev_placeholder;
+    Emit e{pr, ss};
+    int nmax = 0;
+    for (auto* f : fits) nmax = std::max(nmax, f->n());
+    // 1. random initial Y (App. A initialises Y at random)
+    {
+        std::vector<RandTask> rt;
+        for (auto* f : fits)
+            for (int i = 0; i < f->n(); ++i) {
+                RandTask t{};
+                t.ptr = e.ep(f->Y[i]);
+                t.n = (long long)f->ybond[i] * f->O[i].q * f->ybond[i + 1];
+                t.stream = f->stream + (uint64_t)i;
+                t.active = i == 0 ? (int*)P(f->active) : nullptr;
+                rt.push_back(t);
+            }
+        Step s;
+        s.kind = ST_RAND;
+        s.count = (int)rt.size();
+        s.first = push_all(pr.rnd, rt);
+        s.aux = rand_uses_sweep ? 1 : 0;
+        pr.steps.push_back(s);
+    }
+    // 2. right environments from the initial Y (A_1 = B_{L+1} = 1)
+    std::vector<GTask> g;
+    for (int k = 0; k <= nmax - 2; ++k)
+        for (int stage : {0, 1, 3}) {
+            for (auto* f : fits) {
+                const int i = f->n() - 1 - k;
+                if (i >= 1) rl_gc(e, *f, i, stage, nullptr, g);
+            }
+            pr.gc_step(g);
+        }
+    // 3. sweeps
+    std::vector<QRTask> qt;
+    for (int s = 0; s < max_sweeps; ++s) {
+        for (int k = 0; k <= nmax - 2; ++k) {
+            for (int stage = 0; stage < 3; ++stage) {
+                for (auto* f : fits)
+                    if (k <= f->n() - 2) lr_gc(e, *f, k, stage, s ? (const int*)P(f->active) : nullptr, g);
+                pr.gc_step(g);
+            }
+            for (auto* f : fits)
+                if (k <= f->n() - 2) {
+                    const int nu = 2 * (f->n() - 1);
+                    const size_t loss = f->losses + (size_t)(s * nu + k) * sizeof(double);
+                    qt.push_back(qr_task(e, *f, k, false, loss, s ? (const int*)P(f->active) : nullptr));
+                }
+            pr.qr_step(qt);
+            for (auto* f : fits)
+                if (k <= f->n() - 2) lr_gc(e, *f, k, 3, s ? (const int*)P(f->active) : nullptr, g);
+            pr.gc_step(g);
+        }
+        for (int k = 0; k <= nmax - 2; ++k) {
+            for (int stage = 0; stage < 3; ++stage) {
+                for (auto* f : fits) {
+                    const int i = f->n() - 1 - k;
+                    if (i >= 1) rl_gc(e, *f, i, stage, s ? (const int*)P(f->active) : nullptr, g);
+                }
+                pr.gc_step(g);
+            }
+            for (auto* f : fits) {
+                const int i = f->n() - 1 - k;
+                if (i >= 1) {
+                    const int nu = 2 * (f->n() - 1);
+                    const size_t loss = f->losses + (size_t)(s * nu + (f->n() - 1) + k) * sizeof(double);
+                    qt.push_back(qr_task(e, *f, i, true, loss, s ? (const int*)P(f->active) : nullptr));
+                }
+            }
+            pr.qr_step(qt);
+            for (auto* f : fits) {
+                const int i = f->n() - 1 - k;
+                if (i >= 1) rl_gc(e, *f, i, 3, s ? (const int*)P(f->active) : nullptr, g);
+            }
+            pr.gc_step(g);
+        }
+        // stop rule after the full sweep (App. A)
+        std::vector<CheckTask> ct;
+        for (auto* f : fits) {
+            CheckTask t{};
+            const int nu = 2 * (f->n() - 1);
+            t.losses = (const double*)P(f->losses + (size_t)s * nu * sizeof(double));
+            t.active = (int*)P(f->active);
+            t.count = nu;
+            t.counter = (int*)P(f->counter);
+            ct.push_back(t);
+        }
+        Step st;
+        st.kind = ST_CHECK;
+        st.count = (int)ct.size();
+        st.first = push_all(pr.chk, ct);
+        pr.steps.push_back(st);
+        pr.fit_tol = fit_tol;
+    }
+    // 4. final update at site 0 keeps Yt itself
+    for (int stage = 0; stage < 3; ++stage) {
+        for (auto* f : fits) rl_gc(e, *f, 0, stage, nullptr, g, stage == 2 ? f->Y[0] : 0);
+        pr.gc_step(g);
+    }
+    // 5. unit norm (mixed canonical form around site 0)
+    std::vector<ScaleTask> sc;
+    for (auto* f : fits) {
+        ScaleTask t{};
+        t.ptr = e.ep(f->Y[0]);
+        t.n = (long long)f->ybond[0] * f->O[0].q * f->ybond[1];
+        sc.push_back(t);
+    }
+    Step st;
+    st.kind = ST_SCALE;
+    st.count = (int)sc.size();
+    st.first = push_all(pr.scl, sc);
+    pr.steps.push_back(st);
+}
+
+// <M|N> chains for a set of message pairs: per site T = E N, E' = conj(M) T.
+void emit_overlaps(Program& pr, int ss, std::vector<OverlapSpec>& ov) {
+    Emit e{pr, ss};
+    int bmax = 0;
+    for (auto& o : ov) bmax = std::max(bmax, (int)o.M.size());
+    std::vector<GTask> g;
+    for (int j = 0; j < bmax; ++j) {
+        for (auto& o : ov) {
+            if (j >= (int)o.M.size()) continue;
+            const View3& M = o.M[j];
+            const View3& N = o.N[j];
+            const size_t Ein = j == 0 ? o.one : o.E[j % 2];
+            GTask t{};
+            t.A = e.ep(Ein);
+            t.B = e.ep(N.off);
+            t.C = e.ep(o.T);
+            t.M1 = 1; t.M2 = M.a; t.K1 = 1; t.K2 = N.a; t.N1 = N.k; t.N2 = N.b;
+            t.a_m2 = N.a; t.a_k2 = 1;
+            t.b_k2 = N.sa; t.b_n1 = N.sk; t.b_n2 = N.sb;
+            t.c_m2 = (long long)N.k * N.b; t.c_n1 = N.b; t.c_n2 = 1;
+            g.push_back(t);
+        }
+        pr.gc_step(g);
+        for (auto& o : ov) {
+            if (j >= (int)o.M.size()) continue;
+            const View3& M = o.M[j];
+            const View3& N = o.N[j];
+            const size_t Eout = (j + 1 == (int)o.M.size()) ? o.result : o.E[(j + 1) % 2];
+            GTask t{};
+            t.A = e.ep(M.off);
+            t.B = e.ep(o.T);
+            t.C = e.ep(Eout);
+            t.conjA = 1;
+            t.M1 = 1; t.M2 = M.b; t.K1 = M.a; t.K2 = M.k; t.N1 = 1; t.N2 = N.b;
+            t.a_m2 = M.sb; t.a_k1 = M.sa; t.a_k2 = M.sk;
+            t.b_k1 = (long long)N.k * N.b; t.b_k2 = N.b; t.b_n2 = 1;
+            t.c_m2 = N.b; t.c_n2 = 1;
+            g.push_back(t);
+        }
+        pr.gc_step(g);
+    }
+}
+
+// ------------------------------------------------------------------ relocation and upload
+// Offsets below `split` belong to the lattice arena (base), the rest to a second
+// arena (base2) whose offsets start at `split`.
+static inline char* reloc_ptr(uintptr_t off, char* base, size_t split, char* base2) {
+    if (off < split) return base + off;
+    return base2 + (off - split);
+}
+#define RELOC(field)                                                                                        \
+    field = (std::remove_reference_t<decltype(field)>)((field) ? reloc_ptr((uintptr_t)(field), base, split, base2) \
+                                                               : nullptr)
+
+void Program::relocate(char* base, size_t split, char* base2) {
+    for (auto& t : gc) {
+        RELOC(t.A); RELOC(t.B); RELOC(t.C); RELOC(t.active);
+    }
+    for (auto& t : qr) {
+        RELOC(t.in); RELOC(t.out); RELOC(t.work); RELOC(t.loss); RELOC(t.active);
+    }
+    for (auto& t : rnd) {
+        RELOC(t.ptr); RELOC(t.active);
+    }
+    for (auto& t : chk) {
+        RELOC(t.losses); RELOC(t.active); RELOC(t.counter);
+    }
+    for (auto& t : scl) RELOC(t.ptr);
+    for (auto& t : asmb) {
+        for (int s = 0; s < t.nsites; ++s) {
+            RELOC(t.src[s]); RELOC(t.dst[s]);
+        }
+        RELOC(t.corner0); RELOC(t.corner1);
+    }
+    for (auto& t : nrm) {
+        RELOC(t.site0);
+        for (int s = 0; s < t.nsites; ++s) RELOC(t.sites[s]);
+        RELOC(t.mm); RELOC(t.mo); RELOC(t.resid); RELOC(t.status);
+    }
+    for (auto& t : fus) {
+        RELOC(t.A); RELOC(t.B); RELOC(t.out);
+    }
+    for (auto& t : dl) {
+        RELOC(t.T); RELOC(t.E); RELOC(t.O);
+    }
+    for (auto& s : steps) {
+        RELOC(s.p0); RELOC(s.p1);
+    }
+}
+
+template <typename T>
+static cudaError_t upload(std::vector<T>& v, T** dptr) {
+    *dptr = nullptr;
+    if (v.empty()) return cudaSuccess;
+    cudaError_t e = cudaMalloc((void**)dptr, v.size() * sizeof(T));
+    if (e != cudaSuccess) return e;
+    return cudaMemcpy(*dptr, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
+}
+
+cudaError_t Program::upload_tasks() {
+    cudaError_t e;
+    if ((e = upload(gc, &d_gc)) != cudaSuccess) return e;
+    if ((e = upload(qr, &d_qr)) != cudaSuccess) return e;
+    if ((e = upload(rnd, &d_rnd)) != cudaSuccess) return e;
+    if ((e = upload(chk, &d_chk)) != cudaSuccess) return e;
+    if ((e = upload(scl, &d_scl)) != cudaSuccess) return e;
+    if ((e = upload(asmb, &d_asm)) != cudaSuccess) return e;
+    if ((e = upload(nrm, &d_nrm)) != cudaSuccess) return e;
+    if ((e = upload(fus, &d_fus)) != cudaSuccess) return e;
+    if ((e = upload(dl, &d_dl)) != cudaSuccess) return e;
+    if (max_qr_m > 0) {
+        if ((e = qr_prepare(max_qr_m, cplx)) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t Program::launch_all(cudaStream_t st, const int* sweep_ctr, unsigned long long seed) const {
+    cudaError_t e = cudaSuccess;
+    for (const Step& s : steps) {
+        switch (s.kind) {
+            case ST_GC: e = launch_gcontract(d_gc + s.first, s.count, s.aux, cplx, st); break;
+            case ST_QR: e = launch_qr(d_qr + s.first, s.count, s.aux, cplx, st); break;
+            case ST_RAND: e = launch_rand(d_rnd + s.first, s.count, seed, s.aux ? sweep_ctr : nullptr, cplx, st); break;
+            case ST_SETACT: e = launch_set_int((int*)s.p0, (int)s.n, s.aux, st); break;
+            case ST_CHECK: e = launch_check(d_chk + s.first, s.count, fit_tol, st); break;
+            case ST_SCALE: e = launch_scale(d_scl + s.first, s.count, cplx, status, st); break;
+            case ST_ASM: e = launch_assemble(d_asm + s.first, s.count, cplx, st); break;
+            case ST_NORM: e = launch_normalise(d_nrm + s.first, s.count, cplx, st); break;
+            case ST_MEAN: e = launch_mean((const double*)s.p0, (int)s.n, (double*)s.p1, st); break;
+            case ST_COPY: e = launch_copy(s.p0, s.p1, s.n, st); break;
+            case ST_INC: e = launch_add_int((int*)s.p0, 1, st); break;
+            case ST_FUSE: e = launch_fuse(d_fus + s.first, s.count, s.n, cplx, st); break;
+            case ST_DL: e = launch_double_layer(d_dl + s.first, s.count, s.n, cplx, st); break;
+            default: e = cudaErrorInvalidValue;
+        }
+        if (e != cudaSuccess) return e;
+    }
+    return e;
+}
+
+void Program::free_all() {
+    if (exec) cudaGraphExecDestroy(exec);
+    exec = nullptr;
+    cudaFree(d_gc); cudaFree(d_qr); cudaFree(d_rnd); cudaFree(d_chk);
+    cudaFree(d_scl); cudaFree(d_asm); cudaFree(d_nrm); cudaFree(d_fus); cudaFree(d_dl);
+    d_gc = nullptr; d_qr = nullptr; d_rnd = nullptr; d_chk = nullptr;
+    d_scl = nullptr; d_asm = nullptr; d_nrm = nullptr; d_fus = nullptr; d_dl = nullptr;
+}
+
+long long Program::kernel_count() const { return (long long)steps.size(); }
+
+}  // namespace bbp

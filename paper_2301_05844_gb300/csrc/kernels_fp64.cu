@@ -1,0 +1,577 @@
+// FP64 / complex-FP64 kernels of the blockBP sweep and read-out.
+//
+// These are grouped kernels: blockIdx.y (or blockIdx.x) selects a task descriptor,
+// so one launch advances every message of the sweep by one step.  They form the
+// plain FP64 GPU path (every contraction, QR/LQ and reduction in FP64) and supply
+// the FP64 truncation / normalisation stages of the mixed-precision path.
+#include <math.h>
+
+#include "bbp_internal.h"
+
+namespace bbp {
+
+// ---------------------------------------------------------------- scalar helpers
+__device__ __forceinline__ double conjv(double a) { return a; }
+__device__ __forceinline__ double2 conjv(double2 a) { return make_double2(a.x, -a.y); }
+__device__ __forceinline__ void mac(double& c, double a, double b) { c = fma(a, b, c); }
+__device__ __forceinline__ void mac(double2& c, double2 a, double2 b) {
+    c.x = fma(a.x, b.x, fma(-a.y, b.y, c.x));
+    c.y = fma(a.x, b.y, fma(a.y, b.x, c.y));
+}
+__device__ __forceinline__ double abs2(double a) { return a * a; }
+__device__ __forceinline__ double abs2(double2 a) { return a.x * a.x + a.y * a.y; }
+template <typename S> __device__ __forceinline__ S zero();
+template <> __device__ __forceinline__ double zero<double>() { return 0.0; }
+template <> __device__ __forceinline__ double2 zero<double2>() { return make_double2(0.0, 0.0); }
+template <typename S> __device__ __forceinline__ S one();
+template <> __device__ __forceinline__ double one<double>() { return 1.0; }
+template <> __device__ __forceinline__ double2 one<double2>() { return make_double2(1.0, 0.0); }
+__device__ __forceinline__ double add(double a, double b) { return a + b; }
+__device__ __forceinline__ double2 add(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double sub(double a, double b) { return a - b; }
+__device__ __forceinline__ double2 sub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double mul(double a, double b) { return a * b; }
+__device__ __forceinline__ double2 mul(double2 a, double2 b) {
+    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ double scal(double a, double s) { return a * s; }
+__device__ __forceinline__ double2 scal(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
+__device__ __forceinline__ double absv(double a) { return fabs(a); }
+__device__ __forceinline__ double absv(double2 a) { return hypot(a.x, a.y); }
+__device__ __forceinline__ double shfl_down(double v, int o) { return __shfl_down_sync(0xffffffffu, v, o); }
+__device__ __forceinline__ double2 shfl_down(double2 v, int o) {
+    return make_double2(__shfl_down_sync(0xffffffffu, v.x, o), __shfl_down_sync(0xffffffffu, v.y, o));
+}
+__device__ __forceinline__ double shfl_idx(double v, int l) { return __shfl_sync(0xffffffffu, v, l); }
+__device__ __forceinline__ double2 shfl_idx(double2 v, int l) {
+    return make_double2(__shfl_sync(0xffffffffu, v.x, l), __shfl_sync(0xffffffffu, v.y, l));
+}
+template <typename S>
+__device__ __forceinline__ S warp_sum(S v) {
+    for (int o = 16; o > 0; o >>= 1) v = add(v, shfl_down(v, o));
+    return shfl_idx(v, 0);
+}
+// Block-wide sum for 256 threads; every thread gets the result.
+template <typename S>
+__device__ S block_sum(S v, S* red) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    v = warp_sum(v);
+    __syncthreads();
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    S t = zero<S>();
+    if (threadIdx.x < 32) {
+        t = (lane < (int)(blockDim.x >> 5)) ? red[lane] : zero<S>();
+        t = warp_sum(t);
+        if (lane == 0) red[0] = t;
+    }
+    __syncthreads();
+    t = red[0];
+    __syncthreads();
+    return t;
+}
+
+// ---------------------------------------------------------------- SplitMix64
+__host__ __device__ __forceinline__ uint64_t sm64(uint64_t z) {
+    z += 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+__host__ __device__ __forceinline__ double u_pm1(uint64_t key, uint64_t idx) {
+    return (double)(sm64(key + idx) >> 11) * 0x1.0p-52 - 1.0;
+}
+uint64_t splitmix64(uint64_t z) { return sm64(z); }
+double uniform_pm1(uint64_t seed, uint64_t stream, uint64_t idx) { return u_pm1(seed ^ sm64(stream), idx); }
+
+// ---------------------------------------------------------------- generic contraction
+// 64x64 output tile per CTA, K in chunks of 16, 256 threads each owning 4x4 outputs.
+template <typename S>
+__global__ void __launch_bounds__(256) k_gcontract(const GTask* __restrict__ tasks) {
+    const GTask& t = tasks[blockIdx.y];
+    if (t.active && *t.active == 0) return;
+    const int M = t.M1 * t.M2, N = t.N1 * t.N2, Kd = t.K1 * t.K2;
+    const int tilesM = (M + 63) >> 6, tilesN = (N + 63) >> 6;
+    const int tile = blockIdx.x;
+    if (tile >= tilesM * tilesN) return;
+    const int m0 = (tile % tilesM) << 6, n0 = (tile / tilesM) << 6;
+    __shared__ S As[16][65];
+    __shared__ S Bs[16][65];
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const S* __restrict__ Ap = (const S*)t.A;
+    const S* __restrict__ Bp = (const S*)t.B;
+    const int lmn = tid & 63, lk = tid >> 6;  // loader: fixed row/col, k = lk + 4j
+    const int am = m0 + lmn, bn = n0 + lmn;
+    const bool av = am < M, bv = bn < N;
+    const long long aoff = av ? (long long)(am / t.M2) * t.a_m1 + (long long)(am % t.M2) * t.a_m2 : 0;
+    const long long boff = bv ? (long long)(bn / t.N2) * t.b_n1 + (long long)(bn % t.N2) * t.b_n2 : 0;
+    S acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = zero<S>();
+    for (int k0 = 0; k0 < Kd; k0 += 16) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int kk = lk + 4 * j, k = k0 + kk;
+            S a = zero<S>(), b = zero<S>();
+            if (k < Kd) {
+                const int k1 = k / t.K2, k2 = k - k1 * t.K2;
+                if (av) {
+                    a = Ap[aoff + (long long)k1 * t.a_k1 + (long long)k2 * t.a_k2];
+                    if (t.conjA) a = conjv(a);
+                }
+                if (bv) b = Bp[boff + (long long)k1 * t.b_k1 + (long long)k2 * t.b_k2];
+            }
+            As[kk][lmn] = a;
+            Bs[kk][lmn] = b;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < 16; ++kk) {
+            S a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) mac(acc[i][j], a[i], b[j]);
+        }
+        __syncthreads();
+    }
+    S* __restrict__ Cp = (S*)t.C;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int m = m0 + ty + 16 * i;
+        if (m >= M) continue;
+        const long long mo = (long long)(m / t.M2) * t.c_m1 + (long long)(m % t.M2) * t.c_m2;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int n = n0 + tx + 16 * j;
+            if (n >= N) continue;
+            const long long o = mo + (long long)(n / t.N2) * t.c_n1 + (long long)(n % t.N2) * t.c_n2;
+            Cp[o] = t.accumulate ? add(Cp[o], acc[i][j]) : acc[i][j];
+        }
+    }
+}
+
+cudaError_t launch_gcontract(const GTask* d_tasks, int ntasks, int max_tiles, bool cplx, cudaStream_t s) {
+    if (ntasks <= 0) return cudaSuccess;
+    dim3 grid(max_tiles, ntasks);
+    if (cplx)
+        k_gcontract<double2><<<grid, 256, 0, s>>>(d_tasks);
+    else
+        k_gcontract<double><<<grid, 256, 0, s>>>(d_tasks);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- Householder QR / LQ
+// One CTA per task.  H_j = I - coef_j u_j u_j^H with u_j = x - beta_j e_1,
+// beta_j = -phase(x_0) ||x|| (no cancellation), coef_j = 1 / (||x|| (||x|| + |x_0|)).
+// Q = H_0 ... H_{n-1} [I; 0], accumulated backwards; finally column j is multiplied
+// by phase(beta_j) so that R_jj = |beta_j| >= 0.
+constexpr int QR_MAXN = 512;
+template <typename S>
+__global__ void __launch_bounds__(256) k_qr(const QRTask* __restrict__ tasks) {
+    const QRTask& t = tasks[blockIdx.x];
+    if (t.active && *t.active == 0) return;
+    extern __shared__ __align__(16) unsigned char qr_smem[];
+    S* u = (S*)qr_smem;  // m entries
+    __shared__ S betas[QR_MAXN];
+    __shared__ double coefs[QR_MAXN];
+    __shared__ S red[32];
+    __shared__ double redd[32];
+    const int m = t.m, n = t.n, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    S* W = (S*)t.work;
+    S* Q = W + (size_t)m * n;
+    const S* in = (const S*)t.in;
+    S* out = (S*)t.out;
+    double ss = 0.0;
+    for (long long idx = tid; idx < (long long)m * n; idx += 256) {
+        const int i = (int)(idx % m), j = (int)(idx / m);
+        S v = in[(long long)i * t.in_rs + (long long)j * t.in_cs];
+        if (t.conj_io) v = conjv(v);
+        W[(size_t)j * m + i] = v;
+        ss += abs2(v);
+    }
+    ss = block_sum(ss, redd);
+    if (tid == 0 && t.loss) *t.loss = -ss;
+    __syncthreads();
+    for (int j = 0; j < n; ++j) {
+        const S* col = W + (size_t)j * m;
+        double s2 = 0.0;
+        for (int i = j + tid; i < m; i += 256) s2 += abs2(col[i]);
+        s2 = block_sum(s2, redd);
+        const S alpha = col[j];
+        const double nrm = sqrt(s2), aa = absv(alpha);
+        S beta = zero<S>();
+        double coef = 0.0;
+        if (nrm > 0.0) {
+            const S ph = aa > 0.0 ? scal(alpha, 1.0 / aa) : one<S>();
+            beta = scal(ph, -nrm);
+            coef = 1.0 / (nrm * (nrm + aa));
+        }
+        for (int i = j + tid; i < m; i += 256) u[i] = (i == j) ? sub(alpha, beta) : col[i];
+        if (tid == 0) {
+            betas[j] = beta;
+            coefs[j] = coef;
+        }
+        __syncthreads();
+        if (coef != 0.0) {
+            for (int k = j + 1 + warp; k < n; k += 8) {
+                S* ck = W + (size_t)k * m;
+                S dot = zero<S>();
+                for (int i = j + lane; i < m; i += 32) mac(dot, conjv(u[i]), ck[i]);
+                dot = warp_sum(dot);
+                const S f = scal(dot, -coef);
+                for (int i = j + lane; i < m; i += 32) mac(ck[i], u[i], f);
+            }
+        }
+        __syncthreads();
+        for (int i = j + tid; i < m; i += 256) W[(size_t)j * m + i] = u[i];
+        __syncthreads();
+    }
+    for (long long idx = tid; idx < (long long)m * n; idx += 256) {
+        const int i = (int)(idx % m), k = (int)(idx / m);
+        Q[(size_t)k * m + i] = (i == k) ? one<S>() : zero<S>();
+    }
+    __syncthreads();
+    for (int j = n - 1; j >= 0; --j) {
+        const double coef = coefs[j];
+        if (coef == 0.0) continue;
+        const S* uj = W + (size_t)j * m;
+        for (int i = j + tid; i < m; i += 256) u[i] = uj[i];
+        __syncthreads();
+        for (int k = j + warp; k < n; k += 8) {
+            S* qk = Q + (size_t)k * m;
+            S dot = zero<S>();
+            for (int i = j + lane; i < m; i += 32) mac(dot, conjv(u[i]), qk[i]);
+            dot = warp_sum(dot);
+            const S f = scal(dot, -coef);
+            for (int i = j + lane; i < m; i += 32) mac(qk[i], u[i], f);
+        }
+        __syncthreads();
+    }
+    for (long long idx = tid; idx < (long long)m * n; idx += 256) {
+        const int i = (int)(idx % m), k = (int)(idx / m);
+        const double bb = absv(betas[k]);
+        const S ph = bb > 0.0 ? scal(betas[k], 1.0 / bb) : one<S>();
+        S v = mul(Q[(size_t)k * m + i], ph);
+        if (t.conj_io) v = conjv(v);
+        out[(long long)i * t.out_rs + (long long)k * t.out_cs] = v;
+    }
+}
+
+cudaError_t qr_prepare(int max_m, bool cplx) {
+    const size_t sm = (size_t)max_m * (cplx ? sizeof(double2) : sizeof(double));
+    if (cplx) return cudaFuncSetAttribute(k_qr<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    return cudaFuncSetAttribute(k_qr<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+}
+
+cudaError_t launch_qr(const QRTask* d_tasks, int ntasks, int max_m, bool cplx, cudaStream_t s) {
+    if (ntasks <= 0) return cudaSuccess;
+    const size_t sm = (size_t)max_m * (cplx ? sizeof(double2) : sizeof(double));
+    if (cplx)
+        k_qr<double2><<<ntasks, 256, sm, s>>>(d_tasks);
+    else
+        k_qr<double><<<ntasks, 256, sm, s>>>(d_tasks);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- random fill
+__global__ void k_rand(const RandTask* __restrict__ tasks, unsigned long long seed, const int* sweep_ctr, int cplx) {
+    const RandTask& t = tasks[blockIdx.y];
+    const uint64_t stream = t.stream | (sweep_ctr ? ((uint64_t)(*sweep_ctr) << 36) : 0ull);
+    const uint64_t key = seed ^ sm64(stream);
+    const long long cnt = cplx ? 2 * t.n : t.n;
+    double* p = (double*)t.ptr;
+    if (t.active && blockIdx.x == 0 && threadIdx.x == 0) *t.active = 1;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < cnt; i += (long long)gridDim.x * blockDim.x)
+        p[i] = u_pm1(key, (uint64_t)i);
+}
+cudaError_t launch_rand(const RandTask* d_tasks, int ntasks, unsigned long long seed, const int* sweep_ctr,
+                        bool cplx, cudaStream_t s) {
+    if (ntasks <= 0) return cudaSuccess;
+    k_rand<<<dim3(8, ntasks), 256, 0, s>>>(d_tasks, seed, sweep_ctr, cplx ? 1 : 0);
+    return cudaGetLastError();
+}
+
+__global__ void k_set_int(int* p, int n, int v) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) p[i] = v;
+}
+cudaError_t launch_set_int(int* p, int n, int v, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    k_set_int<<<(n + 255) / 256, 256, 0, s>>>(p, n, v);
+    return cudaGetLastError();
+}
+__global__ void k_add_int(int* p, int v) { *p += v; }
+cudaError_t launch_add_int(int* p, int v, cudaStream_t s) {
+    k_add_int<<<1, 1, 0, s>>>(p, v);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- fit stop rule (App. A)
+__global__ void k_check(const CheckTask* __restrict__ tasks, int ntasks, double tol) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ntasks) return;
+    const CheckTask& t = tasks[i];
+    if (*t.active == 0) return;
+    *t.counter += 1;
+    double mean = 0.0;
+    for (int k = 0; k < t.count; ++k) mean += t.losses[k];
+    mean /= t.count;
+    double var = 0.0;
+    for (int k = 0; k < t.count; ++k) {
+        const double dv = t.losses[k] - mean;
+        var += dv * dv;
+    }
+    const double sd = sqrt(var / t.count);
+    if (mean != 0.0 && sd / fabs(mean) < tol) *t.active = 0;
+}
+cudaError_t launch_check(const CheckTask* d_tasks, int ntasks, double tol, cudaStream_t s) {
+    if (ntasks <= 0) return cudaSuccess;
+    k_check<<<(ntasks + 127) / 128, 128, 0, s>>>(d_tasks, ntasks, tol);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- scale to unit norm
+template <typename S>
+__global__ void __launch_bounds__(256) k_scale(const ScaleTask* __restrict__ tasks, int* status) {
+    const ScaleTask& t = tasks[blockIdx.x];
+    __shared__ double red[32];
+    S* p = (S*)t.ptr;
+    double ss = 0.0;
+    for (long long i = threadIdx.x; i < t.n; i += 256) ss += abs2(p[i]);
+    ss = block_sum(ss, red);
+    if (!(ss > 0.0) || !isfinite(ss)) {
+        if (threadIdx.x == 0) atomicExch(status, 1);
+        return;
+    }
+    const double inv = 1.0 / sqrt(ss);
+    for (long long i = threadIdx.x; i < t.n; i += 256) p[i] = scal(p[i], inv);
+}
+cudaError_t launch_scale(const ScaleTask* d_tasks, int ntasks, bool cplx, int* status, cudaStream_t s) {
+    if (ntasks <= 0) return cudaSuccess;
+    if (cplx)
+        k_scale<double2><<<ntasks, 256, 0, s>>>(d_tasks, status);
+    else
+        k_scale<double><<<ntasks, 256, 0, s>>>(d_tasks, status);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- message assembly
+template <typename S>
+__global__ void __launch_bounds__(256) k_assemble(const AssembleTask* __restrict__ tasks) {
+    const AssembleTask& t = tasks[blockIdx.x];
+    const S c = mul(*(const S*)t.corner0, *(const S*)t.corner1);
+    for (int s = 0; s < t.nsites; ++s) {
+        const S* src = (const S*)t.src[s];
+        S* dst = (S*)t.dst[s];
+        for (long long i = threadIdx.x; i < t.size[s]; i += 256) dst[i] = (s == 0) ? mul(src[i], c) : src[i];
+    }
+}
+cudaError_t launch_assemble(const AssembleTask* d_tasks, int ntasks, bool cplx, cudaStream_t s) {
+    if (ntasks <= 0) return cudaSuccess;
+    if (cplx)
+        k_assemble<double2><<<ntasks, 256, 0, s>>>(d_tasks);
+    else
+        k_assemble<double><<<ntasks, 256, 0, s>>>(d_tasks);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- normalisation + residual term
+// tau = <I|m>: per site the matrix sum_k m[a][k*D+k][b], chained left to right.
+constexpr int NORM_MAXB = 1024;
+template <typename S>
+__global__ void __launch_bounds__(256) k_normalise(const NormTask* __restrict__ tasks) {
+    const NormTask& t = tasks[blockIdx.x];
+    __shared__ S v[NORM_MAXB], w[NORM_MAXB];
+    if (threadIdx.x == 0) v[0] = one<S>();
+    __syncthreads();
+    int na = 1;
+    for (int s = 0; s < t.nsites; ++s) {
+        const S* m = (const S*)t.sites[s];
+        const int A = t.a[s], K = t.k[s], B = t.b[s];
+        for (int b = threadIdx.x; b < B; b += 256) {
+            S acc = zero<S>();
+            for (int a = 0; a < na; ++a)
+                for (int k = 0; k < t.D; ++k) mac(acc, v[a], m[((long long)a * K + (k * t.D + k)) * B + b]);
+            w[b] = acc;
+        }
+        __syncthreads();
+        for (int b = threadIdx.x; b < B; b += 256) v[b] = w[b];
+        na = B;
+        (void)A;
+        __syncthreads();
+    }
+    const S tau = v[0];
+    const double mmr = *(const double*)t.mm;  // real part of <m|m>
+    const S mo = *(const S*)t.mo;
+    const double nrm = sqrt(fmax(mmr, 0.0));
+    if (!(nrm > 0.0) || !isfinite(nrm)) {
+        if (threadIdx.x == 0) {
+            atomicExch(t.status, 1);
+            *t.resid = 0.0;
+        }
+        return;
+    }
+    const double at = absv(tau);
+    const S ph = at > 1e-14 * nrm ? scal(conjv(tau), 1.0 / at) : one<S>();
+    const S sc = scal(ph, 1.0 / nrm);
+    S* p = (S*)t.site0;
+    for (long long i = threadIdx.x; i < t.size0; i += 256) p[i] = mul(p[i], sc);
+    if (threadIdx.x == 0) {
+        // <s m | m_old> = conj(s) <m|m_old>
+        const S ov = mul(conjv(sc), mo);
+        double re;
+        if constexpr (sizeof(S) == sizeof(double)) re = *(const double*)&ov;
+        else re = ((const double*)&ov)[0];
+        *t.resid = 2.0 - 2.0 * re;
+    }
+}
+cudaError_t launch_normalise(const NormTask* d_tasks, int ntasks, bool cplx, cudaStream_t s) {
+    if (ntasks <= 0) return cudaSuccess;
+    if (cplx)
+        k_normalise<double2><<<ntasks, 256, 0, s>>>(d_tasks);
+    else
+        k_normalise<double><<<ntasks, 256, 0, s>>>(d_tasks);
+    return cudaGetLastError();
+}
+
+__global__ void k_mean(const double* in, int n, double* out) {
+    __shared__ double red[32];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < n; i += 256) s += in[i];
+    s = block_sum(s, red);
+    if (threadIdx.x == 0) *out = n > 0 ? s / n : 0.0;
+}
+cudaError_t launch_mean(const double* in, int n, double* out, cudaStream_t s) {
+    k_mean<<<1, 256, 0, s>>>(in, n, out);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- double layer (Fig. 1(a,b))
+template <typename S>
+__global__ void k_double_layer(const DLTask* __restrict__ tasks) {
+    const DLTask& t = tasks[blockIdx.y];
+    const int Ku = t.Du * t.Du, Kl = t.Dl * t.Dl, Kd = t.Dd * t.Dd, Kr = t.Dr * t.Dr;
+    const long long total = (long long)Ku * Kl * Kd * Kr;
+    const long long vol = (long long)t.Du * t.Dl * t.Dd * t.Dr;
+    const S* T = (const S*)t.T;
+    const S* O = (const S*)t.O;
+    S* E = (S*)t.E;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+        long long r = e;
+        const int ir = (int)(r % Kr); r /= Kr;
+        const int id = (int)(r % Kd); r /= Kd;
+        const int il = (int)(r % Kl); r /= Kl;
+        const int iu = (int)r;
+        const int u = iu / t.Du, u2 = iu % t.Du, l = il / t.Dl, l2 = il % t.Dl;
+        const int dd = id / t.Dd, d2 = id % t.Dd, rr = ir / t.Dr, r2 = ir % t.Dr;
+        const long long ket = (((long long)u * t.Dl + l) * t.Dd + dd) * t.Dr + rr;
+        const long long bra = (((long long)u2 * t.Dl + l2) * t.Dd + d2) * t.Dr + r2;
+        S acc = zero<S>();
+        for (int pp = 0; pp < t.d; ++pp) {
+            // (O T)[p'] = sum_p O[p'][p] T[p]
+            S ot = zero<S>();
+            if (O) {
+                for (int p = 0; p < t.d; ++p) mac(ot, O[pp * t.d + p], T[p * vol + ket]);
+            } else {
+                ot = T[pp * vol + ket];
+            }
+            mac(acc, ot, conjv(T[pp * vol + bra]));
+        }
+        E[e] = acc;
+    }
+}
+cudaError_t launch_double_layer(const DLTask* d_tasks, int ntasks, long long max_out, bool cplx, cudaStream_t s) {
+    if (ntasks <= 0) return cudaSuccess;
+    long long bx = (max_out + 255) / 256;
+    if (bx > 4096) bx = 4096;
+    dim3 grid((unsigned)bx, ntasks);
+    if (cplx)
+        k_double_layer<double2><<<grid, 256, 0, s>>>(d_tasks);
+    else
+        k_double_layer<double><<<grid, 256, 0, s>>>(d_tasks);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- dtype conversion
+// in_dtype: 0 f64, 1 c128, 2 f32, 3 c64 (the bbp_dtype values).  n = scalar count.
+__global__ void k_convert(const void* in, int in_dtype, void* out, long long n, int cplx_out) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        double re = 0.0, im = 0.0;
+        switch (in_dtype) {
+            case 0: re = ((const double*)in)[i]; break;
+            case 1: re = ((const double*)in)[2 * i]; im = ((const double*)in)[2 * i + 1]; break;
+            case 2: re = ((const float*)in)[i]; break;
+            default: re = ((const float*)in)[2 * i]; im = ((const float*)in)[2 * i + 1]; break;
+        }
+        if (cplx_out) {
+            ((double*)out)[2 * i] = re;
+            ((double*)out)[2 * i + 1] = im;
+        } else {
+            ((double*)out)[i] = re;
+        }
+    }
+}
+cudaError_t launch_convert(const void* in, int in_dtype, void* out, long long n, bool cplx_out, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    long long b = (n + 255) / 256;
+    if (b > 4096) b = 4096;
+    k_convert<<<(unsigned)b, 256, 0, s>>>(in, in_dtype, out, n, cplx_out ? 1 : 0);
+    return cudaGetLastError();
+}
+
+__global__ void k_copy(const uint4* in, uint4* out, long long n16) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n16; i += (long long)gridDim.x * blockDim.x)
+        out[i] = in[i];
+}
+cudaError_t launch_copy(const void* in, void* out, long long bytes, cudaStream_t s) {
+    if (bytes <= 0) return cudaSuccess;
+    // every buffer in the arena is 256-byte aligned and sized in multiples of 16 bytes
+    const long long n16 = bytes / 16;
+    long long b = (n16 + 255) / 256;
+    if (b > 2048) b = 2048;
+    k_copy<<<(unsigned)b, 256, 0, s>>>((const uint4*)in, (uint4*)out, n16);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- fused column pair (read-out)
+template <typename S>
+__global__ void k_fuse(const FuseTask* __restrict__ tasks) {
+    const FuseTask& t = tasks[blockIdx.y];
+    const long long total = (long long)t.u1 * t.u2 * t.l1 * t.d1 * t.d2 * t.r2;
+    const S* A = (const S*)t.A;
+    const S* B = (const S*)t.B;
+    S* out = (S*)t.out;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+        long long r = e;
+        const int r2 = (int)(r % t.r2); r /= t.r2;
+        const int d2 = (int)(r % t.d2); r /= t.d2;
+        const int d1 = (int)(r % t.d1); r /= t.d1;
+        const int l1 = (int)(r % t.l1); r /= t.l1;
+        const int u2 = (int)(r % t.u2); r /= t.u2;
+        const int u1 = (int)r;
+        const S* a = A + u1 * t.a_u + l1 * t.a_l + d1 * t.a_d;
+        const S* b = B + u2 * t.b_u + d2 * t.b_d + r2 * t.b_r;
+        S acc = zero<S>();
+        for (int m = 0; m < t.m; ++m) mac(acc, a[m * t.a_r], b[m * t.b_l]);
+        out[e] = acc;
+    }
+}
+cudaError_t launch_fuse(const FuseTask* d_tasks, int ntasks, long long max_out, bool cplx, cudaStream_t s) {
+    if (ntasks <= 0) return cudaSuccess;
+    long long bx = (max_out + 255) / 256;
+    if (bx > 4096) bx = 4096;
+    dim3 grid((unsigned)bx, ntasks);
+    if (cplx)
+        k_fuse<double2><<<grid, 256, 0, s>>>(d_tasks);
+    else
+        k_fuse<double><<<grid, 256, 0, s>>>(d_tasks);
+    return cudaGetLastError();
+}
+
+}  // namespace bbp

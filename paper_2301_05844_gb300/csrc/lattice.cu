@@ -1,0 +1,739 @@
+// bbp_create_lattice / bbp_set_tensors / bbp_sweep / bbp_destroy and the message
+// inspection calls.  The sweep of Eq. 1 is planned here (see engine.cu for the fit).
+#include <cuda_runtime.h>
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <cmath>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "bbp.h"
+#include "bbp_internal.h"
+#include "engine.h"
+#include "lattice.h"
+
+using namespace bbp;
+
+#define CKR(expr)                                                                            \
+    do {                                                                                     \
+        cudaError_t e_ = (expr);                                                             \
+        if (e_ != cudaSuccess) return fail(BBP_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+// ------------------------------------------------------------------ geometry
+int bbp_lattice::tensor_index(int r, int c) const {
+    if (desc.boundary == BBP_OBC) return r * desc.Lx + c;
+    return (r % desc.Ly) * desc.Lx + (c % desc.Lx);
+}
+
+std::array<int, 4> bbp_lattice::site_dims(int r, int c) const {
+    const int D = desc.D;
+    if (desc.boundary != BBP_OBC) return {D, D, D, D};
+    return {r == 0 ? 1 : D, c == 0 ? 1 : D, r == desc.Ly - 1 ? 1 : D, c == desc.Lx - 1 ? 1 : D};
+}
+
+int bbp_lattice::neighbour(int blk, int dir) const {
+    if (desc.boundary != BBP_OBC) return blk;
+    const int R = blk / nbx, C = blk % nbx;
+    int R2 = R, C2 = C;
+    if (dir == DIR_LEFT) C2--;
+    if (dir == DIR_RIGHT) C2++;
+    if (dir == DIR_UP) R2--;
+    if (dir == DIR_DOWN) R2++;
+    if (R2 < 0 || R2 >= nby || C2 < 0 || C2 >= nbx) return -1;
+    return R2 * nbx + C2;
+}
+
+void bbp_lattice::block_origin(int blk, int& r0, int& c0) const {
+    r0 = (blk / nbx) * desc.by;
+    c0 = (blk % nbx) * desc.bx;
+}
+
+View3 bbp_lattice::msg_site(int it, int s, bool cur) const {
+    const Item& I = items[it];
+    return contiguous3((cur ? msg_cur : msg_new) + I.region_off + I.site_off[s], I.mb[s], K, I.mb[s + 1]);
+}
+
+static View3 one3(size_t one_off) {
+    View3 v;
+    v.off = one_off;
+    return v;  // 1x1x1, zero strides
+}
+
+std::vector<View3> bbp_lattice::incoming(int blk, int dir) const {
+    const int nsite = (dir == DIR_LEFT || dir == DIR_RIGHT) ? desc.by : desc.bx;
+    std::vector<View3> v;
+    const int nb = neighbour(blk, dir);
+    if (nb < 0) {
+        for (int i = 0; i < nsite; ++i) v.push_back(one3(one_off));
+        return v;
+    }
+    const int it = item_of[nb * 4 + opposite(dir)];
+    for (int i = 0; i < nsite; ++i) v.push_back(msg_site(it, i, true));
+    return v;
+}
+
+// Frame site (rf, cf) of a bh x bw region at (r0, c0) rotated so that `dir` is LEFT,
+// as the MPO site O[w,p,q,w2] = E'[u', r', l', d'].
+View4 bbp_lattice::frame_E(int dir, int r0, int c0, int bh, int bw, int rf, int cf) const {
+    int r = rf, c = cf;
+    int map[4] = {0, 1, 2, 3};  // frame leg (u',l',d',r') -> original leg (u,l,d,r)
+    if (dir == DIR_RIGHT) {
+        c = bw - 1 - cf;
+        map[0] = 0; map[1] = 3; map[2] = 2; map[3] = 1;
+    } else if (dir == DIR_UP) {
+        r = cf; c = rf;
+        map[0] = 1; map[1] = 0; map[2] = 3; map[3] = 2;
+    } else if (dir == DIR_DOWN) {
+        r = bh - 1 - cf; c = rf;
+        map[0] = 1; map[1] = 2; map[2] = 3; map[3] = 0;
+    }
+    const int t = tensor_index(r0 + r, c0 + c);
+    const auto dd = site_dims(r0 + r, c0 + c);
+    int Kd[4];
+    for (int i = 0; i < 4; ++i) Kd[i] = dd[i] * dd[i];
+    long long st[4] = {(long long)Kd[1] * Kd[2] * Kd[3], (long long)Kd[2] * Kd[3], Kd[3], 1};
+    View4 o;
+    o.off = E_off[t];
+    o.w = Kd[map[0]]; o.sw = st[map[0]];
+    o.p = Kd[map[3]]; o.sp = st[map[3]];
+    o.q = Kd[map[1]]; o.sq = st[map[1]];
+    o.w2 = Kd[map[2]]; o.sw2 = st[map[2]];
+    return o;
+}
+
+static std::vector<View3> reversed(const std::vector<View3>& m) {
+    std::vector<View3> r;
+    for (int i = (int)m.size() - 1; i >= 0; --i) r.push_back(reversed3(m[i]));
+    return r;
+}
+
+FrameMsgs bbp_lattice::frame_msgs(int dir, const std::vector<View3> in[4]) const {
+    FrameMsgs f;
+    if (dir == DIR_LEFT) {
+        f.T = in[DIR_UP]; f.R = in[DIR_RIGHT]; f.B = in[DIR_DOWN];
+    } else if (dir == DIR_RIGHT) {
+        f.T = reversed(in[DIR_UP]); f.R = in[DIR_LEFT]; f.B = reversed(in[DIR_DOWN]);
+    } else if (dir == DIR_UP) {
+        f.T = in[DIR_LEFT]; f.R = in[DIR_DOWN]; f.B = in[DIR_RIGHT];
+    } else {
+        f.T = reversed(in[DIR_LEFT]); f.R = in[DIR_UP]; f.B = reversed(in[DIR_RIGHT]);
+    }
+    return f;
+}
+
+namespace bbp {
+// Column MPO of frame column c: [top message site, E'(0,c) .. E'(H-1,c), bottom site].
+std::vector<View4> column_mpo(const bbp_lattice* L, int dir, int r0, int c0, int bh, int bw, const FrameMsgs& fm, int c) {
+    const int H = (dir == DIR_LEFT || dir == DIR_RIGHT) ? bh : bw;
+    std::vector<View4> O;
+    const View3& t = fm.T[c];
+    View4 top;
+    top.off = t.off; top.w = 1; top.p = t.b; top.q = t.a; top.w2 = t.k;
+    top.sw = 0; top.sp = t.sb; top.sq = t.sa; top.sw2 = t.sk;
+    O.push_back(top);
+    for (int r = 0; r < H; ++r) O.push_back(L->frame_E(dir, r0, c0, bh, bw, r, c));
+    const View3& b = fm.B[c];
+    View4 bot;
+    bot.off = b.off; bot.w = b.k; bot.p = b.b; bot.q = b.a; bot.w2 = 1;
+    bot.sw = b.sk; bot.sp = b.sb; bot.sq = b.sa; bot.sw2 = 0;
+    O.push_back(bot);
+    return O;
+}
+
+// Lay out and emit the fits of a set of column sweeps.  Each sweep i has a frame
+// (dir, region), its frame messages and chi; `keep` keeps every column's Y (read-out),
+// otherwise two ping-pong buffers are used.  Fills sweeps[i].fits.
+int plan_column_sweeps(bbp_lattice* L, Program& pr, std::vector<ColumnSweep>& cs, int max_sweeps, double fit_tol,
+                       bool rand_uses_sweep) {
+    const int ss = L->ss;
+    auto elem_alloc = [&](size_t elems) { return pr.arena_alloc(elems * (size_t)ss) / (size_t)ss; };
+    for (auto& s : cs) {
+        const int H = (s.dir == DIR_LEFT || s.dir == DIR_RIGHT) ? s.bh : s.bw;
+        const int W = (s.dir == DIR_LEFT || s.dir == DIR_RIGHT) ? s.bw : s.bh;
+        const int n = H + 2;
+        s.H = H;
+        s.W = W;
+        // shapes per column
+        std::vector<std::vector<View4>> Os(W);
+        std::vector<std::vector<int>> q(W), yb(W);
+        for (int c = 0; c < W; ++c) {
+            Os[c] = column_mpo(L, s.dir, s.r0, s.c0, s.bh, s.bw, s.fm, c);
+            for (auto& o : Os[c]) q[c].push_back(o.q);
+            yb[c] = bond_caps(q[c], s.chi);
+        }
+        // capacities
+        const int nbuf = s.keep ? W : 2;
+        std::vector<size_t> ycap(n, 1), acap(n + 1, 1);
+        size_t t1cap = 1, t2cap = 1, ytcap = 1, qrcap = 1;
+        for (int c = 0; c < W; ++c) {
+            for (int i = 0; i < n; ++i) ycap[i] = std::max(ycap[i], (size_t)yb[c][i] * q[c][i] * yb[c][i + 1]);
+            for (int i = 0; i < n; ++i) {
+                const View4& o = Os[c][i];
+                const int y = yb[c][i], y2 = yb[c][i + 1];
+                // X dims of this column
+                int x, x2;
+                if (c == W - 1) {
+                    x = (i == 0 || i == n - 1) ? 1 : s.fm.R[i - 1].a;
+                    x2 = (i == 0 || i == n - 1) ? 1 : s.fm.R[i - 1].b;
+                    if (i == 0) x2 = 1;
+                } else {
+                    x = yb[c + 1][i];
+                    x2 = yb[c + 1][i + 1];
+                }
+                const size_t p = o.p, w = o.w, w2 = o.w2, qq = o.q;
+                acap[i + 1] = std::max(acap[i + 1], (size_t)y2 * w2 * x2);
+                acap[i] = std::max(acap[i], (size_t)y * w * x);
+                t1cap = std::max({t1cap, (size_t)y * w * p * x2, (size_t)x * p * y2 * w2});
+                t2cap = std::max({t2cap, (size_t)y * x2 * qq * w2, (size_t)x * y2 * w * qq});
+                ytcap = std::max(ytcap, (size_t)y * qq * y2);
+                qrcap = std::max(qrcap, 2 * (size_t)y * qq * y2);
+            }
+        }
+        std::vector<std::vector<size_t>> ybuf(nbuf, std::vector<size_t>(n));
+        for (int bi = 0; bi < nbuf; ++bi)
+            for (int i = 0; i < n; ++i) ybuf[bi][i] = elem_alloc(ycap[i]);
+        std::vector<size_t> A(n + 1), B(n + 1);
+        A[0] = L->one_off;
+        B[n] = L->one_off;
+        for (int i = 1; i <= n; ++i) A[i] = elem_alloc(acap[i]);
+        for (int i = 0; i < n; ++i) B[i] = elem_alloc(acap[i]);
+        const size_t T1 = elem_alloc(t1cap), T2 = elem_alloc(t2cap), Yt = elem_alloc(ytcap), qrw = elem_alloc(qrcap);
+        const size_t losses = pr.arena_alloc(sizeof(double) * (size_t)max_sweeps * 2 * (n - 1));
+        const size_t active = pr.arena_alloc(sizeof(int));
+        s.fits.assign(W, FitSpec());
+        for (int c = W - 1; c >= 0; --c) {
+            FitSpec& f = s.fits[c];
+            f.O = Os[c];
+            f.ybond = yb[c];
+            const int bi = s.keep ? c : (c % 2);
+            f.Y = ybuf[bi];
+            if (c == W - 1) {
+                f.X.push_back(one3(L->one_off));
+                for (auto& v : s.fm.R) f.X.push_back(v);
+                f.X.push_back(one3(L->one_off));
+            } else {
+                const int pb = s.keep ? c + 1 : ((c + 1) % 2);
+                for (int i = 0; i < n; ++i)
+                    f.X.push_back(contiguous3(ybuf[pb][i], yb[c + 1][i], q[c + 1][i], yb[c + 1][i + 1]));
+            }
+            for (int i = 0; i < n; ++i)
+                if (f.X[i].k != f.O[i].p) return fail(BBP_ERR_INVALID, "internal: column MPS / MPO leg mismatch");
+            f.Aenv = A;
+            f.Benv = B;
+            f.T1 = T1; f.T2 = T2; f.Yt = Yt; f.qrw = qrw;
+            f.losses = losses;
+            f.active = active;
+            f.counter = pr.arena_alloc(sizeof(int));
+            f.stream = stream_id(s.tag, s.outer, s.msg, (uint64_t)c, 0);
+        }
+    }
+    // emit, lockstep over column steps
+    int Wmax = 0;
+    for (auto& s : cs) Wmax = std::max(Wmax, s.W);
+    for (int k = 0; k < Wmax; ++k) {
+        std::vector<FitSpec*> group;
+        for (auto& s : cs) {
+            const int c = s.W - 1 - k;
+            if (c >= 0) group.push_back(&s.fits[c]);
+        }
+        emit_fits(pr, ss, group, max_sweeps, fit_tol, nullptr, rand_uses_sweep);
+    }
+    return BBP_OK;
+}
+}  // namespace bbp
+
+// ------------------------------------------------------------------ plan one sweep
+static int plan_sweep(bbp_lattice* L) {
+    Program& pr = L->sweep;
+    pr.cplx = L->cplx;
+    const int ss = L->ss;
+    // the column sweep of every item
+    std::vector<ColumnSweep> cs;
+    for (int it = 0; it < (int)L->items.size(); ++it) {
+        const Item& I = L->items[it];
+        std::vector<View3> in[4];
+        for (int d = 0; d < 4; ++d) in[d] = L->incoming(I.block, d);
+        ColumnSweep s;
+        s.dir = I.dir;
+        L->block_origin(I.block, s.r0, s.c0);
+        s.bh = L->desc.by;
+        s.bw = L->desc.bx;
+        s.fm = L->frame_msgs(I.dir, in);
+        s.chi = L->desc.chi;
+        s.keep = false;
+        s.tag = 0;
+        s.outer = 0;
+        s.msg = (uint64_t)I.msgid;
+        cs.push_back(s);
+    }
+    int rc = plan_column_sweeps(L, pr, cs, L->desc.fit_max_sweeps, L->desc.fit_tol, true);
+    if (rc) return rc;
+    for (int it = 0; it < (int)L->items.size(); ++it) L->items[it].fits = cs[it].fits;
+    // message assembly from the final column MPS (column 0)
+    std::vector<OverlapSpec> ov;
+    std::vector<AssembleTask> at;
+    std::vector<NormTask> nt;
+    auto elem_alloc = [&](size_t elems) { return pr.arena_alloc(elems * (size_t)ss) / (size_t)ss; };
+    const int K = L->K;
+    for (int it = 0; it < (int)L->items.size(); ++it) {
+        const Item& I = L->items[it];
+        const FitSpec& f = I.fits[0];
+        const int n = f.n();
+        if (I.b > 16) return fail(BBP_ERR_INVALID, "block edge longer than 16 sites");
+        AssembleTask a{};
+        a.nsites = I.b;
+        for (int s = 0; s < I.b; ++s) {
+            const View3 dst = L->msg_site(it, s, false);
+            if (f.ybond[s + 1] != dst.a || f.O[s + 1].q != dst.k || f.ybond[s + 2] != dst.b)
+                return fail(BBP_ERR_INVALID, "internal: message shape mismatch");
+            a.src[s] = P(f.Y[s + 1] * ss);
+            a.dst[s] = P(dst.off * ss);
+            a.size[s] = (long long)dst.a * dst.k * dst.b;
+        }
+        a.corner0 = P(f.Y[0] * ss);
+        a.corner1 = P(f.Y[n - 1] * ss);
+        at.push_back(a);
+        // overlap chains <m|m> and <m|m_old>
+        int amax = 1;
+        for (int v : I.mb) amax = std::max(amax, v);
+        for (int which = 0; which < 2; ++which) {
+            OverlapSpec o;
+            for (int s = 0; s < I.b; ++s) {
+                o.M.push_back(L->msg_site(it, s, false));
+                o.N.push_back(L->msg_site(it, s, which == 1));
+            }
+            o.one = L->one_off;
+            o.E[0] = elem_alloc((size_t)amax * amax);
+            o.E[1] = elem_alloc((size_t)amax * amax);
+            o.T = elem_alloc((size_t)amax * K * amax);
+            o.result = elem_alloc(1);
+            ov.push_back(o);
+        }
+        NormTask nm{};
+        const View3 s0 = L->msg_site(it, 0, false);
+        nm.site0 = P(s0.off * ss);
+        nm.size0 = (long long)s0.a * s0.k * s0.b;
+        nm.nsites = I.b;
+        nm.D = L->desc.D;
+        for (int s = 0; s < I.b; ++s) {
+            const View3 v = L->msg_site(it, s, false);
+            nm.sites[s] = P(v.off * ss);
+            nm.a[s] = v.a;
+            nm.k[s] = v.k;
+            nm.b[s] = v.b;
+        }
+        nm.mm = P(ov[ov.size() - 2].result * ss);
+        nm.mo = P(ov[ov.size() - 1].result * ss);
+        nm.resid = (double*)P((size_t)it * sizeof(double) + 1);  // patched below
+        nt.push_back(nm);
+    }
+    {
+        Step s;
+        s.kind = ST_ASM;
+        s.first = pr.asmb.size();
+        s.count = (int)at.size();
+        pr.asmb.insert(pr.asmb.end(), at.begin(), at.end());
+        pr.steps.push_back(s);
+    }
+    emit_overlaps(pr, ss, ov);
+    const size_t resid = pr.arena_alloc(sizeof(double) * std::max<size_t>(1, L->items.size()));
+    const size_t residual = pr.arena_alloc(sizeof(double));
+    const size_t status = pr.arena_alloc(sizeof(int));
+    const size_t sweepctr = pr.arena_alloc(sizeof(int));
+    for (int it = 0; it < (int)nt.size(); ++it) {
+        nt[it].resid = (double*)P(resid + (size_t)it * sizeof(double));
+        nt[it].status = (int*)P(status);
+    }
+    {
+        Step s;
+        s.kind = ST_NORM;
+        s.first = pr.nrm.size();
+        s.count = (int)nt.size();
+        pr.nrm.insert(pr.nrm.end(), nt.begin(), nt.end());
+        pr.steps.push_back(s);
+    }
+    pr.simple(ST_MEAN, P(resid), P(residual), (long long)L->items.size(), 0);
+    pr.simple(ST_COPY, P(L->msg_new * ss), P(L->msg_cur * ss), (long long)(L->msg_elems * ss), 0);
+    pr.simple(ST_INC, P(sweepctr), nullptr, 1, 0);
+    L->d_resid_terms = (double*)(uintptr_t)resid;
+    L->d_residual = (double*)(uintptr_t)residual;
+    L->d_status = (int*)(uintptr_t)status;
+    L->d_sweep = (int*)(uintptr_t)sweepctr;
+    return BBP_OK;
+}
+
+// ------------------------------------------------------------------ C ABI
+extern "C" {
+
+const char* bbp_last_error(void) { return bbp::g_err.c_str(); }
+
+static int validate(const bbp_lattice_desc* d) {
+    if (!d) return fail(BBP_ERR_INVALID, "desc is NULL");
+    if (d->Lx < 1 || d->Ly < 1 || d->d < 1 || d->D < 1 || d->bx < 1 || d->by < 1 || d->chi < 1)
+        return fail(BBP_ERR_INVALID, "dimensions must be positive");
+    if (d->boundary != BBP_OBC && d->boundary != BBP_INFINITE) return fail(BBP_ERR_INVALID, "unknown boundary");
+    if (d->boundary == BBP_OBC && (d->Lx % d->bx || d->Ly % d->by))
+        return fail(BBP_ERR_INVALID, "block size must divide the lattice");
+    if (d->boundary == BBP_INFINITE && (d->bx % d->Lx || d->by % d->Ly))
+        return fail(BBP_ERR_INVALID, "infinite block must be a multiple of the unit cell");
+    if (d->dtype < 0 || d->dtype > 3) return fail(BBP_ERR_INVALID, "unknown dtype");
+    if (d->prec != BBP_PREC_FP64) return fail(BBP_ERR_INVALID, "precision not available in this build");
+    if (d->fit_max_sweeps < 1 || d->fit_max_sweeps > 64) return fail(BBP_ERR_INVALID, "fit_max_sweeps must be 1..64");
+    if (d->bx > 16 || d->by > 16) return fail(BBP_ERR_INVALID, "block sides are limited to 16 sites");
+    if (d->D > 16 || d->d > 64) return fail(BBP_ERR_INVALID, "D or d too large");
+    if (d->init_mode != 0 && d->init_mode != 1) return fail(BBP_ERR_INVALID, "init_mode must be 0 or 1");
+    return BBP_OK;
+}
+
+int bbp_create_lattice(const bbp_lattice_desc* desc, bbp_lattice** out) {
+    if (!out) return fail(BBP_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    int rc = validate(desc);
+    if (rc) return rc;
+    bbp_lattice* L = new (std::nothrow) bbp_lattice();
+    if (!L) return fail(BBP_ERR_OOM, "host allocation failed");
+    L->desc = *desc;
+    if (L->desc.chi_exp <= 0) L->desc.chi_exp = std::max(desc->chi, 2 * desc->D * desc->D + 10);
+    L->cplx = desc->dtype == BBP_C128 || desc->dtype == BBP_C64;
+    L->ss = L->cplx ? 16 : 8;
+    L->K = desc->D * desc->D;
+    if (desc->boundary == BBP_OBC) {
+        L->nbx = desc->Lx / desc->bx;
+        L->nby = desc->Ly / desc->by;
+    }
+    L->nblocks = L->nbx * L->nby;
+    L->ntens = desc->Lx * desc->Ly;
+    Program& pr = L->sweep;
+    auto elem_alloc = [&](size_t elems) { return pr.arena_alloc(elems * (size_t)L->ss) / (size_t)L->ss; };
+    L->one_off = elem_alloc(1);
+    // tensors and double layers
+    size_t raw_scalars = 0;
+    for (int r = 0; r < (desc->boundary == BBP_OBC ? desc->Ly : desc->Ly); ++r)
+        for (int c = 0; c < desc->Lx; ++c) {
+            const auto dd = L->site_dims(r, c);
+            L->tdims.push_back(dd);
+            const size_t vol = (size_t)desc->d * dd[0] * dd[1] * dd[2] * dd[3];
+            L->T_off.push_back(elem_alloc(vol));
+            L->E_off.push_back(elem_alloc((size_t)dd[0] * dd[0] * dd[1] * dd[1] * dd[2] * dd[2] * dd[3] * dd[3]));
+            raw_scalars += vol;
+        }
+    L->T_elems = raw_scalars;
+    const int in_ss = (desc->dtype == BBP_F64) ? 8 : (desc->dtype == BBP_C128) ? 16 : (desc->dtype == BBP_F32) ? 4 : 8;
+    L->raw_bytes = raw_scalars * in_ss;
+    L->raw_off = pr.arena_alloc(L->raw_bytes);
+    // items and the message store
+    L->item_of.assign(L->nblocks * 4, -1);
+    for (int blk = 0; blk < L->nblocks; ++blk)
+        for (int dir = 0; dir < 4; ++dir) {
+            if (L->neighbour(blk, dir) < 0) continue;
+            Item I;
+            I.block = blk;
+            I.dir = dir;
+            I.msgid = 4 * blk + dir;
+            I.b = (dir == DIR_LEFT || dir == DIR_RIGHT) ? desc->by : desc->bx;
+            std::vector<int> ph(I.b, L->K);
+            I.mb = bond_caps(ph, desc->chi);
+            L->item_of[blk * 4 + dir] = (int)L->items.size();
+            L->items.push_back(I);
+        }
+    size_t off = 0;
+    for (auto& I : L->items) {
+        I.region_off = off;
+        for (int s = 0; s < I.b; ++s) {
+            I.site_off.push_back(off - I.region_off);
+            off += (size_t)I.mb[s] * L->K * I.mb[s + 1];
+            off = (off + 1) & ~(size_t)1;  // keep every site 16-byte aligned
+        }
+        I.region_elems = off - I.region_off;
+    }
+    L->msg_elems = std::max<size_t>(off, 2);
+    L->msg_cur = elem_alloc(L->msg_elems);
+    L->msg_new = elem_alloc(L->msg_elems);
+    rc = plan_sweep(L);
+    if (rc) {
+        delete L;
+        return rc;
+    }
+    {
+        const std::string v = pr.validate();
+        if (!v.empty()) {
+            delete L;
+            return fail(BBP_ERR_INVALID, "internal plan check: " + v);
+        }
+    }
+    // one arena for everything
+    L->arena_bytes = pr.arena_used;
+    cudaError_t e = cudaMalloc((void**)&L->arena, L->arena_bytes);
+    if (e != cudaSuccess) {
+        delete L;
+        return fail(BBP_ERR_OOM, std::string("arena of ") + std::to_string(L->arena_bytes) + " bytes: " + cudaGetErrorString(e));
+    }
+    char* base = L->arena;
+    pr.relocate(base);
+    pr.status = (int*)(base + (uintptr_t)L->d_status);
+    L->d_status = pr.status;
+    L->d_resid_terms = (double*)(base + (uintptr_t)L->d_resid_terms);
+    L->d_residual = (double*)(base + (uintptr_t)L->d_residual);
+    L->d_sweep = (int*)(base + (uintptr_t)L->d_sweep);
+    e = pr.upload_tasks();
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&L->h_pinned, 64);
+    if (e == cudaSuccess && desc->stream == nullptr) {
+        e = cudaStreamCreateWithFlags(&L->stream, cudaStreamNonBlocking);
+        L->own_stream = true;
+    } else {
+        L->stream = (cudaStream_t)desc->stream;
+    }
+    if (e == cudaSuccess) e = cudaMemsetAsync(L->arena, 0, L->arena_bytes, L->stream);
+    if (e == cudaSuccess) {
+        double one[2] = {1.0, 0.0};
+        e = cudaMemcpyAsync(base + L->one_off * L->ss, one, L->ss, cudaMemcpyHostToDevice, L->stream);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(L->stream);
+    if (e != cudaSuccess) {
+        bbp_destroy(L);
+        return fail(BBP_ERR_CUDA, std::string("create: ") + cudaGetErrorString(e));
+    }
+    *out = L;
+    return BBP_OK;
+}
+
+void bbp_destroy(bbp_lattice* L) {
+    if (!L) return;
+    L->sweep.free_all();
+    if (L->arena) cudaFree(L->arena);
+    if (L->h_pinned) cudaFreeHost(L->h_pinned);
+    if (L->own_stream && L->stream) cudaStreamDestroy(L->stream);
+    delete L;
+}
+
+// Initial messages (App. A: messages start from a chosen state; init_mode 0 is the
+// product of delta_{ket,bra}, init_mode 1 a random positive MPDO of bond 1), each
+// normalised to unit 2-norm with <I|m> > 0.
+static void init_messages(bbp_lattice* L, std::vector<double>& host) {
+    const int D = L->desc.D, K = L->K, cw = L->cplx ? 2 : 1;
+    host.assign(L->msg_elems * cw, 0.0);
+    for (int it = 0; it < (int)L->items.size(); ++it) {
+        const Item& I = L->items[it];
+        double total = 1.0;
+        std::vector<std::vector<double>> sites(I.b);
+        for (int s = 0; s < I.b; ++s) {
+            std::vector<double> v(K, 0.0);
+            if (L->desc.init_mode == 0) {
+                for (int k = 0; k < D; ++k) v[k * D + k] = 1.0;
+            } else {
+                // G with normal entries (Box-Muller on the counter-based uniforms), site = G G^T
+                const uint64_t stream = stream_id(2, 0, (uint64_t)I.msgid, 0, 0) + (uint64_t)s;
+                std::vector<double> g(D * D);
+                for (int j = 0; j < D * D; ++j) {
+                    const double u1 = (uniform_pm1(L->desc.seed, stream, 2 * j) + 1.0) * 0.5;
+                    const double u2 = (uniform_pm1(L->desc.seed, stream, 2 * j + 1) + 1.0) * 0.5;
+                    g[j] = std::sqrt(-2.0 * std::log1p(-u1)) * std::cos(2.0 * M_PI * u2);
+                }
+                for (int a = 0; a < D; ++a)
+                    for (int b = 0; b < D; ++b) {
+                        double acc = 0;
+                        for (int k = 0; k < D; ++k) acc += g[a * D + k] * g[b * D + k];
+                        v[a * D + b] = acc;
+                    }
+            }
+            double n2 = 0;
+            for (double x : v) n2 += x * x;
+            total *= std::sqrt(n2);
+            sites[s] = v;
+        }
+        for (int s = 0; s < I.b; ++s) {
+            // bond-1 sites: only entries [0][k][0] are nonzero
+            const size_t base = I.region_off + I.site_off[s];
+            for (int k = 0; k < K; ++k) {
+                const double val = sites[s][k] / (s == 0 ? total : 1.0);
+                // element [a=0][k][b=0] of a site with bonds (mb[s], mb[s+1]) sits at k * mb[s+1]
+                host[(base + (size_t)k * I.mb[s + 1]) * cw] = val;
+            }
+        }
+    }
+}
+
+int bbp_set_tensors(bbp_lattice* L, const void* data, int on_device) {
+    if (!L) return fail(BBP_ERR_INVALID, "lattice is NULL");
+    if (!data) return fail(BBP_ERR_INVALID, "data is NULL");
+    char* base = L->arena;
+    cudaStream_t st = L->stream;
+    CKR(cudaMemcpyAsync(base + L->raw_off, data, L->raw_bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+    // convert into the compute type, tensor by tensor (raw is packed, T slabs are aligned)
+    size_t in_scalar = 0;
+    const int in_ss = (L->desc.dtype == BBP_F64) ? 8 : (L->desc.dtype == BBP_C128) ? 16 : (L->desc.dtype == BBP_F32) ? 4 : 8;
+    std::vector<DLTask> dl;
+    long long maxout = 1;
+    for (int t = 0; t < L->ntens; ++t) {
+        const auto& dd = L->tdims[t];
+        const long long vol = (long long)L->desc.d * dd[0] * dd[1] * dd[2] * dd[3];
+        CKR(launch_convert(base + L->raw_off + in_scalar * in_ss, L->desc.dtype, base + L->T_off[t] * L->ss, vol, L->cplx, st));
+        in_scalar += vol;
+        DLTask k{};
+        k.T = base + L->T_off[t] * L->ss;
+        k.E = base + L->E_off[t] * L->ss;
+        k.O = nullptr;
+        k.d = L->desc.d;
+        k.Du = dd[0]; k.Dl = dd[1]; k.Dd = dd[2]; k.Dr = dd[3];
+        dl.push_back(k);
+        maxout = std::max(maxout, (long long)dd[0] * dd[0] * dd[1] * dd[1] * dd[2] * dd[2] * dd[3] * dd[3]);
+    }
+    DLTask* d_dl = nullptr;
+    CKR(cudaMallocAsync((void**)&d_dl, dl.size() * sizeof(DLTask), st));
+    CKR(cudaMemcpyAsync(d_dl, dl.data(), dl.size() * sizeof(DLTask), cudaMemcpyHostToDevice, st));
+    CKR(launch_double_layer(d_dl, (int)dl.size(), maxout, L->cplx, st));
+    CKR(cudaFreeAsync(d_dl, st));
+    std::vector<double> host;
+    init_messages(L, host);
+    CKR(cudaMemcpyAsync(base + L->msg_cur * L->ss, host.data(), host.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+    CKR(cudaMemsetAsync(L->d_sweep, 0, sizeof(int), st));
+    CKR(cudaMemsetAsync(L->d_status, 0, sizeof(int), st));
+    CKR(cudaStreamSynchronize(st));
+    L->has_tensors = true;
+    L->sweeps = 0;
+    L->kernels = 0;
+    L->first_residual = L->last_residual = 0;
+    return BBP_OK;
+}
+
+static int ensure_graph(bbp_lattice* L) {
+    Program& pr = L->sweep;
+    if (pr.exec) return BBP_OK;
+    cudaGraph_t g = nullptr;
+    CKR(cudaStreamBeginCapture(L->stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = pr.launch_all(L->stream, L->d_sweep, L->desc.seed);
+    cudaError_t e2 = cudaStreamEndCapture(L->stream, &g);
+    if (e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return fail(BBP_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(e));
+    }
+    CKR(e2);
+    e = cudaGraphInstantiate(&pr.exec, g, 0);
+    cudaGraphDestroy(g);
+    CKR(e);
+    return BBP_OK;
+}
+
+int bbp_sweep(bbp_lattice* L, int n_sweeps, double* residual_out, int* sweeps_done) {
+    if (!L) return fail(BBP_ERR_INVALID, "lattice is NULL");
+    if (!L->has_tensors) return fail(BBP_ERR_STATE, "bbp_set_tensors has not been called");
+    int rc = ensure_graph(L);
+    if (rc) return rc;
+    const bool fixed = n_sweeps > 0;
+    const int cap = fixed ? n_sweeps : std::max(1, L->desc.max_sweeps);
+    int done = 0;
+    double r = 0.0;
+    bool converged = fixed;
+    if (L->items.empty()) {  // a single block without neighbours: nothing to iterate
+        if (residual_out) *residual_out = 0.0;
+        if (sweeps_done) *sweeps_done = 0;
+        return BBP_OK;
+    }
+    for (int k = 0; k < cap; ++k) {
+        CKR(cudaGraphLaunch(L->sweep.exec, L->stream));
+        CKR(cudaMemcpyAsync(L->h_pinned, L->d_residual, sizeof(double), cudaMemcpyDeviceToHost, L->stream));
+        CKR(cudaMemcpyAsync((int*)(L->h_pinned + 1), L->d_status, sizeof(int), cudaMemcpyDeviceToHost, L->stream));
+        CKR(cudaStreamSynchronize(L->stream));
+        L->kernels += L->sweep.kernel_count();
+        done++;
+        L->sweeps++;
+        r = L->h_pinned[0];
+        if (*(int*)(L->h_pinned + 1) != 0 || !std::isfinite(r)) {
+            if (residual_out) *residual_out = r;
+            if (sweeps_done) *sweeps_done = done;
+            return fail(BBP_ERR_NUMERIC, "a message or column MPS has zero or non-finite norm");
+        }
+        if (L->sweeps == 1) L->first_residual = r;
+        L->last_residual = r;
+        if (!fixed) {
+            const double crit = L->desc.stop_relative ? (L->first_residual > 0 ? r / L->first_residual : 0.0) : r;
+            if (crit < L->desc.tol) {
+                converged = true;
+                break;
+            }
+        }
+    }
+    if (residual_out) *residual_out = r;
+    if (sweeps_done) *sweeps_done = done;
+    return converged ? BBP_OK : BBP_NOT_CONVERGED;
+}
+
+int bbp_get_message(bbp_lattice* L, int block, int dir, int* nsites, int* bonds, double* out) {
+    if (!L) return fail(BBP_ERR_INVALID, "lattice is NULL");
+    if (block < 0 || block >= L->nblocks || dir < 0 || dir > 3 || L->item_of[block * 4 + dir] < 0)
+        return fail(BBP_ERR_INVALID, "no such message");
+    const int it = L->item_of[block * 4 + dir];
+    const Item& I = L->items[it];
+    if (nsites) *nsites = I.b;
+    if (bonds)
+        for (int s = 0; s <= I.b; ++s) bonds[s] = I.mb[s];
+    if (out) {
+        size_t o = 0;
+        for (int s = 0; s < I.b; ++s) {
+            const View3 v = L->msg_site(it, s, true);
+            const size_t cnt = (size_t)v.a * v.k * v.b * (L->cplx ? 2 : 1);
+            CKR(cudaMemcpyAsync(out + o, L->arena + v.off * L->ss, cnt * sizeof(double), cudaMemcpyDeviceToHost, L->stream));
+            o += cnt;
+        }
+        CKR(cudaStreamSynchronize(L->stream));
+    }
+    return BBP_OK;
+}
+
+int bbp_set_message(bbp_lattice* L, int block, int dir, const double* in) {
+    if (!L || !in) return fail(BBP_ERR_INVALID, "NULL argument");
+    if (block < 0 || block >= L->nblocks || dir < 0 || dir > 3 || L->item_of[block * 4 + dir] < 0)
+        return fail(BBP_ERR_INVALID, "no such message");
+    const int it = L->item_of[block * 4 + dir];
+    const Item& I = L->items[it];
+    size_t o = 0;
+    for (int s = 0; s < I.b; ++s) {
+        const View3 v = L->msg_site(it, s, true);
+        const size_t cnt = (size_t)v.a * v.k * v.b * (L->cplx ? 2 : 1);
+        CKR(cudaMemcpyAsync(L->arena + v.off * L->ss, in + o, cnt * sizeof(double), cudaMemcpyHostToDevice, L->stream));
+        o += cnt;
+    }
+    CKR(cudaStreamSynchronize(L->stream));
+    return BBP_OK;
+}
+
+int bbp_get_stats(bbp_lattice* L, bbp_stats* out) {
+    if (!L || !out) return fail(BBP_ERR_INVALID, "NULL argument");
+    memset(out, 0, sizeof(*out));
+    // fit sweeps executed: per-fit counters (device)
+    const Program& pr = L->sweep;
+    std::vector<int> cnt(pr.chk.size());
+    long long fs = 0, fits = 0;
+    double gated = 0;
+    // every CheckTask of the sweep points at one counter per fit; read each once
+    std::vector<const int*> seen;
+    for (const auto& t : pr.chk) {
+        if (std::find(seen.begin(), seen.end(), t.counter) != seen.end()) continue;
+        seen.push_back(t.counter);
+        int v = 0;
+        CKR(cudaMemcpy(&v, t.counter, sizeof(int), cudaMemcpyDeviceToHost));
+        fs += v;
+        fits++;
+    }
+    const double per_sweep = pr.gated_flops / std::max(1, L->desc.fit_max_sweeps - 1);
+    (void)gated;
+    out->fit_sweeps = fs;
+    out->fits = fits * (long long)L->sweeps;
+    // flops: the ungated part per sweep, plus the gated sweeps that actually ran
+    const double static_per_sweep = pr.static_flops;
+    const double mean_sweeps_per_fit = fits ? (double)fs / (double)(fits * std::max(1, L->sweeps)) : 0.0;
+    out->flops = L->sweeps * (static_per_sweep + per_sweep * std::max(0.0, mean_sweeps_per_fit - 1.0)) + L->readout_flops;
+    out->qr_flops = L->sweeps * (pr.static_qr_flops +
+                                 pr.gated_qr_flops / std::max(1, L->desc.fit_max_sweeps - 1) * std::max(0.0, mean_sweeps_per_fit - 1.0));
+    out->kernels = L->kernels + L->readout_kernels;
+    out->sweeps = L->sweeps;
+    out->last_residual = L->last_residual;
+    out->first_residual = L->first_residual;
+    return BBP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,486 @@
+// bbp_expect: expectation values from a block and its converged incoming messages.
+//
+// App. A: once the messages have converged, the block plus its four incoming
+// messages is contracted by bMPS with the larger bond chi = 2D^2+10 (Fig. 1(f)).
+// Here every region (a block, or two neighbouring blocks merged for a pair that
+// crosses a block edge) gets its left and right environment columns L_c, R_c from
+// the same lockstep zip-up fits as the sweep, and each term is the exact
+// top-to-bottom closing L_c . column(s) . R_c with E^O at the operator sites;
+// <O> = N_O / N_I is formed in FP64.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <complex>
+#include <cstring>
+#include <map>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "bbp.h"
+#include "bbp_internal.h"
+#include "engine.h"
+#include "lattice.h"
+
+using namespace bbp;
+
+namespace {
+
+struct Op4 {
+    size_t off = 0;
+    int u = 1, l = 1, d = 1, r = 1;
+    long long su = 0, sl = 0, sd = 0, sr = 0;
+};
+
+struct Region {
+    int rid = 0, r0 = 0, c0 = 0, h = 0, w = 0;
+    std::vector<int> blocks;
+    std::vector<View3> in[4];
+    int sweepL = -1, sweepR = -1;  // indices into the column-sweep list
+};
+
+struct Closing {
+    int region = 0, col = 0, ncols = 1;
+    std::vector<std::pair<int, int>> pos;     // local (row, col) of the operator sites
+    std::vector<std::vector<double>> ops;     // d*d scalars each (S layout)
+};
+
+Op4 op_from_top(const View3& t) {
+    Op4 o;
+    o.off = t.off; o.u = 1; o.l = t.a; o.d = t.k; o.r = t.b;
+    o.su = 0; o.sl = t.sa; o.sd = t.sk; o.sr = t.sb;
+    return o;
+}
+Op4 op_from_bottom(const View3& b) {
+    Op4 o;
+    o.off = b.off; o.u = b.k; o.l = b.a; o.d = 1; o.r = b.b;
+    o.su = b.sk; o.sl = b.sa; o.sd = 0; o.sr = b.sb;
+    return o;
+}
+Op4 op_contig(size_t off, int u, int l, int d, int r) {
+    Op4 o;
+    o.off = off; o.u = u; o.l = l; o.d = d; o.r = r;
+    o.su = (long long)l * d * r; o.sl = (long long)d * r; o.sd = r; o.sr = 1;
+    return o;
+}
+
+}  // namespace
+
+#define CKR(expr)                                                                            \
+    do {                                                                                     \
+        cudaError_t e_ = (expr);                                                             \
+        if (e_ != cudaSuccess) return fail(BBP_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+extern "C" int bbp_expect(bbp_lattice* L, const bbp_term* terms, int n_terms, double* out_re, double* out_im) {
+    if (!L) return fail(BBP_ERR_INVALID, "lattice is NULL");
+    if (!L->has_tensors) return fail(BBP_ERR_STATE, "bbp_set_tensors has not been called");
+    if (n_terms < 0 || (n_terms > 0 && (!terms || !out_re))) return fail(BBP_ERR_INVALID, "bad term arguments");
+    if (n_terms == 0) return BBP_OK;
+    const bbp_lattice_desc& ds = L->desc;
+    const int d = ds.d, ss = L->ss;
+    const bool obc = ds.boundary == BBP_OBC;
+    const int Wlat = obc ? ds.Lx : ds.bx, Hlat = obc ? ds.Ly : ds.by;
+
+    // ---- regions and closings
+    std::vector<Region> regions;
+    std::map<int, int> region_of;
+    auto get_region = [&](const std::vector<std::pair<int, int>>& rc, int& out) -> int {
+        int rid, r0, c0, h, w;
+        std::vector<int> blks;
+        if (!obc) {
+            rid = 0; r0 = 0; c0 = 0; h = ds.by; w = ds.bx;
+            blks = {0};
+        } else {
+            for (auto& p : rc) blks.push_back((p.first / ds.by) * L->nbx + p.second / ds.bx);
+            if (blks.size() == 1 || blks[0] == blks[1]) {
+                rid = blks[0];
+                L->block_origin(rid, r0, c0);
+                h = ds.by; w = ds.bx;
+                blks = {rid};
+            } else {
+                const int dr = std::abs(rc[0].first - rc[1].first), dc = std::abs(rc[0].second - rc[1].second);
+                if (dr + dc != 1) return fail(BBP_ERR_INVALID, "a two-site term across blocks must be a nearest-neighbour pair");
+                const int a = std::min(blks[0], blks[1]), b = std::max(blks[0], blks[1]);
+                L->block_origin(a, r0, c0);
+                if (dc == 1) {
+                    rid = L->nblocks + 2 * a; h = ds.by; w = 2 * ds.bx;
+                } else {
+                    rid = L->nblocks + 2 * a + 1; h = 2 * ds.by; w = ds.bx;
+                }
+                blks = {a, b};
+            }
+        }
+        auto it = region_of.find(rid);
+        if (it != region_of.end()) {
+            out = it->second;
+            return BBP_OK;
+        }
+        Region R;
+        R.rid = rid; R.r0 = r0; R.c0 = c0; R.h = h; R.w = w; R.blocks = blks;
+        if (blks.size() == 1) {
+            for (int dd = 0; dd < 4; ++dd) R.in[dd] = L->incoming(blks[0], dd);
+        } else {
+            std::vector<View3> ia[4], ib[4];
+            for (int dd = 0; dd < 4; ++dd) {
+                ia[dd] = L->incoming(blks[0], dd);
+                ib[dd] = L->incoming(blks[1], dd);
+            }
+            const bool horiz = w > ds.bx;
+            auto cat = [](std::vector<View3> x, const std::vector<View3>& y) {
+                x.insert(x.end(), y.begin(), y.end());
+                return x;
+            };
+            if (horiz) {
+                R.in[DIR_LEFT] = ia[DIR_LEFT]; R.in[DIR_RIGHT] = ib[DIR_RIGHT];
+                R.in[DIR_UP] = cat(ia[DIR_UP], ib[DIR_UP]); R.in[DIR_DOWN] = cat(ia[DIR_DOWN], ib[DIR_DOWN]);
+            } else {
+                R.in[DIR_UP] = ia[DIR_UP]; R.in[DIR_DOWN] = ib[DIR_DOWN];
+                R.in[DIR_LEFT] = cat(ia[DIR_LEFT], ib[DIR_LEFT]); R.in[DIR_RIGHT] = cat(ia[DIR_RIGHT], ib[DIR_RIGHT]);
+            }
+        }
+        region_of[rid] = (int)regions.size();
+        out = (int)regions.size();
+        regions.push_back(R);
+        return BBP_OK;
+    };
+
+    std::vector<Closing> closings;
+    std::map<std::tuple<int, int, int>, int> norm_closing;
+    struct TermPlan {
+        std::vector<std::pair<int, std::complex<double>>> parts;  // (closing, coefficient)
+        int denom = 0;
+    };
+    std::vector<TermPlan> tplan(n_terms);
+    for (int t = 0; t < n_terms; ++t) {
+        const bbp_term& T = terms[t];
+        if (T.nsite < 1 || T.nsite > 2) return fail(BBP_ERR_INVALID, "term must have 1 or 2 sites");
+        std::vector<std::pair<int, int>> rc;
+        for (int k = 0; k < T.nsite; ++k) {
+            if (!T.op_re[k]) return fail(BBP_ERR_INVALID, "operator is NULL");
+            const int s = T.site[k];
+            if (s < 0 || s >= Wlat * Hlat) return fail(BBP_ERR_INVALID, "site out of range");
+            rc.push_back({s / Wlat, s % Wlat});
+        }
+        if (T.nsite == 2 && T.site[0] == T.site[1]) return fail(BBP_ERR_INVALID, "two-site term on one site");
+        int ri;
+        int rc_ = get_region(rc, ri);
+        if (rc_) return rc_;
+        const Region& R = regions[ri];
+        std::vector<std::pair<int, int>> loc;
+        int cmin = 1 << 30, cmax = -1;
+        for (auto& p : rc) {
+            loc.push_back({p.first - R.r0, p.second - R.c0});
+            cmin = std::min(cmin, p.second - R.c0);
+            cmax = std::max(cmax, p.second - R.c0);
+        }
+        if (cmax - cmin > 1) return fail(BBP_ERR_INVALID, "a two-site term must lie in one column or two adjacent columns");
+        const int ncols = cmax - cmin + 1;
+        // operator parts: complex lattices take the complex operator; real lattices
+        // split O = O_re + i O_im into real closings with complex coefficients
+        std::vector<std::vector<std::pair<std::vector<double>, std::complex<double>>>> parts(T.nsite);
+        for (int k = 0; k < T.nsite; ++k) {
+            std::vector<double> re(T.op_re[k], T.op_re[k] + d * d), im(d * d, 0.0);
+            if (T.op_im[k]) im.assign(T.op_im[k], T.op_im[k] + d * d);
+            if (L->cplx) {
+                std::vector<double> z(2 * d * d);
+                for (int j = 0; j < d * d; ++j) {
+                    z[2 * j] = re[j];
+                    z[2 * j + 1] = im[j];
+                }
+                parts[k].push_back({z, 1.0});
+            } else {
+                bool has_re = false, has_im = false;
+                for (int j = 0; j < d * d; ++j) {
+                    has_re |= re[j] != 0.0;
+                    has_im |= im[j] != 0.0;
+                }
+                if (has_re || !has_im) parts[k].push_back({re, 1.0});
+                if (has_im) parts[k].push_back({im, std::complex<double>(0.0, 1.0)});
+            }
+        }
+        auto add_closing = [&](const std::vector<std::vector<double>>& ops, std::complex<double> coef) {
+            Closing C;
+            C.region = ri; C.col = cmin; C.ncols = ncols;
+            C.pos = loc;
+            C.ops = ops;
+            tplan[t].parts.push_back({(int)closings.size(), coef});
+            closings.push_back(C);
+        };
+        if (T.nsite == 1) {
+            for (auto& a : parts[0]) add_closing({a.first}, a.second);
+        } else {
+            for (auto& a : parts[0])
+                for (auto& b : parts[1]) add_closing({a.first, b.first}, a.second * b.second);
+        }
+        const auto key = std::make_tuple(ri, cmin, ncols);
+        auto nc = norm_closing.find(key);
+        if (nc == norm_closing.end()) {
+            Closing C;
+            C.region = ri; C.col = cmin; C.ncols = ncols;
+            norm_closing[key] = (int)closings.size();
+            tplan[t].denom = (int)closings.size();
+            closings.push_back(C);
+        } else {
+            tplan[t].denom = nc->second;
+        }
+    }
+
+    // ---- the read-out program: env columns (fits with chi_exp), then closings
+    Program pr;
+    pr.cplx = L->cplx;
+    const size_t split = (L->arena_bytes + 255) & ~(size_t)255;
+    pr.arena_used = split;
+    auto elem_alloc = [&](size_t elems) { return pr.arena_alloc(elems * (size_t)ss) / (size_t)ss; };
+    std::vector<ColumnSweep> cs;
+    for (auto& R : regions) {
+        for (int side = 0; side < 2; ++side) {
+            ColumnSweep s;
+            s.dir = side == 0 ? DIR_LEFT : DIR_RIGHT;
+            s.r0 = R.r0; s.c0 = R.c0; s.bh = R.h; s.bw = R.w;
+            s.fm = L->frame_msgs(s.dir, R.in);
+            s.chi = ds.chi_exp;
+            s.keep = true;
+            s.tag = 1;
+            s.outer = (uint64_t)R.rid;
+            s.msg = (uint64_t)side;
+            (side == 0 ? R.sweepL : R.sweepR) = (int)cs.size();
+            cs.push_back(s);
+        }
+    }
+    int rc = plan_column_sweeps(L, pr, cs, ds.fit_max_sweeps, ds.fit_tol, false);
+    if (rc) return rc;
+
+    auto env_site = [&](const Region& R, bool left_env, int c, int i) -> View3 {
+        // R env of column c: right edge absorbed down to c+1; L env: left edge up to c-1
+        const ColumnSweep& s = cs[left_env ? R.sweepR : R.sweepL];
+        const int W = R.w;
+        int k = left_env ? (W - c) : (c + 1);  // frame column index of the kept fit
+        if (k >= W) {  // the unabsorbed edge: [1, message, 1]
+            if (i == 0 || i == R.h + 1) {
+                View3 v;
+                v.off = L->one_off;
+                return v;
+            }
+            return s.fm.R[i - 1];
+        }
+        const FitSpec& f = s.fits[k];
+        return contiguous3(f.Y[i], f.ybond[i], f.O[i].q, f.ybond[i + 1]);
+    };
+
+    // lane scratch sizing
+    const int K4max = L->K * L->K * L->K * L->K;
+    const size_t nclos = closings.size();
+    const size_t results = elem_alloc(nclos);
+    struct Lane {
+        size_t F[2], G1, G2, EO[2], O12, op[2];
+    };
+    // per-closing maxima of the row intermediates
+    size_t fmax = 1, g1max = 1, g2max = 1, o12max = 1;
+    auto row_op = [&](const Region& R, int c, int i, size_t eo_off, bool use_eo) -> Op4 {
+        if (i == 0) return op_from_top(R.in[DIR_UP][c]);
+        if (i == R.h + 1) return op_from_bottom(R.in[DIR_DOWN][c]);
+        const int r = R.r0 + i - 1, cc = R.c0 + c;
+        const auto dd = L->site_dims(r, cc);
+        const size_t off = use_eo ? eo_off : L->E_off[L->tensor_index(r, cc)];
+        return op_contig(off, dd[0] * dd[0], dd[1] * dd[1], dd[2] * dd[2], dd[3] * dd[3]);
+    };
+    for (auto& C : closings) {
+        const Region& R = regions[C.region];
+        size_t fa = 1, fw = 1, fb = 1;
+        for (int i = 0; i < R.h + 2; ++i) {
+            const View3 Lv = env_site(R, true, C.col, i), Rv = env_site(R, false, C.col + C.ncols - 1, i);
+            Op4 o = row_op(R, C.col, i, 0, false);
+            if (C.ncols == 2) {
+                Op4 o2 = row_op(R, C.col + 1, i, 0, false);
+                o12max = std::max(o12max, (size_t)o.u * o2.u * o.l * o.d * o2.d * o2.r);
+                o.u *= o2.u; o.d *= o2.d; o.r = o2.r;
+            }
+            const size_t s = Lv.k, Ap = Lv.b, v = o.d, t2 = o.r, Bp = Rv.b;
+            g1max = std::max(g1max, fw * fb * s * Ap);
+            g2max = std::max(g2max, fb * Ap * v * t2);
+            fa = Ap; fw = v; fb = Bp;
+            fmax = std::max(fmax, fa * fw * fb);
+        }
+    }
+    const size_t lane_elems = 2 * fmax + g1max + g2max + 2 * (size_t)K4max + o12max + 2 * (size_t)d * d;
+    const size_t budget = (size_t)4 << 30;
+    size_t nlanes = std::max<size_t>(1, std::min(nclos, budget / std::max<size_t>(1, lane_elems * ss)));
+    std::vector<Lane> lanes(nlanes);
+    for (auto& ln : lanes) {
+        ln.F[0] = elem_alloc(fmax); ln.F[1] = elem_alloc(fmax);
+        ln.G1 = elem_alloc(g1max); ln.G2 = elem_alloc(g2max);
+        ln.EO[0] = elem_alloc(K4max); ln.EO[1] = elem_alloc(K4max);
+        ln.O12 = elem_alloc(o12max);
+        ln.op[0] = elem_alloc((size_t)d * d); ln.op[1] = elem_alloc((size_t)d * d);
+    }
+    // operator uploads recorded as (elem offset, values)
+    std::vector<std::pair<size_t, std::vector<double>>> uploads;
+    for (size_t w0 = 0; w0 < nclos; w0 += nlanes) {
+        const size_t w1 = std::min(nclos, w0 + nlanes);
+        // E^O for the operator sites of this wave
+        std::vector<DLTask> dts;
+        long long dlmax = 1;
+        for (size_t ci = w0; ci < w1; ++ci) {
+            const Closing& C = closings[ci];
+            const Region& R = regions[C.region];
+            const Lane& ln = lanes[ci - w0];
+            for (size_t k = 0; k < C.pos.size(); ++k) {
+                const int r = R.r0 + C.pos[k].first, c = R.c0 + C.pos[k].second;
+                const auto dd = L->site_dims(r, c);
+                uploads.push_back({ln.op[k], C.ops[k]});
+                DLTask t{};
+                t.T = P(L->T_off[L->tensor_index(r, c)] * ss);
+                t.E = P(ln.EO[k] * ss);
+                t.O = P(ln.op[k] * ss);
+                t.d = d; t.Du = dd[0]; t.Dl = dd[1]; t.Dd = dd[2]; t.Dr = dd[3];
+                dts.push_back(t);
+                dlmax = std::max(dlmax, (long long)dd[0] * dd[0] * dd[1] * dd[1] * dd[2] * dd[2] * dd[3] * dd[3]);
+            }
+        }
+        if (!dts.empty()) {
+            Step s;
+            s.kind = ST_DL;
+            s.first = pr.dl.size();
+            s.count = (int)dts.size();
+            s.n = dlmax;
+            pr.dl.insert(pr.dl.end(), dts.begin(), dts.end());
+            pr.steps.push_back(s);
+        }
+        int hmax = 0;
+        for (size_t ci = w0; ci < w1; ++ci) hmax = std::max(hmax, regions[closings[ci].region].h);
+        std::vector<size_t> fa(w1 - w0, 1), fw(w1 - w0, 1), fb(w1 - w0, 1);
+        for (int i = 0; i < hmax + 2; ++i) {
+            std::vector<FuseTask> ft;
+            long long fmx = 1;
+            std::vector<Op4> ops(w1 - w0);
+            std::vector<bool> live(w1 - w0, false);
+            for (size_t ci = w0; ci < w1; ++ci) {
+                const Closing& C = closings[ci];
+                const Region& R = regions[C.region];
+                if (i >= R.h + 2) continue;
+                live[ci - w0] = true;
+                const Lane& ln = lanes[ci - w0];
+                auto op_at = [&](int c) {
+                    for (size_t k = 0; k < C.pos.size(); ++k)
+                        if (C.pos[k].first == i - 1 && C.pos[k].second == c) return row_op(R, c, i, ln.EO[k], true);
+                    return row_op(R, c, i, 0, false);
+                };
+                Op4 o = op_at(C.col);
+                if (C.ncols == 2) {
+                    Op4 o2 = op_at(C.col + 1);
+                    FuseTask f{};
+                    f.A = P(o.off * ss); f.B = P(o2.off * ss); f.out = P(ln.O12 * ss);
+                    f.u1 = o.u; f.l1 = o.l; f.d1 = o.d; f.m = o.r; f.u2 = o2.u; f.d2 = o2.d; f.r2 = o2.r;
+                    f.a_u = o.su; f.a_l = o.sl; f.a_d = o.sd; f.a_r = o.sr;
+                    f.b_u = o2.su; f.b_l = o2.sl; f.b_d = o2.sd; f.b_r = o2.sr;
+                    if (o.r != o2.l) return fail(BBP_ERR_INVALID, "internal: column pair leg mismatch");
+                    ft.push_back(f);
+                    fmx = std::max(fmx, (long long)o.u * o2.u * o.l * o.d * o2.d * o2.r);
+                    o = op_contig(ln.O12, o.u * o2.u, o.l, o.d * o2.d, o2.r);
+                }
+                ops[ci - w0] = o;
+            }
+            if (!ft.empty()) {
+                Step s;
+                s.kind = ST_FUSE;
+                s.first = pr.fus.size();
+                s.count = (int)ft.size();
+                s.n = fmx;
+                pr.fus.insert(pr.fus.end(), ft.begin(), ft.end());
+                pr.steps.push_back(s);
+            }
+            std::vector<GTask> g1, g2, g3;
+            for (size_t ci = w0; ci < w1; ++ci) {
+                if (!live[ci - w0]) continue;
+                const Closing& C = closings[ci];
+                const Region& R = regions[C.region];
+                const Lane& ln = lanes[ci - w0];
+                const size_t j = ci - w0;
+                const View3 Lv = env_site(R, true, C.col, i), Rv = env_site(R, false, C.col + C.ncols - 1, i);
+                const Op4& o = ops[j];
+                const size_t Fin = i == 0 ? L->one_off : ln.F[i % 2];
+                const bool last = i == R.h + 1;
+                const size_t Fout = last ? results + ci : ln.F[(i + 1) % 2];
+                const long long A_ = fa[j], Wd = fw[j], B_ = fb[j], s = Lv.k, Ap = Lv.b, v = o.d, t2 = o.r, Bp = Rv.b;
+                if (Lv.a != A_ || Rv.a != B_ || o.u != Wd || o.l != s || Rv.k != t2)
+                    return fail(BBP_ERR_INVALID, "internal: closing leg mismatch");
+                GTask a{};
+                a.A = P(Fin * ss); a.B = P(Lv.off * ss); a.C = P(ln.G1 * ss);
+                a.M1 = (int)Wd; a.M2 = (int)B_; a.K1 = 1; a.K2 = (int)A_; a.N1 = (int)s; a.N2 = (int)Ap;
+                a.a_m1 = B_; a.a_m2 = 1; a.a_k2 = Wd * B_;
+                a.b_k2 = Lv.sa; a.b_n1 = Lv.sk; a.b_n2 = Lv.sb;
+                a.c_m1 = B_ * s * Ap; a.c_m2 = s * Ap; a.c_n1 = Ap; a.c_n2 = 1;
+                g1.push_back(a);
+                GTask b{};
+                b.A = P(ln.G1 * ss); b.B = P(o.off * ss); b.C = P(ln.G2 * ss);
+                b.M1 = (int)B_; b.M2 = (int)Ap; b.K1 = (int)Wd; b.K2 = (int)s; b.N1 = (int)v; b.N2 = (int)t2;
+                b.a_m1 = s * Ap; b.a_m2 = 1; b.a_k1 = B_ * s * Ap; b.a_k2 = Ap;
+                b.b_k1 = o.su; b.b_k2 = o.sl; b.b_n1 = o.sd; b.b_n2 = o.sr;
+                b.c_m1 = Ap * v * t2; b.c_m2 = v * t2; b.c_n1 = t2; b.c_n2 = 1;
+                g2.push_back(b);
+                GTask c{};
+                c.A = P(ln.G2 * ss); c.B = P(Rv.off * ss); c.C = P(Fout * ss);
+                c.M1 = (int)Ap; c.M2 = (int)v; c.K1 = (int)B_; c.K2 = (int)t2; c.N1 = 1; c.N2 = (int)Bp;
+                c.a_m1 = v * t2; c.a_m2 = t2; c.a_k1 = Ap * v * t2; c.a_k2 = 1;
+                c.b_k1 = Rv.sa; c.b_k2 = Rv.sk; c.b_n2 = Rv.sb;
+                c.c_m1 = v * Bp; c.c_m2 = Bp; c.c_n2 = 1;
+                g3.push_back(c);
+                fa[j] = Ap; fw[j] = v; fb[j] = Bp;
+            }
+            pr.gc_step(g1);
+            pr.gc_step(g2);
+            pr.gc_step(g3);
+        }
+    }
+
+    // ---- check, allocate, relocate, upload, run
+    pr.parent = &L->sweep;
+    pr.split = split;
+    {
+        const std::string v = pr.validate();
+        if (!v.empty()) return fail(BBP_ERR_INVALID, "internal read-out plan check: " + v);
+    }
+    const size_t ro_bytes = pr.arena_used - split;
+    char* ro = nullptr;
+    CKR(cudaMalloc((void**)&ro, ro_bytes));
+    struct Guard {
+        char* p;
+        Program* pr;
+        ~Guard() {
+            pr->free_all();
+            cudaFree(p);
+        }
+    } guard{ro, &pr};
+    pr.relocate(L->arena, split, ro);
+    pr.status = L->d_status;
+    CKR(pr.upload_tasks());
+    cudaStream_t st = L->stream;
+    CKR(cudaMemsetAsync(ro, 0, ro_bytes, st));
+    for (auto& u : uploads) {
+        const size_t bytes = u.second.size() * sizeof(double);
+        CKR(cudaMemcpyAsync(ro + (u.first * ss - split), u.second.data(), bytes, cudaMemcpyHostToDevice, st));
+    }
+    CKR(pr.launch_all(st, nullptr, ds.seed));
+    std::vector<double> res(nclos * (L->cplx ? 2 : 1));
+    CKR(cudaMemcpyAsync(res.data(), ro + (results * ss - split), res.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+    int status = 0;
+    CKR(cudaMemcpyAsync(&status, L->d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CKR(cudaStreamSynchronize(st));
+    L->readout_kernels += pr.kernel_count();
+    L->readout_flops += pr.static_flops + pr.gated_flops;
+    if (status) return fail(BBP_ERR_NUMERIC, "an environment column has zero or non-finite norm");
+    auto val = [&](int ci) {
+        return L->cplx ? std::complex<double>(res[2 * ci], res[2 * ci + 1]) : std::complex<double>(res[ci], 0.0);
+    };
+    for (int t = 0; t < n_terms; ++t) {
+        std::complex<double> num = 0.0;
+        for (auto& p : tplan[t].parts) num += p.second * val(p.first);
+        const std::complex<double> den = val(tplan[t].denom);
+        if (den == 0.0) return fail(BBP_ERR_NUMERIC, "the closed network vanished");
+        const std::complex<double> r = num / den;
+        out_re[t] = r.real();
+        if (out_im) out_im[t] = r.imag();
+    }
+    return BBP_OK;
+}

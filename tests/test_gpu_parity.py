@@ -1,0 +1,106 @@
+"""GPU parity: the CUDA library (through the C ABI) against the FP64 oracle on the
+same seeded inputs, same fit-sweep counts and same generator streams.  Compared are
+gauge-invariant quantities only: residuals, <O>, and message overlaps.  FP64 path:
+1e-10 relative (the tolerance the workload statement fixes for the FP64 path)."""
+import math
+
+import numpy as np
+import pytest
+
+import _exact as X
+from _gpu import message_fidelity, run_both
+from paper_2301_05844_gb300 import binding as B
+from paper_2301_05844_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+SZ, SX, SY = I.SIGMA_Z, I.SIGMA_X, I.SIGMA_Y
+TOL64 = 1e-10
+
+
+def close(a, b, tol=TOL64):
+    a, b = np.asarray(a), np.asarray(b)
+    return np.max(np.abs(a - b)) <= tol * max(1.0, np.max(np.abs(b)))
+
+
+def test_config1_fp64_parity_and_brute_force():
+    """4x4 OBC, D=2, 2x2 blocks, chi=16: residual per sweep, messages and the 56
+    standard observables match the oracle; error vs brute force is reported."""
+    cfg = I.config(1)
+    terms = I.standard_terms(4, 4)
+    g, o, gr, orr, gv, ov = run_both(cfg["tensors"], 4, 4, 2, 2, 2, 2, 16, terms, n_sweeps=6)
+    assert close(gr, orr, 1e-9), (gr, orr)
+    assert message_fidelity(g, o) > 1 - 1e-10
+    assert close(gv, ov)
+    psi = X.state_vector(cfg["tensors"], 4, 4)
+    ex = np.array([X.exact_expect(psi, 16, 2, t) for t in terms])
+    err = np.max(np.abs(gv - ex))
+    assert err < 1e-3  # blockBP approximation on a loop block graph (reported, not parity)
+
+
+@pytest.mark.parametrize("bx,by", [(4, 1), (1, 4), (4, 2)])
+def test_tree_strips_exact_on_gpu(bx, by):
+    T = I.uniform_noise_peps(4, 4, 2, 2, seed=1)
+    terms = I.standard_terms(4, 4)
+    nblk = (4 // bx) * (4 // by)
+    g, o, gr, orr, gv, ov = run_both(T, 4, 4, 2, 2, bx, by, 16, terms, n_sweeps=nblk + 1, chi_exp=18)
+    psi = X.state_vector(T, 4, 4)
+    ex = np.array([X.exact_expect(psi, 16, 2, t) for t in terms])
+    assert close(gv, ex, 1e-11)
+    assert close(gv, ov)
+
+
+def test_complex_obc_ragged_tiles():
+    """6x6 OBC, D=3 (K=9), 3x3 blocks, chi=12 (truncating): ragged 64-wide tiles, complex."""
+    rng = np.random.default_rng(31)
+    T = I.uniform_noise_peps(6, 6, 2, 3, seed=5)
+    T = [t + 0.2j * rng.standard_normal(t.shape) for t in T]
+    terms = [[(7, SZ)], [(14, SX)], [(7, SZ), (8, SZ)], [(8, SY), (9, SY)], [(2, SX), (8, SX)], [(20, SZ), (26, SZ)]]
+    g, o, gr, orr, gv, ov = run_both(T, 6, 6, 2, 3, 3, 3, 12, terms, n_sweeps=3, chi_exp=20)
+    assert close(gr, orr, 1e-9)
+    assert message_fidelity(g, o) > 1 - 1e-10
+    assert close(gv, ov)
+
+
+def test_infinite_complex_cell():
+    """Infinite 2x2 unit cell, complex, D=2, 2x2 block messaging itself."""
+    T = I.complex_normal_cell(2, 2, 2, 2, seed=3)
+    T = [t.astype(np.complex128) for t in T]
+    terms = [[(0, SZ)], [(3, SX)], [(0, SZ), (1, SZ)], [(1, SX), (3, SX)]]
+    g, o, gr, orr, gv, ov = run_both(T, 2, 2, 2, 2, 2, 2, 4, terms, n_sweeps=4, boundary="infinite")
+    assert close(gr, orr, 1e-9)
+    assert close(gv, ov)
+
+
+def test_nonsquare_blocks_and_random_init():
+    T = I.uniform_noise_peps(4, 4, 2, 2, seed=1)
+    terms = I.standard_terms(4, 4)
+    g, o, gr, orr, gv, ov = run_both(T, 4, 4, 2, 2, 2, 1, 8, terms, n_sweeps=3, init_mode=1, seed=11)
+    assert close(gr, orr, 1e-9)
+    assert close(gv, ov)
+
+
+def test_single_block_no_messages():
+    T = I.uniform_noise_peps(4, 4, 2, 2, seed=1)
+    terms = I.standard_terms(4, 4)
+    g = B.Lattice(Lx=4, Ly=4, d=2, D=2, bx=4, by=4, chi=16, chi_exp=64, fit_tol=0.0, fit_max_sweeps=2)
+    g.set_tensors(T)
+    r, k, rc = g.sweep(3)
+    assert r == 0.0
+    psi = X.state_vector(T, 4, 4)
+    ex = np.array([X.exact_expect(psi, 16, 2, t) for t in terms])
+    assert close(g.expect(terms), ex, 1e-11)
+
+
+def test_error_paths():
+    g = B.Lattice(Lx=4, Ly=4, d=2, D=2, bx=2, by=2, chi=16)
+    with pytest.raises(B.BBPError) as e:
+        g.sweep(1)
+    assert e.value.code == B.ERR_STATE
+    g.set_tensors(I.uniform_noise_peps(4, 4, 2, 2, seed=1))
+    g.sweep(1)
+    with pytest.raises(B.BBPError) as e:
+        g.expect([[(0, SZ), (10, SZ)]])  # different blocks, not neighbours
+    assert e.value.code == B.ERR_INVALID
+    with pytest.raises(B.BBPError) as e:
+        g.expect([[(99, SZ)]])
+    assert e.value.code == B.ERR_INVALID

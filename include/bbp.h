@@ -148,6 +148,19 @@ typedef struct {
  * shapes; fit sweeps are read back from the device). */
 int bbp_get_stats(bbp_lattice* lat, bbp_stats* out);
 
+/* ---- diagnostics ------------------------------------------------------------------
+ * Not a step of the paper's method: a self-test of the library's tensor-core GEMM
+ * kernel (the contraction engine of the TF32/BF16 path) on host matrices.
+ * C[m][n] = sum_k A[m][k] B[n][k]; A is M x K, B is N x K, C is M x N, all row-major
+ * FP32 on the host; prec is BBP_PREC_TF32 or BBP_PREC_BF16 (operands rounded to it).
+ * Errors: INVALID, CUDA, TIMEOUT (a pipeline wait hit its bound). */
+int bbp_selftest_gemm(int M, int N, int K, int prec, const float* A, const float* B, float* C);
+
+/* The library's counter-based generator (the one that draws the initial fit states
+ * and the random initial messages, App. A), evaluated on the host: out[i] for
+ * i < n, each an exact double in [-1, 1).  Runs without a GPU. */
+int bbp_selftest_rng(unsigned long long seed, unsigned long long stream, long long n, double* out);
+
 #ifdef __cplusplus
 }
 #endif

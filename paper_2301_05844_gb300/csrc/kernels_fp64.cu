@@ -82,7 +82,9 @@ __host__ __device__ __forceinline__ double u_pm1(uint64_t key, uint64_t idx) {
     return (double)(sm64(key + idx) >> 11) * 0x1.0p-52 - 1.0;
 }
 uint64_t splitmix64(uint64_t z) { return sm64(z); }
-double uniform_pm1(uint64_t seed, uint64_t stream, uint64_t idx) { return u_pm1(seed ^ sm64(stream), idx); }
+// key = splitmix64(seed XOR splitmix64(stream)); value i = splitmix64(key + i) mapped to [-1, 1)
+__host__ __device__ __forceinline__ uint64_t rng_key(uint64_t seed, uint64_t stream) { return sm64(seed ^ sm64(stream)); }
+double uniform_pm1(uint64_t seed, uint64_t stream, uint64_t idx) { return u_pm1(rng_key(seed, stream), idx); }
 
 // ---------------------------------------------------------------- generic contraction
 // 64x64 output tile per CTA, K in chunks of 16, 256 threads each owning 4x4 outputs.
@@ -284,7 +286,7 @@ cudaError_t launch_qr(const QRTask* d_tasks, int ntasks, int max_m, bool cplx, c
 __global__ void k_rand(const RandTask* __restrict__ tasks, unsigned long long seed, const int* sweep_ctr, int cplx) {
     const RandTask& t = tasks[blockIdx.y];
     const uint64_t stream = t.stream | (sweep_ctr ? ((uint64_t)(*sweep_ctr) << 36) : 0ull);
-    const uint64_t key = seed ^ sm64(stream);
+    const uint64_t key = rng_key(seed, stream);
     const long long cnt = cplx ? 2 * t.n : t.n;
     double* p = (double*)t.ptr;
     if (t.active && blockIdx.x == 0 && threadIdx.x == 0) *t.active = 1;

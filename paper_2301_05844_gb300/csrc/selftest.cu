@@ -1,0 +1,68 @@
+// bbp_selftest_gemm: runs the tensor-core GEMM on host matrices (diagnostics).
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "bbp.h"
+#include "engine.h"
+#include "tc_gemm.h"
+
+using namespace bbp;
+
+extern "C" int bbp_selftest_gemm(int M, int N, int K, int prec, const float* A, const float* B, float* C) {
+    if (M < 1 || N < 1 || K < 1 || !A || !B || !C || (prec != BBP_PREC_TF32 && prec != BBP_PREC_BF16))
+        return fail(BBP_ERR_INVALID, "selftest: bad arguments");
+    const int kind = prec == BBP_PREC_TF32 ? 0 : 1;
+    const int esz = kind == 0 ? 4 : 2;
+    const long long ld = ((long long)K * esz + 15) / 16 * 16 / esz;  // 16-byte row pitch
+    std::vector<unsigned char> ha((size_t)M * ld * esz, 0), hb((size_t)N * ld * esz, 0);
+    for (long long i = 0; i < M; ++i)
+        for (long long k = 0; k < K; ++k) {
+            if (kind == 0) ((float*)ha.data())[i * ld + k] = A[i * K + k];
+            else ((__nv_bfloat16*)ha.data())[i * ld + k] = __float2bfloat16_rn(A[i * K + k]);
+        }
+    for (long long i = 0; i < N; ++i)
+        for (long long k = 0; k < K; ++k) {
+            if (kind == 0) ((float*)hb.data())[i * ld + k] = B[i * K + k];
+            else ((__nv_bfloat16*)hb.data())[i * ld + k] = __float2bfloat16_rn(B[i * K + k]);
+        }
+    void *da = nullptr, *db = nullptr, *dc = nullptr, *dt = nullptr;
+    int* derr = nullptr;
+    int rc = BBP_OK;
+    const int bn = N <= 32 ? 32 : N <= 64 ? 64 : N <= 128 ? 128 : 256;
+    cudaError_t e = cudaMalloc(&da, ha.size());
+    if (!e) e = cudaMalloc(&db, hb.size());
+    if (!e) e = cudaMalloc(&dc, (size_t)M * N * 4);
+    if (!e) e = cudaMalloc(&dt, sizeof(TCTask));
+    if (!e) e = cudaMalloc((void**)&derr, sizeof(int));
+    if (!e) e = cudaMemcpy(da, ha.data(), ha.size(), cudaMemcpyHostToDevice);
+    if (!e) e = cudaMemcpy(db, hb.data(), hb.size(), cudaMemcpyHostToDevice);
+    if (!e) e = cudaMemset(dc, 0, (size_t)M * N * 4);
+    if (!e) e = cudaMemset(derr, 0, sizeof(int));
+    TCTask t{};
+    if (!e) e = tc_make_map(&t.map_a, da, kind, M, K, ld, 128);
+    if (!e) e = tc_make_map(&t.map_b, db, kind, N, K, ld, bn);
+    t.M = M; t.N = N; t.K = K; t.M2 = M; t.N2 = N; t.out_kind = 0;
+    t.c_m1 = 0; t.c_m2 = N; t.c_n1 = 0; t.c_n2 = 1;
+    t.C = dc; t.C2 = nullptr; t.active = nullptr; t.alpha = 1.0f;
+    if (!e) e = cudaMemcpy(dt, &t, sizeof(t), cudaMemcpyHostToDevice);
+    if (!e) e = tc_prepare();
+    const int tiles = ((M + 127) / 128) * ((N + bn - 1) / bn);
+    if (!e) e = launch_tc_gemm((const TCTask*)dt, 1, kind, bn, tiles, derr, 0);
+    if (!e) e = cudaDeviceSynchronize();
+    int herr = 0;
+    if (!e) e = cudaMemcpy(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost);
+    if (!e) e = cudaMemcpy(C, dc, (size_t)M * N * 4, cudaMemcpyDeviceToHost);
+    if (e) rc = fail(BBP_ERR_CUDA, std::string("selftest: ") + cudaGetErrorString(e));
+    else if (herr) rc = fail(BBP_ERR_TIMEOUT, "selftest: a pipeline wait timed out");
+    cudaFree(da); cudaFree(db); cudaFree(dc); cudaFree(dt); cudaFree(derr);
+    return rc;
+}
+
+extern "C" int bbp_selftest_rng(unsigned long long seed, unsigned long long stream, long long n, double* out) {
+    if (n < 0 || (n > 0 && !out)) return fail(BBP_ERR_INVALID, "selftest_rng: bad arguments");
+    for (long long i = 0; i < n; ++i) out[i] = bbp::uniform_pm1(seed, stream, (uint64_t)i);
+    return BBP_OK;
+}

@@ -1,0 +1,312 @@
+// Tensor-core grouped GEMM for sm_103a (tcgen05 + TMEM + TMA).
+//
+//   C[m][n] = sum_k A[m][k] * B[n][k]      (A, B K-major; FP32 accumulation in TMEM)
+//
+// One CTA computes a 128 x BN tile of one task.  Warp 0 (one lane) streams A and B
+// k-blocks with TMA into a 4-stage ring of 128-byte-swizzled shared memory; warp 1
+// (one lane) issues tcgen05.mma (kind::tf32 or kind::f16 with BF16 operands) into a
+// TMEM accumulator; all four warps then read the accumulator with tcgen05.ld and
+// scatter it through a two-level index map (the same map as the FP64 contraction),
+// optionally to a second destination, rounding to TF32 or BF16 for the next GEMM.
+//
+// Every wait on an mbarrier is bounded: on timeout the CTA records an error in a
+// device word, drains its own outstanding TMA copies (bounded), frees its TMEM and
+// returns, so that a broken pipeline ends the launch with a status, not a hang.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <cudaTypedefs.h>
+#include <stdint.h>
+
+#include "bbp_internal.h"
+#include "tc_gemm.h"
+
+namespace bbp {
+namespace tc {
+
+constexpr int BM = 128;
+constexpr int STAGES = 4;
+constexpr int KBYTES = 128;  // bytes of K per stage row (one 128-byte swizzle atom)
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ uint32_t mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok;
+}
+// Bounded wait for the phase with the given parity to complete.  Returns false (and
+// raises *err) after ~2^22 polls, or immediately once another thread raised *err.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err) {
+    for (uint32_t i = 0; i < (1u << 22); ++i) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((i & 1023u) == 1023u && *(volatile int*)err) return false;
+    }
+    atomicExch(err, 1);
+    return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const void* map, uint64_t* bar, int c0, int c1) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
+            smem_u32(dst)),
+        "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(c0), "r"(c1)
+        : "memory");
+}
+__device__ __forceinline__ void prefetch_map(const void* map) {
+    asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)map) : "memory");
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)), "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+template <int KIND>  // 0: tf32, 1: bf16 (kind::f16)
+__device__ __forceinline__ void umma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    if constexpr (KIND == 0) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d),
+            "l"(a), "l"(b), "r"(idesc), "r"(acc)
+            : "memory");
+    } else {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d),
+            "l"(a), "l"(b), "r"(idesc), "r"(acc)
+            : "memory");
+    }
+}
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* r) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart.
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)1 << 16;             // leading-dimension offset (unused for swizzled K-major)
+    d |= (uint64_t)(1024 >> 4) << 32;   // stride-dimension offset: next 8-row group
+    d |= (uint64_t)1 << 46;             // descriptor version for tcgen05
+    d |= (uint64_t)2 << 61;             // 128-byte swizzle
+    return d;
+}
+// Instruction descriptor: FP32 accumulate, K-major A and B, M = 128, N = bn.
+__host__ __device__ constexpr uint32_t idesc(int kind, int bn) {
+    return (1u << 4) | ((kind == 0 ? 2u : 1u) << 7) | ((kind == 0 ? 2u : 1u) << 10) | ((uint32_t)(bn >> 3) << 17) |
+           ((uint32_t)(BM >> 4) << 24);
+}
+
+__device__ __forceinline__ float round_tf32(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
+template <int KIND, int BN>
+__global__ void __launch_bounds__(128, 1) k_tc_gemm(const TCTask* __restrict__ tasks, int* err) {
+    const TCTask& t = tasks[blockIdx.y];
+    if (t.active && *t.active == 0) return;
+    const int tilesM = (t.M + BM - 1) / BM, tilesN = (t.N + BN - 1) / BN;
+    if ((int)blockIdx.x >= tilesM * tilesN) return;
+    const int m0 = (blockIdx.x % tilesM) * BM, n0 = (blockIdx.x / tilesM) * BN;
+    constexpr int EK = KBYTES / (KIND == 0 ? 4 : 2);  // elements of K per k-block
+    const int nk = (t.K + EK - 1) / EK;
+    constexpr uint32_t A_BYTES = BM * KBYTES, B_BYTES = BN * KBYTES;
+
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    unsigned char* sA = smem;
+    unsigned char* sB = smem + STAGES * A_BYTES;
+    __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES], accum;
+    __shared__ uint32_t tmem_base;
+    __shared__ int issued;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(&accum, 1);
+        issued = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        prefetch_map(&t.map_a);
+        prefetch_map(&t.map_b);
+    }
+    if (warp == 0) tmem_alloc(&tmem_base, BN < 32 ? 32 : BN);
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = tmem_base;
+
+    if (warp == 0 && lane == 0) {
+        // TMA producer
+        for (int kb = 0; kb < nk; ++kb) {
+            const int s = kb % STAGES, r = kb / STAGES;
+            if (r > 0 && !mbar_wait(&empty[s], (r - 1) & 1, err)) break;
+            mbar_expect_tx(&full[s], A_BYTES + B_BYTES);
+            tma_load_2d(sA + s * A_BYTES, &t.map_a, &full[s], kb * EK, m0);
+            tma_load_2d(sB + s * B_BYTES, &t.map_b, &full[s], kb * EK, n0);
+            issued = kb + 1;
+        }
+    } else if (warp == 1 && lane == 0) {
+        // MMA issuer
+        constexpr uint32_t ID = idesc(KIND, BN);
+        bool ok = true;
+        for (int kb = 0; kb < nk && ok; ++kb) {
+            const int s = kb % STAGES, r = kb / STAGES;
+            ok = mbar_wait(&full[s], r & 1, err);
+            if (!ok) break;
+            fence_after();
+            const uint32_t a0 = smem_u32(sA + s * A_BYTES), b0 = smem_u32(sB + s * B_BYTES);
+#pragma unroll
+            for (int k = 0; k < KBYTES / 32; ++k)  // 32 bytes of K per instruction
+                umma<KIND>(tmem, sdesc(a0 + 32 * k), sdesc(b0 + 32 * k), ID, (kb | k) ? 1u : 0u);
+            umma_commit(&empty[s]);
+        }
+        umma_commit(&accum);
+    }
+    __syncwarp();
+    // epilogue: every warp waits for the accumulator
+    const bool ready = mbar_wait(&accum, 0, err);
+    fence_after();
+    if (ready) {
+        const int row = m0 + warp * 32 + lane;
+        const long long mo = row < t.M ? (long long)(row / t.M2) * t.c_m1 + (long long)(row % t.M2) * t.c_m2 : 0;
+        const long long mo2 =
+            (row < t.M && t.C2) ? (long long)(row / t.M2) * t.d_m1 + (long long)(row % t.M2) * t.d_m2 : 0;
+#pragma unroll 1
+        for (int c = 0; c < BN; c += 16) {
+            uint32_t v[16];
+            tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, v);
+            if (row >= t.M) continue;
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const int n = n0 + c + j;
+                if (n >= t.N) break;
+                float x = __uint_as_float(v[j]) * t.alpha;
+                const int n1 = n / t.N2, n2 = n - n1 * t.N2;
+                const long long o = mo + (long long)n1 * t.c_n1 + (long long)n2 * t.c_n2;
+                if (t.out_kind == 0) ((float*)t.C)[o] = x;
+                else if (t.out_kind == 1) ((float*)t.C)[o] = round_tf32(x);
+                else ((__nv_bfloat16*)t.C)[o] = __float2bfloat16_rn(x);
+                if (t.C2) {
+                    const long long o2 = mo2 + (long long)n1 * t.d_n1 + (long long)n2 * t.d_n2;
+                    if (t.out_kind == 0) ((float*)t.C2)[o2] = x;
+                    else if (t.out_kind == 1) ((float*)t.C2)[o2] = round_tf32(x);
+                    else ((__nv_bfloat16*)t.C2)[o2] = __float2bfloat16_rn(x);
+                }
+            }
+        }
+    }
+    fence_before();
+    __syncthreads();
+    // drain: the producer's copies must have landed before shared memory is released
+    if (threadIdx.x == 0) {
+        const int n_issued = issued;
+        for (int kb = (n_issued > STAGES ? n_issued - STAGES : 0); kb < n_issued; ++kb)
+            mbar_wait(&full[kb % STAGES], (kb / STAGES) & 1, err);
+    }
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, BN < 32 ? 32 : BN);
+}
+
+}  // namespace tc
+
+cudaError_t tc_prepare() {
+    // sets the shared-memory limits outside any stream capture
+    cudaError_t e;
+    const int bns[4] = {32, 64, 128, 256};
+    for (int i = 0; i < 4; ++i) {
+        const size_t smem = tc::STAGES * (size_t)(tc::BM + bns[i]) * tc::KBYTES + 1024;
+        switch (bns[i]) {
+            case 32:
+                if ((e = cudaFuncSetAttribute(tc::k_tc_gemm<0, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))) return e;
+                if ((e = cudaFuncSetAttribute(tc::k_tc_gemm<1, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))) return e;
+                break;
+            case 64:
+                if ((e = cudaFuncSetAttribute(tc::k_tc_gemm<0, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))) return e;
+                if ((e = cudaFuncSetAttribute(tc::k_tc_gemm<1, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))) return e;
+                break;
+            case 128:
+                if ((e = cudaFuncSetAttribute(tc::k_tc_gemm<0, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))) return e;
+                if ((e = cudaFuncSetAttribute(tc::k_tc_gemm<1, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))) return e;
+                break;
+            default:
+                if ((e = cudaFuncSetAttribute(tc::k_tc_gemm<0, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))) return e;
+                if ((e = cudaFuncSetAttribute(tc::k_tc_gemm<1, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))) return e;
+        }
+    }
+    return cudaSuccess;
+}
+
+cudaError_t launch_tc_gemm(const TCTask* d_tasks, int ntasks, int kind, int bn, int max_tiles, int* err, cudaStream_t s) {
+    if (ntasks <= 0) return cudaSuccess;
+    const size_t smem = tc::STAGES * (size_t)(tc::BM + bn) * tc::KBYTES + 1024;
+    dim3 grid(max_tiles, ntasks);
+#define TC_CASE(K_, N_)                                                                          \
+    if (kind == K_ && bn == N_) {                                                                \
+        tc::k_tc_gemm<K_, N_><<<grid, 128, smem, s>>>(d_tasks, err);                             \
+        return cudaGetLastError();                                                               \
+    }
+    TC_CASE(0, 32) TC_CASE(0, 64) TC_CASE(0, 128) TC_CASE(0, 256)
+    TC_CASE(1, 32) TC_CASE(1, 64) TC_CASE(1, 128) TC_CASE(1, 256)
+#undef TC_CASE
+    return cudaErrorInvalidValue;
+}
+
+// ---------------------------------------------------------------- host: tensor maps
+static PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+
+cudaError_t tc_make_map(void* map_out, const void* base, int kind, long long rows, long long K, long long ld_elems,
+                        int box_rows) {
+    if (!g_encode) {
+        cudaDriverEntryPointQueryResult q;
+        void* fn = nullptr;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+        if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
+        g_encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+    }
+    const int esz = kind == 0 ? 4 : 2;
+    cuuint64_t gdim[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+    cuuint64_t gstride[1] = {(cuuint64_t)(ld_elems * esz)};
+    cuuint32_t box[2] = {(cuuint32_t)(tc::KBYTES / esz), (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = g_encode((CUtensorMap*)map_out, kind == 0 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
+                          2, const_cast<void*>(base), gdim, gstride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                          CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+}  // namespace bbp

@@ -1,0 +1,36 @@
+// Task descriptor of the tcgen05 grouped GEMM (tc_gemm.cu).
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+namespace bbp {
+
+// C[m][n] = alpha * sum_k A[m][k] B[n][k]; A and B are read by TMA through the two
+// tensor maps (K innermost, rows outer, 128-byte swizzle, zero fill past the edges).
+// The result is written through the two-level map
+//   C[(m/M2)*c_m1 + (m%M2)*c_m2 + (n/N2)*c_n1 + (n%N2)*c_n2]
+// and, if C2 is set, also to C2 through (d_*).  out_kind: 0 FP32, 1 FP32 rounded to
+// TF32, 2 BF16.
+struct TCTask {
+    CUtensorMap map_a;
+    CUtensorMap map_b;
+    int M, N, K, M2, N2, out_kind;
+    long long c_m1, c_m2, c_n1, c_n2;
+    long long d_m1, d_m2, d_n1, d_n2;
+    void* C;
+    void* C2;
+    const int* active;
+    float alpha;
+    int pad;
+};
+
+cudaError_t tc_prepare();
+cudaError_t launch_tc_gemm(const TCTask* d_tasks, int ntasks, int kind, int bn, int max_tiles, int* err,
+                           cudaStream_t s);
+// kind: 0 FP32/TF32 elements, 1 BF16.  rows x K matrix with leading dimension ld_elems
+// (ld * element size must be a multiple of 16 bytes, base 16-byte aligned).
+cudaError_t tc_make_map(void* map_out, const void* base, int kind, long long rows, long long K, long long ld_elems,
+                        int box_rows);
+
+}  // namespace bbp

@@ -72,3 +72,16 @@ def test_sweep_plan_passes_the_bounds_check(libpath, cfg):
     assert "internal" not in msg
     if rc == B.OK:
         L.bbp_destroy(h)
+
+
+def test_library_generator_matches_the_oracle_definition(libpath):
+    """The counter-based generator in the library equals the oracle's SplitMix64
+    definition bit for bit (both sides draw the same initial fit states)."""
+    import numpy as np
+    from oracle import blockbp as ob
+    L = ctypes.CDLL(libpath)
+    L.bbp_selftest_rng.argtypes = [ctypes.c_ulonglong, ctypes.c_ulonglong, ctypes.c_longlong, ctypes.c_void_p]
+    for seed, stream in [(0, 0), (7, ob.stream_id(0, 3, 17, 2, 4)), (2**63 + 5, ob.stream_id(1, 9, 1, 0, 3))]:
+        out = np.zeros(257)
+        assert L.bbp_selftest_rng(seed, stream, 257, out.ctypes.data) == 0
+        assert np.array_equal(out, ob.uniform_pm1(seed, stream, 257))

@@ -68,10 +68,15 @@ typedef struct {
     double tol;              /* residual tolerance (main text: 1e-5) */
     int max_sweeps;          /* cap on sweeps when running to tolerance (10) */
     int stop_relative;       /* 0: residual < tol (main text); 1: r_l / r_1 < tol (App. A) */
-    double fit_tol;          /* zip-up fit: std/|mean| of -||Yt||^2 over a sweep (App. A: 1e-6) */
+    double fit_tol;          /* zip-up fit: std/|mean| of -||Yt||^2 over a sweep (App. A: 1e-6);
+                                on the TF32 / BF16 paths at least 3e-3 / 3e-2, the noise of a
+                                loss computed in that precision */
     int fit_max_sweeps;      /* zip-up fit sweep cap (App. A: 10) */
     unsigned long long seed; /* counter-based generator key (fit initial states, init_mode 1) */
     int init_mode;           /* 0: identity-product messages; 1: random MPDO (App. A) */
+    int warm_start;          /* 0: every zip-up fit starts from a random state (App. A);
+                                1: from the second sweep on, each fit starts from its own
+                                result of the previous sweep */
     void* stream;            /* cudaStream_t for all work; NULL = library-owned stream */
 } bbp_lattice_desc;
 
@@ -155,6 +160,17 @@ int bbp_get_stats(bbp_lattice* lat, bbp_stats* out);
  * FP32 on the host; prec is BBP_PREC_TF32 or BBP_PREC_BF16 (operands rounded to it).
  * Errors: INVALID, CUDA, TIMEOUT (a pipeline wait hit its bound). */
 int bbp_selftest_gemm(int M, int N, int K, int prec, const float* A, const float* B, float* C);
+
+/* Kernel-class timing of one planned sweep, for roofline measurements: replays, on
+ * the handle's stream and bracketed by CUDA events, only the launches of one class
+ * (0: tensor-core GEMM steps, 1: FP64 strided contractions, 2: FP64 QR/LQ),
+ * reps times.  The replay writes only work buffers, never
+ * the message store, so the next bbp_sweep is unaffected.  Outputs (may be NULL):
+ * total device milliseconds, launches, algorithmic flops of those launches (real
+ * multiply-adds counted as 2; complex x4), and the bytes the launches must move at
+ * least (operands read once, results written once).  Errors: INVALID, STATE, CUDA. */
+int bbp_time_kernels(bbp_lattice* lat, int kernel_class, int reps, double* ms, long long* launches,
+                     double* flops, double* bytes);
 
 /* The library's counter-based generator (the one that draws the initial fit states
  * and the random initial messages, App. A), evaluated on the host: out[i] for

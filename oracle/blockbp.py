@@ -263,6 +263,21 @@ def normalise_message(M, D):
     return M
 
 
+def embed_at_caps(M, chi):
+    """The same MPS with every bond zero-padded to the capped dimension
+    min(chi, K^i, K^(n-i)): message storage has the shape of a bond-chi message from
+    the start (the state is unchanged)."""
+    K = M[0].shape[1]
+    caps = bond_caps([K] * len(M), chi)
+    out = []
+    for i, s in enumerate(M):
+        a, k, b = s.shape
+        t = np.zeros((caps[i], k, caps[i + 1]), dtype=s.dtype)
+        t[:a, :, :b] = s
+        out.append(t)
+    return out
+
+
 def trivial_mps(n, dtype):
     """Message from outside an OBC lattice: the scalar 1 on every (dimension-1) leg."""
     return [np.ones((1, 1, 1), dtype=dtype) for _ in range(n)]
@@ -332,7 +347,7 @@ def column_mpo(Ef, mT, mB, c):
     return O
 
 
-def column_sweep(Ef, mT, mR, mB, opts: FitOpts, seed, stream_of, dtype, keep=False):
+def column_sweep(Ef, mT, mR, mB, opts: FitOpts, seed, stream_of, dtype, keep=False, warm=None):
     """bMPS contraction of a block (frame) with its incoming messages (App. A, Fig. 1(d)).
 
     X starts as [1, mR, 1] (corner sites of dimension 1), then every column from the
@@ -340,6 +355,9 @@ def column_sweep(Ef, mT, mR, mB, opts: FitOpts, seed, stream_of, dtype, keep=Fal
     each column the fitted MPS is scaled to unit norm (it is in mixed canonical form
     around site 0, so its norm is the Frobenius norm of site 0); the fits are
     scale-covariant, so this only removes over/underflow.
+    warm (optional dict c -> site list): start column c's fit from that MPS instead of
+    the random state (warm start from the previous sweep's fit of the same column);
+    it is updated in place with every column's fitted MPS.
     Returns (list of column MPS after absorbing columns >= c, indexed by c) if keep,
     else the final column MPS.
     """
@@ -349,13 +367,21 @@ def column_sweep(Ef, mT, mR, mB, opts: FitOpts, seed, stream_of, dtype, keep=Fal
     kept = {W: X}
     for c in range(W - 1, -1, -1):
         O = column_mpo(Ef, mT, mB, c)
-        Y, _ = fit_mpo_mps(O, X, opts, lambda i, shp: random_site(seed, stream_of(c, i), shp, dtype), dtype)
+        if warm is not None and c in warm:
+            prev = warm[c]
+            init = lambda i, shp, prev=prev, c=c: (prev[i].copy() if prev[i].shape == tuple(shp)
+                                                   else random_site(seed, stream_of(c, i), shp, dtype))
+        else:
+            init = lambda i, shp: random_site(seed, stream_of(c, i), shp, dtype)
+        Y, _ = fit_mpo_mps(O, X, opts, init, dtype)
         nrm = float(np.linalg.norm(Y[0]))
         if not np.isfinite(nrm) or nrm == 0.0:
             raise FloatingPointError("column MPS vanished")
         Y[0] = Y[0] / nrm
         X = Y
         kept[c] = X
+        if warm is not None:
+            warm[c] = [s.copy() for s in Y]
     return kept if keep else X
 
 
@@ -393,7 +419,9 @@ class Lattice:
     fit_max_sweeps: int = 10
     seed: int = 0
     init_mode: int = 0
+    warm_start: bool = False
     msgs: dict = field(default_factory=dict)
+    warm: dict = field(default_factory=dict)
     sweeps_done: int = 0
     residuals: list = field(default_factory=list)
 
@@ -420,7 +448,7 @@ class Lattice:
                     m = identity_message(n, self.D, self.dtype)
                 else:
                     m = random_mpdo_message(n, self.D, self.seed, stream_id(2, 0, 4 * bi + dr, 0, 0), self.dtype)
-                self.msgs[(bi, dr)] = normalise_message(m, self.D)
+                self.msgs[(bi, dr)] = embed_at_caps(normalise_message(m, self.D), self.chi)
 
     # -- geometry ------------------------------------------------------------------
     def tensor_index(self, r, c):
@@ -475,8 +503,9 @@ class Lattice:
         Ef, mT, mR, mB = frame(self.block_E(bi), self.incoming(bi, msgs), dr)
         opts = FitOpts(self.chi, self.fit_tol, self.fit_max_sweeps)
         msg = 4 * bi + dr
+        warm = self.warm.setdefault((bi, dr), {}) if self.warm_start else None
         X = column_sweep(Ef, mT, mR, mB, opts, self.seed,
-                         lambda c, i: stream_id(0, sweep_index, msg, c, i), self.dtype)
+                         lambda c, i: stream_id(0, sweep_index, msg, c, i), self.dtype, warm=warm)
         return normalise_message(extract_message(X), self.D)
 
     def sweep(self):

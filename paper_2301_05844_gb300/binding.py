@@ -31,7 +31,7 @@ class Desc(C.Structure):
         ("bx", C.c_int), ("by", C.c_int), ("chi", C.c_int), ("chi_exp", C.c_int),
         ("dtype", C.c_int), ("prec", C.c_int), ("tol", C.c_double), ("max_sweeps", C.c_int),
         ("stop_relative", C.c_int), ("fit_tol", C.c_double), ("fit_max_sweeps", C.c_int),
-        ("seed", C.c_ulonglong), ("init_mode", C.c_int), ("stream", C.c_void_p),
+        ("seed", C.c_ulonglong), ("init_mode", C.c_int), ("warm_start", C.c_int), ("stream", C.c_void_p),
     ]
 
 
@@ -72,6 +72,10 @@ def lib():
     L.bbp_get_message.argtypes = [P, C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_double)]
     L.bbp_set_message.argtypes = [P, C.c_int, C.c_int, C.POINTER(C.c_double)]
     L.bbp_get_stats.argtypes = [P, C.POINTER(Stats)]
+    L.bbp_time_kernels.argtypes = [P, C.c_int, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_longlong),
+                                   C.POINTER(C.c_double), C.POINTER(C.c_double)]
+    L.bbp_selftest_gemm.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, P, P, P]
+    L.bbp_selftest_rng.argtypes = [C.c_ulonglong, C.c_ulonglong, C.c_longlong, P]
     _lib = L
     return L
 
@@ -89,10 +93,11 @@ def _check(rc):
 
 
 def make_desc(Lx, Ly, d, D, bx, by, chi, boundary="obc", chi_exp=0, dtype=F64, prec="fp64", tol=1e-5,
-              max_sweeps=10, stop_relative=0, fit_tol=1e-6, fit_max_sweeps=10, seed=0, init_mode=0, stream=None):
+              max_sweeps=10, stop_relative=0, fit_tol=1e-6, fit_max_sweeps=10, seed=0, init_mode=0, warm_start=0,
+              stream=None):
     return Desc(Lx, Ly, OBC if boundary == "obc" else INFINITE, d, D, bx, by, chi, chi_exp, dtype,
                 _PREC[prec] if isinstance(prec, str) else prec, tol, max_sweeps, stop_relative, fit_tol,
-                fit_max_sweeps, seed, init_mode, stream)
+                fit_max_sweeps, seed, init_mode, int(warm_start), stream)
 
 
 class Lattice:

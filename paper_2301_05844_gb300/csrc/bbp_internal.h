@@ -43,7 +43,23 @@ struct QRTask {
     int m, n;
     long long in_rs, in_cs, out_rs, out_cs;
     int conj_io;
+    int in_float;    // 1: input is FP32 (mixed path), 0: the FP64 scalar type
+    void* out2;      // optional second copy of Q in a low-precision operand layout
+    long long out2_rs, out2_cs;
+    int out2_kind;   // element kind of out2 (see RelayoutTask)
     int pad;
+};
+
+// Strided copy with type conversion over a 4-D index space (dims d0 x d1 x d2 x d3):
+//   dst[sum_i i_k * ds_k] = convert(src[sum_i i_k * ss_k]).
+// Element kinds: 0 FP64, 2 FP32, 3 BF16, 4 FP32 rounded to TF32 (store only).
+struct RelayoutTask {
+    const void* src;
+    void* dst;
+    int d[4];
+    long long ss[4];
+    long long ds[4];
+    int src_kind, dst_kind;
 };
 
 // Fill n scalars (2n doubles if complex) with the counter-based uniforms in [-1,1).
@@ -52,6 +68,8 @@ struct RandTask {
     long long n;
     unsigned long long stream;
     int* active;  // if set, the fit's active flag is reset to 1
+    int warm;     // 1: leave the buffer as it is once the sweep counter is > 0 (warm start)
+    int pad;
 };
 
 // One zip-up fit's convergence check after a sweep (App. A stop rule).
@@ -61,6 +79,17 @@ struct CheckTask {
     int* counter;          // incremented for every sweep that ran (fit sweeps executed)
     int count;
     int pad;
+};
+
+// Fit-sweep loop state in device memory.  In a CUDA graph the loop body is a
+// conditional WHILE node; the check kernel clears the condition once no fit of the
+// group is active or `max` sweeps have run.  handle is written after capture.
+struct LoopDesc {
+    int iter;
+    int max;
+    unsigned long long handle;
+    int use_handle;
+    int total;  // iterations run since creation (statistics)
 };
 
 // Scale an array by 1/||.||_F (the fitted column MPS in mixed canonical form).
@@ -128,7 +157,7 @@ cudaError_t launch_rand(const RandTask* d_tasks, int ntasks, unsigned long long 
                         bool cplx, cudaStream_t s);
 cudaError_t launch_set_int(int* p, int n, int v, cudaStream_t s);
 cudaError_t launch_add_int(int* p, int v, cudaStream_t s);
-cudaError_t launch_check(const CheckTask* d_tasks, int ntasks, double tol, cudaStream_t s);
+cudaError_t launch_check(const CheckTask* d_tasks, int ntasks, double tol, LoopDesc* loop, cudaStream_t s);
 cudaError_t launch_scale(const ScaleTask* d_tasks, int ntasks, bool cplx, int* status, cudaStream_t s);
 cudaError_t launch_assemble(const AssembleTask* d_tasks, int ntasks, bool cplx, cudaStream_t s);
 cudaError_t launch_normalise(const NormTask* d_tasks, int ntasks, bool cplx, cudaStream_t s);
@@ -137,6 +166,7 @@ cudaError_t launch_double_layer(const DLTask* d_tasks, int ntasks, long long max
 cudaError_t launch_convert(const void* in, int in_dtype, void* out, long long n, bool cplx_out, cudaStream_t s);
 cudaError_t launch_copy(const void* in, void* out, long long bytes, cudaStream_t s);
 cudaError_t launch_fuse(const FuseTask* d_tasks, int ntasks, long long max_out, bool cplx, cudaStream_t s);
+cudaError_t launch_relayout(const RelayoutTask* d_tasks, int ntasks, long long max_elems, cudaStream_t s);
 
 // Host-side SplitMix64 (same definition as the device one) for host-drawn values.
 uint64_t splitmix64(uint64_t z);

@@ -14,6 +14,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstddef>
 #include <complex>
 #include <new>
 #include <string>
@@ -105,7 +106,7 @@ std::string Program::validate() const {
     for (size_t i = 0; i < qr.size(); ++i) {
         const QRTask& t = qr[i];
         if (t.n > 512 || t.m < t.n) return "QR shape out of range in task " + std::to_string(i);
-        c.range(t.in, ext2(t.m, t.in_rs, t.n, t.in_cs) + 1, ss, "QR in", i);
+        c.range(t.in, ext2(t.m, t.in_rs, t.n, t.in_cs) + 1, t.in_float ? ss / 2 : ss, "QR in", i);
         c.range(t.out, ext2(t.m, t.out_rs, t.n, t.out_cs) + 1, ss, "QR out", i);
         c.range(t.work, 2LL * t.m * t.n, ss, "QR work", i);
         c.range(t.loss, 1, 8, "QR loss", i);
@@ -154,6 +155,38 @@ std::string Program::validate() const {
         c.range(t.E, vol * vol, ss, "DL E", i);
         c.range(t.O, (long long)t.d * t.d, ss, "DL O", i);
     }
+    for (size_t i = 0; i < qr.size(); ++i) {
+        const QRTask& t = qr[i];
+        if (t.out2) c.range(t.out2, ext2(t.m, t.out2_rs, t.n, t.out2_cs) + 1, t.out2_kind == 3 ? 2 : t.out2_kind == 0 ? 8 : 4, "QR out2", i);
+        if (t.in_float) {
+            // FP32 input read with the same strides (already checked with the scalar size, which is larger)
+        }
+    }
+    for (size_t i = 0; i < tcs.size(); ++i) {
+        const TCTask& t = tcs[i];
+        const TCSpec& sp = tcspec[i];
+        const int esz = sp.kind == 0 ? 4 : 2;
+        if ((sp.a_ld * esz) % 16 || (sp.b_ld * esz) % 16 || sp.K > sp.a_ld || sp.K > sp.b_ld)
+            return "tensor-core operand rows not padded to 16 bytes in task " + std::to_string(i);
+        if (t.M != sp.a_rows || t.N != sp.b_rows || t.M % t.M2 || t.N % t.N2) return "tensor-core shape mismatch " + std::to_string(i);
+        c.range(P(sp.a_off), (sp.a_rows - 1) * sp.a_ld + sp.K, esz, "TC A", i);
+        c.range(P(sp.b_off), (sp.b_rows - 1) * sp.b_ld + sp.K, esz, "TC B", i);
+        const int osz = t.out_kind == 2 ? 2 : t.out_kind == 3 ? 8 : 4;
+        c.range(t.C, ext2(t.M / t.M2, t.c_m1, t.M2, t.c_m2) + ext2(t.N / t.N2, t.c_n1, t.N2, t.c_n2) + 1, osz, "TC C", i);
+        if (t.C2) c.range(t.C2, ext2(t.M / t.M2, t.d_m1, t.M2, t.d_m2) + ext2(t.N / t.N2, t.d_n1, t.N2, t.d_n2) + 1, osz, "TC C2", i);
+        c.range(t.active, 1, 4, "TC active", i);
+    }
+    for (size_t i = 0; i < rel.size(); ++i) {
+        const RelayoutTask& t = rel[i];
+        long long se = 1, de = 1;
+        for (int k = 0; k < 4; ++k) {
+            se += (long long)(t.d[k] - 1) * t.ss[k];
+            de += (long long)(t.d[k] - 1) * t.ds[k];
+        }
+        auto ksz = [](int k) { return k == 0 ? 8 : k == 3 ? 2 : 4; };
+        c.range(t.src, se, ksz(t.src_kind), "relayout src", i);
+        c.range(t.dst, de, ksz(t.dst_kind), "relayout dst", i);
+    }
     for (size_t i = 0; i < steps.size(); ++i) {
         const Step& s = steps[i];
         if (s.kind == ST_COPY) {
@@ -166,6 +199,8 @@ std::string Program::validate() const {
             c.range(s.p1, 1, 8, "mean out", i);
         }
         if (s.kind == ST_INC) c.range(s.p0, 1, 4, "counter", i);
+        if (s.kind == ST_LOOP_BEGIN) c.range(s.p0, (long long)sizeof(LoopDesc), 1, "loop descriptor", i);
+        if (s.kind == ST_CHECK && s.p1) c.range(s.p1, (long long)sizeof(LoopDesc), 1, "loop descriptor", i);
     }
     return c.err;
 }
@@ -352,8 +387,7 @@ static QRTask qr_task(const Emit& e, const FitSpec& f, int i, bool lq, size_t lo
 // Emit a lockstep group of fits.  losses_byte / active / counters are byte offsets
 // of per-fit arrays (losses: fit_max_sweeps * 2(n-1) doubles per fit).
 void emit_fits(Program& pr, int ss, std::vector<FitSpec*>& fits, int max_sweeps, double fit_tol,
-               const int* sweep_ctr_dev_placeholder, bool rand_uses_sweep) {
-    (void)sweep_ctr_dev_placeholder;
+               bool warm, bool rand_uses_sweep) {
     Emit e{pr, ss};
     int nmax = 0;
     for (auto* f : fits) nmax = std::max(nmax, f->n());
@@ -367,6 +401,7 @@ void emit_fits(Program& pr, int ss, std::vector<FitSpec*>& fits, int max_sweeps,
                 t.n = (long long)f->ybond[i] * f->O[i].q * f->ybond[i + 1];
                 t.stream = f->stream + (uint64_t)i;
                 t.active = i == 0 ? (int*)P(f->active) : nullptr;
+                t.warm = warm ? 1 : 0;
                 rt.push_back(t);
             }
         Step s;
@@ -388,44 +423,47 @@ void emit_fits(Program& pr, int ss, std::vector<FitSpec*>& fits, int max_sweeps,
         }
     // 3. sweeps
     std::vector<QRTask> qt;
-    for (int s = 0; s < max_sweeps; ++s) {
+    // the fit sweeps: one gated loop body (a conditional WHILE node in the graph)
+    const size_t loopd = pr.arena_alloc(sizeof(LoopDesc));
+    pr.loop_descs.push_back({loopd, max_sweeps});
+    pr.simple(ST_LOOP_BEGIN, P(loopd), nullptr, 0, max_sweeps);
+    {
+        const int s = 0;
         for (int k = 0; k <= nmax - 2; ++k) {
             for (int stage = 0; stage < 3; ++stage) {
                 for (auto* f : fits)
-                    if (k <= f->n() - 2) lr_gc(e, *f, k, stage, s ? (const int*)P(f->active) : nullptr, g);
+                    if (k <= f->n() - 2) lr_gc(e, *f, k, stage, (const int*)P(f->active), g);
                 pr.gc_step(g);
             }
             for (auto* f : fits)
                 if (k <= f->n() - 2) {
-                    const int nu = 2 * (f->n() - 1);
-                    const size_t loss = f->losses + (size_t)(s * nu + k) * sizeof(double);
-                    qt.push_back(qr_task(e, *f, k, false, loss, s ? (const int*)P(f->active) : nullptr));
+                    const size_t loss = f->losses + (size_t)k * sizeof(double);
+                    qt.push_back(qr_task(e, *f, k, false, loss, (const int*)P(f->active)));
                 }
             pr.qr_step(qt);
             for (auto* f : fits)
-                if (k <= f->n() - 2) lr_gc(e, *f, k, 3, s ? (const int*)P(f->active) : nullptr, g);
+                if (k <= f->n() - 2) lr_gc(e, *f, k, 3, (const int*)P(f->active), g);
             pr.gc_step(g);
         }
         for (int k = 0; k <= nmax - 2; ++k) {
             for (int stage = 0; stage < 3; ++stage) {
                 for (auto* f : fits) {
                     const int i = f->n() - 1 - k;
-                    if (i >= 1) rl_gc(e, *f, i, stage, s ? (const int*)P(f->active) : nullptr, g);
+                    if (i >= 1) rl_gc(e, *f, i, stage, (const int*)P(f->active), g);
                 }
                 pr.gc_step(g);
             }
             for (auto* f : fits) {
                 const int i = f->n() - 1 - k;
                 if (i >= 1) {
-                    const int nu = 2 * (f->n() - 1);
-                    const size_t loss = f->losses + (size_t)(s * nu + (f->n() - 1) + k) * sizeof(double);
-                    qt.push_back(qr_task(e, *f, i, true, loss, s ? (const int*)P(f->active) : nullptr));
+                    const size_t loss = f->losses + (size_t)((f->n() - 1) + k) * sizeof(double);
+                    qt.push_back(qr_task(e, *f, i, true, loss, (const int*)P(f->active)));
                 }
             }
             pr.qr_step(qt);
             for (auto* f : fits) {
                 const int i = f->n() - 1 - k;
-                if (i >= 1) rl_gc(e, *f, i, 3, s ? (const int*)P(f->active) : nullptr, g);
+                if (i >= 1) rl_gc(e, *f, i, 3, (const int*)P(f->active), g);
             }
             pr.gc_step(g);
         }
@@ -434,7 +472,7 @@ void emit_fits(Program& pr, int ss, std::vector<FitSpec*>& fits, int max_sweeps,
         for (auto* f : fits) {
             CheckTask t{};
             const int nu = 2 * (f->n() - 1);
-            t.losses = (const double*)P(f->losses + (size_t)s * nu * sizeof(double));
+            t.losses = (const double*)P(f->losses);
             t.active = (int*)P(f->active);
             t.count = nu;
             t.counter = (int*)P(f->counter);
@@ -442,11 +480,14 @@ void emit_fits(Program& pr, int ss, std::vector<FitSpec*>& fits, int max_sweeps,
         }
         Step st;
         st.kind = ST_CHECK;
+        st.p1 = P(loopd);
         st.count = (int)ct.size();
         st.first = push_all(pr.chk, ct);
         pr.steps.push_back(st);
         pr.fit_tol = fit_tol;
+        (void)s;
     }
+    pr.simple(ST_LOOP_END, nullptr, nullptr, 0, 0);
     // 4. final update at site 0 keeps Yt itself
     for (int stage = 0; stage < 3; ++stage) {
         for (auto* f : fits) rl_gc(e, *f, 0, stage, nullptr, g, stage == 2 ? f->Y[0] : 0);
@@ -552,9 +593,32 @@ void Program::relocate(char* base, size_t split, char* base2) {
     for (auto& t : dl) {
         RELOC(t.T); RELOC(t.E); RELOC(t.O);
     }
+    for (auto& t : tcs) {
+        RELOC(t.C); RELOC(t.C2); RELOC(t.active);
+    }
+    for (auto& t : rel) {
+        RELOC(t.src); RELOC(t.dst);
+    }
+    for (auto& t : qr) {
+        RELOC(t.out2);
+    }
     for (auto& s : steps) {
         RELOC(s.p0); RELOC(s.p1);
     }
+    loop_ptr.clear();
+    for (auto& l : loop_descs) loop_ptr.push_back(reloc_ptr(l.first, base, split, base2));
+}
+
+cudaError_t Program::encode_maps(char* base, size_t split, char* base2) {
+    for (size_t i = 0; i < tcs.size(); ++i) {
+        const TCSpec& sp = tcspec[i];
+        cudaError_t e = tc_make_map(&tcs[i].map_a, reloc_ptr(sp.a_off, base, split, base2), sp.kind, sp.a_rows, sp.K,
+                                    sp.a_ld, 128);
+        if (e != cudaSuccess) return e;
+        e = tc_make_map(&tcs[i].map_b, reloc_ptr(sp.b_off, base, split, base2), sp.kind, sp.b_rows, sp.K, sp.b_ld, sp.bn);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 template <typename T>
@@ -577,34 +641,202 @@ cudaError_t Program::upload_tasks() {
     if ((e = upload(nrm, &d_nrm)) != cudaSuccess) return e;
     if ((e = upload(fus, &d_fus)) != cudaSuccess) return e;
     if ((e = upload(dl, &d_dl)) != cudaSuccess) return e;
+    if ((e = upload(tcs, &d_tcs)) != cudaSuccess) return e;
+    if ((e = upload(rel, &d_rel)) != cudaSuccess) return e;
+    if (!tcs.empty()) {
+        if ((e = tc_prepare()) != cudaSuccess) return e;
+    }
     if (max_qr_m > 0) {
         if ((e = qr_prepare(max_qr_m, cplx)) != cudaSuccess) return e;
     }
     return cudaSuccess;
 }
 
+cudaError_t Program::launch_step(const Step& s, cudaStream_t st, const int* sweep_ctr, unsigned long long seed) const {
+    switch (s.kind) {
+        case ST_GC: return launch_gcontract(d_gc + s.first, s.count, s.aux, cplx, st);
+        case ST_QR: return launch_qr(d_qr + s.first, s.count, s.aux, cplx, st);
+        case ST_RAND: return launch_rand(d_rnd + s.first, s.count, seed, s.aux ? sweep_ctr : nullptr, cplx, st);
+        case ST_SETACT: return launch_set_int((int*)s.p0, (int)s.n, s.aux, st);
+        case ST_CHECK: return launch_check(d_chk + s.first, s.count, fit_tol, (LoopDesc*)s.p1, st);
+        case ST_SCALE: return launch_scale(d_scl + s.first, s.count, cplx, status, st);
+        case ST_ASM: return launch_assemble(d_asm + s.first, s.count, cplx, st);
+        case ST_NORM: return launch_normalise(d_nrm + s.first, s.count, cplx, st);
+        case ST_MEAN: return launch_mean((const double*)s.p0, (int)s.n, (double*)s.p1, st);
+        case ST_COPY: return launch_copy(s.p0, s.p1, s.n, st);
+        case ST_INC: return launch_add_int((int*)s.p0, 1, st);
+        case ST_FUSE: return launch_fuse(d_fus + s.first, s.count, s.n, cplx, st);
+        case ST_DL: return launch_double_layer(d_dl + s.first, s.count, s.n, cplx, st);
+        case ST_TC: return launch_tc_gemm(d_tcs + s.first, s.count, s.aux2 & 0xFF, s.aux, (int)s.n, s.aux2 >> 8, tc_err, st);
+        case ST_REL: return launch_relayout(d_rel + s.first, s.count, s.n, st);
+        case ST_LOOP_BEGIN: return launch_set_int((int*)s.p0, 1, 0, st);  // iteration counter = 0
+        case ST_LOOP_END: return cudaSuccess;
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+size_t Program::loop_end(size_t b) const {
+    for (size_t e = b + 1; e < steps.size(); ++e)
+        if (steps[e].kind == ST_LOOP_END) return e;
+    return steps.size();
+}
+
+// Direct launches: a loop body runs its maximum number of times; the fits that have
+// converged skip their work inside every kernel of the body.
 cudaError_t Program::launch_all(cudaStream_t st, const int* sweep_ctr, unsigned long long seed) const {
-    cudaError_t e = cudaSuccess;
-    for (const Step& s : steps) {
-        switch (s.kind) {
-            case ST_GC: e = launch_gcontract(d_gc + s.first, s.count, s.aux, cplx, st); break;
-            case ST_QR: e = launch_qr(d_qr + s.first, s.count, s.aux, cplx, st); break;
-            case ST_RAND: e = launch_rand(d_rnd + s.first, s.count, seed, s.aux ? sweep_ctr : nullptr, cplx, st); break;
-            case ST_SETACT: e = launch_set_int((int*)s.p0, (int)s.n, s.aux, st); break;
-            case ST_CHECK: e = launch_check(d_chk + s.first, s.count, fit_tol, st); break;
-            case ST_SCALE: e = launch_scale(d_scl + s.first, s.count, cplx, status, st); break;
-            case ST_ASM: e = launch_assemble(d_asm + s.first, s.count, cplx, st); break;
-            case ST_NORM: e = launch_normalise(d_nrm + s.first, s.count, cplx, st); break;
-            case ST_MEAN: e = launch_mean((const double*)s.p0, (int)s.n, (double*)s.p1, st); break;
-            case ST_COPY: e = launch_copy(s.p0, s.p1, s.n, st); break;
-            case ST_INC: e = launch_add_int((int*)s.p0, 1, st); break;
-            case ST_FUSE: e = launch_fuse(d_fus + s.first, s.count, s.n, cplx, st); break;
-            case ST_DL: e = launch_double_layer(d_dl + s.first, s.count, s.n, cplx, st); break;
-            default: e = cudaErrorInvalidValue;
+    for (size_t i = 0; i < steps.size(); ++i) {
+        cudaError_t e = launch_step(steps[i], st, sweep_ctr, seed);
+        if (e != cudaSuccess) return e;
+        if (steps[i].kind == ST_LOOP_BEGIN) {
+            const size_t end = loop_end(i);
+            for (int r = 0; r < steps[i].aux; ++r)
+                for (size_t j = i + 1; j < end; ++j) {
+                    e = launch_step(steps[j], st, sweep_ctr, seed);
+                    if (e != cudaSuccess) return e;
+                }
+            i = end;
         }
+    }
+    return cudaSuccess;
+}
+
+cudaError_t Program::init_loops(cudaStream_t st, bool in_graph, const unsigned long long* handles) const {
+    for (size_t k = 0; k < loop_descs.size(); ++k) {
+        LoopDesc d{};
+        d.iter = 0;
+        d.total = 0;
+        d.max = loop_descs[k].second;
+        d.use_handle = in_graph ? 1 : 0;
+        d.handle = in_graph ? handles[k] : 0ull;
+        cudaError_t e = cudaMemcpyAsync(loop_ptr[k], &d, sizeof(d), cudaMemcpyHostToDevice, st);
         if (e != cudaSuccess) return e;
     }
-    return e;
+    return cudaStreamSynchronize(st);
+}
+
+cudaError_t Program::reset_loop_totals(cudaStream_t st) const {
+    for (void* p : loop_ptr) {
+        cudaError_t e = cudaMemsetAsync((char*)p + offsetof(LoopDesc, total), 0, sizeof(int), st);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+// One CUDA graph for the whole program; every loop becomes a conditional WHILE node
+// whose body graph is captured on a second stream.
+cudaError_t Program::build_graph(cudaStream_t st, const int* sweep_ctr, unsigned long long seed) {
+    cudaStream_t body_stream = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&body_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return e;
+    std::vector<unsigned long long> handles;
+    cudaGraph_t g = nullptr;
+    e = cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed);
+    for (size_t i = 0; e == cudaSuccess && i < steps.size(); ++i) {
+        e = launch_step(steps[i], st, sweep_ctr, seed);
+        if (e != cudaSuccess || steps[i].kind != ST_LOOP_BEGIN) continue;
+        const size_t end = loop_end(i);
+        cudaStreamCaptureStatus cs;
+        cudaGraph_t cg = nullptr;
+        const cudaGraphNode_t* deps = nullptr;
+        size_t ndeps = 0;
+        e = cudaStreamGetCaptureInfo(st, &cs, nullptr, &cg, &deps, nullptr, &ndeps);
+        if (e != cudaSuccess) break;
+        cudaGraphConditionalHandle h;
+        e = cudaGraphConditionalHandleCreate(&h, cg, 1, cudaGraphCondAssignDefault);
+        if (e != cudaSuccess) break;
+        cudaGraphNodeParams np{};
+        np.type = cudaGraphNodeTypeConditional;
+        np.conditional.handle = h;
+        np.conditional.type = cudaGraphCondTypeWhile;
+        np.conditional.size = 1;
+        cudaGraphNode_t node;
+        std::vector<cudaGraphNode_t> dv(deps, deps + ndeps);
+        e = cudaGraphAddNode(&node, cg, dv.data(), nullptr, dv.size(), &np);
+        if (e != cudaSuccess) break;
+        cudaGraph_t body = np.conditional.phGraph_out[0];
+        e = cudaStreamBeginCaptureToGraph(body_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+        for (size_t j = i + 1; e == cudaSuccess && j < end; ++j) e = launch_step(steps[j], body_stream, sweep_ctr, seed);
+        cudaGraph_t bout = nullptr;
+        cudaError_t e2 = cudaStreamEndCapture(body_stream, &bout);
+        if (e == cudaSuccess) e = e2;
+        if (e != cudaSuccess) break;
+        e = cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
+        handles.push_back((unsigned long long)h);
+        i = end;
+    }
+    cudaError_t e2 = cudaStreamEndCapture(st, &g);
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, g, 0);
+    if (g) cudaGraphDestroy(g);
+    cudaStreamDestroy(body_stream);
+    if (e != cudaSuccess) return e;
+    return init_loops(st, true, handles.data());
+}
+
+cudaError_t Program::reset_active(cudaStream_t st) const {
+    for (const RandTask& t : rnd)
+        if (t.active) {
+            cudaError_t e = launch_set_int(t.active, 1, 1, st);
+            if (e != cudaSuccess) return e;
+        }
+    return cudaSuccess;
+}
+
+static int step_class(int kind) {
+    if (kind == ST_TC) return 0;
+    if (kind == ST_GC) return 1;
+    if (kind == ST_QR) return 2;
+    return 3;
+}
+
+cudaError_t Program::launch_class(cudaStream_t st, const int* sweep_ctr, unsigned long long seed, int cls,
+                                  long long* launches, double* flops, double* bytes) const {
+    long long n = 0;
+    double f = 0, b = 0;
+    const int ss = cplx ? 16 : 8;
+    for (const Step& s : steps) {
+        if (step_class(s.kind) != cls) continue;  // loop bodies count once: one fit sweep
+        cudaError_t e = cudaSuccess;
+        switch (s.kind) {
+            case ST_GC:
+                e = launch_gcontract(d_gc + s.first, s.count, s.aux, cplx, st);
+                for (int i = 0; i < s.count; ++i) {
+                    const GTask& t = gc[s.first + i];
+                    const double M = (double)t.M1 * t.M2, N = (double)t.N1 * t.N2, K = (double)t.K1 * t.K2;
+                    f += 2.0 * M * N * K * (cplx ? 4.0 : 1.0);
+                    b += (M * K + K * N + M * N) * ss;
+                }
+                break;
+            case ST_QR:
+                e = launch_qr(d_qr + s.first, s.count, s.aux, cplx, st);
+                for (int i = 0; i < s.count; ++i) {
+                    const QRTask& t = qr[s.first + i];
+                    f += (4.0 * t.m * (double)t.n * t.n - 4.0 / 3.0 * (double)t.n * t.n * t.n) * (cplx ? 4.0 : 1.0);
+                    b += 2.0 * t.m * (double)t.n * ss;
+                }
+                break;
+            case ST_TC:
+                e = launch_tc_gemm(d_tcs + s.first, s.count, s.aux2 & 0xFF, s.aux, (int)s.n, s.aux2 >> 8, tc_err, st);
+                for (int i = 0; i < s.count; ++i) {
+                    const TCTask& t = tcs[s.first + i];
+                    const TCSpec& sp = tcspec[s.first + i];
+                    const int esz = sp.kind == 0 ? 4 : 2, osz = t.out_kind == 2 ? 2 : t.out_kind == 3 ? 8 : 4;
+                    f += 2.0 * (double)t.M * t.N * t.K;
+                    b += ((double)t.M * t.K + (double)t.N * t.K) * esz + (double)t.M * t.N * osz * (t.C2 ? 2 : 1);
+                }
+                break;
+            default:
+                break;
+        }
+        if (e != cudaSuccess) return e;
+        ++n;
+    }
+    if (launches) *launches = n;
+    if (flops) *flops = f;
+    if (bytes) *bytes = b;
+    (void)sweep_ctr;
+    (void)seed;
+    return cudaSuccess;
 }
 
 void Program::free_all() {
@@ -612,10 +844,42 @@ void Program::free_all() {
     exec = nullptr;
     cudaFree(d_gc); cudaFree(d_qr); cudaFree(d_rnd); cudaFree(d_chk);
     cudaFree(d_scl); cudaFree(d_asm); cudaFree(d_nrm); cudaFree(d_fus); cudaFree(d_dl);
+    cudaFree(d_tcs); cudaFree(d_rel);
+    d_tcs = nullptr; d_rel = nullptr;
     d_gc = nullptr; d_qr = nullptr; d_rnd = nullptr; d_chk = nullptr;
     d_scl = nullptr; d_asm = nullptr; d_nrm = nullptr; d_fus = nullptr; d_dl = nullptr;
 }
 
 long long Program::kernel_count() const { return (long long)steps.size(); }
+
+cudaError_t Program::executed(long long runs, long long* launches, double* flops, double* qr_flops) const {
+    // steps outside loops run once per program run; a loop body runs `total` times
+    long long n = 0;
+    std::vector<int> totals(loop_ptr.size(), 0);
+    for (size_t k = 0; k < loop_ptr.size(); ++k) {
+        LoopDesc d{};
+        cudaError_t e = cudaMemcpy(&d, loop_ptr[k], sizeof(d), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return e;
+        totals[k] = d.total;
+    }
+    size_t loop = 0;
+    for (size_t i = 0; i < steps.size(); ++i) {
+        if (steps[i].kind == ST_LOOP_BEGIN) {
+            const size_t end = loop_end(i);
+            n += runs + (long long)(end - i - 1) * totals[loop++];
+            i = end;
+        } else {
+            n += runs;
+        }
+    }
+    long long body_runs = 0;
+    for (int t : totals) body_runs += t;
+    const double per_loop = loop_ptr.empty() ? 0.0 : (double)body_runs / (double)loop_ptr.size();
+    if (launches) *launches = n;
+    // every loop body holds one fit sweep of its group; gated flops are summed over groups
+    if (flops) *flops = runs * static_flops + per_loop * gated_flops;
+    if (qr_flops) *qr_flops = runs * static_qr_flops + per_loop * gated_qr_flops;
+    return cudaSuccess;
+}
 
 }  // namespace bbp

@@ -7,6 +7,7 @@
 
 #include "bbp_internal.h"
 #include "plan.h"
+#include "tc_gemm.h"
 
 namespace bbp {
 
@@ -25,8 +26,23 @@ struct OverlapSpec {
     size_t result = 0;        // final 1x1 environment = the overlap
 };
 
+// Operand geometry of one tensor-core task, kept until the arena exists so that
+// the TMA tensor maps can be encoded with real addresses.
+struct TCSpec {
+    size_t a_off = 0, b_off = 0;          // byte offsets
+    long long a_rows = 1, b_rows = 1, K = 1, a_ld = 1, b_ld = 1;
+    int kind = 0, bn = 32;
+};
+
 struct Program {
     bool cplx = false;
+    int tc_kind = 0;                      // 0 TF32, 1 BF16 (tensor-core path)
+    int* tc_err = nullptr;                // device word raised by a timed-out pipeline wait
+    std::vector<TCTask> tcs;
+    std::vector<TCSpec> tcspec;
+    std::vector<RelayoutTask> rel;
+    TCTask* d_tcs = nullptr;
+    RelayoutTask* d_rel = nullptr;
     std::vector<Step> steps;
     std::vector<GTask> gc;
     std::vector<QRTask> qr;
@@ -66,14 +82,51 @@ struct Program {
     void qr_step(std::vector<QRTask>& ts);
     void simple(int kind, void* p0, void* p1, long long n, int aux);
     void relocate(char* base, size_t split = (size_t)-1, char* base2 = nullptr);
+    void tc_step(std::vector<TCTask>& ts, std::vector<TCSpec>& sp, int kind);
+    void rel_step(std::vector<RelayoutTask>& ts);
+    // encode every TMA tensor map (after relocate)
+    cudaError_t encode_maps(char* base, size_t split = (size_t)-1, char* base2 = nullptr);
     cudaError_t upload_tasks();
+    std::vector<std::pair<size_t, int>> loop_descs;  // (arena byte offset, max iterations)
+    std::vector<void*> loop_ptr;                      // relocated LoopDesc addresses
+    cudaError_t launch_step(const Step& s, cudaStream_t st, const int* sweep_ctr, unsigned long long seed) const;
+    size_t loop_end(size_t begin) const;
     cudaError_t launch_all(cudaStream_t st, const int* sweep_ctr, unsigned long long seed) const;
+    // write every LoopDesc (max, and the conditional handle when running as a graph)
+    cudaError_t init_loops(cudaStream_t st, bool in_graph, const unsigned long long* handles) const;
+    cudaError_t reset_loop_totals(cudaStream_t st) const;
+    // capture the program as one graph with a conditional WHILE node per loop
+    cudaError_t build_graph(cudaStream_t st, const int* sweep_ctr, unsigned long long seed);
+    // set every fit's active flag (so that a replay runs every gated stage)
+    cudaError_t reset_active(cudaStream_t st) const;
+    // launch only the steps of one class (see bbp_time_kernels); returns launches
+    cudaError_t launch_class(cudaStream_t st, const int* sweep_ctr, unsigned long long seed, int cls,
+                             long long* launches, double* flops, double* bytes) const;
     void free_all();
     long long kernel_count() const;
+    // launches and algorithmic flops actually executed over `runs` runs of the program
+    // (loop bodies counted by the iterations the devices ran)
+    cudaError_t executed(long long runs, long long* launches, double* flops, double* qr_flops) const;
 };
 
-void emit_fits(Program& pr, int ss, std::vector<FitSpec*>& fits, int max_sweeps, double fit_tol,
-               const int* unused, bool rand_uses_sweep);
+// warm: the random initial state is drawn only while the sweep counter is 0; later
+// sweeps start each fit from the Y buffer as the previous sweep left it.
+void emit_fits(Program& pr, int ss, std::vector<FitSpec*>& fits, int max_sweeps, double fit_tol, bool warm,
+               bool rand_uses_sweep);
 void emit_overlaps(Program& pr, int ss, std::vector<OverlapSpec>& ov);
+
+// Tensor-core (TF32 / BF16) variant of emit_fits: same stages, same generator
+// streams and the same FP64 QR/LQ, with every contraction on tcgen05.
+struct MixCtx {
+    int ss = 8;      // canonical (FP64) scalar bytes
+    int esz = 4;     // low-precision element bytes
+    int pe = 4;      // row padding unit in elements (16 bytes)
+    int lpk = 4;     // relayout / QR store kind of low-precision operands
+    int tck = 0;     // tensor-core kind: 0 TF32, 1 BF16
+    int tco = 1;     // tensor-core epilogue kind of low-precision results
+};
+void emit_fits_mixed(Program& pr, const MixCtx& cx, std::vector<FitSpec*>& fits, int max_sweeps, double fit_tol,
+                     bool warm, bool rand_uses_sweep);
+long long padded(const MixCtx& cx, long long x);
 
 }  // namespace bbp

@@ -4,6 +4,7 @@
 // so one launch advances every message of the sweep by one step.  They form the
 // plain FP64 GPU path (every contraction, QR/LQ and reduction in FP64) and supply
 // the FP64 truncation / normalisation stages of the mixed-precision path.
+#include <cuda_bf16.h>
 #include <math.h>
 
 #include "bbp_internal.h"
@@ -85,6 +86,38 @@ uint64_t splitmix64(uint64_t z) { return sm64(z); }
 // key = splitmix64(seed XOR splitmix64(stream)); value i = splitmix64(key + i) mapped to [-1, 1)
 __host__ __device__ __forceinline__ uint64_t rng_key(uint64_t seed, uint64_t stream) { return sm64(seed ^ sm64(stream)); }
 double uniform_pm1(uint64_t seed, uint64_t stream, uint64_t idx) { return u_pm1(rng_key(seed, stream), idx); }
+
+// ---------------------------------------------------------------- element kinds
+template <typename S> __device__ __forceinline__ S from_float(const float* p, long long i);
+template <> __device__ __forceinline__ double from_float<double>(const float* p, long long i) { return (double)p[i]; }
+template <> __device__ __forceinline__ double2 from_float<double2>(const float* p, long long i) {
+    return make_double2((double)p[2 * i], (double)p[2 * i + 1]);
+}
+__device__ __forceinline__ float tf32_round(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+// kinds: 0 FP64, 2 FP32, 3 BF16, 4 FP32 rounded to TF32
+__device__ __forceinline__ void store_kind(void* p, long long i, int kind, double v) {
+    switch (kind) {
+        case 0: ((double*)p)[i] = v; break;
+        case 2: ((float*)p)[i] = (float)v; break;
+        case 3: ((__nv_bfloat16*)p)[i] = __double2bfloat16(v); break;
+        default: ((float*)p)[i] = tf32_round((float)v); break;
+    }
+}
+__device__ __forceinline__ void store_kind(void* p, long long i, int kind, double2 v) {
+    store_kind(p, 2 * i, kind, v.x);
+    store_kind(p, 2 * i + 1, kind, v.y);
+}
+__device__ __forceinline__ double load_kind(const void* p, long long i, int kind) {
+    switch (kind) {
+        case 0: return ((const double*)p)[i];
+        case 2: case 4: return (double)((const float*)p)[i];
+        default: return (double)__bfloat162float(((const __nv_bfloat16*)p)[i]);
+    }
+}
 
 // ---------------------------------------------------------------- generic contraction
 // 64x64 output tile per CTA, K in chunks of 16, 256 threads each owning 4x4 outputs.
@@ -193,7 +226,10 @@ __global__ void __launch_bounds__(256) k_qr(const QRTask* __restrict__ tasks) {
     double ss = 0.0;
     for (long long idx = tid; idx < (long long)m * n; idx += 256) {
         const int i = (int)(idx % m), j = (int)(idx / m);
-        S v = in[(long long)i * t.in_rs + (long long)j * t.in_cs];
+        const long long src = (long long)i * t.in_rs + (long long)j * t.in_cs;
+        S v;
+        if (t.in_float) v = from_float<S>(((const float*)t.in), src);
+        else v = in[src];
         if (t.conj_io) v = conjv(v);
         W[(size_t)j * m + i] = v;
         ss += abs2(v);
@@ -263,6 +299,7 @@ __global__ void __launch_bounds__(256) k_qr(const QRTask* __restrict__ tasks) {
         S v = mul(Q[(size_t)k * m + i], ph);
         if (t.conj_io) v = conjv(v);
         out[(long long)i * t.out_rs + (long long)k * t.out_cs] = v;
+        if (t.out2) store_kind(t.out2, (long long)i * t.out2_rs + (long long)k * t.out2_cs, t.out2_kind, v);
     }
 }
 
@@ -290,6 +327,7 @@ __global__ void k_rand(const RandTask* __restrict__ tasks, unsigned long long se
     const long long cnt = cplx ? 2 * t.n : t.n;
     double* p = (double*)t.ptr;
     if (t.active && blockIdx.x == 0 && threadIdx.x == 0) *t.active = 1;
+    if (t.warm && sweep_ctr && *sweep_ctr > 0) return;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < cnt; i += (long long)gridDim.x * blockDim.x)
         p[i] = u_pm1(key, (uint64_t)i);
 }
@@ -315,26 +353,37 @@ cudaError_t launch_add_int(int* p, int v, cudaStream_t s) {
 }
 
 // ---------------------------------------------------------------- fit stop rule (App. A)
-__global__ void k_check(const CheckTask* __restrict__ tasks, int ntasks, double tol) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= ntasks) return;
-    const CheckTask& t = tasks[i];
-    if (*t.active == 0) return;
-    *t.counter += 1;
-    double mean = 0.0;
-    for (int k = 0; k < t.count; ++k) mean += t.losses[k];
-    mean /= t.count;
-    double var = 0.0;
-    for (int k = 0; k < t.count; ++k) {
-        const double dv = t.losses[k] - mean;
-        var += dv * dv;
+// One CTA: every fit of the group tests std/|mean| of its sweep's losses; the loop
+// continues while any fit is still active and fewer than loop->max sweeps have run.
+__global__ void __launch_bounds__(256) k_check(const CheckTask* __restrict__ tasks, int ntasks, double tol, LoopDesc* loop) {
+    int any = 0;
+    for (int i = threadIdx.x; i < ntasks; i += blockDim.x) {
+        const CheckTask& t = tasks[i];
+        if (*t.active == 0) continue;
+        *t.counter += 1;
+        double mean = 0.0;
+        for (int k = 0; k < t.count; ++k) mean += t.losses[k];
+        mean /= t.count;
+        double var = 0.0;
+        for (int k = 0; k < t.count; ++k) {
+            const double dv = t.losses[k] - mean;
+            var += dv * dv;
+        }
+        const double sd = sqrt(var / t.count);
+        if (mean != 0.0 && sd / fabs(mean) < tol) *t.active = 0;
+        else any = 1;
     }
-    const double sd = sqrt(var / t.count);
-    if (mean != 0.0 && sd / fabs(mean) < tol) *t.active = 0;
+    any = __syncthreads_or(any);
+    if (threadIdx.x == 0 && loop) {
+        const int it = ++loop->iter;
+        loop->total += 1;
+        const unsigned int more = (any && it < loop->max) ? 1u : 0u;
+        if (loop->use_handle) cudaGraphSetConditional((cudaGraphConditionalHandle)loop->handle, more);
+    }
 }
-cudaError_t launch_check(const CheckTask* d_tasks, int ntasks, double tol, cudaStream_t s) {
+cudaError_t launch_check(const CheckTask* d_tasks, int ntasks, double tol, LoopDesc* loop, cudaStream_t s) {
     if (ntasks <= 0) return cudaSuccess;
-    k_check<<<(ntasks + 127) / 128, 128, 0, s>>>(d_tasks, ntasks, tol);
+    k_check<<<1, 256, 0, s>>>(d_tasks, ntasks, tol, loop);
     return cudaGetLastError();
 }
 
@@ -573,6 +622,29 @@ cudaError_t launch_fuse(const FuseTask* d_tasks, int ntasks, long long max_out, 
         k_fuse<double2><<<grid, 256, 0, s>>>(d_tasks);
     else
         k_fuse<double><<<grid, 256, 0, s>>>(d_tasks);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- typed 4-D relayout
+__global__ void k_relayout(const RelayoutTask* __restrict__ tasks) {
+    const RelayoutTask& t = tasks[blockIdx.y];
+    const long long total = (long long)t.d[0] * t.d[1] * t.d[2] * t.d[3];
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+        long long r = e;
+        const int i3 = (int)(r % t.d[3]); r /= t.d[3];
+        const int i2 = (int)(r % t.d[2]); r /= t.d[2];
+        const int i1 = (int)(r % t.d[1]); r /= t.d[1];
+        const int i0 = (int)r;
+        const long long so = i0 * t.ss[0] + i1 * t.ss[1] + i2 * t.ss[2] + i3 * t.ss[3];
+        const long long dof = i0 * t.ds[0] + i1 * t.ds[1] + i2 * t.ds[2] + i3 * t.ds[3];
+        store_kind(t.dst, dof, t.dst_kind, load_kind(t.src, so, t.src_kind));
+    }
+}
+cudaError_t launch_relayout(const RelayoutTask* d_tasks, int ntasks, long long max_elems, cudaStream_t s) {
+    if (ntasks <= 0) return cudaSuccess;
+    long long bx = (max_elems + 255) / 256;
+    if (bx > 1024) bx = 1024;
+    k_relayout<<<dim3((unsigned)bx, ntasks), 256, 0, s>>>(d_tasks);
     return cudaGetLastError();
 }
 

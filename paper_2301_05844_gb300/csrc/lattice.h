@@ -46,7 +46,7 @@ struct bbp_lattice;
 namespace bbp {
 std::vector<View4> column_mpo(const bbp_lattice* L, int dir, int r0, int c0, int bh, int bw, const FrameMsgs& fm, int c);
 int plan_column_sweeps(bbp_lattice* L, Program& pr, std::vector<ColumnSweep>& cs, int max_sweeps, double fit_tol,
-                       bool rand_uses_sweep);
+                       bool rand_uses_sweep, bool mixed, bool warm = false);
 }  // namespace bbp
 
 struct bbp_lattice {
@@ -64,6 +64,11 @@ struct bbp_lattice {
     std::vector<int> item_of;               // block*4+dir -> item index or -1
     size_t msg_cur = 0, msg_new = 0, msg_elems = 0;  // element offsets of the two regions
     bbp::Program sweep;
+    bool mixed = false;                     // tensor-core (TF32/BF16) sweep
+    bbp::MixCtx cx;
+    std::vector<std::array<size_t, 4>> EL_off, ER_off;  // per tensor and frame direction (bytes)
+    size_t one_lp = 0;                      // low-precision constant 1 (bytes)
+    int* d_tcerr = nullptr;
     char* arena = nullptr;
     size_t arena_bytes = 0;
     cudaStream_t stream = nullptr;
@@ -89,6 +94,7 @@ struct bbp_lattice {
     void block_origin(int blk, int& r0, int& c0) const;
     bbp::View3 msg_site(int item, int s, bool cur) const;
     std::vector<bbp::View3> incoming(int blk, int dir) const;  // message into blk from side dir
-    bbp::View4 frame_E(int dir, int r0, int c0, int bh, int bw, int rf, int cf) const;
+    bbp::View4 frame_E(int dir, int r0, int c0, int bh, int bw, int rf, int cf, int* tensor = nullptr) const;
+    bbp::View4 E_view(int t, int dir) const;  // MPO view O[w,p,q,w2] of E_t in the frame of dir
     bbp::FrameMsgs frame_msgs(int dir, const std::vector<bbp::View3> in[4]) const;
 };

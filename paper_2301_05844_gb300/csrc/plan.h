@@ -49,6 +49,17 @@ inline View3 reversed3(const View3& s) {
     return v;
 }
 
+// Low-precision operand buffers of one fit on the tensor-core path (byte offsets).
+// Every operand is K-major with its row padded to 16 bytes; no contraction index
+// has padding inside it, so the padding is never read.
+struct MixBufs {
+    std::vector<size_t> XL, XR;      // X as [x2][p][pad x] and [x][p][pad x2]
+    std::vector<size_t> OL, OR;      // MPO as [q][w2][pad(w p)] and [w][q][pad(p w2)]
+    std::vector<size_t> YS, YT;      // Y as [y][pad(q y2)] and [y2][pad(y q)]
+    std::vector<size_t> AR, AK, BR, BK;  // envs as [y][w][pad x] (R) and [y][pad(w x)] (K)
+    size_t T1 = 0, T2a = 0, T2b = 0, Ytf = 0;
+};
+
 // One zip-up fit Y ~ O X (App. A) inside a lockstep group.
 struct FitSpec {
     std::vector<View3> X;     // n input sites
@@ -59,16 +70,24 @@ struct FitSpec {
     size_t T1 = 0, T2 = 0, Yt = 0, qrw = 0;  // per-item scratch (element offsets)
     size_t losses = 0, active = 0, counter = 0;  // byte offsets: doubles, int flag, int counter
     uint64_t stream = 0;      // generator stream of site 0 (site i adds i)
+    bool mixed = false;
+    MixBufs mx;
     int n() const { return (int)X.size(); }
 };
 
-enum StepKind { ST_GC = 0, ST_QR, ST_RAND, ST_SETACT, ST_CHECK, ST_SCALE, ST_ASM, ST_NORM, ST_MEAN, ST_COPY, ST_INC, ST_FUSE, ST_DL };
+enum StepKind {
+    ST_GC = 0, ST_QR, ST_RAND, ST_SETACT, ST_CHECK, ST_SCALE, ST_ASM, ST_NORM, ST_MEAN, ST_COPY, ST_INC, ST_FUSE, ST_DL,
+    ST_TC, ST_REL,
+    ST_LOOP_BEGIN,  // p0: LoopDesc; aux: max iterations; the body runs until the matching ST_LOOP_END
+    ST_LOOP_END
+};
 
 struct Step {
     int kind;
     size_t first = 0;   // index of first task in the per-kind task array
     int count = 0;
-    int aux = 0;        // GC: max tiles; QR: max m
+    int aux = 0;        // GC: max tiles; QR: max m; TC: tile N
+    int aux2 = 0;       // TC: 0 TF32, 1 BF16
     // direct-argument steps
     void* p0 = nullptr;
     void* p1 = nullptr;

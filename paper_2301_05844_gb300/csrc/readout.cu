@@ -248,7 +248,7 @@ extern "C" int bbp_expect(bbp_lattice* L, const bbp_term* terms, int n_terms, do
             cs.push_back(s);
         }
     }
-    int rc = plan_column_sweeps(L, pr, cs, ds.fit_max_sweeps, ds.fit_tol, false);
+    int rc = plan_column_sweeps(L, pr, cs, ds.fit_max_sweeps, ds.fit_tol, false, false);
     if (rc) return rc;
 
     auto env_site = [&](const Region& R, bool left_env, int c, int i) -> View3 {
@@ -461,6 +461,7 @@ extern "C" int bbp_expect(bbp_lattice* L, const bbp_term* terms, int n_terms, do
         const size_t bytes = u.second.size() * sizeof(double);
         CKR(cudaMemcpyAsync(ro + (u.first * ss - split), u.second.data(), bytes, cudaMemcpyHostToDevice, st));
     }
+    CKR(pr.init_loops(st, false, nullptr));
     CKR(pr.launch_all(st, nullptr, ds.seed));
     std::vector<double> res(nclos * (L->cplx ? 2 : 1));
     CKR(cudaMemcpyAsync(res.data(), ro + (results * ss - split), res.size() * sizeof(double), cudaMemcpyDeviceToHost, st));

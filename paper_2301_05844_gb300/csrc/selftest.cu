@@ -50,7 +50,9 @@ extern "C" int bbp_selftest_gemm(int M, int N, int K, int prec, const float* A, 
     if (!e) e = cudaMemcpy(dt, &t, sizeof(t), cudaMemcpyHostToDevice);
     if (!e) e = tc_prepare();
     const int tiles = ((M + 127) / 128) * ((N + bn - 1) / bn);
-    if (!e) e = launch_tc_gemm((const TCTask*)dt, 1, kind, bn, tiles, derr, 0);
+    const int ek = kind == 0 ? 32 : 64;
+    const int nk = (K + ek - 1) / ek;
+    if (!e) e = launch_tc_gemm((const TCTask*)dt, 1, kind, bn, tiles, nk < 4 ? nk : 4, derr, 0);
     if (!e) e = cudaDeviceSynchronize();
     int herr = 0;
     if (!e) e = cudaMemcpy(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost);

@@ -132,8 +132,70 @@ __device__ __forceinline__ float round_tf32(float x) {
     return __uint_as_float(r);
 }
 
+__device__ __forceinline__ void store_out(void* out, long long o, int kind, float x) {
+    if (kind == 0) ((float*)out)[o] = x;
+    else if (kind == 1) ((float*)out)[o] = round_tf32(x);
+    else if (kind == 2) ((__nv_bfloat16*)out)[o] = __float2bfloat16_rn(x);
+    else ((double*)out)[o] = (double)x;
+}
+
+// Write the warp's 32 accumulator rows to one destination through the two-level map.
+// If the destination is contiguous along n2, the rows are staged through shared memory
+// so that the warp stores 32 consecutive columns of a row together; otherwise each
+// lane stores its own row (coalesced when the map is contiguous along m2).
+template <int BN>
+__device__ __forceinline__ void epilogue_dest(uint32_t tmem, int warp, int lane, int m0, int n0, int ncols, int nchunk,
+                                              int M, int M2, int N2, long long sm1, long long sm2, long long sn1,
+                                              long long sn2, int kind, float alpha, void* out, float* stage) {
+    if (sn2 == 1) {
+#pragma unroll 1
+        for (int c = 0; c < nchunk; c += 32) {
+            uint32_t v[32];
+            tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, v);
+            if (c + 16 < nchunk) tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c + 16), v + 16);
+#pragma unroll
+            for (int j = 0; j < 32; ++j) stage[lane * 33 + j] = __uint_as_float(v[j]) * alpha;
+            __syncwarp();
+            const int n = n0 + c + lane;
+            const bool nlive = (c + lane) < ncols;
+            const int n1 = nlive ? n / N2 : 0;
+            const long long co = (long long)n1 * sn1 + (nlive ? n - n1 * N2 : 0);
+#pragma unroll 4
+            for (int r = 0; r < 32; ++r) {
+                const int row = m0 + warp * 32 + r;
+                if (!nlive || row >= M) continue;
+                const int r1 = row / M2, r2 = row - r1 * M2;
+                store_out(out, (long long)r1 * sm1 + (long long)r2 * sm2 + co, kind, stage[r * 33 + lane]);
+            }
+            __syncwarp();
+        }
+        return;
+    }
+    const int row = m0 + warp * 32 + lane;
+    const bool live = row < M;
+    const int r1 = live ? row / M2 : 0, r2 = live ? row - (row / M2) * M2 : 0;
+    const long long mo = (long long)r1 * sm1 + (long long)r2 * sm2;
+    int n1 = n0 / N2, n2 = n0 - (n0 / N2) * N2;
+    long long co = (long long)n1 * sn1 + (long long)n2 * sn2;
+#pragma unroll 1
+    for (int c = 0; c < nchunk; c += 16) {
+        uint32_t v[16];
+        tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, v);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            if (c + j < ncols && live) store_out(out, mo + co, kind, __uint_as_float(v[j]) * alpha);
+            if (++n2 == N2) {
+                n2 = 0;
+                co += sn1 - (long long)(N2 - 1) * sn2;
+            } else {
+                co += sn2;
+            }
+        }
+    }
+}
+
 template <int KIND, int BN>
-__global__ void __launch_bounds__(128, 1) k_tc_gemm(const TCTask* __restrict__ tasks, int* err) {
+__global__ void __launch_bounds__(128) k_tc_gemm(const TCTask* __restrict__ tasks, int* err, int stages) {
     const TCTask& t = tasks[blockIdx.y];
     if (t.active && *t.active == 0) return;
     const int tilesM = (t.M + BM - 1) / BM, tilesN = (t.N + BN - 1) / BN;
@@ -146,14 +208,14 @@ __global__ void __launch_bounds__(128, 1) k_tc_gemm(const TCTask* __restrict__ t
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     unsigned char* sA = smem;
-    unsigned char* sB = smem + STAGES * A_BYTES;
+    unsigned char* sB = smem + stages * A_BYTES;
     __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES], accum;
     __shared__ uint32_t tmem_base;
     __shared__ int issued;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
-        for (int s = 0; s < STAGES; ++s) {
+        for (int s = 0; s < stages; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
@@ -172,7 +234,7 @@ __global__ void __launch_bounds__(128, 1) k_tc_gemm(const TCTask* __restrict__ t
     if (warp == 0 && lane == 0) {
         // TMA producer
         for (int kb = 0; kb < nk; ++kb) {
-            const int s = kb % STAGES, r = kb / STAGES;
+            const int s = kb % stages, r = kb / stages;
             if (r > 0 && !mbar_wait(&empty[s], (r - 1) & 1, err)) break;
             mbar_expect_tx(&full[s], A_BYTES + B_BYTES);
             tma_load_2d(sA + s * A_BYTES, &t.map_a, &full[s], kb * EK, m0);
@@ -184,7 +246,7 @@ __global__ void __launch_bounds__(128, 1) k_tc_gemm(const TCTask* __restrict__ t
         constexpr uint32_t ID = idesc(KIND, BN);
         bool ok = true;
         for (int kb = 0; kb < nk && ok; ++kb) {
-            const int s = kb % STAGES, r = kb / STAGES;
+            const int s = kb % stages, r = kb / stages;
             ok = mbar_wait(&full[s], r & 1, err);
             if (!ok) break;
             fence_after();
@@ -201,32 +263,15 @@ __global__ void __launch_bounds__(128, 1) k_tc_gemm(const TCTask* __restrict__ t
     const bool ready = mbar_wait(&accum, 0, err);
     fence_after();
     if (ready) {
-        const int row = m0 + warp * 32 + lane;
-        const long long mo = row < t.M ? (long long)(row / t.M2) * t.c_m1 + (long long)(row % t.M2) * t.c_m2 : 0;
-        const long long mo2 =
-            (row < t.M && t.C2) ? (long long)(row / t.M2) * t.d_m1 + (long long)(row % t.M2) * t.d_m2 : 0;
-#pragma unroll 1
-        for (int c = 0; c < BN; c += 16) {
-            uint32_t v[16];
-            tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, v);
-            if (row >= t.M) continue;
-#pragma unroll
-            for (int j = 0; j < 16; ++j) {
-                const int n = n0 + c + j;
-                if (n >= t.N) break;
-                float x = __uint_as_float(v[j]) * t.alpha;
-                const int n1 = n / t.N2, n2 = n - n1 * t.N2;
-                const long long o = mo + (long long)n1 * t.c_n1 + (long long)n2 * t.c_n2;
-                if (t.out_kind == 0) ((float*)t.C)[o] = x;
-                else if (t.out_kind == 1) ((float*)t.C)[o] = round_tf32(x);
-                else ((__nv_bfloat16*)t.C)[o] = __float2bfloat16_rn(x);
-                if (t.C2) {
-                    const long long o2 = mo2 + (long long)n1 * t.d_n1 + (long long)n2 * t.d_n2;
-                    if (t.out_kind == 0) ((float*)t.C2)[o2] = x;
-                    else if (t.out_kind == 1) ((float*)t.C2)[o2] = round_tf32(x);
-                    else ((__nv_bfloat16*)t.C2)[o2] = __float2bfloat16_rn(x);
-                }
-            }
+        const int ncols = min(BN, t.N - n0);
+        const int nchunk = (ncols + 15) & ~15;  // tcgen05.ld is warp-collective: uniform bound
+        float* stage = (float*)smem + warp * 32 * 33;
+        for (int dst = 0; dst < (t.C2 ? 2 : 1); ++dst) {
+            void* out = dst ? t.C2 : t.C;
+            const long long sm1 = dst ? t.d_m1 : t.c_m1, sm2 = dst ? t.d_m2 : t.c_m2;
+            const long long sn1 = dst ? t.d_n1 : t.c_n1, sn2 = dst ? t.d_n2 : t.c_n2;
+            epilogue_dest<BN>(tmem, warp, lane, m0, n0, ncols, nchunk, t.M, t.M2, t.N2, sm1, sm2, sn1, sn2,
+                              t.out_kind, t.alpha, out, stage);
         }
     }
     fence_before();
@@ -234,8 +279,8 @@ __global__ void __launch_bounds__(128, 1) k_tc_gemm(const TCTask* __restrict__ t
     // drain: the producer's copies must have landed before shared memory is released
     if (threadIdx.x == 0) {
         const int n_issued = issued;
-        for (int kb = (n_issued > STAGES ? n_issued - STAGES : 0); kb < n_issued; ++kb)
-            mbar_wait(&full[kb % STAGES], (kb / STAGES) & 1, err);
+        for (int kb = (n_issued > stages ? n_issued - stages : 0); kb < n_issued; ++kb)
+            mbar_wait(&full[kb % stages], (kb / stages) & 1, err);
     }
     __syncthreads();
     if (warp == 0) tmem_dealloc(tmem, BN < 32 ? 32 : BN);
@@ -270,13 +315,15 @@ cudaError_t tc_prepare() {
     return cudaSuccess;
 }
 
-cudaError_t launch_tc_gemm(const TCTask* d_tasks, int ntasks, int kind, int bn, int max_tiles, int* err, cudaStream_t s) {
+cudaError_t launch_tc_gemm(const TCTask* d_tasks, int ntasks, int kind, int bn, int max_tiles, int stages, int* err,
+                           cudaStream_t s) {
     if (ntasks <= 0) return cudaSuccess;
-    const size_t smem = tc::STAGES * (size_t)(tc::BM + bn) * tc::KBYTES + 1024;
+    if (stages < 1 || stages > tc::STAGES) return cudaErrorInvalidValue;
+    const size_t smem = (size_t)stages * (tc::BM + bn) * tc::KBYTES + 1024;
     dim3 grid(max_tiles, ntasks);
 #define TC_CASE(K_, N_)                                                                          \
     if (kind == K_ && bn == N_) {                                                                \
-        tc::k_tc_gemm<K_, N_><<<grid, 128, smem, s>>>(d_tasks, err);                             \
+        tc::k_tc_gemm<K_, N_><<<grid, 128, smem, s>>>(d_tasks, err, stages);                     \
         return cudaGetLastError();                                                               \
     }
     TC_CASE(0, 32) TC_CASE(0, 64) TC_CASE(0, 128) TC_CASE(0, 256)

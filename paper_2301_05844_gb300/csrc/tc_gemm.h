@@ -26,7 +26,8 @@ struct TCTask {
 };
 
 cudaError_t tc_prepare();
-cudaError_t launch_tc_gemm(const TCTask* d_tasks, int ntasks, int kind, int bn, int max_tiles, int* err,
+// stages: depth of the shared-memory ring (1..4), at most the number of k-blocks.
+cudaError_t launch_tc_gemm(const TCTask* d_tasks, int ntasks, int kind, int bn, int max_tiles, int stages, int* err,
                            cudaStream_t s);
 // kind: 0 FP32/TF32 elements, 1 BF16.  rows x K matrix with leading dimension ld_elems
 // (ld * element size must be a multiple of 16 bytes, base 16-byte aligned).

@@ -104,3 +104,16 @@ def test_error_paths():
     with pytest.raises(B.BBPError) as e:
         g.expect([[(99, SZ)]])
     assert e.value.code == B.ERR_INVALID
+
+
+@pytest.mark.parametrize("chi", [16, 6])
+def test_warm_start_parity(chi):
+    """Fits started from the previous sweep's result, on both sides: same residuals,
+    messages and <O>, with the full bond (16) and a truncating one (6)."""
+    cfg = I.config(1)
+    terms = I.standard_terms(4, 4)
+    g, o, gr, orr, gv, ov = run_both(cfg["tensors"], 4, 4, 2, 2, 2, 2, chi, terms, n_sweeps=6, warm_start=True,
+                                     fit_max_sweeps=2)
+    assert close(gr, orr, 1e-9), (gr, orr)
+    assert message_fidelity(g, o) > 1 - 1e-10
+    assert close(gv, ov)

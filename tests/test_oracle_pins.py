@@ -288,3 +288,16 @@ def test_residual_is_mean_squared_message_distance():
     new = {k: X.dense_mps(v) for k, v in lat.msgs.items()}
     want = np.mean([np.linalg.norm(new[k] - old[k]) ** 2 for k in old])
     assert abs(r - want) < 1e-13 and r > 1e-6
+
+
+def test_warm_start_reaches_the_same_fixed_point():
+    """Starting each fit from the previous sweep's fitted MPS (warm start) changes the
+    path, not the fixed point: at full chi both runs agree on every <O>."""
+    T = I.uniform_noise_peps(4, 4, 2, 2, seed=1)
+    terms = I.standard_terms(4, 4)
+    vals = []
+    for warm in (False, True):
+        lat = ob.Lattice(4, 4, 2, 2, 2, 2, T, chi=16, fit_tol=1e-12, fit_max_sweeps=6, warm_start=warm)
+        lat.run(n_sweeps=12)
+        vals.append(lat.expect(terms))
+    assert np.max(np.abs(vals[0] - vals[1])) < 1e-10

@@ -138,6 +138,20 @@ int bbp_get_message(bbp_lattice* lat, int block, int dir, int* nsites, int* bond
 /* Replace that message (same layout as bbp_get_message); for checkpoint / resume. */
 int bbp_set_message(bbp_lattice* lat, int block, int dir, const double* in);
 
+/* ---- standalone truncation step ------------------------------------------------- */
+
+/* Batched thin QR with diag(R) real and non-negative: the truncation step of the
+ * zip-up fit (App. A: QR on the left-to-right half sweep, keep Q).  For b < batch the
+ * m x n matrix A_b (row-major, FP64, or interleaved complex FP64 if complex_values)
+ * gives Q_b (m x n, orthonormal columns), matrices packed back to back.  A, Q and
+ * loss are device pointers; loss (may be NULL) receives -||A_b||^2, the fit loss of
+ * App. A.  Requires 1 <= n <= m and n <= 512.  stream: cudaStream_t (NULL: legacy
+ * stream); the call returns after the stream has finished the work.  Allocates a
+ * workspace of 2*m*n scalars per matrix for the duration of the call.
+ * Errors: INVALID, OOM, CUDA. */
+int bbp_qr_batched(int batch, int m, int n, int complex_values, const double* A, double* Q, double* loss,
+                   void* stream);
+
 typedef struct {
     double flops;            /* algorithmic site-update flops executed (see DESIGN) */
     double qr_flops;         /* FP64 QR/LQ flops executed */
@@ -150,7 +164,7 @@ typedef struct {
 } bbp_stats;
 
 /* Counters since bbp_set_tensors (flops are counted on the host from the planned
- * shapes; fit sweeps are read back from the device). */
+ * shapes; fit sweeps and loop iterations are read back from the device). */
 int bbp_get_stats(bbp_lattice* lat, bbp_stats* out);
 
 /* ---- diagnostics ------------------------------------------------------------------

@@ -304,9 +304,14 @@ __global__ void __launch_bounds__(256) k_qr(const QRTask* __restrict__ tasks) {
 }
 
 cudaError_t qr_prepare(int max_m, bool cplx) {
+    // the limit only ever grows, so that a smaller request cannot break a larger user
+    static size_t limit[2] = {0, 0};
     const size_t sm = (size_t)max_m * (cplx ? sizeof(double2) : sizeof(double));
-    if (cplx) return cudaFuncSetAttribute(k_qr<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    return cudaFuncSetAttribute(k_qr<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (sm <= limit[cplx ? 1 : 0]) return cudaSuccess;
+    cudaError_t e = cplx ? cudaFuncSetAttribute(k_qr<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)
+                         : cudaFuncSetAttribute(k_qr<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e == cudaSuccess) limit[cplx ? 1 : 0] = sm;
+    return e;
 }
 
 cudaError_t launch_qr(const QRTask* d_tasks, int ntasks, int max_m, bool cplx, cudaStream_t s) {

@@ -152,6 +152,28 @@ int bbp_set_message(bbp_lattice* lat, int block, int dir, const double* in);
 int bbp_qr_batched(int batch, int m, int n, int complex_values, const double* A, double* Q, double* loss,
                    void* stream);
 
+/* The same batched QR for callers that cannot allocate device memory while they
+ * run: programs that reserve the whole GPU up front under their own memory manager,
+ * or that must not risk an allocation failure (or the implicit synchronisation of an
+ * allocation) in the middle of their work.  The paper has no counterpart: this is a
+ * deployment variant of bbp_qr_batched.
+ *   - Allocates nothing: no cudaMalloc / cudaFree / allocating library call.  The
+ *     workspace is a fixed device array of BBP_QR_NOALLOC_SCRATCH_BYTES (16 MiB),
+ *     held by every GPU that loads the library until the process exits.
+ *   - Needs batch * (2*m*n scalars) plus 256 bytes per 2 matrices of descriptors to
+ *     fit in that array; larger requests fail with BBP_ERR_INVALID.
+ *   - The first call on a device resolves the array's device address and sets the
+ *     kernel's shared-memory limit (cudaGetSymbolAddress, cudaFuncSetAttribute);
+ *     make that first call before any stream capture.
+ *   - Asynchronous: returns once the work is queued on `stream`.  All calls share the
+ *     array, so calls whose work overlaps on the GPU (different streams, or different
+ *     host threads) race on it; serialise them.  Nothing in the array needs to start
+ *     at zero: every call writes all of the workspace it reads.
+ * Same arguments, layout and results as bbp_qr_batched.  Errors: INVALID, CUDA. */
+#define BBP_QR_NOALLOC_SCRATCH_BYTES (16u << 20)
+int bbp_qr_batched_noalloc(int batch, int m, int n, int complex_values, const double* A, double* Q, double* loss,
+                           void* stream);
+
 typedef struct {
     double flops;            /* algorithmic site-update flops executed (see DESIGN) */
     double qr_flops;         /* FP64 QR/LQ flops executed */

@@ -77,6 +77,7 @@ def lib():
     L.bbp_selftest_gemm.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, P, P, P]
     L.bbp_selftest_rng.argtypes = [C.c_ulonglong, C.c_ulonglong, C.c_longlong, P]
     L.bbp_qr_batched.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, P, P, P, P]
+    L.bbp_qr_batched_noalloc.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, P, P, P, P]
     _lib = L
     return L
 

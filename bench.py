@@ -9,6 +9,7 @@ FP64 QR/LQ, fit tol 1e-6 / 10 sweeps, residual target 1e-8.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--prec tf32|bf16|fp64]
   python bench.py --impl reference      # the FP64 CPU oracle, same workload
+  python bench.py --serve [--requests N] # served mix: Poisson arrivals of whole solves
 
 Prints one JSON line on rank 0.
 """
@@ -214,7 +215,7 @@ def run_ours(args):
     flops = s1["flops"] - s0["flops"]
     qr_flops = s1["qr_flops"] - s0["qr_flops"]
     kernels = s1["kernels"] - s0["kernels"]
-    vals = g.expect(terms)
+    vals = g.expect(terms) if not args.no_readout else None
 
     # kernel classes of one sweep (every fit stage active), replayed with events
     classes = {}
@@ -260,9 +261,10 @@ def run_ours(args):
             evs.append((a, b))
         torch.cuda.synchronize()
         t64 = sum(a.elapsed_time(b) for a, b in evs) / 1e3
-        v64 = h.expect(terms)
+        v64 = h.expect(terms) if vals is not None else None
         fp64 = {"sweeps_per_s": args.steps / t64, "speedup": (args.steps / dev_s) / (args.steps / t64),
-                "max_abs_dO": float(np.max(np.abs(vals - v64))), "observables": len(terms)}
+                "max_abs_dO": float(np.max(np.abs(vals - v64))) if vals is not None else None,
+                "observables": len(terms) if vals is not None else 0}
         h.close()
 
     # end to end through the C ABI from host memory: upload, solve to tolerance, read out
@@ -299,7 +301,8 @@ def run_ours(args):
                                                                 "fp64": "f64"}[prec],
                "data": "synthetic", "config": {"workload": cfg["name"], "lattice": f"{cfg['Lx']}x{cfg['Ly']}",
                                               "d": cfg["d"], "D": cfg["D"], "chi": cfg["chi"],
-                                              "block": f"{cfg['bx']}x{cfg['by']}", "messages": 48 if args.config == 2 else None,
+                                              "block": f"{cfg['bx']}x{cfg['by']}",
+                                              "messages": 2 * ((cfg["Lx"] // cfg["bx"] - 1) * (cfg["Ly"] // cfg["by"]) + (cfg["Ly"] // cfg["by"] - 1) * (cfg["Lx"] // cfg["bx"])) if cfg["boundary"] == "obc" else 4,
                                               "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{world}"},
                "tflops": flops / dev_s / 1e12, "fp64_qr_gflops": qr_flops / dev_s / 1e9,
                "gpu_launches": kernels, "latency_ms": {"p50": p50, "p99": p99}, "wall_s": wall,
@@ -308,6 +311,102 @@ def run_ours(args):
     g.close()
     if dist:
         dist.destroy_process_group()
+
+
+def serve_mix(n, seed):
+    """Seeded mix of whole solves: L in {6,...,24} (square, OBC), block b in {2,3,4}
+    dividing L, D in {2,...,5}, chi in {16,32,64}, tensors U[0,1] + 0.1 N(0,1),
+    BF16 (residual tol 1e-5) or TF32 (tol 1e-6) contractions with FP64 truncation,
+    at most 50 sweeps; read-out <sz> on every site."""
+    from paper_2301_05844_gb300 import inputs as I
+    rng = np.random.default_rng(seed)
+    reqs = []
+    for i in range(n):
+        L = int(rng.choice(np.arange(6, 25, 2)))
+        b = int(rng.choice([x for x in (2, 3, 4) if L % x == 0]))
+        D = int(rng.integers(2, 6))
+        chi = int(rng.choice([16, 32, 64]))
+        prec = "bf16" if rng.random() < 0.5 else "tf32"
+        T = I.uniform_noise_peps(L, L, 2, D, seed=1000 + i)
+        kw = dict(Lx=L, Ly=L, d=2, D=D, bx=b, by=b, chi=chi, prec=prec, tol=1e-5 if prec == "bf16" else 1e-6,
+                  max_sweeps=50, fit_tol=1e-6, fit_max_sweeps=10, seed=i + 1, warm_start=WARM)
+        reqs.append((T, [[(s, I.SIGMA_Z)] for s in range(L * L)], kw))
+    return reqs
+
+
+def run_serve(args):
+    """Served mix: every request first solved alone (sequential capacity and the
+    reference results), then all of them submitted to the request server with
+    Poisson arrivals at 0.8x the sequential capacity."""
+    import threading
+
+    import torch
+    from paper_2301_05844_gb300 import binding as B
+    torch.cuda.set_device(0)
+    reqs = serve_mix(args.requests, args.seed)
+    # warm-up: module load and the first graph capture
+    w = B.Lattice(**reqs[0][2])
+    w.set_tensors(reqs[0][0])
+    w.sweep(1)
+    w.close()
+    alone = []
+    for T, terms, kw in reqs:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        g = B.Lattice(**kw)
+        g.set_tensors(T)
+        r, k, _ = g.sweep(0)
+        v = g.expect(terms)
+        g.close()
+        torch.cuda.synchronize()
+        alone.append(dict(t=time.perf_counter() - t0, sweeps=k, values=v))
+    solo_s = sum(a["t"] for a in alone)
+    lam = 0.8 * len(reqs) / solo_s
+    gaps = np.random.default_rng(args.seed + 1).exponential(1.0 / lam, len(reqs))
+    arrivals = np.cumsum(gaps) - gaps[0]
+    feet = [B.footprint(**kw) for _, _, kw in reqs]
+    budget = int(args.serve_gb * (1 << 30))
+    srv = B.Server(max_bytes=max(budget, max(feet)), max_active=args.max_active)
+    ids = [None] * len(reqs)
+    with Clocks(0) as clk:
+        t0 = time.perf_counter()
+
+        def submitter():
+            for i, (T, terms, kw) in enumerate(reqs):
+                dt = t0 + arrivals[i] - time.perf_counter()
+                if dt > 0:
+                    time.sleep(dt)
+                ids[i] = srv.submit(T, terms, **kw)
+
+        th = threading.Thread(target=submitter)
+        th.start()
+        th.join()
+        outs = [srv.wait(i, timeout_s=3600.0) for i in ids]
+        makespan = time.perf_counter() - t0
+    st = srv.stats()
+    srv.close()
+    lat = sorted(o["latency_s"] for o in outs)
+    p = lambda q: lat[min(len(lat) - 1, int(q * len(lat)))]
+    sweeps = sum(o["sweeps"] for o in outs)
+    diffs = [float(np.max(np.abs(o["values"] - a["values"]))) for o, a in zip(outs, alone)]
+    same_sweeps = all(o["sweeps"] == a["sweeps"] for o, a in zip(outs, alone))
+    out = {"metric": "served blockBP mix: aggregate sweeps/s; p50/p99 solve latency", "value": sweeps / makespan,
+           "unit": "sweeps/s", "n_gpus": 1, "higher_is_better": True, "data": "synthetic",
+           "config": {"workload": "served mix", "requests": len(reqs), "seed": args.seed,
+                      "L": sorted({kw["Lx"] for _, _, kw in reqs}), "D": sorted({kw["D"] for _, _, kw in reqs}),
+                      "chi": sorted({kw["chi"] for _, _, kw in reqs}),
+                      "block": sorted({kw["bx"] for _, _, kw in reqs}),
+                      "prec": {p_: sum(kw["prec"] == p_ for _, _, kw in reqs) for p_ in ("bf16", "tf32")},
+                      "arrivals": f"Poisson, rate 0.8 x sequential capacity = {lam:.3f} req/s",
+                      "budget_gb": budget / (1 << 30), "max_active": args.max_active,
+                      "largest_footprint_gb": max(feet) / 1e9},
+           "latency_s": {"p50": p(0.5), "p99": p(0.99), "max": lat[-1]},
+           "sequential": {"solve_s_total": solo_s, "sweeps_per_s": sum(a["sweeps"] for a in alone) / solo_s},
+           "makespan_s": makespan, "sweeps": sweeps, "served_vs_sequential": (sweeps / makespan) /
+           (sum(a["sweeps"] for a in alone) / solo_s),
+           "alone_vs_mix": {"max_abs_dO": max(diffs), "same_sweeps": same_sweeps},
+           "server_stats": st, "clocks": clk.summary()}
+    print(json.dumps(out), flush=True)
 
 
 def main():
@@ -322,8 +421,16 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-readout", action="store_true")
+    ap.add_argument("--serve", action="store_true")
+    ap.add_argument("--requests", type=int, default=24)
+    ap.add_argument("--seed", type=int, default=5)
+    ap.add_argument("--serve-gb", type=float, default=64.0)
+    ap.add_argument("--max-active", type=int, default=16)
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.serve and args.impl == "ours":
+        run_serve(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

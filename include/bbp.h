@@ -84,6 +84,11 @@ typedef struct {
  * buffers) and plan one sweep.  *out receives the handle.  Errors: INVALID, OOM, CUDA. */
 int bbp_create_lattice(const bbp_lattice_desc* desc, bbp_lattice** out);
 
+/* Device bytes a lattice with this desc would hold (arena plus task descriptors),
+ * from the same planning as bbp_create_lattice, without allocating.  Used for
+ * admission by footprint.  Errors: INVALID. */
+int bbp_lattice_footprint(const bbp_lattice_desc* desc, size_t* bytes);
+
 /* Upload every site tensor and build the double-layer network (Fig. 1(a,b)).
  * data: OBC -> Lx*Ly tensors in row-major site order; INFINITE -> Lx*Ly unit-cell
  * tensors.  Each tensor T[p][u][l][d][r] in C order with the OBC edge legs of
@@ -212,6 +217,49 @@ int bbp_time_kernels(bbp_lattice* lat, int kernel_class, int reps, double* ms, l
  * and the random initial messages, App. A), evaluated on the host: out[i] for
  * i < n, each an exact double in [-1, 1).  Runs without a GPU. */
 int bbp_selftest_rng(unsigned long long seed, unsigned long long stream, long long n, double* out);
+
+/* ---- Request server: continuous batching of whole solves (Sec. III workflow) ----
+ * A solve is one lattice run to convergence under its desc (tol, stop_relative,
+ * max_sweeps), then read out.  A worker thread owned by the server admits queued
+ * solves in submission order whenever their resident footprint (bbp_lattice_footprint)
+ * fits in max_bytes and fewer than max_active are running; a solve that does not fit
+ * yet does not hold back smaller ones queued after it.  Every running solve has its
+ * own stream and keeps one sweep in flight, so sweeps of different solves overlap on
+ * the device; a finished solve is read out with bbp_expect and its memory released at
+ * once.  The transient read-out buffers are not part of the footprint.  Results of a
+ * solve are the same as those of bbp_create_lattice / bbp_set_tensors / bbp_sweep /
+ * bbp_expect on its own (desc->stream is ignored). */
+typedef struct bbp_server bbp_server; /* opaque; owned by the caller until bbp_server_destroy */
+
+/* Start a server on the current device.  Errors: INVALID (max_bytes 0, max_active < 1). */
+int bbp_server_create(size_t max_bytes, int max_active, bbp_server** out);
+
+/* Queue one solve.  tensors: host memory laid out as for bbp_set_tensors; terms as for
+ * bbp_expect (n_terms may be 0).  Both are copied before the call returns.  *id
+ * receives the request id.  Errors: INVALID (bad desc or term), OOM (footprint above
+ * max_bytes: the request could never be admitted). */
+int bbp_server_submit(bbp_server* srv, const bbp_lattice_desc* desc, const void* tensors, const bbp_term* terms,
+                      int n_terms, long long* id);
+
+/* Non-blocking status of request id.  *state: 0 queued, 1 running, 2 done, or the
+ * negative error code the solve failed with (bbp_last_error then holds its message).
+ * When done, out_re/out_im (n_terms each, may be NULL) receive the expectation values.
+ * sweeps / residual: sweeps run so far and the last residual; latency_s: seconds from
+ * submission to completion (0 while not finished).  Any output may be NULL.
+ * Errors: INVALID (unknown id). */
+int bbp_server_poll(bbp_server* srv, long long id, int* state, double* out_re, double* out_im, int* sweeps,
+                    double* residual, double* latency_s);
+
+/* Block until request id has finished or timeout_s has passed.  Returns OK when done,
+ * the solve's error code when it failed, TIMEOUT when still running. */
+int bbp_server_wait(bbp_server* srv, long long id, double timeout_s);
+
+/* Requests submitted and done, sweeps run by all solves, and admitted bytes in use. */
+int bbp_server_stats(bbp_server* srv, long long* submitted, long long* done, long long* sweeps, size_t* bytes_in_use);
+
+/* Finish the running solves, drop the queued ones (their state becomes STATE) and
+ * stop the worker.  Results of finished requests are released with the server. */
+void bbp_server_destroy(bbp_server* srv);
 
 #ifdef __cplusplus
 }

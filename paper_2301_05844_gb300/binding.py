@@ -78,6 +78,17 @@ def lib():
     L.bbp_selftest_rng.argtypes = [C.c_ulonglong, C.c_ulonglong, C.c_longlong, P]
     L.bbp_qr_batched.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, P, P, P, P]
     L.bbp_qr_batched_noalloc.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, P, P, P, P]
+    L.bbp_lattice_footprint.argtypes = [C.POINTER(Desc), C.POINTER(C.c_size_t)]
+    L.bbp_server_create.argtypes = [C.c_size_t, C.c_int, C.POINTER(P)]
+    L.bbp_server_submit.argtypes = [P, C.POINTER(Desc), P, C.POINTER(Term), C.c_int, C.POINTER(C.c_longlong)]
+    L.bbp_server_poll.argtypes = [P, C.c_longlong, C.POINTER(C.c_int), C.POINTER(C.c_double),
+                                  C.POINTER(C.c_double), C.POINTER(C.c_int), C.POINTER(C.c_double),
+                                  C.POINTER(C.c_double)]
+    L.bbp_server_wait.argtypes = [P, C.c_longlong, C.c_double]
+    L.bbp_server_stats.argtypes = [P, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong), C.POINTER(C.c_longlong),
+                                   C.POINTER(C.c_size_t)]
+    L.bbp_server_destroy.argtypes = [P]
+    L.bbp_server_destroy.restype = None
     _lib = L
     return L
 
@@ -100,6 +111,91 @@ def make_desc(Lx, Ly, d, D, bx, by, chi, boundary="obc", chi_exp=0, dtype=F64, p
     return Desc(Lx, Ly, OBC if boundary == "obc" else INFINITE, d, D, bx, by, chi, chi_exp, dtype,
                 _PREC[prec] if isinstance(prec, str) else prec, tol, max_sweeps, stop_relative, fit_tol,
                 fit_max_sweeps, seed, init_mode, int(warm_start), stream)
+
+
+def _term_array(terms):
+    """ctypes bbp_term array for [(site, op), ...] terms, plus the arrays it points into."""
+    n = len(terms)
+    arr = (Term * max(n, 1))()
+    keep = []
+    for i, term in enumerate(terms):
+        arr[i].nsite = len(term)
+        for k, (s, op) in enumerate(term):
+            op = np.asarray(op)
+            re = np.ascontiguousarray(op.real, dtype=np.float64)
+            im = np.ascontiguousarray(op.imag, dtype=np.float64) if np.iscomplexobj(op) else None
+            keep += [re, im]
+            arr[i].site[k] = s
+            arr[i].op_re[k] = re.ctypes.data_as(C.POINTER(C.c_double))
+            arr[i].op_im[k] = im.ctypes.data_as(C.POINTER(C.c_double)) if im is not None else None
+    return arr, keep
+
+
+def _flat_tensors(tensors, dtype):
+    dt = _NP_DTYPE[dtype]
+    return np.concatenate([np.ascontiguousarray(t, dtype=dt).reshape(-1) for t in tensors])
+
+
+def footprint(**kw):
+    """Resident device bytes of a lattice with this description (no allocation)."""
+    desc = make_desc(**kw)
+    b = C.c_size_t()
+    _check(lib().bbp_lattice_footprint(C.byref(desc), C.byref(b)))
+    return b.value
+
+
+class Server:
+    """Owning wrapper of a bbp_server (continuous batching of whole solves)."""
+
+    QUEUED, RUNNING, DONE = 0, 1, 2
+
+    def __init__(self, max_bytes, max_active=64):
+        self.h = C.c_void_p()
+        _check(lib().bbp_server_create(int(max_bytes), int(max_active), C.byref(self.h)))
+        self._nterms = {}
+
+    def submit(self, tensors, terms=(), **kw):
+        desc = make_desc(**kw)
+        flat = _flat_tensors(tensors, desc.dtype)
+        arr, _keep = _term_array(list(terms))
+        rid = C.c_longlong()
+        _check(lib().bbp_server_submit(self.h, C.byref(desc), flat.ctypes.data_as(C.c_void_p), arr, len(terms),
+                                       C.byref(rid)))
+        self._nterms[rid.value] = len(terms)
+        return rid.value
+
+    def poll(self, rid):
+        """dict(state, values (complex array once done), sweeps, residual, latency_s)."""
+        n = self._nterms[rid]
+        st, k = C.c_int(), C.c_int()
+        res, lat = C.c_double(), C.c_double()
+        re, im = np.zeros(max(n, 1)), np.zeros(max(n, 1))
+        _check(lib().bbp_server_poll(self.h, rid, C.byref(st), re.ctypes.data_as(C.POINTER(C.c_double)),
+                                     im.ctypes.data_as(C.POINTER(C.c_double)), C.byref(k), C.byref(res),
+                                     C.byref(lat)))
+        return dict(state=st.value, values=(re + 1j * im)[:n] if st.value == self.DONE else None,
+                    sweeps=k.value, residual=res.value, latency_s=lat.value)
+
+    def wait(self, rid, timeout_s=600.0):
+        _check(lib().bbp_server_wait(self.h, rid, float(timeout_s)))
+        return self.poll(rid)
+
+    def stats(self):
+        a, b, c = C.c_longlong(), C.c_longlong(), C.c_longlong()
+        u = C.c_size_t()
+        _check(lib().bbp_server_stats(self.h, C.byref(a), C.byref(b), C.byref(c), C.byref(u)))
+        return dict(submitted=a.value, done=b.value, sweeps=c.value, bytes_in_use=u.value)
+
+    def close(self):
+        if self.h:
+            lib().bbp_server_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Lattice:
@@ -126,8 +222,7 @@ class Lattice:
         device_ptr: address of the same data already on the GPU."""
         if device_ptr is not None:
             return _check(lib().bbp_set_tensors(self.h, C.c_void_p(device_ptr), 1))
-        dt = _NP_DTYPE[self.desc.dtype]
-        flat = np.concatenate([np.ascontiguousarray(t, dtype=dt).reshape(-1) for t in tensors])
+        flat = _flat_tensors(tensors, self.desc.dtype)
         self._host = flat
         return _check(lib().bbp_set_tensors(self.h, flat.ctypes.data_as(C.c_void_p), 0))
 
@@ -140,18 +235,7 @@ class Lattice:
     def expect(self, terms):
         """terms: list of [(site, op), ...] with d x d numpy operators."""
         n = len(terms)
-        arr = (Term * n)()
-        keep = []
-        for i, term in enumerate(terms):
-            arr[i].nsite = len(term)
-            for k, (s, op) in enumerate(term):
-                op = np.asarray(op)
-                re = np.ascontiguousarray(op.real, dtype=np.float64)
-                im = np.ascontiguousarray(op.imag, dtype=np.float64) if np.iscomplexobj(op) else None
-                keep += [re, im]
-                arr[i].site[k] = s
-                arr[i].op_re[k] = re.ctypes.data_as(C.POINTER(C.c_double))
-                arr[i].op_im[k] = im.ctypes.data_as(C.POINTER(C.c_double)) if im is not None else None
+        arr, keep = _term_array(terms)
         out_re = np.zeros(n)
         out_im = np.zeros(n)
         _check(lib().bbp_expect(self.h, arr, n, out_re.ctypes.data_as(C.POINTER(C.c_double)),

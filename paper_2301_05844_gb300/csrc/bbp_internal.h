@@ -151,7 +151,8 @@ struct FuseTask {
 // Launchers (kernels.cu).  cplx selects double2 (complex) over double.
 cudaError_t launch_gcontract(const GTask* d_tasks, int ntasks, int max_tiles, bool cplx, cudaStream_t s);
 cudaError_t qr_prepare(int max_m, bool cplx);  // sets the dynamic shared memory limit once
-cudaError_t launch_qr(const QRTask* d_tasks, int ntasks, int max_m, bool cplx, cudaStream_t s);
+// max_mn: largest m*n of the launch; small problems keep their matrices in shared memory.
+cudaError_t launch_qr(const QRTask* d_tasks, int ntasks, int max_m, long long max_mn, bool cplx, cudaStream_t s);
 // sweep_ctr != nullptr: the current sweep index is OR-ed into bits 36.. of each stream.
 cudaError_t launch_rand(const RandTask* d_tasks, int ntasks, unsigned long long seed, const int* sweep_ctr,
                         bool cplx, cudaStream_t s);

@@ -7,6 +7,8 @@
 #include <cuda_bf16.h>
 #include <math.h>
 
+#include <algorithm>
+
 #include "bbp_internal.h"
 
 namespace bbp {
@@ -37,6 +39,8 @@ __device__ __forceinline__ double2 mul(double2 a, double2 b) {
 }
 __device__ __forceinline__ double scal(double a, double s) { return a * s; }
 __device__ __forceinline__ double2 scal(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
+__device__ __forceinline__ double divr(double a, double d) { return a / d; }
+__device__ __forceinline__ double2 divr(double2 a, double d) { return make_double2(a.x / d, a.y / d); }
 __device__ __forceinline__ double absv(double a) { return fabs(a); }
 __device__ __forceinline__ double absv(double2 a) { return hypot(a.x, a.y); }
 __device__ __forceinline__ double shfl_down(double v, int o) { return __shfl_down_sync(0xffffffffu, v, o); }
@@ -64,6 +68,25 @@ __device__ S block_sum(S v, S* red) {
     if (threadIdx.x < 32) {
         t = (lane < (int)(blockDim.x >> 5)) ? red[lane] : zero<S>();
         t = warp_sum(t);
+        if (lane == 0) red[0] = t;
+    }
+    __syncthreads();
+    t = red[0];
+    __syncthreads();
+    return t;
+}
+
+// Block-wide maximum for 256 threads; every thread gets the result.
+__device__ double block_max(double v, double* red) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+    __syncthreads();
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x < 32) {
+        t = (lane < (int)(blockDim.x >> 5)) ? red[lane] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) t = fmax(t, __shfl_down_sync(0xffffffffu, t, o));
         if (lane == 0) red[0] = t;
     }
     __syncthreads();
@@ -203,13 +226,21 @@ cudaError_t launch_gcontract(const GTask* d_tasks, int ntasks, int max_tiles, bo
 }
 
 // ---------------------------------------------------------------- Householder QR / LQ
-// One CTA per task.  H_j = I - coef_j u_j u_j^H with u_j = x - beta_j e_1,
-// beta_j = -phase(x_0) ||x|| (no cancellation), coef_j = 1 / (||x|| (||x|| + |x_0|)).
+// One CTA per task.  Column j: alpha = x_j, x' = x_{j+1..m-1}, nrm = sqrt(|alpha|^2 + ||x'||^2),
+// beta_j = -phase(alpha) nrm (no cancellation).  The reflector is kept in the scaled form
+// H_j = I - tau_j v_j v_j^H with v_j = (x - beta_j e_j) / (alpha - beta_j), so v_j[j] = 1,
+// |v_j[i]| <= 1 and tau_j = 1 + |alpha| / nrm in [1, 2]: nothing overflows however small the
+// column is (the unscaled coefficient 1 / (nrm (nrm + |alpha|)) does once nrm is below
+// ~1e-154, which happens to columns beyond the numerical rank).  ||x'|| is accumulated
+// unscaled and recomputed relative to max |x'_i| when the sum is near underflow.  A column
+// with x' = 0 gets H_j = I and beta_j = alpha.
 // Q = H_0 ... H_{n-1} [I; 0], accumulated backwards; finally column j is multiplied
 // by phase(beta_j) so that R_jj = |beta_j| >= 0.
 constexpr int QR_MAXN = 512;
+// resident != 0: the working matrix W and Q live in dynamic shared memory (after u),
+// which holds (m + 2*m*n) scalars; otherwise they live in the task's global workspace.
 template <typename S>
-__global__ void __launch_bounds__(256) k_qr(const QRTask* __restrict__ tasks) {
+__global__ void __launch_bounds__(256) k_qr(const QRTask* __restrict__ tasks, int resident) {
     const QRTask& t = tasks[blockIdx.x];
     if (t.active && *t.active == 0) return;
     extern __shared__ __align__(16) unsigned char qr_smem[];
@@ -219,7 +250,7 @@ __global__ void __launch_bounds__(256) k_qr(const QRTask* __restrict__ tasks) {
     __shared__ S red[32];
     __shared__ double redd[32];
     const int m = t.m, n = t.n, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    S* W = (S*)t.work;
+    S* W = resident ? u + m : (S*)t.work;
     S* Q = W + (size_t)m * n;
     const S* in = (const S*)t.in;
     S* out = (S*)t.out;
@@ -238,37 +269,51 @@ __global__ void __launch_bounds__(256) k_qr(const QRTask* __restrict__ tasks) {
     if (tid == 0 && t.loss) *t.loss = -ss;
     __syncthreads();
     for (int j = 0; j < n; ++j) {
-        const S* col = W + (size_t)j * m;
-        double s2 = 0.0;
-        for (int i = j + tid; i < m; i += 256) s2 += abs2(col[i]);
-        s2 = block_sum(s2, redd);
-        const S alpha = col[j];
-        const double nrm = sqrt(s2), aa = absv(alpha);
-        S beta = zero<S>();
-        double coef = 0.0;
-        if (nrm > 0.0) {
-            const S ph = aa > 0.0 ? scal(alpha, 1.0 / aa) : one<S>();
-            beta = scal(ph, -nrm);
-            coef = 1.0 / (nrm * (nrm + aa));
+        S* col = W + (size_t)j * m;
+        double xs2 = 0.0;
+        for (int i = j + 1 + tid; i < m; i += 256) xs2 += abs2(col[i]);
+        xs2 = block_sum(xs2, redd);
+        double xnorm = sqrt(xs2);
+        if (xs2 < 1e-280) {  // near underflow (uniform branch): rescale by max |x'_i|
+            double amax = 0.0;
+            for (int i = j + 1 + tid; i < m; i += 256) amax = fmax(amax, absv(col[i]));
+            amax = block_max(amax, redd);
+            double t2 = 0.0;
+            if (amax > 0.0)
+                for (int i = j + 1 + tid; i < m; i += 256) t2 += abs2(divr(col[i], amax));
+            t2 = block_sum(t2, redd);
+            xnorm = amax > 0.0 ? amax * sqrt(t2) : 0.0;
         }
-        for (int i = j + tid; i < m; i += 256) u[i] = (i == j) ? sub(alpha, beta) : col[i];
+        const S alpha = col[j];
+        const double aa = absv(alpha);
+        S beta = alpha;
+        double tau = 0.0;
+        if (xnorm > 0.0) {
+            const double nrm = hypot(aa, xnorm);
+            const S ph = aa > 0.0 ? divr(alpha, aa) : one<S>();
+            beta = scal(ph, -nrm);
+            tau = 1.0 + aa / nrm;
+            const double den = aa + nrm;  // |alpha - beta|
+            const S cph = conjv(ph);
+            for (int i = j + tid; i < m; i += 256) u[i] = (i == j) ? one<S>() : divr(mul(col[i], cph), den);
+        }
         if (tid == 0) {
             betas[j] = beta;
-            coefs[j] = coef;
+            coefs[j] = tau;
         }
         __syncthreads();
-        if (coef != 0.0) {
+        if (tau != 0.0) {
             for (int k = j + 1 + warp; k < n; k += 8) {
                 S* ck = W + (size_t)k * m;
                 S dot = zero<S>();
                 for (int i = j + lane; i < m; i += 32) mac(dot, conjv(u[i]), ck[i]);
                 dot = warp_sum(dot);
-                const S f = scal(dot, -coef);
+                const S f = scal(dot, -tau);
                 for (int i = j + lane; i < m; i += 32) mac(ck[i], u[i], f);
             }
+            __syncthreads();
+            for (int i = j + tid; i < m; i += 256) col[i] = u[i];
         }
-        __syncthreads();
-        for (int i = j + tid; i < m; i += 256) W[(size_t)j * m + i] = u[i];
         __syncthreads();
     }
     for (long long idx = tid; idx < (long long)m * n; idx += 256) {
@@ -295,7 +340,7 @@ __global__ void __launch_bounds__(256) k_qr(const QRTask* __restrict__ tasks) {
     for (long long idx = tid; idx < (long long)m * n; idx += 256) {
         const int i = (int)(idx % m), k = (int)(idx / m);
         const double bb = absv(betas[k]);
-        const S ph = bb > 0.0 ? scal(betas[k], 1.0 / bb) : one<S>();
+        const S ph = bb > 0.0 ? divr(betas[k], bb) : one<S>();
         S v = mul(Q[(size_t)k * m + i], ph);
         if (t.conj_io) v = conjv(v);
         out[(long long)i * t.out_rs + (long long)k * t.out_cs] = v;
@@ -303,10 +348,21 @@ __global__ void __launch_bounds__(256) k_qr(const QRTask* __restrict__ tasks) {
     }
 }
 
+constexpr size_t QR_SMEM_LIMIT = 200 * 1024;
+
+static size_t qr_smem_bytes(int max_m, long long max_mn, bool cplx, int* resident) {
+    const size_t ss = cplx ? sizeof(double2) : sizeof(double);
+    const size_t all = ((size_t)max_m + 2 * (size_t)max_mn) * ss;
+    *resident = all <= QR_SMEM_LIMIT ? 1 : 0;
+    return *resident ? all : (size_t)max_m * ss;
+}
+
 cudaError_t qr_prepare(int max_m, bool cplx) {
-    // the limit only ever grows, so that a smaller request cannot break a larger user
+    // the limit only ever grows, so that a smaller request cannot break a larger user;
+    // it covers the shared-memory-resident form up to QR_SMEM_LIMIT as well
     static size_t limit[2] = {0, 0};
-    const size_t sm = (size_t)max_m * (cplx ? sizeof(double2) : sizeof(double));
+    const size_t ss = cplx ? sizeof(double2) : sizeof(double);
+    const size_t sm = std::max((size_t)max_m * ss, QR_SMEM_LIMIT);
     if (sm <= limit[cplx ? 1 : 0]) return cudaSuccess;
     cudaError_t e = cplx ? cudaFuncSetAttribute(k_qr<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)
                          : cudaFuncSetAttribute(k_qr<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
@@ -314,13 +370,14 @@ cudaError_t qr_prepare(int max_m, bool cplx) {
     return e;
 }
 
-cudaError_t launch_qr(const QRTask* d_tasks, int ntasks, int max_m, bool cplx, cudaStream_t s) {
+cudaError_t launch_qr(const QRTask* d_tasks, int ntasks, int max_m, long long max_mn, bool cplx, cudaStream_t s) {
     if (ntasks <= 0) return cudaSuccess;
-    const size_t sm = (size_t)max_m * (cplx ? sizeof(double2) : sizeof(double));
+    int resident = 0;
+    const size_t sm = qr_smem_bytes(max_m, max_mn, cplx, &resident);
     if (cplx)
-        k_qr<double2><<<ntasks, 256, sm, s>>>(d_tasks);
+        k_qr<double2><<<ntasks, 256, sm, s>>>(d_tasks, resident);
     else
-        k_qr<double><<<ntasks, 256, sm, s>>>(d_tasks);
+        k_qr<double><<<ntasks, 256, sm, s>>>(d_tasks, resident);
     return cudaGetLastError();
 }
 

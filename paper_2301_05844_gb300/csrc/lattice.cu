@@ -525,8 +525,10 @@ static int validate(const bbp_lattice_desc* d) {
     return BBP_OK;
 }
 
-int bbp_create_lattice(const bbp_lattice_desc* desc, bbp_lattice** out) {
-    if (!out) return fail(BBP_ERR_INVALID, "out is NULL");
+}  // extern "C"
+
+// Geometry, layout and the whole sweep program, checked on the host; no device memory.
+int bbp::plan_lattice(const bbp_lattice_desc* desc, bbp_lattice** out) {
     *out = nullptr;
     int rc = validate(desc);
     if (rc) return rc;
@@ -625,8 +627,31 @@ int bbp_create_lattice(const bbp_lattice_desc* desc, bbp_lattice** out) {
             return fail(BBP_ERR_INVALID, "internal plan check: " + v);
         }
     }
-    // one arena for everything
     L->arena_bytes = pr.arena_used;
+    *out = L;
+    return BBP_OK;
+}
+
+extern "C" {
+
+int bbp_lattice_footprint(const bbp_lattice_desc* desc, size_t* bytes) {
+    if (!bytes) return fail(BBP_ERR_INVALID, "bytes is NULL");
+    bbp_lattice* L = nullptr;
+    int rc = plan_lattice(desc, &L);
+    if (rc) return rc;
+    *bytes = planned_bytes(L);
+    delete L;
+    return BBP_OK;
+}
+
+int bbp_create_lattice(const bbp_lattice_desc* desc, bbp_lattice** out) {
+    if (!out) return fail(BBP_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    bbp_lattice* L = nullptr;
+    int rc = plan_lattice(desc, &L);
+    if (rc) return rc;
+    Program& pr = L->sweep;
+    // one arena for everything
     cudaError_t e = cudaMalloc((void**)&L->arena, L->arena_bytes);
     if (e != cudaSuccess) {
         delete L;
@@ -649,13 +674,14 @@ int bbp_create_lattice(const bbp_lattice_desc* desc, bbp_lattice** out) {
     L->d_residual = (double*)(base + (uintptr_t)L->d_residual);
     L->d_sweep = (int*)(base + (uintptr_t)L->d_sweep);
     e = pr.upload_tasks();
-    if (e == cudaSuccess) e = cudaMallocHost((void**)&L->h_pinned, 64);
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&L->h_pinned, sizeof(PinnedWords));
     if (e == cudaSuccess && desc->stream == nullptr) {
         e = cudaStreamCreateWithFlags(&L->stream, cudaStreamNonBlocking);
         L->own_stream = true;
     } else {
         L->stream = (cudaStream_t)desc->stream;
     }
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&L->done, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaMemsetAsync(L->arena, 0, L->arena_bytes, L->stream);
     if (e == cudaSuccess) {
         double one[2] = {1.0, 0.0};
@@ -681,6 +707,7 @@ void bbp_destroy(bbp_lattice* L) {
     L->sweep.free_all();
     if (L->arena) cudaFree(L->arena);
     if (L->h_pinned) cudaFreeHost(L->h_pinned);
+    if (L->done) cudaEventDestroy(L->done);
     if (L->own_stream && L->stream) cudaStreamDestroy(L->stream);
     delete L;
 }
@@ -819,11 +846,54 @@ static int ensure_graph(bbp_lattice* L) {
     return BBP_OK;
 }
 
+}  // extern "C"
+
+namespace bbp {
+
+// Queue one sweep (graph launch) and the copies of its residual and error words into
+// pinned memory, then record the sweep's event.  Asynchronous.
+int sweep_launch(bbp_lattice* L) {
+    int rc = ensure_graph(L);
+    if (rc) return rc;
+    CKR(cudaGraphLaunch(L->sweep.exec, L->stream));
+    CKR(cudaMemcpyAsync(&L->h_pinned->residual, L->d_residual, sizeof(double), cudaMemcpyDeviceToHost, L->stream));
+    CKR(cudaMemcpyAsync(&L->h_pinned->status, L->d_status, sizeof(int), cudaMemcpyDeviceToHost, L->stream));
+    if (L->mixed) CKR(cudaMemcpyAsync(&L->h_pinned->tc_err, L->d_tcerr, sizeof(int), cudaMemcpyDeviceToHost, L->stream));
+    CKR(cudaEventRecord(L->done, L->stream));
+    return BBP_OK;
+}
+
+bool sweep_ready(bbp_lattice* L) { return cudaEventQuery(L->done) != cudaErrorNotReady; }
+
+size_t planned_bytes(const bbp_lattice* L) {
+    return L->arena_bytes + L->sweep.tcs.size() * sizeof(TCTask) + L->sweep.gc.size() * sizeof(GTask) +
+           L->sweep.qr.size() * sizeof(QRTask);
+}
+
+// After the sweep's event: account for it and apply the stop rule.  *stop is set when
+// the residual meets the tolerance (absolute, or relative to the first sweep).
+int sweep_collect(bbp_lattice* L, double* residual, bool* stop) {
+    CKR(cudaEventSynchronize(L->done));
+    L->sweeps++;
+    const double r = L->h_pinned->residual;
+    if (residual) *residual = r;
+    if (L->mixed && L->h_pinned->tc_err) return fail(BBP_ERR_TIMEOUT, "a tensor-core pipeline wait exceeded its bound");
+    if (L->h_pinned->status != 0 || !std::isfinite(r))
+        return fail(BBP_ERR_NUMERIC, "a message or column MPS has zero or non-finite norm");
+    if (L->sweeps == 1) L->first_residual = r;
+    L->last_residual = r;
+    const double crit = L->desc.stop_relative ? (L->first_residual > 0 ? r / L->first_residual : 0.0) : r;
+    if (stop) *stop = crit < L->desc.tol;
+    return BBP_OK;
+}
+
+}  // namespace bbp
+
+extern "C" {
+
 int bbp_sweep(bbp_lattice* L, int n_sweeps, double* residual_out, int* sweeps_done) {
     if (!L) return fail(BBP_ERR_INVALID, "lattice is NULL");
     if (!L->has_tensors) return fail(BBP_ERR_STATE, "bbp_set_tensors has not been called");
-    int rc = ensure_graph(L);
-    if (rc) return rc;
     const bool fixed = n_sweeps > 0;
     const int cap = fixed ? n_sweeps : std::max(1, L->desc.max_sweeps);
     int done = 0;
@@ -835,31 +905,18 @@ int bbp_sweep(bbp_lattice* L, int n_sweeps, double* residual_out, int* sweeps_do
         return BBP_OK;
     }
     for (int k = 0; k < cap; ++k) {
-        CKR(cudaGraphLaunch(L->sweep.exec, L->stream));
-        CKR(cudaMemcpyAsync(L->h_pinned, L->d_residual, sizeof(double), cudaMemcpyDeviceToHost, L->stream));
-        CKR(cudaMemcpyAsync((int*)(L->h_pinned + 1), L->d_status, sizeof(int), cudaMemcpyDeviceToHost, L->stream));
-        CKR(cudaStreamSynchronize(L->stream));
-        done++;
-        L->sweeps++;
-        r = L->h_pinned[0];
-        if (L->mixed) {
-            int te = 0;
-            CKR(cudaMemcpy(&te, L->d_tcerr, sizeof(int), cudaMemcpyDeviceToHost));
-            if (te) return fail(BBP_ERR_TIMEOUT, "a tensor-core pipeline wait exceeded its bound");
-        }
-        if (*(int*)(L->h_pinned + 1) != 0 || !std::isfinite(r)) {
+        int rc = sweep_launch(L);
+        bool stop = false;
+        if (!rc) rc = sweep_collect(L, &r, &stop);
+        done += rc ? 0 : 1;
+        if (rc) {
             if (residual_out) *residual_out = r;
             if (sweeps_done) *sweeps_done = done;
-            return fail(BBP_ERR_NUMERIC, "a message or column MPS has zero or non-finite norm");
+            return rc;
         }
-        if (L->sweeps == 1) L->first_residual = r;
-        L->last_residual = r;
-        if (!fixed) {
-            const double crit = L->desc.stop_relative ? (L->first_residual > 0 ? r / L->first_residual : 0.0) : r;
-            if (crit < L->desc.tol) {
-                converged = true;
-                break;
-            }
+        if (!fixed && stop) {
+            converged = true;
+            break;
         }
     }
     if (residual_out) *residual_out = r;

@@ -40,6 +40,13 @@ struct ColumnSweep {
     std::vector<FitSpec> fits;
 };
 
+// Words read back after every sweep (pinned host memory).
+struct PinnedWords {
+    double residual;
+    int status;
+    int tc_err;
+};
+
 }  // namespace bbp
 
 struct bbp_lattice;
@@ -79,7 +86,8 @@ struct bbp_lattice {
     double* d_resid_terms = nullptr;
     int* d_counters = nullptr;
     int ncounters = 0;
-    double* h_pinned = nullptr;
+    bbp::PinnedWords* h_pinned = nullptr;
+    cudaEvent_t done = nullptr;  // recorded after each sweep's read-back copies
     bool has_tensors = false;
     // stats
     int sweeps = 0;
@@ -98,3 +106,14 @@ struct bbp_lattice {
     bbp::View4 E_view(int t, int dir) const;  // MPO view O[w,p,q,w2] of E_t in the frame of dir
     bbp::FrameMsgs frame_msgs(int dir, const std::vector<bbp::View3> in[4]) const;
 };
+
+namespace bbp {
+// Asynchronous sweep interface (used by bbp_sweep and the request server).
+int sweep_launch(bbp_lattice* L);
+bool sweep_ready(bbp_lattice* L);
+int sweep_collect(bbp_lattice* L, double* residual, bool* stop);
+// Plan a lattice without allocating device memory (arena_bytes set); nullptr on error.
+int plan_lattice(const bbp_lattice_desc* desc, bbp_lattice** out);
+// Resident device bytes of a planned lattice: arena plus sweep task descriptors.
+size_t planned_bytes(const bbp_lattice* L);
+}  // namespace bbp

@@ -39,7 +39,7 @@ extern "C" int bbp_qr_batched(int batch, int m, int n, int complex_values, const
     }
     e = cudaMemcpyAsync(d_ts, ts.data(), ts.size() * sizeof(QRTask), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = qr_prepare(m, complex_values != 0);
-    if (e == cudaSuccess) e = launch_qr(d_ts, batch, m, complex_values != 0, st);
+    if (e == cudaSuccess) e = launch_qr(d_ts, batch, m, (long long)m * n, complex_values != 0, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // ts is released on return
     cudaFreeAsync(d_ts, st);
     cudaFreeAsync(work, st);

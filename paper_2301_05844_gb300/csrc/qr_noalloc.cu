@@ -71,7 +71,7 @@ extern "C" int bbp_qr_batched_noalloc(int batch, int m, int n, int complex_value
     cudaStream_t st = (cudaStream_t)stream;
     k_build_qr_tasks<<<(batch + 127) / 128, 128, 0, st>>>(tasks, batch, m, n, ss, A, Q, loss, base + task_bytes);
     e = cudaGetLastError();
-    if (e == cudaSuccess) e = launch_qr(tasks, batch, m, complex_values != 0, st);
+    if (e == cudaSuccess) e = launch_qr(tasks, batch, m, (long long)m * n, complex_values != 0, st);
     if (e != cudaSuccess) return fail(BBP_ERR_CUDA, std::string("qr_batched_noalloc: ") + cudaGetErrorString(e));
     return BBP_OK;
 }

@@ -121,6 +121,8 @@ def config(k: int) -> dict:
     2: 12x12 OBC, d=2, D=3, near-product (+0.05N), 3x3 blocks, chi=32, FP32/TF32, residual 1e-8.
     3: infinite 2x2 cell, d=2, D=4, complex64 N(0,1)/sqrt(D), 4x4 block, chi=64, BF16.
     4: 32x32 OBC, d=2, D=5, U[0,1]+0.1N as float32, 4x4 blocks, chi=96, TF32.
+    6: 20x20 OBC, d=2, D=4, U[0,1]+0.1N, 4x4 blocks (80 messages), chi=64, BF16 -- the
+       tensor-core measurement workload (D=4, chi=64 contractions over >= 64 messages).
     """
     if k == 1:
         return dict(name="peps4x4_D2_chi16_fp64", Lx=4, Ly=4, d=2, D=2, bx=2, by=2, chi=16,
@@ -136,6 +138,10 @@ def config(k: int) -> dict:
         return dict(name="peps32x32_D5_chi96_tf32", Lx=32, Ly=32, d=2, D=5, bx=4, by=4, chi=96,
                     boundary="obc", tensors=uniform_noise_peps(32, 32, 2, 5, seed=4, dtype=np.float32),
                     prec="tf32")
+    if k == 6:
+        # tensor-core measurement workload: D=4, chi=64 contractions batched over 80 messages
+        return dict(name="peps20x20_D4_chi64_bf16", Lx=20, Ly=20, d=2, D=4, bx=4, by=4, chi=64,
+                    boundary="obc", tensors=uniform_noise_peps(20, 20, 2, 4, seed=6), prec="bf16", tol=1e-6)
     raise ValueError(k)
 
 

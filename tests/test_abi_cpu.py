@@ -85,3 +85,52 @@ def test_library_generator_matches_the_oracle_definition(libpath):
         out = np.zeros(257)
         assert L.bbp_selftest_rng(seed, stream, 257, out.ctypes.data) == 0
         assert np.array_equal(out, ob.uniform_pm1(seed, stream, 257))
+
+
+def test_footprint_is_planned_without_allocating(libpath):
+    """bbp_lattice_footprint runs the planning only: it works without a GPU, grows
+    with chi and with the lattice, and rejects what bbp_create_lattice rejects."""
+    from paper_2301_05844_gb300 import binding as B
+    f8 = B.footprint(Lx=12, Ly=12, d=2, D=3, bx=3, by=3, chi=8)
+    f32 = B.footprint(Lx=12, Ly=12, d=2, D=3, bx=3, by=3, chi=32)
+    big = B.footprint(Lx=24, Ly=24, d=2, D=3, bx=3, by=3, chi=8)
+    assert 0 < f8 < f32 and f8 < big
+    with pytest.raises(B.BBPError) as e:
+        B.footprint(Lx=4, Ly=4, d=2, D=2, bx=3, by=2, chi=16)
+    assert e.value.code == B.ERR_INVALID
+
+
+def test_server_host_logic_without_a_gpu(libpath):
+    """Argument checks and admission run on the host: a request above the byte budget
+    is refused at submission, bad descriptions and terms are rejected, and a request
+    whose device allocation fails (no GPU here) finishes with that error code."""
+    import numpy as np
+    from paper_2301_05844_gb300 import binding as B
+    from paper_2301_05844_gb300 import inputs
+    L = B.lib()
+    h = ctypes.c_void_p()
+    assert L.bbp_server_create(0, 4, ctypes.byref(h)) == B.ERR_INVALID
+    assert L.bbp_server_create(1 << 20, 0, ctypes.byref(h)) == B.ERR_INVALID
+    cfg = dict(Lx=4, Ly=4, d=2, D=2, bx=2, by=2, chi=16)
+    T = inputs.uniform_noise_peps(4, 4, 2, 2, seed=1)
+    need = B.footprint(**cfg)
+    srv = B.Server(max_bytes=need, max_active=2)
+    try:
+        with pytest.raises(B.BBPError) as e:
+            srv.submit(T, **dict(cfg, Lx=8, Ly=8))  # refused before its tensors are read
+        assert e.value.code == B.ERR_OOM
+        with pytest.raises(B.BBPError) as e:
+            srv.submit(T, **dict(cfg, bx=3))
+        assert e.value.code == B.ERR_INVALID
+        with pytest.raises(B.BBPError) as e:
+            srv.submit(T, [[]], **cfg)  # a term on no site
+        assert e.value.code == B.ERR_INVALID
+        rid = srv.submit(T, [[(0, inputs.SIGMA_Z)]], **cfg)
+        assert L.bbp_server_wait(srv.h, rid, 60.0) in (B.ERR_OOM, B.ERR_CUDA)
+        st = srv.poll(rid)
+        assert st["state"] in (B.ERR_OOM, B.ERR_CUDA) and st["values"] is None
+        s = srv.stats()
+        assert s["submitted"] == 1 and s["done"] == 0 and s["bytes_in_use"] == 0
+        assert L.bbp_server_poll(srv.h, 12345, None, None, None, None, None, None) == B.ERR_INVALID
+    finally:
+        srv.close()

@@ -117,3 +117,14 @@ def test_warm_start_parity(chi):
     assert close(gr, orr, 1e-9), (gr, orr)
     assert message_fidelity(g, o) > 1 - 1e-10
     assert close(gv, ov)
+
+
+def test_bonds_above_the_numerical_rank():
+    """chi = 64 > the rank that the column MPS can carry next to an open edge: the fits
+    meet QR columns beyond the numerical rank (tiny norms) and must still match the
+    oracle (FP64, 1e-10)."""
+    T = I.uniform_noise_peps(6, 6, 2, 3, seed=11)
+    terms = I.standard_terms(6, 6)
+    g, o, gres, ores, gv, ov = run_both(T, 6, 6, 2, 3, 3, 3, 64, terms, 3, fit_tol=0.0, fit_max_sweeps=2, seed=7)
+    assert np.allclose(gres, ores, rtol=1e-8, atol=1e-14)
+    assert np.max(np.abs(gv - ov)) < 1e-10

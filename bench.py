@@ -384,7 +384,13 @@ def run_serve(args):
         outs = [srv.wait(i, timeout_s=3600.0) for i in ids]
         makespan = time.perf_counter() - t0
     st = srv.stats()
+    # saturation: every request submitted at once (throughput with all slots busy)
+    t1 = time.perf_counter()
+    bids = [srv.submit(T, terms, **kw) for T, terms, kw in reqs]
+    bouts = [srv.wait(i, timeout_s=3600.0) for i in bids]
+    burst_s = time.perf_counter() - t1
     srv.close()
+    bdiff = max(float(np.max(np.abs(o["values"] - a["values"]))) for o, a in zip(bouts, alone))
     lat = sorted(o["latency_s"] for o in outs)
     p = lambda q: lat[min(len(lat) - 1, int(q * len(lat)))]
     sweeps = sum(o["sweeps"] for o in outs)
@@ -405,6 +411,9 @@ def run_serve(args):
            "makespan_s": makespan, "sweeps": sweeps, "served_vs_sequential": (sweeps / makespan) /
            (sum(a["sweeps"] for a in alone) / solo_s),
            "alone_vs_mix": {"max_abs_dO": max(diffs), "same_sweeps": same_sweeps},
+           "saturated": {"makespan_s": burst_s, "sweeps_per_s": sum(o["sweeps"] for o in bouts) / burst_s,
+                         "vs_sequential": (sum(o["sweeps"] for o in bouts) / burst_s) /
+                         (sum(a["sweeps"] for a in alone) / solo_s), "max_abs_dO_vs_alone": bdiff},
            "server_stats": st, "clocks": clk.summary()}
     print(json.dumps(out), flush=True)
 

@@ -624,28 +624,30 @@ cudaError_t Program::encode_maps(char* base, size_t split, char* base2) {
     return cudaSuccess;
 }
 
+// Stream-ordered allocations (cudaMallocAsync / cudaFreeAsync) do not synchronise the
+// device, so creating or destroying one lattice never waits for another's kernels.
 template <typename T>
-static cudaError_t upload(std::vector<T>& v, T** dptr) {
+static cudaError_t upload(std::vector<T>& v, T** dptr, cudaStream_t st) {
     *dptr = nullptr;
     if (v.empty()) return cudaSuccess;
-    cudaError_t e = cudaMalloc((void**)dptr, v.size() * sizeof(T));
+    cudaError_t e = cudaMallocAsync((void**)dptr, v.size() * sizeof(T), st);
     if (e != cudaSuccess) return e;
-    return cudaMemcpy(*dptr, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
+    return cudaMemcpyAsync(*dptr, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, st);
 }
 
-cudaError_t Program::upload_tasks() {
+cudaError_t Program::upload_tasks(cudaStream_t st) {
     cudaError_t e;
-    if ((e = upload(gc, &d_gc)) != cudaSuccess) return e;
-    if ((e = upload(qr, &d_qr)) != cudaSuccess) return e;
-    if ((e = upload(rnd, &d_rnd)) != cudaSuccess) return e;
-    if ((e = upload(chk, &d_chk)) != cudaSuccess) return e;
-    if ((e = upload(scl, &d_scl)) != cudaSuccess) return e;
-    if ((e = upload(asmb, &d_asm)) != cudaSuccess) return e;
-    if ((e = upload(nrm, &d_nrm)) != cudaSuccess) return e;
-    if ((e = upload(fus, &d_fus)) != cudaSuccess) return e;
-    if ((e = upload(dl, &d_dl)) != cudaSuccess) return e;
-    if ((e = upload(tcs, &d_tcs)) != cudaSuccess) return e;
-    if ((e = upload(rel, &d_rel)) != cudaSuccess) return e;
+    if ((e = upload(gc, &d_gc, st)) != cudaSuccess) return e;
+    if ((e = upload(qr, &d_qr, st)) != cudaSuccess) return e;
+    if ((e = upload(rnd, &d_rnd, st)) != cudaSuccess) return e;
+    if ((e = upload(chk, &d_chk, st)) != cudaSuccess) return e;
+    if ((e = upload(scl, &d_scl, st)) != cudaSuccess) return e;
+    if ((e = upload(asmb, &d_asm, st)) != cudaSuccess) return e;
+    if ((e = upload(nrm, &d_nrm, st)) != cudaSuccess) return e;
+    if ((e = upload(fus, &d_fus, st)) != cudaSuccess) return e;
+    if ((e = upload(dl, &d_dl, st)) != cudaSuccess) return e;
+    if ((e = upload(tcs, &d_tcs, st)) != cudaSuccess) return e;
+    if ((e = upload(rel, &d_rel, st)) != cudaSuccess) return e;
     if (!tcs.empty()) {
         if ((e = tc_prepare()) != cudaSuccess) return e;
     }
@@ -842,12 +844,12 @@ cudaError_t Program::launch_class(cudaStream_t st, const int* sweep_ctr, unsigne
     return cudaSuccess;
 }
 
-void Program::free_all() {
+void Program::free_all(cudaStream_t st) {
     if (exec) cudaGraphExecDestroy(exec);
     exec = nullptr;
-    cudaFree(d_gc); cudaFree(d_qr); cudaFree(d_rnd); cudaFree(d_chk);
-    cudaFree(d_scl); cudaFree(d_asm); cudaFree(d_nrm); cudaFree(d_fus); cudaFree(d_dl);
-    cudaFree(d_tcs); cudaFree(d_rel);
+    for (void* p : {(void*)d_gc, (void*)d_qr, (void*)d_rnd, (void*)d_chk, (void*)d_scl, (void*)d_asm, (void*)d_nrm,
+                    (void*)d_fus, (void*)d_dl, (void*)d_tcs, (void*)d_rel})
+        if (p) cudaFreeAsync(p, st);
     d_tcs = nullptr; d_rel = nullptr;
     d_gc = nullptr; d_qr = nullptr; d_rnd = nullptr; d_chk = nullptr;
     d_scl = nullptr; d_asm = nullptr; d_nrm = nullptr; d_fus = nullptr; d_dl = nullptr;

@@ -86,7 +86,8 @@ struct Program {
     void rel_step(std::vector<RelayoutTask>& ts);
     // encode every TMA tensor map (after relocate)
     cudaError_t encode_maps(char* base, size_t split = (size_t)-1, char* base2 = nullptr);
-    cudaError_t upload_tasks();
+    // task descriptors to the device (stream-ordered allocation on st)
+    cudaError_t upload_tasks(cudaStream_t st);
     std::vector<std::pair<size_t, int>> loop_descs;  // (arena byte offset, max iterations)
     std::vector<void*> loop_ptr;                      // relocated LoopDesc addresses
     cudaError_t launch_step(const Step& s, cudaStream_t st, const int* sweep_ctr, unsigned long long seed) const;
@@ -102,7 +103,8 @@ struct Program {
     // launch only the steps of one class (see bbp_time_kernels); returns launches
     cudaError_t launch_class(cudaStream_t st, const int* sweep_ctr, unsigned long long seed, int cls,
                              long long* launches, double* flops, double* bytes) const;
-    void free_all();
+    // release the graph and the task descriptors (stream-ordered on st)
+    void free_all(cudaStream_t st);
     long long kernel_count() const;
     // launches and algorithmic flops actually executed over `runs` runs of the program
     // (loop bodies counted by the iterations the devices ran)

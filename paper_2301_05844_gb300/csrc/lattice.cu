@@ -6,6 +6,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -16,6 +17,31 @@
 #include "lattice.h"
 
 using namespace bbp;
+
+// Pinned read-back words come from slabs that live as long as the process: freeing
+// page-locked memory synchronises the whole device, which a lattice destroyed while
+// others run must not do.
+static std::mutex g_pin_mu;
+static std::vector<PinnedWords*> g_pin_free;
+
+static PinnedWords* pinned_get() {
+    std::lock_guard<std::mutex> g(g_pin_mu);
+    if (g_pin_free.empty()) {
+        constexpr int SLAB = 64;
+        PinnedWords* slab = nullptr;
+        if (cudaMallocHost((void**)&slab, SLAB * sizeof(PinnedWords)) != cudaSuccess) return nullptr;
+        for (int i = SLAB - 1; i >= 0; --i) g_pin_free.push_back(slab + i);
+    }
+    PinnedWords* p = g_pin_free.back();
+    g_pin_free.pop_back();
+    *p = PinnedWords{};
+    return p;
+}
+
+static void pinned_put(PinnedWords* p) {
+    std::lock_guard<std::mutex> g(g_pin_mu);
+    g_pin_free.push_back(p);
+}
 
 #define CKR(expr)                                                                            \
     do {                                                                                     \
@@ -651,10 +677,19 @@ int bbp_create_lattice(const bbp_lattice_desc* desc, bbp_lattice** out) {
     int rc = plan_lattice(desc, &L);
     if (rc) return rc;
     Program& pr = L->sweep;
-    // one arena for everything
-    cudaError_t e = cudaMalloc((void**)&L->arena, L->arena_bytes);
+    cudaError_t e = cudaSuccess;
+    if (desc->stream == nullptr) {
+        e = cudaStreamCreateWithFlags(&L->stream, cudaStreamNonBlocking);
+        L->own_stream = e == cudaSuccess;
+    } else {
+        L->stream = (cudaStream_t)desc->stream;
+    }
+    // one arena for everything, stream-ordered so that creating a lattice never waits
+    // for the kernels of another
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)&L->arena, L->arena_bytes, L->stream);
     if (e != cudaSuccess) {
-        delete L;
+        L->arena = nullptr;
+        bbp_destroy(L);
         return fail(BBP_ERR_OOM, std::string("arena of ") + std::to_string(L->arena_bytes) + " bytes: " + cudaGetErrorString(e));
     }
     char* base = L->arena;
@@ -673,13 +708,10 @@ int bbp_create_lattice(const bbp_lattice_desc* desc, bbp_lattice** out) {
     L->d_resid_terms = (double*)(base + (uintptr_t)L->d_resid_terms);
     L->d_residual = (double*)(base + (uintptr_t)L->d_residual);
     L->d_sweep = (int*)(base + (uintptr_t)L->d_sweep);
-    e = pr.upload_tasks();
-    if (e == cudaSuccess) e = cudaMallocHost((void**)&L->h_pinned, sizeof(PinnedWords));
-    if (e == cudaSuccess && desc->stream == nullptr) {
-        e = cudaStreamCreateWithFlags(&L->stream, cudaStreamNonBlocking);
-        L->own_stream = true;
-    } else {
-        L->stream = (cudaStream_t)desc->stream;
+    e = pr.upload_tasks(L->stream);
+    if (e == cudaSuccess) {
+        L->h_pinned = pinned_get();
+        if (!L->h_pinned) e = cudaErrorMemoryAllocation;
     }
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&L->done, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaMemsetAsync(L->arena, 0, L->arena_bytes, L->stream);
@@ -704,9 +736,12 @@ int bbp_create_lattice(const bbp_lattice_desc* desc, bbp_lattice** out) {
 
 void bbp_destroy(bbp_lattice* L) {
     if (!L) return;
-    L->sweep.free_all();
-    if (L->arena) cudaFree(L->arena);
-    if (L->h_pinned) cudaFreeHost(L->h_pinned);
+    // waits for this lattice's own work only; the frees are stream-ordered
+    if (L->stream) cudaStreamSynchronize(L->stream);
+    L->sweep.free_all(L->stream);
+    if (L->arena) cudaFreeAsync(L->arena, L->stream);
+    if (L->stream) cudaStreamSynchronize(L->stream);
+    if (L->h_pinned) pinned_put(L->h_pinned);
     if (L->done) cudaEventDestroy(L->done);
     if (L->own_stream && L->stream) cudaStreamDestroy(L->stream);
     delete L;

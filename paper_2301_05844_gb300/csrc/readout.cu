@@ -443,19 +443,20 @@ extern "C" int bbp_expect(bbp_lattice* L, const bbp_term* terms, int n_terms, do
     }
     const size_t ro_bytes = pr.arena_used - split;
     char* ro = nullptr;
-    CKR(cudaMalloc((void**)&ro, ro_bytes));
-    struct Guard {
+    cudaStream_t st = L->stream;
+    CKR(cudaMallocAsync((void**)&ro, ro_bytes, st));
+    struct Guard {  // stream-ordered release after the read-out's last kernel
         char* p;
         Program* pr;
+        cudaStream_t st;
         ~Guard() {
-            pr->free_all();
-            cudaFree(p);
+            pr->free_all(st);
+            cudaFreeAsync(p, st);
         }
-    } guard{ro, &pr};
+    } guard{ro, &pr, st};
     pr.relocate(L->arena, split, ro);
     pr.status = L->d_status;
-    CKR(pr.upload_tasks());
-    cudaStream_t st = L->stream;
+    CKR(pr.upload_tasks(st));
     CKR(cudaMemsetAsync(ro, 0, ro_bytes, st));
     for (auto& u : uploads) {
         const size_t bytes = u.second.size() * sizeof(double);

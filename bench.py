@@ -166,10 +166,9 @@ def run_reference(args):
 def run_ours(args):
     import torch
     from paper_2301_05844_gb300 import binding as B
+    from paper_2301_05844_gb300 import replicas as R
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    rank, local, world = R.rank_info()
     torch.cuda.set_device(local)
     dist = None
     if world > 1:
@@ -206,12 +205,8 @@ def run_ours(args):
     step_ms = [a.elapsed_time(b) for a, b in ev]
     dev_s = sum(step_ms) / 1e3
     s1 = g.stats()
-    tmax = dev_s
-    if dist:
-        t = torch.tensor([dev_s], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tmax = float(t.item())
-    value = world * args.steps / tmax
+    tmax = R.max_over_ranks(dev_s, device=dev)
+    value = R.whole_job_rate(args.steps, world, tmax)
     flops = s1["flops"] - s0["flops"]
     qr_flops = s1["qr_flops"] - s0["qr_flops"]
     kernels = s1["kernels"] - s0["kernels"]

@@ -44,6 +44,15 @@ def workload(cfg_id):
     from paper_2301_05844_gb300 import inputs as I
     cfg = I.config(cfg_id)
     Lx, Ly = cfg["Lx"], cfg["Ly"]
+    if cfg["boundary"] == "infinite":
+        # 2-site terms on the 4 nearest-neighbour bonds of the 2x2 centre of the block:
+        # sx sx, sy sy, sz sz each (the Heisenberg term is their sum / 4)
+        bx = cfg["bx"]
+        c0 = bx // 2 - 1
+        ctr = [(c0 + i) * bx + c0 + j for i in range(2) for j in range(2)]
+        bonds = [(ctr[0], ctr[1]), (ctr[2], ctr[3]), (ctr[0], ctr[2]), (ctr[1], ctr[3])]
+        terms = [[(a, P), (b, P)] for a, b in bonds for P in (I.SIGMA_X, I.SIGMA_Y, I.SIGMA_Z)]
+        return cfg, terms
     terms = [[(s, I.SIGMA_Z)] for s in range(Lx * Ly)] + [[(s, I.SIGMA_X)] for s in range(Lx * Ly)]
     return cfg, terms
 
@@ -108,8 +117,6 @@ class Clocks:
 def make_lattice(B, cfg, prec, stream):
     dtype = {np.dtype(np.float64): B.F64, np.dtype(np.float32): B.F32, np.dtype(np.complex64): B.C64,
              np.dtype(np.complex128): B.C128}[np.asarray(cfg["tensors"][0]).dtype]
-    if prec != "fp64" and dtype in (B.C64, B.C128):
-        dtype = B.C128
     g = B.Lattice(Lx=cfg["Lx"], Ly=cfg["Ly"], d=cfg["d"], D=cfg["D"], bx=cfg["bx"], by=cfg["by"], chi=cfg["chi"],
                   boundary=cfg["boundary"], dtype=dtype, prec=prec, tol=cfg.get("tol", 1e-8), max_sweeps=50,
                   fit_tol=FIT_TOL[prec], fit_max_sweeps=10, seed=1, warm_start=WARM, stream=stream)

@@ -77,6 +77,23 @@ typedef struct {
     int warm_start;          /* 0: every zip-up fit starts from a random state (App. A);
                                 1: from the second sweep on, each fit starts from its own
                                 result of the previous sweep */
+    int hermitian_basis;     /* complex tensors only.  0: complex arithmetic on the FP64 path;
+                                1: Hermitian basis on the FP64 path too.  The TF32 / BF16
+                                paths always use it.  In the Hermitian basis every merged
+                                ket/bra leg of the double layer (Fig. 1(b)) is rotated by a
+                                fixed unitary V: a vector v indexed by (ket a, bra b) gets
+                                the coordinate v_(a,a) at k = a*D + a, (v_(a,b) + v_(b,a)) / sqrt 2
+                                at k = a*D + b for a < b and (v_(b,a) - v_(a,b)) / (i sqrt 2)
+                                at k = a*D + b for a > b, on up and left legs; down and right
+                                legs take conj(V) (the a > b coordinate changes sign), so
+                                that every bond contracts through V^T conj(V) = I.  The
+                                double layer of a Hermitian operator and the (Hermitian)
+                                messages are real there, so sweeps and read-out run in real
+                                arithmetic at a quarter of the complex flops; V is unitary,
+                                so overlaps, residuals and <O> are unchanged.
+                                bbp_get_message and bbp_set_message then use real messages
+                                in the basis of the legs they carry: V for messages sent
+                                left or up, conj(V) for messages sent right or down. */
     void* stream;            /* cudaStream_t for all work; NULL = library-owned stream */
 } bbp_lattice_desc;
 

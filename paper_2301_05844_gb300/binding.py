@@ -31,7 +31,8 @@ class Desc(C.Structure):
         ("bx", C.c_int), ("by", C.c_int), ("chi", C.c_int), ("chi_exp", C.c_int),
         ("dtype", C.c_int), ("prec", C.c_int), ("tol", C.c_double), ("max_sweeps", C.c_int),
         ("stop_relative", C.c_int), ("fit_tol", C.c_double), ("fit_max_sweeps", C.c_int),
-        ("seed", C.c_ulonglong), ("init_mode", C.c_int), ("warm_start", C.c_int), ("stream", C.c_void_p),
+        ("seed", C.c_ulonglong), ("init_mode", C.c_int), ("warm_start", C.c_int),
+        ("hermitian_basis", C.c_int), ("stream", C.c_void_p),
     ]
 
 
@@ -107,10 +108,10 @@ def _check(rc):
 
 def make_desc(Lx, Ly, d, D, bx, by, chi, boundary="obc", chi_exp=0, dtype=F64, prec="fp64", tol=1e-5,
               max_sweeps=10, stop_relative=0, fit_tol=1e-6, fit_max_sweeps=10, seed=0, init_mode=0, warm_start=0,
-              stream=None):
+              hermitian_basis=0, stream=None):
     return Desc(Lx, Ly, OBC if boundary == "obc" else INFINITE, d, D, bx, by, chi, chi_exp, dtype,
                 _PREC[prec] if isinstance(prec, str) else prec, tol, max_sweeps, stop_relative, fit_tol,
-                fit_max_sweeps, seed, init_mode, int(warm_start), stream)
+                fit_max_sweeps, seed, init_mode, int(warm_start), int(hermitian_basis), stream)
 
 
 def _term_array(terms):
@@ -248,7 +249,7 @@ class Lattice:
         _check(lib().bbp_get_message(self.h, block, direction, C.byref(ns), bonds, None))
         b = [bonds[i] for i in range(ns.value + 1)]
         K = self.desc.D ** 2
-        cplx = self.desc.dtype in (C128, C64)
+        cplx = self.complex_messages()
         total = sum(b[i] * K * b[i + 1] for i in range(ns.value)) * (2 if cplx else 1)
         buf = np.zeros(total)
         _check(lib().bbp_get_message(self.h, block, direction, None, None, buf.ctypes.data_as(C.POINTER(C.c_double))))
@@ -260,6 +261,12 @@ class Lattice:
             out.append(buf[o:o + n].reshape(b[i], K, b[i + 1]))
             o += n
         return out
+
+    def complex_messages(self):
+        """False when the lattice runs in real arithmetic (real tensors, or complex ones in
+        the Hermitian basis)."""
+        d = self.desc
+        return d.dtype in (C128, C64) and d.prec == PREC_FP64 and not d.hermitian_basis
 
     def stats(self):
         s = Stats()

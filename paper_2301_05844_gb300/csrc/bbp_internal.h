@@ -131,7 +131,7 @@ struct DLTask {
     void* E;         // [Du^2][Dl^2][Dd^2][Dr^2]
     const void* O;   // d x d row-major (nullptr: identity)
     int d, Du, Dl, Dd, Dr;
-    int pad;
+    int hb;          // 1: T and O complex, E real in the Hermitian basis (launch_double_layer_hb)
 };
 
 // Two neighbouring column operators of one row fused over their shared horizontal
@@ -164,6 +164,8 @@ cudaError_t launch_assemble(const AssembleTask* d_tasks, int ntasks, bool cplx, 
 cudaError_t launch_normalise(const NormTask* d_tasks, int ntasks, bool cplx, cudaStream_t s);
 cudaError_t launch_mean(const double* in, int n, double* out, cudaStream_t s);
 cudaError_t launch_double_layer(const DLTask* d_tasks, int ntasks, long long max_out, bool cplx, cudaStream_t s);
+// complex T and O (Hermitian), real E in the Hermitian basis of every merged leg
+cudaError_t launch_double_layer_hb(const DLTask* d_tasks, int ntasks, long long max_out, cudaStream_t s);
 cudaError_t launch_convert(const void* in, int in_dtype, void* out, long long n, bool cplx_out, cudaStream_t s);
 cudaError_t launch_copy(const void* in, void* out, long long bytes, cudaStream_t s);
 cudaError_t launch_fuse(const FuseTask* d_tasks, int ntasks, long long max_out, bool cplx, cudaStream_t s);

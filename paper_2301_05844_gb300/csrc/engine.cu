@@ -151,9 +151,10 @@ std::string Program::validate() const {
     for (size_t i = 0; i < dl.size(); ++i) {
         const DLTask& t = dl[i];
         const long long vol = (long long)t.Du * t.Dl * t.Dd * t.Dr;
-        c.range(t.T, t.d * vol, ss, "DL T", i);
+        const int ts = t.hb ? 16 : ss;  // complex T and O in the Hermitian basis
+        c.range(t.T, t.d * vol, ts, "DL T", i);
         c.range(t.E, vol * vol, ss, "DL E", i);
-        c.range(t.O, (long long)t.d * t.d, ss, "DL O", i);
+        c.range(t.O, (long long)t.d * t.d, ts, "DL O", i);
     }
     for (size_t i = 0; i < qr.size(); ++i) {
         const QRTask& t = qr[i];
@@ -671,7 +672,9 @@ cudaError_t Program::launch_step(const Step& s, cudaStream_t st, const int* swee
         case ST_COPY: return launch_copy(s.p0, s.p1, s.n, st);
         case ST_INC: return launch_add_int((int*)s.p0, 1, st);
         case ST_FUSE: return launch_fuse(d_fus + s.first, s.count, s.n, cplx, st);
-        case ST_DL: return launch_double_layer(d_dl + s.first, s.count, s.n, cplx, st);
+        case ST_DL:
+            return s.aux2 == 1 ? launch_double_layer_hb(d_dl + s.first, s.count, s.n, st)
+                               : launch_double_layer(d_dl + s.first, s.count, s.n, cplx, st);
         case ST_TC: return launch_tc_gemm(d_tcs + s.first, s.count, s.aux2 & 0xFF, s.aux, (int)s.n, s.aux2 >> 8, tc_err, st);
         case ST_REL: return launch_relayout(d_rel + s.first, s.count, s.n, st);
         case ST_LOOP_BEGIN: return launch_set_int((int*)s.p0, 1, 0, st);  // iteration counter = 0

@@ -611,6 +611,86 @@ cudaError_t launch_double_layer(const DLTask* d_tasks, int ntasks, long long max
     return cudaGetLastError();
 }
 
+// Double layer in the Hermitian basis: T and O complex (O Hermitian or NULL), E real.
+// Each merged leg index k = a*D + b is the V coordinate of the pair (a, b):
+// a == b -> v_(a,a); a < b -> (v_(a,b) + v_(b,a)) / sqrt 2; a > b -> (v_(b,a) - v_(a,b)) / (i sqrt 2),
+// on the up and left legs; the down and right legs take conj(V) (the a > b coordinate
+// changes sign).  Every bond joins a down (right) leg to an up (left) leg, and
+// V^T conj(V) = I, so contractions over bonds are unchanged (V^T V alone would swap ket
+// and bra).  E'[ku][kl][kd][kr] = Re sum over the (<= 2 per leg) pairs of the product of the
+// leg coefficients times E^O at those pairs; the imaginary part vanishes for Hermitian O.
+struct HbLeg {
+    int ket[2], bra[2];
+    double2 c[2];
+    int n;
+};
+__device__ __forceinline__ HbLeg hb_leg(int k, int D, bool conj_basis) {
+    HbLeg h;
+    const int a = k / D, b = k % D;
+    const double s = 0.70710678118654752440;
+    if (a == b) {
+        h.n = 1;
+        h.ket[0] = a; h.bra[0] = a; h.c[0] = make_double2(1.0, 0.0);
+    } else if (a < b) {
+        h.n = 2;
+        h.ket[0] = a; h.bra[0] = b; h.c[0] = make_double2(s, 0.0);
+        h.ket[1] = b; h.bra[1] = a; h.c[1] = make_double2(s, 0.0);
+    } else {
+        h.n = 2;  // V: 1/(i sqrt 2) = -i/sqrt 2 on v_(b,a), +i/sqrt 2 on v_(a,b); conj(V): opposite
+        const double sg = conj_basis ? -1.0 : 1.0;
+        h.ket[0] = b; h.bra[0] = a; h.c[0] = make_double2(0.0, -s * sg);
+        h.ket[1] = a; h.bra[1] = b; h.c[1] = make_double2(0.0, s * sg);
+    }
+    return h;
+}
+__global__ void k_double_layer_hb(const DLTask* __restrict__ tasks) {
+    const DLTask& t = tasks[blockIdx.y];
+    const int Ku = t.Du * t.Du, Kl = t.Dl * t.Dl, Kd = t.Dd * t.Dd, Kr = t.Dr * t.Dr;
+    const long long total = (long long)Ku * Kl * Kd * Kr;
+    const long long vol = (long long)t.Du * t.Dl * t.Dd * t.Dr;
+    const double2* T = (const double2*)t.T;
+    const double2* O = (const double2*)t.O;
+    double* E = (double*)t.E;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+        long long r = e;
+        const int ir = (int)(r % Kr); r /= Kr;
+        const int id = (int)(r % Kd); r /= Kd;
+        const int il = (int)(r % Kl); r /= Kl;
+        const int iu = (int)r;
+        const HbLeg hu = hb_leg(iu, t.Du, false), hl = hb_leg(il, t.Dl, false);
+        const HbLeg hd = hb_leg(id, t.Dd, true), hr = hb_leg(ir, t.Dr, true);
+        double2 acc = make_double2(0.0, 0.0);
+        for (int a = 0; a < hu.n; ++a)
+            for (int b = 0; b < hl.n; ++b)
+                for (int c = 0; c < hd.n; ++c)
+                    for (int f = 0; f < hr.n; ++f) {
+                        const long long ket = (((long long)hu.ket[a] * t.Dl + hl.ket[b]) * t.Dd + hd.ket[c]) * t.Dr + hr.ket[f];
+                        const long long bra = (((long long)hu.bra[a] * t.Dl + hl.bra[b]) * t.Dd + hd.bra[c]) * t.Dr + hr.bra[f];
+                        double2 v = make_double2(0.0, 0.0);
+                        for (int pp = 0; pp < t.d; ++pp) {
+                            double2 ot = make_double2(0.0, 0.0);
+                            if (O) {
+                                for (int p = 0; p < t.d; ++p) mac(ot, O[pp * t.d + p], T[p * vol + ket]);
+                            } else {
+                                ot = T[pp * vol + ket];
+                            }
+                            mac(v, ot, conjv(T[pp * vol + bra]));
+                        }
+                        const double2 cf = mul(mul(hu.c[a], hl.c[b]), mul(hd.c[c], hr.c[f]));
+                        mac(acc, cf, v);
+                    }
+        E[e] = acc.x;
+    }
+}
+cudaError_t launch_double_layer_hb(const DLTask* d_tasks, int ntasks, long long max_out, cudaStream_t s) {
+    if (ntasks <= 0) return cudaSuccess;
+    long long bx = (max_out + 255) / 256;
+    if (bx > 4096) bx = 4096;
+    dim3 grid((unsigned)bx, ntasks);
+    k_double_layer_hb<<<grid, 256, 0, s>>>(d_tasks);
+    return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------- dtype conversion
 // in_dtype: 0 f64, 1 c128, 2 f32, 3 c64 (the bbp_dtype values).  n = scalar count.
 __global__ void k_convert(const void* in, int in_dtype, void* out, long long n, int cplx_out) {

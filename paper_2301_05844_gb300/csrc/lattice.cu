@@ -541,8 +541,7 @@ static int validate(const bbp_lattice_desc* d) {
         return fail(BBP_ERR_INVALID, "infinite block must be a multiple of the unit cell");
     if (d->dtype < 0 || d->dtype > 3) return fail(BBP_ERR_INVALID, "unknown dtype");
     if (d->prec < 0 || d->prec > 2) return fail(BBP_ERR_INVALID, "unknown precision");
-    if (d->prec != BBP_PREC_FP64 && (d->dtype == BBP_C128 || d->dtype == BBP_C64))
-        return fail(BBP_ERR_INVALID, "complex tensors run on the FP64 path in this build");
+    if (d->hermitian_basis != 0 && d->hermitian_basis != 1) return fail(BBP_ERR_INVALID, "hermitian_basis must be 0 or 1");
     if (d->fit_max_sweeps < 1 || d->fit_max_sweeps > 64) return fail(BBP_ERR_INVALID, "fit_max_sweeps must be 1..64");
     if (d->bx > 16 || d->by > 16) return fail(BBP_ERR_INVALID, "block sides are limited to 16 sites");
     if (d->D > 16 || d->d > 64) return fail(BBP_ERR_INVALID, "D or d too large");
@@ -562,7 +561,9 @@ int bbp::plan_lattice(const bbp_lattice_desc* desc, bbp_lattice** out) {
     if (!L) return fail(BBP_ERR_OOM, "host allocation failed");
     L->desc = *desc;
     if (L->desc.chi_exp <= 0) L->desc.chi_exp = std::max(desc->chi, 2 * desc->D * desc->D + 10);
-    L->cplx = desc->dtype == BBP_C128 || desc->dtype == BBP_C64;
+    const bool in_cplx = desc->dtype == BBP_C128 || desc->dtype == BBP_C64;
+    L->hb = in_cplx && (desc->prec != BBP_PREC_FP64 || desc->hermitian_basis != 0);
+    L->cplx = in_cplx && !L->hb;
     L->ss = L->cplx ? 16 : 8;
     L->K = desc->D * desc->D;
     if (desc->boundary == BBP_OBC) {
@@ -581,7 +582,7 @@ int bbp::plan_lattice(const bbp_lattice_desc* desc, bbp_lattice** out) {
             const auto dd = L->site_dims(r, c);
             L->tdims.push_back(dd);
             const size_t vol = (size_t)desc->d * dd[0] * dd[1] * dd[2] * dd[3];
-            L->T_off.push_back(elem_alloc(vol));
+            L->T_off.push_back(elem_alloc(vol * (L->hb ? 2 : 1)));  // T stays complex in the Hermitian basis
             L->E_off.push_back(elem_alloc((size_t)dd[0] * dd[0] * dd[1] * dd[1] * dd[2] * dd[2] * dd[3] * dd[3]));
             raw_scalars += vol;
         }
@@ -776,6 +777,16 @@ static void init_messages(bbp_lattice* L, std::vector<double>& host) {
                         for (int k = 0; k < D; ++k) acc += g[a * D + k] * g[b * D + k];
                         v[a * D + b] = acc;
                     }
+                if (L->hb) {
+                    // G G^T is real symmetric: Hermitian-basis coordinates (v_ab + v_ba)/sqrt 2
+                    // for a < b, 0 for a > b, v_aa on the diagonal
+                    std::vector<double> w(v);
+                    for (int a = 0; a < D; ++a)
+                        for (int b = 0; b < D; ++b)
+                            if (a < b) w[a * D + b] = (v[a * D + b] + v[b * D + a]) / std::sqrt(2.0);
+                            else if (a > b) w[a * D + b] = 0.0;
+                    v = w;
+                }
             }
             double n2 = 0;
             for (double x : v) n2 += x * x;
@@ -808,7 +819,8 @@ int bbp_set_tensors(bbp_lattice* L, const void* data, int on_device) {
     for (int t = 0; t < L->ntens; ++t) {
         const auto& dd = L->tdims[t];
         const long long vol = (long long)L->desc.d * dd[0] * dd[1] * dd[2] * dd[3];
-        CKR(launch_convert(base + L->raw_off + in_scalar * in_ss, L->desc.dtype, base + L->T_off[t] * L->ss, vol, L->cplx, st));
+        CKR(launch_convert(base + L->raw_off + in_scalar * in_ss, L->desc.dtype, base + L->T_off[t] * L->ss, vol,
+                           L->cplx || L->hb, st));
         in_scalar += vol;
         DLTask k{};
         k.T = base + L->T_off[t] * L->ss;
@@ -816,13 +828,17 @@ int bbp_set_tensors(bbp_lattice* L, const void* data, int on_device) {
         k.O = nullptr;
         k.d = L->desc.d;
         k.Du = dd[0]; k.Dl = dd[1]; k.Dd = dd[2]; k.Dr = dd[3];
+        k.hb = L->hb ? 1 : 0;
         dl.push_back(k);
         maxout = std::max(maxout, (long long)dd[0] * dd[0] * dd[1] * dd[1] * dd[2] * dd[2] * dd[3] * dd[3]);
     }
     DLTask* d_dl = nullptr;
     CKR(cudaMallocAsync((void**)&d_dl, dl.size() * sizeof(DLTask), st));
     CKR(cudaMemcpyAsync(d_dl, dl.data(), dl.size() * sizeof(DLTask), cudaMemcpyHostToDevice, st));
-    CKR(launch_double_layer(d_dl, (int)dl.size(), maxout, L->cplx, st));
+    if (L->hb)
+        CKR(launch_double_layer_hb(d_dl, (int)dl.size(), maxout, st));
+    else
+        CKR(launch_double_layer(d_dl, (int)dl.size(), maxout, L->cplx, st));
     CKR(cudaFreeAsync(d_dl, st));
     if (L->mixed) {
         // low-precision operand layouts of every double-layer tensor in every frame

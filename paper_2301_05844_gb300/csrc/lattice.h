@@ -58,7 +58,8 @@ int plan_column_sweeps(bbp_lattice* L, Program& pr, std::vector<ColumnSweep>& cs
 
 struct bbp_lattice {
     bbp_lattice_desc desc{};
-    bool cplx = false;
+    bool cplx = false;  // complex arithmetic (complex tensors on the FP64 path)
+    bool hb = false;    // complex tensors in the Hermitian basis: real arithmetic, complex T
     int ss = 8;  // scalar bytes
     int K = 1;
     int nbx = 1, nby = 1, nblocks = 1;

@@ -189,6 +189,25 @@ extern "C" int bbp_expect(bbp_lattice* L, const bbp_term* terms, int n_terms, do
                     z[2 * j + 1] = im[j];
                 }
                 parts[k].push_back({z, 1.0});
+            } else if (L->hb) {
+                // Hermitian basis: O = H + i A with H = (O + O^dagger)/2 and
+                // A = (O - O^dagger)/(2i) both Hermitian, so that each E^H, E^A is real there;
+                // uploaded as complex d x d matrices for the double-layer kernel
+                std::vector<double> h(2 * d * d), a(2 * d * d);
+                bool has_h = false, has_a = false;
+                for (int r = 0; r < d; ++r)
+                    for (int c = 0; c < d; ++c) {
+                        const int j = r * d + c, jt = c * d + r;
+                        const double zr = re[j] - re[jt], zi = im[j] + im[jt];  // O_rc - conj(O_cr)
+                        h[2 * j] = 0.5 * (re[j] + re[jt]);
+                        h[2 * j + 1] = 0.5 * (im[j] - im[jt]);
+                        a[2 * j] = 0.5 * zi;
+                        a[2 * j + 1] = -0.5 * zr;
+                        has_h |= h[2 * j] != 0.0 || h[2 * j + 1] != 0.0;
+                        has_a |= a[2 * j] != 0.0 || a[2 * j + 1] != 0.0;
+                    }
+                if (has_h || !has_a) parts[k].push_back({h, 1.0});
+                if (has_a) parts[k].push_back({a, std::complex<double>(0.0, 1.0)});
             } else {
                 bool has_re = false, has_im = false;
                 for (int j = 0; j < d * d; ++j) {
@@ -312,7 +331,8 @@ extern "C" int bbp_expect(bbp_lattice* L, const bbp_term* terms, int n_terms, do
         ln.G1 = elem_alloc(g1max); ln.G2 = elem_alloc(g2max);
         ln.EO[0] = elem_alloc(K4max); ln.EO[1] = elem_alloc(K4max);
         ln.O12 = elem_alloc(o12max);
-        ln.op[0] = elem_alloc((size_t)d * d); ln.op[1] = elem_alloc((size_t)d * d);
+        const size_t opn = (size_t)d * d * (L->hb ? 2 : 1);  // complex operators in the Hermitian basis
+        ln.op[0] = elem_alloc(opn); ln.op[1] = elem_alloc(opn);
     }
     // operator uploads recorded as (elem offset, values)
     std::vector<std::pair<size_t, std::vector<double>>> uploads;
@@ -334,6 +354,7 @@ extern "C" int bbp_expect(bbp_lattice* L, const bbp_term* terms, int n_terms, do
                 t.E = P(ln.EO[k] * ss);
                 t.O = P(ln.op[k] * ss);
                 t.d = d; t.Du = dd[0]; t.Dl = dd[1]; t.Dd = dd[2]; t.Dr = dd[3];
+                t.hb = L->hb ? 1 : 0;
                 dts.push_back(t);
                 dlmax = std::max(dlmax, (long long)dd[0] * dd[0] * dd[1] * dd[1] * dd[2] * dd[2] * dd[3] * dd[3]);
             }
@@ -344,6 +365,7 @@ extern "C" int bbp_expect(bbp_lattice* L, const bbp_term* terms, int n_terms, do
             s.first = pr.dl.size();
             s.count = (int)dts.size();
             s.n = dlmax;
+            s.aux2 = L->hb ? 1 : 0;
             pr.dl.insert(pr.dl.end(), dts.begin(), dts.end());
             pr.steps.push_back(s);
         }

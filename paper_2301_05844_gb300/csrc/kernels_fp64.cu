@@ -4,6 +4,7 @@
 // so one launch advances every message of the sweep by one step.  They form the
 // plain FP64 GPU path (every contraction, QR/LQ and reduction in FP64) and supply
 // the FP64 truncation / normalisation stages of the mixed-precision path.
+#include <cooperative_groups.h>
 #include <cuda_bf16.h>
 #include <math.h>
 
@@ -350,6 +351,162 @@ __global__ void __launch_bounds__(256) k_qr(const QRTask* __restrict__ tasks, in
 
 constexpr size_t QR_SMEM_LIMIT = 200 * 1024;
 
+// The same QR with one task spread over a thread-block cluster of C CTAs (C <= 8), for
+// launches with too few tasks to fill the SMs: column j belongs to CTA j % C, which keeps
+// its columns of W and Q in shared memory.  Per column j the owner forms the reflector
+// (scaled form, as above) in place in its column of W, the cluster synchronises, and every
+// CTA reads v_j and tau_j from the owner's shared memory (distributed shared memory) to
+// update its own columns k > j.  Q is then accumulated backwards column-locally, each CTA
+// reading every v_j from its owner; no CTA leaves before the others have finished reading.
+// Shared memory per CTA: u (m) | W (m x nl) | Q (m x nl) | tau (n) | beta (n) | partial norm.
+template <typename S>
+__global__ void __launch_bounds__(256) k_qr_cluster(const QRTask* __restrict__ tasks, int C) {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cluster = cg::this_cluster();
+    const int rank = (int)cluster.block_rank();
+    const QRTask& t = tasks[blockIdx.x / C];
+    if (t.active && *t.active == 0) return;  // uniform over the cluster
+    const int m = t.m, n = t.n, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nl = (n - rank + C - 1) / C;   // local columns j = rank + lc * C
+    const int nlmax = (n + C - 1) / C;       // same layout in every CTA of the cluster
+    extern __shared__ __align__(16) unsigned char qr_smem[];
+    S* u = (S*)qr_smem;
+    S* W = u + m;
+    S* Q = W + (size_t)m * nlmax;
+    double* taus = (double*)(Q + (size_t)m * nlmax);
+    S* betas = (S*)(taus + QR_MAXN);
+    double* part = (double*)(betas + QR_MAXN);
+    __shared__ double redd[32];
+    const S* in = (const S*)t.in;
+    double ss = 0.0;
+    for (long long idx = tid; idx < (long long)m * nl; idx += 256) {
+        const int i = (int)(idx % m), lc = (int)(idx / m), j = rank + lc * C;
+        const long long src = (long long)i * t.in_rs + (long long)j * t.in_cs;
+        S v;
+        if (t.in_float) v = from_float<S>(((const float*)t.in), src);
+        else v = in[src];
+        if (t.conj_io) v = conjv(v);
+        W[(size_t)lc * m + i] = v;
+        ss += abs2(v);
+    }
+    ss = block_sum(ss, redd);
+    if (tid == 0) part[0] = ss;
+    cluster.sync();
+    if (rank == 0 && tid == 0 && t.loss) {
+        double tot = 0.0;
+        for (int r = 0; r < C; ++r) tot += *cluster.map_shared_rank(part, r);
+        *t.loss = -tot;
+    }
+    for (int j = 0; j < n; ++j) {
+        const int owner = j % C, lj = j / C;
+        if (rank == owner) {
+            S* col = W + (size_t)lj * m;
+            double xs2 = 0.0;
+            for (int i = j + 1 + tid; i < m; i += 256) xs2 += abs2(col[i]);
+            xs2 = block_sum(xs2, redd);
+            double xnorm = sqrt(xs2);
+            if (xs2 < 1e-280) {
+                double amax = 0.0;
+                for (int i = j + 1 + tid; i < m; i += 256) amax = fmax(amax, absv(col[i]));
+                amax = block_max(amax, redd);
+                double t2 = 0.0;
+                if (amax > 0.0)
+                    for (int i = j + 1 + tid; i < m; i += 256) t2 += abs2(divr(col[i], amax));
+                t2 = block_sum(t2, redd);
+                xnorm = amax > 0.0 ? amax * sqrt(t2) : 0.0;
+            }
+            const S alpha = col[j];
+            const double aa = absv(alpha);
+            __syncthreads();  // every thread has read alpha before column j is overwritten
+            S beta = alpha;
+            double tau = 0.0;
+            if (xnorm > 0.0) {
+                const double nrm = hypot(aa, xnorm);
+                const S ph = aa > 0.0 ? divr(alpha, aa) : one<S>();
+                beta = scal(ph, -nrm);
+                tau = 1.0 + aa / nrm;
+                const double den = aa + nrm;
+                const S cph = conjv(ph);
+                for (int i = j + tid; i < m; i += 256) col[i] = (i == j) ? one<S>() : divr(mul(col[i], cph), den);
+            }
+            if (tid == 0) {
+                taus[j] = tau;
+                betas[j] = beta;
+            }
+        }
+        cluster.sync();  // v_j and tau_j published by the owner
+        const double tau = *cluster.map_shared_rank(taus + j, owner);
+        const int lk0 = (j + 1 - rank + C - 1) / C;  // first local column with k > j
+        if (tau != 0.0 && lk0 < nl) {
+            const S* vj = cluster.map_shared_rank(W + (size_t)lj * m, owner);
+            for (int i = j + tid; i < m; i += 256) u[i] = vj[i];
+            __syncthreads();
+            for (int lk = lk0 + warp; lk < nl; lk += 8) {
+                S* ck = W + (size_t)lk * m;
+                S dot = zero<S>();
+                for (int i = j + lane; i < m; i += 32) mac(dot, conjv(u[i]), ck[i]);
+                dot = warp_sum(dot);
+                const S f = scal(dot, -tau);
+                for (int i = j + lane; i < m; i += 32) mac(ck[i], u[i], f);
+            }
+            __syncthreads();
+        }
+    }
+    cluster.sync();  // every reflector is final
+    for (long long idx = tid; idx < (long long)m * nl; idx += 256) {
+        const int i = (int)(idx % m), lc = (int)(idx / m), k = rank + lc * C;
+        Q[(size_t)lc * m + i] = (i == k) ? one<S>() : zero<S>();
+    }
+    __syncthreads();
+    for (int j = n - 1; j >= 0; --j) {
+        const int owner = j % C, lj = j / C;
+        const double tau = *cluster.map_shared_rank(taus + j, owner);
+        const int lk0 = (j - rank + C - 1) / C;  // first local column with k >= j
+        if (tau == 0.0 || lk0 >= nl) continue;  // uniform within the CTA
+        const S* vj = cluster.map_shared_rank(W + (size_t)lj * m, owner);
+        for (int i = j + tid; i < m; i += 256) u[i] = vj[i];
+        __syncthreads();
+        for (int lk = lk0 + warp; lk < nl; lk += 8) {
+            S* qk = Q + (size_t)lk * m;
+            S dot = zero<S>();
+            for (int i = j + lane; i < m; i += 32) mac(dot, conjv(u[i]), qk[i]);
+            dot = warp_sum(dot);
+            const S f = scal(dot, -tau);
+            for (int i = j + lane; i < m; i += 32) mac(qk[i], u[i], f);
+        }
+        __syncthreads();
+    }
+    S* out = (S*)t.out;
+    for (long long idx = tid; idx < (long long)m * nl; idx += 256) {
+        const int i = (int)(idx % m), lc = (int)(idx / m), k = rank + lc * C;
+        const double bb = absv(betas[k]);  // column k is local: its beta is in this CTA
+        const S ph = bb > 0.0 ? divr(betas[k], bb) : one<S>();
+        S v = mul(Q[(size_t)lc * m + i], ph);
+        if (t.conj_io) v = conjv(v);
+        out[(long long)i * t.out_rs + (long long)k * t.out_cs] = v;
+        if (t.out2) store_kind(t.out2, (long long)i * t.out2_rs + (long long)k * t.out2_cs, t.out2_kind, v);
+    }
+    cluster.sync();  // no CTA leaves while another may still read its shared memory
+}
+
+constexpr size_t QR_CLUSTER_SMEM = QR_SMEM_LIMIT + QR_MAXN * (8 + 16) + 16;
+
+static int sm_count() {
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) n = 1;
+    }
+    return n;
+}
+
+static size_t qr_cluster_smem(int max_m, long long max_mn, int C, size_t ss) {
+    // m * ceil(n / C) <= m * n / C + m
+    const size_t cols = (size_t)(max_mn / C) + (size_t)max_m;
+    return ((size_t)max_m + 2 * cols) * ss + QR_MAXN * (8 + ss) + 16;
+}
+
 static size_t qr_smem_bytes(int max_m, long long max_mn, bool cplx, int* resident) {
     const size_t ss = cplx ? sizeof(double2) : sizeof(double);
     const size_t all = ((size_t)max_m + 2 * (size_t)max_mn) * ss;
@@ -361,6 +518,15 @@ cudaError_t qr_prepare(int max_m, bool cplx) {
     // the limit only ever grows, so that a smaller request cannot break a larger user;
     // it covers the shared-memory-resident form up to QR_SMEM_LIMIT as well
     static size_t limit[2] = {0, 0};
+    static bool cluster_set[2] = {false, false};
+    if (!cluster_set[cplx ? 1 : 0]) {
+        cudaError_t e = cplx ? cudaFuncSetAttribute(k_qr_cluster<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                    (int)QR_CLUSTER_SMEM)
+                             : cudaFuncSetAttribute(k_qr_cluster<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                    (int)QR_CLUSTER_SMEM);
+        if (e != cudaSuccess) return e;
+        cluster_set[cplx ? 1 : 0] = true;
+    }
     const size_t ss = cplx ? sizeof(double2) : sizeof(double);
     const size_t sm = std::max((size_t)max_m * ss, QR_SMEM_LIMIT);
     if (sm <= limit[cplx ? 1 : 0]) return cudaSuccess;
@@ -372,6 +538,26 @@ cudaError_t qr_prepare(int max_m, bool cplx) {
 
 cudaError_t launch_qr(const QRTask* d_tasks, int ntasks, int max_m, long long max_mn, bool cplx, cudaStream_t s) {
     if (ntasks <= 0) return cudaSuccess;
+    // few tasks: spread each over a cluster so that the launch covers the SMs
+    const size_t ssz = cplx ? sizeof(double2) : sizeof(double);
+    const int C = std::min(8, std::max(1, sm_count() / ntasks));
+    if (C > 1 && max_mn / max_m >= 2 * C && qr_cluster_smem(max_m, max_mn, C, ssz) <= QR_CLUSTER_SMEM) {
+        const size_t sm = qr_cluster_smem(max_m, max_mn, C, ssz);
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = C;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.gridDim = dim3(C * ntasks);
+        cfg.blockDim = dim3(256);
+        cfg.dynamicSmemBytes = sm;
+        cfg.stream = s;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        return cplx ? cudaLaunchKernelEx(&cfg, k_qr_cluster<double2>, d_tasks, C)
+                    : cudaLaunchKernelEx(&cfg, k_qr_cluster<double>, d_tasks, C);
+    }
     int resident = 0;
     const size_t sm = qr_smem_bytes(max_m, max_mn, cplx, &resident);
     if (cplx)

@@ -44,10 +44,11 @@ struct QRTask {
     long long in_rs, in_cs, out_rs, out_cs;
     int conj_io;
     int in_float;    // 1: input is FP32 (mixed path), 0: the FP64 scalar type
-    void* out2;      // optional second copy of Q in a low-precision operand layout
-    long long out2_rs, out2_cs;
+    void* out2;      // optional second copy of Q in a low-precision operand layout:
+                     // element (i, k) at (i / out2_M2) * out2_rs + (i % out2_M2) * out2_rs2 + k * out2_cs
+    long long out2_rs, out2_cs, out2_rs2;
     int out2_kind;   // element kind of out2 (see RelayoutTask)
-    int pad;
+    int out2_M2;     // >= 1
 };
 
 // Strided copy with type conversion over a 4-D index space (dims d0 x d1 x d2 x d3):

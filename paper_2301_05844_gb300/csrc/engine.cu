@@ -109,6 +109,12 @@ std::string Program::validate() const {
         c.range(t.in, ext2(t.m, t.in_rs, t.n, t.in_cs) + 1, t.in_float ? ss / 2 : ss, "QR in", i);
         c.range(t.out, ext2(t.m, t.out_rs, t.n, t.out_cs) + 1, ss, "QR out", i);
         c.range(t.work, 2LL * t.m * t.n, ss, "QR work", i);
+        if (t.out2) {
+            const int M2 = t.out2_M2 > 1 ? t.out2_M2 : 1;
+            const long long ext = (long long)((t.m - 1) / M2) * t.out2_rs + (long long)(std::min(M2, t.m) - 1) * t.out2_rs2 +
+                                  (long long)(t.n - 1) * t.out2_cs + 1;
+            c.range(t.out2, ext, t.out2_kind == 0 ? 8 : t.out2_kind == 3 ? 2 : 4, "QR out2", i);
+        }
         c.range(t.loss, 1, 8, "QR loss", i);
         c.range(t.active, 1, 4, "QR active", i);
     }

@@ -345,7 +345,11 @@ __global__ void __launch_bounds__(256) k_qr(const QRTask* __restrict__ tasks, in
         S v = mul(Q[(size_t)k * m + i], ph);
         if (t.conj_io) v = conjv(v);
         out[(long long)i * t.out_rs + (long long)k * t.out_cs] = v;
-        if (t.out2) store_kind(t.out2, (long long)i * t.out2_rs + (long long)k * t.out2_cs, t.out2_kind, v);
+        if (t.out2) {
+            const int M2 = t.out2_M2 > 1 ? t.out2_M2 : 1, i1 = i / M2;
+            store_kind(t.out2, (long long)i1 * t.out2_rs + (long long)(i - i1 * M2) * t.out2_rs2 + (long long)k * t.out2_cs,
+                       t.out2_kind, v);
+        }
     }
 }
 
@@ -484,7 +488,11 @@ __global__ void __launch_bounds__(256) k_qr_cluster(const QRTask* __restrict__ t
         S v = mul(Q[(size_t)lc * m + i], ph);
         if (t.conj_io) v = conjv(v);
         out[(long long)i * t.out_rs + (long long)k * t.out_cs] = v;
-        if (t.out2) store_kind(t.out2, (long long)i * t.out2_rs + (long long)k * t.out2_cs, t.out2_kind, v);
+        if (t.out2) {
+            const int M2 = t.out2_M2 > 1 ? t.out2_M2 : 1, i1 = i / M2;
+            store_kind(t.out2, (long long)i1 * t.out2_rs + (long long)(i - i1 * M2) * t.out2_rs2 + (long long)k * t.out2_cs,
+                       t.out2_kind, v);
+        }
     }
     cluster.sync();  // no CTA leaves while another may still read its shared memory
 }

@@ -370,10 +370,10 @@ int plan_column_sweeps(bbp_lattice* L, Program& pr, std::vector<ColumnSweep>& cs
             r.dst = P(dst);
             r.src_kind = 0;
             r.dst_kind = cx.lpk;
-            if (order == 0) {  // OL[q][w2][pad(w p)]
-                r.d[0] = o.q; r.d[1] = o.w2; r.d[2] = o.w; r.d[3] = o.p;
-                r.ss[0] = o.sq; r.ss[1] = o.sw2; r.ss[2] = o.sw; r.ss[3] = o.sp;
-                r.ds[0] = (long long)o.w2 * pad((long long)o.w * o.p); r.ds[1] = pad((long long)o.w * o.p); r.ds[2] = o.p; r.ds[3] = 1;
+            if (order == 0) {  // OL[w2][q][pad(w p)]
+                r.d[0] = o.w2; r.d[1] = o.q; r.d[2] = o.w; r.d[3] = o.p;
+                r.ss[0] = o.sw2; r.ss[1] = o.sq; r.ss[2] = o.sw; r.ss[3] = o.sp;
+                r.ds[0] = (long long)o.q * pad((long long)o.w * o.p); r.ds[1] = pad((long long)o.w * o.p); r.ds[2] = o.p; r.ds[3] = 1;
             } else {  // OR[w][q][pad(p w2)]
                 r.d[0] = o.w; r.d[1] = o.q; r.d[2] = o.p; r.d[3] = o.w2;
                 r.ss[0] = o.sw; r.ss[1] = o.sq; r.ss[2] = o.sp; r.ss[3] = o.sw2;
@@ -854,11 +854,11 @@ int bbp_set_tensors(bbp_lattice* L, const void* data, int on_device) {
                     r.src_kind = 0;
                     r.dst_kind = cx.lpk;
                     if (order == 0) {
-                        r.dst = base + L->EL_off[t][dir];
+                        r.dst = base + L->EL_off[t][dir];  // OL[w2][q][pad(w p)]
                         const long long wp = padded(cx, (long long)o.w * o.p);
-                        r.d[0] = o.q; r.d[1] = o.w2; r.d[2] = o.w; r.d[3] = o.p;
-                        r.ss[0] = o.sq; r.ss[1] = o.sw2; r.ss[2] = o.sw; r.ss[3] = o.sp;
-                        r.ds[0] = (long long)o.w2 * wp; r.ds[1] = wp; r.ds[2] = o.p; r.ds[3] = 1;
+                        r.d[0] = o.w2; r.d[1] = o.q; r.d[2] = o.w; r.d[3] = o.p;
+                        r.ss[0] = o.sw2; r.ss[1] = o.sq; r.ss[2] = o.sw; r.ss[3] = o.sp;
+                        r.ds[0] = (long long)o.q * wp; r.ds[1] = wp; r.ds[2] = o.p; r.ds[3] = 1;
                     } else {
                         r.dst = base + L->ER_off[t][dir];
                         const long long pw = padded(cx, (long long)o.p * o.w2);

@@ -5,11 +5,14 @@
 //
 // Operand layouts (low precision, every row padded to 16 bytes):
 //   X   : XL[x2][p][pad x]        XR[x][p][pad x2]
-//   O   : OL[q][w2][pad(w p)]     OR[w][q][pad(p w2)]
+//   O   : OL[w2][q][pad(w p)]     OR[w][q][pad(p w2)]
 //   env : ER[y][w][pad x]         EK[y][pad(w x)]      (A and B envs, both forms)
-//   Y   : YS[y][pad(q y2)]        YT[y2][pad(y q)]
+//   Y   : YS[y][pad(y2 q)]        YT[y2][pad(y q)]
 //   L->R: T1[y][x2][pad(w p)]  T2a[y][q][pad(w2 x2)]  T2b[w2][x2][pad(y q)]
-//   R->L: T1[y2][x][pad(p w2)] T2a[q][y2][pad(w x)]   T2b[w][x][pad(q y2)]
+//   R->L: T1[y2][x][pad(p w2)] T2a[q][y2][pad(w x)]   T2b[w][x][pad(y2 q)]
+// Row orders are chosen so that every destination of a GEMM is contiguous either
+// along its columns (n2 stride 1) or along its rows (m2 stride 1), which the epilogue
+// writes with vector stores.
 // The site update is K2 (A X), K3 (T1 O), K4 (T2 B) in either direction, the env
 // update K5 (conj(Y) T2); each GEMM's epilogue scatters its result straight into the
 // layout(s) its consumers read, so no transpose kernel runs between them.
@@ -119,11 +122,11 @@ void lr(Program& pr, const MixCtx& cx, TB& tb, const FitSpec& f, int i, int stag
         const long long WP = padded(cx, d.w * d.p);
         add(pr, tb, m.AR[i], d.y * d.w, d.x, padded(cx, d.x), m.XL[i], d.x2 * d.p, padded(cx, d.x), (int)d.w, (int)d.p,
             P(m.T1), d.x2 * WP, d.p, WP, 1, nullptr, 0, 0, 0, 0, lo, act, 2.0 * d.y * d.w * d.x * d.p * d.x2);
-    } else if (stage == 1) {  // T2 = T1[(y,x2)][(w p)] OL[(q,w2)][(w p)]
+    } else if (stage == 1) {  // T2 = T1[(y,x2)][(w p)] OL[(w2,q)][(w p)]
         const long long WP = padded(cx, d.w * d.p), WX2 = padded(cx, d.w2 * d.x2), YQ = padded(cx, d.y * d.q);
-        add(pr, tb, m.T1, d.y * d.x2, d.w * d.p, WP, m.OL[i], d.q * d.w2, WP, (int)d.x2, (int)d.w2,
-            P(m.T2a), d.q * WX2, 1, WX2, d.x2,                 // T2a[y][q][pad(w2 x2)]
-            P(m.T2b), d.q, YQ, 1, d.x2 * YQ,                    // T2b[w2][x2][pad(y q)]
+        add(pr, tb, m.T1, d.y * d.x2, d.w * d.p, WP, m.OL[i], d.w2 * d.q, WP, (int)d.x2, (int)d.q,
+            P(m.T2a), d.q * WX2, 1, d.x2, WX2,                 // T2a[y][q][pad(w2 x2)]
+            P(m.T2b), d.q, YQ, d.x2 * YQ, 1,                    // T2b[w2][x2][pad(y q)]
             lo, act, 2.0 * d.y * d.x2 * d.w * d.p * d.q * d.w2);
     } else if (stage == 2) {  // Yt[y][q][y2] = T2a[(y,q)][(w2 x2)] EK_B[y2][(w2 x2)]  (FP32)
         const long long WX2 = padded(cx, d.w2 * d.x2);
@@ -152,7 +155,7 @@ void rl(Program& pr, const MixCtx& cx, TB& tb, const FitSpec& f, int i, int stag
         const long long PW = padded(cx, d.p * d.w2), WX = padded(cx, d.w * d.x), QY2 = padded(cx, d.q * d.y2);
         add(pr, tb, m.T1, d.y2 * d.x, d.p * d.w2, PW, m.OR[i], d.w * d.q, PW, (int)d.x, (int)d.q,
             P(m.T2a), WX, 1, d.x, d.y2 * WX,                    // T2a[q][y2][pad(w x)]
-            P(m.T2b), 1, QY2, d.x * QY2, d.y2,                  // T2b[w][x][pad(q y2)]
+            P(m.T2b), d.q, QY2, d.x * QY2, 1,                   // T2b[w][x][pad(y2 q)]
             lo, act, 2.0 * d.x * d.y2 * d.p * d.w2 * d.w * d.q);
     } else if (stage == 2) {  // Yt[y][q][y2] = EK_A[y][(w x)] T2a[(q,y2)][(w x)]
         const long long WX = padded(cx, d.w * d.x);
@@ -163,7 +166,7 @@ void rl(Program& pr, const MixCtx& cx, TB& tb, const FitSpec& f, int i, int stag
         else
             add(pr, tb, m.AK[i], d.y, d.w * d.x, WX, m.T2a, d.q * d.y2, WX, (int)d.y, (int)d.y2,
                 P(m.Ytf), 0, d.q * d.y2, d.y2, 1, nullptr, 0, 0, 0, 0, 0, act, 2.0 * d.y * d.w * d.x * d.q * d.y2);
-    } else {  // B_i = YS[y][(q y2)] T2b[(w,x)][(q y2)] in both env forms
+    } else {  // B_i = YS[y][(y2 q)] T2b[(w,x)][(y2 q)] in both env forms
         const long long QY2 = padded(cx, d.q * d.y2), X = padded(cx, d.x), WX = padded(cx, d.w * d.x);
         add(pr, tb, m.YS[i], d.y, d.q * d.y2, QY2, m.T2b, d.w * d.x, QY2, (int)d.y, (int)d.x,
             P(m.BR[i]), 0, d.w * X, X, 1,                       // ER[y][w][pad x]
@@ -186,12 +189,13 @@ QRTask qr_mixed(const MixCtx& cx, const FitSpec& f, int i, bool lq, size_t loss_
         t.m = (int)(y * q); t.n = (int)y2;
         t.in_rs = y2; t.in_cs = 1; t.out_rs = y2; t.out_cs = 1; t.conj_io = 0;
         t.out2 = P(f.mx.YT[i]);
-        t.out2_rs = 1; t.out2_cs = padded(cx, y * q);   // YT[y2][pad(y q)]
+        t.out2_M2 = 1; t.out2_rs = 1; t.out2_rs2 = 0; t.out2_cs = padded(cx, y * q);   // YT[y2][pad(y q)]
     } else {
         t.m = (int)(q * y2); t.n = (int)y;
         t.in_rs = 1; t.in_cs = q * y2; t.out_rs = 1; t.out_cs = q * y2; t.conj_io = 1;
         t.out2 = P(f.mx.YS[i]);
-        t.out2_rs = 1; t.out2_cs = padded(cx, q * y2);   // YS[y][pad(q y2)]
+        // row i = (q, y2) of the LQ matrix goes to YS[y][pad(y2 q)]
+        t.out2_M2 = (int)y2; t.out2_rs = 1; t.out2_rs2 = q; t.out2_cs = padded(cx, q * y2);
     }
     return t;
 }
@@ -232,7 +236,7 @@ void emit_fits_mixed(Program& pr, const MixCtx& cx, std::vector<FitSpec*>& fits,
                 r.dst = P(f->mx.YS[i]);
                 r.d[0] = (int)y; r.d[1] = (int)q; r.d[2] = (int)y2; r.d[3] = 1;
                 r.ss[0] = q * y2; r.ss[1] = y2; r.ss[2] = 1;
-                r.ds[0] = padded(cx, q * y2); r.ds[1] = y2; r.ds[2] = 1;
+                r.ds[0] = padded(cx, q * y2); r.ds[1] = 1; r.ds[2] = q;  // YS[y][pad(y2 q)]
                 r.src_kind = 0;
                 r.dst_kind = cx.lpk;
                 rl_.push_back(r);

@@ -18,6 +18,8 @@
 #include <cudaTypedefs.h>
 #include <stdint.h>
 
+#include <algorithm>
+
 #include "bbp_internal.h"
 #include "tc_gemm.h"
 
@@ -139,57 +141,85 @@ __device__ __forceinline__ void store_out(void* out, long long o, int kind, floa
     else ((double*)out)[o] = (double)x;
 }
 
-// Write the warp's 32 accumulator rows to one destination through the two-level map.
-// If the destination is contiguous along n2, the rows are staged through shared memory
-// so that the warp stores 32 consecutive columns of a row together; otherwise each
-// lane stores its own row (coalesced when the map is contiguous along m2).
-template <int BN>
-__device__ __forceinline__ void epilogue_dest(uint32_t tmem, int warp, int lane, int m0, int n0, int ncols, int nchunk,
-                                              int M, int M2, int N2, long long sm1, long long sm2, long long sn1,
-                                              long long sn2, int kind, float alpha, void* out, float* stage) {
-    if (sn2 == 1) {
-#pragma unroll 1
-        for (int c = 0; c < nchunk; c += 32) {
-            uint32_t v[32];
-            tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, v);
-            if (c + 16 < nchunk) tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c + 16), v + 16);
+// Epilogue.  The accumulator tile is staged in shared memory as FP32 [BM][BN+1] (odd
+// row pitch: row-wise and column-wise accesses are both free of bank conflicts), then
+// written to each destination through the two-level index map, with the row and column
+// offsets (m1*sm1 + m2*sm2, n1*sn1 + n2*sn2) computed once per tile.  A destination that is
+// contiguous along n2 is written row by row, one 16-byte vector per thread (a warp covers
+// up to 32 vectors of one row); one contiguous along m2 is written column by column in
+// 16-byte vectors down the rows; any other map falls back to element stores.  A vector is
+// used only where its elements are contiguous and 16-byte aligned in the destination.
+__device__ __forceinline__ int out_esz(int kind) { return kind == 3 ? 8 : kind == 2 ? 2 : 4; }
+
+__device__ __forceinline__ void store_vec(void* out, long long o, int kind, const float* x) {
+    // element o of out starts a 16-byte-aligned run of 16 / element-size elements
+    if (kind == 2) {
+        __nv_bfloat162 h[4];
 #pragma unroll
-            for (int j = 0; j < 32; ++j) stage[lane * 33 + j] = __uint_as_float(v[j]) * alpha;
-            __syncwarp();
-            const int n = n0 + c + lane;
-            const bool nlive = (c + lane) < ncols;
-            const int n1 = nlive ? n / N2 : 0;
-            const long long co = (long long)n1 * sn1 + (nlive ? n - n1 * N2 : 0);
-#pragma unroll 4
-            for (int r = 0; r < 32; ++r) {
-                const int row = m0 + warp * 32 + r;
-                if (!nlive || row >= M) continue;
-                const int r1 = row / M2, r2 = row - r1 * M2;
-                store_out(out, (long long)r1 * sm1 + (long long)r2 * sm2 + co, kind, stage[r * 33 + lane]);
-            }
-            __syncwarp();
-        }
-        return;
+        for (int j = 0; j < 4; ++j) h[j] = __floats2bfloat162_rn(x[2 * j], x[2 * j + 1]);
+        *(uint4*)((__nv_bfloat16*)out + o) = *(const uint4*)h;
+    } else if (kind == 3) {
+        *(double2*)((double*)out + o) = make_double2((double)x[0], (double)x[1]);
+    } else if (kind == 1) {
+        *(float4*)((float*)out + o) = make_float4(round_tf32(x[0]), round_tf32(x[1]), round_tf32(x[2]), round_tf32(x[3]));
+    } else {
+        *(float4*)((float*)out + o) = make_float4(x[0], x[1], x[2], x[3]);
     }
-    const int row = m0 + warp * 32 + lane;
-    const bool live = row < M;
-    const int r1 = live ? row / M2 : 0, r2 = live ? row - (row / M2) * M2 : 0;
-    const long long mo = (long long)r1 * sm1 + (long long)r2 * sm2;
-    int n1 = n0 / N2, n2 = n0 - (n0 / N2) * N2;
-    long long co = (long long)n1 * sn1 + (long long)n2 * sn2;
-#pragma unroll 1
-    for (int c = 0; c < nchunk; c += 16) {
-        uint32_t v[16];
-        tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, v);
+}
+
+template <int BN>
+__device__ __forceinline__ void epilogue_dest(const float* tile, long long* roff, long long* coff, int rows, int ncols,
+                                              int m0, int n0, int M2, int N2, long long sm1, long long sm2,
+                                              long long sn1, long long sn2, int kind, float alpha, void* out) {
+    constexpr int P = BN + 1;
+    const int tid = threadIdx.x;
+    __syncthreads();  // the previous destination has finished with the offsets
+    for (int r = tid; r < rows; r += 128) {
+        const int m = m0 + r, m1 = m / M2;
+        roff[r] = (long long)m1 * sm1 + (long long)(m - m1 * M2) * sm2;
+    }
+    for (int c = tid; c < ncols; c += 128) {
+        const int n = n0 + c, n1 = n / N2;
+        coff[c] = (long long)n1 * sn1 + (long long)(n - n1 * N2) * sn2;
+    }
+    __syncthreads();
+    const int esz = out_esz(kind), VW = 16 / esz;
+    const uintptr_t base = (uintptr_t)out;
+    float x[8];
+    if (sn2 == 1) {
+        const int G = (ncols + VW - 1) / VW;
+        for (int it = tid; it < rows * G; it += 128) {
+            const int r = it / G, c0 = (it - r * G) * VW;
+            const long long o = roff[r] + coff[c0];
+            bool vec = c0 + VW <= ncols && ((base + (uintptr_t)(o * esz)) & 15) == 0 && coff[c0 + VW - 1] == coff[c0] + VW - 1;
+            if (vec) {
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-            if (c + j < ncols && live) store_out(out, mo + co, kind, __uint_as_float(v[j]) * alpha);
-            if (++n2 == N2) {
-                n2 = 0;
-                co += sn1 - (long long)(N2 - 1) * sn2;
+                for (int j = 0; j < 8; ++j)
+                    if (j < VW) x[j] = tile[r * P + c0 + j] * alpha;
+                store_vec(out, o, kind, x);
             } else {
-                co += sn2;
+                for (int j = 0; j < VW && c0 + j < ncols; ++j) store_out(out, roff[r] + coff[c0 + j], kind, tile[r * P + c0 + j] * alpha);
             }
+        }
+    } else if (sm2 == 1) {
+        const int G = (rows + VW - 1) / VW;
+        for (int it = tid; it < ncols * G; it += 128) {
+            const int c = it / G, r0 = (it - c * G) * VW;
+            const long long o = roff[r0] + coff[c];
+            bool vec = r0 + VW <= rows && ((base + (uintptr_t)(o * esz)) & 15) == 0 && roff[r0 + VW - 1] == roff[r0] + VW - 1;
+            if (vec) {
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+                    if (j < VW) x[j] = tile[(r0 + j) * P + c] * alpha;
+                store_vec(out, o, kind, x);
+            } else {
+                for (int j = 0; j < VW && r0 + j < rows; ++j) store_out(out, roff[r0 + j] + coff[c], kind, tile[(r0 + j) * P + c] * alpha);
+            }
+        }
+    } else {
+        for (int it = tid; it < rows * ncols; it += 128) {
+            const int c = it / rows, r = it - c * rows;
+            store_out(out, roff[r] + coff[c], kind, tile[r * P + c] * alpha);
         }
     }
 }
@@ -259,19 +289,31 @@ __global__ void __launch_bounds__(128) k_tc_gemm(const TCTask* __restrict__ task
         umma_commit(&accum);
     }
     __syncwarp();
-    // epilogue: every warp waits for the accumulator
+    // epilogue: every warp waits for the accumulator, stages its 32 rows in shared memory
+    // (the operand ring is free: every issued copy was consumed by a finished MMA)
     const bool ready = mbar_wait(&accum, 0, err);
     fence_after();
-    if (ready) {
-        const int ncols = min(BN, t.N - n0);
+    if (__syncthreads_and(ready ? 1 : 0)) {
+        const int ncols = min(BN, t.N - n0), rows = min(BM, t.M - m0);
         const int nchunk = (ncols + 15) & ~15;  // tcgen05.ld is warp-collective: uniform bound
-        float* stage = (float*)smem + warp * 32 * 33;
+        float* tile = (float*)smem;
+        long long* roff = (long long*)(tile + BM * (BN + 1));
+        long long* coff = roff + BM;
+        const int row = warp * 32 + lane;
+#pragma unroll 1
+        for (int c = 0; c < nchunk; c += 16) {
+            uint32_t v[16];
+            tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, v);
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+                if (c + j < BN) tile[row * (BN + 1) + c + j] = __uint_as_float(v[j]);
+        }
         for (int dst = 0; dst < (t.C2 ? 2 : 1); ++dst) {
             void* out = dst ? t.C2 : t.C;
             const long long sm1 = dst ? t.d_m1 : t.c_m1, sm2 = dst ? t.d_m2 : t.c_m2;
             const long long sn1 = dst ? t.d_n1 : t.c_n1, sn2 = dst ? t.d_n2 : t.c_n2;
-            epilogue_dest<BN>(tmem, warp, lane, m0, n0, ncols, nchunk, t.M, t.M2, t.N2, sm1, sm2, sn1, sn2,
-                              t.out_kind, t.alpha, out, stage);
+            epilogue_dest<BN>(tile, roff, coff, rows, ncols, m0, n0, t.M2, t.N2, sm1, sm2, sn1, sn2, t.out_kind,
+                              t.alpha, out);
         }
     }
     fence_before();
@@ -288,12 +330,20 @@ __global__ void __launch_bounds__(128) k_tc_gemm(const TCTask* __restrict__ task
 
 }  // namespace tc
 
+// Dynamic shared memory: the operand ring, or the staged epilogue tile and its offsets
+// if that is larger, plus 1 KB for the 1024-byte alignment of the swizzled ring.
+static size_t tc_smem(int stages, int bn) {
+    const size_t ring = (size_t)stages * (tc::BM + bn) * tc::KBYTES;
+    const size_t tile = (size_t)tc::BM * (bn + 1) * sizeof(float) + (size_t)(tc::BM + bn) * sizeof(long long);
+    return std::max(ring, tile) + 1024;
+}
+
 cudaError_t tc_prepare() {
     // sets the shared-memory limits outside any stream capture
     cudaError_t e;
     const int bns[4] = {32, 64, 128, 256};
     for (int i = 0; i < 4; ++i) {
-        const size_t smem = tc::STAGES * (size_t)(tc::BM + bns[i]) * tc::KBYTES + 1024;
+        const size_t smem = tc_smem(tc::STAGES, bns[i]);
         switch (bns[i]) {
             case 32:
                 if ((e = cudaFuncSetAttribute(tc::k_tc_gemm<0, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))) return e;
@@ -319,7 +369,7 @@ cudaError_t launch_tc_gemm(const TCTask* d_tasks, int ntasks, int kind, int bn, 
                            cudaStream_t s) {
     if (ntasks <= 0) return cudaSuccess;
     if (stages < 1 || stages > tc::STAGES) return cudaErrorInvalidValue;
-    const size_t smem = (size_t)stages * (tc::BM + bn) * tc::KBYTES + 1024;
+    const size_t smem = tc_smem(stages, bn);
     dim3 grid(max_tiles, ntasks);
 #define TC_CASE(K_, N_)                                                                          \
     if (kind == K_ && bn == N_) {                                                                \

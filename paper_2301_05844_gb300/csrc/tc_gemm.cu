@@ -141,10 +141,11 @@ __device__ __forceinline__ void store_out(void* out, long long o, int kind, floa
     else ((double*)out)[o] = (double)x;
 }
 
-// Epilogue.  The accumulator tile is staged in shared memory as FP32 [BM][BN+1] (odd
-// row pitch: row-wise and column-wise accesses are both free of bank conflicts), then
-// written to each destination through the two-level index map, with the row and column
-// offsets (m1*sm1 + m2*sm2, n1*sn1 + n2*sn2) computed once per tile.  A destination that is
+// Epilogue.  The accumulator is staged in shared memory 64 columns at a time as FP32
+// [BM][EC+1] (odd row pitch: row-wise and column-wise accesses are both free of bank
+// conflicts), and each chunk is written to each destination through the two-level index
+// map, with the row and column offsets (m1*sm1 + m2*sm2, n1*sn1 + n2*sn2) computed once
+// per chunk.  A destination that is
 // contiguous along n2 is written row by row, one 16-byte vector per thread (a warp covers
 // up to 32 vectors of one row); one contiguous along m2 is written column by column in
 // 16-byte vectors down the rows; any other map falls back to element stores.  A vector is
@@ -167,11 +168,12 @@ __device__ __forceinline__ void store_vec(void* out, long long o, int kind, cons
     }
 }
 
-template <int BN>
+constexpr int EC = 64;  // epilogue chunk (columns)
+
 __device__ __forceinline__ void epilogue_dest(const float* tile, long long* roff, long long* coff, int rows, int ncols,
                                               int m0, int n0, int M2, int N2, long long sm1, long long sm2,
                                               long long sn1, long long sn2, int kind, float alpha, void* out) {
-    constexpr int P = BN + 1;
+    constexpr int P = EC + 1;
     const int tid = threadIdx.x;
     __syncthreads();  // the previous destination has finished with the offsets
     for (int r = tid; r < rows; r += 128) {
@@ -295,25 +297,30 @@ __global__ void __launch_bounds__(128) k_tc_gemm(const TCTask* __restrict__ task
     fence_after();
     if (__syncthreads_and(ready ? 1 : 0)) {
         const int ncols = min(BN, t.N - n0), rows = min(BM, t.M - m0);
-        const int nchunk = (ncols + 15) & ~15;  // tcgen05.ld is warp-collective: uniform bound
         float* tile = (float*)smem;
-        long long* roff = (long long*)(tile + BM * (BN + 1));
+        long long* roff = (long long*)(tile + BM * (EC + 1));
         long long* coff = roff + BM;
         const int row = warp * 32 + lane;
 #pragma unroll 1
-        for (int c = 0; c < nchunk; c += 16) {
-            uint32_t v[16];
-            tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, v);
+        for (int c0 = 0; c0 < ncols; c0 += EC) {
+            const int cn = min(EC, ncols - c0);
+            const int nchunk = (cn + 15) & ~15;  // tcgen05.ld is warp-collective: uniform bound
+            __syncthreads();                     // the previous chunk has been written out
+#pragma unroll 1
+            for (int c = 0; c < nchunk; c += 16) {
+                uint32_t v[16];
+                tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c0 + c), v);
 #pragma unroll
-            for (int j = 0; j < 16; ++j)
-                if (c + j < BN) tile[row * (BN + 1) + c + j] = __uint_as_float(v[j]);
-        }
-        for (int dst = 0; dst < (t.C2 ? 2 : 1); ++dst) {
-            void* out = dst ? t.C2 : t.C;
-            const long long sm1 = dst ? t.d_m1 : t.c_m1, sm2 = dst ? t.d_m2 : t.c_m2;
-            const long long sn1 = dst ? t.d_n1 : t.c_n1, sn2 = dst ? t.d_n2 : t.c_n2;
-            epilogue_dest<BN>(tile, roff, coff, rows, ncols, m0, n0, t.M2, t.N2, sm1, sm2, sn1, sn2, t.out_kind,
+                for (int j = 0; j < 16; ++j)
+                    if (c + j < EC) tile[row * (EC + 1) + c + j] = __uint_as_float(v[j]);
+            }
+            for (int dst = 0; dst < (t.C2 ? 2 : 1); ++dst) {
+                void* out = dst ? t.C2 : t.C;
+                const long long sm1 = dst ? t.d_m1 : t.c_m1, sm2 = dst ? t.d_m2 : t.c_m2;
+                const long long sn1 = dst ? t.d_n1 : t.c_n1, sn2 = dst ? t.d_n2 : t.c_n2;
+                epilogue_dest(tile, roff, coff, rows, cn, m0, n0 + c0, t.M2, t.N2, sm1, sm2, sn1, sn2, t.out_kind,
                               t.alpha, out);
+            }
         }
     }
     fence_before();
@@ -334,7 +341,7 @@ __global__ void __launch_bounds__(128) k_tc_gemm(const TCTask* __restrict__ task
 // if that is larger, plus 1 KB for the 1024-byte alignment of the swizzled ring.
 static size_t tc_smem(int stages, int bn) {
     const size_t ring = (size_t)stages * (tc::BM + bn) * tc::KBYTES;
-    const size_t tile = (size_t)tc::BM * (bn + 1) * sizeof(float) + (size_t)(tc::BM + bn) * sizeof(long long);
+    const size_t tile = (size_t)tc::BM * (tc::EC + 1) * sizeof(float) + (size_t)(tc::BM + tc::EC) * sizeof(long long);
     return std::max(ring, tile) + 1024;
 }
 

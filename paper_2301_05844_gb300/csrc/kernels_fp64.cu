@@ -245,13 +245,14 @@ __global__ void __launch_bounds__(256) k_qr(const QRTask* __restrict__ tasks, in
     const QRTask& t = tasks[blockIdx.x];
     if (t.active && *t.active == 0) return;
     extern __shared__ __align__(16) unsigned char qr_smem[];
-    S* u = (S*)qr_smem;  // m entries
+    // u: two buffers of m entries (the reflector of the current and of the previous column)
+    S* ubuf = (S*)qr_smem;
     __shared__ S betas[QR_MAXN];
     __shared__ double coefs[QR_MAXN];
-    __shared__ S red[32];
     __shared__ double redd[32];
+    __shared__ double next_x2;  // ||x'||^2 of the next column, from the warp that updated it
     const int m = t.m, n = t.n, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    S* W = resident ? u + m : (S*)t.work;
+    S* W = resident ? ubuf + 2 * m : (S*)t.work;
     S* Q = W + (size_t)m * n;
     const S* in = (const S*)t.in;
     S* out = (S*)t.out;
@@ -268,12 +269,18 @@ __global__ void __launch_bounds__(256) k_qr(const QRTask* __restrict__ tasks, in
     }
     ss = block_sum(ss, redd);
     if (tid == 0 && t.loss) *t.loss = -ss;
-    __syncthreads();
+    bool fused = false;  // next_x2 holds the sub-diagonal norm of column j (uniform)
     for (int j = 0; j < n; ++j) {
         S* col = W + (size_t)j * m;
-        double xs2 = 0.0;
-        for (int i = j + 1 + tid; i < m; i += 256) xs2 += abs2(col[i]);
-        xs2 = block_sum(xs2, redd);
+        S* u = ubuf + (size_t)(j & 1) * m;
+        double xs2;
+        if (fused) {
+            xs2 = next_x2;
+        } else {
+            xs2 = 0.0;
+            for (int i = j + 1 + tid; i < m; i += 256) xs2 += abs2(col[i]);
+            xs2 = block_sum(xs2, redd);
+        }
         double xnorm = sqrt(xs2);
         if (xs2 < 1e-280) {  // near underflow (uniform branch): rescale by max |x'_i|
             double amax = 0.0;
@@ -296,26 +303,53 @@ __global__ void __launch_bounds__(256) k_qr(const QRTask* __restrict__ tasks, in
             tau = 1.0 + aa / nrm;
             const double den = aa + nrm;  // |alpha - beta|
             const S cph = conjv(ph);
-            for (int i = j + tid; i < m; i += 256) u[i] = (i == j) ? one<S>() : divr(mul(col[i], cph), den);
+            if (den > 1e-290) {
+                const S sc = scal(cph, 1.0 / den);
+                for (int i = j + 1 + tid; i < m; i += 256) {
+                    const S v = mul(col[i], sc);
+                    u[i] = v;
+                    col[i] = v;  // rows below the diagonal: nobody else reads them in this step
+                }
+            } else {
+                for (int i = j + 1 + tid; i < m; i += 256) {
+                    const S v = divr(mul(col[i], cph), den);
+                    u[i] = v;
+                    col[i] = v;
+                }
+            }
+            if (tid == 0) u[j] = one<S>();
         }
         if (tid == 0) {
             betas[j] = beta;
             coefs[j] = tau;
         }
-        __syncthreads();
+        __syncthreads();  // u complete; every thread has read alpha
+        fused = false;
         if (tau != 0.0) {
+            if (tid == 0) col[j] = one<S>();
             for (int k = j + 1 + warp; k < n; k += 8) {
                 S* ck = W + (size_t)k * m;
                 S dot = zero<S>();
                 for (int i = j + lane; i < m; i += 32) mac(dot, conjv(u[i]), ck[i]);
                 dot = warp_sum(dot);
                 const S f = scal(dot, -tau);
-                for (int i = j + lane; i < m; i += 32) mac(ck[i], u[i], f);
+                if (k == j + 1) {  // the next column: also its norm below the next diagonal
+                    double nx = 0.0;
+                    for (int i = j + lane; i < m; i += 32) {
+                        S c = ck[i];
+                        mac(c, u[i], f);
+                        ck[i] = c;
+                        if (i > k) nx += abs2(c);
+                    }
+                    nx = warp_sum(nx);
+                    if (lane == 0) next_x2 = nx;
+                } else {
+                    for (int i = j + lane; i < m; i += 32) mac(ck[i], u[i], f);
+                }
             }
+            fused = j + 1 < n;
             __syncthreads();
-            for (int i = j + tid; i < m; i += 256) col[i] = u[i];
         }
-        __syncthreads();
     }
     for (long long idx = tid; idx < (long long)m * n; idx += 256) {
         const int i = (int)(idx % m), k = (int)(idx / m);
@@ -325,16 +359,21 @@ __global__ void __launch_bounds__(256) k_qr(const QRTask* __restrict__ tasks, in
     for (int j = n - 1; j >= 0; --j) {
         const double coef = coefs[j];
         if (coef == 0.0) continue;
-        const S* uj = W + (size_t)j * m;
-        for (int i = j + tid; i < m; i += 256) u[i] = uj[i];
-        __syncthreads();
+        const S* uj = W + (size_t)j * m;  // v_j with v_j[j] = 1
+        const S* v = uj;
+        if (!resident) {  // stage v_j in shared memory
+            S* u = ubuf + (size_t)(j & 1) * m;
+            for (int i = j + tid; i < m; i += 256) u[i] = uj[i];
+            __syncthreads();
+            v = u;
+        }
         for (int k = j + warp; k < n; k += 8) {
             S* qk = Q + (size_t)k * m;
             S dot = zero<S>();
-            for (int i = j + lane; i < m; i += 32) mac(dot, conjv(u[i]), qk[i]);
+            for (int i = j + lane; i < m; i += 32) mac(dot, conjv(v[i]), qk[i]);
             dot = warp_sum(dot);
             const S f = scal(dot, -coef);
-            for (int i = j + lane; i < m; i += 32) mac(qk[i], u[i], f);
+            for (int i = j + lane; i < m; i += 32) mac(qk[i], v[i], f);
         }
         __syncthreads();
     }
@@ -517,9 +556,9 @@ static size_t qr_cluster_smem(int max_m, long long max_mn, int C, size_t ss) {
 
 static size_t qr_smem_bytes(int max_m, long long max_mn, bool cplx, int* resident) {
     const size_t ss = cplx ? sizeof(double2) : sizeof(double);
-    const size_t all = ((size_t)max_m + 2 * (size_t)max_mn) * ss;
+    const size_t all = (2 * (size_t)max_m + 2 * (size_t)max_mn) * ss;  // u (two buffers), W, Q
     *resident = all <= QR_SMEM_LIMIT ? 1 : 0;
-    return *resident ? all : (size_t)max_m * ss;
+    return *resident ? all : 2 * (size_t)max_m * ss;
 }
 
 cudaError_t qr_prepare(int max_m, bool cplx) {
@@ -536,7 +575,7 @@ cudaError_t qr_prepare(int max_m, bool cplx) {
         cluster_set[cplx ? 1 : 0] = true;
     }
     const size_t ss = cplx ? sizeof(double2) : sizeof(double);
-    const size_t sm = std::max((size_t)max_m * ss, QR_SMEM_LIMIT);
+    const size_t sm = std::max(2 * (size_t)max_m * ss, QR_SMEM_LIMIT);
     if (sm <= limit[cplx ? 1 : 0]) return cudaSuccess;
     cudaError_t e = cplx ? cudaFuncSetAttribute(k_qr<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)
                          : cudaFuncSetAttribute(k_qr<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);

@@ -440,13 +440,20 @@ __global__ void __launch_bounds__(256) k_qr_cluster(const QRTask* __restrict__ t
         for (int r = 0; r < C; ++r) tot += *cluster.map_shared_rank(part, r);
         *t.loss = -tot;
     }
+    __shared__ double next_x2;  // sub-diagonal norm of the next column, when this CTA owns it
+    bool fused = false;         // uniform over the cluster: the previous step updated column j
     for (int j = 0; j < n; ++j) {
         const int owner = j % C, lj = j / C;
         if (rank == owner) {
             S* col = W + (size_t)lj * m;
-            double xs2 = 0.0;
-            for (int i = j + 1 + tid; i < m; i += 256) xs2 += abs2(col[i]);
-            xs2 = block_sum(xs2, redd);
+            double xs2;
+            if (fused) {
+                xs2 = next_x2;
+            } else {
+                xs2 = 0.0;
+                for (int i = j + 1 + tid; i < m; i += 256) xs2 += abs2(col[i]);
+                xs2 = block_sum(xs2, redd);
+            }
             double xnorm = sqrt(xs2);
             if (xs2 < 1e-280) {
                 double amax = 0.0;
@@ -470,7 +477,12 @@ __global__ void __launch_bounds__(256) k_qr_cluster(const QRTask* __restrict__ t
                 tau = 1.0 + aa / nrm;
                 const double den = aa + nrm;
                 const S cph = conjv(ph);
-                for (int i = j + tid; i < m; i += 256) col[i] = (i == j) ? one<S>() : divr(mul(col[i], cph), den);
+                if (den > 1e-290) {
+                    const S sc = scal(cph, 1.0 / den);
+                    for (int i = j + tid; i < m; i += 256) col[i] = (i == j) ? one<S>() : mul(col[i], sc);
+                } else {
+                    for (int i = j + tid; i < m; i += 256) col[i] = (i == j) ? one<S>() : divr(mul(col[i], cph), den);
+                }
             }
             if (tid == 0) {
                 taus[j] = tau;
@@ -486,14 +498,28 @@ __global__ void __launch_bounds__(256) k_qr_cluster(const QRTask* __restrict__ t
             __syncthreads();
             for (int lk = lk0 + warp; lk < nl; lk += 8) {
                 S* ck = W + (size_t)lk * m;
+                const int k = rank + lk * C;
                 S dot = zero<S>();
                 for (int i = j + lane; i < m; i += 32) mac(dot, conjv(u[i]), ck[i]);
                 dot = warp_sum(dot);
                 const S f = scal(dot, -tau);
-                for (int i = j + lane; i < m; i += 32) mac(ck[i], u[i], f);
+                if (k == j + 1) {  // the next column: also its norm below the next diagonal
+                    double nx = 0.0;
+                    for (int i = j + lane; i < m; i += 32) {
+                        S c = ck[i];
+                        mac(c, u[i], f);
+                        ck[i] = c;
+                        if (i > k) nx += abs2(c);
+                    }
+                    nx = warp_sum(nx);
+                    if (lane == 0) next_x2 = nx;
+                } else {
+                    for (int i = j + lane; i < m; i += 32) mac(ck[i], u[i], f);
+                }
             }
             __syncthreads();
         }
+        fused = tau != 0.0 && j + 1 < n;
     }
     cluster.sync();  // every reflector is final
     for (long long idx = tid; idx < (long long)m * nl; idx += 256) {

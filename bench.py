@@ -32,7 +32,9 @@ sys.path.insert(0, ROOT)
 
 METRIC = "blockBP sweeps/s + TFLOP/s vs FP64 GPU path at stated <O> error; p50/p99 latency"
 NOMINAL_TF32_OVER_BF16 = 1.1 / 2.25   # dense nominal ratio (recipe table)
-NOMINAL_FP64_TFLOPS = 1.25            # recipe table, GB300 FP64
+# FP64 ALU peak: 2 DFMA per cycle per SM (ncu peak_sustained of the DFMA counter) x 2 flop
+# x SMs x max SM clock; 152 SMs at 2070 MHz gives 1.26 TFLOP/s (recipe nominal: 1.25)
+DFMA_PER_SM_CLK = 2
 FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
 # zip-up fit stop rule (App. A: std/|mean| of the sweep's losses): the paper's 1e-6; the
 # library raises it to the loss noise of TF32 / BF16 contractions on those paths
@@ -238,7 +240,10 @@ def run_ours(args):
             peak = base if prec == "bf16" else base * NOMINAL_TF32_OVER_BF16
             bound, note = "tensor", f"of {src} bf16 burst" + ("" if prec == "bf16" else " x nominal tf32/bf16")
         else:
-            peak, bound, note = NOMINAL_FP64_TFLOPS, "alu", "of nominal FP64"
+            sms = torch.cuda.get_device_properties(dev).multi_processor_count
+            mhz = pk.get("sm_max_mhz", 2070.0)
+            peak = DFMA_PER_SM_CLK * 2 * sms * mhz * 1e6 / 1e12
+            bound, note = "alu", f"of derived FP64 DFMA peak ({DFMA_PER_SM_CLK} DFMA/clk/SM x {sms} SMs x {mhz:.0f} MHz)"
         roofline = {"bound": bound, "kernel": dom, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
                     "frac": ach / peak, "traffic": None, "peak_source": note,
                     "classes_ms_per_sweep": {k: round(v["ms"], 4) for k, v in classes.items()},

@@ -38,7 +38,7 @@ DFMA_PER_SM_CLK = 2
 FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
 # zip-up fit stop rule (App. A: std/|mean| of the sweep's losses): the paper's 1e-6; the
 # library raises it to the loss noise of TF32 / BF16 contractions on those paths
-FIT_TOL = {"fp64": 1e-6, "tf32": 1e-6, "bf16": 1e-6}
+FIT_TOL = {"fp64": 1e-6, "tf32": 1e-6, "bf16": 1e-6, "tf32x3": 1e-6}
 WARM = 1  # each fit starts from its previous-sweep result (identical option in the oracle)
 
 
@@ -305,7 +305,7 @@ def run_ours(args):
         out = {"metric": METRIC, "value": value, "unit": "sweeps/s", "n_gpus": world, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": 1e3 * tmax / args.steps, "higher_is_better": True,
                "scaling": "weak", "vs_baseline": None, "dtype": {"tf32": "tf32+f64qr", "bf16": "bf16+f64qr",
-                                                                "fp64": "f64"}[prec],
+                                                                "tf32x3": "3xtf32+f64qr", "fp64": "f64"}[prec],
                "data": "synthetic", "config": {"workload": cfg["name"], "lattice": f"{cfg['Lx']}x{cfg['Ly']}",
                                               "d": cfg["d"], "D": cfg["D"], "chi": cfg["chi"],
                                               "block": f"{cfg['bx']}x{cfg['by']}",
@@ -432,7 +432,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", type=int, default=2)
-    ap.add_argument("--prec", default=None, choices=[None, "fp64", "tf32", "bf16"])
+    ap.add_argument("--prec", default=None, choices=[None, "fp64", "tf32", "bf16", "tf32x3"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")

@@ -51,8 +51,11 @@ typedef enum { BBP_OBC = 0, BBP_INFINITE = 1 } bbp_boundary;
 typedef enum { BBP_F64 = 0, BBP_C128 = 1, BBP_F32 = 2, BBP_C64 = 3 } bbp_dtype;
 /* Arithmetic of the contractions.  FP64: every step in FP64 on the GPU.  TF32 and
  * BF16: the site-update contractions on tensor cores with FP32 accumulation, while
- * the QR/LQ truncation, message normalisation, residual and read-out ratios stay FP64. */
-typedef enum { BBP_PREC_FP64 = 0, BBP_PREC_TF32 = 1, BBP_PREC_BF16 = 2 } bbp_prec;
+ * the QR/LQ truncation, message normalisation, residual and read-out ratios stay FP64.
+ * TF32X3: as TF32, but every operand is split into a TF32 high part and a TF32 low part
+ * (the rounding remainder) and each product is A_hi B_hi + A_lo B_hi + A_hi B_lo, all in
+ * one FP32 accumulator: FP32-level contraction accuracy at three times the MMA work. */
+typedef enum { BBP_PREC_FP64 = 0, BBP_PREC_TF32 = 1, BBP_PREC_BF16 = 2, BBP_PREC_TF32X3 = 3 } bbp_prec;
 
 typedef struct {
     int Lx, Ly;              /* OBC: lattice columns, rows.  INFINITE: unit cell columns, rows */

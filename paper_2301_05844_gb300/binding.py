@@ -18,11 +18,11 @@ OK, NOT_CONVERGED = 0, 1
 ERR_INVALID, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_NUMERIC, ERR_STATE = -1, -2, -3, -4, -5, -6
 OBC, INFINITE = 0, 1
 F64, C128, F32, C64 = 0, 1, 2, 3
-PREC_FP64, PREC_TF32, PREC_BF16 = 0, 1, 2
+PREC_FP64, PREC_TF32, PREC_BF16, PREC_TF32X3 = 0, 1, 2, 3
 LEFT, RIGHT, UP, DOWN = 0, 1, 2, 3
 
 _NP_DTYPE = {F64: np.float64, C128: np.complex128, F32: np.float32, C64: np.complex64}
-_PREC = {"fp64": PREC_FP64, "tf32": PREC_TF32, "bf16": PREC_BF16}
+_PREC = {"fp64": PREC_FP64, "tf32": PREC_TF32, "bf16": PREC_BF16, "tf32x3": PREC_TF32X3}
 
 
 class Desc(C.Structure):

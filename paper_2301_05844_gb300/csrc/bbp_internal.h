@@ -49,6 +49,8 @@ struct QRTask {
     long long out2_rs, out2_cs, out2_rs2;
     int out2_kind;   // element kind of out2 (see RelayoutTask)
     int out2_M2;     // >= 1
+    int out2_x3;     // split TF32 operand rows (see RelayoutTask)
+    long long out2_kseg;
 };
 
 // Strided copy with type conversion over a 4-D index space (dims d0 x d1 x d2 x d3):
@@ -61,6 +63,8 @@ struct RelayoutTask {
     long long ss[4];
     long long ds[4];
     int src_kind, dst_kind;
+    int x3;          // split TF32 operand (see store_split): 0 no, 1 A rows [hi|lo|hi], 2 B rows [hi|hi|lo]
+    long long kseg;  // K extent: distance between the three segments of a split row
 };
 
 // Fill n scalars (2n doubles if complex) with the counter-based uniforms in [-1,1).

@@ -112,7 +112,7 @@ std::string Program::validate() const {
         if (t.out2) {
             const int M2 = t.out2_M2 > 1 ? t.out2_M2 : 1;
             const long long ext = (long long)((t.m - 1) / M2) * t.out2_rs + (long long)(std::min(M2, t.m) - 1) * t.out2_rs2 +
-                                  (long long)(t.n - 1) * t.out2_cs + 1;
+                                  (long long)(t.n - 1) * t.out2_cs + 1 + (t.out2_x3 ? 2 * t.out2_kseg : 0);
             c.range(t.out2, ext, t.out2_kind == 0 ? 8 : t.out2_kind == 3 ? 2 : 4, "QR out2", i);
         }
         c.range(t.loss, 1, 8, "QR loss", i);
@@ -164,7 +164,6 @@ std::string Program::validate() const {
     }
     for (size_t i = 0; i < qr.size(); ++i) {
         const QRTask& t = qr[i];
-        if (t.out2) c.range(t.out2, ext2(t.m, t.out2_rs, t.n, t.out2_cs) + 1, t.out2_kind == 3 ? 2 : t.out2_kind == 0 ? 8 : 4, "QR out2", i);
         if (t.in_float) {
             // FP32 input read with the same strides (already checked with the scalar size, which is larger)
         }
@@ -179,8 +178,9 @@ std::string Program::validate() const {
         c.range(P(sp.a_off), (sp.a_rows - 1) * sp.a_ld + sp.K, esz, "TC A", i);
         c.range(P(sp.b_off), (sp.b_rows - 1) * sp.b_ld + sp.K, esz, "TC B", i);
         const int osz = t.out_kind == 2 ? 2 : t.out_kind == 3 ? 8 : 4;
-        c.range(t.C, ext2(t.M / t.M2, t.c_m1, t.M2, t.c_m2) + ext2(t.N / t.N2, t.c_n1, t.N2, t.c_n2) + 1, osz, "TC C", i);
-        if (t.C2) c.range(t.C2, ext2(t.M / t.M2, t.d_m1, t.M2, t.d_m2) + ext2(t.N / t.N2, t.d_n1, t.N2, t.d_n2) + 1, osz, "TC C2", i);
+        const long long xc = (t.x3 & 3) ? 2 * t.kseg : 0, xd = ((t.x3 >> 2) & 3) ? 2 * t.kseg2 : 0;  // split segments
+        c.range(t.C, ext2(t.M / t.M2, t.c_m1, t.M2, t.c_m2) + ext2(t.N / t.N2, t.c_n1, t.N2, t.c_n2) + 1 + xc, osz, "TC C", i);
+        if (t.C2) c.range(t.C2, ext2(t.M / t.M2, t.d_m1, t.M2, t.d_m2) + ext2(t.N / t.N2, t.d_n1, t.N2, t.d_n2) + 1 + xd, osz, "TC C2", i);
         c.range(t.active, 1, 4, "TC active", i);
     }
     for (size_t i = 0; i < rel.size(); ++i) {
@@ -192,7 +192,7 @@ std::string Program::validate() const {
         }
         auto ksz = [](int k) { return k == 0 ? 8 : k == 3 ? 2 : 4; };
         c.range(t.src, se, ksz(t.src_kind), "relayout src", i);
-        c.range(t.dst, de, ksz(t.dst_kind), "relayout dst", i);
+        c.range(t.dst, de + (t.x3 ? 2 * t.kseg : 0), ksz(t.dst_kind), "relayout dst", i);
     }
     for (size_t i = 0; i < steps.size(); ++i) {
         const Step& s = steps[i];

@@ -126,6 +126,7 @@ struct MixCtx {
     int lpk = 4;     // relayout / QR store kind of low-precision operands
     int tck = 0;     // tensor-core kind: 0 TF32, 1 BF16
     int tco = 1;     // tensor-core epilogue kind of low-precision results
+    bool x3 = false; // split TF32 operands: every K-major row holds three K-segments
 };
 void emit_fits_mixed(Program& pr, const MixCtx& cx, std::vector<FitSpec*>& fits, int max_sweeps, double fit_tol,
                      bool warm, bool rand_uses_sweep);

@@ -135,6 +135,25 @@ __device__ __forceinline__ void store_kind(void* p, long long i, int kind, doubl
     store_kind(p, 2 * i, kind, v.x);
     store_kind(p, 2 * i + 1, kind, v.y);
 }
+// Split TF32 operand (x3 != 0, kind 4): hi = tf32(v), lo = tf32(v - hi) written to the three
+// K-segments of the row, kseg elements apart: [hi|lo|hi] for an A operand (x3 = 1),
+// [hi|hi|lo] for a B operand (x3 = 2), so that a GEMM over 3K forms
+// A_hi B_hi + A_lo B_hi + A_hi B_lo.
+__device__ __forceinline__ void store_split(void* p, long long i, int kind, double v, int x3, long long kseg) {
+    if (!x3) {
+        store_kind(p, i, kind, v);
+        return;
+    }
+    const float hi = tf32_round((float)v), lo = tf32_round((float)(v - (double)hi));
+    float* f = (float*)p;
+    f[i] = hi;
+    f[i + kseg] = x3 == 1 ? lo : hi;
+    f[i + 2 * kseg] = x3 == 1 ? hi : lo;
+}
+__device__ __forceinline__ void store_split(void* p, long long i, int kind, double2 v, int x3, long long kseg) {
+    store_split(p, 2 * i, kind, v.x, x3, kseg);
+    store_split(p, 2 * i + 1, kind, v.y, x3, kseg);
+}
 __device__ __forceinline__ double load_kind(const void* p, long long i, int kind) {
     switch (kind) {
         case 0: return ((const double*)p)[i];
@@ -386,8 +405,8 @@ __global__ void __launch_bounds__(256) k_qr(const QRTask* __restrict__ tasks, in
         out[(long long)i * t.out_rs + (long long)k * t.out_cs] = v;
         if (t.out2) {
             const int M2 = t.out2_M2 > 1 ? t.out2_M2 : 1, i1 = i / M2;
-            store_kind(t.out2, (long long)i1 * t.out2_rs + (long long)(i - i1 * M2) * t.out2_rs2 + (long long)k * t.out2_cs,
-                       t.out2_kind, v);
+            store_split(t.out2, (long long)i1 * t.out2_rs + (long long)(i - i1 * M2) * t.out2_rs2 + (long long)k * t.out2_cs,
+                        t.out2_kind, v, t.out2_x3, t.out2_kseg);
         }
     }
 }
@@ -555,8 +574,8 @@ __global__ void __launch_bounds__(256) k_qr_cluster(const QRTask* __restrict__ t
         out[(long long)i * t.out_rs + (long long)k * t.out_cs] = v;
         if (t.out2) {
             const int M2 = t.out2_M2 > 1 ? t.out2_M2 : 1, i1 = i / M2;
-            store_kind(t.out2, (long long)i1 * t.out2_rs + (long long)(i - i1 * M2) * t.out2_rs2 + (long long)k * t.out2_cs,
-                       t.out2_kind, v);
+            store_split(t.out2, (long long)i1 * t.out2_rs + (long long)(i - i1 * M2) * t.out2_rs2 + (long long)k * t.out2_cs,
+                        t.out2_kind, v, t.out2_x3, t.out2_kseg);
         }
     }
     cluster.sync();  // no CTA leaves while another may still read its shared memory
@@ -1038,7 +1057,7 @@ __global__ void k_relayout(const RelayoutTask* __restrict__ tasks) {
         const int i0 = (int)r;
         const long long so = i0 * t.ss[0] + i1 * t.ss[1] + i2 * t.ss[2] + i3 * t.ss[3];
         const long long dof = i0 * t.ds[0] + i1 * t.ds[1] + i2 * t.ds[2] + i3 * t.ds[3];
-        store_kind(t.dst, dof, t.dst_kind, load_kind(t.src, so, t.src_kind));
+        store_split(t.dst, dof, t.dst_kind, load_kind(t.src, so, t.src_kind), t.x3, t.kseg);
     }
 }
 cudaError_t launch_relayout(const RelayoutTask* d_tasks, int ntasks, long long max_elems, cudaStream_t s) {

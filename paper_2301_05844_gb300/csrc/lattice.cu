@@ -307,8 +307,8 @@ int plan_column_sweeps(bbp_lattice* L, Program& pr, std::vector<ColumnSweep>& cs
             const bool edgeA = i == 0, edgeB = i == n;
             mb.AR.push_back(edgeA ? L->one_lp : lp_alloc(cer[i]));
             mb.AK.push_back(edgeA ? L->one_lp : lp_alloc(cek[i]));
-            mb.BR.push_back(edgeB ? L->one_lp : lp_alloc(cer[i]));
-            mb.BK.push_back(edgeB ? L->one_lp : lp_alloc(cek[i]));
+            mb.BR.push_back(edgeB ? L->one_lp_b : lp_alloc(cer[i]));
+            mb.BK.push_back(edgeB ? L->one_lp_b : lp_alloc(cek[i]));
         }
         mb.T1 = lp_alloc(ct1);
         mb.T2a = lp_alloc(ct2a);
@@ -353,14 +353,16 @@ int plan_column_sweeps(bbp_lattice* L, Program& pr, std::vector<ColumnSweep>& cs
             r.dst = P(dst);
             r.src_kind = 0;
             r.dst_kind = cx.lpk;
-            if (order == 0) {  // XL[x2][p][pad x]
+            if (order == 0) {  // XL[x2][p][pad x]  (B operand of K2)
                 r.d[0] = v.b; r.d[1] = v.k; r.d[2] = v.a; r.d[3] = 1;
                 r.ss[0] = v.sb; r.ss[1] = v.sk; r.ss[2] = v.sa;
                 r.ds[0] = (long long)v.k * pad(v.a); r.ds[1] = pad(v.a); r.ds[2] = 1;
-            } else {  // XR[x][p][pad x2]
+                r.x3 = cx.x3 ? 2 : 0; r.kseg = v.a;
+            } else {  // XR[x][p][pad x2]  (A operand of K2r)
                 r.d[0] = v.a; r.d[1] = v.k; r.d[2] = v.b; r.d[3] = 1;
                 r.ss[0] = v.sa; r.ss[1] = v.sk; r.ss[2] = v.sb;
                 r.ds[0] = (long long)v.k * pad(v.b); r.ds[1] = pad(v.b); r.ds[2] = 1;
+                r.x3 = cx.x3 ? 1 : 0; r.kseg = v.b;
             }
             rt.push_back(r);
         };
@@ -374,10 +376,12 @@ int plan_column_sweeps(bbp_lattice* L, Program& pr, std::vector<ColumnSweep>& cs
                 r.d[0] = o.w2; r.d[1] = o.q; r.d[2] = o.w; r.d[3] = o.p;
                 r.ss[0] = o.sw2; r.ss[1] = o.sq; r.ss[2] = o.sw; r.ss[3] = o.sp;
                 r.ds[0] = (long long)o.q * pad((long long)o.w * o.p); r.ds[1] = pad((long long)o.w * o.p); r.ds[2] = o.p; r.ds[3] = 1;
+                r.x3 = cx.x3 ? 2 : 0; r.kseg = (long long)o.w * o.p;  // B operand of K3
             } else {  // OR[w][q][pad(p w2)]
                 r.d[0] = o.w; r.d[1] = o.q; r.d[2] = o.p; r.d[3] = o.w2;
                 r.ss[0] = o.sw; r.ss[1] = o.sq; r.ss[2] = o.sp; r.ss[3] = o.sw2;
                 r.ds[0] = (long long)o.q * pad((long long)o.p * o.w2); r.ds[1] = pad((long long)o.p * o.w2); r.ds[2] = o.w2; r.ds[3] = 1;
+                r.x3 = cx.x3 ? 2 : 0; r.kseg = (long long)o.p * o.w2;  // B operand of K3r
             }
             rt.push_back(r);
         };
@@ -540,7 +544,7 @@ static int validate(const bbp_lattice_desc* d) {
     if (d->boundary == BBP_INFINITE && (d->bx % d->Lx || d->by % d->Ly))
         return fail(BBP_ERR_INVALID, "infinite block must be a multiple of the unit cell");
     if (d->dtype < 0 || d->dtype > 3) return fail(BBP_ERR_INVALID, "unknown dtype");
-    if (d->prec < 0 || d->prec > 2) return fail(BBP_ERR_INVALID, "unknown precision");
+    if (d->prec < 0 || d->prec > 3) return fail(BBP_ERR_INVALID, "unknown precision");
     if (d->hermitian_basis != 0 && d->hermitian_basis != 1) return fail(BBP_ERR_INVALID, "hermitian_basis must be 0 or 1");
     if (d->fit_max_sweeps < 1 || d->fit_max_sweeps > 64) return fail(BBP_ERR_INVALID, "fit_max_sweeps must be 1..64");
     if (d->bx > 16 || d->by > 16) return fail(BBP_ERR_INVALID, "block sides are limited to 16 sites");
@@ -622,13 +626,15 @@ int bbp::plan_lattice(const bbp_lattice_desc* desc, bbp_lattice** out) {
         L->mixed = true;
         MixCtx& cx = L->cx;
         cx.ss = L->ss;
-        cx.tck = desc->prec == BBP_PREC_TF32 ? 0 : 1;
+        cx.tck = desc->prec == BBP_PREC_BF16 ? 1 : 0;
+        cx.x3 = desc->prec == BBP_PREC_TF32X3;
         cx.esz = cx.tck == 0 ? 4 : 2;
         cx.pe = 16 / cx.esz;
         cx.lpk = cx.tck == 0 ? 4 : 3;
         cx.tco = cx.tck == 0 ? 1 : 2;
         pr.tc_kind = cx.tck;
         L->one_lp = pr.arena_alloc(16);
+        L->one_lp_b = cx.x3 ? pr.arena_alloc(16) : L->one_lp;
         const size_t errw = pr.arena_alloc(sizeof(int));
         L->d_tcerr = (int*)(uintptr_t)errw;
         for (int t = 0; t < L->ntens; ++t) {
@@ -723,8 +729,12 @@ int bbp_create_lattice(const bbp_lattice_desc* desc, bbp_lattice** out) {
     if (e == cudaSuccess && L->mixed) {
         static const float one_f[4] = {1.0f, 0.0f, 0.0f, 0.0f};
         static const unsigned short one_b[8] = {0x3F80, 0, 0, 0, 0, 0, 0, 0};
-        e = cudaMemcpyAsync(base + L->one_lp, L->cx.tck == 0 ? (const void*)one_f : (const void*)one_b, 16,
-                            cudaMemcpyHostToDevice, L->stream);
+        // split TF32 rows of the constant 1 (K = 1): A [hi|lo|hi] = [1|0|1], B [hi|hi|lo] = [1|1|0]
+        static const float one_xa[4] = {1.0f, 0.0f, 1.0f, 0.0f}, one_xb[4] = {1.0f, 1.0f, 0.0f, 0.0f};
+        const void* src = L->cx.x3 ? (const void*)one_xa : L->cx.tck == 0 ? (const void*)one_f : (const void*)one_b;
+        e = cudaMemcpyAsync(base + L->one_lp, src, 16, cudaMemcpyHostToDevice, L->stream);
+        if (e == cudaSuccess && L->cx.x3)
+            e = cudaMemcpyAsync(base + L->one_lp_b, one_xb, 16, cudaMemcpyHostToDevice, L->stream);
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(L->stream);
     if (e != cudaSuccess) {
@@ -859,12 +869,14 @@ int bbp_set_tensors(bbp_lattice* L, const void* data, int on_device) {
                         r.d[0] = o.w2; r.d[1] = o.q; r.d[2] = o.w; r.d[3] = o.p;
                         r.ss[0] = o.sw2; r.ss[1] = o.sq; r.ss[2] = o.sw; r.ss[3] = o.sp;
                         r.ds[0] = (long long)o.q * wp; r.ds[1] = wp; r.ds[2] = o.p; r.ds[3] = 1;
+                        r.x3 = cx.x3 ? 2 : 0; r.kseg = (long long)o.w * o.p;  // B operand of K3
                     } else {
                         r.dst = base + L->ER_off[t][dir];
                         const long long pw = padded(cx, (long long)o.p * o.w2);
                         r.d[0] = o.w; r.d[1] = o.q; r.d[2] = o.p; r.d[3] = o.w2;
                         r.ss[0] = o.sw; r.ss[1] = o.sq; r.ss[2] = o.sp; r.ss[3] = o.sw2;
                         r.ds[0] = (long long)o.q * pw; r.ds[1] = pw; r.ds[2] = o.w2; r.ds[3] = 1;
+                        r.x3 = cx.x3 ? 2 : 0; r.kseg = (long long)o.p * o.w2;  // B operand of K3r
                     }
                     mx = std::max(mx, (long long)o.w * o.p * o.q * o.w2);
                     rt.push_back(r);

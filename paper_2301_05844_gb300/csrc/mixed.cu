@@ -23,7 +23,12 @@
 
 namespace bbp {
 
-long long padded(const MixCtx& cx, long long x) { return (x + cx.pe - 1) / cx.pe * cx.pe; }
+// Row pitch of a K-major operand with K = x: three K-segments per row for split TF32
+// operands, padded to 16 bytes.
+long long padded(const MixCtx& cx, long long x) {
+    const long long k = cx.x3 ? 3 * x : x;
+    return (k + cx.pe - 1) / cx.pe * cx.pe;
+}
 
 void Program::tc_step(std::vector<TCTask>& ts, std::vector<TCSpec>& sp, int kind) {
     if (ts.empty()) return;
@@ -77,16 +82,31 @@ struct TB {  // tasks of one tensor-core step
     std::vector<TCSpec> sp;
 };
 
+// Role of a low-precision destination in its consumer GEMM (split TF32 rows: A [hi|lo|hi],
+// B [hi|hi|lo]); the segment length is the consumer's K.
+constexpr int ROLE_A = 1, ROLE_B = 2;
+struct Dst {
+    int role = 0;
+    long long kseg = 0;
+};
+
 // C = A B^T with A (a_rows x K, leading dim a_ld) and B (b_rows x K, b_ld), both K-major;
-// result element (m, n), m = m1*M2 + m2, n = n1*N2 + n2, goes to C (and C2).
-void add(Program& pr, TB& tb, size_t a_off, long long a_rows, long long K, long long a_ld, size_t b_off,
-         long long b_rows, long long b_ld, int M2, int N2, void* C, long long cm1, long long cm2, long long cn1,
-         long long cn2, void* C2, long long dm1, long long dm2, long long dn1, long long dn2, int out_kind,
-         const int* active, double alg_flops) {
+// result element (m, n), m = m1*M2 + m2, n = n1*N2 + n2, goes to C (and C2).  With split
+// TF32 operands the GEMM runs over the three K-segments of every row (3K).
+void add(Program& pr, const MixCtx& cx, TB& tb, size_t a_off, long long a_rows, long long K, long long a_ld,
+         size_t b_off, long long b_rows, long long b_ld, int M2, int N2, void* C, long long cm1, long long cm2,
+         long long cn1, long long cn2, void* C2, long long dm1, long long dm2, long long dn1, long long dn2,
+         int out_kind, const int* active, double alg_flops, Dst dc = Dst(), Dst dd = Dst()) {
+    if (cx.x3) K *= 3;
     TCTask t{};
     t.M = (int)a_rows;
     t.N = (int)b_rows;
     t.K = (int)K;
+    if (cx.x3) {
+        t.x3 = dc.role | (dd.role << 2);
+        t.kseg = dc.kseg;
+        t.kseg2 = dd.kseg;
+    }
     t.M2 = M2;
     t.N2 = N2;
     t.out_kind = out_kind;
@@ -124,24 +144,25 @@ void lr(Program& pr, const MixCtx& cx, TB& tb, const FitSpec& f, int i, int stag
     const int lo = cx.tco;
     if (stage == 0) {  // T1[y][x2][pad(w p)] = sum_x ER_A[(y,w)][x] XL[(x2,p)][x]
         const long long WP = padded(cx, d.w * d.p);
-        add(pr, tb, m.AR[i], d.y * d.w, d.x, padded(cx, d.x), m.XL[i], d.x2 * d.p, padded(cx, d.x), (int)d.w, (int)d.p,
-            P(m.T1), d.x2 * WP, d.p, WP, 1, nullptr, 0, 0, 0, 0, lo, act, 2.0 * d.y * d.w * d.x * d.p * d.x2);
+        add(pr, cx, tb, m.AR[i], d.y * d.w, d.x, padded(cx, d.x), m.XL[i], d.x2 * d.p, padded(cx, d.x), (int)d.w, (int)d.p,
+            P(m.T1), d.x2 * WP, d.p, WP, 1, nullptr, 0, 0, 0, 0, lo, act, 2.0 * d.y * d.w * d.x * d.p * d.x2,
+            Dst{ROLE_A, d.w * d.p});
     } else if (stage == 1) {  // T2 = T1[(y,x2)][(w p)] OL[(w2,q)][(w p)]
         const long long WP = padded(cx, d.w * d.p), WX2 = padded(cx, d.w2 * d.x2), YQ = padded(cx, d.y * d.q);
-        add(pr, tb, m.T1, d.y * d.x2, d.w * d.p, WP, m.OL[i], d.w2 * d.q, WP, (int)d.x2, (int)d.q,
+        add(pr, cx, tb, m.T1, d.y * d.x2, d.w * d.p, WP, m.OL[i], d.w2 * d.q, WP, (int)d.x2, (int)d.q,
             P(m.T2a), d.q * WX2, 1, d.x2, WX2,                 // T2a[y][q][pad(w2 x2)]
             P(m.T2b), d.q, YQ, d.x2 * YQ, 1,                    // T2b[w2][x2][pad(y q)]
-            lo, act, 2.0 * d.y * d.x2 * d.w * d.p * d.q * d.w2);
+            lo, act, 2.0 * d.y * d.x2 * d.w * d.p * d.q * d.w2, Dst{ROLE_A, d.w2 * d.x2}, Dst{ROLE_B, d.y * d.q});
     } else if (stage == 2) {  // Yt[y][q][y2] = T2a[(y,q)][(w2 x2)] EK_B[y2][(w2 x2)]  (FP32)
         const long long WX2 = padded(cx, d.w2 * d.x2);
-        add(pr, tb, m.T2a, d.y * d.q, d.w2 * d.x2, WX2, m.BK[i + 1], d.y2, WX2, (int)d.q, (int)d.y2,
+        add(pr, cx, tb, m.T2a, d.y * d.q, d.w2 * d.x2, WX2, m.BK[i + 1], d.y2, WX2, (int)d.q, (int)d.y2,
             P(m.Ytf), d.q * d.y2, d.y2, 0, 1, nullptr, 0, 0, 0, 0, 0, act, 2.0 * d.y * d.q * d.w2 * d.x2 * d.y2);
     } else {  // A_{i+1} = YT[y2][(y q)] T2b[(w2,x2)][(y q)] in both env forms
         const long long YQ = padded(cx, d.y * d.q), X2 = padded(cx, d.x2), WX2 = padded(cx, d.w2 * d.x2);
-        add(pr, tb, m.YT[i], d.y2, d.y * d.q, YQ, m.T2b, d.w2 * d.x2, YQ, (int)d.y2, (int)d.x2,
+        add(pr, cx, tb, m.YT[i], d.y2, d.y * d.q, YQ, m.T2b, d.w2 * d.x2, YQ, (int)d.y2, (int)d.x2,
             P(m.AR[i + 1]), 0, d.w2 * X2, X2, 1,                // ER[y2][w2][pad x2]
             P(m.AK[i + 1]), 0, WX2, d.x2, 1,                    // EK[y2][pad(w2 x2)]
-            lo, act, 2.0 * d.y2 * d.y * d.q * d.w2 * d.x2);
+            lo, act, 2.0 * d.y2 * d.y * d.q * d.w2 * d.x2, Dst{ROLE_A, d.x2}, Dst{ROLE_A, d.w2 * d.x2});
     }
 }
 
@@ -152,30 +173,30 @@ void rl(Program& pr, const MixCtx& cx, TB& tb, const FitSpec& f, int i, int stag
     const int lo = cx.tco;
     if (stage == 0) {  // T1[y2][x][pad(p w2)] = XR[(x,p)][x2] ER_B[(y2,w2)][x2]
         const long long PW = padded(cx, d.p * d.w2);
-        add(pr, tb, m.XR[i], d.x * d.p, d.x2, padded(cx, d.x2), m.BR[i + 1], d.y2 * d.w2, padded(cx, d.x2), (int)d.p,
+        add(pr, cx, tb, m.XR[i], d.x * d.p, d.x2, padded(cx, d.x2), m.BR[i + 1], d.y2 * d.w2, padded(cx, d.x2), (int)d.p,
             (int)d.w2, P(m.T1), PW, d.w2, d.x * PW, 1, nullptr, 0, 0, 0, 0, lo, act,
-            2.0 * d.x * d.p * d.x2 * d.y2 * d.w2);
+            2.0 * d.x * d.p * d.x2 * d.y2 * d.w2, Dst{ROLE_A, d.p * d.w2});
     } else if (stage == 1) {  // T2 = T1[(y2,x)][(p w2)] OR[(w,q)][(p w2)]
         const long long PW = padded(cx, d.p * d.w2), WX = padded(cx, d.w * d.x), QY2 = padded(cx, d.q * d.y2);
-        add(pr, tb, m.T1, d.y2 * d.x, d.p * d.w2, PW, m.OR[i], d.w * d.q, PW, (int)d.x, (int)d.q,
+        add(pr, cx, tb, m.T1, d.y2 * d.x, d.p * d.w2, PW, m.OR[i], d.w * d.q, PW, (int)d.x, (int)d.q,
             P(m.T2a), WX, 1, d.x, d.y2 * WX,                    // T2a[q][y2][pad(w x)]
             P(m.T2b), d.q, QY2, d.x * QY2, 1,                   // T2b[w][x][pad(y2 q)]
-            lo, act, 2.0 * d.x * d.y2 * d.p * d.w2 * d.w * d.q);
+            lo, act, 2.0 * d.x * d.y2 * d.p * d.w2 * d.w * d.q, Dst{ROLE_B, d.w * d.x}, Dst{ROLE_B, d.q * d.y2});
     } else if (stage == 2) {  // Yt[y][q][y2] = EK_A[y][(w x)] T2a[(q,y2)][(w x)]
         const long long WX = padded(cx, d.w * d.x);
         if (final_)
-            add(pr, tb, m.AK[i], d.y, d.w * d.x, WX, m.T2a, d.q * d.y2, WX, (int)d.y, (int)d.y2,
+            add(pr, cx, tb, m.AK[i], d.y, d.w * d.x, WX, m.T2a, d.q * d.y2, WX, (int)d.y, (int)d.y2,
                 P(f.Y[i] * (size_t)cx.ss), 0, d.q * d.y2, d.y2, 1, nullptr, 0, 0, 0, 0, 3, act,
                 2.0 * d.y * d.w * d.x * d.q * d.y2);
         else
-            add(pr, tb, m.AK[i], d.y, d.w * d.x, WX, m.T2a, d.q * d.y2, WX, (int)d.y, (int)d.y2,
+            add(pr, cx, tb, m.AK[i], d.y, d.w * d.x, WX, m.T2a, d.q * d.y2, WX, (int)d.y, (int)d.y2,
                 P(m.Ytf), 0, d.q * d.y2, d.y2, 1, nullptr, 0, 0, 0, 0, 0, act, 2.0 * d.y * d.w * d.x * d.q * d.y2);
     } else {  // B_i = YS[y][(y2 q)] T2b[(w,x)][(y2 q)] in both env forms
         const long long QY2 = padded(cx, d.q * d.y2), X = padded(cx, d.x), WX = padded(cx, d.w * d.x);
-        add(pr, tb, m.YS[i], d.y, d.q * d.y2, QY2, m.T2b, d.w * d.x, QY2, (int)d.y, (int)d.x,
+        add(pr, cx, tb, m.YS[i], d.y, d.q * d.y2, QY2, m.T2b, d.w * d.x, QY2, (int)d.y, (int)d.x,
             P(m.BR[i]), 0, d.w * X, X, 1,                       // ER[y][w][pad x]
             P(m.BK[i]), 0, WX, d.x, 1,                          // EK[y][pad(w x)]
-            lo, act, 2.0 * d.y * d.q * d.y2 * d.w * d.x);
+            lo, act, 2.0 * d.y * d.q * d.y2 * d.w * d.x, Dst{ROLE_B, d.x}, Dst{ROLE_B, d.w * d.x});
     }
 }
 
@@ -194,12 +215,14 @@ QRTask qr_mixed(const MixCtx& cx, const FitSpec& f, int i, bool lq, size_t loss_
         t.in_rs = y2; t.in_cs = 1; t.out_rs = y2; t.out_cs = 1; t.conj_io = 0;
         t.out2 = P(f.mx.YT[i]);
         t.out2_M2 = 1; t.out2_rs = 1; t.out2_rs2 = 0; t.out2_cs = padded(cx, y * q);   // YT[y2][pad(y q)]
+        t.out2_x3 = cx.x3 ? ROLE_A : 0; t.out2_kseg = y * q;
     } else {
         t.m = (int)(q * y2); t.n = (int)y;
         t.in_rs = 1; t.in_cs = q * y2; t.out_rs = 1; t.out_cs = q * y2; t.conj_io = 1;
         t.out2 = P(f.mx.YS[i]);
         // row i = (q, y2) of the LQ matrix goes to YS[y][pad(y2 q)]
         t.out2_M2 = (int)y2; t.out2_rs = 1; t.out2_rs2 = q; t.out2_cs = padded(cx, q * y2);
+        t.out2_x3 = cx.x3 ? ROLE_A : 0; t.out2_kseg = q * y2;
     }
     return t;
 }
@@ -241,6 +264,8 @@ void emit_fits_mixed(Program& pr, const MixCtx& cx, std::vector<FitSpec*>& fits,
                 r.d[0] = (int)y; r.d[1] = (int)q; r.d[2] = (int)y2; r.d[3] = 1;
                 r.ss[0] = q * y2; r.ss[1] = y2; r.ss[2] = 1;
                 r.ds[0] = padded(cx, q * y2); r.ds[1] = 1; r.ds[2] = q;  // YS[y][pad(y2 q)]
+                r.x3 = cx.x3 ? ROLE_A : 0;
+                r.kseg = q * y2;
                 r.src_kind = 0;
                 r.dst_kind = cx.lpk;
                 rl_.push_back(r);

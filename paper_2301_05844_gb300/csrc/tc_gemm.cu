@@ -170,9 +170,31 @@ __device__ __forceinline__ void store_vec(void* out, long long o, int kind, cons
 
 constexpr int EC = 64;  // epilogue chunk (columns)
 
+// Split TF32 destination (x3 = 1: A rows [hi|lo|hi], 2: B rows [hi|hi|lo], segments kseg
+// elements apart): hi = tf32(x), lo = tf32(x - hi).
+__device__ __forceinline__ void store_split1(float* out, long long o, float x, int x3, long long kseg) {
+    const float hi = round_tf32(x), lo = round_tf32(x - hi);
+    out[o] = hi;
+    out[o + kseg] = x3 == 1 ? lo : hi;
+    out[o + 2 * kseg] = x3 == 1 ? hi : lo;
+}
+__device__ __forceinline__ void store_split4(float* out, long long o, const float* x, int x3, long long kseg) {
+    float hi[4], lo[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        hi[j] = round_tf32(x[j]);
+        lo[j] = round_tf32(x[j] - hi[j]);
+    }
+    const float4 H = make_float4(hi[0], hi[1], hi[2], hi[3]), Lo = make_float4(lo[0], lo[1], lo[2], lo[3]);
+    *(float4*)(out + o) = H;
+    *(float4*)(out + o + kseg) = x3 == 1 ? Lo : H;
+    *(float4*)(out + o + 2 * kseg) = x3 == 1 ? H : Lo;
+}
+
 __device__ __forceinline__ void epilogue_dest(const float* tile, long long* roff, long long* coff, int rows, int ncols,
                                               int m0, int n0, int M2, int N2, long long sm1, long long sm2,
-                                              long long sn1, long long sn2, int kind, float alpha, void* out) {
+                                              long long sn1, long long sn2, int kind, float alpha, void* out, int x3,
+                                              long long kseg) {
     constexpr int P = EC + 1;
     const int tid = threadIdx.x;
     __syncthreads();  // the previous destination has finished with the offsets
@@ -187,20 +209,28 @@ __device__ __forceinline__ void epilogue_dest(const float* tile, long long* roff
     __syncthreads();
     const int esz = out_esz(kind), VW = 16 / esz;
     const uintptr_t base = (uintptr_t)out;
+    // a split destination vectorises only if every segment start stays 16-byte aligned
+    const bool segs_aligned = !x3 || ((kseg * esz) & 15) == 0;
     float x[8];
     if (sn2 == 1) {
         const int G = (ncols + VW - 1) / VW;
         for (int it = tid; it < rows * G; it += 128) {
             const int r = it / G, c0 = (it - r * G) * VW;
             const long long o = roff[r] + coff[c0];
-            bool vec = c0 + VW <= ncols && ((base + (uintptr_t)(o * esz)) & 15) == 0 && coff[c0 + VW - 1] == coff[c0] + VW - 1;
+            bool vec = segs_aligned && c0 + VW <= ncols && ((base + (uintptr_t)(o * esz)) & 15) == 0 &&
+                       coff[c0 + VW - 1] == coff[c0] + VW - 1;
             if (vec) {
 #pragma unroll
                 for (int j = 0; j < 8; ++j)
                     if (j < VW) x[j] = tile[r * P + c0 + j] * alpha;
-                store_vec(out, o, kind, x);
+                if (x3) store_split4((float*)out, o, x, x3, kseg);
+                else store_vec(out, o, kind, x);
             } else {
-                for (int j = 0; j < VW && c0 + j < ncols; ++j) store_out(out, roff[r] + coff[c0 + j], kind, tile[r * P + c0 + j] * alpha);
+                for (int j = 0; j < VW && c0 + j < ncols; ++j) {
+                    const float xv = tile[r * P + c0 + j] * alpha;
+                    if (x3) store_split1((float*)out, roff[r] + coff[c0 + j], xv, x3, kseg);
+                    else store_out(out, roff[r] + coff[c0 + j], kind, xv);
+                }
             }
         }
     } else if (sm2 == 1) {
@@ -208,20 +238,28 @@ __device__ __forceinline__ void epilogue_dest(const float* tile, long long* roff
         for (int it = tid; it < ncols * G; it += 128) {
             const int c = it / G, r0 = (it - c * G) * VW;
             const long long o = roff[r0] + coff[c];
-            bool vec = r0 + VW <= rows && ((base + (uintptr_t)(o * esz)) & 15) == 0 && roff[r0 + VW - 1] == roff[r0] + VW - 1;
+            bool vec = segs_aligned && r0 + VW <= rows && ((base + (uintptr_t)(o * esz)) & 15) == 0 &&
+                       roff[r0 + VW - 1] == roff[r0] + VW - 1;
             if (vec) {
 #pragma unroll
                 for (int j = 0; j < 8; ++j)
                     if (j < VW) x[j] = tile[(r0 + j) * P + c] * alpha;
-                store_vec(out, o, kind, x);
+                if (x3) store_split4((float*)out, o, x, x3, kseg);
+                else store_vec(out, o, kind, x);
             } else {
-                for (int j = 0; j < VW && r0 + j < rows; ++j) store_out(out, roff[r0 + j] + coff[c], kind, tile[(r0 + j) * P + c] * alpha);
+                for (int j = 0; j < VW && r0 + j < rows; ++j) {
+                    const float xv = tile[(r0 + j) * P + c] * alpha;
+                    if (x3) store_split1((float*)out, roff[r0 + j] + coff[c], xv, x3, kseg);
+                    else store_out(out, roff[r0 + j] + coff[c], kind, xv);
+                }
             }
         }
     } else {
         for (int it = tid; it < rows * ncols; it += 128) {
             const int c = it / rows, r = it - c * rows;
-            store_out(out, roff[r] + coff[c], kind, tile[r * P + c] * alpha);
+            const float xv = tile[r * P + c] * alpha;
+            if (x3) store_split1((float*)out, roff[r] + coff[c], xv, x3, kseg);
+            else store_out(out, roff[r] + coff[c], kind, xv);
         }
     }
 }
@@ -318,8 +356,9 @@ __global__ void __launch_bounds__(128) k_tc_gemm(const TCTask* __restrict__ task
                 void* out = dst ? t.C2 : t.C;
                 const long long sm1 = dst ? t.d_m1 : t.c_m1, sm2 = dst ? t.d_m2 : t.c_m2;
                 const long long sn1 = dst ? t.d_n1 : t.c_n1, sn2 = dst ? t.d_n2 : t.c_n2;
+                const int x3 = (t.x3 >> (2 * dst)) & 3;
                 epilogue_dest(tile, roff, coff, rows, cn, m0, n0 + c0, t.M2, t.N2, sm1, sm2, sn1, sn2, t.out_kind,
-                              t.alpha, out);
+                              t.alpha, out, x3, dst ? t.kseg2 : t.kseg);
             }
         }
     }

@@ -11,7 +11,9 @@ namespace bbp {
 // The result is written through the two-level map
 //   C[(m/M2)*c_m1 + (m%M2)*c_m2 + (n/N2)*c_n1 + (n%N2)*c_n2]
 // and, if C2 is set, also to C2 through (d_*).  out_kind: 0 FP32, 1 FP32 rounded to
-// TF32, 2 BF16.
+// TF32, 2 BF16, 3 FP64.  x3 (bits 0-1 for C, 2-3 for C2): the destination is a split TF32
+// operand whose rows hold K-segments [hi|lo|hi] (1, A operand) or [hi|hi|lo] (2, B
+// operand) kseg (kseg2) elements apart; the element offset is that of the first segment.
 struct TCTask {
     CUtensorMap map_a;
     CUtensorMap map_b;
@@ -22,7 +24,8 @@ struct TCTask {
     void* C2;
     const int* active;
     float alpha;
-    int pad;
+    int x3;
+    long long kseg, kseg2;
 };
 
 cudaError_t tc_prepare();

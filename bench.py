@@ -4,10 +4,11 @@
 One step = one synchronous blockBP sweep (Eq. 1): every directed block message of
 the lattice recomputed by the zip-up bMPS fits, normalised, and the fixed-point
 residual reduced.  Default workload: the 12x12 PEPS, d=2, D=3, near-product
-tensors, 3x3-site blocks (16 blocks, 48 messages), chi=32, TF32 contractions with
-FP64 QR/LQ, fit tol 1e-6 / 10 sweeps, residual target 1e-8.
+tensors, 3x3-site blocks (16 blocks, 48 messages), chi=32, FP32-level contractions on
+TF32 tensor cores (split operands) with FP64 QR/LQ, fit tol 1e-6 / 10 sweeps, residual
+target 1e-8.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--prec tf32|bf16|fp64]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--prec tf32x3|tf32|bf16|fp64]
   python bench.py --impl reference      # the FP64 CPU oracle, same workload
   python bench.py --serve [--requests N] # served mix: Poisson arrivals of whole solves
 

@@ -118,7 +118,8 @@ def config(k: int) -> dict:
     """The five benchmark workloads (seed = config number).
 
     1: 4x4 OBC, d=2, D=2, U[0,1]+0.1N, 2x2 blocks, chi=16, FP64.
-    2: 12x12 OBC, d=2, D=3, near-product (+0.05N), 3x3 blocks, chi=32, FP32/TF32, residual 1e-8.
+    2: 12x12 OBC, d=2, D=3, near-product (+0.05N), 3x3 blocks, chi=32, residual 1e-8; FP32-level
+       contractions on TF32 tensor cores (split operands, "tf32x3").
     3: infinite 2x2 cell, d=2, D=4, complex64 N(0,1)/sqrt(D), 4x4 block, chi=64, BF16.
     4: 32x32 OBC, d=2, D=5, U[0,1]+0.1N as float32, 4x4 blocks, chi=96, TF32.
     6: 20x20 OBC, d=2, D=4, U[0,1]+0.1N, 4x4 blocks (80 messages), chi=64, BF16 -- the
@@ -128,8 +129,8 @@ def config(k: int) -> dict:
         return dict(name="peps4x4_D2_chi16_fp64", Lx=4, Ly=4, d=2, D=2, bx=2, by=2, chi=16,
                     boundary="obc", tensors=uniform_noise_peps(4, 4, 2, 2, seed=1), prec="fp64")
     if k == 2:
-        return dict(name="peps12x12_D3_chi32_tf32", Lx=12, Ly=12, d=2, D=3, bx=3, by=3, chi=32,
-                    boundary="obc", tensors=near_product_peps(12, 12, 2, 3, seed=2), prec="tf32",
+        return dict(name="peps12x12_D3_chi32", Lx=12, Ly=12, d=2, D=3, bx=3, by=3, chi=32,
+                    boundary="obc", tensors=near_product_peps(12, 12, 2, 3, seed=2), prec="tf32x3",
                     tol=1e-8)
     if k == 3:
         return dict(name="ipeps2x2_D4_chi64_bf16", Lx=2, Ly=2, d=2, D=4, bx=4, by=4, chi=64,

@@ -248,6 +248,9 @@ def run_ours(args):
         roofline = {"bound": bound, "kernel": dom, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
                     "frac": ach / peak, "traffic": None, "peak_source": note,
                     "classes_ms_per_sweep": {k: round(v["ms"], 4) for k, v in classes.items()},
+                    # algorithmic TFLOP/s of each class over its replayed launches
+                    "classes_tflops": {k: round(v["flops"] / (v["ms"] / 1e3) / 1e12, 4) for k, v in classes.items()
+                                       if v["ms"] > 0},
                     "classes_launches_per_sweep": {k: v["launches"] for k, v in classes.items()}}
 
     # the plain FP64 GPU path on the same workload, same number of sweeps

@@ -161,3 +161,21 @@ def standard_terms(Lx, Ly):
             if r + 1 < Ly:
                 terms.append([(s, SIGMA_Z), (s + Lx, SIGMA_Z)])
     return terms
+
+
+def ising_peps(beta, h=0.0):
+    """One site tensor (1x1 unit cell, d=2, D=2) of the PEPS sum_s exp(beta/2 sum_<ij> s_i s_j) |s>.
+
+    Its norm <psi|psi> is the partition function of the classical 2D Ising model at
+    inverse temperature beta, and <psi|sz|psi>/<psi|psi> is that model's magnetisation.
+    The bond weight W[s,s'] = exp(beta s s' / 2) is split as W = M M^T (M the symmetric
+    square root) and each site carries M[s, .] on its four legs.  h != 0 multiplies the
+    amplitudes of up / down by (1 + h) / (1 - h), a small field that selects the up
+    ordered state."""
+    W = np.array([[np.exp(beta / 2), np.exp(-beta / 2)], [np.exp(-beta / 2), np.exp(beta / 2)]])
+    ev, U = np.linalg.eigh(W)
+    M = U @ np.diag(np.sqrt(ev)) @ U.T
+    T = np.zeros((2, 2, 2, 2, 2))
+    for p in range(2):
+        T[p] = np.einsum("u,l,d,r->uldr", M[p], M[p], M[p], M[p]) * (1.0 + (h if p == 0 else -h))
+    return T

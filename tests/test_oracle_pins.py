@@ -301,3 +301,38 @@ def test_warm_start_reaches_the_same_fixed_point():
         lat.run(n_sweeps=12)
         vals.append(lat.expect(terms))
     assert np.max(np.abs(vals[0] - vals[1])) < 1e-10
+
+
+def _onsager(beta):
+    """Spontaneous magnetisation of the 2D square-lattice Ising model (Onsager, Yang):
+    (1 - sinh(2 beta)^-4)^(1/8) below the critical temperature, 0 above it."""
+    s = math.sinh(2 * beta)
+    return (1 - s ** -4) ** 0.125 if s > 1 else 0.0
+
+
+def _ising_m(beta, b, h, chi=16):
+    T = I.ising_peps(beta, h=h)
+    o = ob.Lattice(1, 1, 2, 2, b, b, [T], boundary="infinite", chi=chi, fit_tol=1e-10, fit_max_sweeps=20, seed=3,
+                   init_mode=1)
+    r, k, conv = o.run(tol=1e-12, max_sweeps=80)
+    assert conv
+    c = (b // 2) * b + b // 2 - 1  # a site next to the block centre
+    return o.expect([[(c, I.SIGMA_Z)]])[0].real
+
+
+def test_infinite_ising_magnetisation_against_onsager():
+    """The infinite path on the PEPS whose norm is the classical Ising partition function
+    (Sec. "The blockBP algorithm": one block messaging itself): deep in the ordered phase
+    <sz> approaches Onsager's magnetisation, about tenfold closer per block-size step
+    (measured 5.8e-4, 6.0e-5, 7.5e-6 for blocks 2, 4, 6 at beta = 0.6); in the disordered
+    phase without a field <sz> vanishes.  The model is isotropic, so this does not tell
+    the four directions apart (the gauge-dressed infinite cell pins that); it pins the
+    feedback of the block's own messages on the infinite path, the fits and the read-out
+    against the exact thermodynamics (a planted mistake that stops feeding the messages
+    back fails it)."""
+    beta = 0.6
+    err = [abs(_ising_m(beta, b, 1e-6) - _onsager(beta)) for b in (2, 4, 6)]
+    assert err[0] < 1e-3 and err[1] < 1.5e-4 and err[2] < 2e-5, err
+    assert err[0] > err[1] > err[2]
+    assert abs(_ising_m(0.7, 4, 1e-6) - _onsager(0.7)) < 1e-5
+    assert abs(_ising_m(0.3, 4, 0.0)) < 1e-5

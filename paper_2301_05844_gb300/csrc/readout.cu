@@ -267,7 +267,17 @@ extern "C" int bbp_expect(bbp_lattice* L, const bbp_term* terms, int n_terms, do
             cs.push_back(s);
         }
     }
-    int rc = plan_column_sweeps(L, pr, cs, ds.fit_max_sweeps, ds.fit_tol, false, false);
+    // The environment columns are fits like those of a sweep.  On a split-TF32 lattice they run
+    // on its tensor-core path (FP32-level contractions, FP64 QR, the same fit-tolerance floor);
+    // TF32 / BF16 lattices keep FP64 fits here, so that the read-out adds no error of its own
+    // at their precision.  The closings and the ratio N_O / N_I are FP64 in every case.
+    const bool tc_env = L->mixed && L->cx.x3;
+    if (tc_env) {
+        pr.tc_kind = L->cx.tck;
+        pr.tc_err = L->d_tcerr;
+    }
+    int rc = plan_column_sweeps(L, pr, cs, ds.fit_max_sweeps, tc_env ? std::max(ds.fit_tol, 3e-3) : ds.fit_tol,
+                                false, tc_env);
     if (rc) return rc;
 
     auto env_site = [&](const Region& R, bool left_env, int c, int i) -> View3 {
@@ -478,19 +488,29 @@ extern "C" int bbp_expect(bbp_lattice* L, const bbp_term* terms, int n_terms, do
     } guard{ro, &pr, st};
     pr.relocate(L->arena, split, ro);
     pr.status = L->d_status;
+    if (tc_env) CKR(pr.encode_maps(L->arena, split, ro));
     CKR(pr.upload_tasks(st));
     CKR(cudaMemsetAsync(ro, 0, ro_bytes, st));
     for (auto& u : uploads) {
         const size_t bytes = u.second.size() * sizeof(double);
         CKR(cudaMemcpyAsync(ro + (u.first * ss - split), u.second.data(), bytes, cudaMemcpyHostToDevice, st));
     }
-    CKR(pr.init_loops(st, false, nullptr));
-    CKR(pr.launch_all(st, nullptr, ds.seed));
+    if (!pr.loop_descs.empty()) {
+        // one graph: each fit loop is a conditional WHILE node that stops when its fits
+        // have converged, instead of launching every loop body its maximum number of times
+        CKR(pr.build_graph(st, nullptr, ds.seed));
+        CKR(cudaGraphLaunch(pr.exec, st));
+    } else {
+        CKR(pr.init_loops(st, false, nullptr));
+        CKR(pr.launch_all(st, nullptr, ds.seed));
+    }
     std::vector<double> res(nclos * (L->cplx ? 2 : 1));
     CKR(cudaMemcpyAsync(res.data(), ro + (results * ss - split), res.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
-    int status = 0;
+    int status = 0, tc_status = 0;
     CKR(cudaMemcpyAsync(&status, L->d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    if (tc_env) CKR(cudaMemcpyAsync(&tc_status, L->d_tcerr, sizeof(int), cudaMemcpyDeviceToHost, st));
     CKR(cudaStreamSynchronize(st));
+    if (tc_status) return fail(BBP_ERR_TIMEOUT, "a tensor-core pipeline wait exceeded its bound");
     L->readout_kernels += pr.kernel_count();
     L->readout_flops += pr.static_flops + pr.gated_flops;
     if (status) return fail(BBP_ERR_NUMERIC, "an environment column has zero or non-finite norm");

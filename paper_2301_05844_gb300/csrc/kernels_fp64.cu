@@ -420,7 +420,59 @@ constexpr size_t QR_SMEM_LIMIT = 200 * 1024;
 // CTA reads v_j and tau_j from the owner's shared memory (distributed shared memory) to
 // update its own columns k > j.  Q is then accumulated backwards column-locally, each CTA
 // reading every v_j from its owner; no CTA leaves before the others have finished reading.
-// Shared memory per CTA: u (m) | W (m x nl) | Q (m x nl) | tau (n) | beta (n) | partial norm.
+// Shared memory per CTA: u (2 x m) | W (m x nl) | Q (m x nl) | tau (n) | beta (n) | partial norm.
+__device__ __forceinline__ void cluster_arrive() { asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory"); }
+__device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory"); }
+
+// Owner CTA of column j: turn its local column col into the scaled reflector v_j (in place,
+// v_j[j] = 1) and record tau_j and beta_j.  xs2_in < 0: compute the sub-diagonal norm here.
+// Called by every thread of the CTA.
+template <typename S>
+__device__ void cluster_reflector(S* col, int j, int m, double xs2_in, double* taus, S* betas, double* redd) {
+    const int tid = threadIdx.x;
+    double xs2 = xs2_in;
+    if (xs2 < 0.0) {
+        xs2 = 0.0;
+        for (int i = j + 1 + tid; i < m; i += 256) xs2 += abs2(col[i]);
+        xs2 = block_sum(xs2, redd);
+    }
+    double xnorm = sqrt(xs2);
+    if (xs2 < 1e-280) {
+        double amax = 0.0;
+        for (int i = j + 1 + tid; i < m; i += 256) amax = fmax(amax, absv(col[i]));
+        amax = block_max(amax, redd);
+        double t2 = 0.0;
+        if (amax > 0.0)
+            for (int i = j + 1 + tid; i < m; i += 256) t2 += abs2(divr(col[i], amax));
+        t2 = block_sum(t2, redd);
+        xnorm = amax > 0.0 ? amax * sqrt(t2) : 0.0;
+    }
+    const S alpha = col[j];
+    const double aa = absv(alpha);
+    __syncthreads();  // every thread has read alpha before column j is overwritten
+    S beta = alpha;
+    double tau = 0.0;
+    if (xnorm > 0.0) {
+        const double nrm = hypot(aa, xnorm);
+        const S ph = aa > 0.0 ? divr(alpha, aa) : one<S>();
+        beta = scal(ph, -nrm);
+        tau = 1.0 + aa / nrm;
+        const double den = aa + nrm;
+        const S cph = conjv(ph);
+        if (den > 1e-290) {
+            const S sc = scal(cph, 1.0 / den);
+            for (int i = j + tid; i < m; i += 256) col[i] = (i == j) ? one<S>() : mul(col[i], sc);
+        } else {
+            for (int i = j + tid; i < m; i += 256) col[i] = (i == j) ? one<S>() : divr(mul(col[i], cph), den);
+        }
+    }
+    if (tid == 0) {
+        taus[j] = tau;
+        betas[j] = beta;
+    }
+    __syncthreads();
+}
+
 template <typename S>
 __global__ void __launch_bounds__(256) k_qr_cluster(const QRTask* __restrict__ tasks, int C) {
     namespace cg = cooperative_groups;
@@ -432,8 +484,8 @@ __global__ void __launch_bounds__(256) k_qr_cluster(const QRTask* __restrict__ t
     const int nl = (n - rank + C - 1) / C;   // local columns j = rank + lc * C
     const int nlmax = (n + C - 1) / C;       // same layout in every CTA of the cluster
     extern __shared__ __align__(16) unsigned char qr_smem[];
-    S* u = (S*)qr_smem;
-    S* W = u + m;
+    S* u = (S*)qr_smem;  // two staging buffers of m entries
+    S* W = u + 2 * m;
     S* Q = W + (size_t)m * nlmax;
     double* taus = (double*)(Q + (size_t)m * nlmax);
     S* betas = (S*)(taus + QR_MAXN);
@@ -459,108 +511,96 @@ __global__ void __launch_bounds__(256) k_qr_cluster(const QRTask* __restrict__ t
         for (int r = 0; r < C; ++r) tot += *cluster.map_shared_rank(part, r);
         *t.loss = -tot;
     }
-    __shared__ double next_x2;  // sub-diagonal norm of the next column, when this CTA owns it
-    bool fused = false;         // uniform over the cluster: the previous step updated column j
+    __shared__ double next_x2;  // sub-diagonal norm of the next column, from its owner's update
+    // Forward: the owner of column j+1 updates that column with v_j first, forms v_{j+1} and
+    // arrives on the split cluster barrier; the other CTAs arrive as soon as they hold v_j.
+    // Everyone then applies v_j to its remaining columns and waits for v_{j+1} only before
+    // the next step, so the bulk updates overlap the next reflector's critical path.
+    if (rank == 0) cluster_reflector(W, 0, m, -1.0, taus, betas, redd);
+    cluster_arrive();
     for (int j = 0; j < n; ++j) {
-        const int owner = j % C, lj = j / C;
-        if (rank == owner) {
-            S* col = W + (size_t)lj * m;
-            double xs2;
-            if (fused) {
-                xs2 = next_x2;
-            } else {
-                xs2 = 0.0;
-                for (int i = j + 1 + tid; i < m; i += 256) xs2 += abs2(col[i]);
-                xs2 = block_sum(xs2, redd);
-            }
-            double xnorm = sqrt(xs2);
-            if (xs2 < 1e-280) {
-                double amax = 0.0;
-                for (int i = j + 1 + tid; i < m; i += 256) amax = fmax(amax, absv(col[i]));
-                amax = block_max(amax, redd);
-                double t2 = 0.0;
-                if (amax > 0.0)
-                    for (int i = j + 1 + tid; i < m; i += 256) t2 += abs2(divr(col[i], amax));
-                t2 = block_sum(t2, redd);
-                xnorm = amax > 0.0 ? amax * sqrt(t2) : 0.0;
-            }
-            const S alpha = col[j];
-            const double aa = absv(alpha);
-            __syncthreads();  // every thread has read alpha before column j is overwritten
-            S beta = alpha;
-            double tau = 0.0;
-            if (xnorm > 0.0) {
-                const double nrm = hypot(aa, xnorm);
-                const S ph = aa > 0.0 ? divr(alpha, aa) : one<S>();
-                beta = scal(ph, -nrm);
-                tau = 1.0 + aa / nrm;
-                const double den = aa + nrm;
-                const S cph = conjv(ph);
-                if (den > 1e-290) {
-                    const S sc = scal(cph, 1.0 / den);
-                    for (int i = j + tid; i < m; i += 256) col[i] = (i == j) ? one<S>() : mul(col[i], sc);
-                } else {
-                    for (int i = j + tid; i < m; i += 256) col[i] = (i == j) ? one<S>() : divr(mul(col[i], cph), den);
-                }
-            }
-            if (tid == 0) {
-                taus[j] = tau;
-                betas[j] = beta;
-            }
-        }
-        cluster.sync();  // v_j and tau_j published by the owner
+        const int owner = j % C, lj = j / C, nxt = j + 1;
+        cluster_wait();  // v_j and tau_j are published
         const double tau = *cluster.map_shared_rank(taus + j, owner);
-        const int lk0 = (j + 1 - rank + C - 1) / C;  // first local column with k > j
-        if (tau != 0.0 && lk0 < nl) {
+        if (tau != 0.0) {
             const S* vj = cluster.map_shared_rank(W + (size_t)lj * m, owner);
             for (int i = j + tid; i < m; i += 256) u[i] = vj[i];
             __syncthreads();
+        }
+        if (nxt < n && rank == nxt % C) {
+            S* cn = W + (size_t)(nxt / C) * m;
+            double x2 = -1.0;
+            if (tau != 0.0) {
+                if (warp == 0) {
+                    S dot = zero<S>();
+                    for (int i = j + lane; i < m; i += 32) mac(dot, conjv(u[i]), cn[i]);
+                    dot = warp_sum(dot);
+                    const S f = scal(dot, -tau);
+                    double nx = 0.0;
+                    for (int i = j + lane; i < m; i += 32) {
+                        S c = cn[i];
+                        mac(c, u[i], f);
+                        cn[i] = c;
+                        if (i > nxt) nx += abs2(c);
+                    }
+                    nx = warp_sum(nx);
+                    if (lane == 0) next_x2 = nx;
+                }
+                __syncthreads();
+                x2 = next_x2;
+            }
+            cluster_reflector(cn, nxt, m, x2, taus, betas, redd);
+        }
+        if (nxt < n) cluster_arrive();
+        if (tau != 0.0) {
+            const int lk0 = (j + 1 - rank + C - 1) / C;  // first local column with k > j
             for (int lk = lk0 + warp; lk < nl; lk += 8) {
-                S* ck = W + (size_t)lk * m;
                 const int k = rank + lk * C;
+                if (k == nxt) continue;  // already updated by its owner in the lookahead
+                S* ck = W + (size_t)lk * m;
                 S dot = zero<S>();
                 for (int i = j + lane; i < m; i += 32) mac(dot, conjv(u[i]), ck[i]);
                 dot = warp_sum(dot);
                 const S f = scal(dot, -tau);
-                if (k == j + 1) {  // the next column: also its norm below the next diagonal
-                    double nx = 0.0;
-                    for (int i = j + lane; i < m; i += 32) {
-                        S c = ck[i];
-                        mac(c, u[i], f);
-                        ck[i] = c;
-                        if (i > k) nx += abs2(c);
-                    }
-                    nx = warp_sum(nx);
-                    if (lane == 0) next_x2 = nx;
-                } else {
-                    for (int i = j + lane; i < m; i += 32) mac(ck[i], u[i], f);
-                }
+                for (int i = j + lane; i < m; i += 32) mac(ck[i], u[i], f);
             }
             __syncthreads();
         }
-        fused = tau != 0.0 && j + 1 < n;
     }
     cluster.sync();  // every reflector is final
     for (long long idx = tid; idx < (long long)m * nl; idx += 256) {
         const int i = (int)(idx % m), lc = (int)(idx / m), k = rank + lc * C;
         Q[(size_t)lc * m + i] = (i == k) ? one<S>() : zero<S>();
     }
+    // Q, column-locally and backwards; the next reflector is read from its owner while the
+    // current one is applied (two staging buffers)
+    S* ub[2] = {u, u + m};
+    {
+        const int j = n - 1;
+        if (*cluster.map_shared_rank(taus + j, j % C) != 0.0) {
+            const S* vj = cluster.map_shared_rank(W + (size_t)(j / C) * m, j % C);
+            for (int i = j + tid; i < m; i += 256) ub[j & 1][i] = vj[i];
+        }
+    }
     __syncthreads();
     for (int j = n - 1; j >= 0; --j) {
-        const int owner = j % C, lj = j / C;
-        const double tau = *cluster.map_shared_rank(taus + j, owner);
+        const double tau = *cluster.map_shared_rank(taus + j, j % C);
+        if (j > 0 && *cluster.map_shared_rank(taus + j - 1, (j - 1) % C) != 0.0) {
+            const S* vp = cluster.map_shared_rank(W + (size_t)((j - 1) / C) * m, (j - 1) % C);
+            S* dst = ub[(j - 1) & 1];
+            for (int i = j - 1 + tid; i < m; i += 256) dst[i] = vp[i];
+        }
         const int lk0 = (j - rank + C - 1) / C;  // first local column with k >= j
-        if (tau == 0.0 || lk0 >= nl) continue;  // uniform within the CTA
-        const S* vj = cluster.map_shared_rank(W + (size_t)lj * m, owner);
-        for (int i = j + tid; i < m; i += 256) u[i] = vj[i];
-        __syncthreads();
-        for (int lk = lk0 + warp; lk < nl; lk += 8) {
-            S* qk = Q + (size_t)lk * m;
-            S dot = zero<S>();
-            for (int i = j + lane; i < m; i += 32) mac(dot, conjv(u[i]), qk[i]);
-            dot = warp_sum(dot);
-            const S f = scal(dot, -tau);
-            for (int i = j + lane; i < m; i += 32) mac(qk[i], u[i], f);
+        if (tau != 0.0 && lk0 < nl) {
+            const S* v = ub[j & 1];
+            for (int lk = lk0 + warp; lk < nl; lk += 8) {
+                S* qk = Q + (size_t)lk * m;
+                S dot = zero<S>();
+                for (int i = j + lane; i < m; i += 32) mac(dot, conjv(v[i]), qk[i]);
+                dot = warp_sum(dot);
+                const S f = scal(dot, -tau);
+                for (int i = j + lane; i < m; i += 32) mac(qk[i], v[i], f);
+            }
         }
         __syncthreads();
     }
@@ -596,7 +636,7 @@ static int sm_count() {
 static size_t qr_cluster_smem(int max_m, long long max_mn, int C, size_t ss) {
     // m * ceil(n / C) <= m * n / C + m
     const size_t cols = (size_t)(max_mn / C) + (size_t)max_m;
-    return ((size_t)max_m + 2 * cols) * ss + QR_MAXN * (8 + ss) + 16;
+    return (2 * (size_t)max_m + 2 * cols) * ss + QR_MAXN * (8 + ss) + 16;
 }
 
 static size_t qr_smem_bytes(int max_m, long long max_mn, bool cplx, int* resident) {

@@ -192,6 +192,11 @@ def run_ours(args):
 
     g = make_lattice(B, cfg, prec, stream.cuda_stream)
     g.set_tensors(cfg["tensors"])
+    tune = None
+    if prec != "fp64" and not args.no_autotune:
+        tb, ta, tk = g.autotune(3)
+        tune = {"ms_per_sweep_default_tiles": round(tb, 4), "ms_per_sweep_tuned_tiles": round(ta, 4),
+                "steps_retiled": tk}
     for _ in range(args.warmup):
         g.sweep(1)
     s0 = g.stats()
@@ -317,7 +322,8 @@ def run_ours(args):
                                               "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{world}"},
                "tflops": flops / dev_s / 1e12, "fp64_qr_gflops": qr_flops / dev_s / 1e9,
                "gpu_launches": kernels, "latency_ms": {"p50": p50, "p99": p99}, "wall_s": wall,
-               "fp64_path": fp64, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary()}
+               "fp64_path": fp64, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(),
+               "autotune": tune}
         print(json.dumps(out), flush=True)
     g.close()
     if dist:
@@ -442,6 +448,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-readout", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--serve", action="store_true")
     ap.add_argument("--requests", type=int, default=24)
     ap.add_argument("--seed", type=int, default=5)

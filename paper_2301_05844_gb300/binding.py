@@ -80,6 +80,7 @@ def lib():
     L.bbp_qr_batched.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, P, P, P, P]
     L.bbp_qr_batched_noalloc.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, P, P, P, P]
     L.bbp_lattice_footprint.argtypes = [C.POINTER(Desc), C.POINTER(C.c_size_t)]
+    L.bbp_autotune.argtypes = [P, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_int)]
     L.bbp_server_create.argtypes = [C.c_size_t, C.c_int, C.POINTER(P)]
     L.bbp_server_submit.argtypes = [P, C.POINTER(Desc), P, C.POINTER(Term), C.c_int, C.POINTER(C.c_longlong)]
     L.bbp_server_poll.argtypes = [P, C.c_longlong, C.POINTER(C.c_int), C.POINTER(C.c_double),
@@ -267,6 +268,13 @@ class Lattice:
         the Hermitian basis)."""
         d = self.desc
         return d.dtype in (C128, C64) and d.prec == PREC_FP64 and not d.hermitian_basis
+
+    def autotune(self, reps=3):
+        """Choose the tensor-core tile shapes of the planned sweep by timing them (before
+        the first sweep).  Returns (ms_before, ms_after, steps_changed)."""
+        a, b, k = C.c_double(), C.c_double(), C.c_int()
+        _check(lib().bbp_autotune(self.h, int(reps), C.byref(a), C.byref(b), C.byref(k)))
+        return a.value, b.value, k.value
 
     def stats(self):
         s = Stats()

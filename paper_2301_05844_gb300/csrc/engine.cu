@@ -631,6 +631,25 @@ cudaError_t Program::encode_maps(char* base, size_t split, char* base2) {
     return cudaSuccess;
 }
 
+cudaError_t Program::tc_retile(size_t si, int bn, int depth, char* base, size_t split, char* base2, cudaStream_t st) {
+    Step& s = steps[si];
+    int tiles = 1;
+    for (int i = 0; i < s.count; ++i) {
+        const size_t k = s.first + (size_t)i;
+        TCSpec& sp = tcspec[k];
+        sp.bn = bn;
+        cudaError_t e = tc_make_map(&tcs[k].map_b, reloc_ptr(sp.b_off, base, split, base2), sp.kind, sp.b_rows, sp.K,
+                                    sp.b_ld, bn);
+        if (e != cudaSuccess) return e;
+        tiles = std::max(tiles, ((tcs[k].M + 127) / 128) * ((tcs[k].N + bn - 1) / bn));
+    }
+    s.aux = bn;
+    s.n = tiles;
+    s.aux2 = (s.aux2 & 0xFF) | (depth << 8);
+    return cudaMemcpyAsync(d_tcs + s.first, tcs.data() + s.first, (size_t)s.count * sizeof(TCTask), cudaMemcpyHostToDevice,
+                           st);
+}
+
 // Stream-ordered allocations (cudaMallocAsync / cudaFreeAsync) do not synchronise the
 // device, so creating or destroying one lattice never waits for another's kernels.
 template <typename T>

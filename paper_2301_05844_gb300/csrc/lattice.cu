@@ -1056,6 +1056,70 @@ int bbp_time_kernels(bbp_lattice* L, int cls, int reps, double* ms, long long* l
     return BBP_OK;
 }
 
+int bbp_autotune(bbp_lattice* L, int reps, double* ms_before, double* ms_after, int* steps_changed) {
+    if (!L) return fail(BBP_ERR_INVALID, "lattice is NULL");
+    if (reps < 1) return fail(BBP_ERR_INVALID, "reps must be >= 1");
+    if (!L->has_tensors) return fail(BBP_ERR_STATE, "bbp_set_tensors has not been called");
+    if (L->sweeps > 0 || L->sweep.exec) return fail(BBP_ERR_STATE, "autotune must run before the first sweep");
+    double before = 0.0, after = 0.0;
+    int changed = 0;
+    if (L->mixed) {
+        Program& pr = L->sweep;
+        cudaStream_t st = L->stream;
+        cudaEvent_t a, b;
+        CKR(cudaEventCreate(&a));
+        CKR(cudaEventCreate(&b));
+        CKR(pr.reset_active(st));  // every fit stage runs, as in a first sweep
+        const int ek = L->cx.tck == 0 ? 32 : 64;  // K elements per k-block
+        for (size_t si = 0; si < pr.steps.size(); ++si) {
+            if (pr.steps[si].kind != ST_TC) continue;
+            const Step s0 = pr.steps[si];
+            int nmax = 1, kmax = 1;
+            for (int i = 0; i < s0.count; ++i) {
+                nmax = std::max(nmax, pr.tcs[s0.first + i].N);
+                kmax = std::max(kmax, (pr.tcs[s0.first + i].K + ek - 1) / ek);
+            }
+            const int bn0 = s0.aux, d0 = s0.aux2 >> 8;
+            int best_bn = bn0, best_d = d0;
+            float best = -1.0f, t0 = -1.0f;
+            for (int bn : {32, 64, 128, 256}) {
+                if (bn > 32 && bn / 2 >= nmax) break;  // wider tiles than the widest result
+                for (int depth = 2; depth <= 4; ++depth) {
+                    if (depth > std::max(2, kmax)) break;
+                    CKR(pr.tc_retile(si, bn, depth, L->arena, (size_t)-1, nullptr, st));
+                    CKR(pr.launch_step(pr.steps[si], st, L->d_sweep, L->desc.seed));  // warm-up
+                    CKR(cudaEventRecord(a, st));
+                    for (int r = 0; r < reps; ++r) CKR(pr.launch_step(pr.steps[si], st, L->d_sweep, L->desc.seed));
+                    CKR(cudaEventRecord(b, st));
+                    CKR(cudaEventSynchronize(b));
+                    float t = 0.0f;
+                    CKR(cudaEventElapsedTime(&t, a, b));
+                    if (bn == bn0 && depth == d0) t0 = t;
+                    if (best < 0.0f || t < best) {
+                        best = t;
+                        best_bn = bn;
+                        best_d = depth;
+                    }
+                }
+            }
+            CKR(pr.tc_retile(si, best_bn, best_d, L->arena, (size_t)-1, nullptr, st));
+            if (best_bn != bn0 || best_d != d0) ++changed;
+            before += (t0 >= 0.0f ? t0 : best) / reps;
+            after += best / reps;
+        }
+        CKR(cudaStreamSynchronize(st));
+        cudaEventDestroy(a);
+        cudaEventDestroy(b);
+        int te = 0;
+        CKR(cudaMemcpy(&te, L->d_tcerr, sizeof(int), cudaMemcpyDeviceToHost));
+        if (te) return fail(BBP_ERR_TIMEOUT, "a tensor-core pipeline wait exceeded its bound");
+    }
+    if (ms_before) *ms_before = before;
+    if (ms_after) *ms_after = after;
+    if (steps_changed) *steps_changed = changed;
+    return BBP_OK;
+}
+
 int bbp_get_stats(bbp_lattice* L, bbp_stats* out) {
     if (!L || !out) return fail(BBP_ERR_INVALID, "NULL argument");
     memset(out, 0, sizeof(*out));

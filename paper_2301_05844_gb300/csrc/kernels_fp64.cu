@@ -9,6 +9,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <mutex>
 
 #include "bbp_internal.h"
 
@@ -647,6 +648,8 @@ static size_t qr_smem_bytes(int max_m, long long max_mn, bool cplx, int* residen
 }
 
 cudaError_t qr_prepare(int max_m, bool cplx) {
+    static std::mutex mu;  // the request server reads out on a second thread
+    std::lock_guard<std::mutex> guard(mu);
     // the limit only ever grows, so that a smaller request cannot break a larger user;
     // it covers the shared-memory-resident form up to QR_SMEM_LIMIT as well
     static size_t limit[2] = {0, 0};

@@ -6,7 +6,9 @@
 // is free), uploads them, and keeps one sweep of every admitted solve in flight, each
 // on the solve's own stream, so that the kernels of different solves overlap on the
 // device.  A solve whose residual meets its tolerance (or that reaches max_sweeps) is
-// read out (bbp_expect) and released, and its bytes go to the next admissions.
+// handed to a second thread that reads it out (bbp_expect) and releases it, so that the
+// sweeps of the other solves keep flowing meanwhile; its bytes then go to the next
+// admissions.
 #include <cuda_runtime.h>
 
 #include <atomic>
@@ -66,15 +68,52 @@ struct bbp_server {
     std::deque<Request*> queue;
     std::unordered_map<long long, std::unique_ptr<Request>> reqs;
     std::vector<Request*> active;  // worker thread only
+    std::deque<Request*> ro_queue;  // converged solves waiting for their read-out
+    std::condition_variable cv_ro;
     size_t used = 0;
     long long next_id = 1;
     std::atomic<bool> stop{false};
-    std::thread worker;
-    long long sweeps_total = 0;
+    bool ro_stop = false;
+    std::thread worker, ro_worker;
+    std::atomic<long long> sweeps_total{0};
 
     void run();
+    void run_readouts();
+    int readout(Request* r);
     void finish(Request* r, int rc, const std::string& err);
 };
+
+int bbp_server::readout(Request* r) {
+    const int n = (int)r->terms.size();
+    std::vector<bbp_term> ts(n);
+    for (int k = 0; k < n; ++k) {
+        ts[k].nsite = r->terms[k].nsite;
+        for (int j = 0; j < r->terms[k].nsite; ++j) {
+            ts[k].site[j] = r->terms[k].site[j];
+            ts[k].op_re[j] = r->terms[k].re[j].data();
+            ts[k].op_im[j] = r->terms[k].has_im[j] ? r->terms[k].im[j].data() : nullptr;
+        }
+    }
+    r->out_re.assign(n, 0.0);
+    r->out_im.assign(n, 0.0);
+    return n ? bbp_expect(r->L, ts.data(), n, r->out_re.data(), r->out_im.data()) : BBP_OK;
+}
+
+void bbp_server::run_readouts() {
+    cudaSetDevice(device);
+    for (;;) {
+        Request* r = nullptr;
+        {
+            std::unique_lock<std::mutex> lk(mu);
+            cv_ro.wait(lk, [this] { return !ro_queue.empty() || ro_stop; });
+            if (ro_queue.empty()) return;  // stopping and drained
+            r = ro_queue.front();
+            ro_queue.pop_front();
+        }
+        const int rc = readout(r);
+        finish(r, rc, rc ? bbp_last_error() : "");
+    }
+}
 
 void bbp_server::finish(Request* r, int rc, const std::string& err) {
     if (r->L) {
@@ -155,23 +194,16 @@ void bbp_server::run() {
                     }
                 }
             }
-            if (!rc && done) {
-                const int n = (int)r->terms.size();
-                std::vector<bbp_term> ts(n);
-                for (int k = 0; k < n; ++k) {
-                    ts[k].nsite = r->terms[k].nsite;
-                    for (int j = 0; j < r->terms[k].nsite; ++j) {
-                        ts[k].site[j] = r->terms[k].site[j];
-                        ts[k].op_re[j] = r->terms[k].re[j].data();
-                        ts[k].op_im[j] = r->terms[k].has_im[j] ? r->terms[k].im[j].data() : nullptr;
-                    }
+            if (!rc && done) {  // converged: the read-out thread takes the solve from here
+                {
+                    std::lock_guard<std::mutex> g(mu);
+                    ro_queue.push_back(r);
                 }
-                r->out_re.assign(n, 0.0);
-                r->out_im.assign(n, 0.0);
-                if (n) rc = bbp_expect(r->L, ts.data(), n, r->out_re.data(), r->out_im.data());
-            }
-            if (rc || done) {
-                finish(r, rc, rc ? bbp_last_error() : "");
+                cv_ro.notify_one();
+                active.erase(active.begin() + i);
+                progressed = true;
+            } else if (rc) {
+                finish(r, rc, bbp_last_error());
                 active.erase(active.begin() + i);
                 progressed = true;
             } else {
@@ -192,6 +224,7 @@ int bbp_server_create(size_t max_bytes, int max_active, bbp_server** out) {
     s->max_active = max_active;
     if (cudaGetDevice(&s->device) != cudaSuccess) s->device = 0;
     s->worker = std::thread([s] { s->run(); });
+    s->ro_worker = std::thread([s] { s->run_readouts(); });
     *out = s;
     return BBP_OK;
 }
@@ -280,7 +313,7 @@ int bbp_server_stats(bbp_server* s, long long* submitted, long long* done, long 
     for (auto& kv : s->reqs) d += kv.second->state == 2 ? 1 : 0;
     if (submitted) *submitted = (long long)s->reqs.size();
     if (done) *done = d;
-    if (sweeps) *sweeps = s->sweeps_total;
+    if (sweeps) *sweeps = s->sweeps_total.load();
     if (bytes_in_use) *bytes_in_use = s->used;
     return BBP_OK;
 }
@@ -298,7 +331,13 @@ void bbp_server_destroy(bbp_server* s) {
         s->queue.clear();
     }
     s->cv_work.notify_all();
-    if (s->worker.joinable()) s->worker.join();
+    if (s->worker.joinable()) s->worker.join();  // runs the admitted solves to the end
+    {
+        std::lock_guard<std::mutex> g(s->mu);
+        s->ro_stop = true;
+    }
+    s->cv_ro.notify_all();
+    if (s->ro_worker.joinable()) s->ro_worker.join();  // reads out what is left
     delete s;
 }
 

@@ -9,6 +9,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <atomic>
 #include <mutex>
 
 #include "bbp_internal.h"
@@ -625,11 +626,13 @@ __global__ void __launch_bounds__(256) k_qr_cluster(const QRTask* __restrict__ t
 constexpr size_t QR_CLUSTER_SMEM = QR_SMEM_LIMIT + QR_MAXN * (8 + 16) + 16;
 
 static int sm_count() {
-    static int n = 0;
+    static std::atomic<int> cached{0};  // read by the server's worker and read-out threads
+    int n = cached.load(std::memory_order_relaxed);
     if (n == 0) {
         int dev = 0;
         cudaGetDevice(&dev);
         if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) n = 1;
+        cached.store(n, std::memory_order_relaxed);
     }
     return n;
 }

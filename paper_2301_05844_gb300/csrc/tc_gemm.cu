@@ -429,17 +429,22 @@ cudaError_t launch_tc_gemm(const TCTask* d_tasks, int ntasks, int kind, int bn, 
 }
 
 // ---------------------------------------------------------------- host: tensor maps
-static PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+// The driver's tensor-map encoder, looked up once (the request server encodes maps from its
+// worker and read-out threads).
+static PFN_cuTensorMapEncodeTiled_v12000 encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+        cudaDriverEntryPointQueryResult q;
+        void* p = nullptr;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q);
+        return (e == cudaSuccess && q == cudaDriverEntryPointSuccess) ? (PFN_cuTensorMapEncodeTiled_v12000)p : nullptr;
+    }();
+    return fn;
+}
 
 cudaError_t tc_make_map(void* map_out, const void* base, int kind, long long rows, long long K, long long ld_elems,
                         int box_rows) {
-    if (!g_encode) {
-        cudaDriverEntryPointQueryResult q;
-        void* fn = nullptr;
-        cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
-        if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
-        g_encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
-    }
+    const PFN_cuTensorMapEncodeTiled_v12000 g_encode = encoder();
+    if (!g_encode) return cudaErrorNotSupported;
     const int esz = kind == 0 ? 4 : 2;
     cuuint64_t gdim[2] = {(cuuint64_t)K, (cuuint64_t)rows};
     cuuint64_t gstride[1] = {(cuuint64_t)(ld_elems * esz)};

@@ -146,7 +146,7 @@ __device__ __forceinline__ void store_split(void* p, long long i, int kind, doub
         store_kind(p, i, kind, v);
         return;
     }
-    const float hi = tf32_round((float)v), lo = tf32_round((float)(v - (double)hi));
+    const float f32 = (float)v, hi = tf32_round(f32), lo = tf32_round(f32 - hi);  // f32 - hi is exact
     float* f = (float*)p;
     f[i] = hi;
     f[i + kseg] = x3 == 1 ? lo : hi;
@@ -415,64 +415,204 @@ __global__ void __launch_bounds__(256) k_qr(const QRTask* __restrict__ tasks, in
 
 constexpr size_t QR_SMEM_LIMIT = 200 * 1024;
 
-// The same QR with one task spread over a thread-block cluster of C CTAs (C <= 8), for
-// launches with too few tasks to fill the SMs: column j belongs to CTA j % C, which keeps
-// its columns of W and Q in shared memory.  Per column j the owner forms the reflector
-// (scaled form, as above) in place in its column of W, the cluster synchronises, and every
-// CTA reads v_j and tau_j from the owner's shared memory (distributed shared memory) to
-// update its own columns k > j.  Q is then accumulated backwards column-locally, each CTA
-// reading every v_j from its owner; no CTA leaves before the others have finished reading.
-// Shared memory per CTA: u (2 x m) | W (m x nl) | Q (m x nl) | tau (n) | beta (n) | partial norm.
+// The QR with one task spread over a thread-block cluster of C CTAs (1 <= C <= 8), W and Q
+// in shared memory.  On GB300 every warp-wide FP64 instruction occupies its SM sub-partition's
+// FP64 unit for 64 cycles, however many lanes are active, and a square root or division is
+// about ten such instructions.  So the cost of a Householder QR of these sizes is its count
+// of FP64 instructions: along the per-column critical chain (the next column's update, its
+// norm, the reflector's scalars) and per sub-partition for the bulk updates.  This form:
+//  * column j belongs to CTA j % C, which keeps its columns of W in shared memory;
+//  * in step j, warps 0-3 of the CTA owning column j+1 (one warp per sub-partition, rows
+//    split between them) apply H_j to that column, form the reflector v_{j+1} from it and
+//    publish it on a split cluster barrier; only then do that CTA's eight warps apply H_j
+//    to its remaining columns, while every other CTA does so at once (each step begins
+//    with a CTA barrier, so that no warp reads a column another is still updating);
+//  * the reflector's square root and reciprocal are FP32 seeds refined by one third-order
+//    step in FP64 (a handful of FP64 instructions instead of about thirty);
+//  * the bulk updates take two columns per warp with one shared reduction tree;
+//  * Q is formed column by column, Q e_k = H_0 H_1 ... H_k e_k, with the columns dealt to
+//    the sub-partitions in snake order (balanced work) and no barrier, each v_j read from
+//    its owner (distributed shared memory).
+// The arithmetic on a column does not depend on which CTA or warp performs it, so the result
+// is the same for every C.
+// Shared memory per CTA: u (2 x m) | W (m x nl) | Q (m x nl) | tau (n) | all taus (n) |
+// beta (n) | partial norm.
 __device__ __forceinline__ void cluster_arrive() { asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory"); }
 __device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory"); }
+// named barrier 1: the four chain warps
+__device__ __forceinline__ void chain_sync() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
 
-// Owner CTA of column j: turn its local column col into the scaled reflector v_j (in place,
-// v_j[j] = 1) and record tau_j and beta_j.  xs2_in < 0: compute the sub-diagonal norm here.
-// Called by every thread of the CTA.
+__device__ __forceinline__ double shfl_xor(double v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
+__device__ __forceinline__ double2 shfl_xor(double2 v, int o) {
+    return make_double2(__shfl_xor_sync(0xffffffffu, v.x, o), __shfl_xor_sync(0xffffffffu, v.y, o));
+}
+// Butterfly sum over the warp: every lane ends with the same total.
 template <typename S>
-__device__ void cluster_reflector(S* col, int j, int m, double xs2_in, double* taus, S* betas, double* redd) {
-    const int tid = threadIdx.x;
-    double xs2 = xs2_in;
-    if (xs2 < 0.0) {
-        xs2 = 0.0;
-        for (int i = j + 1 + tid; i < m; i += 256) xs2 += abs2(col[i]);
-        xs2 = block_sum(xs2, redd);
+__device__ __forceinline__ S warp_tree(S x) {
+    for (int o = 16; o > 0; o >>= 1) x = add(x, shfl_xor(x, o));
+    return x;
+}
+// Two sums in one tree: lanes < 16 end with the warp total of a, lanes >= 16 with that of b.
+template <typename S>
+__device__ __forceinline__ S pair_tree(S a, S b) {
+    const bool lo = (threadIdx.x & 31) < 16;
+    S x = add(lo ? a : b, shfl_xor(lo ? b : a, 16));
+    for (int o = 8; o > 0; o >>= 1) x = add(x, shfl_xor(x, o));
+    return x;
+}
+__device__ __forceinline__ double warp_max(double v) {
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+// x or -x by the sign bit (an integer operation, no FP64 instruction)
+__device__ __forceinline__ double flip(double x, bool neg) {
+    return __longlong_as_double(__double_as_longlong(x) ^ (neg ? (long long)0x8000000000000000ull : 0ll));
+}
+// alpha / |alpha| (1 for alpha = 0)
+__device__ __forceinline__ double phase_of(double a, double aa) { return aa > 0.0 && a < 0.0 ? -1.0 : 1.0; }
+__device__ __forceinline__ double2 phase_of(double2 a, double aa) { return aa > 0.0 ? divr(a, aa) : one<double2>(); }
+__device__ __forceinline__ double apply_phase(double x, double ph) { return flip(x, ph < 0.0); }
+template <typename S> __device__ __forceinline__ S from_real(double x);
+template <> __device__ __forceinline__ double from_real<double>(double x) { return x; }
+template <> __device__ __forceinline__ double2 from_real<double2>(double x) { return make_double2(x, 0.0); }
+__device__ __forceinline__ double2 apply_phase(double2 x, double2 ph) { return mul(x, ph); }
+
+// 1/sqrt(s), s in [2^-100, 2^100]: the FP32 estimate y (relative error < 2^-21) refined by one
+// step of Householder's third-order iteration for s^(-1/2), y (1 + e/2 + 3e^2/8) with
+// e = 1 - s y^2 (remaining relative error ~ e^3, below FP64 rounding).
+__device__ __forceinline__ double rsqrt_refined(double s) {
+    const double y = (double)rsqrtf((float)s);
+    const double e = fma(-(s * y), y, 1.0);
+    return fma(y * fma(0.375, e, 0.5), e, y);
+}
+// 1/d, d in [2^-100, 2^100]: the FP32 reciprocal r refined by r (1 + e + e^2), e = 1 - d r
+// (the third-order Newton-Raphson iteration for 1/d).
+__device__ __forceinline__ double rcp_refined(double d) {
+    const double r = (double)__frcp_rn((float)d);
+    const double e = fma(-d, r, 1.0);
+    return fma(r, fma(e, e, e), r);
+}
+
+// One warp: c <- c - tau v (v^H c) on rows >= j for c1 and, if c2 != nullptr, c2 (v may live
+// in another CTA's shared memory).  A call is bound by the latency of its dependent FP64
+// operations (each fed from shared memory), not by FP64 throughput, so a second column rides
+// along almost for free: the two dot products share one reduction tree.  Each sums its rows
+// in ascending order, so the result for a column does not depend on whether it is passed as
+// c1 or c2.
+template <typename S>
+__device__ void warp_apply2(S* c1, S* c2, const S* v, double tau, int j, int m) {
+    const int lane = threadIdx.x & 31;
+    S a = zero<S>(), b = zero<S>();
+    for (int i = j + lane; i < m; i += 32) {
+        const S x = conjv(v[i]);
+        mac(a, x, c1[i]);
+        if (c2) mac(b, x, c2[i]);
     }
-    double xnorm = sqrt(xs2);
-    if (xs2 < 1e-280) {
-        double amax = 0.0;
-        for (int i = j + 1 + tid; i < m; i += 256) amax = fmax(amax, absv(col[i]));
-        amax = block_max(amax, redd);
-        double t2 = 0.0;
-        if (amax > 0.0)
-            for (int i = j + 1 + tid; i < m; i += 256) t2 += abs2(divr(col[i], amax));
-        t2 = block_sum(t2, redd);
-        xnorm = amax > 0.0 ? amax * sqrt(t2) : 0.0;
+    const S f = scal(pair_tree(a, b), -tau);
+    const S f1 = shfl_idx(f, 0), f2 = shfl_idx(f, 16);
+    for (int i = j + lane; i < m; i += 32) {
+        const S x = v[i];
+        mac(c1[i], x, f1);
+        if (c2) mac(c2[i], x, f2);
     }
-    const S alpha = col[j];
+    __syncwarp();
+}
+
+// Scratch of the chain warps (static shared memory).
+template <typename S>
+struct ChainScratch {
+    S dot[4];
+    double nrm[4];
+    double amax[4];
+    S alpha;
+};
+
+// Warps 0-3 of the CTA owning column nxt: if tau != 0, apply H_j (v_j in ub) to column c on
+// rows >= j; then turn c into the scaled reflector v_nxt in place (v_nxt[nxt] = 1; see k_qr
+// for the scaled form) and record tau_nxt, beta_nxt.  Warp w takes the rows
+// base + 32 (4 t + w) + lane, base = j (nxt when there is no H_j).
+template <typename S>
+__device__ void chain_reflector(S* c, const S* ub, double tau, int j, int nxt, int m, ChainScratch<S>& cs,
+                                double* taus, S* betas) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int base = tau != 0.0 ? j : nxt;
+    double p = 0.0;
+    if (tau != 0.0) {
+        S a = zero<S>();
+        for (int i = base + 32 * w + lane; i < m; i += 128) mac(a, conjv(ub[i]), c[i]);
+        a = warp_tree(a);
+        if (lane == 0) cs.dot[w] = a;
+        chain_sync();
+        const S f = scal(add(add(cs.dot[0], cs.dot[1]), add(cs.dot[2], cs.dot[3])), -tau);
+        for (int i = base + 32 * w + lane; i < m; i += 128) {
+            S x = c[i];
+            mac(x, ub[i], f);
+            c[i] = x;
+            if (i > nxt) p += abs2(x);
+        }
+    } else {
+        for (int i = base + 32 * w + lane; i < m; i += 128)
+            if (i > nxt) p += abs2(c[i]);
+    }
+    if (w == 0 && lane == nxt - base) cs.alpha = c[nxt];  // row nxt lies in warp 0's first block
+    p = warp_tree(p);
+    if (lane == 0) cs.nrm[w] = p;
+    chain_sync();
+    const double xs2 = (cs.nrm[0] + cs.nrm[1]) + (cs.nrm[2] + cs.nrm[3]);
+    const S alpha = cs.alpha;
     const double aa = absv(alpha);
-    __syncthreads();  // every thread has read alpha before column j is overwritten
-    S beta = alpha;
-    double tau = 0.0;
-    if (xnorm > 0.0) {
-        const double nrm = hypot(aa, xnorm);
-        const S ph = aa > 0.0 ? divr(alpha, aa) : one<S>();
-        beta = scal(ph, -nrm);
-        tau = 1.0 + aa / nrm;
-        const double den = aa + nrm;
-        const S cph = conjv(ph);
-        if (den > 1e-290) {
-            const S sc = scal(cph, 1.0 / den);
-            for (int i = j + tid; i < m; i += 256) col[i] = (i == j) ? one<S>() : mul(col[i], sc);
+    double nrm = 0.0, tau_n = 0.0, rd = 0.0;
+    bool any = true;
+    if (xs2 < 1e-280) {  // near underflow (uniform branch): rescale by max |x'_i|
+        double am = 0.0;
+        for (int i = base + 32 * w + lane; i < m; i += 128)
+            if (i > nxt) am = fmax(am, absv(c[i]));
+        am = warp_max(am);
+        if (lane == 0) cs.amax[w] = am;
+        chain_sync();
+        am = fmax(fmax(cs.amax[0], cs.amax[1]), fmax(cs.amax[2], cs.amax[3]));
+        double t2 = 0.0;
+        if (am > 0.0)
+            for (int i = base + 32 * w + lane; i < m; i += 128)
+                if (i > nxt) t2 += abs2(divr(c[i], am));
+        t2 = warp_tree(t2);
+        chain_sync();  // every warp has read cs.nrm and cs.amax
+        if (lane == 0) cs.nrm[w] = t2;
+        chain_sync();
+        t2 = (cs.nrm[0] + cs.nrm[1]) + (cs.nrm[2] + cs.nrm[3]);
+        any = am > 0.0;
+        if (any) {
+            nrm = hypot(aa, am * sqrt(t2));
+            tau_n = 1.0 + aa / nrm;
+            rd = 1.0 / (aa + nrm);
+        }
+    } else {
+        const double s = fma(aa, aa, xs2);
+        if (s >= 0x1p-100 && s <= 0x1p100) {
+            const double y = rsqrt_refined(s);
+            nrm = s * y;
+            tau_n = fma(aa, y, 1.0);
+            rd = rcp_refined(aa + nrm);
         } else {
-            for (int i = j + tid; i < m; i += 256) col[i] = (i == j) ? one<S>() : divr(mul(col[i], cph), den);
+            nrm = (aa < 1e150 && xs2 < 1e300) ? sqrt(s) : hypot(aa, sqrt(xs2));
+            tau_n = 1.0 + aa / nrm;
+            rd = 1.0 / (aa + nrm);
         }
     }
-    if (tid == 0) {
-        taus[j] = tau;
-        betas[j] = beta;
+    S beta = alpha;
+    if (any) {
+        const S ph = phase_of(alpha, aa);
+        beta = apply_phase(from_real<S>(flip(nrm, true)), ph);  // -phase(alpha) nrm
+        const S sc = apply_phase(from_real<S>(rd), conjv(ph));
+        for (int i = base + 32 * w + lane; i < m; i += 128)
+            if (i > nxt) c[i] = mul(c[i], sc);
+        if (w == 0 && lane == nxt - base) c[nxt] = one<S>();
     }
-    __syncthreads();
+    if (w == 0 && lane == 0) {
+        taus[nxt] = any ? tau_n : 0.0;
+        betas[nxt] = beta;
+    }
+    __syncwarp();
 }
 
 template <typename S>
@@ -490,128 +630,112 @@ __global__ void __launch_bounds__(256) k_qr_cluster(const QRTask* __restrict__ t
     S* W = u + 2 * m;
     S* Q = W + (size_t)m * nlmax;
     double* taus = (double*)(Q + (size_t)m * nlmax);
-    S* betas = (S*)(taus + QR_MAXN);
+    double* tall = taus + QR_MAXN;
+    S* betas = (S*)(tall + QR_MAXN);
     double* part = (double*)(betas + QR_MAXN);
     __shared__ double redd[32];
+    __shared__ S phs[QR_MAXN];
+    __shared__ ChainScratch<S> cs;
     const S* in = (const S*)t.in;
     double ss = 0.0;
-    for (long long idx = tid; idx < (long long)m * nl; idx += 256) {
-        const int i = (int)(idx % m), lc = (int)(idx / m), j = rank + lc * C;
+    for (int idx = tid; idx < m * nl; idx += 256) {
+        const int lc = idx / m, i = idx - lc * m, j = rank + lc * C;
         const long long src = (long long)i * t.in_rs + (long long)j * t.in_cs;
         S v;
         if (t.in_float) v = from_float<S>(((const float*)t.in), src);
         else v = in[src];
         if (t.conj_io) v = conjv(v);
-        W[(size_t)lc * m + i] = v;
-        ss += abs2(v);
+        W[idx] = v;
+        if (t.loss) ss += abs2(v);
     }
-    ss = block_sum(ss, redd);
-    if (tid == 0) part[0] = ss;
-    cluster.sync();
+    if (t.loss) {  // uniform: the loss -||A||^2 of the fit (App. A)
+        ss = block_sum(ss, redd);
+        if (tid == 0) part[0] = ss;
+    }
+    cluster.sync();  // W loaded everywhere; partial norms published
     if (rank == 0 && tid == 0 && t.loss) {
         double tot = 0.0;
         for (int r = 0; r < C; ++r) tot += *cluster.map_shared_rank(part, r);
         *t.loss = -tot;
     }
-    __shared__ double next_x2;  // sub-diagonal norm of the next column, from its owner's update
-    // Forward: the owner of column j+1 updates that column with v_j first, forms v_{j+1} and
-    // arrives on the split cluster barrier; the other CTAs arrive as soon as they hold v_j.
-    // Everyone then applies v_j to its remaining columns and waits for v_{j+1} only before
-    // the next step, so the bulk updates overlap the next reflector's critical path.
-    if (rank == 0) cluster_reflector(W, 0, m, -1.0, taus, betas, redd);
-    cluster_arrive();
+    // ---- R: phase p of the split cluster barrier publishes v_p and tau_p
+    if (n > 0) {
+        if (rank == 0 && warp < 4) chain_reflector(W, u, 0.0, 0, 0, m, cs, taus, betas);
+        cluster_arrive();
+    }
     for (int j = 0; j < n; ++j) {
-        const int owner = j % C, lj = j / C, nxt = j + 1;
+        const int owner = j % C, nxt = j + 1;
         cluster_wait();  // v_j and tau_j are published
-        const double tau = *cluster.map_shared_rank(taus + j, owner);
-        if (tau != 0.0) {
-            const S* vj = cluster.map_shared_rank(W + (size_t)lj * m, owner);
-            for (int i = j + tid; i < m; i += 256) u[i] = vj[i];
+        const double tau = owner == rank ? taus[j] : *cluster.map_shared_rank(taus + j, owner);
+        S* ub = u + (size_t)(j & 1) * m;
+        const S* vj = W + (size_t)(j / C) * m;
+        if (owner != rank) vj = cluster.map_shared_rank(vj, owner);
+        const bool own_next = nxt < n && rank == nxt % C;
+        if (tau != 0.0)
+            for (int i = j + tid; i < m; i += 256) ub[i] = vj[i];
+        __syncthreads();  // u holds v_j; every warp has finished step j-1
+        if (own_next) {
+            // the chain first; the bulk update of this CTA waits for it
+            if (warp < 4) chain_reflector(W + (size_t)(nxt / C) * m, ub, tau, j, nxt, m, cs, taus, betas);
             __syncthreads();
-        }
-        if (nxt < n && rank == nxt % C) {
-            S* cn = W + (size_t)(nxt / C) * m;
-            double x2 = -1.0;
-            if (tau != 0.0) {
-                if (warp == 0) {
-                    S dot = zero<S>();
-                    for (int i = j + lane; i < m; i += 32) mac(dot, conjv(u[i]), cn[i]);
-                    dot = warp_sum(dot);
-                    const S f = scal(dot, -tau);
-                    double nx = 0.0;
-                    for (int i = j + lane; i < m; i += 32) {
-                        S c = cn[i];
-                        mac(c, u[i], f);
-                        cn[i] = c;
-                        if (i > nxt) nx += abs2(c);
-                    }
-                    nx = warp_sum(nx);
-                    if (lane == 0) next_x2 = nx;
-                }
-                __syncthreads();
-                x2 = next_x2;
-            }
-            cluster_reflector(cn, nxt, m, x2, taus, betas, redd);
         }
         if (nxt < n) cluster_arrive();
         if (tau != 0.0) {
-            const int lk0 = (j + 1 - rank + C - 1) / C;  // first local column with k > j
-            for (int lk = lk0 + warp; lk < nl; lk += 8) {
-                const int k = rank + lk * C;
-                if (k == nxt) continue;  // already updated by its owner in the lookahead
-                S* ck = W + (size_t)lk * m;
-                S dot = zero<S>();
-                for (int i = j + lane; i < m; i += 32) mac(dot, conjv(u[i]), ck[i]);
-                dot = warp_sum(dot);
-                const S f = scal(dot, -tau);
-                for (int i = j + lane; i < m; i += 32) mac(ck[i], u[i], f);
+            // local columns k > j, without column j+1 on its owner: eight warps, two columns each
+            const int lk0 = (nxt - rank + C - 1) / C + (own_next ? 1 : 0);
+            for (int t0 = warp; lk0 + t0 < nl; t0 += 16) {
+                const int l1 = lk0 + t0, l2 = l1 + 8;
+                warp_apply2(W + (size_t)l1 * m, l2 < nl ? W + (size_t)l2 * m : (S*)nullptr, ub, tau, j, m);
             }
-            __syncthreads();
         }
     }
     cluster.sync();  // every reflector is final
-    for (long long idx = tid; idx < (long long)m * nl; idx += 256) {
-        const int i = (int)(idx % m), lc = (int)(idx / m), k = rank + lc * C;
-        Q[(size_t)lc * m + i] = (i == k) ? one<S>() : zero<S>();
+    for (int jj = tid; jj < n; jj += 256) tall[jj] = jj % C == rank ? taus[jj] : *cluster.map_shared_rank(taus + jj, jj % C);
+    for (int lc = tid; lc < nl; lc += 256) {  // phase(beta_k) of the local columns, so that R_kk >= 0
+        const S b = betas[rank + lc * C];
+        phs[lc] = phase_of(b, absv(b));
     }
-    // Q, column-locally and backwards; the next reflector is read from its owner while the
-    // current one is applied (two staging buffers)
-    S* ub[2] = {u, u + m};
+    __syncthreads();
+    // ---- Q: local columns in descending k; the eight longest get a warp each (warp t), the
+    // next eight are dealt back from warp 7 to warp 0, and so on; each warp takes its
+    // columns two at a time (a short column rides along with a long one)
     {
-        const int j = n - 1;
-        if (*cluster.map_shared_rank(taus + j, j % C) != 0.0) {
-            const S* vj = cluster.map_shared_rank(W + (size_t)(j / C) * m, j % C);
-            for (int i = j + tid; i < m; i += 256) ub[j & 1][i] = vj[i];
+        int pend = -1;
+        for (int q = 0; q <= nl; ++q) {
+            int lc = -1;
+            if (q < nl) {
+                const int b = q >> 3, p = q & 7;
+                if (((b & 1) ? 7 - p : p) != warp) continue;
+                lc = nl - 1 - q;
+                if (pend < 0) {
+                    pend = lc;
+                    continue;
+                }
+            }
+            if (pend < 0) break;
+            const int k1 = rank + pend * C, k2 = lc >= 0 ? rank + lc * C : -1;  // k1 > k2
+            S* y1 = Q + (size_t)pend * m;
+            S* y2 = lc >= 0 ? Q + (size_t)lc * m : nullptr;
+            for (int i = lane; i < m; i += 32) {
+                y1[i] = i == k1 ? one<S>() : zero<S>();
+                if (y2) y2[i] = i == k2 ? one<S>() : zero<S>();
+            }
+            __syncwarp();
+            for (int jj = k1; jj >= 0; --jj) {  // H_jj leaves e_k unchanged for jj > k
+                const double tj = tall[jj];
+                if (tj == 0.0) continue;
+                const S* v = W + (size_t)(jj / C) * m;
+                if (jj % C != rank) v = cluster.map_shared_rank(v, jj % C);
+                warp_apply2(y1, jj <= k2 ? y2 : (S*)nullptr, v, tj, jj, m);
+            }
+            pend = -1;
         }
     }
     __syncthreads();
-    for (int j = n - 1; j >= 0; --j) {
-        const double tau = *cluster.map_shared_rank(taus + j, j % C);
-        if (j > 0 && *cluster.map_shared_rank(taus + j - 1, (j - 1) % C) != 0.0) {
-            const S* vp = cluster.map_shared_rank(W + (size_t)((j - 1) / C) * m, (j - 1) % C);
-            S* dst = ub[(j - 1) & 1];
-            for (int i = j - 1 + tid; i < m; i += 256) dst[i] = vp[i];
-        }
-        const int lk0 = (j - rank + C - 1) / C;  // first local column with k >= j
-        if (tau != 0.0 && lk0 < nl) {
-            const S* v = ub[j & 1];
-            for (int lk = lk0 + warp; lk < nl; lk += 8) {
-                S* qk = Q + (size_t)lk * m;
-                S dot = zero<S>();
-                for (int i = j + lane; i < m; i += 32) mac(dot, conjv(v[i]), qk[i]);
-                dot = warp_sum(dot);
-                const S f = scal(dot, -tau);
-                for (int i = j + lane; i < m; i += 32) mac(qk[i], v[i], f);
-            }
-        }
-        __syncthreads();
-    }
     S* out = (S*)t.out;
-    for (long long idx = tid; idx < (long long)m * nl; idx += 256) {
-        const int i = (int)(idx % m), lc = (int)(idx / m), k = rank + lc * C;
-        const double bb = absv(betas[k]);  // column k is local: its beta is in this CTA
-        const S ph = bb > 0.0 ? divr(betas[k], bb) : one<S>();
-        S v = mul(Q[(size_t)lc * m + i], ph);
+    for (int idx = tid; idx < m * nl; idx += 256) {
+        const int lc = idx / m, i = idx - lc * m, k = rank + lc * C;
+        S v = apply_phase(Q[idx], phs[lc]);
         if (t.conj_io) v = conjv(v);
         out[(long long)i * t.out_rs + (long long)k * t.out_cs] = v;
         if (t.out2) {
@@ -623,7 +747,7 @@ __global__ void __launch_bounds__(256) k_qr_cluster(const QRTask* __restrict__ t
     cluster.sync();  // no CTA leaves while another may still read its shared memory
 }
 
-constexpr size_t QR_CLUSTER_SMEM = QR_SMEM_LIMIT + QR_MAXN * (8 + 16) + 16;
+constexpr size_t QR_CLUSTER_SMEM = QR_SMEM_LIMIT + QR_MAXN * (16 + 16) + 16;
 
 static int sm_count() {
     static std::atomic<int> cached{0};  // read by the server's worker and read-out threads
@@ -640,7 +764,7 @@ static int sm_count() {
 static size_t qr_cluster_smem(int max_m, long long max_mn, int C, size_t ss) {
     // m * ceil(n / C) <= m * n / C + m
     const size_t cols = (size_t)(max_mn / C) + (size_t)max_m;
-    return (2 * (size_t)max_m + 2 * cols) * ss + QR_MAXN * (8 + ss) + 16;
+    return (2 * (size_t)max_m + 2 * cols) * ss + QR_MAXN * (16 + ss) + 16;
 }
 
 static size_t qr_smem_bytes(int max_m, long long max_mn, bool cplx, int* resident) {
@@ -676,10 +800,14 @@ cudaError_t qr_prepare(int max_m, bool cplx) {
 
 cudaError_t launch_qr(const QRTask* d_tasks, int ntasks, int max_m, long long max_mn, bool cplx, cudaStream_t s) {
     if (ntasks <= 0) return cudaSuccess;
-    // few tasks: spread each over a cluster so that the launch covers the SMs
+    // Spread each task over C CTAs so that the launch covers the SMs (with at least two
+    // columns per CTA), and over more CTAs if its matrix does not fit one CTA's shared memory.
     const size_t ssz = cplx ? sizeof(double2) : sizeof(double);
-    const int C = std::min(8, std::max(1, sm_count() / ntasks));
-    if (C > 1 && max_mn / max_m >= 2 * C && qr_cluster_smem(max_m, max_mn, C, ssz) <= QR_CLUSTER_SMEM) {
+    const int n_est = (int)std::max<long long>(1, max_mn / std::max(1, max_m));
+    int C = std::min(8, std::max(1, sm_count() / ntasks));
+    C = std::max(1, std::min(C, n_est / 2));
+    while (C < 8 && qr_cluster_smem(max_m, max_mn, C, ssz) > QR_CLUSTER_SMEM) ++C;
+    if (qr_cluster_smem(max_m, max_mn, C, ssz) <= QR_CLUSTER_SMEM) {
         const size_t sm = qr_cluster_smem(max_m, max_mn, C, ssz);
         cudaLaunchConfig_t cfg = {};
         cudaLaunchAttribute attr[1];
@@ -696,6 +824,8 @@ cudaError_t launch_qr(const QRTask* d_tasks, int ntasks, int max_m, long long ma
         return cplx ? cudaLaunchKernelEx(&cfg, k_qr_cluster<double2>, d_tasks, C)
                     : cudaLaunchKernelEx(&cfg, k_qr_cluster<double>, d_tasks, C);
     }
+    // too large for the shared memory of a cluster: one CTA per task, W and Q in the task's
+    // global workspace
     int resident = 0;
     const size_t sm = qr_smem_bytes(max_m, max_mn, cplx, &resident);
     if (cplx)

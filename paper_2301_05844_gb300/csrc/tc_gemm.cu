@@ -3,7 +3,7 @@
 //   C[m][n] = sum_k A[m][k] * B[n][k]      (A, B K-major; FP32 accumulation in TMEM)
 //
 // One CTA computes a 128 x BN tile of one task.  Warp 0 (one lane) streams A and B
-// k-blocks with TMA into a 4-stage ring of 128-byte-swizzled shared memory; warp 1
+// k-blocks with TMA into a ring of 2-8 stages of 128-byte-swizzled shared memory; warp 1
 // (one lane) issues tcgen05.mma (kind::tf32 or kind::f16 with BF16 operands) into a
 // TMEM accumulator; all four warps then read the accumulator with tcgen05.ld and
 // scatter it through a two-level index map (the same map as the FP64 contraction),
@@ -27,7 +27,7 @@ namespace bbp {
 namespace tc {
 
 constexpr int BM = 128;
-constexpr int STAGES = 4;
+constexpr int STAGES = 8;  // deepest operand ring (mbarrier arrays); see tc_max_stages
 constexpr int KBYTES = 128;  // bytes of K per stage row (one 128-byte swizzle atom)
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -384,12 +384,20 @@ static size_t tc_smem(int stages, int bn) {
     return std::max(ring, tile) + 1024;
 }
 
+// Deepest ring that fits the 227 KB of shared memory a CTA may hold (2 KB kept for the
+// static barriers): 8 stages for BN <= 64, 7 for 128, 4 for 256.
+int tc_max_stages(int bn) {
+    const size_t per = (size_t)(tc::BM + bn) * tc::KBYTES;
+    const size_t cap = 232448 - 2048 - 1024;
+    return std::max(1, std::min(tc::STAGES, (int)(cap / per)));
+}
+
 cudaError_t tc_prepare() {
     // sets the shared-memory limits outside any stream capture
     cudaError_t e;
     const int bns[4] = {32, 64, 128, 256};
     for (int i = 0; i < 4; ++i) {
-        const size_t smem = tc_smem(tc::STAGES, bns[i]);
+        const size_t smem = tc_smem(tc_max_stages(bns[i]), bns[i]);
         switch (bns[i]) {
             case 32:
                 if ((e = cudaFuncSetAttribute(tc::k_tc_gemm<0, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))) return e;
@@ -414,7 +422,7 @@ cudaError_t tc_prepare() {
 cudaError_t launch_tc_gemm(const TCTask* d_tasks, int ntasks, int kind, int bn, int max_tiles, int stages, int* err,
                            cudaStream_t s) {
     if (ntasks <= 0) return cudaSuccess;
-    if (stages < 1 || stages > tc::STAGES) return cudaErrorInvalidValue;
+    if (stages < 1 || stages > tc_max_stages(bn)) return cudaErrorInvalidValue;
     const size_t smem = tc_smem(stages, bn);
     dim3 grid(max_tiles, ntasks);
 #define TC_CASE(K_, N_)                                                                          \

@@ -266,7 +266,14 @@ __device__ __forceinline__ void epilogue_dest(const float* tile, long long* roff
 
 template <int KIND, int BN>
 __global__ void __launch_bounds__(128) k_tc_gemm(const TCTask* __restrict__ tasks, int* err, int stages) {
-    const TCTask& t = tasks[blockIdx.y];
+    // The task descriptor is copied to shared memory in one coalesced read (its fields are
+    // otherwise fetched from global memory one dependent load at a time); the TMA copies use
+    // the tensor maps at their global address.
+    __shared__ TCTask t;
+    const TCTask* gt = tasks + blockIdx.y;
+    for (int w = threadIdx.x; w < (int)(sizeof(TCTask) / 4); w += 128)
+        ((uint32_t*)&t)[w] = ((const uint32_t*)gt)[w];
+    __syncthreads();
     if (t.active && *t.active == 0) return;
     const int tilesM = (t.M + BM - 1) / BM, tilesN = (t.N + BN - 1) / BN;
     if ((int)blockIdx.x >= tilesM * tilesN) return;
@@ -292,8 +299,8 @@ __global__ void __launch_bounds__(128) k_tc_gemm(const TCTask* __restrict__ task
         mbar_init(&accum, 1);
         issued = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        prefetch_map(&t.map_a);
-        prefetch_map(&t.map_b);
+        prefetch_map(&gt->map_a);
+        prefetch_map(&gt->map_b);
     }
     if (warp == 0) tmem_alloc(&tmem_base, BN < 32 ? 32 : BN);
     fence_before();
@@ -307,8 +314,8 @@ __global__ void __launch_bounds__(128) k_tc_gemm(const TCTask* __restrict__ task
             const int s = kb % stages, r = kb / stages;
             if (r > 0 && !mbar_wait(&empty[s], (r - 1) & 1, err)) break;
             mbar_expect_tx(&full[s], A_BYTES + B_BYTES);
-            tma_load_2d(sA + s * A_BYTES, &t.map_a, &full[s], kb * EK, m0);
-            tma_load_2d(sB + s * B_BYTES, &t.map_b, &full[s], kb * EK, n0);
+            tma_load_2d(sA + s * A_BYTES, &gt->map_a, &full[s], kb * EK, m0);
+            tma_load_2d(sB + s * B_BYTES, &gt->map_b, &full[s], kb * EK, n0);
             issued = kb + 1;
         }
     } else if (warp == 1 && lane == 0) {

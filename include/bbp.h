@@ -233,17 +233,21 @@ int bbp_selftest_gemm(int M, int N, int K, int prec, const float* A, const float
 int bbp_time_kernels(bbp_lattice* lat, int kernel_class, int reps, double* ms, long long* launches,
                      double* flops, double* bytes);
 
-/* Tile-shape autotuner for the tensor-core path (the batching pattern's tiles chosen per
- * workload rather than by a fixed rule).  Must run after bbp_set_tensors and before the
- * first bbp_sweep.  For every tensor-core step of the planned sweep it times, with CUDA
- * events on the handle's stream and every fit stage active, each candidate tile width
- * BN in {32, 64, 128, 256} (up to the widest result) and TMA ring depth in {2, 3, 4} (up to
- * the number of k-blocks), reps launches each after one warm-up, and keeps the fastest.
- * Results do not change: the K-accumulation order of a tile is the same for every
- * candidate.  The replays write only work buffers (the fits start from fresh draws at the
- * first sweep).  Outputs (may be NULL): summed per-launch milliseconds of the steps with the
- * default and with the chosen tiles, and how many steps changed.  No-op (OK, zeros) on
- * the FP64 path.  Errors: INVALID, STATE (no tensors, or sweeps already run), TIMEOUT, CUDA. */
+/* Launch-shape autotuner (the batching pattern's tiles chosen per workload rather than by a
+ * fixed rule).  Must run after bbp_set_tensors and before the first bbp_sweep.  It times,
+ * with CUDA events on the handle's stream and every fit stage active, reps launches of each
+ * candidate after one warm-up, and keeps the fastest:
+ *  - tensor-core steps (TF32 / BF16 paths): tile width BN in {32, 64, 128, 256} (up to the
+ *    widest result) and TMA ring depth in {2, 3, 4, 6, 8} (up to the number of k-blocks and
+ *    what shared memory holds); the K-accumulation order of a tile is the same for every
+ *    candidate;
+ *  - QR/LQ steps (every path): the number of CTAs (1-8) one matrix is spread over, kept
+ *    only if clearly faster than the built-in rule; every column's arithmetic, and the fit
+ *    loss, are the same for every cluster size.
+ * Results therefore do not change.  The replays write only work buffers (the fits start from
+ * fresh draws at the first sweep).  Outputs (may be NULL): summed per-launch milliseconds of
+ * the tuned steps with the default and with the chosen shapes, and how many steps changed.
+ * Errors: INVALID, STATE (no tensors, or sweeps already run), TIMEOUT, CUDA. */
 int bbp_autotune(bbp_lattice* lat, int reps, double* ms_before, double* ms_after, int* steps_changed);
 
 /* The library's counter-based generator (the one that draws the initial fit states

@@ -157,7 +157,12 @@ struct FuseTask {
 cudaError_t launch_gcontract(const GTask* d_tasks, int ntasks, int max_tiles, bool cplx, cudaStream_t s);
 cudaError_t qr_prepare(int max_m, bool cplx);  // sets the dynamic shared memory limit once
 // max_mn: largest m*n of the launch; small problems keep their matrices in shared memory.
-cudaError_t launch_qr(const QRTask* d_tasks, int ntasks, int max_m, long long max_mn, bool cplx, cudaStream_t s);
+// cluster > 0: spread each task over that many CTAs (if its matrices fit; else the smallest
+// larger C that fits); 0: the built-in rule.  The result does not depend on it.
+cudaError_t launch_qr(const QRTask* d_tasks, int ntasks, int max_m, long long max_mn, bool cplx, cudaStream_t s,
+                      int cluster = 0);
+// whether one QR of the given maximal shape fits a cluster of C CTAs
+bool qr_cluster_fits(int max_m, long long max_mn, bool cplx, int C);
 // sweep_ctr != nullptr: the current sweep index is OR-ed into bits 36.. of each stream.
 cudaError_t launch_rand(const RandTask* d_tasks, int ntasks, unsigned long long seed, const int* sweep_ctr,
                         bool cplx, cudaStream_t s);

@@ -686,7 +686,7 @@ cudaError_t Program::upload_tasks(cudaStream_t st) {
 cudaError_t Program::launch_step(const Step& s, cudaStream_t st, const int* sweep_ctr, unsigned long long seed) const {
     switch (s.kind) {
         case ST_GC: return launch_gcontract(d_gc + s.first, s.count, s.aux, cplx, st);
-        case ST_QR: return launch_qr(d_qr + s.first, s.count, s.aux, s.n, cplx, st);
+        case ST_QR: return launch_qr(d_qr + s.first, s.count, s.aux, s.n, cplx, st, s.aux2);
         case ST_RAND: return launch_rand(d_rnd + s.first, s.count, seed, s.aux ? sweep_ctr : nullptr, cplx, st);
         case ST_SETACT: return launch_set_int((int*)s.p0, (int)s.n, s.aux, st);
         case ST_CHECK: return launch_check(d_chk + s.first, s.count, fit_tol, (LoopDesc*)s.p1, st);
@@ -841,7 +841,7 @@ cudaError_t Program::launch_class(cudaStream_t st, const int* sweep_ctr, unsigne
                 }
                 break;
             case ST_QR:
-                e = launch_qr(d_qr + s.first, s.count, s.aux, s.n, cplx, st);
+                e = launch_qr(d_qr + s.first, s.count, s.aux, s.n, cplx, st, s.aux2);
                 for (int i = 0; i < s.count; ++i) {
                     const QRTask& t = qr[s.first + i];
                     f += (4.0 * t.m * (double)t.n * t.n - 4.0 / 3.0 * (double)t.n * t.n * t.n) * (cplx ? 4.0 : 1.0);

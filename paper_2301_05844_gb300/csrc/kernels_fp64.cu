@@ -632,12 +632,9 @@ __global__ void __launch_bounds__(256) k_qr_cluster(const QRTask* __restrict__ t
     double* taus = (double*)(Q + (size_t)m * nlmax);
     double* tall = taus + QR_MAXN;
     S* betas = (S*)(tall + QR_MAXN);
-    double* part = (double*)(betas + QR_MAXN);
-    __shared__ double redd[32];
     __shared__ S phs[QR_MAXN];
     __shared__ ChainScratch<S> cs;
     const S* in = (const S*)t.in;
-    double ss = 0.0;
     for (int idx = tid; idx < m * nl; idx += 256) {
         const int lc = idx / m, i = idx - lc * m, j = rank + lc * C;
         const long long src = (long long)i * t.in_rs + (long long)j * t.in_cs;
@@ -646,18 +643,25 @@ __global__ void __launch_bounds__(256) k_qr_cluster(const QRTask* __restrict__ t
         else v = in[src];
         if (t.conj_io) v = conjv(v);
         W[idx] = v;
-        if (t.loss) ss += abs2(v);
     }
-    if (t.loss) {  // uniform: the loss -||A||^2 of the fit (App. A)
-        ss = block_sum(ss, redd);
-        if (tid == 0) part[0] = ss;
+    if (t.loss) {  // uniform: squared column norms, for the loss -||A||^2 of the fit (App. A)
+        __syncthreads();
+        for (int lc = warp; lc < nl; lc += 8) {
+            double p = 0.0;
+            for (int i = lane; i < m; i += 32) p += abs2(W[(size_t)lc * m + i]);
+            p = warp_tree(p);
+            if (lane == 0) tall[lc] = p;  // tall is free until the R phase ends
+        }
     }
-    cluster.sync();  // W loaded everywhere; partial norms published
-    if (rank == 0 && tid == 0 && t.loss) {
-        double tot = 0.0;
-        for (int r = 0; r < C; ++r) tot += *cluster.map_shared_rank(part, r);
-        *t.loss = -tot;
-    }
+    cluster.sync();  // W loaded everywhere; column norms published
+    if (rank == 0 && warp == 0 && t.loss) {
+        // summed over columns in a fixed order (lane j takes columns j, j + 32, ...), so that
+        // the loss does not depend on how the columns are spread over the cluster
+        double p = 0.0;
+        for (int j = lane; j < n; j += 32) p += *cluster.map_shared_rank(tall + j / C, j % C);
+        p = warp_tree(p);
+        if (lane == 0) *t.loss = -p;
+    }  // tall is rewritten only after the R phase, when every CTA is past this read
     // ---- R: phase p of the split cluster barrier publishes v_p and tau_p
     if (n > 0) {
         if (rank == 0 && warp < 4) chain_reflector(W, u, 0.0, 0, 0, m, cs, taus, betas);
@@ -798,14 +802,21 @@ cudaError_t qr_prepare(int max_m, bool cplx) {
     return e;
 }
 
-cudaError_t launch_qr(const QRTask* d_tasks, int ntasks, int max_m, long long max_mn, bool cplx, cudaStream_t s) {
+bool qr_cluster_fits(int max_m, long long max_mn, bool cplx, int C) {
+    return C >= 1 && C <= 8 && qr_cluster_smem(max_m, max_mn, C, cplx ? sizeof(double2) : sizeof(double)) <= QR_CLUSTER_SMEM;
+}
+
+cudaError_t launch_qr(const QRTask* d_tasks, int ntasks, int max_m, long long max_mn, bool cplx, cudaStream_t s,
+                      int cluster) {
     if (ntasks <= 0) return cudaSuccess;
     // Spread each task over C CTAs so that the launch covers the SMs (with at least two
     // columns per CTA), and over more CTAs if its matrix does not fit one CTA's shared memory.
+    // cluster > 0 asks for that C (the autotuner's choice; the result is the same for every C).
     const size_t ssz = cplx ? sizeof(double2) : sizeof(double);
     const int n_est = (int)std::max<long long>(1, max_mn / std::max(1, max_m));
     int C = std::min(8, std::max(1, sm_count() / ntasks));
     C = std::max(1, std::min(C, n_est / 2));
+    if (cluster > 0) C = std::min(8, cluster);
     while (C < 8 && qr_cluster_smem(max_m, max_mn, C, ssz) > QR_CLUSTER_SMEM) ++C;
     if (qr_cluster_smem(max_m, max_mn, C, ssz) <= QR_CLUSTER_SMEM) {
         const size_t sm = qr_cluster_smem(max_m, max_mn, C, ssz);

@@ -1056,6 +1056,19 @@ int bbp_time_kernels(bbp_lattice* L, int cls, int reps, double* ms, long long* l
     return BBP_OK;
 }
 
+// Time `reps` launches of step si (after one warm-up) with CUDA events on the handle's stream.
+static cudaError_t time_step(bbp_lattice* L, size_t si, int reps, cudaEvent_t a, cudaEvent_t b, float* ms) {
+    Program& pr = L->sweep;
+    cudaStream_t st = L->stream;
+    cudaError_t e = pr.launch_step(pr.steps[si], st, L->d_sweep, L->desc.seed);
+    if (e == cudaSuccess) e = cudaEventRecord(a, st);
+    for (int r = 0; r < reps && e == cudaSuccess; ++r) e = pr.launch_step(pr.steps[si], st, L->d_sweep, L->desc.seed);
+    if (e == cudaSuccess) e = cudaEventRecord(b, st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(b);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(ms, a, b);
+    return e;
+}
+
 int bbp_autotune(bbp_lattice* L, int reps, double* ms_before, double* ms_after, int* steps_changed) {
     if (!L) return fail(BBP_ERR_INVALID, "lattice is NULL");
     if (reps < 1) return fail(BBP_ERR_INVALID, "reps must be >= 1");
@@ -1063,17 +1076,17 @@ int bbp_autotune(bbp_lattice* L, int reps, double* ms_before, double* ms_after, 
     if (L->sweeps > 0 || L->sweep.exec) return fail(BBP_ERR_STATE, "autotune must run before the first sweep");
     double before = 0.0, after = 0.0;
     int changed = 0;
-    if (L->mixed) {
-        Program& pr = L->sweep;
-        cudaStream_t st = L->stream;
-        cudaEvent_t a, b;
-        CKR(cudaEventCreate(&a));
-        CKR(cudaEventCreate(&b));
-        CKR(pr.reset_active(st));  // every fit stage runs, as in a first sweep
-        const int ek = L->cx.tck == 0 ? 32 : 64;  // K elements per k-block
-        for (size_t si = 0; si < pr.steps.size(); ++si) {
-            if (pr.steps[si].kind != ST_TC) continue;
-            const Step s0 = pr.steps[si];
+    Program& pr = L->sweep;
+    cudaStream_t st = L->stream;
+    cudaEvent_t a, b;
+    CKR(cudaEventCreate(&a));
+    CKR(cudaEventCreate(&b));
+    CKR(pr.reset_active(st));  // every fit stage runs, as in a first sweep
+    const int ek = L->cx.tck == 0 ? 32 : 64;  // K elements per k-block
+    for (size_t si = 0; si < pr.steps.size(); ++si) {
+        const Step s0 = pr.steps[si];
+        if (s0.kind == ST_TC && L->mixed) {
+            // tensor-core tiles: width BN and TMA ring depth
             int nmax = 1, kmax = 1;
             for (int i = 0; i < s0.count; ++i) {
                 nmax = std::max(nmax, pr.tcs[s0.first + i].N);
@@ -1087,13 +1100,8 @@ int bbp_autotune(bbp_lattice* L, int reps, double* ms_before, double* ms_after, 
                 for (int depth : {2, 3, 4, 6, 8}) {
                     if (depth > std::max(2, kmax) || depth > tc_max_stages(bn)) break;
                     CKR(pr.tc_retile(si, bn, depth, L->arena, (size_t)-1, nullptr, st));
-                    CKR(pr.launch_step(pr.steps[si], st, L->d_sweep, L->desc.seed));  // warm-up
-                    CKR(cudaEventRecord(a, st));
-                    for (int r = 0; r < reps; ++r) CKR(pr.launch_step(pr.steps[si], st, L->d_sweep, L->desc.seed));
-                    CKR(cudaEventRecord(b, st));
-                    CKR(cudaEventSynchronize(b));
                     float t = 0.0f;
-                    CKR(cudaEventElapsedTime(&t, a, b));
+                    CKR(time_step(L, si, reps, a, b, &t));
                     if (bn == bn0 && depth == d0) t0 = t;
                     if (best < 0.0f || t < best) {
                         best = t;
@@ -1106,14 +1114,33 @@ int bbp_autotune(bbp_lattice* L, int reps, double* ms_before, double* ms_after, 
             if (best_bn != bn0 || best_d != d0) ++changed;
             before += (t0 >= 0.0f ? t0 : best) / reps;
             after += best / reps;
+        } else if (s0.kind == ST_QR && qr_cluster_fits(s0.aux, s0.n, pr.cplx, 1)) {
+            // QR/LQ: cluster size (0: the built-in rule); the result is the same for every C
+            int best_c = 0;
+            float best = -1.0f, t0 = -1.0f;
+            for (int c = 0; c <= 8; ++c) {
+                if (c > 0 && !qr_cluster_fits(s0.aux, s0.n, pr.cplx, c)) continue;
+                pr.steps[si].aux2 = c;
+                float t = 0.0f;
+                CKR(time_step(L, si, reps, a, b, &t));
+                if (c == 0) t0 = t;
+                if (best < 0.0f || t < best * 0.98f) {  // keep the rule unless a size is clearly faster
+                    best = t;
+                    best_c = c;
+                }
+            }
+            pr.steps[si].aux2 = best_c;
+            if (best_c != 0) ++changed;
+            before += t0 / reps;
+            after += best / reps;
         }
-        CKR(cudaStreamSynchronize(st));
-        cudaEventDestroy(a);
-        cudaEventDestroy(b);
-        int te = 0;
-        CKR(cudaMemcpy(&te, L->d_tcerr, sizeof(int), cudaMemcpyDeviceToHost));
-        if (te) return fail(BBP_ERR_TIMEOUT, "a tensor-core pipeline wait exceeded its bound");
     }
+    CKR(cudaStreamSynchronize(st));
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    int te = 0;
+    if (L->mixed) CKR(cudaMemcpy(&te, L->d_tcerr, sizeof(int), cudaMemcpyDeviceToHost));
+    if (te) return fail(BBP_ERR_TIMEOUT, "a tensor-core pipeline wait exceeded its bound");
     if (ms_before) *ms_before = before;
     if (ms_after) *ms_after = after;
     if (steps_changed) *steps_changed = changed;

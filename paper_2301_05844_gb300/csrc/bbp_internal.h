@@ -154,7 +154,9 @@ struct FuseTask {
 };
 
 // Launchers (kernels.cu).  cplx selects double2 (complex) over double.
-cudaError_t launch_gcontract(const GTask* d_tasks, int ntasks, int max_tiles, bool cplx, cudaStream_t s);
+// small != 0: 16x16 output tiles, one output per thread (steps whose outputs have a
+// dimension of at most 16); max_tiles counts tiles of the chosen size.
+cudaError_t launch_gcontract(const GTask* d_tasks, int ntasks, int max_tiles, bool cplx, cudaStream_t s, int small);
 cudaError_t qr_prepare(int max_m, bool cplx);  // sets the dynamic shared memory limit once
 // max_mn: largest m*n of the launch; small problems keep their matrices in shared memory.
 // cluster > 0: spread each task over that many CTAs (if its matrices fit; else the smallest

@@ -218,10 +218,15 @@ void Program::gc_step(std::vector<GTask>& ts) {
     s.kind = ST_GC;
     s.first = gc.size();
     s.count = (int)ts.size();
+    // 64x64 output tiles, or 16x16 ones (k_gcontract_small) when every task has an output
+    // dimension of at most 16, where a 64x64 tile would be mostly padding
+    bool small = true;
+    for (auto& t : ts) small = small && std::min((long long)t.M1 * t.M2, (long long)t.N1 * t.N2) <= 16;
+    const int tile = small ? 16 : 64;
     int mt = 1;
     for (auto& t : ts) {
         const long long M = (long long)t.M1 * t.M2, N = (long long)t.N1 * t.N2, K = (long long)t.K1 * t.K2;
-        const int tiles = (int)(((M + 63) / 64) * ((N + 63) / 64));
+        const int tiles = (int)(((M + tile - 1) / tile) * ((N + tile - 1) / tile));
         mt = std::max(mt, tiles);
         const double f = 2.0 * (double)M * (double)N * (double)K * (cplx ? 4.0 : 1.0);
         if (t.active) gated_flops += f;
@@ -229,6 +234,7 @@ void Program::gc_step(std::vector<GTask>& ts) {
         gc.push_back(t);
     }
     s.aux = mt;
+    s.aux2 = small ? 1 : 0;
     steps.push_back(s);
     ts.clear();
 }
@@ -685,7 +691,7 @@ cudaError_t Program::upload_tasks(cudaStream_t st) {
 
 cudaError_t Program::launch_step(const Step& s, cudaStream_t st, const int* sweep_ctr, unsigned long long seed) const {
     switch (s.kind) {
-        case ST_GC: return launch_gcontract(d_gc + s.first, s.count, s.aux, cplx, st);
+        case ST_GC: return launch_gcontract(d_gc + s.first, s.count, s.aux, cplx, st, s.aux2);
         case ST_QR: return launch_qr(d_qr + s.first, s.count, s.aux, s.n, cplx, st, s.aux2);
         case ST_RAND: return launch_rand(d_rnd + s.first, s.count, seed, s.aux ? sweep_ctr : nullptr, cplx, st);
         case ST_SETACT: return launch_set_int((int*)s.p0, (int)s.n, s.aux, st);
@@ -832,7 +838,7 @@ cudaError_t Program::launch_class(cudaStream_t st, const int* sweep_ctr, unsigne
         cudaError_t e = cudaSuccess;
         switch (s.kind) {
             case ST_GC:
-                e = launch_gcontract(d_gc + s.first, s.count, s.aux, cplx, st);
+                e = launch_gcontract(d_gc + s.first, s.count, s.aux, cplx, st, s.aux2);
                 for (int i = 0; i < s.count; ++i) {
                     const GTask& t = gc[s.first + i];
                     const double M = (double)t.M1 * t.M2, N = (double)t.N1 * t.N2, K = (double)t.K1 * t.K2;

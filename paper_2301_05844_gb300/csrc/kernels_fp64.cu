@@ -237,13 +237,59 @@ __global__ void __launch_bounds__(256) k_gcontract(const GTask* __restrict__ tas
     }
 }
 
-cudaError_t launch_gcontract(const GTask* d_tasks, int ntasks, int max_tiles, bool cplx, cudaStream_t s) {
+// Small contractions (an output dimension of at most 16, e.g. the message overlaps): a 16x16
+// output tile per CTA, one output per thread, operands read through the cache.  A 64x64 tile
+// would spend most of its FP64 instructions on padding, and each warp-wide FP64 instruction
+// costs the same however few lanes do useful work.  The K sum runs in four interleaved partial
+// sums (four independent FP64 chains instead of one), added in a fixed order.
+template <typename S>
+__global__ void __launch_bounds__(256) k_gcontract_small(const GTask* __restrict__ tasks) {
+    const GTask& t = tasks[blockIdx.y];
+    if (t.active && *t.active == 0) return;
+    const int M = t.M1 * t.M2, N = t.N1 * t.N2, Kd = t.K1 * t.K2;
+    const int tilesM = (M + 15) >> 4, tilesN = (N + 15) >> 4;
+    if ((int)blockIdx.x >= tilesM * tilesN) return;
+    const int m = ((blockIdx.x % tilesM) << 4) + (threadIdx.x & 15);
+    const int n = ((blockIdx.x / tilesM) << 4) + (threadIdx.x >> 4);
+    if (m >= M || n >= N) return;
+    const S* __restrict__ Ap = (const S*)t.A;
+    const S* __restrict__ Bp = (const S*)t.B;
+    const long long aoff = (long long)(m / t.M2) * t.a_m1 + (long long)(m % t.M2) * t.a_m2;
+    const long long boff = (long long)(n / t.N2) * t.b_n1 + (long long)(n % t.N2) * t.b_n2;
+    S p[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) p[q] = zero<S>();
+    int k1 = 0, k2 = 0;  // k = k1 * K2 + k2
+#pragma unroll 4
+    for (int k = 0; k < Kd; ++k) {
+        S a = Ap[aoff + (long long)k1 * t.a_k1 + (long long)k2 * t.a_k2];
+        if (t.conjA) a = conjv(a);
+        mac(p[k & 3], a, Bp[boff + (long long)k1 * t.b_k1 + (long long)k2 * t.b_k2]);
+        if (++k2 == t.K2) {
+            k2 = 0;
+            ++k1;
+        }
+    }
+    const S r = add(add(p[0], p[1]), add(p[2], p[3]));
+    S* __restrict__ Cp = (S*)t.C;
+    const long long o = (long long)(m / t.M2) * t.c_m1 + (long long)(m % t.M2) * t.c_m2 +
+                        (long long)(n / t.N2) * t.c_n1 + (long long)(n % t.N2) * t.c_n2;
+    Cp[o] = t.accumulate ? add(Cp[o], r) : r;
+}
+
+cudaError_t launch_gcontract(const GTask* d_tasks, int ntasks, int max_tiles, bool cplx, cudaStream_t s, int small) {
     if (ntasks <= 0) return cudaSuccess;
     dim3 grid(max_tiles, ntasks);
-    if (cplx)
+    if (small) {
+        if (cplx)
+            k_gcontract_small<double2><<<grid, 256, 0, s>>>(d_tasks);
+        else
+            k_gcontract_small<double><<<grid, 256, 0, s>>>(d_tasks);
+    } else if (cplx) {
         k_gcontract<double2><<<grid, 256, 0, s>>>(d_tasks);
-    else
+    } else {
         k_gcontract<double><<<grid, 256, 0, s>>>(d_tasks);
+    }
     return cudaGetLastError();
 }
 

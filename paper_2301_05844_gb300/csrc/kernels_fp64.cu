@@ -681,14 +681,27 @@ __global__ void __launch_bounds__(256) k_qr_cluster(const QRTask* __restrict__ t
     __shared__ S phs[QR_MAXN];
     __shared__ ChainScratch<S> cs;
     const S* in = (const S*)t.in;
-    for (int idx = tid; idx < m * nl; idx += 256) {
-        const int lc = idx / m, i = idx - lc * m, j = rank + lc * C;
-        const long long src = (long long)i * t.in_rs + (long long)j * t.in_cs;
-        S v;
-        if (t.in_float) v = from_float<S>(((const float*)t.in), src);
-        else v = in[src];
-        if (t.conj_io) v = conjv(v);
-        W[idx] = v;
+    {
+        // eight loads per thread in flight at a time (each is a round trip to L2)
+        constexpr int LB = 8;
+        const int total = m * nl;
+        for (int base = 0; base < total; base += 256 * LB) {
+            S v[LB];
+#pragma unroll
+            for (int q = 0; q < LB; ++q) {
+                const int idx = base + q * 256 + tid;
+                if (idx < total) {
+                    const int lc = idx / m, i = idx - lc * m, j = rank + lc * C;
+                    const long long src = (long long)i * t.in_rs + (long long)j * t.in_cs;
+                    v[q] = t.in_float ? from_float<S>(((const float*)t.in), src) : in[src];
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < LB; ++q) {
+                const int idx = base + q * 256 + tid;
+                if (idx < total) W[idx] = t.conj_io ? conjv(v[q]) : v[q];
+            }
+        }
     }
     if (t.loss) {  // uniform: squared column norms, for the loss -||A||^2 of the fit (App. A)
         __syncthreads();

@@ -32,6 +32,11 @@ constexpr int KBYTES = 128;  // bytes of K per stage row (one 128-byte swizzle a
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
+// Programmatic dependent launch: wait for the previous kernel's completion (and its memory),
+// and allow the next kernel to be scheduled.
+__device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
 }
@@ -274,7 +279,6 @@ __global__ void __launch_bounds__(128) k_tc_gemm(const TCTask* __restrict__ task
     for (int w = threadIdx.x; w < (int)(sizeof(TCTask) / 4); w += 128)
         ((uint32_t*)&t)[w] = ((const uint32_t*)gt)[w];
     __syncthreads();
-    if (t.active && *t.active == 0) return;
     const int tilesM = (t.M + BM - 1) / BM, tilesN = (t.N + BN - 1) / BN;
     if ((int)blockIdx.x >= tilesM * tilesN) return;
     const int m0 = (blockIdx.x % tilesM) * BM, n0 = (blockIdx.x / tilesM) * BN;
@@ -307,6 +311,13 @@ __global__ void __launch_bounds__(128) k_tc_gemm(const TCTask* __restrict__ task
     __syncthreads();
     fence_after();
     const uint32_t tmem = tmem_base;
+    // Everything above reads only the static task descriptor, so it may overlap the previous
+    // kernel (programmatic dependent launch); the active flag and the operands are its output.
+    grid_dependency_wait();
+    if (t.active && *t.active == 0) {
+        if (warp == 0) tmem_dealloc(tmem, BN < 32 ? 32 : BN);
+        return;
+    }
 
     if (warp == 0 && lane == 0) {
         // TMA producer
@@ -339,6 +350,7 @@ __global__ void __launch_bounds__(128) k_tc_gemm(const TCTask* __restrict__ task
     // epilogue: every warp waits for the accumulator, stages its 32 rows in shared memory
     // (the operand ring is free: every issued copy was consumed by a finished MMA)
     const bool ready = mbar_wait(&accum, 0, err);
+    launch_dependents();  // the next kernel may start its prologue during this epilogue
     fence_after();
     if (__syncthreads_and(ready ? 1 : 0)) {
         const int ncols = min(BN, t.N - n0), rows = min(BM, t.M - m0);
@@ -432,11 +444,20 @@ cudaError_t launch_tc_gemm(const TCTask* d_tasks, int ntasks, int kind, int bn, 
     if (stages < 1 || stages > tc_max_stages(bn)) return cudaErrorInvalidValue;
     const size_t smem = tc_smem(stages, bn);
     dim3 grid(max_tiles, ntasks);
-#define TC_CASE(K_, N_)                                                                          \
-    if (kind == K_ && bn == N_) {                                                                \
-        tc::k_tc_gemm<K_, N_><<<grid, 128, smem, s>>>(d_tasks, err, stages);                     \
-        return cudaGetLastError();                                                               \
-    }
+    // programmatic dependent launch: the kernel waits (griddepcontrol.wait) before it reads
+    // anything an earlier kernel wrote
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3(128);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+#define TC_CASE(K_, N_)                                                              \
+    if (kind == K_ && bn == N_) return cudaLaunchKernelEx(&cfg, tc::k_tc_gemm<K_, N_>, d_tasks, err, stages);
     TC_CASE(0, 32) TC_CASE(0, 64) TC_CASE(0, 128) TC_CASE(0, 256)
     TC_CASE(1, 32) TC_CASE(1, 64) TC_CASE(1, 128) TC_CASE(1, 256)
 #undef TC_CASE

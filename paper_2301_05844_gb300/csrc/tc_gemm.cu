@@ -352,7 +352,8 @@ __global__ void __launch_bounds__(128) k_tc_gemm(const TCTask* __restrict__ task
     const bool ready = mbar_wait(&accum, 0, err);
     launch_dependents();  // the next kernel may start its prologue during this epilogue
     fence_after();
-    if (__syncthreads_and(ready ? 1 : 0)) {
+    const int all_ready = __syncthreads_and(ready ? 1 : 0);
+    if (all_ready) {
         const int ncols = min(BN, t.N - n0), rows = min(BM, t.M - m0);
         float* tile = (float*)smem;
         long long* roff = (long long*)(tile + BM * (EC + 1));
@@ -383,8 +384,10 @@ __global__ void __launch_bounds__(128) k_tc_gemm(const TCTask* __restrict__ task
     }
     fence_before();
     __syncthreads();
-    // drain: the producer's copies must have landed before shared memory is released
-    if (threadIdx.x == 0) {
+    // drain: the producer's copies must have landed before shared memory is released.  On
+    // success the MMA warp already waited for every issued copy, so only a pipeline that
+    // stopped on a timed-out wait can still have copies in flight.
+    if (!all_ready && threadIdx.x == 0) {
         const int n_issued = issued;
         for (int kb = (n_issued > stages ? n_issued - stages : 0); kb < n_issued; ++kb)
             mbar_wait(&full[kb % stages], (kb / stages) & 1, err);

@@ -1097,8 +1097,8 @@ int bbp_autotune(bbp_lattice* L, int reps, double* ms_before, double* ms_after, 
             float best = -1.0f, t0 = -1.0f;
             for (int bn : {32, 64, 128, 256}) {
                 if (bn > 32 && bn / 2 >= nmax) break;  // wider tiles than the widest result
-                for (int depth : {2, 3, 4, 6, 8}) {
-                    if (depth > std::max(2, kmax) || depth > tc_max_stages(bn)) break;
+                for (int depth : {2, 3, 4, 5}) {  // stages of two k-blocks
+                    if (depth > std::max(2, (kmax + 1) / 2) || depth > tc_max_stages(bn)) break;
                     CKR(pr.tc_retile(si, bn, depth, L->arena, (size_t)-1, nullptr, st));
                     float t = 0.0f;
                     CKR(time_step(L, si, reps, a, b, &t));

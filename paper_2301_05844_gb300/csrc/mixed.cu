@@ -48,11 +48,7 @@ void Program::tc_step(std::vector<TCTask>& ts, std::vector<TCSpec>& sp, int kind
     s.first = tcs.size();
     s.count = (int)ts.size();
     s.aux = bn;
-    // ring depth: up to 4 stages within ~96 KB of shared memory, so that two CTAs share an
-    // SM and one's epilogue overlaps the other's loads and MMAs
-    const int per_stage = (128 + bn) * 128;
-    const int depth = std::max(2, std::min(4, (96 * 1024) / per_stage));
-    s.aux2 = kind | (std::min(kmax, depth) << 8);  // kind, ring depth
+    s.aux2 = kind | (tc_default_stages(bn, kmax) << 8);  // kind, ring depth
     s.n = tiles;
     tcs.insert(tcs.end(), ts.begin(), ts.end());
     tcspec.insert(tcspec.end(), sp.begin(), sp.end());

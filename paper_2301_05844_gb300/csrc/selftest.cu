@@ -52,7 +52,7 @@ extern "C" int bbp_selftest_gemm(int M, int N, int K, int prec, const float* A, 
     const int tiles = ((M + 127) / 128) * ((N + bn - 1) / bn);
     const int ek = kind == 0 ? 32 : 64;
     const int nk = (K + ek - 1) / ek;
-    if (!e) e = launch_tc_gemm((const TCTask*)dt, 1, kind, bn, tiles, nk < 4 ? nk : 4, derr, 0);
+    if (!e) e = launch_tc_gemm((const TCTask*)dt, 1, kind, bn, tiles, tc_default_stages(bn, nk), derr, 0);
     if (!e) e = cudaDeviceSynchronize();
     int herr = 0;
     if (!e) e = cudaMemcpy(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost);

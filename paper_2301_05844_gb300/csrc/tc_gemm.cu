@@ -28,7 +28,8 @@ namespace tc {
 
 constexpr int BM = 128;
 constexpr int STAGES = 8;  // deepest operand ring (mbarrier arrays); see tc_max_stages
-constexpr int KBYTES = 128;  // bytes of K per stage row (one 128-byte swizzle atom)
+constexpr int KBYTES = 128;  // bytes of K per k-block row (one 128-byte swizzle atom)
+constexpr int KSUB = 2;      // k-blocks per ring stage: one full/empty barrier round trip per two
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -43,11 +44,13 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
 }
+// Non-blocking test of a phase (a satisfied mbarrier.try_wait measured ~280 cycles on this
+// GPU, a satisfied test_wait ~150; the waits below poll it in a bounded loop).
 __device__ __forceinline__ uint32_t mbar_try_wait(uint64_t* bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}\n"
         : "=r"(ok)
         : "r"(smem_u32(bar)), "r"(parity)
@@ -284,12 +287,14 @@ __global__ void __launch_bounds__(128) k_tc_gemm(const TCTask* __restrict__ task
     const int m0 = (blockIdx.x % tilesM) * BM, n0 = (blockIdx.x / tilesM) * BN;
     constexpr int EK = KBYTES / (KIND == 0 ? 4 : 2);  // elements of K per k-block
     const int nk = (t.K + EK - 1) / EK;
-    constexpr uint32_t A_BYTES = BM * KBYTES, B_BYTES = BN * KBYTES;
+    constexpr uint32_t A_BYTES = BM * KBYTES, B_BYTES = BN * KBYTES;  // one k-block
+    constexpr uint32_t A_STAGE = A_BYTES * KSUB, B_STAGE = B_BYTES * KSUB;
+    const int nst = (nk + KSUB - 1) / KSUB;  // ring stages of KSUB k-blocks
 
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     unsigned char* sA = smem;
-    unsigned char* sB = smem + stages * A_BYTES;
+    unsigned char* sB = smem + stages * A_STAGE;
     __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES], accum;
     __shared__ uint32_t tmem_base;
     __shared__ int issued;
@@ -320,28 +325,36 @@ __global__ void __launch_bounds__(128) k_tc_gemm(const TCTask* __restrict__ task
     }
 
     if (warp == 0 && lane == 0) {
-        // TMA producer
-        for (int kb = 0; kb < nk; ++kb) {
-            const int s = kb % stages, r = kb / stages;
+        // TMA producer: stage ks holds k-blocks ks*KSUB .. (the last stage may hold fewer)
+        for (int ks = 0; ks < nst; ++ks) {
+            const int s = ks % stages, r = ks / stages;
             if (r > 0 && !mbar_wait(&empty[s], (r - 1) & 1, err)) break;
-            mbar_expect_tx(&full[s], A_BYTES + B_BYTES);
-            tma_load_2d(sA + s * A_BYTES, &gt->map_a, &full[s], kb * EK, m0);
-            tma_load_2d(sB + s * B_BYTES, &gt->map_b, &full[s], kb * EK, n0);
-            issued = kb + 1;
+            const int na = min(KSUB, nk - ks * KSUB);
+            mbar_expect_tx(&full[s], (uint32_t)na * (A_BYTES + B_BYTES));
+            for (int a = 0; a < na; ++a) {
+                const int kb = ks * KSUB + a;
+                tma_load_2d(sA + s * A_STAGE + a * A_BYTES, &gt->map_a, &full[s], kb * EK, m0);
+                tma_load_2d(sB + s * B_STAGE + a * B_BYTES, &gt->map_b, &full[s], kb * EK, n0);
+            }
+            issued = ks + 1;
         }
     } else if (warp == 1 && lane == 0) {
         // MMA issuer
         constexpr uint32_t ID = idesc(KIND, BN);
         bool ok = true;
-        for (int kb = 0; kb < nk && ok; ++kb) {
-            const int s = kb % stages, r = kb / stages;
+        for (int ks = 0; ks < nst && ok; ++ks) {
+            const int s = ks % stages, r = ks / stages;
             ok = mbar_wait(&full[s], r & 1, err);
             if (!ok) break;
             fence_after();
-            const uint32_t a0 = smem_u32(sA + s * A_BYTES), b0 = smem_u32(sB + s * B_BYTES);
+            const int na = min(KSUB, nk - ks * KSUB);
+            for (int a = 0; a < na; ++a) {
+                const int kb = ks * KSUB + a;
+                const uint32_t a0 = smem_u32(sA + s * A_STAGE + a * A_BYTES), b0 = smem_u32(sB + s * B_STAGE + a * B_BYTES);
 #pragma unroll
-            for (int k = 0; k < KBYTES / 32; ++k)  // 32 bytes of K per instruction
-                umma<KIND>(tmem, sdesc(a0 + 32 * k), sdesc(b0 + 32 * k), ID, (kb | k) ? 1u : 0u);
+                for (int k = 0; k < KBYTES / 32; ++k)  // 32 bytes of K per instruction, K order as in one stage per k-block
+                    umma<KIND>(tmem, sdesc(a0 + 32 * k), sdesc(b0 + 32 * k), ID, (kb | k) ? 1u : 0u);
+            }
             umma_commit(&empty[s]);
         }
         umma_commit(&accum);
@@ -401,15 +414,26 @@ __global__ void __launch_bounds__(128) k_tc_gemm(const TCTask* __restrict__ task
 // Dynamic shared memory: the operand ring, or the staged epilogue tile and its offsets
 // if that is larger, plus 1 KB for the 1024-byte alignment of the swizzled ring.
 static size_t tc_smem(int stages, int bn) {
-    const size_t ring = (size_t)stages * (tc::BM + bn) * tc::KBYTES;
+    const size_t ring = (size_t)stages * (tc::BM + bn) * tc::KBYTES * tc::KSUB;
     const size_t tile = (size_t)tc::BM * (tc::EC + 1) * sizeof(float) + (size_t)(tc::BM + tc::EC) * sizeof(long long);
     return std::max(ring, tile) + 1024;
 }
 
-// Deepest ring that fits the 227 KB of shared memory a CTA may hold (2 KB kept for the
-// static barriers): 8 stages for BN <= 64, 7 for 128, 4 for 256.
+// Deepest ring (stages of KSUB k-blocks) that fits the 227 KB of shared memory a CTA may hold
+// (2 KB kept for the static barriers and the task): 5 stages for BN = 32, 4 for 64, 3 for 128,
+// 2 for 256.
+
+// Default ring depth: up to 4 stages within ~96 KB of shared memory (so that two CTAs share an
+// SM and one's epilogue overlaps the other's loads and MMAs), at least 2, at most the stages
+// the K extent needs.
+int tc_default_stages(int bn, int kblocks) {
+    const int per = (tc::BM + bn) * tc::KBYTES * tc::KSUB;
+    const int depth = std::max(2, std::min(4, (96 * 1024) / per));
+    const int need = (kblocks + tc::KSUB - 1) / tc::KSUB;
+    return std::max(1, std::min(std::min(need, depth), tc_max_stages(bn)));
+}
 int tc_max_stages(int bn) {
-    const size_t per = (size_t)(tc::BM + bn) * tc::KBYTES;
+    const size_t per = (size_t)(tc::BM + bn) * tc::KBYTES * tc::KSUB;
     const size_t cap = 232448 - 2048 - 1024;
     return std::max(1, std::min(tc::STAGES, (int)(cap / per)));
 }

@@ -29,9 +29,11 @@ struct TCTask {
 };
 
 cudaError_t tc_prepare();
-// Deepest shared-memory ring for tile width bn (8 stages for bn <= 64, 7 for 128, 4 for 256).
+// The operand ring holds stages of two k-blocks (128 bytes of K each).  Deepest ring for tile
+// width bn, and the planner's default depth for a step of `kblocks` k-blocks.
 int tc_max_stages(int bn);
-// stages: depth of the shared-memory ring (1..tc_max_stages(bn)), at most the number of k-blocks.
+int tc_default_stages(int bn, int kblocks);
+// stages: depth of the shared-memory ring (1..tc_max_stages(bn)).
 cudaError_t launch_tc_gemm(const TCTask* d_tasks, int ntasks, int kind, int bn, int max_tiles, int stages, int* err,
                            cudaStream_t s);
 // kind: 0 FP32/TF32 elements, 1 BF16.  rows x K matrix with leading dimension ld_elems

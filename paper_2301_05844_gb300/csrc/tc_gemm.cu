@@ -273,7 +273,7 @@ __device__ __forceinline__ void epilogue_dest(const float* tile, long long* roff
 }
 
 template <int KIND, int BN>
-__global__ void __launch_bounds__(128) k_tc_gemm(const TCTask* __restrict__ tasks, int* err, int stages) {
+__global__ void __launch_bounds__(128, 1) k_tc_gemm(const TCTask* __restrict__ tasks, int* err, int stages) {
     // The task descriptor is copied to shared memory in one coalesced read (its fields are
     // otherwise fetched from global memory one dependent load at a time); the TMA copies use
     // the tensor maps at their global address.

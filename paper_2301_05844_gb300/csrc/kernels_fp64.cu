@@ -734,8 +734,9 @@ __global__ void __launch_bounds__(256) k_qr_cluster(const QRTask* __restrict__ t
         const S* vj = W + (size_t)(j / C) * m;
         if (owner != rank) vj = cluster.map_shared_rank(vj, owner);
         const bool own_next = nxt < n && rank == nxt % C;
-        if (tau != 0.0)
-            for (int i = j + tid; i < m; i += 256) ub[i] = vj[i];
+        // copied whatever tau is (unused when tau = 0), so that this read of the owner's shared
+        // memory overlaps the read of tau instead of waiting for it
+        for (int i = j + tid; i < m; i += 256) ub[i] = vj[i];
         __syncthreads();  // u holds v_j; every warp has finished step j-1
         if (own_next) {
             // the chain first; the bulk update of this CTA waits for it

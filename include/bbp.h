@@ -238,9 +238,9 @@ int bbp_time_kernels(bbp_lattice* lat, int kernel_class, int reps, double* ms, l
  * with CUDA events on the handle's stream and every fit stage active, reps launches of each
  * candidate after one warm-up, and keeps the fastest:
  *  - tensor-core steps (TF32 / BF16 paths): tile width BN in {32, 64, 128, 256} (up to the
- *    widest result) and TMA ring depth in {2, 3, 4, 5} stages of two k-blocks (up to what
- *    the K extent needs and shared memory holds); the K-accumulation order of a tile is the
- *    same for every candidate;
+ *    widest result), TMA ring stages of one or two k-blocks and ring depth in {2, 3, 4, 6, 8}
+ *    (up to what the K extent needs and shared memory holds); the K-accumulation order of a
+ *    tile is the same for every candidate;
  *  - QR/LQ steps (every path): the number of CTAs (1-8) one matrix is spread over, kept
  *    only if clearly faster than the built-in rule; every column's arithmetic, and the fit
  *    loss, are the same for every cluster size.

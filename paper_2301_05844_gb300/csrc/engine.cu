@@ -637,7 +637,8 @@ cudaError_t Program::encode_maps(char* base, size_t split, char* base2) {
     return cudaSuccess;
 }
 
-cudaError_t Program::tc_retile(size_t si, int bn, int depth, char* base, size_t split, char* base2, cudaStream_t st) {
+cudaError_t Program::tc_retile(size_t si, int bn, int depth, char* base, size_t split, char* base2, cudaStream_t st,
+                               int ksub) {
     Step& s = steps[si];
     int tiles = 1;
     for (int i = 0; i < s.count; ++i) {
@@ -651,7 +652,7 @@ cudaError_t Program::tc_retile(size_t si, int bn, int depth, char* base, size_t 
     }
     s.aux = bn;
     s.n = tiles;
-    s.aux2 = (s.aux2 & 0xFF) | (depth << 8);
+    s.aux2 = (s.aux2 & 0xFF) | (depth << 8) | (ksub << 16);
     return cudaMemcpyAsync(d_tcs + s.first, tcs.data() + s.first, (size_t)s.count * sizeof(TCTask), cudaMemcpyHostToDevice,
                            st);
 }
@@ -706,7 +707,8 @@ cudaError_t Program::launch_step(const Step& s, cudaStream_t st, const int* swee
         case ST_DL:
             return s.aux2 == 1 ? launch_double_layer_hb(d_dl + s.first, s.count, s.n, st)
                                : launch_double_layer(d_dl + s.first, s.count, s.n, cplx, st);
-        case ST_TC: return launch_tc_gemm(d_tcs + s.first, s.count, s.aux2 & 0xFF, s.aux, (int)s.n, s.aux2 >> 8, tc_err, st);
+        case ST_TC: return launch_tc_gemm(d_tcs + s.first, s.count, s.aux2 & 0xFF, s.aux, (int)s.n, (s.aux2 >> 8) & 0xFF, tc_err, st,
+                                          (s.aux2 >> 16) & 0xFF);
         case ST_REL: return launch_relayout(d_rel + s.first, s.count, s.n, st);
         case ST_LOOP_BEGIN: return launch_set_int((int*)s.p0, 1, 0, st);  // iteration counter = 0
         case ST_LOOP_END: return cudaSuccess;
@@ -855,7 +857,8 @@ cudaError_t Program::launch_class(cudaStream_t st, const int* sweep_ctr, unsigne
                 }
                 break;
             case ST_TC:
-                e = launch_tc_gemm(d_tcs + s.first, s.count, s.aux2 & 0xFF, s.aux, (int)s.n, s.aux2 >> 8, tc_err, st);
+                e = launch_tc_gemm(d_tcs + s.first, s.count, s.aux2 & 0xFF, s.aux, (int)s.n, (s.aux2 >> 8) & 0xFF, tc_err, st,
+                                   (s.aux2 >> 16) & 0xFF);
                 for (int i = 0; i < s.count; ++i) {
                     const TCTask& t = tcs[s.first + i];
                     const TCSpec& sp = tcspec[s.first + i];

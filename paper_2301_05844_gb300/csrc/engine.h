@@ -86,9 +86,11 @@ struct Program {
     void rel_step(std::vector<RelayoutTask>& ts);
     // encode every TMA tensor map (after relocate)
     cudaError_t encode_maps(char* base, size_t split = (size_t)-1, char* base2 = nullptr);
-    // give tensor-core step si the tile width bn and TMA ring depth: its B maps re-encoded,
-    // its tile count updated and its task descriptors re-uploaded on st (after upload_tasks)
-    cudaError_t tc_retile(size_t si, int bn, int depth, char* base, size_t split, char* base2, cudaStream_t st);
+    // give tensor-core step si the tile width bn and a TMA ring of `depth` stages of ksub
+    // k-blocks: its B maps re-encoded, its tile count updated and its task descriptors
+    // re-uploaded on st (after upload_tasks)
+    cudaError_t tc_retile(size_t si, int bn, int depth, char* base, size_t split, char* base2, cudaStream_t st,
+                          int ksub = 1);
     // task descriptors to the device (stream-ordered allocation on st)
     cudaError_t upload_tasks(cudaStream_t st);
     std::vector<std::pair<size_t, int>> loop_descs;  // (arena byte offset, max iterations)

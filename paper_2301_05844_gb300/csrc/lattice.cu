@@ -1092,26 +1092,31 @@ int bbp_autotune(bbp_lattice* L, int reps, double* ms_before, double* ms_after, 
                 nmax = std::max(nmax, pr.tcs[s0.first + i].N);
                 kmax = std::max(kmax, (pr.tcs[s0.first + i].K + ek - 1) / ek);
             }
-            const int bn0 = s0.aux, d0 = s0.aux2 >> 8;
-            int best_bn = bn0, best_d = d0;
+            const int bn0 = s0.aux, d0 = (s0.aux2 >> 8) & 0xFF, k0 = std::max(1, (s0.aux2 >> 16) & 0xFF);
+            int best_bn = bn0, best_d = d0, best_k = k0;
             float best = -1.0f, t0 = -1.0f;
             for (int bn : {32, 64, 128, 256}) {
                 if (bn > 32 && bn / 2 >= nmax) break;  // wider tiles than the widest result
-                for (int depth : {2, 3, 4, 5}) {  // stages of two k-blocks
-                    if (depth > std::max(2, (kmax + 1) / 2) || depth > tc_max_stages(bn)) break;
-                    CKR(pr.tc_retile(si, bn, depth, L->arena, (size_t)-1, nullptr, st));
-                    float t = 0.0f;
-                    CKR(time_step(L, si, reps, a, b, &t));
-                    if (bn == bn0 && depth == d0) t0 = t;
-                    if (best < 0.0f || t < best) {
-                        best = t;
-                        best_bn = bn;
-                        best_d = depth;
+                for (int ksub : {1, 2}) {                 // k-blocks per ring stage
+                    const int need = (kmax + ksub - 1) / ksub;  // stages the K extent fills
+                    if (ksub > 1 && kmax < 2) break;
+                    for (int depth : {2, 3, 4, 6, 8}) {
+                        if (depth > std::max(2, need) || depth > tc_max_stages(bn, ksub)) break;
+                        CKR(pr.tc_retile(si, bn, depth, L->arena, (size_t)-1, nullptr, st, ksub));
+                        float t = 0.0f;
+                        CKR(time_step(L, si, reps, a, b, &t));
+                        if (bn == bn0 && depth == d0 && ksub == k0) t0 = t;
+                        if (best < 0.0f || t < best) {
+                            best = t;
+                            best_bn = bn;
+                            best_d = depth;
+                            best_k = ksub;
+                        }
                     }
                 }
             }
-            CKR(pr.tc_retile(si, best_bn, best_d, L->arena, (size_t)-1, nullptr, st));
-            if (best_bn != bn0 || best_d != d0) ++changed;
+            CKR(pr.tc_retile(si, best_bn, best_d, L->arena, (size_t)-1, nullptr, st, best_k));
+            if (best_bn != bn0 || best_d != d0 || best_k != k0) ++changed;
             before += (t0 >= 0.0f ? t0 : best) / reps;
             after += best / reps;
         } else if (s0.kind == ST_QR && qr_cluster_fits(s0.aux, s0.n, pr.cplx, 1)) {

@@ -87,7 +87,8 @@ struct Step {
     size_t first = 0;   // index of first task in the per-kind task array
     int count = 0;
     int aux = 0;        // GC: max tiles; QR: max m; TC: tile N
-    int aux2 = 0;       // TC: 0 TF32, 1 BF16 (| ring depth << 8); QR: cluster size (0: rule); GC: 16x16 tiles
+    int aux2 = 0;       // TC: 0 TF32, 1 BF16 | ring depth << 8 | k-blocks per stage << 16 (0: 1);
+                        // QR: cluster size (0: rule); GC: 16x16 tiles
     // direct-argument steps
     void* p0 = nullptr;
     void* p1 = nullptr;

@@ -29,7 +29,7 @@ namespace tc {
 constexpr int BM = 128;
 constexpr int STAGES = 8;  // deepest operand ring (mbarrier arrays); see tc_max_stages
 constexpr int KBYTES = 128;  // bytes of K per k-block row (one 128-byte swizzle atom)
-constexpr int KSUB = 2;      // k-blocks per ring stage: one full/empty barrier round trip per two
+constexpr int KSUB_MAX = 2;  // k-blocks per ring stage: 1 or 2 (autotuned per step)
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -273,7 +273,7 @@ __device__ __forceinline__ void epilogue_dest(const float* tile, long long* roff
 }
 
 template <int KIND, int BN>
-__global__ void __launch_bounds__(128, 1) k_tc_gemm(const TCTask* __restrict__ tasks, int* err, int stages) {
+__global__ void __launch_bounds__(128, 1) k_tc_gemm(const TCTask* __restrict__ tasks, int* err, int stages, int ksub) {
     // The task descriptor is copied to shared memory in one coalesced read (its fields are
     // otherwise fetched from global memory one dependent load at a time); the TMA copies use
     // the tensor maps at their global address.
@@ -288,8 +288,10 @@ __global__ void __launch_bounds__(128, 1) k_tc_gemm(const TCTask* __restrict__ t
     constexpr int EK = KBYTES / (KIND == 0 ? 4 : 2);  // elements of K per k-block
     const int nk = (t.K + EK - 1) / EK;
     constexpr uint32_t A_BYTES = BM * KBYTES, B_BYTES = BN * KBYTES;  // one k-block
-    constexpr uint32_t A_STAGE = A_BYTES * KSUB, B_STAGE = B_BYTES * KSUB;
-    const int nst = (nk + KSUB - 1) / KSUB;  // ring stages of KSUB k-blocks
+    // a ring stage holds ksub k-blocks: one full/empty barrier round trip per stage (two
+    // halve the round trips, one keeps rings small enough for two CTAs per SM)
+    const uint32_t A_STAGE = A_BYTES * ksub, B_STAGE = B_BYTES * ksub;
+    const int nst = (nk + ksub - 1) / ksub;
 
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -325,14 +327,14 @@ __global__ void __launch_bounds__(128, 1) k_tc_gemm(const TCTask* __restrict__ t
     }
 
     if (warp == 0 && lane == 0) {
-        // TMA producer: stage ks holds k-blocks ks*KSUB .. (the last stage may hold fewer)
+        // TMA producer: stage ks holds k-blocks ks*ksub .. (the last stage may hold fewer)
         for (int ks = 0; ks < nst; ++ks) {
             const int s = ks % stages, r = ks / stages;
             if (r > 0 && !mbar_wait(&empty[s], (r - 1) & 1, err)) break;
-            const int na = min(KSUB, nk - ks * KSUB);
+            const int na = min(ksub, nk - ks * ksub);
             mbar_expect_tx(&full[s], (uint32_t)na * (A_BYTES + B_BYTES));
             for (int a = 0; a < na; ++a) {
-                const int kb = ks * KSUB + a;
+                const int kb = ks * ksub + a;
                 tma_load_2d(sA + s * A_STAGE + a * A_BYTES, &gt->map_a, &full[s], kb * EK, m0);
                 tma_load_2d(sB + s * B_STAGE + a * B_BYTES, &gt->map_b, &full[s], kb * EK, n0);
             }
@@ -347,9 +349,9 @@ __global__ void __launch_bounds__(128, 1) k_tc_gemm(const TCTask* __restrict__ t
             ok = mbar_wait(&full[s], r & 1, err);
             if (!ok) break;
             fence_after();
-            const int na = min(KSUB, nk - ks * KSUB);
+            const int na = min(ksub, nk - ks * ksub);
             for (int a = 0; a < na; ++a) {
-                const int kb = ks * KSUB + a;
+                const int kb = ks * ksub + a;
                 const uint32_t a0 = smem_u32(sA + s * A_STAGE + a * A_BYTES), b0 = smem_u32(sB + s * B_STAGE + a * B_BYTES);
 #pragma unroll
                 for (int k = 0; k < KBYTES / 32; ++k)  // 32 bytes of K per instruction, K order as in one stage per k-block
@@ -413,27 +415,27 @@ __global__ void __launch_bounds__(128, 1) k_tc_gemm(const TCTask* __restrict__ t
 
 // Dynamic shared memory: the operand ring, or the staged epilogue tile and its offsets
 // if that is larger, plus 1 KB for the 1024-byte alignment of the swizzled ring.
-static size_t tc_smem(int stages, int bn) {
-    const size_t ring = (size_t)stages * (tc::BM + bn) * tc::KBYTES * tc::KSUB;
+static size_t tc_smem(int stages, int bn, int ksub) {
+    const size_t ring = (size_t)stages * (tc::BM + bn) * tc::KBYTES * ksub;
     const size_t tile = (size_t)tc::BM * (tc::EC + 1) * sizeof(float) + (size_t)(tc::BM + tc::EC) * sizeof(long long);
     return std::max(ring, tile) + 1024;
 }
 
-// Deepest ring (stages of KSUB k-blocks) that fits the 227 KB of shared memory a CTA may hold
-// (2 KB kept for the static barriers and the task): 5 stages for BN = 32, 4 for 64, 3 for 128,
-// 2 for 256.
+// Deepest ring (stages of ksub k-blocks) that fits the 227 KB of shared memory a CTA may hold
+// (2 KB kept for the static barriers and the task): for ksub = 1, 8 stages for BN <= 64, 7 for
+// 128, 4 for 256; for ksub = 2, 5 / 4 / 3 / 2 for BN = 32 / 64 / 128 / 256.
 
 // Default ring depth: up to 4 stages within ~96 KB of shared memory (so that two CTAs share an
 // SM and one's epilogue overlaps the other's loads and MMAs), at least 2, at most the stages
 // the K extent needs.
-int tc_default_stages(int bn, int kblocks) {
-    const int per = (tc::BM + bn) * tc::KBYTES * tc::KSUB;
+int tc_default_stages(int bn, int kblocks) {  // one k-block per stage
+    const int per = (tc::BM + bn) * tc::KBYTES;
     const int depth = std::max(2, std::min(4, (96 * 1024) / per));
-    const int need = (kblocks + tc::KSUB - 1) / tc::KSUB;
-    return std::max(1, std::min(std::min(need, depth), tc_max_stages(bn)));
+    return std::max(1, std::min(std::min(kblocks, depth), tc_max_stages(bn, 1)));
 }
-int tc_max_stages(int bn) {
-    const size_t per = (size_t)(tc::BM + bn) * tc::KBYTES * tc::KSUB;
+int tc_max_stages(int bn, int ksub) {
+    if (ksub < 1 || ksub > tc::KSUB_MAX) return 0;
+    const size_t per = (size_t)(tc::BM + bn) * tc::KBYTES * ksub;
     const size_t cap = 232448 - 2048 - 1024;
     return std::max(1, std::min(tc::STAGES, (int)(cap / per)));
 }
@@ -443,7 +445,7 @@ cudaError_t tc_prepare() {
     cudaError_t e;
     const int bns[4] = {32, 64, 128, 256};
     for (int i = 0; i < 4; ++i) {
-        const size_t smem = tc_smem(tc_max_stages(bns[i]), bns[i]);
+        const size_t smem = std::max(tc_smem(tc_max_stages(bns[i], 1), bns[i], 1), tc_smem(tc_max_stages(bns[i], 2), bns[i], 2));
         switch (bns[i]) {
             case 32:
                 if ((e = cudaFuncSetAttribute(tc::k_tc_gemm<0, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))) return e;
@@ -466,10 +468,11 @@ cudaError_t tc_prepare() {
 }
 
 cudaError_t launch_tc_gemm(const TCTask* d_tasks, int ntasks, int kind, int bn, int max_tiles, int stages, int* err,
-                           cudaStream_t s) {
+                           cudaStream_t s, int ksub) {
     if (ntasks <= 0) return cudaSuccess;
-    if (stages < 1 || stages > tc_max_stages(bn)) return cudaErrorInvalidValue;
-    const size_t smem = tc_smem(stages, bn);
+    if (ksub < 1) ksub = 1;
+    if (stages < 1 || stages > tc_max_stages(bn, ksub)) return cudaErrorInvalidValue;
+    const size_t smem = tc_smem(stages, bn, ksub);
     dim3 grid(max_tiles, ntasks);
     // programmatic dependent launch: the kernel waits (griddepcontrol.wait) before it reads
     // anything an earlier kernel wrote
@@ -484,7 +487,7 @@ cudaError_t launch_tc_gemm(const TCTask* d_tasks, int ntasks, int kind, int bn, 
     cfg.attrs = attr;
     cfg.numAttrs = 1;
 #define TC_CASE(K_, N_)                                                              \
-    if (kind == K_ && bn == N_) return cudaLaunchKernelEx(&cfg, tc::k_tc_gemm<K_, N_>, d_tasks, err, stages);
+    if (kind == K_ && bn == N_) return cudaLaunchKernelEx(&cfg, tc::k_tc_gemm<K_, N_>, d_tasks, err, stages, ksub);
     TC_CASE(0, 32) TC_CASE(0, 64) TC_CASE(0, 128) TC_CASE(0, 256)
     TC_CASE(1, 32) TC_CASE(1, 64) TC_CASE(1, 128) TC_CASE(1, 256)
 #undef TC_CASE

@@ -29,13 +29,14 @@ struct TCTask {
 };
 
 cudaError_t tc_prepare();
-// The operand ring holds stages of two k-blocks (128 bytes of K each).  Deepest ring for tile
-// width bn, and the planner's default depth for a step of `kblocks` k-blocks.
-int tc_max_stages(int bn);
+// The operand ring holds stages of ksub k-blocks (1 or 2; 128 bytes of K each).  Deepest ring
+// for tile width bn (0 for an unsupported ksub), and the planner's default depth (one k-block
+// per stage) for a step of `kblocks` k-blocks.
+int tc_max_stages(int bn, int ksub = 1);
 int tc_default_stages(int bn, int kblocks);
-// stages: depth of the shared-memory ring (1..tc_max_stages(bn)).
+// stages: depth of the shared-memory ring (1..tc_max_stages(bn, ksub)).
 cudaError_t launch_tc_gemm(const TCTask* d_tasks, int ntasks, int kind, int bn, int max_tiles, int stages, int* err,
-                           cudaStream_t s);
+                           cudaStream_t s, int ksub = 1);
 // kind: 0 FP32/TF32 elements, 1 BF16.  rows x K matrix with leading dimension ld_elems
 // (ld * element size must be a multiple of 16 bytes, base 16-byte aligned).
 cudaError_t tc_make_map(void* map_out, const void* base, int kind, long long rows, long long K, long long ld_elems,

@@ -35,6 +35,24 @@ int fail(int code, const std::string& msg) {
     return code;
 }
 
+int abi_error() noexcept {
+    int code = BBP_ERR_INVALID;
+    try {
+        try {
+            throw;
+        } catch (const std::bad_alloc&) {
+            code = BBP_ERR_OOM;
+            g_err = "host allocation failed";
+        } catch (const std::exception& e) {
+            g_err = std::string("host error: ") + e.what();
+        } catch (...) {
+            g_err = "host error";
+        }
+    } catch (...) {  // the message itself could not be stored
+    }
+    return code;
+}
+
 int bond_cap(const std::vector<int>& phys, int i, int chi) {
     // bond between site i-1 and i of an MPS with physical dims phys
     if (i <= 0 || i >= (int)phys.size()) return 1;

@@ -13,6 +13,10 @@ namespace bbp {
 
 extern thread_local std::string g_err;
 int fail(int code, const std::string& msg);
+// Handler of every C entry point (a function-try-block around its body): turns the C++
+// exception in flight (a failed host allocation, a thread that could not start) into an
+// error code and message, so that no exception crosses the C boundary.
+int abi_error() noexcept;
 int bond_cap(const std::vector<int>& phys, int i, int chi);
 std::vector<int> bond_caps(const std::vector<int>& phys, int chi);
 uint64_t stream_id(uint64_t tag, uint64_t outer, uint64_t msg, uint64_t col, uint64_t site);

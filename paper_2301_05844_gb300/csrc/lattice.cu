@@ -530,6 +530,23 @@ static int plan_sweep(bbp_lattice* L) {
 }
 
 // ------------------------------------------------------------------ C ABI
+// CUDA events and stream-ordered device allocations released on every return path.
+struct EventPair {
+    cudaEvent_t a = nullptr, b = nullptr;
+    ~EventPair() {
+        if (a) cudaEventDestroy(a);
+        if (b) cudaEventDestroy(b);
+    }
+};
+struct AsyncBuffer {
+    void* p = nullptr;
+    cudaStream_t s = nullptr;
+    explicit AsyncBuffer(cudaStream_t st) : s(st) {}
+    ~AsyncBuffer() {
+        if (p) cudaFreeAsync(p, s);
+    }
+};
+
 extern "C" {
 
 const char* bbp_last_error(void) { return bbp::g_err.c_str(); }
@@ -548,6 +565,7 @@ static int validate(const bbp_lattice_desc* d) {
     if (d->hermitian_basis != 0 && d->hermitian_basis != 1) return fail(BBP_ERR_INVALID, "hermitian_basis must be 0 or 1");
     if (d->fit_max_sweeps < 1 || d->fit_max_sweeps > 64) return fail(BBP_ERR_INVALID, "fit_max_sweeps must be 1..64");
     if (d->bx > 16 || d->by > 16) return fail(BBP_ERR_INVALID, "block sides are limited to 16 sites");
+    if (d->Lx > 4096 || d->Ly > 4096) return fail(BBP_ERR_INVALID, "lattice sides are limited to 4096 sites");
     if (d->D > 16 || d->d > 64) return fail(BBP_ERR_INVALID, "D or d too large");
     if (d->init_mode != 0 && d->init_mode != 1) return fail(BBP_ERR_INVALID, "init_mode must be 0 or 1");
     if (d->warm_start != 0 && d->warm_start != 1) return fail(BBP_ERR_INVALID, "warm_start must be 0 or 1");
@@ -667,7 +685,7 @@ int bbp::plan_lattice(const bbp_lattice_desc* desc, bbp_lattice** out) {
 
 extern "C" {
 
-int bbp_lattice_footprint(const bbp_lattice_desc* desc, size_t* bytes) {
+int bbp_lattice_footprint(const bbp_lattice_desc* desc, size_t* bytes) try {
     if (!bytes) return fail(BBP_ERR_INVALID, "bytes is NULL");
     bbp_lattice* L = nullptr;
     int rc = plan_lattice(desc, &L);
@@ -675,9 +693,11 @@ int bbp_lattice_footprint(const bbp_lattice_desc* desc, size_t* bytes) {
     *bytes = planned_bytes(L);
     delete L;
     return BBP_OK;
+} catch (...) {
+    return abi_error();
 }
 
-int bbp_create_lattice(const bbp_lattice_desc* desc, bbp_lattice** out) {
+int bbp_create_lattice(const bbp_lattice_desc* desc, bbp_lattice** out) try {
     if (!out) return fail(BBP_ERR_INVALID, "out is NULL");
     *out = nullptr;
     bbp_lattice* L = nullptr;
@@ -743,9 +763,11 @@ int bbp_create_lattice(const bbp_lattice_desc* desc, bbp_lattice** out) {
     }
     *out = L;
     return BBP_OK;
+} catch (...) {
+    return abi_error();
 }
 
-void bbp_destroy(bbp_lattice* L) {
+void bbp_destroy(bbp_lattice* L) try {
     if (!L) return;
     // waits for this lattice's own work only; the frees are stream-ordered
     if (L->stream) cudaStreamSynchronize(L->stream);
@@ -756,6 +778,8 @@ void bbp_destroy(bbp_lattice* L) {
     if (L->done) cudaEventDestroy(L->done);
     if (L->own_stream && L->stream) cudaStreamDestroy(L->stream);
     delete L;
+} catch (...) {
+    abi_error();
 }
 
 // Initial messages (App. A: messages start from a chosen state; init_mode 0 is the
@@ -815,7 +839,7 @@ static void init_messages(bbp_lattice* L, std::vector<double>& host) {
     }
 }
 
-int bbp_set_tensors(bbp_lattice* L, const void* data, int on_device) {
+int bbp_set_tensors(bbp_lattice* L, const void* data, int on_device) try {
     if (!L) return fail(BBP_ERR_INVALID, "lattice is NULL");
     if (!data) return fail(BBP_ERR_INVALID, "data is NULL");
     char* base = L->arena;
@@ -842,14 +866,14 @@ int bbp_set_tensors(bbp_lattice* L, const void* data, int on_device) {
         dl.push_back(k);
         maxout = std::max(maxout, (long long)dd[0] * dd[0] * dd[1] * dd[1] * dd[2] * dd[2] * dd[3] * dd[3]);
     }
-    DLTask* d_dl = nullptr;
-    CKR(cudaMallocAsync((void**)&d_dl, dl.size() * sizeof(DLTask), st));
+    AsyncBuffer dlb(st);
+    CKR(cudaMallocAsync(&dlb.p, dl.size() * sizeof(DLTask), st));
+    DLTask* d_dl = (DLTask*)dlb.p;
     CKR(cudaMemcpyAsync(d_dl, dl.data(), dl.size() * sizeof(DLTask), cudaMemcpyHostToDevice, st));
     if (L->hb)
         CKR(launch_double_layer_hb(d_dl, (int)dl.size(), maxout, st));
     else
         CKR(launch_double_layer(d_dl, (int)dl.size(), maxout, L->cplx, st));
-    CKR(cudaFreeAsync(d_dl, st));
     if (L->mixed) {
         // low-precision operand layouts of every double-layer tensor in every frame
         std::vector<RelayoutTask> rt;
@@ -882,11 +906,11 @@ int bbp_set_tensors(bbp_lattice* L, const void* data, int on_device) {
                     rt.push_back(r);
                 }
             }
-        RelayoutTask* d_rt = nullptr;
-        CKR(cudaMallocAsync((void**)&d_rt, rt.size() * sizeof(RelayoutTask), st));
+        AsyncBuffer rtb(st);
+        CKR(cudaMallocAsync(&rtb.p, rt.size() * sizeof(RelayoutTask), st));
+        RelayoutTask* d_rt = (RelayoutTask*)rtb.p;
         CKR(cudaMemcpyAsync(d_rt, rt.data(), rt.size() * sizeof(RelayoutTask), cudaMemcpyHostToDevice, st));
         CKR(launch_relayout(d_rt, (int)rt.size(), mx, st));
-        CKR(cudaFreeAsync(d_rt, st));
         CKR(cudaMemsetAsync(L->d_tcerr, 0, sizeof(int), st));
     }
     std::vector<double> host;
@@ -900,6 +924,8 @@ int bbp_set_tensors(bbp_lattice* L, const void* data, int on_device) {
     L->first_residual = L->last_residual = 0;
     CKR(L->sweep.reset_loop_totals(st));  // a new solve restarts the loop statistics
     return BBP_OK;
+} catch (...) {
+    return abi_error();
 }
 
 static int ensure_graph(bbp_lattice* L) {
@@ -954,7 +980,7 @@ int sweep_collect(bbp_lattice* L, double* residual, bool* stop) {
 
 extern "C" {
 
-int bbp_sweep(bbp_lattice* L, int n_sweeps, double* residual_out, int* sweeps_done) {
+int bbp_sweep(bbp_lattice* L, int n_sweeps, double* residual_out, int* sweeps_done) try {
     if (!L) return fail(BBP_ERR_INVALID, "lattice is NULL");
     if (!L->has_tensors) return fail(BBP_ERR_STATE, "bbp_set_tensors has not been called");
     const bool fixed = n_sweeps > 0;
@@ -985,9 +1011,11 @@ int bbp_sweep(bbp_lattice* L, int n_sweeps, double* residual_out, int* sweeps_do
     if (residual_out) *residual_out = r;
     if (sweeps_done) *sweeps_done = done;
     return converged ? BBP_OK : BBP_NOT_CONVERGED;
+} catch (...) {
+    return abi_error();
 }
 
-int bbp_get_message(bbp_lattice* L, int block, int dir, int* nsites, int* bonds, double* out) {
+int bbp_get_message(bbp_lattice* L, int block, int dir, int* nsites, int* bonds, double* out) try {
     if (!L) return fail(BBP_ERR_INVALID, "lattice is NULL");
     if (block < 0 || block >= L->nblocks || dir < 0 || dir > 3 || L->item_of[block * 4 + dir] < 0)
         return fail(BBP_ERR_INVALID, "no such message");
@@ -1007,9 +1035,11 @@ int bbp_get_message(bbp_lattice* L, int block, int dir, int* nsites, int* bonds,
         CKR(cudaStreamSynchronize(L->stream));
     }
     return BBP_OK;
+} catch (...) {
+    return abi_error();
 }
 
-int bbp_set_message(bbp_lattice* L, int block, int dir, const double* in) {
+int bbp_set_message(bbp_lattice* L, int block, int dir, const double* in) try {
     if (!L || !in) return fail(BBP_ERR_INVALID, "NULL argument");
     if (block < 0 || block >= L->nblocks || dir < 0 || dir > 3 || L->item_of[block * 4 + dir] < 0)
         return fail(BBP_ERR_INVALID, "no such message");
@@ -1024,15 +1054,18 @@ int bbp_set_message(bbp_lattice* L, int block, int dir, const double* in) {
     }
     CKR(cudaStreamSynchronize(L->stream));
     return BBP_OK;
+} catch (...) {
+    return abi_error();
 }
 
-int bbp_time_kernels(bbp_lattice* L, int cls, int reps, double* ms, long long* launches, double* flops, double* bytes) {
+int bbp_time_kernels(bbp_lattice* L, int cls, int reps, double* ms, long long* launches, double* flops, double* bytes) try {
     if (!L) return fail(BBP_ERR_INVALID, "lattice is NULL");
     if (!L->has_tensors) return fail(BBP_ERR_STATE, "bbp_set_tensors has not been called");
     if (cls < 0 || cls > 2 || reps < 1) return fail(BBP_ERR_INVALID, "kernel class must be 0..2 and reps >= 1");
-    cudaEvent_t a, b;
-    CKR(cudaEventCreate(&a));
-    CKR(cudaEventCreate(&b));
+    EventPair ev;
+    CKR(cudaEventCreate(&ev.a));
+    CKR(cudaEventCreate(&ev.b));
+    cudaEvent_t a = ev.a, b = ev.b;
     long long n = 0;
     double f = 0, by = 0;
     CKR(L->sweep.reset_active(L->stream));
@@ -1042,8 +1075,6 @@ int bbp_time_kernels(bbp_lattice* L, int cls, int reps, double* ms, long long* l
     CKR(cudaEventSynchronize(b));
     float t = 0;
     CKR(cudaEventElapsedTime(&t, a, b));
-    cudaEventDestroy(a);
-    cudaEventDestroy(b);
     if (L->mixed) {
         int te = 0;
         CKR(cudaMemcpy(&te, L->d_tcerr, sizeof(int), cudaMemcpyDeviceToHost));
@@ -1054,6 +1085,8 @@ int bbp_time_kernels(bbp_lattice* L, int cls, int reps, double* ms, long long* l
     if (flops) *flops = f;
     if (bytes) *bytes = by;
     return BBP_OK;
+} catch (...) {
+    return abi_error();
 }
 
 // Time `reps` launches of step si (after one warm-up) with CUDA events on the handle's stream.
@@ -1069,7 +1102,7 @@ static cudaError_t time_step(bbp_lattice* L, size_t si, int reps, cudaEvent_t a,
     return e;
 }
 
-int bbp_autotune(bbp_lattice* L, int reps, double* ms_before, double* ms_after, int* steps_changed) {
+int bbp_autotune(bbp_lattice* L, int reps, double* ms_before, double* ms_after, int* steps_changed) try {
     if (!L) return fail(BBP_ERR_INVALID, "lattice is NULL");
     if (reps < 1) return fail(BBP_ERR_INVALID, "reps must be >= 1");
     if (!L->has_tensors) return fail(BBP_ERR_STATE, "bbp_set_tensors has not been called");
@@ -1078,9 +1111,10 @@ int bbp_autotune(bbp_lattice* L, int reps, double* ms_before, double* ms_after, 
     int changed = 0;
     Program& pr = L->sweep;
     cudaStream_t st = L->stream;
-    cudaEvent_t a, b;
-    CKR(cudaEventCreate(&a));
-    CKR(cudaEventCreate(&b));
+    EventPair ev;
+    CKR(cudaEventCreate(&ev.a));
+    CKR(cudaEventCreate(&ev.b));
+    cudaEvent_t a = ev.a, b = ev.b;
     CKR(pr.reset_active(st));  // every fit stage runs, as in a first sweep
     const int ek = L->cx.tck == 0 ? 32 : 64;  // K elements per k-block
     for (size_t si = 0; si < pr.steps.size(); ++si) {
@@ -1141,8 +1175,6 @@ int bbp_autotune(bbp_lattice* L, int reps, double* ms_before, double* ms_after, 
         }
     }
     CKR(cudaStreamSynchronize(st));
-    cudaEventDestroy(a);
-    cudaEventDestroy(b);
     int te = 0;
     if (L->mixed) CKR(cudaMemcpy(&te, L->d_tcerr, sizeof(int), cudaMemcpyDeviceToHost));
     if (te) return fail(BBP_ERR_TIMEOUT, "a tensor-core pipeline wait exceeded its bound");
@@ -1150,9 +1182,11 @@ int bbp_autotune(bbp_lattice* L, int reps, double* ms_before, double* ms_after, 
     if (ms_after) *ms_after = after;
     if (steps_changed) *steps_changed = changed;
     return BBP_OK;
+} catch (...) {
+    return abi_error();
 }
 
-int bbp_get_stats(bbp_lattice* L, bbp_stats* out) {
+int bbp_get_stats(bbp_lattice* L, bbp_stats* out) try {
     if (!L || !out) return fail(BBP_ERR_INVALID, "NULL argument");
     memset(out, 0, sizeof(*out));
     const Program& pr = L->sweep;
@@ -1178,6 +1212,8 @@ int bbp_get_stats(bbp_lattice* L, bbp_stats* out) {
     out->last_residual = L->last_residual;
     out->first_residual = L->first_residual;
     return BBP_OK;
+} catch (...) {
+    return abi_error();
 }
 
 }  // extern "C"

@@ -11,7 +11,7 @@
 using namespace bbp;
 
 extern "C" int bbp_qr_batched(int batch, int m, int n, int complex_values, const double* A, double* Q, double* loss,
-                              void* stream) {
+                              void* stream) try {
     if (batch < 1 || n < 1 || m < n || n > 512 || !A || !Q)
         return fail(BBP_ERR_INVALID, "qr_batched: need batch >= 1, 1 <= n <= m, n <= 512 and non-NULL A, Q");
     const size_t ss = complex_values ? 16 : 8;
@@ -45,4 +45,6 @@ extern "C" int bbp_qr_batched(int batch, int m, int n, int complex_values, const
     cudaFreeAsync(work, st);
     if (e != cudaSuccess) return fail(BBP_ERR_CUDA, std::string("qr_batched: ") + cudaGetErrorString(e));
     return BBP_OK;
+} catch (...) {
+    return abi_error();
 }

@@ -40,7 +40,7 @@ __global__ void k_build_qr_tasks(QRTask* tasks, int batch, int m, int n, size_t 
 }  // namespace
 
 extern "C" int bbp_qr_batched_noalloc(int batch, int m, int n, int complex_values, const double* A, double* Q,
-                                      double* loss, void* stream) {
+                                      double* loss, void* stream) try {
     if (batch < 1 || n < 1 || m < n || n > 512 || !A || !Q)
         return fail(BBP_ERR_INVALID, "qr_batched_noalloc: need batch >= 1, 1 <= n <= m, n <= 512 and non-NULL A, Q");
     const size_t ss = complex_values ? 16 : 8;
@@ -74,4 +74,6 @@ extern "C" int bbp_qr_batched_noalloc(int batch, int m, int n, int complex_value
     if (e == cudaSuccess) e = launch_qr(tasks, batch, m, (long long)m * n, complex_values != 0, st);
     if (e != cudaSuccess) return fail(BBP_ERR_CUDA, std::string("qr_batched_noalloc: ") + cudaGetErrorString(e));
     return BBP_OK;
+} catch (...) {
+    return abi_error();
 }

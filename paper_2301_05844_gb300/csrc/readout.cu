@@ -72,7 +72,7 @@ Op4 op_contig(size_t off, int u, int l, int d, int r) {
         if (e_ != cudaSuccess) return fail(BBP_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(e_)); \
     } while (0)
 
-extern "C" int bbp_expect(bbp_lattice* L, const bbp_term* terms, int n_terms, double* out_re, double* out_im) {
+extern "C" int bbp_expect(bbp_lattice* L, const bbp_term* terms, int n_terms, double* out_re, double* out_im) try {
     if (!L) return fail(BBP_ERR_INVALID, "lattice is NULL");
     if (!L->has_tensors) return fail(BBP_ERR_STATE, "bbp_set_tensors has not been called");
     if (n_terms < 0 || (n_terms > 0 && (!terms || !out_re))) return fail(BBP_ERR_INVALID, "bad term arguments");
@@ -527,4 +527,6 @@ extern "C" int bbp_expect(bbp_lattice* L, const bbp_term* terms, int n_terms, do
         if (out_im) out_im[t] = r.imag();
     }
     return BBP_OK;
+} catch (...) {
+    return abi_error();
 }

@@ -11,7 +11,7 @@
 
 using namespace bbp;
 
-extern "C" int bbp_selftest_gemm(int M, int N, int K, int prec, const float* A, const float* B, float* C) {
+extern "C" int bbp_selftest_gemm(int M, int N, int K, int prec, const float* A, const float* B, float* C) try {
     if (M < 1 || N < 1 || K < 1 || !A || !B || !C || (prec != BBP_PREC_TF32 && prec != BBP_PREC_BF16))
         return fail(BBP_ERR_INVALID, "selftest: bad arguments");
     const int kind = prec == BBP_PREC_TF32 ? 0 : 1;
@@ -61,10 +61,14 @@ extern "C" int bbp_selftest_gemm(int M, int N, int K, int prec, const float* A, 
     else if (herr) rc = fail(BBP_ERR_TIMEOUT, "selftest: a pipeline wait timed out");
     cudaFree(da); cudaFree(db); cudaFree(dc); cudaFree(dt); cudaFree(derr);
     return rc;
+} catch (...) {
+    return abi_error();
 }
 
-extern "C" int bbp_selftest_rng(unsigned long long seed, unsigned long long stream, long long n, double* out) {
+extern "C" int bbp_selftest_rng(unsigned long long seed, unsigned long long stream, long long n, double* out) try {
     if (n < 0 || (n > 0 && !out)) return fail(BBP_ERR_INVALID, "selftest_rng: bad arguments");
     for (long long i = 0; i < n; ++i) out[i] = bbp::uniform_pm1(seed, stream, (uint64_t)i);
     return BBP_OK;
+} catch (...) {
+    return abi_error();
 }

@@ -216,21 +216,38 @@ void bbp_server::run() {
 
 extern "C" {
 
-int bbp_server_create(size_t max_bytes, int max_active, bbp_server** out) {
+int bbp_server_create(size_t max_bytes, int max_active, bbp_server** out) try {
     if (!out || max_bytes == 0 || max_active < 1) return fail(BBP_ERR_INVALID, "server: need out, max_bytes > 0, max_active >= 1");
     bbp_server* s = new (std::nothrow) bbp_server();
     if (!s) return fail(BBP_ERR_OOM, "server: host allocation failed");
     s->max_bytes = max_bytes;
     s->max_active = max_active;
     if (cudaGetDevice(&s->device) != cudaSuccess) s->device = 0;
-    s->worker = std::thread([s] { s->run(); });
-    s->ro_worker = std::thread([s] { s->run_readouts(); });
+    try {
+        s->worker = std::thread([s] { s->run(); });
+        s->ro_worker = std::thread([s] { s->run_readouts(); });
+    } catch (...) {
+        // a thread could not start: stop the one that did, then report
+        {
+            std::lock_guard<std::mutex> g(s->mu);
+            s->stop = true;
+            s->ro_stop = true;
+        }
+        s->cv_work.notify_all();
+        s->cv_ro.notify_all();
+        if (s->worker.joinable()) s->worker.join();
+        if (s->ro_worker.joinable()) s->ro_worker.join();
+        delete s;
+        return fail(BBP_ERR_OOM, "server: a worker thread could not start");
+    }
     *out = s;
     return BBP_OK;
+} catch (...) {
+    return abi_error();
 }
 
 int bbp_server_submit(bbp_server* s, const bbp_lattice_desc* desc, const void* tensors, const bbp_term* terms,
-                      int n_terms, long long* id) {
+                      int n_terms, long long* id) try {
     if (!s || !desc || !tensors || !id || n_terms < 0 || (n_terms > 0 && !terms))
         return fail(BBP_ERR_INVALID, "server_submit: bad arguments");
     bbp_lattice* plan = nullptr;
@@ -267,10 +284,12 @@ int bbp_server_submit(bbp_server* s, const bbp_lattice_desc* desc, const void* t
     s->reqs[r->id] = std::move(r);
     s->cv_work.notify_one();
     return BBP_OK;
+} catch (...) {
+    return abi_error();
 }
 
 int bbp_server_poll(bbp_server* s, long long id, int* state, double* out_re, double* out_im, int* sweeps,
-                    double* residual, double* latency_s) {
+                    double* residual, double* latency_s) try {
     if (!s) return fail(BBP_ERR_INVALID, "server_poll: server is NULL");
     std::lock_guard<std::mutex> g(s->mu);
     auto it = s->reqs.find(id);
@@ -288,10 +307,13 @@ int bbp_server_poll(bbp_server* s, long long id, int* state, double* out_re, dou
     if (latency_s) *latency_s = r->state == 2 || r->state < 0 ? r->t_finish - r->t_submit : 0.0;
     if (r->state < 0) g_err = r->error;
     return BBP_OK;
+} catch (...) {
+    return abi_error();
 }
 
-int bbp_server_wait(bbp_server* s, long long id, double timeout_s) {
+int bbp_server_wait(bbp_server* s, long long id, double timeout_s) try {
     if (!s) return fail(BBP_ERR_INVALID, "server_wait: server is NULL");
+    if (!(timeout_s >= 0.0)) return fail(BBP_ERR_INVALID, "server_wait: timeout must be >= 0");
     std::unique_lock<std::mutex> lk(s->mu);
     auto it = s->reqs.find(id);
     if (it == s->reqs.end()) return fail(BBP_ERR_INVALID, "server_wait: unknown request");
@@ -304,9 +326,11 @@ int bbp_server_wait(bbp_server* s, long long id, double timeout_s) {
         return r->state;
     }
     return BBP_OK;
+} catch (...) {
+    return abi_error();
 }
 
-int bbp_server_stats(bbp_server* s, long long* submitted, long long* done, long long* sweeps, size_t* bytes_in_use) {
+int bbp_server_stats(bbp_server* s, long long* submitted, long long* done, long long* sweeps, size_t* bytes_in_use) try {
     if (!s) return fail(BBP_ERR_INVALID, "server_stats: server is NULL");
     std::lock_guard<std::mutex> g(s->mu);
     long long d = 0;
@@ -316,9 +340,11 @@ int bbp_server_stats(bbp_server* s, long long* submitted, long long* done, long 
     if (sweeps) *sweeps = s->sweeps_total.load();
     if (bytes_in_use) *bytes_in_use = s->used;
     return BBP_OK;
+} catch (...) {
+    return abi_error();
 }
 
-void bbp_server_destroy(bbp_server* s) {
+void bbp_server_destroy(bbp_server* s) try {
     if (!s) return;
     {
         std::lock_guard<std::mutex> g(s->mu);
@@ -339,6 +365,8 @@ void bbp_server_destroy(bbp_server* s) {
     s->cv_ro.notify_all();
     if (s->ro_worker.joinable()) s->ro_worker.join();  // reads out what is left
     delete s;
+} catch (...) {
+    abi_error();
 }
 
 }  // extern "C"

@@ -98,6 +98,24 @@ def test_footprint_is_planned_without_allocating(libpath):
     with pytest.raises(B.BBPError) as e:
         B.footprint(Lx=4, Ly=4, d=2, D=2, bx=3, by=2, chi=16)
     assert e.value.code == B.ERR_INVALID
+    with pytest.raises(B.BBPError) as e:  # refused before any per-site host allocation
+        B.footprint(Lx=8192, Ly=4, d=2, D=2, bx=2, by=2, chi=16)
+    assert e.value.code == B.ERR_INVALID and "4096" in str(e.value)
+
+
+def test_every_entry_point_catches_host_exceptions():
+    """No C++ exception crosses the C boundary: every function the header declares
+    (but bbp_last_error, which only returns a pointer) is defined with a
+    function-try-block whose handler turns the exception into an error code."""
+    csrc = os.path.join(ROOT, "paper_2301_05844_gb300", "csrc")
+    src = "".join(open(os.path.join(csrc, f)).read() for f in sorted(os.listdir(csrc)) if f.endswith(".cu"))
+    for f in declared_functions():
+        if f == "bbp_last_error":
+            continue
+        m = re.search(rf"^(?:extern \"C\" )?(?:int|void) {f}\(([^)]*)\)\s*(try\s*)?\{{", src, flags=re.M)
+        assert m, f"definition of {f} not found"
+        assert m.group(2), f"{f} is not guarded by a function-try-block"
+    assert src.count("abi_error();") >= len(declared_functions()) - 1
 
 
 def test_server_host_logic_without_a_gpu(libpath):
@@ -126,6 +144,8 @@ def test_server_host_logic_without_a_gpu(libpath):
             srv.submit(T, [[]], **cfg)  # a term on no site
         assert e.value.code == B.ERR_INVALID
         rid = srv.submit(T, [[(0, inputs.SIGMA_Z)]], **cfg)
+        assert L.bbp_server_wait(srv.h, rid, -1.0) == B.ERR_INVALID
+        assert L.bbp_server_wait(srv.h, rid, float("nan")) == B.ERR_INVALID
         assert L.bbp_server_wait(srv.h, rid, 60.0) in (B.ERR_OOM, B.ERR_CUDA)
         st = srv.poll(rid)
         assert st["state"] in (B.ERR_OOM, B.ERR_CUDA) and st["values"] is None

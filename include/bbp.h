@@ -38,7 +38,7 @@ extern "C" {
 #define BBP_OK 0
 #define BBP_NOT_CONVERGED 1 /* max_sweeps reached; results are still valid      */
 #define BBP_ERR_INVALID (-1) /* bad argument, dimensions or term geometry         */
-#define BBP_ERR_OOM (-2)     /* device allocation failed                          */
+#define BBP_ERR_OOM (-2)     /* device (or host) allocation failed                */
 #define BBP_ERR_CUDA (-3)    /* a CUDA runtime call failed                        */
 #define BBP_ERR_TIMEOUT (-4) /* a device wait exceeded its bound                  */
 #define BBP_ERR_NUMERIC (-5) /* NaN/Inf or a message of zero norm                 */
@@ -101,7 +101,9 @@ typedef struct {
 } bbp_lattice_desc;
 
 /* Validate desc, allocate the device arena (double layer, message store, work
- * buffers) and plan one sweep.  *out receives the handle.  Errors: INVALID, OOM, CUDA. */
+ * buffers) and plan one sweep.  *out receives the handle.  Limits checked here:
+ * Lx, Ly <= 4096; bx, by <= 16; D <= 16; d <= 64; 1 <= fit_max_sweeps <= 64;
+ * init_mode, warm_start and hermitian_basis 0 or 1.  Errors: INVALID, OOM, CUDA. */
 int bbp_create_lattice(const bbp_lattice_desc* desc, bbp_lattice** out);
 
 /* Device bytes a lattice with this desc would hold (arena plus task descriptors),

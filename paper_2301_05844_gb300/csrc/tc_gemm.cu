@@ -495,7 +495,7 @@ cudaError_t launch_tc_gemm(const TCTask* d_tasks, int ntasks, int kind, int bn, 
 }
 
 // ---------------------------------------------------------------- host: tensor maps
-// The driver's tensor-map encoder, looked up once (the request server encodes maps from its
+// The CUDA driver's tensor-map encoder (cuTensorMapEncodeTiled), looked up once (the request server encodes maps from its
 // worker and read-out threads).
 static PFN_cuTensorMapEncodeTiled_v12000 encoder() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = [] {

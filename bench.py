@@ -225,6 +225,9 @@ def run_ours(args):
     flops = s1["flops"] - s0["flops"]
     qr_flops = s1["qr_flops"] - s0["qr_flops"]
     kernels = s1["kernels"] - s0["kernels"]
+    # fit sweeps each column's zip-up fit loop ran (device counters), over the timed sweeps
+    loops = s1["fits"] - s0["fits"]
+    fit_sweeps = (s1["fit_sweeps"] - s0["fit_sweeps"]) / loops if loops > 0 else None
     vals = g.expect(terms) if not args.no_readout else None
 
     # kernel classes of one sweep (every fit stage active), replayed with events
@@ -321,7 +324,8 @@ def run_ours(args):
                                               "messages": 2 * ((cfg["Lx"] // cfg["bx"] - 1) * (cfg["Ly"] // cfg["by"]) + (cfg["Ly"] // cfg["by"] - 1) * (cfg["Lx"] // cfg["bx"])) if cfg["boundary"] == "obc" else 4,
                                               "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{world}"},
                "tflops": flops / dev_s / 1e12, "fp64_qr_gflops": qr_flops / dev_s / 1e9,
-               "gpu_launches": kernels, "latency_ms": {"p50": p50, "p99": p99}, "wall_s": wall,
+               "gpu_launches": kernels, "fit_sweeps_per_column": fit_sweeps,
+               "latency_ms": {"p50": p50, "p99": p99}, "wall_s": wall,
                "fp64_path": fp64, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(),
                "autotune": tune}
         print(json.dumps(out), flush=True)

@@ -245,19 +245,30 @@ def identity_trace(M, D):
     return t[0]
 
 
-def normalise_message(M, D):
+def ones_trace(M):
+    """<1|m>: contract every site's physical leg with the all-ones vector (the phase
+    reference of a single-layer network, whose legs carry no (ket, bra) pair)."""
+    t = np.ones((1,), dtype=M[0].dtype)
+    for s in M:
+        t = t @ s.sum(axis=1)
+    return t[0]
+
+
+def normalise_message(M, D, single=False):
     """Unit 2-norm, then the phase/sign fixed so that <I|m> is real positive.
 
     The paper normalises messages before comparing them (Sec. "The blockBP
     algorithm", stop rule) without naming the norm; the 2-norm and the identity-trace
     phase are the readings taken.  The phase is left alone when |<I|m>| < 1e-14.
+    single: the message of a single-layer network, whose phase reference is <1|m>
+    (the all-ones vector on every site) instead.
     """
     M = [s.copy() for s in M]
     nrm = math.sqrt(max(float(mps_overlap(M, M).real), 0.0))
     if not np.isfinite(nrm) or nrm == 0.0:
         raise FloatingPointError("zero-norm or non-finite message")
     M[0] = M[0] / nrm
-    tau = identity_trace(M, D)
+    tau = ones_trace(M) if single else identity_trace(M, D)
     if abs(tau) > 1e-14:
         M[0] = M[0] * (np.conj(tau) / abs(tau))
     return M
@@ -302,6 +313,19 @@ def random_mpdo_message(n, D, seed, stream, dtype):
         G = g.reshape(D, D).astype(dtype)
         out.append((G @ np.conj(G.T)).reshape(1, D * D, 1))
     return out
+
+
+def ones_message(n, K, dtype):
+    """Single-layer network, init mode 0: the all-ones vector on every site, bond 1."""
+    return [np.ones((1, K, 1), dtype=dtype) for _ in range(n)]
+
+
+def uniform_message(n, K, seed, stream, dtype):
+    """Single-layer network, init mode 1: a product message with independent uniform
+    entries in [0, 1) on every site, bond 1 (the paper starts the message passing of a
+    single-layer network from uniform random messages, Sec. on the 2D Ising model).  The
+    uniforms are the counter-based ones, (u + 1) / 2 for u in [-1, 1)."""
+    return [((uniform_pm1(seed, stream + i, K) + 1.0) * 0.5).astype(dtype).reshape(1, K, 1) for i in range(n)]
 
 
 # --------------------------------------------------------------------------------------
@@ -404,6 +428,10 @@ class Lattice:
     INFINITE: Lx x Ly is the unit cell; the single block (by x bx, multiples of the
     cell) is tiled from it and messages itself (Sec. "The blockBP algorithm": one
     block suffices for an iPEPS; incoming left = own outgoing right, etc.).
+    single_layer: the tensors are the network's own site tensors E[u, l, d, r] with
+    bond D on every leg (d = 1, real; a 2D classical model's partition function, Sec.
+    on the 2D Ising model), used as they are instead of a double layer; a term's
+    "operator" at a site is then the impurity tensor that replaces E there.
     """
     Lx: int
     Ly: int
@@ -420,6 +448,7 @@ class Lattice:
     seed: int = 0
     init_mode: int = 0
     warm_start: bool = False
+    single_layer: bool = False
     msgs: dict = field(default_factory=dict)
     warm: dict = field(default_factory=dict)
     sweeps_done: int = 0
@@ -435,20 +464,32 @@ class Lattice:
             assert self.bx % self.Lx == 0 and self.by % self.Ly == 0
             assert len(self.tensors) == self.Lx * self.Ly
             self.nbx = self.nby = 1
+        # bond of the double-layer (or single-layer) network; the read-out bond of App. A,
+        # 2D^2 + 10, is 2K + 10 in these terms
+        self.K = self.D if self.single_layer else self.D * self.D
         if self.chi_exp <= 0:
-            self.chi_exp = max(self.chi, 2 * self.D * self.D + 10)
+            self.chi_exp = max(self.chi, 2 * self.K + 10)
         cplx = any(np.iscomplexobj(t) for t in self.tensors)
         self.dtype = np.complex128 if cplx else np.float64
-        self.tensors = [np.asarray(t, dtype=self.dtype) for t in self.tensors]
-        self.E = [double_layer(t) for t in self.tensors]
+        if self.single_layer:
+            assert self.d == 1 and not cplx, "a single-layer network is real and has no physical leg"
+            self.tensors = [np.asarray(t, dtype=np.float64).reshape(np.shape(t)[-4:]) for t in self.tensors]
+            self.E = list(self.tensors)
+        else:
+            self.tensors = [np.asarray(t, dtype=self.dtype) for t in self.tensors]
+            self.E = [double_layer(t) for t in self.tensors]
         for bi in range(self.nbx * self.nby):
             for dr in self.directions(bi):
                 n = self.by if dr in (LEFT, RIGHT) else self.bx
-                if self.init_mode == 0:
+                stream = stream_id(2, 0, 4 * bi + dr, 0, 0)
+                if self.single_layer:
+                    m = ones_message(n, self.K, self.dtype) if self.init_mode == 0 else \
+                        uniform_message(n, self.K, self.seed, stream, self.dtype)
+                elif self.init_mode == 0:
                     m = identity_message(n, self.D, self.dtype)
                 else:
-                    m = random_mpdo_message(n, self.D, self.seed, stream_id(2, 0, 4 * bi + dr, 0, 0), self.dtype)
-                self.msgs[(bi, dr)] = embed_at_caps(normalise_message(m, self.D), self.chi)
+                    m = random_mpdo_message(n, self.D, self.seed, stream, self.dtype)
+                self.msgs[(bi, dr)] = embed_at_caps(normalise_message(m, self.D, self.single_layer), self.chi)
 
     # -- geometry ------------------------------------------------------------------
     def tensor_index(self, r, c):
@@ -482,9 +523,18 @@ class Lattice:
             row = []
             for c in range(self.bx):
                 t = self.tensor_index(r0 + r, c0 + c)
-                row.append(double_layer(self.tensors[t], ops[(r, c)]) if (r, c) in ops else self.E[t])
+                row.append(self.site_operator(t, ops[(r, c)]) if (r, c) in ops else self.E[t])
             grid.append(row)
         return grid
+
+    def site_operator(self, t, op):
+        """E^O of tensor t: the double layer with op on the ket (Fig. 1(a,b)), or, on a
+        single-layer network, the impurity tensor op itself."""
+        if self.single_layer:
+            op = np.asarray(op, dtype=np.float64)
+            assert op.shape == self.E[t].shape, "an impurity tensor has the shape of the site tensor it replaces"
+            return op
+        return double_layer(self.tensors[t], op)
 
     def incoming(self, bi, msgs=None):
         """Messages into block bi: the neighbour's outgoing message toward bi, or the
@@ -506,7 +556,7 @@ class Lattice:
         warm = self.warm.setdefault((bi, dr), {}) if self.warm_start else None
         X = column_sweep(Ef, mT, mR, mB, opts, self.seed,
                          lambda c, i: stream_id(0, sweep_index, msg, c, i), self.dtype, warm=warm)
-        return normalise_message(extract_message(X), self.D)
+        return normalise_message(extract_message(X), self.D, self.single_layer)
 
     def sweep(self):
         """One synchronous (Jacobi) update of every message; returns the residual
@@ -639,8 +689,7 @@ class Lattice:
             col = [mT[c][None]]  # [1, alpha_c, v, alpha_{c+1}] as u,l,d,r
             for r in range(h):
                 if (r, c) in loc:
-                    t = self.tensor_index(r0 + r, c0 + c)
-                    col.append(double_layer(self.tensors[t], loc[(r, c)]))
+                    col.append(self.site_operator(self.tensor_index(r0 + r, c0 + c), loc[(r, c)]))
                 else:
                     col.append(grid[r][c])
             col.append(mB[c].transpose(1, 0, 2)[:, :, None, :])  # [v, beta_c, 1, beta_{c+1}]

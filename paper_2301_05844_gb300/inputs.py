@@ -179,3 +179,36 @@ def ising_peps(beta, h=0.0):
     for p in range(2):
         T[p] = np.einsum("u,l,d,r->uldr", M[p], M[p], M[p], M[p]) * (1.0 + (h if p == 0 else -h))
     return T
+
+
+def ising_network(beta, h=0.0):
+    """Site tensor E[u, l, d, r] (bond 2) of the single-layer network whose contraction is
+    the partition function of the classical 2D Ising model, and the impurity tensor that
+    gives sum_s s exp(...) at one site, so that <impurity> = Z_s / Z is the magnetisation.
+
+    The bond weight B[s, s'] = exp(beta s s') (s = +1 for index 0, -1 for index 1) is split
+    as B = M M^T (M the symmetric square root) and each site carries M[s, .] on its four
+    legs.  h != 0 weights the site's up / down state by (1 + h) / (1 - h), a small field that
+    selects the up ordered state."""
+    B = np.array([[np.exp(beta), np.exp(-beta)], [np.exp(-beta), np.exp(beta)]])
+    ev, U = np.linalg.eigh(B)
+    M = U @ np.diag(np.sqrt(ev)) @ U.T
+    E = np.zeros((2, 2, 2, 2))
+    Ez = np.zeros((2, 2, 2, 2))
+    for p, s in ((0, 1.0), (1, -1.0)):
+        w = np.einsum("u,l,d,r->uldr", M[p], M[p], M[p], M[p]) * (1.0 + h * s)
+        E += w
+        Ez += s * w
+    return E, Ez
+
+
+def positive_network(Lx, Ly, K, seed, noise=0.1, boundary="obc"):
+    """Single-layer network of real K-leg site tensors E[u, l, d, r] = U[0,1] + noise N(0,1)
+    (U block then N block per site, row-major sites, OBC edge legs of dimension 1)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for r in range(Ly):
+        for c in range(Lx):
+            shp = site_shape(r, c, Lx, Ly, 1, K, boundary)[1:]
+            out.append(rng.uniform(0.0, 1.0, shp) + noise * rng.standard_normal(shp))
+    return out

@@ -170,3 +170,21 @@ def dense_mpo_apply(O, X):
         t = np.tensordot(t, o, axes=([-3, -2], [0, 1]))   # [..., x', q, w']
         t = np.moveaxis(t, -3, -1)                        # [..., q, w', x']
     return t.reshape(-1)
+
+
+def network_value(E, Lx, Ly, replace=None):
+    """Exact contraction of an OBC single-layer network of site tensors E[u, l, d, r]
+    (row-major), with E at the sites in `replace` (site -> tensor) swapped for the given
+    tensors: a row-by-row transfer over the open vertical legs, no messages, no fits."""
+    replace = replace or {}
+    # S axes: the open down legs of the previous row, one per column, then the open right leg
+    S = np.ones((1,) * Lx + (1,))
+    for r in range(Ly):
+        for c in range(Lx):
+            s = r * Lx + c
+            T = np.asarray(replace.get(s, E[s]), dtype=np.float64)
+            # contract the column's open leg (axis c) with u and the running right leg with l
+            S = np.tensordot(S, T, axes=([c, Lx], [0, 1]))  # axes: other columns..., d, r
+            # put the new down leg back at position c; the right leg stays last
+            S = np.moveaxis(S, Lx - 1, c)
+    return float(S.reshape(-1)[0])

@@ -65,7 +65,8 @@ typedef struct {
                                 INFINITE: multiples of the unit cell (one block, Sec. "The
                                 blockBP algorithm": the block messages itself) */
     int chi;                 /* message bond chi_m (Sec. "The blockBP algorithm", default D^2) */
-    int chi_exp;             /* read-out bond; <= 0 selects max(chi, 2 D^2 + 10) (App. A) */
+    int chi_exp;             /* read-out bond; <= 0 selects max(chi, 2 K + 10) (App. A: 2 D^2 + 10),
+                                K = D^2 (or D for a single-layer network) */
     int dtype;               /* bbp_dtype of the input tensors */
     int prec;                /* bbp_prec */
     double tol;              /* residual tolerance (main text: 1e-5) */
@@ -98,6 +99,15 @@ typedef struct {
                                 in the basis of the legs they carry: V for messages sent
                                 left or up, conj(V) for messages sent right or down. */
     void* stream;            /* cudaStream_t for all work; NULL = library-owned stream */
+    int single_layer;        /* 0: the tensors are PEPS tensors, contracted as the double layer
+                                (Fig. 1(a,b)).  1: they are the network's own site tensors
+                                E[u][l][d][r] (a 2D classical model's partition function, Sec.
+                                on the 2D Ising model), used as they are with bond K = D on
+                                every leg: d must be 1 and dtype real.  The initial messages
+                                are then the all-ones product (init_mode 0) or positive uniform
+                                entries (init_mode 1), the phase reference of the normalisation
+                                is <1|m> (all-ones vector) instead of <I|m>, and a term's
+                                op_re[k] is the impurity tensor that replaces E at site[k]. */
 } bbp_lattice_desc;
 
 /* Validate desc, allocate the device arena (double layer, message store, work
@@ -130,7 +140,11 @@ int bbp_set_tensors(bbp_lattice* lat, const void* data, int on_device);
 int bbp_sweep(bbp_lattice* lat, int n_sweeps, double* residual_out, int* sweeps_done);
 
 /* One expectation-value term: a product of nsite (1 or 2) single-site d x d
- * operators, row-major, real and imaginary parts (op_im may be NULL).
+ * operators, row-major, real and imaginary parts (op_im may be NULL).  On a
+ * single-layer network op_re[k] (and op_im[k], if not NULL) hold instead the impurity
+ * tensor that replaces the site tensor at site[k]: its shape (Du, Dl, Dd, Dr) with the
+ * OBC edge legs of dimension 1, C order; <O> is then the ratio of the network with the
+ * impurities to the network without them.
  * OBC sites are lattice sites; INFINITE sites index the bx x by block (row-major). */
 typedef struct {
     int nsite;

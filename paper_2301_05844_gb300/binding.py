@@ -32,7 +32,7 @@ class Desc(C.Structure):
         ("dtype", C.c_int), ("prec", C.c_int), ("tol", C.c_double), ("max_sweeps", C.c_int),
         ("stop_relative", C.c_int), ("fit_tol", C.c_double), ("fit_max_sweeps", C.c_int),
         ("seed", C.c_ulonglong), ("init_mode", C.c_int), ("warm_start", C.c_int),
-        ("hermitian_basis", C.c_int), ("stream", C.c_void_p),
+        ("hermitian_basis", C.c_int), ("stream", C.c_void_p), ("single_layer", C.c_int),
     ]
 
 
@@ -109,10 +109,10 @@ def _check(rc):
 
 def make_desc(Lx, Ly, d, D, bx, by, chi, boundary="obc", chi_exp=0, dtype=F64, prec="fp64", tol=1e-5,
               max_sweeps=10, stop_relative=0, fit_tol=1e-6, fit_max_sweeps=10, seed=0, init_mode=0, warm_start=0,
-              hermitian_basis=0, stream=None):
+              hermitian_basis=0, stream=None, single_layer=0):
     return Desc(Lx, Ly, OBC if boundary == "obc" else INFINITE, d, D, bx, by, chi, chi_exp, dtype,
                 _PREC[prec] if isinstance(prec, str) else prec, tol, max_sweeps, stop_relative, fit_tol,
-                fit_max_sweeps, seed, init_mode, int(warm_start), int(hermitian_basis), stream)
+                fit_max_sweeps, seed, init_mode, int(warm_start), int(hermitian_basis), stream, int(single_layer))
 
 
 def _term_array(terms):
@@ -220,8 +220,8 @@ class Lattice:
             pass
 
     def set_tensors(self, tensors=None, device_ptr=None):
-        """tensors: list of numpy arrays T[p,u,l,d,r] (cast to the desc dtype), or
-        device_ptr: address of the same data already on the GPU."""
+        """tensors: list of numpy arrays T[p,u,l,d,r] (E[u,l,d,r] on a single-layer network;
+        cast to the desc dtype), or device_ptr: address of the same data already on the GPU."""
         if device_ptr is not None:
             return _check(lib().bbp_set_tensors(self.h, C.c_void_p(device_ptr), 1))
         flat = _flat_tensors(tensors, self.desc.dtype)
@@ -235,7 +235,8 @@ class Lattice:
         return r.value, k.value, rc
 
     def expect(self, terms):
-        """terms: list of [(site, op), ...] with d x d numpy operators."""
+        """terms: list of [(site, op), ...] with d x d numpy operators (on a single-layer
+        network, the impurity tensors that replace the site tensors)."""
         n = len(terms)
         arr, keep = _term_array(terms)
         out_re = np.zeros(n)
@@ -249,7 +250,7 @@ class Lattice:
         bonds = (C.c_int * 64)()
         _check(lib().bbp_get_message(self.h, block, direction, C.byref(ns), bonds, None))
         b = [bonds[i] for i in range(ns.value + 1)]
-        K = self.desc.D ** 2
+        K = self.desc.D if self.desc.single_layer else self.desc.D ** 2
         cplx = self.complex_messages()
         total = sum(b[i] * K * b[i + 1] for i in range(ns.value)) * (2 if cplx else 1)
         buf = np.zeros(total)

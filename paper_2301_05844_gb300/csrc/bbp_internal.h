@@ -124,6 +124,7 @@ struct NormTask {
     const void* sites[16];
     int a[16], k[16], b[16];
     int nsites, D;
+    int ones;            // phase reference <1|m> (single-layer network) instead of <I|m>
     const void* mm;      // <m|m> (1 scalar)
     const void* mo;      // <m|m_old> (1 scalar)
     double* resid;       // output term

@@ -1020,7 +1020,8 @@ cudaError_t launch_assemble(const AssembleTask* d_tasks, int ntasks, bool cplx, 
 }
 
 // ---------------------------------------------------------------- normalisation + residual term
-// tau = <I|m>: per site the matrix sum_k m[a][k*D+k][b], chained left to right.
+// tau = <I|m>: per site the matrix sum_k m[a][k*D+k][b], chained left to right (on a
+// single-layer network <1|m>: the sum over every k).
 constexpr int NORM_MAXB = 1024;
 template <typename S>
 __global__ void __launch_bounds__(256) k_normalise(const NormTask* __restrict__ tasks) {
@@ -1034,8 +1035,12 @@ __global__ void __launch_bounds__(256) k_normalise(const NormTask* __restrict__ 
         const int A = t.a[s], K = t.k[s], B = t.b[s];
         for (int b = threadIdx.x; b < B; b += 256) {
             S acc = zero<S>();
-            for (int a = 0; a < na; ++a)
-                for (int k = 0; k < t.D; ++k) mac(acc, v[a], m[((long long)a * K + (k * t.D + k)) * B + b]);
+            for (int a = 0; a < na; ++a) {
+                if (t.ones)
+                    for (int k = 0; k < K; ++k) mac(acc, v[a], m[((long long)a * K + k) * B + b]);
+                else
+                    for (int k = 0; k < t.D; ++k) mac(acc, v[a], m[((long long)a * K + (k * t.D + k)) * B + b]);
+            }
             w[b] = acc;
         }
         __syncthreads();

@@ -114,7 +114,7 @@ View4 bbp_lattice::E_view(int t, int dir) const {
     }
     const auto& dd = tdims[t];
     int Kd[4];
-    for (int i = 0; i < 4; ++i) Kd[i] = dd[i] * dd[i];
+    for (int i = 0; i < 4; ++i) Kd[i] = single ? dd[i] : dd[i] * dd[i];
     long long st[4] = {(long long)Kd[1] * Kd[2] * Kd[3], (long long)Kd[2] * Kd[3], Kd[3], 1};
     View4 o;
     o.off = E_off[t];
@@ -482,6 +482,7 @@ static int plan_sweep(bbp_lattice* L) {
         nm.size0 = (long long)s0.a * s0.k * s0.b;
         nm.nsites = I.b;
         nm.D = L->desc.D;
+        nm.ones = L->single ? 1 : 0;
         for (int s = 0; s < I.b; ++s) {
             const View3 v = L->msg_site(it, s, false);
             nm.sites[s] = P(v.off * ss);
@@ -569,6 +570,9 @@ static int validate(const bbp_lattice_desc* d) {
     if (d->D > 16 || d->d > 64) return fail(BBP_ERR_INVALID, "D or d too large");
     if (d->init_mode != 0 && d->init_mode != 1) return fail(BBP_ERR_INVALID, "init_mode must be 0 or 1");
     if (d->warm_start != 0 && d->warm_start != 1) return fail(BBP_ERR_INVALID, "warm_start must be 0 or 1");
+    if (d->single_layer != 0 && d->single_layer != 1) return fail(BBP_ERR_INVALID, "single_layer must be 0 or 1");
+    if (d->single_layer && (d->d != 1 || (d->dtype != BBP_F64 && d->dtype != BBP_F32)))
+        return fail(BBP_ERR_INVALID, "a single-layer network has d = 1 and real tensors");
     return BBP_OK;
 }
 
@@ -582,12 +586,14 @@ int bbp::plan_lattice(const bbp_lattice_desc* desc, bbp_lattice** out) {
     bbp_lattice* L = new (std::nothrow) bbp_lattice();
     if (!L) return fail(BBP_ERR_OOM, "host allocation failed");
     L->desc = *desc;
-    if (L->desc.chi_exp <= 0) L->desc.chi_exp = std::max(desc->chi, 2 * desc->D * desc->D + 10);
+    L->single = desc->single_layer != 0;
+    L->K = L->single ? desc->D : desc->D * desc->D;
+    // App. A's read-out bond 2 D^2 + 10 in terms of the network's leg dimension K
+    if (L->desc.chi_exp <= 0) L->desc.chi_exp = std::max(desc->chi, 2 * L->K + 10);
     const bool in_cplx = desc->dtype == BBP_C128 || desc->dtype == BBP_C64;
     L->hb = in_cplx && (desc->prec != BBP_PREC_FP64 || desc->hermitian_basis != 0);
     L->cplx = in_cplx && !L->hb;
     L->ss = L->cplx ? 16 : 8;
-    L->K = desc->D * desc->D;
     if (desc->boundary == BBP_OBC) {
         L->nbx = desc->Lx / desc->bx;
         L->nby = desc->Ly / desc->by;
@@ -604,8 +610,14 @@ int bbp::plan_lattice(const bbp_lattice_desc* desc, bbp_lattice** out) {
             const auto dd = L->site_dims(r, c);
             L->tdims.push_back(dd);
             const size_t vol = (size_t)desc->d * dd[0] * dd[1] * dd[2] * dd[3];
-            L->T_off.push_back(elem_alloc(vol * (L->hb ? 2 : 1)));  // T stays complex in the Hermitian basis
-            L->E_off.push_back(elem_alloc((size_t)dd[0] * dd[0] * dd[1] * dd[1] * dd[2] * dd[2] * dd[3] * dd[3]));
+            if (L->single) {
+                // the network's own tensor is E: converted straight into its slot
+                L->E_off.push_back(elem_alloc(vol));
+                L->T_off.push_back(L->E_off.back());
+            } else {
+                L->T_off.push_back(elem_alloc(vol * (L->hb ? 2 : 1)));  // T stays complex in the Hermitian basis
+                L->E_off.push_back(elem_alloc((size_t)dd[0] * dd[0] * dd[1] * dd[1] * dd[2] * dd[2] * dd[3] * dd[3]));
+            }
             raw_scalars += vol;
         }
     L->T_elems = raw_scalars;
@@ -783,8 +795,9 @@ void bbp_destroy(bbp_lattice* L) try {
 }
 
 // Initial messages (App. A: messages start from a chosen state; init_mode 0 is the
-// product of delta_{ket,bra}, init_mode 1 a random positive MPDO of bond 1), each
-// normalised to unit 2-norm with <I|m> > 0.
+// product of delta_{ket,bra}, init_mode 1 a random positive MPDO of bond 1; on a
+// single-layer network the all-ones product or positive uniform entries), each
+// normalised to unit 2-norm with <I|m> (<1|m>) > 0.
 static void init_messages(bbp_lattice* L, std::vector<double>& host) {
     const int D = L->desc.D, K = L->K, cw = L->cplx ? 2 : 1;
     host.assign(L->msg_elems * cw, 0.0);
@@ -794,11 +807,16 @@ static void init_messages(bbp_lattice* L, std::vector<double>& host) {
         std::vector<std::vector<double>> sites(I.b);
         for (int s = 0; s < I.b; ++s) {
             std::vector<double> v(K, 0.0);
-            if (L->desc.init_mode == 0) {
+            const uint64_t stream = stream_id(2, 0, (uint64_t)I.msgid, 0, 0) + (uint64_t)s;
+            if (L->single) {
+                // single-layer network: the all-ones product (mode 0) or positive uniform
+                // entries (mode 1), the start the paper uses for single-layer networks
+                for (int k = 0; k < K; ++k)
+                    v[k] = L->desc.init_mode == 0 ? 1.0 : (uniform_pm1(L->desc.seed, stream, k) + 1.0) * 0.5;
+            } else if (L->desc.init_mode == 0) {
                 for (int k = 0; k < D; ++k) v[k * D + k] = 1.0;
             } else {
                 // G with normal entries (Box-Muller on the counter-based uniforms), site = G G^T
-                const uint64_t stream = stream_id(2, 0, (uint64_t)I.msgid, 0, 0) + (uint64_t)s;
                 std::vector<double> g(D * D);
                 for (int j = 0; j < D * D; ++j) {
                     const double u1 = (uniform_pm1(L->desc.seed, stream, 2 * j) + 1.0) * 0.5;
@@ -856,6 +874,7 @@ int bbp_set_tensors(bbp_lattice* L, const void* data, int on_device) try {
         CKR(launch_convert(base + L->raw_off + in_scalar * in_ss, L->desc.dtype, base + L->T_off[t] * L->ss, vol,
                            L->cplx || L->hb, st));
         in_scalar += vol;
+        if (L->single) continue;  // E is the converted tensor itself
         DLTask k{};
         k.T = base + L->T_off[t] * L->ss;
         k.E = base + L->E_off[t] * L->ss;
@@ -867,13 +886,15 @@ int bbp_set_tensors(bbp_lattice* L, const void* data, int on_device) try {
         maxout = std::max(maxout, (long long)dd[0] * dd[0] * dd[1] * dd[1] * dd[2] * dd[2] * dd[3] * dd[3]);
     }
     AsyncBuffer dlb(st);
-    CKR(cudaMallocAsync(&dlb.p, dl.size() * sizeof(DLTask), st));
-    DLTask* d_dl = (DLTask*)dlb.p;
-    CKR(cudaMemcpyAsync(d_dl, dl.data(), dl.size() * sizeof(DLTask), cudaMemcpyHostToDevice, st));
-    if (L->hb)
-        CKR(launch_double_layer_hb(d_dl, (int)dl.size(), maxout, st));
-    else
-        CKR(launch_double_layer(d_dl, (int)dl.size(), maxout, L->cplx, st));
+    if (!dl.empty()) {
+        CKR(cudaMallocAsync(&dlb.p, dl.size() * sizeof(DLTask), st));
+        DLTask* d_dl = (DLTask*)dlb.p;
+        CKR(cudaMemcpyAsync(d_dl, dl.data(), dl.size() * sizeof(DLTask), cudaMemcpyHostToDevice, st));
+        if (L->hb)
+            CKR(launch_double_layer_hb(d_dl, (int)dl.size(), maxout, st));
+        else
+            CKR(launch_double_layer(d_dl, (int)dl.size(), maxout, L->cplx, st));
+    }
     if (L->mixed) {
         // low-precision operand layouts of every double-layer tensor in every frame
         std::vector<RelayoutTask> rt;

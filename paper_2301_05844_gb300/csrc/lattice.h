@@ -61,7 +61,8 @@ struct bbp_lattice {
     bool cplx = false;  // complex arithmetic (complex tensors on the FP64 path)
     bool hb = false;    // complex tensors in the Hermitian basis: real arithmetic, complex T
     int ss = 8;  // scalar bytes
-    int K = 1;
+    int K = 1;          // leg dimension of the network: D^2 (double layer) or D (single layer)
+    bool single = false;  // single-layer network: the tensors are used as they are
     int nbx = 1, nby = 1, nblocks = 1;
     int ntens = 0;
     std::vector<std::array<int, 4>> tdims;  // Du, Dl, Dd, Dr per distinct tensor

@@ -42,7 +42,8 @@ struct Region {
 struct Closing {
     int region = 0, col = 0, ncols = 1;
     std::vector<std::pair<int, int>> pos;     // local (row, col) of the operator sites
-    std::vector<std::vector<double>> ops;     // d*d scalars each (S layout)
+    std::vector<std::vector<double>> ops;     // d*d scalars each (S layout); impurity tensors
+                                              // on a single-layer network
 };
 
 Op4 op_from_top(const View3& t) {
@@ -180,8 +181,14 @@ extern "C" int bbp_expect(bbp_lattice* L, const bbp_term* terms, int n_terms, do
         // split O = O_re + i O_im into real closings with complex coefficients
         std::vector<std::vector<std::pair<std::vector<double>, std::complex<double>>>> parts(T.nsite);
         for (int k = 0; k < T.nsite; ++k) {
-            std::vector<double> re(T.op_re[k], T.op_re[k] + d * d), im(d * d, 0.0);
-            if (T.op_im[k]) im.assign(T.op_im[k], T.op_im[k] + d * d);
+            // d x d operator, or the impurity tensor of the site on a single-layer network
+            size_t nop = (size_t)d * d;
+            if (L->single) {
+                const auto dd = L->site_dims(rc[k].first, rc[k].second);
+                nop = (size_t)dd[0] * dd[1] * dd[2] * dd[3];
+            }
+            std::vector<double> re(T.op_re[k], T.op_re[k] + nop), im(nop, 0.0);
+            if (T.op_im[k]) im.assign(T.op_im[k], T.op_im[k] + nop);
             if (L->cplx) {
                 std::vector<double> z(2 * d * d);
                 for (int j = 0; j < d * d; ++j) {
@@ -210,7 +217,7 @@ extern "C" int bbp_expect(bbp_lattice* L, const bbp_term* terms, int n_terms, do
                 if (has_a) parts[k].push_back({a, std::complex<double>(0.0, 1.0)});
             } else {
                 bool has_re = false, has_im = false;
-                for (int j = 0; j < d * d; ++j) {
+                for (size_t j = 0; j < nop; ++j) {
                     has_re |= re[j] != 0.0;
                     has_im |= im[j] != 0.0;
                 }
@@ -302,7 +309,7 @@ extern "C" int bbp_expect(bbp_lattice* L, const bbp_term* terms, int n_terms, do
     const size_t nclos = closings.size();
     const size_t results = elem_alloc(nclos);
     struct Lane {
-        size_t F[2], G1, G2, EO[2], O12, op[2];
+        size_t F[2], G1, G2, EO[2], O12;
     };
     // per-closing maxima of the row intermediates
     size_t fmax = 1, g1max = 1, g2max = 1, o12max = 1;
@@ -312,6 +319,7 @@ extern "C" int bbp_expect(bbp_lattice* L, const bbp_term* terms, int n_terms, do
         const int r = R.r0 + i - 1, cc = R.c0 + c;
         const auto dd = L->site_dims(r, cc);
         const size_t off = use_eo ? eo_off : L->E_off[L->tensor_index(r, cc)];
+        if (L->single) return op_contig(off, dd[0], dd[1], dd[2], dd[3]);
         return op_contig(off, dd[0] * dd[0], dd[1] * dd[1], dd[2] * dd[2], dd[3] * dd[3]);
     };
     for (auto& C : closings) {
@@ -332,20 +340,30 @@ extern "C" int bbp_expect(bbp_lattice* L, const bbp_term* terms, int n_terms, do
             fmax = std::max(fmax, fa * fw * fb);
         }
     }
-    const size_t lane_elems = 2 * fmax + g1max + g2max + 2 * (size_t)K4max + o12max + 2 * (size_t)d * d;
+    const size_t lane_elems = 2 * fmax + g1max + g2max + (L->single ? 0 : 2 * (size_t)K4max) + o12max;
     const size_t budget = (size_t)4 << 30;
     size_t nlanes = std::max<size_t>(1, std::min(nclos, budget / std::max<size_t>(1, lane_elems * ss)));
     std::vector<Lane> lanes(nlanes);
     for (auto& ln : lanes) {
         ln.F[0] = elem_alloc(fmax); ln.F[1] = elem_alloc(fmax);
         ln.G1 = elem_alloc(g1max); ln.G2 = elem_alloc(g2max);
-        ln.EO[0] = elem_alloc(K4max); ln.EO[1] = elem_alloc(K4max);
+        if (!L->single) {
+            ln.EO[0] = elem_alloc(K4max);
+            ln.EO[1] = elem_alloc(K4max);
+        }
         ln.O12 = elem_alloc(o12max);
-        const size_t opn = (size_t)d * d * (L->hb ? 2 : 1);  // complex operators in the Hermitian basis
-        ln.op[0] = elem_alloc(opn); ln.op[1] = elem_alloc(opn);
     }
-    // operator uploads recorded as (elem offset, values)
+    // operators (impurity tensors) of every closing, each in its own slab: uploaded once
+    // before the read-out runs, whichever wave of lanes uses them
     std::vector<std::pair<size_t, std::vector<double>>> uploads;
+    std::vector<std::array<size_t, 2>> opoff(nclos, std::array<size_t, 2>{0, 0});
+    for (size_t ci = 0; ci < nclos; ++ci)
+        for (size_t k = 0; k < closings[ci].pos.size(); ++k) {
+            const std::vector<double>& v = closings[ci].ops[k];
+            // complex operators take two doubles per element in the Hermitian basis
+            opoff[ci][k] = elem_alloc(L->cplx ? v.size() / 2 : v.size());
+            uploads.push_back({opoff[ci][k], v});
+        }
     for (size_t w0 = 0; w0 < nclos; w0 += nlanes) {
         const size_t w1 = std::min(nclos, w0 + nlanes);
         // E^O for the operator sites of this wave
@@ -355,14 +373,14 @@ extern "C" int bbp_expect(bbp_lattice* L, const bbp_term* terms, int n_terms, do
             const Closing& C = closings[ci];
             const Region& R = regions[C.region];
             const Lane& ln = lanes[ci - w0];
+            if (L->single) continue;  // the impurity tensor is E^O itself
             for (size_t k = 0; k < C.pos.size(); ++k) {
                 const int r = R.r0 + C.pos[k].first, c = R.c0 + C.pos[k].second;
                 const auto dd = L->site_dims(r, c);
-                uploads.push_back({ln.op[k], C.ops[k]});
                 DLTask t{};
                 t.T = P(L->T_off[L->tensor_index(r, c)] * ss);
                 t.E = P(ln.EO[k] * ss);
-                t.O = P(ln.op[k] * ss);
+                t.O = P(opoff[ci][k] * ss);
                 t.d = d; t.Du = dd[0]; t.Dl = dd[1]; t.Dd = dd[2]; t.Dr = dd[3];
                 t.hb = L->hb ? 1 : 0;
                 dts.push_back(t);
@@ -395,7 +413,8 @@ extern "C" int bbp_expect(bbp_lattice* L, const bbp_term* terms, int n_terms, do
                 const Lane& ln = lanes[ci - w0];
                 auto op_at = [&](int c) {
                     for (size_t k = 0; k < C.pos.size(); ++k)
-                        if (C.pos[k].first == i - 1 && C.pos[k].second == c) return row_op(R, c, i, ln.EO[k], true);
+                        if (C.pos[k].first == i - 1 && C.pos[k].second == c)
+                            return row_op(R, c, i, L->single ? opoff[ci][k] : ln.EO[k], true);
                     return row_op(R, c, i, 0, false);
                 };
                 Op4 o = op_at(C.col);

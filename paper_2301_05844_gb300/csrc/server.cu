@@ -214,6 +214,19 @@ void bbp_server::run() {
     }
 }
 
+// Entries of a term's operator at `site`: d x d, or on a single-layer network the impurity
+// tensor with the site tensor's shape (OBC edge legs of dimension 1); 0 for a site outside
+// the lattice (OBC) or the block (INFINITE).
+static size_t op_entries(const bbp_lattice_desc& ds, int site) {
+    if (!ds.single_layer) return (size_t)ds.d * ds.d;
+    const bool obc = ds.boundary == BBP_OBC;
+    const int W = obc ? ds.Lx : ds.bx, H = obc ? ds.Ly : ds.by, D = ds.D;
+    if (site < 0 || site >= W * H) return 0;
+    if (!obc) return (size_t)D * D * D * D;
+    const int r = site / W, c = site % W;
+    return (size_t)(r == 0 ? 1 : D) * (c == 0 ? 1 : D) * (r == H - 1 ? 1 : D) * (c == W - 1 ? 1 : D);
+}
+
 extern "C" {
 
 int bbp_server_create(size_t max_bytes, int max_active, bbp_server** out) try {
@@ -260,7 +273,6 @@ int bbp_server_submit(bbp_server* s, const bbp_lattice_desc* desc, const void* t
     delete plan;
     if (r->footprint > s->max_bytes) return fail(BBP_ERR_OOM, "server_submit: the request alone exceeds the byte budget");
     r->tensors.assign((const unsigned char*)tensors, (const unsigned char*)tensors + raw_bytes);
-    const int d = desc->d;
     for (int k = 0; k < n_terms; ++k) {
         TermCopy t;
         t.nsite = terms[k].nsite;
@@ -268,9 +280,11 @@ int bbp_server_submit(bbp_server* s, const bbp_lattice_desc* desc, const void* t
         for (int j = 0; j < t.nsite; ++j) {
             if (!terms[k].op_re[j]) return fail(BBP_ERR_INVALID, "server_submit: operator is NULL");
             t.site[j] = terms[k].site[j];
-            t.re[j].assign(terms[k].op_re[j], terms[k].op_re[j] + d * d);
+            const size_t n = op_entries(*desc, t.site[j]);
+            if (n == 0) return fail(BBP_ERR_INVALID, "server_submit: site out of range");
+            t.re[j].assign(terms[k].op_re[j], terms[k].op_re[j] + n);
             if (terms[k].op_im[j]) {
-                t.im[j].assign(terms[k].op_im[j], terms[k].op_im[j] + d * d);
+                t.im[j].assign(terms[k].op_im[j], terms[k].op_im[j] + n);
                 t.has_im[j] = true;
             }
         }

@@ -57,6 +57,9 @@ def test_binding_has_no_fallback_and_null_handles_are_rejected(libpath):
     dict(Lx=2, Ly=2, d=2, D=4, bx=4, by=4, chi=64, boundary="infinite", dtype=3),
     dict(Lx=6, Ly=6, d=2, D=3, bx=3, by=2, chi=12, dtype=1),
     dict(Lx=4, Ly=4, d=2, D=2, bx=4, by=4, chi=16),
+    dict(Lx=6, Ly=6, d=1, D=3, bx=3, by=3, chi=8, single_layer=1, init_mode=1),
+    dict(Lx=6, Ly=6, d=1, D=3, bx=3, by=3, chi=8, single_layer=1, prec="tf32x3", warm_start=1),
+    dict(Lx=1, Ly=1, d=1, D=2, bx=4, by=4, chi=16, boundary="infinite", single_layer=1, prec="bf16"),
 ])
 def test_sweep_plan_passes_the_bounds_check(libpath, cfg):
     """Planning and the host-side bounds check of every task run before any CUDA
@@ -101,6 +104,18 @@ def test_footprint_is_planned_without_allocating(libpath):
     with pytest.raises(B.BBPError) as e:  # refused before any per-site host allocation
         B.footprint(Lx=8192, Ly=4, d=2, D=2, bx=2, by=2, chi=16)
     assert e.value.code == B.ERR_INVALID and "4096" in str(e.value)
+
+
+def test_single_layer_descriptions(libpath):
+    """A single-layer network is planned with legs of dimension D (not D^2): it holds less
+    than the PEPS of the same D, and it must have d = 1 and real tensors."""
+    from paper_2301_05844_gb300 import binding as B
+    cfg = dict(Lx=6, Ly=6, D=3, bx=3, by=3, chi=8)
+    assert 0 < B.footprint(d=1, single_layer=1, **cfg) < B.footprint(d=2, **cfg)
+    for bad in (dict(d=2, single_layer=1), dict(d=1, single_layer=1, dtype=B.C128), dict(d=1, single_layer=2)):
+        with pytest.raises(B.BBPError) as e:
+            B.footprint(**cfg, **bad)
+        assert e.value.code == B.ERR_INVALID
 
 
 def test_every_entry_point_catches_host_exceptions():

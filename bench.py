@@ -47,6 +47,11 @@ def workload(cfg_id):
     from paper_2301_05844_gb300 import inputs as I
     cfg = I.config(cfg_id)
     Lx, Ly = cfg["Lx"], cfg["Ly"]
+    if cfg.get("single_layer"):
+        # the magnetisation impurity on the 2x2 centre of the block
+        bx = cfg["bx"]
+        c0 = bx // 2 - 1
+        return cfg, [[((c0 + i) * bx + c0 + j, cfg["impurity"])] for i in range(2) for j in range(2)]
     if cfg["boundary"] == "infinite":
         # 2-site terms on the 4 nearest-neighbour bonds of the 2x2 centre of the block:
         # sx sx, sy sy, sz sz each (the Heisenberg term is their sum / 4)
@@ -122,7 +127,8 @@ def make_lattice(B, cfg, prec, stream):
              np.dtype(np.complex128): B.C128}[np.asarray(cfg["tensors"][0]).dtype]
     g = B.Lattice(Lx=cfg["Lx"], Ly=cfg["Ly"], d=cfg["d"], D=cfg["D"], bx=cfg["bx"], by=cfg["by"], chi=cfg["chi"],
                   boundary=cfg["boundary"], dtype=dtype, prec=prec, tol=cfg.get("tol", 1e-8), max_sweeps=50,
-                  fit_tol=FIT_TOL[prec], fit_max_sweeps=10, seed=1, warm_start=WARM, stream=stream)
+                  fit_tol=FIT_TOL[prec], fit_max_sweeps=10, seed=1, warm_start=WARM, stream=stream,
+                  single_layer=cfg.get("single_layer", 0))
     return g
 
 
@@ -131,7 +137,8 @@ def oracle_sample(cfg, seconds, warmup=3):
     from oracle import blockbp as ob
     o = ob.Lattice(cfg["Lx"], cfg["Ly"], cfg["d"], cfg["D"], cfg["bx"], cfg["by"],
                    [np.asarray(t) for t in cfg["tensors"]], boundary=cfg["boundary"], chi=cfg["chi"],
-                   fit_tol=1e-6, fit_max_sweeps=10, seed=1, warm_start=bool(WARM))
+                   fit_tol=1e-6, fit_max_sweeps=10, seed=1, warm_start=bool(WARM),
+                   single_layer=bool(cfg.get("single_layer", 0)))
     for _ in range(warmup):
         o.sweep()
     t0 = time.perf_counter()
@@ -154,7 +161,8 @@ def run_reference(args):
     cfg, _ = workload(args.config)
     o = ob.Lattice(cfg["Lx"], cfg["Ly"], cfg["d"], cfg["D"], cfg["bx"], cfg["by"],
                    [np.asarray(t) for t in cfg["tensors"]], boundary=cfg["boundary"], chi=cfg["chi"],
-                   fit_tol=1e-6, fit_max_sweeps=10, seed=1, warm_start=bool(WARM))
+                   fit_tol=1e-6, fit_max_sweeps=10, seed=1, warm_start=bool(WARM),
+                   single_layer=bool(cfg.get("single_layer", 0)))
     for _ in range(args.warmup):
         o.sweep()
     t0 = time.perf_counter()
@@ -322,6 +330,7 @@ def run_ours(args):
                                               "d": cfg["d"], "D": cfg["D"], "chi": cfg["chi"],
                                               "block": f"{cfg['bx']}x{cfg['by']}",
                                               "messages": 2 * ((cfg["Lx"] // cfg["bx"] - 1) * (cfg["Ly"] // cfg["by"]) + (cfg["Ly"] // cfg["by"] - 1) * (cfg["Lx"] // cfg["bx"])) if cfg["boundary"] == "obc" else 4,
+                                              "network": "single-layer" if cfg.get("single_layer") else "double-layer",
                                               "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{world}"},
                "tflops": flops / dev_s / 1e12, "fp64_qr_gflops": qr_flops / dev_s / 1e9,
                "gpu_launches": kernels, "fit_sweeps_per_column": fit_sweeps,

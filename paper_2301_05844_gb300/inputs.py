@@ -124,6 +124,9 @@ def config(k: int) -> dict:
     4: 32x32 OBC, d=2, D=5, U[0,1]+0.1N as float32, 4x4 blocks, chi=96, TF32.
     6: 20x20 OBC, d=2, D=4, U[0,1]+0.1N, 4x4 blocks (80 messages), chi=64, BF16 -- the
        tensor-core measurement workload (D=4, chi=64 contractions over >= 64 messages).
+    7: the infinite classical 2D Ising model at beta = 0.6 as its own single-layer network
+       (bond 2, 1x1 cell, field 1e-6 selecting the up state), one 8x8 block, chi=32,
+       split-TF32 contractions; read out with the magnetisation impurity.
     """
     if k == 1:
         return dict(name="peps4x4_D2_chi16_fp64", Lx=4, Ly=4, d=2, D=2, bx=2, by=2, chi=16,
@@ -143,6 +146,10 @@ def config(k: int) -> dict:
         # tensor-core measurement workload: D=4, chi=64 contractions batched over 80 messages
         return dict(name="peps20x20_D4_chi64_bf16", Lx=20, Ly=20, d=2, D=4, bx=4, by=4, chi=64,
                     boundary="obc", tensors=uniform_noise_peps(20, 20, 2, 4, seed=6), prec="bf16", tol=1e-6)
+    if k == 7:
+        E, Ez = ising_network(0.6, h=1e-6)
+        return dict(name="ising_network_inf_b8_chi32", Lx=1, Ly=1, d=1, D=2, bx=8, by=8, chi=32,
+                    boundary="infinite", tensors=[E], impurity=Ez, single_layer=1, prec="tf32x3", tol=1e-8)
     raise ValueError(k)
 
 

@@ -678,6 +678,27 @@ class Lattice:
             out.append(num / den)
         return np.array(out, dtype=np.complex128)
 
+    def rdm(self, sites):
+        """Reduced density matrix of 1 or 2 sites (the 2-local RDMs the paper compares
+        between methods, Sec. on the transverse Ising model): rho = Tr_rest |psi><psi| /
+        <psi|psi>, indices (site0, site1) row-major.  Entry (a, b) is <a|rho|b> = Tr(rho |b><a|),
+        read out as the expectation of the matrix unit |b><a| (a product of single-site units
+        for two sites), so that Tr(rho O) = <O>."""
+        assert not self.single_layer, "a single-layer network has no physical leg"
+        d, n = self.d, len(sites)
+        dim = d ** n
+        terms = []
+        for a in range(dim):
+            for b in range(dim):
+                ai, bi = np.unravel_index(a, (d,) * n), np.unravel_index(b, (d,) * n)
+                term = []
+                for k, s in enumerate(sites):
+                    U = np.zeros((d, d))
+                    U[bi[k], ai[k]] = 1.0
+                    term.append((s, U))
+                terms.append(term)
+        return self.expect(terms).reshape(dim, dim)
+
     def _close(self, grid, m_in, Lenv, Renv, r0, c0, cs, loc):
         """Exact top-to-bottom transfer through Lenv[cs[0]], columns cs, Renv[cs[-1]]."""
         L, R = Lenv[cs[0]], Renv[cs[-1]]
@@ -709,3 +730,10 @@ class Lattice:
             G = np.tensordot(G, colops[1][i], axes=([0, 4], [0, 1]))      # [b, A, v, y, t]
             F = np.tensordot(G, R[i], axes=([0, 4], [0, 1]))              # [A, v, y, B]
         return F[0, 0, 0, 0]
+
+
+def trace_distance(rho, sigma):
+    """D(rho, sigma) = (1/2) ||rho - sigma||_1 (the paper's RDM comparison, Sec. on the
+    transverse Ising model): half the sum of |eigenvalues| of the Hermitian difference."""
+    diff = np.asarray(rho) - np.asarray(sigma)
+    return 0.5 * float(np.sum(np.abs(np.linalg.eigvalsh(0.5 * (diff + np.conj(diff.T))))))

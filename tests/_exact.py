@@ -188,3 +188,13 @@ def network_value(E, Lx, Ly, replace=None):
             # put the new down leg back at position c; the right leg stays last
             S = np.moveaxis(S, Lx - 1, c)
     return float(S.reshape(-1)[0])
+
+
+def exact_rdm(psi, n_sites, d, sites):
+    """Reduced density matrix of `sites` (index order as given) by the partial trace of
+    |psi><psi| / <psi|psi> over every other site."""
+    phi = psi.reshape((d,) * n_sites).astype(np.complex128)
+    rest = [s for s in range(n_sites) if s not in sites]
+    A = np.transpose(phi, list(sites) + rest).reshape(d ** len(sites), -1)
+    rho = A @ np.conj(A.T)
+    return rho / np.trace(rho)

@@ -417,3 +417,25 @@ def test_single_layer_message_normalisation():
         assert s.shape == (1, 4, 1) and np.all(s == 1.0)
     U = ob.uniform_message(3, 4, 9, ob.stream_id(2, 0, 5, 0, 0), np.float64)
     assert all(np.all((s >= 0.0) & (s < 1.0)) for s in U) and len({s.tobytes() for s in U}) == 3
+
+
+# ---- reduced density matrices and their trace distance ----
+
+def test_rdm_equals_partial_trace_and_trace_distance():
+    """The read-out's RDMs (entries read as expectations of matrix units) on one block
+    covering the lattice equal the state's partial trace; they are Hermitian with unit
+    trace and give Tr(rho O) = <O>.  The trace distance is 1 for orthogonal pure states,
+    0 for equal ones, and |p - q| for diagonal qubit states."""
+    T = I.uniform_noise_peps(4, 4, 2, 2, seed=1)
+    o = ob.Lattice(4, 4, 2, 2, 4, 4, T, chi=16, chi_exp=64)
+    psi = X.state_vector(T, 4, 4)
+    for sites in ([5], [5, 6], [6, 10], [0, 4]):
+        rho = o.rdm(sites)
+        assert np.max(np.abs(rho - X.exact_rdm(psi, 16, 2, sites))) < 1e-12
+        assert abs(np.trace(rho) - 1) < 1e-12 and np.max(np.abs(rho - rho.conj().T)) < 1e-12
+    rho = o.rdm([5, 6])
+    O = np.kron(I.SIGMA_Z, I.SIGMA_X)
+    assert abs(np.trace(rho @ O) - o.expect([[(5, I.SIGMA_Z), (6, I.SIGMA_X)]])[0]) < 1e-12
+    up, down = np.diag([1.0, 0.0]), np.diag([0.0, 1.0])
+    assert abs(ob.trace_distance(up, down) - 1.0) < 1e-15 and ob.trace_distance(up, up) == 0.0
+    assert abs(ob.trace_distance(np.diag([0.7, 0.3]), np.diag([0.2, 0.8])) - 0.5) < 1e-15

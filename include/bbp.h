@@ -161,6 +161,16 @@ typedef struct {
  * doubles each (host memory; out_im may be NULL).  Errors: INVALID, STATE, CUDA. */
 int bbp_expect(bbp_lattice* lat, const bbp_term* terms, int n_terms, double* out_re, double* out_im);
 
+/* Reduced density matrix of nsite (1 or 2) sites, rho = Tr_rest |psi><psi| / <psi|psi>
+ * (the 2-local RDMs that the paper compares between methods by their trace distance
+ * D(rho, sigma) = ||rho - sigma||_1 / 2, Sec. on the transverse Ising model).  Entry
+ * (a, b) = <a|rho|b> is the read-out of the matrix unit |b><a| (a product of single-site
+ * units for two sites, site[0] the leading index digit), so Tr(rho O) = <O>; the sites
+ * follow bbp_expect's rules.  rho_re / rho_im: d^nsite x d^nsite doubles each, row-major
+ * (host memory; rho_im may be NULL).  Errors: INVALID (also for a single-layer network),
+ * STATE, NUMERIC, TIMEOUT, CUDA. */
+int bbp_rdm(bbp_lattice* lat, int nsite, const int* sites, double* rho_re, double* rho_im);
+
 /* Free the handle and its device arena.  NULL is a no-op. */
 void bbp_destroy(bbp_lattice* lat);
 

@@ -68,6 +68,7 @@ def lib():
     L.bbp_sweep.argtypes = [P, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_int)]
     L.bbp_expect.argtypes = [P, C.POINTER(Term), C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)]
     L.bbp_destroy.argtypes = [P]
+    L.bbp_rdm.argtypes = [P, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_double), C.POINTER(C.c_double)]
     L.bbp_destroy.restype = None
     L.bbp_last_error.restype = C.c_char_p
     L.bbp_get_message.argtypes = [P, C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_double)]
@@ -244,6 +245,16 @@ class Lattice:
         _check(lib().bbp_expect(self.h, arr, n, out_re.ctypes.data_as(C.POINTER(C.c_double)),
                                 out_im.ctypes.data_as(C.POINTER(C.c_double))))
         return out_re + 1j * out_im
+
+    def rdm(self, sites):
+        """Reduced density matrix (d^n x d^n complex, n = len(sites) = 1 or 2) of the sites."""
+        n = len(sites)
+        dim = self.desc.d ** n
+        s = (C.c_int * 2)(*sites, *([0] * (2 - n)))
+        re, im = np.zeros(dim * dim), np.zeros(dim * dim)
+        _check(lib().bbp_rdm(self.h, n, s, re.ctypes.data_as(C.POINTER(C.c_double)),
+                             im.ctypes.data_as(C.POINTER(C.c_double))))
+        return (re + 1j * im).reshape(dim, dim)
 
     def get_message(self, block, direction):
         ns = C.c_int()

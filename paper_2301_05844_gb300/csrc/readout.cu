@@ -549,3 +549,37 @@ extern "C" int bbp_expect(bbp_lattice* L, const bbp_term* terms, int n_terms, do
 } catch (...) {
     return abi_error();
 }
+
+// Reduced density matrix of one or two sites (the 2-local RDMs compared between methods by
+// their trace distance, Sec. on the transverse Ising model): entry (a, b) = <a|rho|b> is the
+// expectation of the matrix unit |b><a| (a product of single-site units for two sites), read
+// out in one bbp_expect call, so that Tr(rho O) = <O> for every operator O on those sites.
+extern "C" int bbp_rdm(bbp_lattice* L, int nsite, const int* sites, double* rho_re, double* rho_im) try {
+    if (!L) return fail(BBP_ERR_INVALID, "lattice is NULL");
+    if (nsite < 1 || nsite > 2 || !sites || !rho_re) return fail(BBP_ERR_INVALID, "rdm: need 1 or 2 sites and rho_re");
+    if (L->single) return fail(BBP_ERR_INVALID, "rdm: a single-layer network has no physical leg");
+    const int d = L->desc.d, dim = nsite == 1 ? d : d * d;
+    // unit[(b * d + a) * d * d ...]: the d x d matrix unit with a 1 at row b, column a
+    std::vector<double> units((size_t)d * d * d * d, 0.0);
+    for (int b = 0; b < d; ++b)
+        for (int a = 0; a < d; ++a) units[((size_t)b * d + a) * d * d + (size_t)b * d + a] = 1.0;
+    auto unit = [&](int b, int a) { return units.data() + ((size_t)b * d + a) * d * d; };
+    std::vector<bbp_term> terms((size_t)dim * dim);
+    for (int a = 0; a < dim; ++a)
+        for (int b = 0; b < dim; ++b) {
+            bbp_term& t = terms[(size_t)a * dim + b];
+            t = bbp_term{};
+            t.nsite = nsite;
+            for (int k = 0; k < nsite; ++k) {
+                // digit k of the row / column index (site 0 is the leading digit)
+                const int ak = nsite == 1 ? a : (k == 0 ? a / d : a % d);
+                const int bk = nsite == 1 ? b : (k == 0 ? b / d : b % d);
+                t.site[k] = sites[k];
+                t.op_re[k] = unit(bk, ak);
+                t.op_im[k] = nullptr;
+            }
+        }
+    return bbp_expect(L, terms.data(), dim * dim, rho_re, rho_im);
+} catch (...) {
+    return abi_error();
+}

@@ -128,3 +128,28 @@ def test_bonds_above_the_numerical_rank():
     g, o, gres, ores, gv, ov = run_both(T, 6, 6, 2, 3, 3, 3, 64, terms, 3, fit_tol=0.0, fit_max_sweeps=2, seed=7)
     assert np.allclose(gres, ores, rtol=1e-8, atol=1e-14)
     assert np.max(np.abs(gv - ov)) < 1e-10
+
+
+def test_rdm_parity_and_exact_on_trees():
+    """bbp_rdm: 1- and 2-site reduced density matrices (inside a block, across a block
+    edge) equal the oracle's on the loop block graph of C1 and the exact partial trace on
+    a tree of strip blocks; Tr(rho O) = <O>; the trace distance of the C1 RDMs to the
+    exact ones (the blockBP error on a loop) is stated, not pinned."""
+    import _exact as Xe
+    from oracle import blockbp as ob
+    cfg = I.config(1)
+    sites = ([5], [5, 6], [6, 10], [1, 2])
+    g, o, gr, orr, gv, ov = run_both(cfg["tensors"], 4, 4, 2, 2, 2, 2, 16, [], n_sweeps=6)
+    psi = Xe.state_vector(cfg["tensors"], 4, 4)
+    for s in sites:
+        rg = g.rdm(s)
+        assert close(rg, o.rdm(s))
+        assert abs(np.trace(rg) - 1) < 1e-12 and np.max(np.abs(rg - rg.conj().T)) < 1e-12
+        assert ob.trace_distance(rg, Xe.exact_rdm(psi, 16, 2, s)) < 1e-2
+    rho = g.rdm([5, 6])
+    assert abs(np.trace(rho @ np.kron(SZ, SX)) - g.expect([[(5, SZ), (6, SX)]])[0]) < 1e-12
+    T = I.uniform_noise_peps(4, 4, 2, 2, seed=1)
+    g, o, gr, orr, gv, ov = run_both(T, 4, 4, 2, 2, 4, 2, 16, [], n_sweeps=3, chi_exp=18)
+    psi = Xe.state_vector(T, 4, 4)
+    for s in sites:
+        assert np.max(np.abs(g.rdm(s) - Xe.exact_rdm(psi, 16, 2, s))) < 1e-11

@@ -264,7 +264,8 @@ def run_ours(args):
         roofline = {"bound": bound, "kernel": dom, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
                     "frac": ach / peak, "traffic": None, "peak_source": note,
                     "classes_ms_per_sweep": {k: round(v["ms"], 4) for k, v in classes.items()},
-                    # algorithmic TFLOP/s of each class over its replayed launches
+                    # TFLOP/s of each class over its replayed launches (split-TF32 GEMMs counted
+                    # over 3K, their MMA work)
                     "classes_tflops": {k: round(v["flops"] / (v["ms"] / 1e3) / 1e12, 4) for k, v in classes.items()
                                        if v["ms"] > 0},
                     "classes_launches_per_sweep": {k: v["launches"] for k, v in classes.items()}}

@@ -158,6 +158,11 @@ def test_server_host_logic_without_a_gpu(libpath):
         with pytest.raises(B.BBPError) as e:
             srv.submit(T, [[]], **cfg)  # a term on no site
         assert e.value.code == B.ERR_INVALID
+        E = inputs.positive_network(4, 4, 2, seed=3)
+        sl = dict(cfg, d=1, single_layer=1)
+        with pytest.raises(B.BBPError) as e:  # an impurity at a site outside the lattice
+            srv.submit(E, [[(16, np.ones((2, 2, 2, 2)))]], **sl)
+        assert e.value.code == B.ERR_INVALID
         rid = srv.submit(T, [[(0, inputs.SIGMA_Z)]], **cfg)
         assert L.bbp_server_wait(srv.h, rid, -1.0) == B.ERR_INVALID
         assert L.bbp_server_wait(srv.h, rid, float("nan")) == B.ERR_INVALID

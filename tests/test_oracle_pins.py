@@ -439,3 +439,33 @@ def test_rdm_equals_partial_trace_and_trace_distance():
     up, down = np.diag([1.0, 0.0]), np.diag([0.0, 1.0])
     assert abs(ob.trace_distance(up, down) - 1.0) < 1e-15 and ob.trace_distance(up, up) == 0.0
     assert abs(ob.trace_distance(np.diag([0.7, 0.3]), np.diag([0.2, 0.8])) - 0.5) < 1e-15
+
+
+def test_single_layer_gauge_invariance_full_rank():
+    """Random invertible gauges G, G^-1 on every bond of a single-layer network (a loop of
+    2x2 blocks) leave the network, and the blockBP read-out at full chi, unchanged.  The
+    impurity tensors are dressed with the same gauges as the tensors they replace."""
+    E = I.positive_network(4, 4, 2, seed=11)
+    rng = np.random.default_rng(5)
+    imp = {s: rng.uniform(-1.0, 1.0, np.shape(E[s])) for s in (0, 5, 6)}
+
+    def dress(tensors):
+        return [t[0] for t in I.gauge_dress([np.asarray(t)[None] for t in tensors], 4, 4, seed=17)]
+
+    Eg = dress(E)
+    assert abs(X.network_value(Eg, 4, 4) / X.network_value(E, 4, 4) - 1.0) < 1e-12
+    sets = ([5], [0], [5, 6])
+    terms, gterms = [], []
+    for sites in sets:
+        Es = list(E)
+        for s in sites:
+            Es[s] = imp[s]
+        Ed = dress(Es)
+        terms.append([(s, imp[s]) for s in sites])
+        gterms.append([(s, Ed[s]) for s in sites])
+    vals = []
+    for tensors, tt in ((E, terms), (Eg, gterms)):
+        lat = ob.Lattice(4, 4, 1, 2, 2, 2, tensors, chi=16, fit_tol=1e-12, fit_max_sweeps=6, single_layer=True)
+        lat.run(n_sweeps=12)
+        vals.append(lat.expect(tt))
+    assert np.max(np.abs(vals[0] - vals[1])) < 1e-10

@@ -5,6 +5,7 @@ import os
 import re
 import subprocess
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -104,6 +105,36 @@ def test_footprint_is_planned_without_allocating(libpath):
     with pytest.raises(B.BBPError) as e:  # refused before any per-site host allocation
         B.footprint(Lx=8192, Ly=4, d=2, D=2, bx=2, by=2, chi=16)
     assert e.value.code == B.ERR_INVALID and "4096" in str(e.value)
+
+
+def test_random_descriptions_plan_within_bounds(libpath):
+    """Property test of the host planner: 500 seeded random descriptions (OBC and infinite,
+    every precision, real, complex and single-layer tensors, blocks 1-15 sites a side,
+    chi 1-79, fit and read-out options) all plan completely, and every task of every plan
+    passes the host check of its operand ranges against the arena (bbp_lattice_footprint
+    runs the planning and that check of bbp_create_lattice without allocating)."""
+    from paper_2301_05844_gb300 import binding as B
+    L = B.lib()
+    rng = np.random.default_rng(2024)
+    for _ in range(500):
+        inf, single = rng.random() < 0.3, rng.random() < 0.25
+        D, d = int(rng.integers(1, 6)), 1 if single else int(rng.integers(1, 4))
+        if inf:
+            Lx, Ly = int(rng.integers(1, 3)), int(rng.integers(1, 3))
+            bx, by = Lx * int(rng.integers(1, 4)), Ly * int(rng.integers(1, 4))
+        else:
+            bx, by = int(rng.integers(1, 6)), int(rng.integers(1, 6))
+            Lx, Ly = bx * int(rng.integers(1, 4)), by * int(rng.integers(1, 4))
+        dtypes = [B.F64, B.F32] if single else [B.F64, B.C128, B.F32, B.C64]
+        desc = B.make_desc(Lx, Ly, d, D, bx, by, int(rng.integers(1, 80)), boundary="infinite" if inf else "obc",
+                           chi_exp=int(rng.integers(0, 40)), dtype=dtypes[int(rng.integers(0, len(dtypes)))],
+                           prec=["fp64", "tf32", "bf16", "tf32x3"][int(rng.integers(0, 4))],
+                           fit_max_sweeps=int(rng.integers(1, 11)), init_mode=int(rng.integers(0, 2)),
+                           warm_start=int(rng.integers(0, 2)), hermitian_basis=int(rng.integers(0, 2)),
+                           single_layer=int(single))
+        nbytes = ctypes.c_size_t()
+        rc = L.bbp_lattice_footprint(ctypes.byref(desc), ctypes.byref(nbytes))
+        assert rc == B.OK and nbytes.value > 0, (rc, L.bbp_last_error().decode())
 
 
 def test_single_layer_descriptions(libpath):

@@ -121,7 +121,8 @@ int bbp_create_lattice(const bbp_lattice_desc* desc, bbp_lattice** out);
  * admission by footprint.  Errors: INVALID. */
 int bbp_lattice_footprint(const bbp_lattice_desc* desc, size_t* bytes);
 
-/* Upload every site tensor and build the double-layer network (Fig. 1(a,b)).
+/* Upload every site tensor and build the double-layer network (Fig. 1(a,b)); on a
+ * single-layer network (desc->single_layer) the tensors are its site tensors E[u][l][d][r].
  * data: OBC -> Lx*Ly tensors in row-major site order; INFINITE -> Lx*Ly unit-cell
  * tensors.  Each tensor T[p][u][l][d][r] in C order with the OBC edge legs of
  * dimension 1, element type desc->dtype, concatenated without padding.
@@ -181,7 +182,8 @@ const char* bbp_last_error(void);
 
 /* Outgoing message of block `block` (row-major block index) toward direction dir
  * (0 left, 1 right, 2 up, 3 down).  nsites/bonds (may be NULL) receive the site
- * count and the nsites+1 bond dimensions; the message has physical dimension D^2.
+ * count and the nsites+1 bond dimensions; the message has physical dimension D^2 (D on a
+ * single-layer network).
  * If out != NULL the sites are written in order, each [a][k][b] in C order, as
  * doubles (complex interleaved).  Errors: INVALID (no such message), STATE. */
 int bbp_get_message(bbp_lattice* lat, int block, int dir, int* nsites, int* bonds, double* out);
@@ -226,11 +228,14 @@ int bbp_qr_batched_noalloc(int batch, int m, int n, int complex_values, const do
                            void* stream);
 
 typedef struct {
-    double flops;            /* algorithmic site-update flops executed (see DESIGN) */
-    double qr_flops;         /* FP64 QR/LQ flops executed */
+    double flops;            /* algorithmic flops executed: the K2-K5 contractions of every site
+                                update (App. A, Eq. "update" and the A/B recurrences) at their
+                                actual bonds, plus the read-out's contractions */
+    double qr_flops;         /* FP64 QR/LQ flops executed (4mn^2 - 4n^3/3 per m x n matrix) */
     long long kernels;       /* kernel launches issued by the library */
-    long long fit_sweeps;    /* zip-up fit sweeps executed, summed over fits */
-    long long fits;          /* zip-up fits executed */
+    long long fit_sweeps;    /* zip-up fit sweeps executed, summed over the fit loops */
+    long long fits;          /* zip-up fit loops executed (one per column stage of a message
+                                sweep, the fits of all messages in lockstep) */
     int sweeps;              /* message sweeps executed since set_tensors */
     double last_residual;
     double first_residual;

@@ -428,6 +428,10 @@ class Lattice:
     INFINITE: Lx x Ly is the unit cell; the single block (by x bx, multiples of the
     cell) is tiled from it and messages itself (Sec. "The blockBP algorithm": one
     block suffices for an iPEPS; incoming left = own outgoing right, etc.).
+    shift: (sx, sy), INFINITE only: the partition shifted by sx columns and sy rows (the
+    paper covers every bond from a block centre by several partitions of the lattice into
+    blocks, which on a translation-invariant lattice are shifts of one another, Sec. "The
+    blockBP algorithm"); block site (r, c) is lattice site (r + sy, c + sx).
     single_layer: the tensors are the network's own site tensors E[u, l, d, r] with
     bond D on every leg (d = 1, real; a 2D classical model's partition function, Sec.
     on the 2D Ising model), used as they are instead of a double layer; a term's
@@ -449,6 +453,7 @@ class Lattice:
     init_mode: int = 0
     warm_start: bool = False
     single_layer: bool = False
+    shift: tuple = (0, 0)
     msgs: dict = field(default_factory=dict)
     warm: dict = field(default_factory=dict)
     sweeps_done: int = 0
@@ -456,6 +461,7 @@ class Lattice:
 
     def __post_init__(self):
         assert self.boundary in ("obc", "infinite")
+        assert self.boundary == "infinite" or tuple(self.shift) == (0, 0), "shifted partitions: infinite lattices"
         if self.boundary == "obc":
             assert self.Lx % self.bx == 0 and self.Ly % self.by == 0
             assert len(self.tensors) == self.Lx * self.Ly
@@ -496,7 +502,8 @@ class Lattice:
         """Site (r, c) -> index into tensors (OBC: r*Lx+c; INFINITE: unit cell)."""
         if self.boundary == "obc":
             return r * self.Lx + c
-        return (r % self.Ly) * self.Lx + (c % self.Lx)
+        sx, sy = self.shift
+        return ((r + sy) % self.Ly) * self.Lx + ((c + sx) % self.Lx)
 
     def block_origin(self, bi):
         return (bi // self.nbx) * self.by, (bi % self.nbx) * self.bx

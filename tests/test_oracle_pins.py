@@ -469,3 +469,58 @@ def test_single_layer_gauge_invariance_full_rank():
         lat.run(n_sweeps=12)
         vals.append(lat.expect(tt))
     assert np.max(np.abs(vals[0] - vals[1])) < 1e-10
+
+
+# ---- shifted partitions of an infinite lattice ----
+
+@pytest.mark.parametrize("Lx,Ly,bx,by,shift", [(2, 2, 4, 4, (1, 0)), (2, 2, 4, 4, (0, 1)), (2, 2, 4, 4, (1, 1)),
+                                              (3, 1, 3, 3, (1, 0)), (3, 1, 3, 3, (2, 0))])
+def test_shifted_partition_maps_block_sites_to_the_shifted_cell(Lx, Ly, bx, by, shift):
+    """A partition shifted by (sx, sy) puts lattice site (r + sy, c + sx) at block site (r, c).
+    Pinned on a product state with a different state on every site of the cell, dressed with
+    complex gauges (exact for any partition): <sz>, <sx> and <sz sz> at every block site equal
+    the closed-form values of the shifted cell sites (the 3-site cell tells +1 from -1)."""
+    n = Lx * Ly
+    vecs = [np.array([math.cos(0.45 * i), math.sin(0.45 * i)]) for i in range(n)]
+    T = I.gauge_dress(I.product_peps(Lx, Ly, 2, 2, vecs, boundary="infinite"), Lx, Ly, seed=3, boundary="infinite",
+                      complex_gauge=True)
+    sx, sy = shift
+    lat = ob.Lattice(Lx, Ly, 2, 2, bx, by, T, boundary="infinite", chi=2, fit_tol=0.0, fit_max_sweeps=2,
+                     shift=shift)
+    lat.run(n_sweeps=3)
+
+    def cell(r, c):
+        return vecs[((r + sy) % Ly) * Lx + (c + sx) % Lx]
+
+    def ev(v, O):
+        return float(v @ O @ v) / float(v @ v)
+
+    terms, want = [], []
+    for r in range(by):
+        for c in range(bx):
+            s = r * bx + c
+            terms += [[(s, SZ)], [(s, SX)]]
+            want += [ev(cell(r, c), SZ), ev(cell(r, c), SX)]
+            if c + 1 < bx:
+                terms.append([(s, SZ), (s + 1, SZ)])
+                want.append(ev(cell(r, c), SZ) * ev(cell(r, c + 1), SZ))
+    assert np.max(np.abs(lat.expect(terms) - np.array(want))) < 1e-10
+
+
+def test_shifted_partition_equals_the_rolled_cell():
+    """Shifting the partition by (1, 1) is the same computation as rolling the unit cell by one
+    site in each direction (bit-identical), and a shift by whole cells changes nothing."""
+    T = I.complex_normal_cell(2, 2, 2, 2, seed=3)
+    T = [t.astype(np.complex128) for t in T]
+    terms = [[(0, SZ)], [(5, SX)], [(5, SZ), (6, SZ)], [(6, SX), (10, SX)]]
+    kw = dict(boundary="infinite", chi=4, fit_tol=0.0, fit_max_sweeps=2, seed=5)
+    a = ob.Lattice(2, 2, 2, 2, 4, 4, T, shift=(1, 1), **kw)
+    rolled = [T[((r + 1) % 2) * 2 + (c + 1) % 2] for r in range(2) for c in range(2)]
+    b = ob.Lattice(2, 2, 2, 2, 4, 4, rolled, **kw)
+    c = ob.Lattice(2, 2, 2, 2, 4, 4, T, shift=(2, 4), **kw)
+    d = ob.Lattice(2, 2, 2, 2, 4, 4, T, **kw)
+    for lat in (a, b, c, d):
+        lat.run(n_sweeps=3)
+    assert np.array_equal(a.expect(terms), b.expect(terms))
+    assert np.array_equal(c.expect(terms), d.expect(terms))
+    assert np.max(np.abs(a.expect(terms) - d.expect(terms))) > 1e-6  # the shift does change the partition

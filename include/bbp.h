@@ -108,6 +108,11 @@ typedef struct {
                                 entries (init_mode 1), the phase reference of the normalisation
                                 is <1|m> (all-ones vector) instead of <I|m>, and a term's
                                 op_re[k] is the impurity tensor that replaces E at site[k]. */
+    int shift_x, shift_y;    /* INFINITE only (0 for OBC): the partition shifted by shift_x
+                                columns and shift_y rows, 0 <= shift < Lx (Ly), so that block
+                                site (r, c) is lattice site (r + shift_y, c + shift_x); the
+                                paper covers every bond from a block centre by such shifted
+                                partitions (Sec. "The blockBP algorithm"). */
 } bbp_lattice_desc;
 
 /* Validate desc, allocate the device arena (double layer, message store, work

@@ -33,6 +33,7 @@ class Desc(C.Structure):
         ("stop_relative", C.c_int), ("fit_tol", C.c_double), ("fit_max_sweeps", C.c_int),
         ("seed", C.c_ulonglong), ("init_mode", C.c_int), ("warm_start", C.c_int),
         ("hermitian_basis", C.c_int), ("stream", C.c_void_p), ("single_layer", C.c_int),
+        ("shift_x", C.c_int), ("shift_y", C.c_int),
     ]
 
 
@@ -110,10 +111,11 @@ def _check(rc):
 
 def make_desc(Lx, Ly, d, D, bx, by, chi, boundary="obc", chi_exp=0, dtype=F64, prec="fp64", tol=1e-5,
               max_sweeps=10, stop_relative=0, fit_tol=1e-6, fit_max_sweeps=10, seed=0, init_mode=0, warm_start=0,
-              hermitian_basis=0, stream=None, single_layer=0):
+              hermitian_basis=0, stream=None, single_layer=0, shift=(0, 0)):
     return Desc(Lx, Ly, OBC if boundary == "obc" else INFINITE, d, D, bx, by, chi, chi_exp, dtype,
                 _PREC[prec] if isinstance(prec, str) else prec, tol, max_sweeps, stop_relative, fit_tol,
-                fit_max_sweeps, seed, init_mode, int(warm_start), int(hermitian_basis), stream, int(single_layer))
+                fit_max_sweeps, seed, init_mode, int(warm_start), int(hermitian_basis), stream, int(single_layer),
+                int(shift[0]), int(shift[1]))
 
 
 def _term_array(terms):

@@ -52,7 +52,8 @@ static void pinned_put(PinnedWords* p) {
 // ------------------------------------------------------------------ geometry
 int bbp_lattice::tensor_index(int r, int c) const {
     if (desc.boundary == BBP_OBC) return r * desc.Lx + c;
-    return (r % desc.Ly) * desc.Lx + (c % desc.Lx);
+    // block site (r, c) of a shifted partition is lattice site (r + shift_y, c + shift_x)
+    return ((r + desc.shift_y) % desc.Ly) * desc.Lx + ((c + desc.shift_x) % desc.Lx);
 }
 
 std::array<int, 4> bbp_lattice::site_dims(int r, int c) const {
@@ -571,6 +572,9 @@ static int validate(const bbp_lattice_desc* d) {
     if (d->init_mode != 0 && d->init_mode != 1) return fail(BBP_ERR_INVALID, "init_mode must be 0 or 1");
     if (d->warm_start != 0 && d->warm_start != 1) return fail(BBP_ERR_INVALID, "warm_start must be 0 or 1");
     if (d->single_layer != 0 && d->single_layer != 1) return fail(BBP_ERR_INVALID, "single_layer must be 0 or 1");
+    if (d->boundary == BBP_OBC ? (d->shift_x != 0 || d->shift_y != 0)
+                               : (d->shift_x < 0 || d->shift_x >= d->Lx || d->shift_y < 0 || d->shift_y >= d->Ly))
+        return fail(BBP_ERR_INVALID, "shifts: 0 <= shift < unit cell on infinite lattices, 0 with OBC");
     if (d->single_layer && (d->d != 1 || (d->dtype != BBP_F64 && d->dtype != BBP_F32)))
         return fail(BBP_ERR_INVALID, "a single-layer network has d = 1 and real tensors");
     return BBP_OK;

@@ -137,6 +137,18 @@ def test_random_descriptions_plan_within_bounds(libpath):
         assert rc == B.OK and nbytes.value > 0, (rc, L.bbp_last_error().decode())
 
 
+def test_shifted_partition_descriptions(libpath):
+    """Shifted partitions exist on infinite lattices only, with 0 <= shift < unit cell."""
+    from paper_2301_05844_gb300 import binding as B
+    cell = dict(Lx=2, Ly=2, d=2, D=2, bx=4, by=4, chi=4, boundary="infinite")
+    assert B.footprint(shift=(1, 1), **cell) == B.footprint(**cell)
+    for bad in (dict(cell, shift=(2, 0)), dict(cell, shift=(0, -1)),
+                dict(Lx=4, Ly=4, d=2, D=2, bx=2, by=2, chi=4, shift=(1, 0))):
+        with pytest.raises(B.BBPError) as e:
+            B.footprint(**bad)
+        assert e.value.code == B.ERR_INVALID
+
+
 def test_single_layer_descriptions(libpath):
     """A single-layer network is planned with legs of dimension D (not D^2): it holds less
     than the PEPS of the same D, and it must have d = 1 and real tensors."""

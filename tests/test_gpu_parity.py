@@ -71,6 +71,20 @@ def test_infinite_complex_cell():
     assert close(gv, ov)
 
 
+def test_infinite_shifted_partition():
+    """Infinite 2x2 complex cell, 4x4 block, the partition shifted by (1, 1): parity with the
+    oracle's shifted partition, and bit for bit the run of the cell rolled by one site."""
+    T = [t.astype(np.complex128) for t in I.complex_normal_cell(2, 2, 2, 2, seed=3)]
+    terms = [[(0, SZ)], [(5, SX)], [(5, SZ), (6, SZ)], [(6, SX), (10, SX)]]
+    g, o, gr, orr, gv, ov = run_both(T, 2, 2, 2, 2, 4, 4, 4, terms, n_sweeps=3, boundary="infinite",
+                                     shift=(1, 1))
+    assert close(gr, orr, 1e-9)
+    assert close(gv, ov)
+    rolled = [T[((r + 1) % 2) * 2 + (c + 1) % 2] for r in range(2) for c in range(2)]
+    g2, o2, gr2, orr2, gv2, ov2 = run_both(rolled, 2, 2, 2, 2, 4, 4, 4, terms, n_sweeps=3, boundary="infinite")
+    assert np.array_equal(gv, gv2)
+
+
 def test_nonsquare_blocks_and_random_init():
     T = I.uniform_noise_peps(4, 4, 2, 2, seed=1)
     terms = I.standard_terms(4, 4)

@@ -118,7 +118,8 @@ typedef struct {
 /* Validate desc, allocate the device arena (double layer, message store, work
  * buffers) and plan one sweep.  *out receives the handle.  Limits checked here:
  * Lx, Ly <= 4096; bx, by <= 16; D <= 16; d <= 64; 1 <= fit_max_sweeps <= 64;
- * init_mode, warm_start and hermitian_basis 0 or 1.  Errors: INVALID, OOM, CUDA. */
+ * init_mode, warm_start, hermitian_basis and single_layer 0 or 1; 0 <= shift_x < Lx and
+ * 0 <= shift_y < Ly on infinite lattices, both 0 with OBC.  Errors: INVALID, OOM, CUDA. */
 int bbp_create_lattice(const bbp_lattice_desc* desc, bbp_lattice** out);
 
 /* Device bytes a lattice with this desc would hold (arena plus task descriptors),

@@ -428,10 +428,14 @@ class Lattice:
     INFINITE: Lx x Ly is the unit cell; the single block (by x bx, multiples of the
     cell) is tiled from it and messages itself (Sec. "The blockBP algorithm": one
     block suffices for an iPEPS; incoming left = own outgoing right, etc.).
-    shift: (sx, sy), INFINITE only: the partition shifted by sx columns and sy rows (the
-    paper covers every bond from a block centre by several partitions of the lattice into
-    blocks, which on a translation-invariant lattice are shifts of one another, Sec. "The
-    blockBP algorithm"); block site (r, c) is lattice site (r + sy, c + sx).
+    shift: (sx, sy), the partition shifted by sx columns and sy rows (the paper covers every
+    bond from a block centre by several partitions of the lattice into blocks, shifts of one
+    another, Sec. "The blockBP algorithm").  INFINITE: block site (r, c) is lattice site
+    (r + sy, c + sx).  OBC (0 <= sx < bx, 0 <= sy < by): the block boundaries move to columns
+    sx, sx + bx, ... and rows sy, sy + by, ..., so the blocks on the lattice edges are
+    narrower.  The paper embeds the OBC lattice in a periodic one and shifts that; a block
+    straddling the embedding's seam is two pieces joined only by bonds of dimension 1, across
+    which every message and environment factorises, so it acts as the two edge blocks here.
     single_layer: the tensors are the network's own site tensors E[u, l, d, r] with
     bond D on every leg (d = 1, real; a 2D classical model's partition function, Sec.
     on the 2D Ising model), used as they are instead of a double layer; a term's
@@ -461,15 +465,20 @@ class Lattice:
 
     def __post_init__(self):
         assert self.boundary in ("obc", "infinite")
-        assert self.boundary == "infinite" or tuple(self.shift) == (0, 0), "shifted partitions: infinite lattices"
+        sx, sy = self.shift
         if self.boundary == "obc":
             assert self.Lx % self.bx == 0 and self.Ly % self.by == 0
+            assert 0 <= sx < self.bx and 0 <= sy < self.by
             assert len(self.tensors) == self.Lx * self.Ly
-            self.nbx, self.nby = self.Lx // self.bx, self.Ly // self.by
+            # block boundaries: every bx columns from sx (every by rows from sy)
+            self.xs = sorted({0, self.Lx} | set(range(sx, self.Lx, self.bx)))
+            self.ys = sorted({0, self.Ly} | set(range(sy, self.Ly, self.by)))
         else:
             assert self.bx % self.Lx == 0 and self.by % self.Ly == 0
+            assert 0 <= sx < self.Lx and 0 <= sy < self.Ly
             assert len(self.tensors) == self.Lx * self.Ly
-            self.nbx = self.nby = 1
+            self.xs, self.ys = [0, self.bx], [0, self.by]
+        self.nbx, self.nby = len(self.xs) - 1, len(self.ys) - 1
         # bond of the double-layer (or single-layer) network; the read-out bond of App. A,
         # 2D^2 + 10, is 2K + 10 in these terms
         self.K = self.D if self.single_layer else self.D * self.D
@@ -486,7 +495,7 @@ class Lattice:
             self.E = [double_layer(t) for t in self.tensors]
         for bi in range(self.nbx * self.nby):
             for dr in self.directions(bi):
-                n = self.by if dr in (LEFT, RIGHT) else self.bx
+                n = self.edge_length(bi, dr)
                 stream = stream_id(2, 0, 4 * bi + dr, 0, 0)
                 if self.single_layer:
                     m = ones_message(n, self.K, self.dtype) if self.init_mode == 0 else \
@@ -506,7 +515,24 @@ class Lattice:
         return ((r + sy) % self.Ly) * self.Lx + ((c + sx) % self.Lx)
 
     def block_origin(self, bi):
-        return (bi // self.nbx) * self.by, (bi % self.nbx) * self.bx
+        R, C = divmod(bi, self.nbx)
+        return self.ys[R], self.xs[C]
+
+    def block_size(self, bi):
+        """(rows, columns) of block bi."""
+        R, C = divmod(bi, self.nbx)
+        return self.ys[R + 1] - self.ys[R], self.xs[C + 1] - self.xs[C]
+
+    def edge_length(self, bi, dr):
+        """Sites along side dr of block bi (the length of a message through it)."""
+        h, w = self.block_size(bi)
+        return h if dr in (LEFT, RIGHT) else w
+
+    def block_of(self, r, c):
+        """Block containing lattice site (r, c) (OBC)."""
+        R = max(i for i in range(self.nby) if self.ys[i] <= r)
+        C = max(i for i in range(self.nbx) if self.xs[i] <= c)
+        return R * self.nbx + C
 
     def neighbour(self, bi, dr):
         """Block on side dr of block bi, or None at an OBC lattice edge."""
@@ -524,11 +550,12 @@ class Lattice:
 
     def block_E(self, bi, ops=None):
         r0, c0 = self.block_origin(bi)
+        h, w = self.block_size(bi)
         ops = ops or {}
         grid = []
-        for r in range(self.by):
+        for r in range(h):
             row = []
-            for c in range(self.bx):
+            for c in range(w):
                 t = self.tensor_index(r0 + r, c0 + c)
                 row.append(self.site_operator(t, ops[(r, c)]) if (r, c) in ops else self.E[t])
             grid.append(row)
@@ -550,7 +577,7 @@ class Lattice:
         out = {}
         for dr in (LEFT, RIGHT, UP, DOWN):
             nb = self.neighbour(bi, dr)
-            n = self.by if dr in (LEFT, RIGHT) else self.bx
+            n = self.edge_length(bi, dr)
             out[dr] = trivial_mps(n, self.dtype) if nb is None else msgs[(nb, OPPOSITE[dr])]
         return out
 
@@ -612,20 +639,22 @@ class Lattice:
         for r, c in rc:
             if not (0 <= r < self.Ly and 0 <= c < self.Lx):
                 raise ValueError("site outside the lattice")
-            blks.append((r // self.by) * self.nbx + (c // self.bx))
+            blks.append(self.block_of(r, c))
         nb = self.nbx * self.nby
         if len(set(blks)) == 1:
             bi = blks[0]
             r0, c0 = self.block_origin(bi)
-            return bi, r0, c0, self.by, self.bx, [bi]
+            h, w = self.block_size(bi)
+            return bi, r0, c0, h, w, [bi]
         (r1, c1), (r2, c2) = rc
         if abs(r1 - r2) + abs(c1 - c2) != 1:
             raise ValueError("two-site term across blocks must be nearest neighbours")
         a, b = sorted(blks)
         r0, c0 = self.block_origin(a)
+        (ha, wa), (hb, wb) = self.block_size(a), self.block_size(b)
         if c1 != c2:  # horizontal pair: a left of b
-            return nb + 2 * a, r0, c0, self.by, 2 * self.bx, [a, b]
-        return nb + 2 * a + 1, r0, c0, 2 * self.by, self.bx, [a, b]
+            return nb + 2 * a, r0, c0, ha, wa + wb, [a, b]
+        return nb + 2 * a + 1, r0, c0, ha + hb, wa, [a, b]
 
     def region_incoming(self, blocks, horizontal):
         """Incoming messages of a block or a merged two-block region.  The two messages
@@ -643,7 +672,8 @@ class Lattice:
         Lenv[c] = left edge absorbed up to column c-1, Renv[c] = right edge absorbed
         down to column c+1."""
         grid = [[self.E[self.tensor_index(r0 + r, c0 + c)] for c in range(w)] for r in range(h)]
-        m_in = self.region_incoming(blocks, horizontal=(w > self.bx))
+        horizontal = len(blocks) == 2 and blocks[0] // self.nbx == blocks[1] // self.nbx
+        m_in = self.region_incoming(blocks, horizontal=horizontal)
         opts = FitOpts(self.chi_exp, self.fit_tol, self.fit_max_sweeps)
         Ef, mT, mR, mB = frame(grid, m_in, LEFT)
         keptR = column_sweep(Ef, mT, mR, mB, opts, self.seed,

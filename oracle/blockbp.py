@@ -51,7 +51,7 @@ _MUL2 = np.uint64(0x94D049BB133111EB)
 
 
 def splitmix64(z):
-    """One SplitMix64 output step applied elementwise to uint64 values."""
+    """One SplitMix64 output step applied elementwise to uint64 values. (The published SplitMix64 step of Steele, Lea & Flood; it stands in for the paper's unspecified random source, App. A, reading 4.)"""
     z = np.asarray(z, dtype=np.uint64)
     with np.errstate(over="ignore"):
         z = z + _GAMMA
@@ -61,7 +61,7 @@ def splitmix64(z):
 
 
 def uniform_pm1(seed: int, stream: int, n: int) -> np.ndarray:
-    """n exact doubles in [-1, 1) from the counter-based generator."""
+    """n exact doubles in [-1, 1) from the counter-based generator. (App. A draws the fit's initial states at random; reading 4.)"""
     key = splitmix64(np.uint64(seed) ^ splitmix64(np.uint64(stream)))
     with np.errstate(over="ignore"):
         z = splitmix64(key + np.arange(n, dtype=np.uint64))
@@ -73,13 +73,14 @@ def stream_id(tag: int, outer: int, msg: int, col: int, site: int) -> int:
 
     tag 0 = message update (outer = BP sweep index, msg = 4*block + direction);
     tag 1 = read-out environment (outer = region id, msg = 0 right env, 1 left env).
+    (Reading 4: one stream per fit-initial site.)
     """
     assert site < 256 and col < 256 and msg < (1 << 20) and outer < (1 << 20) and tag < 256
     return (tag << 56) | (outer << 36) | (msg << 16) | (col << 8) | site
 
 
 def random_site(seed: int, stream: int, shape, dtype) -> np.ndarray:
-    """Fit-initial site tensor: C-order fill; complex entries interleave (re, im)."""
+    """Fit-initial site tensor: C-order fill; complex entries interleave (re, im). (App. A: each fit starts from a random MPS.)"""
     n = int(np.prod(shape))
     if np.issubdtype(dtype, np.complexfloating):
         v = uniform_pm1(seed, stream, 2 * n)
@@ -96,6 +97,7 @@ def double_layer(T: np.ndarray, O: np.ndarray | None = None) -> np.ndarray:
     Contracting the physical legs of ket and bra gives the closed network for
     <psi|psi>; with a local operator O between them it gives <psi|O|psi>.
     O=None means the identity.  Merged leg index = ket * D + bra.
+    (Fig. 1(a,b).)
     """
     d, Du, Dl, Dd, Dr = T.shape
     OT = T if O is None else np.einsum("qp,puldr->quldr", O, T)
@@ -108,7 +110,7 @@ def double_layer(T: np.ndarray, O: np.ndarray | None = None) -> np.ndarray:
 # half sweep, LQ on the right-to-left half sweep; only the orthonormal factor is kept).
 # --------------------------------------------------------------------------------------
 def qr_q(M: np.ndarray) -> np.ndarray:
-    """Thin Q of M (m x n, m >= n) with the diagonal of R made real non-negative."""
+    """Thin Q of M (m x n, m >= n) with the diagonal of R made real non-negative. (App. A: the left-to-right half sweep keeps Q of a QR.)"""
     Q, R = np.linalg.qr(M, mode="reduced")
     dg = np.diag(R)
     ph = np.ones_like(dg)
@@ -118,7 +120,7 @@ def qr_q(M: np.ndarray) -> np.ndarray:
 
 
 def lq_q(M: np.ndarray) -> np.ndarray:
-    """Row-orthonormal Q of M = L Q (m x n, m <= n), diag(L) real non-negative."""
+    """Row-orthonormal Q of M = L Q (m x n, m <= n), diag(L) real non-negative. (App. A: the right-to-left half sweep keeps Q of an LQ.)"""
     return qr_q(np.conj(M.T)).conj().T
 
 
@@ -154,7 +156,7 @@ def env_right(B, Y, O, X):
 
 def bond_caps(phys, chi):
     """Bond dimensions of an n-site MPS with physical dims phys, capped at chi:
-    bond_i = min(chi, prod(phys[:i]), prod(phys[i:])), ends 1."""
+    bond_i = min(chi, prod(phys[:i]), prod(phys[i:])), ends 1. (App. A: the bonds of a boundary MPS are capped at chi.)"""
     n = len(phys)
     b = [1]
     for i in range(1, n):
@@ -221,7 +223,7 @@ def fit_mpo_mps(O, X, opts: FitOpts, init_site, dtype):
 # MPS utilities.
 # --------------------------------------------------------------------------------------
 def mps_overlap(M1, M2):
-    """<M1|M2> for two MPS with equal physical dims (conj on M1)."""
+    """<M1|M2> for two MPS with equal physical dims (conj on M1). (Used for norms and the residual, Sec. "The blockBP algorithm", stop rule.)"""
     t = np.ones((1, 1), dtype=np.result_type(M1[0], M2[0]))
     for a, b in zip(M1, M2):
         t = np.tensordot(t, np.conj(a), axes=([0], [0]))      # [b_, k, c]
@@ -230,12 +232,12 @@ def mps_overlap(M1, M2):
 
 
 def mps_reverse(M):
-    """Mirror an MPS: site order reversed, each site's two bonds swapped."""
+    """Mirror an MPS: site order reversed, each site's two bonds swapped. (Reading 6: frames.)"""
     return [s.transpose(2, 1, 0) for s in reversed(M)]
 
 
 def identity_trace(M, D):
-    """<I|m>: contract every site's merged (ket, bra) leg with delta_{ket,bra}."""
+    """<I|m>: contract every site's merged (ket, bra) leg with delta_{ket,bra}. (Reading 2: the phase reference.)"""
     t = np.ones((1,), dtype=M[0].dtype)
     for s in M:
         a, k, b = s.shape
@@ -247,7 +249,7 @@ def identity_trace(M, D):
 
 def ones_trace(M):
     """<1|m>: contract every site's physical leg with the all-ones vector (the phase
-    reference of a single-layer network, whose legs carry no (ket, bra) pair)."""
+    reference of a single-layer network, whose legs carry no (ket, bra) pair). (Reading 12.)"""
     t = np.ones((1,), dtype=M[0].dtype)
     for s in M:
         t = t @ s.sum(axis=1)
@@ -277,7 +279,7 @@ def normalise_message(M, D, single=False):
 def embed_at_caps(M, chi):
     """The same MPS with every bond zero-padded to the capped dimension
     min(chi, K^i, K^(n-i)): message storage has the shape of a bond-chi message from
-    the start (the state is unchanged)."""
+    the start (the state is unchanged). (Reading 5.)"""
     K = M[0].shape[1]
     caps = bond_caps([K] * len(M), chi)
     out = []
@@ -290,12 +292,12 @@ def embed_at_caps(M, chi):
 
 
 def trivial_mps(n, dtype):
-    """Message from outside an OBC lattice: the scalar 1 on every (dimension-1) leg."""
+    """Message from outside an OBC lattice: the scalar 1 on every (dimension-1) leg. (Sec. "The blockBP algorithm": an OBC lattice is a periodic one with bonds of dimension 1 on the boundary.)"""
     return [np.ones((1, 1, 1), dtype=dtype) for _ in range(n)]
 
 
 def identity_message(n, D, dtype):
-    """Product of delta_{ket,bra} on every site, bond 1 (init mode 0)."""
+    """Product of delta_{ket,bra} on every site, bond 1 (init mode 0). (App. A starts the messages from a chosen state; reading 5.)"""
     v = np.eye(D, dtype=dtype).reshape(1, D * D, 1)
     return [v.copy() for _ in range(n)]
 
@@ -316,7 +318,7 @@ def random_mpdo_message(n, D, seed, stream, dtype):
 
 
 def ones_message(n, K, dtype):
-    """Single-layer network, init mode 0: the all-ones vector on every site, bond 1."""
+    """Single-layer network, init mode 0: the all-ones vector on every site, bond 1. (Reading 11.)"""
     return [np.ones((1, K, 1), dtype=dtype) for _ in range(n)]
 
 
@@ -363,6 +365,7 @@ def column_mpo(Ef, mT, mB, c):
     Horizontal legs run right (input) to left (output); vertical MPO bonds are the
     u/d legs.  Top site: O[1, alpha_{c+1}, alpha_c, v] = mT[c][alpha_c, v, alpha_{c+1}].
     Bottom site: O[v, beta_{c+1}, beta_c, 1] = mB[c][beta_c, v, beta_{c+1}].
+    (App. A: one column of the block is applied as an MPO to the boundary MPS, Fig. 1(c).)
     """
     H = len(Ef)
     O = [mT[c].transpose(2, 0, 1)[None]]
@@ -410,7 +413,7 @@ def column_sweep(Ef, mT, mR, mB, opts: FitOpts, seed, stream_of, dtype, keep=Fal
 
 
 def extract_message(X):
-    """Drop the two corner sites (both 1x1x1 after the last column) into the message."""
+    """Drop the two corner sites (both 1x1x1 after the last column) into the message. (Eq. 1: the outgoing message is what is left after the last column, App. A.)"""
     assert X[0].shape == (1, 1, 1) and X[-1].shape == (1, 1, 1)
     M = [s.copy() for s in X[1:-1]]
     M[0] = M[0] * X[0][0, 0, 0] * X[-1][0, 0, 0]
@@ -464,6 +467,8 @@ class Lattice:
     residuals: list = field(default_factory=list)
 
     def __post_init__(self):
+        """The partition into blocks, the double layers (Fig. 1(a,b)) and the initial messages
+        (App. A; readings 5 and 11)."""
         assert self.boundary in ("obc", "infinite")
         sx, sy = self.shift
         if self.boundary == "obc":
@@ -508,34 +513,35 @@ class Lattice:
 
     # -- geometry ------------------------------------------------------------------
     def tensor_index(self, r, c):
-        """Site (r, c) -> index into tensors (OBC: r*Lx+c; INFINITE: unit cell)."""
+        """Site (r, c) -> index into tensors (OBC: r*Lx+c; INFINITE: unit cell). (Sec. "The blockBP algorithm": partition of the lattice into blocks.)"""
         if self.boundary == "obc":
             return r * self.Lx + c
         sx, sy = self.shift
         return ((r + sy) % self.Ly) * self.Lx + ((c + sx) % self.Lx)
 
     def block_origin(self, bi):
+        """(row, column) of block bi's top-left site (Sec. "The blockBP algorithm")."""
         R, C = divmod(bi, self.nbx)
         return self.ys[R], self.xs[C]
 
     def block_size(self, bi):
-        """(rows, columns) of block bi."""
+        """(rows, columns) of block bi. (Sec. "The blockBP algorithm"; reading 14 for shifted OBC partitions.)"""
         R, C = divmod(bi, self.nbx)
         return self.ys[R + 1] - self.ys[R], self.xs[C + 1] - self.xs[C]
 
     def edge_length(self, bi, dr):
-        """Sites along side dr of block bi (the length of a message through it)."""
+        """Sites along side dr of block bi (the length of a message through it). (Sec. "The blockBP algorithm": a message is an MPS along the shared block edge.)"""
         h, w = self.block_size(bi)
         return h if dr in (LEFT, RIGHT) else w
 
     def block_of(self, r, c):
-        """Block containing lattice site (r, c) (OBC)."""
+        """Block containing lattice site (r, c) (OBC). (Sec. "The blockBP algorithm"; reading 14.)"""
         R = max(i for i in range(self.nby) if self.ys[i] <= r)
         C = max(i for i in range(self.nbx) if self.xs[i] <= c)
         return R * self.nbx + C
 
     def neighbour(self, bi, dr):
-        """Block on side dr of block bi, or None at an OBC lattice edge."""
+        """Block on side dr of block bi, or None at an OBC lattice edge. (Sec. "The blockBP algorithm": the block graph.)"""
         if self.boundary == "infinite":
             return bi
         R, C = divmod(bi, self.nbx)
@@ -545,10 +551,11 @@ class Lattice:
         return None
 
     def directions(self, bi):
-        """Outgoing directions whose receiver exists (interior edges; all four if infinite)."""
+        """Outgoing directions whose receiver exists (interior edges; all four if infinite). (Sec. "The blockBP algorithm".)"""
         return [dr for dr in (LEFT, RIGHT, UP, DOWN) if self.neighbour(bi, dr) is not None]
 
     def block_E(self, bi, ops=None):
+        """Double layers of block bi's sites (Fig. 1(a,b)), E^O at the sites in ops."""
         r0, c0 = self.block_origin(bi)
         h, w = self.block_size(bi)
         ops = ops or {}
@@ -572,7 +579,7 @@ class Lattice:
 
     def incoming(self, bi, msgs=None):
         """Messages into block bi: the neighbour's outgoing message toward bi, or the
-        trivial message at an OBC edge."""
+        trivial message at an OBC edge. (Eq. 1: the messages a block receives; App. A, OBC edges.)"""
         msgs = self.msgs if msgs is None else msgs
         out = {}
         for dr in (LEFT, RIGHT, UP, DOWN):
@@ -594,7 +601,7 @@ class Lattice:
 
     def sweep(self):
         """One synchronous (Jacobi) update of every message; returns the residual
-        r = mean over messages of ||m_new - m_old||^2 = mean(2 - 2 Re<m_new|m_old>)."""
+        r = mean over messages of ||m_new - m_old||^2 = mean(2 - 2 Re<m_new|m_old>). (Eq. 1, synchronous update; residual of reading 2.)"""
         old = self.msgs
         new = {}
         for (bi, dr) in old:
@@ -659,7 +666,7 @@ class Lattice:
     def region_incoming(self, blocks, horizontal):
         """Incoming messages of a block or a merged two-block region.  The two messages
         on a long side of a merged region are joined with a bond of dimension 1, since
-        the blockBP environment has no bond between different blocks' messages."""
+        the blockBP environment has no bond between different blocks' messages. (Reading 7.)"""
         if len(blocks) == 1:
             return self.incoming(blocks[0])
         ia, ib = self.incoming(blocks[0]), self.incoming(blocks[1])
@@ -691,6 +698,7 @@ class Lattice:
         The closing contraction runs exactly from top to bottom through
         Lenv[c] . column c (. column c+1) . Renv[c or c+1], with E^O at the operator
         sites, and the ratio is taken in FP64 / complex128.
+        (App. A read-out, Fig. 1(f).)
         """
         cache = {}
         out = []
@@ -737,7 +745,7 @@ class Lattice:
         return self.expect(terms).reshape(dim, dim)
 
     def _close(self, grid, m_in, Lenv, Renv, r0, c0, cs, loc):
-        """Exact top-to-bottom transfer through Lenv[cs[0]], columns cs, Renv[cs[-1]]."""
+        """Exact top-to-bottom transfer through Lenv[cs[0]], columns cs, Renv[cs[-1]]. (App. A read-out: the exact closing of the region.)"""
         L, R = Lenv[cs[0]], Renv[cs[-1]]
         h = len(grid)
         mT, mB = m_in[UP], m_in[DOWN]

@@ -51,7 +51,7 @@ _MUL2 = np.uint64(0x94D049BB133111EB)
 
 
 def splitmix64(z):
-    """One SplitMix64 output step applied elementwise to uint64 values. (The published SplitMix64 step of Steele, Lea & Flood; it stands in for the paper's unspecified random source, App. A, reading 4.)"""
+    """One SplitMix64 output step applied elementwise to uint64 values. (The published SplitMix64 step of Steele, Lea & Flood: the paper draws the fits' initial states at random without naming a generator, App. A, so both implementations use this counter-based one.)"""
     z = np.asarray(z, dtype=np.uint64)
     with np.errstate(over="ignore"):
         z = z + _GAMMA
@@ -61,7 +61,7 @@ def splitmix64(z):
 
 
 def uniform_pm1(seed: int, stream: int, n: int) -> np.ndarray:
-    """n exact doubles in [-1, 1) from the counter-based generator. (App. A draws the fit's initial states at random; reading 4.)"""
+    """n exact doubles in [-1, 1) from the counter-based generator. (App. A draws the fits' initial states at random; these uniforms are that draw.)"""
     key = splitmix64(np.uint64(seed) ^ splitmix64(np.uint64(stream)))
     with np.errstate(over="ignore"):
         z = splitmix64(key + np.arange(n, dtype=np.uint64))
@@ -73,7 +73,7 @@ def stream_id(tag: int, outer: int, msg: int, col: int, site: int) -> int:
 
     tag 0 = message update (outer = BP sweep index, msg = 4*block + direction);
     tag 1 = read-out environment (outer = region id, msg = 0 right env, 1 left env).
-    (Reading 4: one stream per fit-initial site.)
+    (One stream per fit-initial site, so that every implementation draws the same numbers.)
     """
     assert site < 256 and col < 256 and msg < (1 << 20) and outer < (1 << 20) and tag < 256
     return (tag << 56) | (outer << 36) | (msg << 16) | (col << 8) | site
@@ -232,12 +232,12 @@ def mps_overlap(M1, M2):
 
 
 def mps_reverse(M):
-    """Mirror an MPS: site order reversed, each site's two bonds swapped. (Reading 6: frames.)"""
+    """Mirror an MPS: site order reversed, each site's two bonds swapped. (Used to rotate a block so that every outgoing message is computed as a left message.)"""
     return [s.transpose(2, 1, 0) for s in reversed(M)]
 
 
 def identity_trace(M, D):
-    """<I|m>: contract every site's merged (ket, bra) leg with delta_{ket,bra}. (Reading 2: the phase reference.)"""
+    """<I|m>: contract every site's merged (ket, bra) leg with delta_{ket,bra}. (The phase reference of a message: the paper fixes no phase, and <I|m> is made real positive.)"""
     t = np.ones((1,), dtype=M[0].dtype)
     for s in M:
         a, k, b = s.shape
@@ -249,7 +249,7 @@ def identity_trace(M, D):
 
 def ones_trace(M):
     """<1|m>: contract every site's physical leg with the all-ones vector (the phase
-    reference of a single-layer network, whose legs carry no (ket, bra) pair). (Reading 12.)"""
+    reference of a single-layer network, whose legs carry no (ket, bra) pair)."""
     t = np.ones((1,), dtype=M[0].dtype)
     for s in M:
         t = t @ s.sum(axis=1)
@@ -279,7 +279,7 @@ def normalise_message(M, D, single=False):
 def embed_at_caps(M, chi):
     """The same MPS with every bond zero-padded to the capped dimension
     min(chi, K^i, K^(n-i)): message storage has the shape of a bond-chi message from
-    the start (the state is unchanged). (Reading 5.)"""
+    the start (the state is unchanged)."""
     K = M[0].shape[1]
     caps = bond_caps([K] * len(M), chi)
     out = []
@@ -297,7 +297,7 @@ def trivial_mps(n, dtype):
 
 
 def identity_message(n, D, dtype):
-    """Product of delta_{ket,bra} on every site, bond 1 (init mode 0). (App. A starts the messages from a chosen state; reading 5.)"""
+    """Product of delta_{ket,bra} on every site, bond 1 (init mode 0). (App. A starts the messages from a chosen state.)"""
     v = np.eye(D, dtype=dtype).reshape(1, D * D, 1)
     return [v.copy() for _ in range(n)]
 
@@ -318,7 +318,7 @@ def random_mpdo_message(n, D, seed, stream, dtype):
 
 
 def ones_message(n, K, dtype):
-    """Single-layer network, init mode 0: the all-ones vector on every site, bond 1. (Reading 11.)"""
+    """Single-layer network, init mode 0: the all-ones vector on every site, bond 1. (The deterministic alternative to the uniform random start the paper uses for single-layer messages.)"""
     return [np.ones((1, K, 1), dtype=dtype) for _ in range(n)]
 
 
@@ -468,7 +468,7 @@ class Lattice:
 
     def __post_init__(self):
         """The partition into blocks, the double layers (Fig. 1(a,b)) and the initial messages
-        (App. A; readings 5 and 11)."""
+        (App. A)."""
         assert self.boundary in ("obc", "infinite")
         sx, sy = self.shift
         if self.boundary == "obc":
@@ -525,7 +525,7 @@ class Lattice:
         return self.ys[R], self.xs[C]
 
     def block_size(self, bi):
-        """(rows, columns) of block bi. (Sec. "The blockBP algorithm"; reading 14 for shifted OBC partitions.)"""
+        """(rows, columns) of block bi. (Sec. "The blockBP algorithm"; a shifted OBC partition has narrower blocks on the lattice edges.)"""
         R, C = divmod(bi, self.nbx)
         return self.ys[R + 1] - self.ys[R], self.xs[C + 1] - self.xs[C]
 
@@ -535,7 +535,7 @@ class Lattice:
         return h if dr in (LEFT, RIGHT) else w
 
     def block_of(self, r, c):
-        """Block containing lattice site (r, c) (OBC). (Sec. "The blockBP algorithm"; reading 14.)"""
+        """Block containing lattice site (r, c) (OBC). (Sec. "The blockBP algorithm".)"""
         R = max(i for i in range(self.nby) if self.ys[i] <= r)
         C = max(i for i in range(self.nbx) if self.xs[i] <= c)
         return R * self.nbx + C
@@ -601,7 +601,7 @@ class Lattice:
 
     def sweep(self):
         """One synchronous (Jacobi) update of every message; returns the residual
-        r = mean over messages of ||m_new - m_old||^2 = mean(2 - 2 Re<m_new|m_old>). (Eq. 1, synchronous update; residual of reading 2.)"""
+        r = mean over messages of ||m_new - m_old||^2 = mean(2 - 2 Re<m_new|m_old>). (Eq. 1, synchronous update; the residual is the mean squared distance of the unit-norm, phase-fixed messages.)"""
         old = self.msgs
         new = {}
         for (bi, dr) in old:
@@ -666,7 +666,7 @@ class Lattice:
     def region_incoming(self, blocks, horizontal):
         """Incoming messages of a block or a merged two-block region.  The two messages
         on a long side of a merged region are joined with a bond of dimension 1, since
-        the blockBP environment has no bond between different blocks' messages. (Reading 7.)"""
+        the blockBP environment has no bond between different blocks' messages."""
         if len(blocks) == 1:
             return self.incoming(blocks[0])
         ia, ib = self.incoming(blocks[0]), self.incoming(blocks[1])

@@ -54,8 +54,16 @@ typedef enum { BBP_F64 = 0, BBP_C128 = 1, BBP_F32 = 2, BBP_C64 = 3 } bbp_dtype;
  * the QR/LQ truncation, message normalisation, residual and read-out ratios stay FP64.
  * TF32X3: as TF32, but every operand is split into a TF32 high part and a TF32 low part
  * (the rounding remainder) and each product is A_hi B_hi + A_lo B_hi + A_hi B_lo, all in
- * one FP32 accumulator: FP32-level contraction accuracy at three times the MMA work. */
-typedef enum { BBP_PREC_FP64 = 0, BBP_PREC_TF32 = 1, BBP_PREC_BF16 = 2, BBP_PREC_TF32X3 = 3 } bbp_prec;
+ * one FP32 accumulator: FP32-level contraction accuracy at three times the MMA work.
+ * BF16X3: the same split with BF16 parts (hi = bf16(x), lo = bf16(x - hi)): operands carry
+ * 16 significant bits, at three BF16 MMAs per product (1.5 times the TF32 MMA time). */
+typedef enum {
+    BBP_PREC_FP64 = 0,
+    BBP_PREC_TF32 = 1,
+    BBP_PREC_BF16 = 2,
+    BBP_PREC_TF32X3 = 3,
+    BBP_PREC_BF16X3 = 4
+} bbp_prec;
 
 typedef struct {
     int Lx, Ly;              /* OBC: lattice columns, rows.  INFINITE: unit cell columns, rows */
@@ -73,8 +81,9 @@ typedef struct {
     int max_sweeps;          /* cap on sweeps when running to tolerance (10) */
     int stop_relative;       /* 0: residual < tol (main text); 1: r_l / r_1 < tol (App. A) */
     double fit_tol;          /* zip-up fit: std/|mean| of -||Yt||^2 over a sweep (App. A: 1e-6);
-                                on the TF32 / BF16 paths at least 3e-3 / 3e-2, the noise of a
-                                loss computed in that precision */
+                                on the TF32 / BF16 / BF16X3 paths at least 3e-3 / 3e-2 / 3e-5,
+                                the noise of a loss computed in that precision (TF32X3 and
+                                FP64: as given) */
     int fit_max_sweeps;      /* zip-up fit sweep cap (App. A: 10) */
     unsigned long long seed; /* counter-based generator key (fit initial states, init_mode 1) */
     int init_mode;           /* 0: identity-product messages; 1: random MPDO (App. A) */
@@ -113,12 +122,17 @@ typedef struct {
                                 site (r, c) is lattice site (r + shift_y, c + shift_x); the
                                 paper covers every bond from a block centre by such shifted
                                 partitions (Sec. "The blockBP algorithm"). */
+    int launch_mode;         /* 0: each sweep is one CUDA graph whose fit loops are conditional
+                                nodes that stop when the fits have met the stop rule; 1: the
+                                same kernels launched one by one on the stream, each fit loop
+                                run to fit_max_sweeps with the converged fits skipped (same
+                                results; lets a kernel profiler see every launch) */
 } bbp_lattice_desc;
 
 /* Validate desc, allocate the device arena (double layer, message store, work
  * buffers) and plan one sweep.  *out receives the handle.  Limits checked here:
  * Lx, Ly <= 4096; bx, by <= 16; D <= 16; d <= 64; 1 <= fit_max_sweeps <= 64;
- * init_mode, warm_start, hermitian_basis and single_layer 0 or 1; 0 <= shift_x < Lx and
+ * init_mode, warm_start, hermitian_basis, single_layer and launch_mode 0 or 1; 0 <= shift_x < Lx and
  * 0 <= shift_y < Ly on infinite lattices, both 0 with OBC.  Errors: INVALID, OOM, CUDA. */
 int bbp_create_lattice(const bbp_lattice_desc* desc, bbp_lattice** out);
 
@@ -219,16 +233,22 @@ int bbp_qr_batched(int batch, int m, int n, int complex_values, const double* A,
  *   - Allocates nothing: no cudaMalloc / cudaFree / allocating library call.  The
  *     workspace is a fixed device array of BBP_QR_NOALLOC_SCRATCH_BYTES (16 MiB),
  *     held by every GPU that loads the library until the process exits.
- *   - Needs batch * (2*m*n scalars) plus 256 bytes per 2 matrices of descriptors to
- *     fit in that array; larger requests fail with BBP_ERR_INVALID.
- *   - The first call on a device resolves the array's device address and sets the
- *     kernel's shared-memory limit (cudaGetSymbolAddress, cudaFuncSetAttribute);
- *     make that first call before any stream capture.
+ *   - A request needs round_up(batch * 144, 256) bytes of task descriptors plus
+ *     batch * 2*m*n scalars (8 bytes real, 16 complex) of that array; larger requests
+ *     fail with BBP_ERR_INVALID.
+ *   - The first call on a device resolves the array's device address
+ *     (cudaGetSymbolAddress; with CUDA's lazy module loading this is also when the
+ *     library's module is loaded on that device and the 16 MiB are committed) and sets
+ *     the QR kernels' shared-memory limits for real and complex matrices of up to 512
+ *     rows (cudaFuncSetAttribute).  Make that first call at start-up, before the caller
+ *     reserves the rest of the GPU and before any stream capture; if the array cannot
+ *     be committed it returns BBP_ERR_OOM.  First calls from several host threads are
+ *     serialised.  Later calls with m > 512 raise the limit again.
  *   - Asynchronous: returns once the work is queued on `stream`.  All calls share the
  *     array, so calls whose work overlaps on the GPU (different streams, or different
  *     host threads) race on it; serialise them.  Nothing in the array needs to start
  *     at zero: every call writes all of the workspace it reads.
- * Same arguments, layout and results as bbp_qr_batched.  Errors: INVALID, CUDA. */
+ * Same arguments, layout and results as bbp_qr_batched.  Errors: INVALID, OOM, CUDA. */
 #define BBP_QR_NOALLOC_SCRATCH_BYTES (16u << 20)
 int bbp_qr_batched_noalloc(int batch, int m, int n, int complex_values, const double* A, double* Q, double* loss,
                            void* stream);
@@ -258,6 +278,23 @@ int bbp_get_stats(bbp_lattice* lat, bbp_stats* out);
  * FP32 on the host; prec is BBP_PREC_TF32 or BBP_PREC_BF16 (operands rounded to it).
  * Errors: INVALID, CUDA, TIMEOUT (a pipeline wait hit its bound). */
 int bbp_selftest_gemm(int M, int N, int K, int prec, const float* A, const float* B, float* C);
+
+/* Not a step of the method: the self-test of the bounded pipeline waits (a device wait
+ * that must end with a status, never hang).  Launches a small tensor-core GEMM whose
+ * operand copies are withheld, so that the first wait on a loaded stage can never succeed:
+ * it gives up after its poll bound (well under a second), raises the error word, the CTAs
+ * release their tensor memory and return, and the call returns BBP_ERR_TIMEOUT with the
+ * context still usable.  Any other result means the bound did not work.  Errors: CUDA. */
+int bbp_selftest_gemm_timeout(void);
+
+/* Not a step of the method: the self-test of the FP64 scalars of the cluster QR (Householder
+ * step, App. A truncation), whose 1/sqrt(s) and 1/d are FP32 seeds refined by one
+ * third-order iteration (Householder's for s^(-1/2), Newton-Raphson's for 1/d).  For the n
+ * host values x[i] in [2^-100, 2^100] it writes those refined values and CUDA's own
+ * 1.0 / sqrt(x) and 1.0 / x, all computed on the device.  Errors: INVALID (x out of range),
+ * OOM, CUDA. */
+int bbp_selftest_scalar(long long n, const double* x, double* rsqrt_ours, double* rcp_ours, double* rsqrt_cuda,
+                        double* rcp_cuda);
 
 /* Kernel-class timing of one planned sweep, for roofline measurements: replays, on
  * the handle's stream and bracketed by CUDA events, only the launches of one class

@@ -105,6 +105,52 @@ def double_layer(T: np.ndarray, O: np.ndarray | None = None) -> np.ndarray:
     return E.reshape(Du * Du, Dl * Dl, Dd * Dd, Dr * Dr)
 
 
+def hermitian_basis_matrix(D: int) -> np.ndarray:
+    """Unitary V on a merged (ket a, bra b) leg, k = a * D + b, whose rows give the coordinates
+    v_(a,a) at k = a*D+a, (v_(a,b) + v_(b,a)) / sqrt 2 at k = a*D+b for a < b, and
+    (v_(b,a) - v_(a,b)) / (i sqrt 2) at k = a*D+b for a > b.
+
+    Not a step of the paper: a fixed change of basis on every leg of the double layer
+    (Fig. 1(b)) in which a vector that is Hermitian under the swap of ket and bra has real
+    coordinates.  Up and left legs take V, down and right legs conj(V), so that every bond
+    contracts through V^T conj(V) = I and each contraction keeps its value."""
+    V = np.zeros((D * D, D * D), dtype=np.complex128)
+    h = 1.0 / math.sqrt(2.0)
+    for a in range(D):
+        for b in range(D):
+            k, kt = a * D + b, b * D + a
+            if a == b:
+                V[k, k] = 1.0
+            elif a < b:
+                V[k, k] = h
+                V[k, kt] = h
+            else:
+                V[k, kt] = h / 1j
+                V[k, k] = -h / 1j
+    return V
+
+
+def to_hermitian_basis_E(E: np.ndarray, Dims) -> np.ndarray:
+    """E[u, l, d, r] with V on the up and left legs and conj(V) on the down and right legs
+    (the double layer in the Hermitian basis; real when E is Hermitian under the joint swap
+    of ket and bra on all legs)."""
+    Du, Dl, Dd, Dr = Dims
+    Vs = [hermitian_basis_matrix(Du), hermitian_basis_matrix(Dl),
+          np.conj(hermitian_basis_matrix(Dd)), np.conj(hermitian_basis_matrix(Dr))]
+    out = np.asarray(E, dtype=np.complex128)
+    for leg, V in enumerate(Vs):  # one leg at a time: out[..., K, ...] = sum_k V[K, k] out[..., k, ...]
+        out = np.moveaxis(np.tensordot(V, out, axes=([1], [leg])), 0, leg)
+    return out
+
+
+def to_hermitian_basis_mps(M, D: int, conj_basis: bool):
+    """Message sites [a, k, b] with V (conj(V) when conj_basis) on every physical leg."""
+    V = hermitian_basis_matrix(D)
+    if conj_basis:
+        V = np.conj(V)
+    return [np.einsum("Kk,akb->aKb", V, s) for s in M]
+
+
 # --------------------------------------------------------------------------------------
 # Orthonormal factors with diag(R) real and >= 0 (App. A, QR on the left-to-right
 # half sweep, LQ on the right-to-left half sweep; only the orthonormal factor is kept).
@@ -374,7 +420,7 @@ def column_mpo(Ef, mT, mB, c):
     return O
 
 
-def column_sweep(Ef, mT, mR, mB, opts: FitOpts, seed, stream_of, dtype, keep=False, warm=None):
+def column_sweep(Ef, mT, mR, mB, opts: FitOpts, seed, stream_of, dtype, keep=False, warm=None, counts=None):
     """bMPS contraction of a block (frame) with its incoming messages (App. A, Fig. 1(d)).
 
     X starts as [1, mR, 1] (corner sites of dimension 1), then every column from the
@@ -385,6 +431,7 @@ def column_sweep(Ef, mT, mR, mB, opts: FitOpts, seed, stream_of, dtype, keep=Fal
     warm (optional dict c -> site list): start column c's fit from that MPS instead of
     the random state (warm start from the previous sweep's fit of the same column);
     it is updated in place with every column's fitted MPS.
+    counts (optional list): receives the number of fit sweeps each column's fit ran.
     Returns (list of column MPS after absorbing columns >= c, indexed by c) if keep,
     else the final column MPS.
     """
@@ -400,7 +447,9 @@ def column_sweep(Ef, mT, mR, mB, opts: FitOpts, seed, stream_of, dtype, keep=Fal
                                                    else random_site(seed, stream_of(c, i), shp, dtype))
         else:
             init = lambda i, shp: random_site(seed, stream_of(c, i), shp, dtype)
-        Y, _ = fit_mpo_mps(O, X, opts, init, dtype)
+        Y, hist = fit_mpo_mps(O, X, opts, init, dtype)
+        if counts is not None:
+            counts.append(len(hist))
         nrm = float(np.linalg.norm(Y[0]))
         if not np.isfinite(nrm) or nrm == 0.0:
             raise FloatingPointError("column MPS vanished")
@@ -443,6 +492,14 @@ class Lattice:
     bond D on every leg (d = 1, real; a 2D classical model's partition function, Sec.
     on the 2D Ising model), used as they are instead of a double layer; a term's
     "operator" at a site is then the impurity tensor that replaces E there.
+    hermitian_basis: run the whole method after the fixed unitary change of basis of
+    hermitian_basis_matrix on every merged leg (not a step of the paper; the basis in which
+    the double layer and the messages of a complex PEPS are real).  Every contraction keeps
+    its value, so only the arithmetic changes: real E, real messages and real fits (drawn as
+    real numbers); E^O of a read-out term is that of the complex double layer, transformed.
+    fit_sweeps: per message sweep, the number of fit sweeps every column fit ran (App. A stop
+    rule), summed over the messages.
+    readout_fit_tol: the fit tolerance of the read-out's environment fits (None: fit_tol).
     """
     Lx: int
     Ly: int
@@ -461,10 +518,13 @@ class Lattice:
     warm_start: bool = False
     single_layer: bool = False
     shift: tuple = (0, 0)
+    hermitian_basis: bool = False
+    readout_fit_tol: float | None = None
     msgs: dict = field(default_factory=dict)
     warm: dict = field(default_factory=dict)
     sweeps_done: int = 0
     residuals: list = field(default_factory=list)
+    fit_sweeps: list = field(default_factory=list)
 
     def __post_init__(self):
         """The partition into blocks, the double layers (Fig. 1(a,b)) and the initial messages
@@ -491,6 +551,8 @@ class Lattice:
             self.chi_exp = max(self.chi, 2 * self.K + 10)
         cplx = any(np.iscomplexobj(t) for t in self.tensors)
         self.dtype = np.complex128 if cplx else np.float64
+        hb = self.hermitian_basis
+        assert not (hb and self.single_layer), "a single-layer network has no (ket, bra) legs"
         if self.single_layer:
             assert self.d == 1 and not cplx, "a single-layer network is real and has no physical leg"
             self.tensors = [np.asarray(t, dtype=np.float64).reshape(np.shape(t)[-4:]) for t in self.tensors]
@@ -498,6 +560,10 @@ class Lattice:
         else:
             self.tensors = [np.asarray(t, dtype=self.dtype) for t in self.tensors]
             self.E = [double_layer(t) for t in self.tensors]
+        if hb:
+            self.E = [np.ascontiguousarray(to_hermitian_basis_E(e, t.shape[1:]).real)
+                      for e, t in zip(self.E, self.tensors)]
+            self.dtype = np.float64
         for bi in range(self.nbx * self.nby):
             for dr in self.directions(bi):
                 n = self.edge_length(bi, dr)
@@ -509,6 +575,11 @@ class Lattice:
                     m = identity_message(n, self.D, self.dtype)
                 else:
                     m = random_mpdo_message(n, self.D, self.seed, stream, self.dtype)
+                if hb:
+                    # a message carries the legs of the side it leaves through: right and down
+                    # legs are in the conj(V) basis
+                    m = [np.ascontiguousarray(x.real) for x in
+                         to_hermitian_basis_mps(m, self.D, conj_basis=dr in (RIGHT, DOWN))]
                 self.msgs[(bi, dr)] = embed_at_caps(normalise_message(m, self.D, self.single_layer), self.chi)
 
     # -- geometry ------------------------------------------------------------------
@@ -575,7 +646,10 @@ class Lattice:
             op = np.asarray(op, dtype=np.float64)
             assert op.shape == self.E[t].shape, "an impurity tensor has the shape of the site tensor it replaces"
             return op
-        return double_layer(self.tensors[t], op)
+        EO = double_layer(self.tensors[t], op)
+        if self.hermitian_basis:
+            EO = to_hermitian_basis_E(EO, self.tensors[t].shape[1:])
+        return EO
 
     def incoming(self, bi, msgs=None):
         """Messages into block bi: the neighbour's outgoing message toward bi, or the
@@ -589,14 +663,14 @@ class Lattice:
         return out
 
     # -- Eq. 1 -----------------------------------------------------------------------
-    def compute_message(self, bi, dr, msgs, sweep_index):
+    def compute_message(self, bi, dr, msgs, sweep_index, counts=None):
         """m_{A->B}^{(l+1)} = Tr(T_A prod_{A' in N_A minus B} m_{A'->A}^{(l)}) (Eq. 1)."""
         Ef, mT, mR, mB = frame(self.block_E(bi), self.incoming(bi, msgs), dr)
         opts = FitOpts(self.chi, self.fit_tol, self.fit_max_sweeps)
         msg = 4 * bi + dr
         warm = self.warm.setdefault((bi, dr), {}) if self.warm_start else None
         X = column_sweep(Ef, mT, mR, mB, opts, self.seed,
-                         lambda c, i: stream_id(0, sweep_index, msg, c, i), self.dtype, warm=warm)
+                         lambda c, i: stream_id(0, sweep_index, msg, c, i), self.dtype, warm=warm, counts=counts)
         return normalise_message(extract_message(X), self.D, self.single_layer)
 
     def sweep(self):
@@ -604,8 +678,10 @@ class Lattice:
         r = mean over messages of ||m_new - m_old||^2 = mean(2 - 2 Re<m_new|m_old>). (Eq. 1, synchronous update; the residual is the mean squared distance of the unit-norm, phase-fixed messages.)"""
         old = self.msgs
         new = {}
+        counts = []
         for (bi, dr) in old:
-            new[(bi, dr)] = self.compute_message(bi, dr, old, self.sweeps_done)
+            new[(bi, dr)] = self.compute_message(bi, dr, old, self.sweeps_done, counts)
+        self.fit_sweeps.append(int(sum(counts)))
         res = float(np.mean([2.0 - 2.0 * mps_overlap(new[k], old[k]).real for k in old])) if old else 0.0
         self.msgs = new
         self.sweeps_done += 1
@@ -681,7 +757,8 @@ class Lattice:
         grid = [[self.E[self.tensor_index(r0 + r, c0 + c)] for c in range(w)] for r in range(h)]
         horizontal = len(blocks) == 2 and blocks[0] // self.nbx == blocks[1] // self.nbx
         m_in = self.region_incoming(blocks, horizontal=horizontal)
-        opts = FitOpts(self.chi_exp, self.fit_tol, self.fit_max_sweeps)
+        tol = self.fit_tol if self.readout_fit_tol is None else self.readout_fit_tol
+        opts = FitOpts(self.chi_exp, tol, self.fit_max_sweeps)
         Ef, mT, mR, mB = frame(grid, m_in, LEFT)
         keptR = column_sweep(Ef, mT, mR, mB, opts, self.seed,
                              lambda c, i: stream_id(1, rid, 0, c, i), self.dtype, keep=True)

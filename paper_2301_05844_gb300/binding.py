@@ -18,11 +18,11 @@ OK, NOT_CONVERGED = 0, 1
 ERR_INVALID, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_NUMERIC, ERR_STATE = -1, -2, -3, -4, -5, -6
 OBC, INFINITE = 0, 1
 F64, C128, F32, C64 = 0, 1, 2, 3
-PREC_FP64, PREC_TF32, PREC_BF16, PREC_TF32X3 = 0, 1, 2, 3
+PREC_FP64, PREC_TF32, PREC_BF16, PREC_TF32X3, PREC_BF16X3 = 0, 1, 2, 3, 4
 LEFT, RIGHT, UP, DOWN = 0, 1, 2, 3
 
 _NP_DTYPE = {F64: np.float64, C128: np.complex128, F32: np.float32, C64: np.complex64}
-_PREC = {"fp64": PREC_FP64, "tf32": PREC_TF32, "bf16": PREC_BF16, "tf32x3": PREC_TF32X3}
+_PREC = {"fp64": PREC_FP64, "tf32": PREC_TF32, "bf16": PREC_BF16, "tf32x3": PREC_TF32X3, "bf16x3": PREC_BF16X3}
 
 
 class Desc(C.Structure):
@@ -33,7 +33,7 @@ class Desc(C.Structure):
         ("stop_relative", C.c_int), ("fit_tol", C.c_double), ("fit_max_sweeps", C.c_int),
         ("seed", C.c_ulonglong), ("init_mode", C.c_int), ("warm_start", C.c_int),
         ("hermitian_basis", C.c_int), ("stream", C.c_void_p), ("single_layer", C.c_int),
-        ("shift_x", C.c_int), ("shift_y", C.c_int),
+        ("shift_x", C.c_int), ("shift_y", C.c_int), ("launch_mode", C.c_int),
     ]
 
 
@@ -111,11 +111,11 @@ def _check(rc):
 
 def make_desc(Lx, Ly, d, D, bx, by, chi, boundary="obc", chi_exp=0, dtype=F64, prec="fp64", tol=1e-5,
               max_sweeps=10, stop_relative=0, fit_tol=1e-6, fit_max_sweeps=10, seed=0, init_mode=0, warm_start=0,
-              hermitian_basis=0, stream=None, single_layer=0, shift=(0, 0)):
+              hermitian_basis=0, stream=None, single_layer=0, shift=(0, 0), launch_mode=0):
     return Desc(Lx, Ly, OBC if boundary == "obc" else INFINITE, d, D, bx, by, chi, chi_exp, dtype,
                 _PREC[prec] if isinstance(prec, str) else prec, tol, max_sweeps, stop_relative, fit_tol,
                 fit_max_sweeps, seed, init_mode, int(warm_start), int(hermitian_basis), stream, int(single_layer),
-                int(shift[0]), int(shift[1]))
+                int(shift[0]), int(shift[1]), int(launch_mode))
 
 
 def _term_array(terms):

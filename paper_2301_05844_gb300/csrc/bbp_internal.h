@@ -154,6 +154,34 @@ struct FuseTask {
     long long b_u, b_l, b_d, b_r;
 };
 
+// Initial state of one message (App. A: messages start from a chosen state): bond-1 sites,
+// each a K-vector written at element [0][k][0] of its slot (k * kstride from dst), the slots
+// zero beforehand.  mode 0: the product of delta_{ket,bra} (the all-ones product on a
+// single-layer network); mode 1: a random positive MPDO G G^T per site, G with normal entries
+// (Box-Muller on the counter-based uniforms; positive uniform entries on a single-layer
+// network).  The first site is divided by the product of the site norms (unit 2-norm).
+struct MsgInitTask {
+    double* dst[16];
+    long long kstride[16];
+    int nsites, K, D, mode;
+    int single;             // single-layer network
+    int hb;                 // Hermitian-basis coordinates
+    int cw;                 // doubles per scalar (2: complex storage, imaginary part left 0)
+    int pad;
+    unsigned long long seed, stream;  // generator key and the stream of site 0 (site s: stream + s)
+};
+
+// One read-out ratio (App. A read-out): <O> = (sum_k c_k N_k) / N_I, N_k and N_I closed
+// networks (results of the read-out's closings, complex if the lattice is), c_k the complex
+// coefficients of the operator's parts (O = H + i A in the Hermitian basis).
+struct RatioTask {
+    int nparts;     // 1..4
+    int part[4];    // closing index of each part
+    int denom;      // closing index of N_I
+    int pad[2];
+    double c_re[4], c_im[4];
+};
+
 // Launchers (kernels.cu).  cplx selects double2 (complex) over double.
 // small != 0: 16x16 output tiles, one output per thread (steps whose outputs have a
 // dimension of at most 16); max_tiles counts tiles of the chosen size.
@@ -183,6 +211,15 @@ cudaError_t launch_convert(const void* in, int in_dtype, void* out, long long n,
 cudaError_t launch_copy(const void* in, void* out, long long bytes, cudaStream_t s);
 cudaError_t launch_fuse(const FuseTask* d_tasks, int ntasks, long long max_out, bool cplx, cudaStream_t s);
 cudaError_t launch_relayout(const RelayoutTask* d_tasks, int ntasks, long long max_elems, cudaStream_t s);
+cudaError_t launch_msg_init(const MsgInitTask* d_tasks, int ntasks, cudaStream_t s);
+// out[2t], out[2t+1] = Re, Im of task t's ratio; *status = 1 where a denominator vanishes
+cudaError_t launch_ratio(const RatioTask* d_tasks, int ntasks, const void* closings, bool cplx, double* out,
+                         int* status, cudaStream_t s);
+
+// Self-test of the QR's refined scalars: for x[i] in [2^-100, 2^100], the refined 1/sqrt(x)
+// and 1/x that the cluster QR uses, and CUDA's 1.0 / sqrt(x) and 1.0 / x (device buffers).
+cudaError_t launch_scalar_selftest(const double* x, long long n, double* rsqrt_ours, double* rcp_ours,
+                                   double* rsqrt_cuda, double* rcp_cuda, cudaStream_t s);
 
 // Host-side SplitMix64 (same definition as the device one) for host-drawn values.
 uint64_t splitmix64(uint64_t z);

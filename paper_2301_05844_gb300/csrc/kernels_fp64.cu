@@ -137,16 +137,26 @@ __device__ __forceinline__ void store_kind(void* p, long long i, int kind, doubl
     store_kind(p, 2 * i, kind, v.x);
     store_kind(p, 2 * i + 1, kind, v.y);
 }
-// Split TF32 operand (x3 != 0, kind 4): hi = tf32(v), lo = tf32(v - hi) written to the three
-// K-segments of the row, kseg elements apart: [hi|lo|hi] for an A operand (x3 = 1),
-// [hi|hi|lo] for a B operand (x3 = 2), so that a GEMM over 3K forms
-// A_hi B_hi + A_lo B_hi + A_hi B_lo.
+// Split operand (x3 != 0; kind 4 TF32, kind 3 BF16): hi = r(v), lo = r(v - hi), r the rounding
+// of the kind applied to the FP32 rounding of v, written to the three K-segments of the row,
+// kseg elements apart: [hi|lo|hi] for an A operand (x3 = 1), [hi|hi|lo] for a B operand
+// (x3 = 2), so that a GEMM over 3K forms A_hi B_hi + A_lo B_hi + A_hi B_lo.
 __device__ __forceinline__ void store_split(void* p, long long i, int kind, double v, int x3, long long kseg) {
     if (!x3) {
         store_kind(p, i, kind, v);
         return;
     }
-    const float f32 = (float)v, hi = tf32_round(f32), lo = tf32_round(f32 - hi);  // f32 - hi is exact
+    const float f32 = (float)v;
+    if (kind == 3) {
+        const __nv_bfloat16 hb = __float2bfloat16_rn(f32);
+        const __nv_bfloat16 lb = __float2bfloat16_rn(f32 - __bfloat162float(hb));  // f32 - hi is exact
+        __nv_bfloat16* b = (__nv_bfloat16*)p;
+        b[i] = hb;
+        b[i + kseg] = x3 == 1 ? lb : hb;
+        b[i + 2 * kseg] = x3 == 1 ? hb : lb;
+        return;
+    }
+    const float hi = tf32_round(f32), lo = tf32_round(f32 - hi);  // f32 - hi is exact
     float* f = (float*)p;
     f[i] = hi;
     f[i + kseg] = x3 == 1 ? lo : hi;
@@ -539,6 +549,24 @@ __device__ __forceinline__ double rcp_refined(double d) {
     return fma(r, fma(e, e, e), r);
 }
 
+__global__ void k_scalar_selftest(const double* __restrict__ x, long long n, double* rs, double* rc, double* rs_ref,
+                                  double* rc_ref) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const double v = x[i];
+        rs[i] = rsqrt_refined(v);
+        rc[i] = rcp_refined(v);
+        rs_ref[i] = 1.0 / sqrt(v);
+        rc_ref[i] = 1.0 / v;
+    }
+}
+cudaError_t launch_scalar_selftest(const double* x, long long n, double* rsqrt_ours, double* rcp_ours,
+                                   double* rsqrt_cuda, double* rcp_cuda, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    const long long b = std::min<long long>((n + 255) / 256, 1024);
+    k_scalar_selftest<<<(unsigned)b, 256, 0, s>>>(x, n, rsqrt_ours, rcp_ours, rsqrt_cuda, rcp_cuda);
+    return cudaGetLastError();
+}
+
 // One warp: c <- c - tau v (v^H c) on rows >= j for c1 and, if c2 != nullptr, c2 (v may live
 // in another CTA's shared memory).  A call is bound by the latency of its dependent FP64
 // operations (each fed from shared memory), not by FP64 throughput, so a second column rides
@@ -841,10 +869,16 @@ static size_t qr_smem_bytes(int max_m, long long max_mn, bool cplx, int* residen
 cudaError_t qr_prepare(int max_m, bool cplx) {
     static std::mutex mu;  // the request server reads out on a second thread
     std::lock_guard<std::mutex> guard(mu);
-    // the limit only ever grows, so that a smaller request cannot break a larger user;
-    // it covers the shared-memory-resident form up to QR_SMEM_LIMIT as well
-    static size_t limit[2] = {0, 0};
-    static bool cluster_set[2] = {false, false};
+    // A kernel attribute applies to the current device only, so the state is kept per device.
+    // The limit only ever grows, so that a smaller request cannot break a larger user; it
+    // covers the shared-memory-resident form up to QR_SMEM_LIMIT as well.
+    constexpr int kMaxDev = 64;
+    static size_t limits[kMaxDev][2] = {};
+    static bool cluster_sets[kMaxDev][2] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) return cudaErrorInvalidDevice;
+    size_t* limit = limits[dev];
+    bool* cluster_set = cluster_sets[dev];
     if (!cluster_set[cplx ? 1 : 0]) {
         cudaError_t e = cplx ? cudaFuncSetAttribute(k_qr_cluster<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                     (int)QR_CLUSTER_SMEM)
@@ -1218,6 +1252,96 @@ cudaError_t launch_double_layer_hb(const DLTask* d_tasks, int ntasks, long long 
     if (bx > 4096) bx = 4096;
     dim3 grid((unsigned)bx, ntasks);
     k_double_layer_hb<<<grid, 256, 0, s>>>(d_tasks);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- initial messages
+// One thread per message (a handful of sites of at most 256 entries each).
+__device__ double init_entry(const MsgInitTask& t, uint64_t key, int k) {
+    const int D = t.D;
+    if (t.single) return t.mode == 0 ? 1.0 : (u_pm1(key, (uint64_t)k) + 1.0) * 0.5;
+    const int a = k / D, b = k - a * D;
+    if (t.mode == 0) return a == b ? 1.0 : 0.0;
+    // site = G G^T with G[i][j] = sqrt(-2 log(1 - u1)) cos(2 pi u2), u1, u2 uniform in [0, 1)
+    auto g = [&](int i, int j) {
+        const uint64_t jj = (uint64_t)(i * D + j);
+        const double u1 = (u_pm1(key, 2 * jj) + 1.0) * 0.5, u2 = (u_pm1(key, 2 * jj + 1) + 1.0) * 0.5;
+        return sqrt(-2.0 * log1p(-u1)) * cos(2.0 * 3.141592653589793 * u2);
+    };
+    auto ggt = [&](int x, int y) {
+        double acc = 0.0;
+        for (int j = 0; j < D; ++j) acc += g(x, j) * g(y, j);
+        return acc;
+    };
+    if (!t.hb) return ggt(a, b);
+    // G G^T is real symmetric: Hermitian-basis coordinates v_aa, (v_ab + v_ba) / sqrt 2 for a < b,
+    // 0 for a > b
+    if (a == b) return ggt(a, a);
+    if (a > b) return 0.0;
+    return (ggt(a, b) + ggt(b, a)) / sqrt(2.0);
+}
+__global__ void k_msg_init(const MsgInitTask* __restrict__ tasks, int ntasks) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ntasks) return;
+    const MsgInitTask& t = tasks[i];
+    double total = 1.0;
+    for (int s = 0; s < t.nsites; ++s) {
+        const uint64_t key = rng_key(t.seed, t.stream + (uint64_t)s);
+        double n2 = 0.0;
+        for (int k = 0; k < t.K; ++k) {
+            const double v = init_entry(t, key, k);
+            n2 += v * v;
+            t.dst[s][(long long)k * t.kstride[s] * t.cw] = v;
+        }
+        total *= sqrt(n2);
+    }
+    for (int k = 0; k < t.K; ++k) {
+        double* p = t.dst[0] + (long long)k * t.kstride[0] * t.cw;
+        *p = *p / total;
+    }
+}
+cudaError_t launch_msg_init(const MsgInitTask* d_tasks, int ntasks, cudaStream_t s) {
+    if (ntasks <= 0) return cudaSuccess;
+    k_msg_init<<<(ntasks + 63) / 64, 64, 0, s>>>(d_tasks, ntasks);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- read-out ratios
+// <O> = N_O / N_I in FP64 (App. A read-out), the complex quotient by Smith's algorithm
+// (R. L. Smith, CACM 1962: scale by the larger part of the divisor, no intermediate overflow).
+__global__ void k_ratio(const RatioTask* __restrict__ tasks, int ntasks, const double* __restrict__ clos, int cplx,
+                        double* __restrict__ out, int* status) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ntasks) return;
+    const RatioTask& r = tasks[t];
+    auto val = [&](int c) { return cplx ? make_double2(clos[2 * c], clos[2 * c + 1]) : make_double2(clos[c], 0.0); };
+    double nr = 0.0, ni = 0.0;
+    for (int k = 0; k < r.nparts; ++k) {
+        const double2 v = val(r.part[k]);
+        nr += r.c_re[k] * v.x - r.c_im[k] * v.y;
+        ni += r.c_re[k] * v.y + r.c_im[k] * v.x;
+    }
+    const double2 d = val(r.denom);
+    double qr, qi;
+    if (d.x == 0.0 && d.y == 0.0) {
+        atomicExch(status, 1);
+        qr = qi = 0.0;
+    } else if (fabs(d.y) <= fabs(d.x)) {
+        const double e = d.y / d.x, f = d.x + d.y * e;
+        qr = (nr + ni * e) / f;
+        qi = (ni - nr * e) / f;
+    } else {
+        const double e = d.x / d.y, f = d.y + d.x * e;
+        qr = (nr * e + ni) / f;
+        qi = (ni * e - nr) / f;
+    }
+    out[2 * t] = qr;
+    out[2 * t + 1] = qi;
+}
+cudaError_t launch_ratio(const RatioTask* d_tasks, int ntasks, const void* closings, bool cplx, double* out,
+                         int* status, cudaStream_t s) {
+    if (ntasks <= 0) return cudaSuccess;
+    k_ratio<<<(ntasks + 127) / 128, 128, 0, s>>>(d_tasks, ntasks, (const double*)closings, cplx ? 1 : 0, out, status);
     return cudaGetLastError();
 }
 

@@ -404,6 +404,21 @@ int plan_column_sweeps(bbp_lattice* L, Program& pr, std::vector<ColumnSweep>& cs
 }
 }  // namespace bbp
 
+// Lower bound on the zip-up fit tolerance of a precision.  The stop rule compares
+// std/|mean| of a sweep's losses (App. A); a loss computed from plain TF32 / BF16
+// contractions carries relative noise near 1e-3 / 1e-2, below which the rule never fires,
+// so those paths raise the tolerance to 3e-3 / 3e-2.  The split paths carry FP32-level
+// (TF32X3) and 16-bit (BF16X3) operands, whose loss noise sits below the paper's 1e-6
+// (TF32X3) or near 1e-5 (BF16X3): no floor, and 3e-5.
+double bbp::fit_tol_floor(int prec) {
+    switch (prec) {
+        case BBP_PREC_TF32: return 3e-3;
+        case BBP_PREC_BF16: return 3e-2;
+        case BBP_PREC_BF16X3: return 3e-5;
+        default: return 0.0;
+    }
+}
+
 // ------------------------------------------------------------------ plan one sweep
 static int plan_sweep(bbp_lattice* L) {
     Program& pr = L->sweep;
@@ -428,11 +443,7 @@ static int plan_sweep(bbp_lattice* L) {
         s.msg = (uint64_t)I.msgid;
         cs.push_back(s);
     }
-    // The fit stop rule compares std/|mean| of the sweep's losses; a loss computed from
-    // TF32 / BF16 contractions carries relative noise near 1e-3 / 1e-2, so on those
-    // paths the tolerance is raised to 3e-3 / 3e-2 (below it the rule never fires).
-    double fit_tol = L->desc.fit_tol;
-    if (L->mixed) fit_tol = std::max(fit_tol, L->cx.tck == 0 ? 3e-3 : 3e-2);
+    double fit_tol = std::max(L->desc.fit_tol, fit_tol_floor(L->desc.prec));
     int rc = plan_column_sweeps(L, pr, cs, L->desc.fit_max_sweeps, fit_tol, true, L->mixed,
                                 L->desc.warm_start != 0);
     if (rc) return rc;
@@ -563,7 +574,7 @@ static int validate(const bbp_lattice_desc* d) {
     if (d->boundary == BBP_INFINITE && (d->bx % d->Lx || d->by % d->Ly))
         return fail(BBP_ERR_INVALID, "infinite block must be a multiple of the unit cell");
     if (d->dtype < 0 || d->dtype > 3) return fail(BBP_ERR_INVALID, "unknown dtype");
-    if (d->prec < 0 || d->prec > 3) return fail(BBP_ERR_INVALID, "unknown precision");
+    if (d->prec < 0 || d->prec > 4) return fail(BBP_ERR_INVALID, "unknown precision");
     if (d->hermitian_basis != 0 && d->hermitian_basis != 1) return fail(BBP_ERR_INVALID, "hermitian_basis must be 0 or 1");
     if (d->fit_max_sweeps < 1 || d->fit_max_sweeps > 64) return fail(BBP_ERR_INVALID, "fit_max_sweeps must be 1..64");
     if (d->bx > 16 || d->by > 16) return fail(BBP_ERR_INVALID, "block sides are limited to 16 sites");
@@ -572,6 +583,7 @@ static int validate(const bbp_lattice_desc* d) {
     if (d->init_mode != 0 && d->init_mode != 1) return fail(BBP_ERR_INVALID, "init_mode must be 0 or 1");
     if (d->warm_start != 0 && d->warm_start != 1) return fail(BBP_ERR_INVALID, "warm_start must be 0 or 1");
     if (d->single_layer != 0 && d->single_layer != 1) return fail(BBP_ERR_INVALID, "single_layer must be 0 or 1");
+    if (d->launch_mode != 0 && d->launch_mode != 1) return fail(BBP_ERR_INVALID, "launch_mode must be 0 or 1");
     if (d->boundary == BBP_OBC ? (d->shift_x != 0 || d->shift_y != 0)
                                : (d->shift_x < 0 || d->shift_x >= d->Lx || d->shift_y < 0 || d->shift_y >= d->Ly))
         return fail(BBP_ERR_INVALID, "shifts: 0 <= shift < unit cell on infinite lattices, 0 with OBC");
@@ -660,8 +672,8 @@ int bbp::plan_lattice(const bbp_lattice_desc* desc, bbp_lattice** out) {
         L->mixed = true;
         MixCtx& cx = L->cx;
         cx.ss = L->ss;
-        cx.tck = desc->prec == BBP_PREC_BF16 ? 1 : 0;
-        cx.x3 = desc->prec == BBP_PREC_TF32X3;
+        cx.tck = (desc->prec == BBP_PREC_BF16 || desc->prec == BBP_PREC_BF16X3) ? 1 : 0;
+        cx.x3 = desc->prec == BBP_PREC_TF32X3 || desc->prec == BBP_PREC_BF16X3;
         cx.esz = cx.tck == 0 ? 4 : 2;
         cx.pe = 16 / cx.esz;
         cx.lpk = cx.tck == 0 ? 4 : 3;
@@ -765,12 +777,17 @@ int bbp_create_lattice(const bbp_lattice_desc* desc, bbp_lattice** out) try {
     if (e == cudaSuccess && L->mixed) {
         static const float one_f[4] = {1.0f, 0.0f, 0.0f, 0.0f};
         static const unsigned short one_b[8] = {0x3F80, 0, 0, 0, 0, 0, 0, 0};
-        // split TF32 rows of the constant 1 (K = 1): A [hi|lo|hi] = [1|0|1], B [hi|hi|lo] = [1|1|0]
+        // split rows of the constant 1 (K = 1): A [hi|lo|hi] = [1|0|1], B [hi|hi|lo] = [1|1|0]
         static const float one_xa[4] = {1.0f, 0.0f, 1.0f, 0.0f}, one_xb[4] = {1.0f, 1.0f, 0.0f, 0.0f};
-        const void* src = L->cx.x3 ? (const void*)one_xa : L->cx.tck == 0 ? (const void*)one_f : (const void*)one_b;
+        static const unsigned short one_bxa[8] = {0x3F80, 0, 0x3F80, 0, 0, 0, 0, 0};
+        static const unsigned short one_bxb[8] = {0x3F80, 0x3F80, 0, 0, 0, 0, 0, 0};
+        const bool bf = L->cx.tck == 1;
+        const void* src = L->cx.x3 ? (bf ? (const void*)one_bxa : (const void*)one_xa)
+                                   : (bf ? (const void*)one_b : (const void*)one_f);
         e = cudaMemcpyAsync(base + L->one_lp, src, 16, cudaMemcpyHostToDevice, L->stream);
         if (e == cudaSuccess && L->cx.x3)
-            e = cudaMemcpyAsync(base + L->one_lp_b, one_xb, 16, cudaMemcpyHostToDevice, L->stream);
+            e = cudaMemcpyAsync(base + L->one_lp_b, bf ? (const void*)one_bxb : (const void*)one_xb, 16,
+                                cudaMemcpyHostToDevice, L->stream);
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(L->stream);
     if (e != cudaSuccess) {
@@ -801,64 +818,30 @@ void bbp_destroy(bbp_lattice* L) try {
 // Initial messages (App. A: messages start from a chosen state; init_mode 0 is the
 // product of delta_{ket,bra}, init_mode 1 a random positive MPDO of bond 1; on a
 // single-layer network the all-ones product or positive uniform entries), each
-// normalised to unit 2-norm with <I|m> (<1|m>) > 0.
-static void init_messages(bbp_lattice* L, std::vector<double>& host) {
-    const int D = L->desc.D, K = L->K, cw = L->cplx ? 2 : 1;
-    host.assign(L->msg_elems * cw, 0.0);
+// normalised to unit 2-norm with <I|m> (<1|m>) > 0: one task per message for k_msg_init.
+static std::vector<MsgInitTask> init_tasks(bbp_lattice* L) {
+    std::vector<MsgInitTask> ts;
+    char* base = L->arena;
     for (int it = 0; it < (int)L->items.size(); ++it) {
         const Item& I = L->items[it];
-        double total = 1.0;
-        std::vector<std::vector<double>> sites(I.b);
+        MsgInitTask t{};
+        t.nsites = I.b;
+        t.K = L->K;
+        t.D = L->desc.D;
+        t.mode = L->desc.init_mode;
+        t.single = L->single ? 1 : 0;
+        t.hb = L->hb ? 1 : 0;
+        t.cw = L->cplx ? 2 : 1;
+        t.seed = L->desc.seed;
+        t.stream = stream_id(2, 0, (uint64_t)I.msgid, 0, 0);
         for (int s = 0; s < I.b; ++s) {
-            std::vector<double> v(K, 0.0);
-            const uint64_t stream = stream_id(2, 0, (uint64_t)I.msgid, 0, 0) + (uint64_t)s;
-            if (L->single) {
-                // single-layer network: the all-ones product (mode 0) or positive uniform
-                // entries (mode 1), the start the paper uses for single-layer networks
-                for (int k = 0; k < K; ++k)
-                    v[k] = L->desc.init_mode == 0 ? 1.0 : (uniform_pm1(L->desc.seed, stream, k) + 1.0) * 0.5;
-            } else if (L->desc.init_mode == 0) {
-                for (int k = 0; k < D; ++k) v[k * D + k] = 1.0;
-            } else {
-                // G with normal entries (Box-Muller on the counter-based uniforms), site = G G^T
-                std::vector<double> g(D * D);
-                for (int j = 0; j < D * D; ++j) {
-                    const double u1 = (uniform_pm1(L->desc.seed, stream, 2 * j) + 1.0) * 0.5;
-                    const double u2 = (uniform_pm1(L->desc.seed, stream, 2 * j + 1) + 1.0) * 0.5;
-                    g[j] = std::sqrt(-2.0 * std::log1p(-u1)) * std::cos(2.0 * M_PI * u2);
-                }
-                for (int a = 0; a < D; ++a)
-                    for (int b = 0; b < D; ++b) {
-                        double acc = 0;
-                        for (int k = 0; k < D; ++k) acc += g[a * D + k] * g[b * D + k];
-                        v[a * D + b] = acc;
-                    }
-                if (L->hb) {
-                    // G G^T is real symmetric: Hermitian-basis coordinates (v_ab + v_ba)/sqrt 2
-                    // for a < b, 0 for a > b, v_aa on the diagonal
-                    std::vector<double> w(v);
-                    for (int a = 0; a < D; ++a)
-                        for (int b = 0; b < D; ++b)
-                            if (a < b) w[a * D + b] = (v[a * D + b] + v[b * D + a]) / std::sqrt(2.0);
-                            else if (a > b) w[a * D + b] = 0.0;
-                    v = w;
-                }
-            }
-            double n2 = 0;
-            for (double x : v) n2 += x * x;
-            total *= std::sqrt(n2);
-            sites[s] = v;
+            // element [a=0][k][b=0] of a site with bonds (mb[s], mb[s+1]) sits at k * mb[s+1]
+            t.dst[s] = (double*)(base + (L->msg_cur + I.region_off + I.site_off[s]) * L->ss);
+            t.kstride[s] = I.mb[s + 1];
         }
-        for (int s = 0; s < I.b; ++s) {
-            // bond-1 sites: only entries [0][k][0] are nonzero
-            const size_t base = I.region_off + I.site_off[s];
-            for (int k = 0; k < K; ++k) {
-                const double val = sites[s][k] / (s == 0 ? total : 1.0);
-                // element [a=0][k][b=0] of a site with bonds (mb[s], mb[s+1]) sits at k * mb[s+1]
-                host[(base + (size_t)k * I.mb[s + 1]) * cw] = val;
-            }
-        }
+        ts.push_back(t);
     }
+    return ts;
 }
 
 int bbp_set_tensors(bbp_lattice* L, const void* data, int on_device) try {
@@ -938,9 +921,17 @@ int bbp_set_tensors(bbp_lattice* L, const void* data, int on_device) try {
         CKR(launch_relayout(d_rt, (int)rt.size(), mx, st));
         CKR(cudaMemsetAsync(L->d_tcerr, 0, sizeof(int), st));
     }
-    std::vector<double> host;
-    init_messages(L, host);
-    CKR(cudaMemcpyAsync(base + L->msg_cur * L->ss, host.data(), host.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+    // initial messages, built on the device into the zeroed message region
+    CKR(cudaMemsetAsync(base + L->msg_cur * L->ss, 0, L->msg_elems * L->ss, st));
+    {
+        const std::vector<MsgInitTask> mt = init_tasks(L);
+        if (!mt.empty()) {
+            AsyncBuffer mb(st);
+            CKR(cudaMallocAsync(&mb.p, mt.size() * sizeof(MsgInitTask), st));
+            CKR(cudaMemcpyAsync(mb.p, mt.data(), mt.size() * sizeof(MsgInitTask), cudaMemcpyHostToDevice, st));
+            CKR(launch_msg_init((const MsgInitTask*)mb.p, (int)mt.size(), st));
+        }
+    }
     CKR(cudaMemsetAsync(L->d_sweep, 0, sizeof(int), st));
     CKR(cudaMemsetAsync(L->d_status, 0, sizeof(int), st));
     CKR(cudaStreamSynchronize(st));
@@ -967,9 +958,19 @@ namespace bbp {
 // Queue one sweep (graph launch) and the copies of its residual and error words into
 // pinned memory, then record the sweep's event.  Asynchronous.
 int sweep_launch(bbp_lattice* L) {
-    int rc = ensure_graph(L);
-    if (rc) return rc;
-    CKR(cudaGraphLaunch(L->sweep.exec, L->stream));
+    if (L->desc.launch_mode == 1) {
+        // the sweep's kernels one by one; every fit loop runs its maximum count, the fits that
+        // have met the stop rule skipping their work (the graph's result, launch by launch)
+        if (!L->direct_ready) {
+            CKR(L->sweep.init_loops(L->stream, false, nullptr));
+            L->direct_ready = true;
+        }
+        CKR(L->sweep.launch_all(L->stream, L->d_sweep, L->desc.seed));
+    } else {
+        int rc = ensure_graph(L);
+        if (rc) return rc;
+        CKR(cudaGraphLaunch(L->sweep.exec, L->stream));
+    }
     CKR(cudaMemcpyAsync(&L->h_pinned->residual, L->d_residual, sizeof(double), cudaMemcpyDeviceToHost, L->stream));
     CKR(cudaMemcpyAsync(&L->h_pinned->status, L->d_status, sizeof(int), cudaMemcpyDeviceToHost, L->stream));
     if (L->mixed) CKR(cudaMemcpyAsync(&L->h_pinned->tc_err, L->d_tcerr, sizeof(int), cudaMemcpyDeviceToHost, L->stream));

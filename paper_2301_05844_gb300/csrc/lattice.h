@@ -92,6 +92,7 @@ struct bbp_lattice {
     bbp::PinnedWords* h_pinned = nullptr;
     cudaEvent_t done = nullptr;  // recorded after each sweep's read-back copies
     bool has_tensors = false;
+    bool direct_ready = false;  // launch_mode 1: loop descriptors written for direct launches
     // stats
     int sweeps = 0;
     double first_residual = 0, last_residual = 0;
@@ -117,6 +118,8 @@ bool sweep_ready(bbp_lattice* L);
 int sweep_collect(bbp_lattice* L, double* residual, bool* stop);
 // Plan a lattice without allocating device memory (arena_bytes set); nullptr on error.
 int plan_lattice(const bbp_lattice_desc* desc, bbp_lattice** out);
+// Lower bound on the zip-up fit tolerance on the path of precision prec (bbp_prec).
+double fit_tol_floor(int prec);
 // Resident device bytes of a planned lattice: arena plus sweep task descriptors.
 size_t planned_bytes(const bbp_lattice* L);
 }  // namespace bbp

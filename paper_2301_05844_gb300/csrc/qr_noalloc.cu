@@ -2,6 +2,7 @@
 // allocation.  Its workspace and task descriptors live in a file-scope device array.
 #include <cuda_runtime.h>
 
+#include <mutex>
 #include <string>
 
 #include "bbp.h"
@@ -14,9 +15,13 @@ using namespace bbp;
 // that loads the library holds these 16 MiB until the process exits.
 static __device__ __align__(256) unsigned char g_qr_scratch[BBP_QR_NOALLOC_SCRATCH_BYTES];
 
+// The header states the descriptor bytes a request needs (144 per matrix).
+static_assert(sizeof(QRTask) == 144, "bbp.h states 144 descriptor bytes per matrix");
+
 namespace {
 constexpr int kMaxDevices = 64;
 void* g_scratch_addr[kMaxDevices] = {};  // device address of g_qr_scratch, per device
+std::mutex g_setup_mu;                   // serialises the first call on each device
 
 // Task descriptors are built on the device, so the call needs no host staging buffer.
 __global__ void k_build_qr_tasks(QRTask* tasks, int batch, int m, int n, size_t ss, const double* A, double* Q,
@@ -53,20 +58,34 @@ extern "C" int bbp_qr_batched_noalloc(int batch, int m, int n, int complex_value
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices)
         return fail(BBP_ERR_CUDA, std::string("qr_batched_noalloc: no current device: ") + cudaGetErrorString(e));
-    if (!g_scratch_addr[dev]) {
-        // first call on this device: resolve the device address of the array (the
-        // host-side symbol is only a stand-in) and raise the kernel's shared-memory limit
-        void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_qr_scratch);
-        if (e != cudaSuccess || !p)
-            return fail(BBP_ERR_CUDA, std::string("qr_batched_noalloc: workspace address: ") + cudaGetErrorString(e));
-        e = qr_prepare(512, complex_values != 0);
-        if (e != cudaSuccess) return fail(BBP_ERR_CUDA, std::string("qr_batched_noalloc: ") + cudaGetErrorString(e));
-        g_scratch_addr[dev] = p;
+    void* addr = nullptr;
+    {
+        std::lock_guard<std::mutex> guard(g_setup_mu);
+        if (!g_scratch_addr[dev]) {
+            // first call on this device: resolve the device address of the array (the host-side
+            // symbol is only a stand-in; under lazy module loading this also loads the module and
+            // commits the array) and raise the QR kernels' shared-memory limits for both scalar
+            // types, so that no later call changes a kernel attribute
+            void* p = nullptr;
+            e = cudaGetSymbolAddress(&p, g_qr_scratch);
+            if (e != cudaSuccess || !p) {
+                const bool oom = e == cudaErrorMemoryAllocation;
+                return fail(oom ? BBP_ERR_OOM : BBP_ERR_CUDA,
+                            std::string("qr_batched_noalloc: workspace address: ") + cudaGetErrorString(e));
+            }
+            e = qr_prepare(512, false);
+            if (e == cudaSuccess) e = qr_prepare(512, true);
+            if (e != cudaSuccess)
+                return fail(e == cudaErrorMemoryAllocation ? BBP_ERR_OOM : BBP_ERR_CUDA,
+                            std::string("qr_batched_noalloc: ") + cudaGetErrorString(e));
+            g_scratch_addr[dev] = p;
+        }
+        addr = g_scratch_addr[dev];
     }
+    // a no-op unless m is above the 512 rows prepared at the first call (the limit only grows)
     e = qr_prepare(m, complex_values != 0);
     if (e != cudaSuccess) return fail(BBP_ERR_CUDA, std::string("qr_batched_noalloc: ") + cudaGetErrorString(e));
-    unsigned char* base = (unsigned char*)g_scratch_addr[dev];
+    unsigned char* base = (unsigned char*)addr;
     QRTask* tasks = (QRTask*)base;
     cudaStream_t st = (cudaStream_t)stream;
     k_build_qr_tasks<<<(batch + 127) / 128, 128, 0, st>>>(tasks, batch, m, n, ss, A, Q, loss, base + task_bytes);

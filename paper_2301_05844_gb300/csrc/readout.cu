@@ -275,15 +275,15 @@ extern "C" int bbp_expect(bbp_lattice* L, const bbp_term* terms, int n_terms, do
         }
     }
     // The environment columns are fits like those of a sweep.  On a split-TF32 lattice they run
-    // on its tensor-core path (FP32-level contractions, FP64 QR, the same fit-tolerance floor);
-    // TF32 / BF16 lattices keep FP64 fits here, so that the read-out adds no error of its own
-    // at their precision.  The closings and the ratio N_O / N_I are FP64 in every case.
-    const bool tc_env = L->mixed && L->cx.x3;
+    // on its tensor-core path (FP32-level contractions, FP64 QR, the same fit tolerance);
+    // TF32 / BF16 / split-BF16 lattices keep FP64 fits here, so that the read-out adds no error
+    // of its own at their precision.  The closings and the ratio N_O / N_I are FP64 in every case.
+    const bool tc_env = L->mixed && L->cx.x3 && L->cx.tck == 0;
     if (tc_env) {
         pr.tc_kind = L->cx.tck;
         pr.tc_err = L->d_tcerr;
     }
-    int rc = plan_column_sweeps(L, pr, cs, ds.fit_max_sweeps, tc_env ? std::max(ds.fit_tol, 3e-3) : ds.fit_tol,
+    int rc = plan_column_sweeps(L, pr, cs, ds.fit_max_sweeps, tc_env ? std::max(ds.fit_tol, fit_tol_floor(ds.prec)) : ds.fit_tol,
                                 false, tc_env);
     if (rc) return rc;
 
@@ -308,6 +308,11 @@ extern "C" int bbp_expect(bbp_lattice* L, const bbp_term* terms, int n_terms, do
     const int K4max = L->K * L->K * L->K * L->K;
     const size_t nclos = closings.size();
     const size_t results = elem_alloc(nclos);
+    // the ratios N_O / N_I, formed on the device: task descriptors, (re, im) per term, status
+    static_assert(sizeof(RatioTask) % sizeof(double) == 0, "ratio tasks are uploaded as doubles");
+    const size_t ratio_tasks = pr.arena_alloc((size_t)n_terms * sizeof(RatioTask));
+    const size_t ratio_out = pr.arena_alloc((size_t)n_terms * 2 * sizeof(double));
+    const size_t ratio_status = pr.arena_alloc(sizeof(int));
     struct Lane {
         size_t F[2], G1, G2, EO[2], O12;
     };
@@ -356,6 +361,24 @@ extern "C" int bbp_expect(bbp_lattice* L, const bbp_term* terms, int n_terms, do
     // operators (impurity tensors) of every closing, each in its own slab: uploaded once
     // before the read-out runs, whichever wave of lanes uses them
     std::vector<std::pair<size_t, std::vector<double>>> uploads;
+    {
+        std::vector<RatioTask> rt(n_terms);
+        for (int t = 0; t < n_terms; ++t) {
+            RatioTask& r = rt[t];
+            r = RatioTask{};
+            if (tplan[t].parts.size() > 4) return fail(BBP_ERR_INVALID, "internal: more than four operator parts");
+            r.nparts = (int)tplan[t].parts.size();
+            for (int k = 0; k < r.nparts; ++k) {
+                r.part[k] = tplan[t].parts[k].first;
+                r.c_re[k] = tplan[t].parts[k].second.real();
+                r.c_im[k] = tplan[t].parts[k].second.imag();
+            }
+            r.denom = tplan[t].denom;
+        }
+        std::vector<double> words(rt.size() * sizeof(RatioTask) / sizeof(double));
+        if (!rt.empty()) std::memcpy(words.data(), rt.data(), rt.size() * sizeof(RatioTask));
+        uploads.push_back({ratio_tasks / (size_t)ss, words});  // byte offsets are 256-aligned
+    }
     std::vector<std::array<size_t, 2>> opoff(nclos, std::array<size_t, 2>{0, 0});
     for (size_t ci = 0; ci < nclos; ++ci)
         for (size_t k = 0; k < closings[ci].pos.size(); ++k) {
@@ -523,27 +546,25 @@ extern "C" int bbp_expect(bbp_lattice* L, const bbp_term* terms, int n_terms, do
         CKR(pr.init_loops(st, false, nullptr));
         CKR(pr.launch_all(st, nullptr, ds.seed));
     }
-    std::vector<double> res(nclos * (L->cplx ? 2 : 1));
-    CKR(cudaMemcpyAsync(res.data(), ro + (results * ss - split), res.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
-    int status = 0, tc_status = 0;
+    // <O> = N_O / N_I for every term on the device (FP64), then one copy of the results
+    char* rbase = ro - split;  // arena byte offset -> address in the read-out buffer
+    CKR(launch_ratio((const RatioTask*)(rbase + ratio_tasks), n_terms, rbase + results * ss, L->cplx,
+                     (double*)(rbase + ratio_out), (int*)(rbase + ratio_status), st));
+    std::vector<double> res((size_t)n_terms * 2);
+    CKR(cudaMemcpyAsync(res.data(), rbase + ratio_out, res.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+    int status = 0, tc_status = 0, ratio_st = 0;
     CKR(cudaMemcpyAsync(&status, L->d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CKR(cudaMemcpyAsync(&ratio_st, rbase + ratio_status, sizeof(int), cudaMemcpyDeviceToHost, st));
     if (tc_env) CKR(cudaMemcpyAsync(&tc_status, L->d_tcerr, sizeof(int), cudaMemcpyDeviceToHost, st));
     CKR(cudaStreamSynchronize(st));
     if (tc_status) return fail(BBP_ERR_TIMEOUT, "a tensor-core pipeline wait exceeded its bound");
-    L->readout_kernels += pr.kernel_count();
+    L->readout_kernels += pr.kernel_count() + 1;
     L->readout_flops += pr.static_flops + pr.gated_flops;
     if (status) return fail(BBP_ERR_NUMERIC, "an environment column has zero or non-finite norm");
-    auto val = [&](int ci) {
-        return L->cplx ? std::complex<double>(res[2 * ci], res[2 * ci + 1]) : std::complex<double>(res[ci], 0.0);
-    };
+    if (ratio_st) return fail(BBP_ERR_NUMERIC, "the closed network vanished");
     for (int t = 0; t < n_terms; ++t) {
-        std::complex<double> num = 0.0;
-        for (auto& p : tplan[t].parts) num += p.second * val(p.first);
-        const std::complex<double> den = val(tplan[t].denom);
-        if (den == 0.0) return fail(BBP_ERR_NUMERIC, "the closed network vanished");
-        const std::complex<double> r = num / den;
-        out_re[t] = r.real();
-        if (out_im) out_im[t] = r.imag();
+        out_re[t] = res[2 * (size_t)t];
+        if (out_im) out_im[t] = res[2 * (size_t)t + 1];
     }
     return BBP_OK;
 } catch (...) {

@@ -11,7 +11,8 @@
 
 using namespace bbp;
 
-extern "C" int bbp_selftest_gemm(int M, int N, int K, int prec, const float* A, const float* B, float* C) try {
+// The GEMM of bbp_selftest_gemm; stall: launch with the producer's copies withheld.
+static int selftest_gemm(int M, int N, int K, int prec, const float* A, const float* B, float* C, int stall) {
     if (M < 1 || N < 1 || K < 1 || !A || !B || !C || (prec != BBP_PREC_TF32 && prec != BBP_PREC_BF16))
         return fail(BBP_ERR_INVALID, "selftest: bad arguments");
     const int kind = prec == BBP_PREC_TF32 ? 0 : 1;
@@ -52,7 +53,7 @@ extern "C" int bbp_selftest_gemm(int M, int N, int K, int prec, const float* A, 
     const int tiles = ((M + 127) / 128) * ((N + bn - 1) / bn);
     const int ek = kind == 0 ? 32 : 64;
     const int nk = (K + ek - 1) / ek;
-    if (!e) e = launch_tc_gemm((const TCTask*)dt, 1, kind, bn, tiles, tc_default_stages(bn, nk), derr, 0);
+    if (!e) e = launch_tc_gemm((const TCTask*)dt, 1, kind, bn, tiles, tc_default_stages(bn, nk), derr, 0, 1, stall);
     if (!e) e = cudaDeviceSynchronize();
     int herr = 0;
     if (!e) e = cudaMemcpy(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost);
@@ -61,6 +62,40 @@ extern "C" int bbp_selftest_gemm(int M, int N, int K, int prec, const float* A, 
     else if (herr) rc = fail(BBP_ERR_TIMEOUT, "selftest: a pipeline wait timed out");
     cudaFree(da); cudaFree(db); cudaFree(dc); cudaFree(dt); cudaFree(derr);
     return rc;
+}
+
+extern "C" int bbp_selftest_gemm(int M, int N, int K, int prec, const float* A, const float* B, float* C) try {
+    return selftest_gemm(M, N, K, prec, A, B, C, 0);
+} catch (...) {
+    return abi_error();
+}
+
+extern "C" int bbp_selftest_gemm_timeout(void) try {
+    // a 256 x 64 x 64 TF32 GEMM (two tiles) whose operands are never loaded
+    std::vector<float> a(256 * 64, 1.0f), b(64 * 64, 1.0f), c(256 * 64, 0.0f);
+    return selftest_gemm(256, 64, 64, BBP_PREC_TF32, a.data(), b.data(), c.data(), 1);
+} catch (...) {
+    return abi_error();
+}
+
+extern "C" int bbp_selftest_scalar(long long n, const double* x, double* rsqrt_ours, double* rcp_ours,
+                                   double* rsqrt_cuda, double* rcp_cuda) try {
+    if (n < 1 || !x || !rsqrt_ours || !rcp_ours || !rsqrt_cuda || !rcp_cuda)
+        return fail(BBP_ERR_INVALID, "selftest_scalar: bad arguments");
+    for (long long i = 0; i < n; ++i)
+        if (!(x[i] >= 0x1p-100 && x[i] <= 0x1p100)) return fail(BBP_ERR_INVALID, "selftest_scalar: x outside [2^-100, 2^100]");
+    double* d = nullptr;
+    const size_t bytes = (size_t)n * sizeof(double);
+    cudaError_t e = cudaMalloc((void**)&d, 5 * bytes);
+    if (e) return fail(BBP_ERR_OOM, std::string("selftest_scalar: ") + cudaGetErrorString(e));
+    e = cudaMemcpy(d, x, bytes, cudaMemcpyHostToDevice);
+    if (!e) e = launch_scalar_selftest(d, n, d + n, d + 2 * n, d + 3 * n, d + 4 * n, 0);
+    if (!e) e = cudaDeviceSynchronize();
+    double* outs[4] = {rsqrt_ours, rcp_ours, rsqrt_cuda, rcp_cuda};
+    for (int k = 0; k < 4 && !e; ++k) e = cudaMemcpy(outs[k], d + (k + 1) * n, bytes, cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e) return fail(BBP_ERR_CUDA, std::string("selftest_scalar: ") + cudaGetErrorString(e));
+    return BBP_OK;
 } catch (...) {
     return abi_error();
 }

@@ -68,6 +68,15 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* e
     return false;
 }
 
+// Bounded wait that ignores the error word: drains a CTA's own asynchronous work on the
+// failure path (its copies and MMAs must finish before its shared memory and TMEM are
+// released, whichever CTA raised the error).  Gives up after ~2^22 polls.
+__device__ __forceinline__ bool mbar_wait_own(uint64_t* bar, uint32_t parity) {
+    for (uint32_t i = 0; i < (1u << 22); ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
 __device__ __forceinline__ void tma_load_2d(void* dst, const void* map, uint64_t* bar, int c0, int c1) {
     asm volatile(
         "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
@@ -178,25 +187,56 @@ __device__ __forceinline__ void store_vec(void* out, long long o, int kind, cons
 
 constexpr int EC = 64;  // epilogue chunk (columns)
 
-// Split TF32 destination (x3 = 1: A rows [hi|lo|hi], 2: B rows [hi|hi|lo], segments kseg
-// elements apart): hi = tf32(x), lo = tf32(x - hi).
-__device__ __forceinline__ void store_split1(float* out, long long o, float x, int x3, long long kseg) {
+// Split destination (x3 = 1: A rows [hi|lo|hi], 2: B rows [hi|hi|lo], segments kseg
+// elements apart): hi = r(x), lo = r(x - hi), r the rounding of the element kind (TF32 for
+// kind 1, BF16 for kind 2); x - hi is exact in FP32 for both.
+__device__ __forceinline__ void store_split1(void* out, long long o, int kind, float x, int x3, long long kseg) {
+    if (kind == 2) {
+        const __nv_bfloat16 hb = __float2bfloat16_rn(x);
+        const __nv_bfloat16 lb = __float2bfloat16_rn(x - __bfloat162float(hb));
+        __nv_bfloat16* b = (__nv_bfloat16*)out;
+        b[o] = hb;
+        b[o + kseg] = x3 == 1 ? lb : hb;
+        b[o + 2 * kseg] = x3 == 1 ? hb : lb;
+        return;
+    }
+    float* f = (float*)out;
     const float hi = round_tf32(x), lo = round_tf32(x - hi);
-    out[o] = hi;
-    out[o + kseg] = x3 == 1 ? lo : hi;
-    out[o + 2 * kseg] = x3 == 1 ? hi : lo;
+    f[o] = hi;
+    f[o + kseg] = x3 == 1 ? lo : hi;
+    f[o + 2 * kseg] = x3 == 1 ? hi : lo;
 }
-__device__ __forceinline__ void store_split4(float* out, long long o, const float* x, int x3, long long kseg) {
+// 16 bytes per segment: 4 TF32 elements (kind 1) or 8 BF16 elements (kind 2)
+__device__ __forceinline__ void store_split_vec(void* out, long long o, int kind, const float* x, int x3,
+                                                long long kseg) {
+    uint4 H, Lo;
+    if (kind == 2) {
+        __nv_bfloat162 h[4], l[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            h[j] = __floats2bfloat162_rn(x[2 * j], x[2 * j + 1]);
+            const float2 hf = __bfloat1622float2(h[j]);
+            l[j] = __floats2bfloat162_rn(x[2 * j] - hf.x, x[2 * j + 1] - hf.y);
+        }
+        H = *(const uint4*)h;
+        Lo = *(const uint4*)l;
+        __nv_bfloat16* b = (__nv_bfloat16*)out;
+        *(uint4*)(b + o) = H;
+        *(uint4*)(b + o + kseg) = x3 == 1 ? Lo : H;
+        *(uint4*)(b + o + 2 * kseg) = x3 == 1 ? H : Lo;
+        return;
+    }
     float hi[4], lo[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
         hi[j] = round_tf32(x[j]);
         lo[j] = round_tf32(x[j] - hi[j]);
     }
-    const float4 H = make_float4(hi[0], hi[1], hi[2], hi[3]), Lo = make_float4(lo[0], lo[1], lo[2], lo[3]);
-    *(float4*)(out + o) = H;
-    *(float4*)(out + o + kseg) = x3 == 1 ? Lo : H;
-    *(float4*)(out + o + 2 * kseg) = x3 == 1 ? H : Lo;
+    float* f = (float*)out;
+    const float4 Hf = make_float4(hi[0], hi[1], hi[2], hi[3]), Lf = make_float4(lo[0], lo[1], lo[2], lo[3]);
+    *(float4*)(f + o) = Hf;
+    *(float4*)(f + o + kseg) = x3 == 1 ? Lf : Hf;
+    *(float4*)(f + o + 2 * kseg) = x3 == 1 ? Hf : Lf;
 }
 
 __device__ __forceinline__ void epilogue_dest(const float* tile, long long* roff, long long* coff, int rows, int ncols,
@@ -231,12 +271,12 @@ __device__ __forceinline__ void epilogue_dest(const float* tile, long long* roff
 #pragma unroll
                 for (int j = 0; j < 8; ++j)
                     if (j < VW) x[j] = tile[r * P + c0 + j] * alpha;
-                if (x3) store_split4((float*)out, o, x, x3, kseg);
+                if (x3) store_split_vec(out, o, kind, x, x3, kseg);
                 else store_vec(out, o, kind, x);
             } else {
                 for (int j = 0; j < VW && c0 + j < ncols; ++j) {
                     const float xv = tile[r * P + c0 + j] * alpha;
-                    if (x3) store_split1((float*)out, roff[r] + coff[c0 + j], xv, x3, kseg);
+                    if (x3) store_split1(out, roff[r] + coff[c0 + j], kind, xv, x3, kseg);
                     else store_out(out, roff[r] + coff[c0 + j], kind, xv);
                 }
             }
@@ -252,12 +292,12 @@ __device__ __forceinline__ void epilogue_dest(const float* tile, long long* roff
 #pragma unroll
                 for (int j = 0; j < 8; ++j)
                     if (j < VW) x[j] = tile[(r0 + j) * P + c] * alpha;
-                if (x3) store_split4((float*)out, o, x, x3, kseg);
+                if (x3) store_split_vec(out, o, kind, x, x3, kseg);
                 else store_vec(out, o, kind, x);
             } else {
                 for (int j = 0; j < VW && r0 + j < rows; ++j) {
                     const float xv = tile[(r0 + j) * P + c] * alpha;
-                    if (x3) store_split1((float*)out, roff[r0 + j] + coff[c], xv, x3, kseg);
+                    if (x3) store_split1(out, roff[r0 + j] + coff[c], kind, xv, x3, kseg);
                     else store_out(out, roff[r0 + j] + coff[c], kind, xv);
                 }
             }
@@ -266,14 +306,17 @@ __device__ __forceinline__ void epilogue_dest(const float* tile, long long* roff
         for (int it = tid; it < rows * ncols; it += 128) {
             const int c = it / rows, r = it - c * rows;
             const float xv = tile[r * P + c] * alpha;
-            if (x3) store_split1((float*)out, roff[r] + coff[c], xv, x3, kseg);
+            if (x3) store_split1(out, roff[r] + coff[c], kind, xv, x3, kseg);
             else store_out(out, roff[r] + coff[c], kind, xv);
         }
     }
 }
 
 template <int KIND, int BN>
-__global__ void __launch_bounds__(128, 1) k_tc_gemm(const TCTask* __restrict__ tasks, int* err, int stages, int ksub) {
+// stall != 0 (self-test of the bounded waits only): the producer issues no copy, so the
+// first wait on a full stage never succeeds and must end by its bound.
+__global__ void __launch_bounds__(128, 1) k_tc_gemm(const TCTask* __restrict__ tasks, int* err, int stages, int ksub,
+                                                    int stall) {
     // The task descriptor is copied to shared memory in one coalesced read (its fields are
     // otherwise fetched from global memory one dependent load at a time); the TMA copies use
     // the tensor maps at their global address.
@@ -328,7 +371,7 @@ __global__ void __launch_bounds__(128, 1) k_tc_gemm(const TCTask* __restrict__ t
 
     if (warp == 0 && lane == 0) {
         // TMA producer: stage ks holds k-blocks ks*ksub .. (the last stage may hold fewer)
-        for (int ks = 0; ks < nst; ++ks) {
+        for (int ks = 0; ks < (stall ? 0 : nst); ++ks) {
             const int s = ks % stages, r = ks / stages;
             if (r > 0 && !mbar_wait(&empty[s], (r - 1) & 1, err)) break;
             const int na = min(ksub, nk - ks * ksub);
@@ -399,13 +442,17 @@ __global__ void __launch_bounds__(128, 1) k_tc_gemm(const TCTask* __restrict__ t
     }
     fence_before();
     __syncthreads();
-    // drain: the producer's copies must have landed before shared memory is released.  On
-    // success the MMA warp already waited for every issued copy, so only a pipeline that
-    // stopped on a timed-out wait can still have copies in flight.
+    // drain: the MMAs issued must have finished before TMEM is released, and the producer's
+    // copies must have landed before shared memory is.  On success the MMA warp already waited
+    // for every issued copy and the epilogue for every MMA, so only a pipeline that stopped on
+    // a timed-out wait (here or in another CTA) can still have work in flight.  The MMA warp
+    // commits the accumulator barrier after its loop in every case, so it completes once the
+    // MMAs issued before it have; these waits ignore the error word.
     if (!all_ready && threadIdx.x == 0) {
+        mbar_wait_own(&accum, 0);
         const int n_issued = issued;
         for (int kb = (n_issued > stages ? n_issued - stages : 0); kb < n_issued; ++kb)
-            mbar_wait(&full[kb % stages], (kb / stages) & 1, err);
+            mbar_wait_own(&full[kb % stages], (kb / stages) & 1);
     }
     __syncthreads();
     if (warp == 0) tmem_dealloc(tmem, BN < 32 ? 32 : BN);
@@ -468,7 +515,7 @@ cudaError_t tc_prepare() {
 }
 
 cudaError_t launch_tc_gemm(const TCTask* d_tasks, int ntasks, int kind, int bn, int max_tiles, int stages, int* err,
-                           cudaStream_t s, int ksub) {
+                           cudaStream_t s, int ksub, int stall) {
     if (ntasks <= 0) return cudaSuccess;
     if (ksub < 1) ksub = 1;
     if (stages < 1 || stages > tc_max_stages(bn, ksub)) return cudaErrorInvalidValue;
@@ -487,7 +534,7 @@ cudaError_t launch_tc_gemm(const TCTask* d_tasks, int ntasks, int kind, int bn, 
     cfg.attrs = attr;
     cfg.numAttrs = 1;
 #define TC_CASE(K_, N_)                                                              \
-    if (kind == K_ && bn == N_) return cudaLaunchKernelEx(&cfg, tc::k_tc_gemm<K_, N_>, d_tasks, err, stages, ksub);
+    if (kind == K_ && bn == N_) return cudaLaunchKernelEx(&cfg, tc::k_tc_gemm<K_, N_>, d_tasks, err, stages, ksub, stall);
     TC_CASE(0, 32) TC_CASE(0, 64) TC_CASE(0, 128) TC_CASE(0, 256)
     TC_CASE(1, 32) TC_CASE(1, 64) TC_CASE(1, 128) TC_CASE(1, 256)
 #undef TC_CASE

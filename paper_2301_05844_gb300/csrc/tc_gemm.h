@@ -34,9 +34,11 @@ cudaError_t tc_prepare();
 // per stage) for a step of `kblocks` k-blocks.
 int tc_max_stages(int bn, int ksub = 1);
 int tc_default_stages(int bn, int kblocks);
-// stages: depth of the shared-memory ring (1..tc_max_stages(bn, ksub)).
+// stages: depth of the shared-memory ring (1..tc_max_stages(bn, ksub)).  stall != 0 only in
+// the self-test of the bounded waits: no operand is loaded, so a CTA's first wait runs out
+// (or returns on the error another CTA raised), *err is raised and the launch ends.
 cudaError_t launch_tc_gemm(const TCTask* d_tasks, int ntasks, int kind, int bn, int max_tiles, int stages, int* err,
-                           cudaStream_t s, int ksub = 1);
+                           cudaStream_t s, int ksub = 1, int stall = 0);
 // kind: 0 FP32/TF32 elements, 1 BF16.  rows x K matrix with leading dimension ld_elems
 // (ld * element size must be a multiple of 16 bytes, base 16-byte aligned).
 cudaError_t tc_make_map(void* map_out, const void* base, int kind, long long rows, long long K, long long ld_elems,

@@ -8,7 +8,10 @@ from paper_2301_05844_gb300 import binding as B
 
 def run_both(T, Lx, Ly, d, D, bx, by, chi, terms, n_sweeps, boundary="obc", chi_exp=0, fit_tol=0.0,
              fit_max_sweeps=2, seed=7, init_mode=0, dtype=None, prec="fp64", warm_start=False, hermitian_basis=0,
-             single_layer=False, shift=(0, 0)):
+             single_layer=False, shift=(0, 0), oracle_hb=False, oracle_fit_tol=None):
+    """oracle_hb: run the oracle in its Hermitian-basis option (the basis of the library's
+    real-arithmetic paths for complex tensors).  oracle_fit_tol: the fit tolerance of the
+    oracle's message sweeps (default: fit_tol; its read-out fits keep fit_tol)."""
     cplx = any(np.iscomplexobj(t) for t in T)
     if dtype is None:
         dtype = B.C128 if cplx else B.F64
@@ -17,8 +20,9 @@ def run_both(T, Lx, Ly, d, D, bx, by, chi, terms, n_sweeps, boundary="obc", chi_
                   warm_start=warm_start, hermitian_basis=hermitian_basis, single_layer=int(single_layer), shift=shift)
     g.set_tensors(T)
     o = ob.Lattice(Lx, Ly, d, D, bx, by, [np.asarray(t) for t in T], boundary=boundary, chi=chi, chi_exp=chi_exp,
-                   fit_tol=fit_tol, fit_max_sweeps=fit_max_sweeps, seed=seed, init_mode=init_mode,
-                   warm_start=warm_start, single_layer=single_layer, shift=shift)
+                   fit_tol=fit_tol if oracle_fit_tol is None else oracle_fit_tol, fit_max_sweeps=fit_max_sweeps,
+                   seed=seed, init_mode=init_mode, warm_start=warm_start, single_layer=single_layer, shift=shift,
+                   hermitian_basis=oracle_hb, readout_fit_tol=fit_tol)
     gres, ores = [], []
     for _ in range(n_sweeps):
         gres.append(g.sweep(1)[0])

@@ -557,3 +557,90 @@ def test_shifted_obc_partition_geometry_and_loops():
     psi = X.state_vector(T, 4, 4)
     exact = np.array([X.exact_expect(psi, 16, 2, t) for t in terms])
     assert np.max(np.abs(lat.expect(terms) - exact)) < 1e-2
+
+
+# -------------------------------------------------------------------------------------
+# The Hermitian-basis option: the same method after a fixed unitary change of basis on
+# every merged leg (the basis of the library's real-arithmetic paths for complex tensors).
+def _complex_peps(Lx, Ly, D, seed):
+    re = I.uniform_noise_peps(Lx, Ly, 2, D, seed=seed)
+    im = I.uniform_noise_peps(Lx, Ly, 2, D, seed=seed + 100)
+    return [a + 0.4j * (b - 0.5) for a, b in zip(re, im)]
+
+
+def test_hermitian_basis_matrix_and_real_double_layer():
+    """V is unitary and V^T conj(V) = I (every bond keeps its value); the double layer of
+    a complex tensor is real in the basis, and so is E^O for a Hermitian O but not for a
+    non-Hermitian one; transforming the merged legs one by one equals the dense map."""
+    for D in (1, 2, 3, 4):
+        V = ob.hermitian_basis_matrix(D)
+        assert np.allclose(V @ np.conj(V.T), np.eye(D * D), atol=1e-15)
+        assert np.allclose(V.T @ np.conj(V), np.eye(D * D), atol=1e-15)
+        # Hermitian (ket, bra) matrices map to real vectors, anti-Hermitian ones to i * real
+        rng = np.random.default_rng(D)
+        G = rng.standard_normal((D, D)) + 1j * rng.standard_normal((D, D))
+        h = (G + np.conj(G.T)).reshape(-1)
+        assert np.max(np.abs((V @ h).imag)) < 1e-14
+        assert np.max(np.abs((V @ (G - np.conj(G.T)).reshape(-1)).real)) < 1e-14
+    T = _complex_peps(3, 3, 2, seed=41)[4]  # interior site: every leg D = 2
+    E = ob.double_layer(T)
+    Eh = ob.to_hermitian_basis_E(E, T.shape[1:])
+    assert np.max(np.abs(Eh.imag)) < 1e-13 * np.max(np.abs(Eh))
+    V = ob.hermitian_basis_matrix(2)
+    dense = np.einsum("Uu,Ll,Dd,Rr,uldr->ULDR", V, V, np.conj(V), np.conj(V), E, optimize=True)
+    assert np.max(np.abs(Eh - dense)) < 1e-13
+    Eo = ob.to_hermitian_basis_E(ob.double_layer(T, SY), T.shape[1:])
+    assert np.max(np.abs(Eo.imag)) < 1e-13 * np.max(np.abs(Eo))
+    Ep = ob.to_hermitian_basis_E(ob.double_layer(T, (SX + 1j * SY) / 2), T.shape[1:])
+    assert np.max(np.abs(Ep.imag)) > 1e-3 * np.max(np.abs(Ep))
+
+
+def test_hermitian_basis_single_block_and_trees_exact():
+    """In the Hermitian basis a block covering the lattice, and strip blocks (a tree), still
+    give the exact <O> of a complex PEPS, non-Hermitian operators included."""
+    T = _complex_peps(4, 4, 2, seed=23)
+    SP = (SX + 1j * SY) / 2
+    terms = [[(s, SZ)] for s in range(16)] + [[(5, SY)], [(9, SP)], [(10, SY), (11, SY)], [(5, SP), (9, SZ)]]
+    ex = exact_values(T, 4, 4, terms)
+    one = ob.Lattice(4, 4, 2, 2, 4, 4, T, chi=16, chi_exp=64, fit_tol=0.0, fit_max_sweeps=2, hermitian_basis=True)
+    assert np.max(np.abs(one.expect(terms) - ex)) < 1e-12
+    for bx, by in ((4, 1), (2, 4)):
+        lat = ob.Lattice(4, 4, 2, 2, bx, by, T, chi=16, chi_exp=18, fit_tol=0.0, fit_max_sweeps=2,
+                         hermitian_basis=True)
+        assert all(m[0].dtype == np.float64 for m in lat.msgs.values())
+        lat.run(n_sweeps=lat.nbx * lat.nby + 1)
+        assert np.max(np.abs(lat.expect(terms) - ex)) < 1e-11
+
+
+@pytest.mark.parametrize("init_mode", [0, 1])
+def test_hermitian_basis_equals_complex_at_full_rank(init_mode):
+    """At full message rank the fixed point does not depend on how the fits start, so the
+    real-arithmetic run agrees with the complex one: residuals, <O>, and every message
+    equals the complex message mapped by V (conj(V) for messages sent right or down)."""
+    T = _complex_peps(4, 4, 2, seed=21)
+    terms = I.standard_terms(4, 4) + [[(5, SY), (6, SY)], [(9, (SX + 1j * SY) / 2)]]
+    a = ob.Lattice(4, 4, 2, 2, 2, 2, T, chi=16, fit_tol=0.0, fit_max_sweeps=3, seed=7, init_mode=init_mode)
+    b = ob.Lattice(4, 4, 2, 2, 2, 2, T, chi=16, fit_tol=0.0, fit_max_sweeps=3, seed=7, init_mode=init_mode,
+                   hermitian_basis=True)
+    ra = [a.sweep() for _ in range(6)]
+    rb = [b.sweep() for _ in range(6)]
+    assert np.allclose(ra, rb, rtol=1e-6, atol=1e-14)
+    assert np.max(np.abs(a.expect(terms) - b.expect(terms))) < 1e-12
+    for (bi, dr), m in a.msgs.items():
+        mh = ob.to_hermitian_basis_mps(m, 2, conj_basis=dr in (ob.RIGHT, ob.DOWN))
+        assert abs(abs(ob.mps_overlap(b.msgs[(bi, dr)], mh)) - 1.0) < 1e-12
+
+
+def test_fit_sweep_counts():
+    """fit_sweeps[l] sums, over the column fits of sweep l, the fit sweeps each ran: every fit
+    runs fit_max_sweeps when the tolerance is 0, one when any tolerance is met at once, and
+    with the paper's 1e-6 a number in between for each fit (App. A stop rule)."""
+    T = I.uniform_noise_peps(6, 6, 2, 2, seed=3)
+    nfits = 8 * 3  # 8 messages (2x2 blocks of 3x3 sites, 4 interior edges) x 3 frame columns
+    for tol, mx, want in ((0.0, 3, nfits * 3), (10.0, 5, nfits)):
+        lat = ob.Lattice(6, 6, 2, 2, 3, 3, T, chi=4, fit_tol=tol, fit_max_sweeps=mx, seed=2)
+        lat.run(n_sweeps=2)
+        assert lat.fit_sweeps == [want, want]
+    lat = ob.Lattice(6, 6, 2, 2, 3, 3, T, chi=4, fit_tol=1e-6, fit_max_sweeps=10, seed=2)
+    lat.run(n_sweeps=2)
+    assert all(nfits < f < 10 * nfits for f in lat.fit_sweeps), lat.fit_sweeps

@@ -3,12 +3,11 @@
 
 One step = one synchronous blockBP sweep (Eq. 1): every directed block message of
 the lattice recomputed by the zip-up bMPS fits, normalised, and the fixed-point
-residual reduced.  Default workload: the 12x12 PEPS, d=2, D=3, near-product
-tensors, 3x3-site blocks (16 blocks, 48 messages), chi=32, FP32-level contractions on
-TF32 tensor cores (split operands) with FP64 QR/LQ, fit tol 1e-6 / 10 sweeps, residual
-target 1e-8.
+residual reduced.  Default workload: the 32x32 PEPS, d=2, D=5, tensors U[0,1] + 0.1 N(0,1)
+in FP32, 4x4-site blocks (64 blocks, 224 messages), chi=96, split-precision contractions on
+the tensor cores with FP64 QR/LQ, fit tol 1e-6 / 10 sweeps (App. A), warm-started fits.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--prec tf32x3|tf32|bf16|fp64]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--config C] [--prec P]
   python bench.py --impl reference      # the FP64 CPU oracle, same workload
   python bench.py --serve [--requests N] # served mix: Poisson arrivals of whole solves
 
@@ -39,7 +38,8 @@ DFMA_PER_SM_CLK = 2
 FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
 # zip-up fit stop rule (App. A: std/|mean| of the sweep's losses): the paper's 1e-6; the
 # library raises it to the loss noise of TF32 / BF16 contractions on those paths
-FIT_TOL = {"fp64": 1e-6, "tf32": 1e-6, "bf16": 1e-6, "tf32x3": 1e-6}
+FIT_TOL = {"fp64": 1e-6, "tf32": 1e-6, "bf16": 1e-6, "tf32x3": 1e-6, "bf16x3": 1e-6}
+DTYPE = {"tf32": "tf32+f64qr", "bf16": "bf16+f64qr", "tf32x3": "3xtf32+f64qr", "bf16x3": "3xbf16+f64qr", "fp64": "f64"}
 WARM = 1  # each fit starts from its previous-sweep result (identical option in the oracle)
 
 
@@ -132,53 +132,182 @@ def make_lattice(B, cfg, prec, stream):
     return g
 
 
-def oracle_sample(cfg, seconds, warmup=3):
-    """The FP64 oracle as it stands: warm-up sweeps, then sweeps until `seconds` pass."""
+def oracle_lattice(cfg):
     from oracle import blockbp as ob
-    o = ob.Lattice(cfg["Lx"], cfg["Ly"], cfg["d"], cfg["D"], cfg["bx"], cfg["by"],
-                   [np.asarray(t) for t in cfg["tensors"]], boundary=cfg["boundary"], chi=cfg["chi"],
-                   fit_tol=1e-6, fit_max_sweeps=10, seed=1, warm_start=bool(WARM),
-                   single_layer=bool(cfg.get("single_layer", 0)))
-    for _ in range(warmup):
-        o.sweep()
+    return ob.Lattice(cfg["Lx"], cfg["Ly"], cfg["d"], cfg["D"], cfg["bx"], cfg["by"],
+                      [np.asarray(t) for t in cfg["tensors"]], boundary=cfg["boundary"], chi=cfg["chi"],
+                      fit_tol=1e-6, fit_max_sweeps=10, seed=1, warm_start=bool(WARM),
+                      single_layer=bool(cfg.get("single_layer", 0)))
+
+
+def oracle_units(cfg):
+    """Unit of the oracle's timed samples: whole sweeps where one takes seconds, else single
+    messages (a sweep of the 224-message D=5 workload takes the oracle tens of minutes)."""
+    return "message" if cfg["D"] >= 5 else "sweep"
+
+
+def oracle_steps(o, unit, n=None, seconds=None):
+    """Run the oracle as it stands for n units, or until `seconds` pass; returns (units, s).
+    A message unit is one message of the current sweep, in order (Eq. 1 for one block and
+    direction, from the previous sweep's messages)."""
+    keys = sorted(o.msgs)
     t0 = time.perf_counter()
-    n = 0
-    while True:
-        o.sweep()
-        n += 1
-        if time.perf_counter() - t0 > seconds:
-            break
-    dt = time.perf_counter() - t0
-    return n, dt
+    k = 0
+    while (n is not None and k < n) or (seconds is not None and time.perf_counter() - t0 < seconds):
+        if unit == "sweep":
+            o.sweep()
+        else:
+            bi, dr = keys[k % len(keys)]
+            o.compute_message(bi, dr, o.msgs, o.sweeps_done)
+        k += 1
+    return k, time.perf_counter() - t0
+
+
+def oracle_rate(cfg, o, unit, k, dt):
+    """Sweeps per second from k units in dt seconds (a message unit counts 1/messages of a sweep)."""
+    per_sweep = 1 if unit == "sweep" else len(o.msgs)
+    return k / dt / per_sweep
 
 
 def run_reference(args):
-    """The oracle as it stands on the host cores, same workload, same step definition."""
+    """The oracle as it stands on the host cores, same workload and metric.  One step is one
+    sweep, or, on the D=5 workload, one message of a sweep (a bounded sample of the sweep;
+    the rate is scaled by the messages per sweep)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    from oracle import blockbp as ob
     cfg, _ = workload(args.config)
-    o = ob.Lattice(cfg["Lx"], cfg["Ly"], cfg["d"], cfg["D"], cfg["bx"], cfg["by"],
-                   [np.asarray(t) for t in cfg["tensors"]], boundary=cfg["boundary"], chi=cfg["chi"],
-                   fit_tol=1e-6, fit_max_sweeps=10, seed=1, warm_start=bool(WARM),
-                   single_layer=bool(cfg.get("single_layer", 0)))
-    for _ in range(args.warmup):
-        o.sweep()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        o.sweep()
-    dt = time.perf_counter() - t0
-    v = args.steps / dt
+    o = oracle_lattice(cfg)
+    unit = oracle_units(cfg)
+    oracle_steps(o, unit, n=args.warmup)
+    k, dt = oracle_steps(o, unit, n=args.steps)
+    v = oracle_rate(cfg, o, unit, k, dt)
+    sample = (f"{args.steps} sweeps after {args.warmup} warm-up sweeps" if unit == "sweep" else
+              f"{args.steps} messages of the first sweep after {args.warmup} warm-up messages "
+              f"(random fit starts), scaled by the {len(o.msgs)} messages of a sweep")
     out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "sweeps/s", "n_gpus": args.gpus,
-           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / max(args.steps, 1),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": {"workload": cfg["name"], "lattice": f"{cfg['Lx']}x{cfg['Ly']}", "D": cfg["D"],
-                      "chi": cfg["chi"], "block": f"{cfg['bx']}x{cfg['by']}"},
+                      "chi": cfg["chi"], "block": f"{cfg['bx']}x{cfg['by']}", "step": unit},
            "cpu_baseline": {"value": v, "unit": "sweeps/s", "cores": os.cpu_count(), "kind": "oracle",
-                            "sample": f"{args.steps} sweeps after {args.warmup} warm-up sweeps"},
+                            "sample": sample},
            "e2e": {"value": v, "unit": "sweeps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
+
+
+def timed_sweeps(torch, g, stream, flush, steps):
+    """steps sweeps, each bracketed by CUDA events on the library's stream, an L2 flush
+    (a 256 MB write) before each outside the events; per-sweep milliseconds."""
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for k in range(steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(k & 0xFF)
+            ev[k][0].record(stream)
+        g.sweep(1)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in ev]
+
+
+def fit_sweeps_per_column(s0, s1):
+    """Fit sweeps the zip-up fit loops ran per column fit between two stats snapshots
+    (counted on the device)."""
+    loops = s1["fits"] - s0["fits"]
+    return (s1["fit_sweeps"] - s0["fit_sweeps"]) / loops if loops > 0 else None
+
+
+def kernel_roofline(B, g, prec, torch, dev):
+    """Kernel-class replay of one sweep (every fit stage active, CUDA events on the library's
+    stream, bbp_time_kernels); the roofline object of the dominant class."""
+    classes = {}
+    for cls, name in ((0, "tcgen05_gemm"), (1, "fp64_contraction"), (2, "fp64_qr")):
+        ms, n, f, by = C.c_double(), C.c_longlong(), C.c_double(), C.c_double()
+        rc = B.lib().bbp_time_kernels(g.h, cls, 3, C.byref(ms), C.byref(n), C.byref(f), C.byref(by))
+        if rc == 0 and n.value > 0:
+            classes[name] = {"ms": ms.value, "launches": n.value, "flops": f.value, "bytes": by.value}
+    if not classes:
+        return None
+    pk, src = peaks()
+    dom = max(classes, key=lambda k: classes[k]["ms"])
+    c = classes[dom]
+    per_launch_s = c["ms"] / 1e3 / c["launches"]
+    ach = c["flops"] / c["launches"] / per_launch_s / 1e12
+    if dom == "tcgen05_gemm":
+        base = pk["bf16_tflops"]
+        bf = prec in ("bf16", "bf16x3")
+        peak = base if bf else base * NOMINAL_TF32_OVER_BF16
+        bound, note = "tensor", f"of {src} bf16 burst" + ("" if bf else " x nominal tf32/bf16")
+    else:
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        mhz = pk.get("sm_max_mhz", 2070.0)
+        peak = DFMA_PER_SM_CLK * 2 * sms * mhz * 1e6 / 1e12
+        bound, note = "alu", f"of derived FP64 DFMA peak ({DFMA_PER_SM_CLK} DFMA/clk/SM x {sms} SMs x {mhz:.0f} MHz)"
+    traffic = measured_traffic(dom, g, c["launches"])
+    return {"bound": bound, "kernel": dom, "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+            "traffic": traffic["bytes_per_launch"] if traffic else None,
+            "traffic_source": traffic["source"] if traffic else "no ncu capture of the current kernel source",
+            "algorithmic_bytes_per_launch": c["bytes"] / c["launches"], "peak_source": note,
+            "classes_ms_per_sweep": {k: round(v["ms"], 4) for k, v in classes.items()},
+            # TFLOP/s of each class over its replayed launches (split-operand GEMMs counted over
+            # 3K, their MMA work)
+            "classes_tflops": {k: round(v["flops"] / (v["ms"] / 1e3) / 1e12, 4) for k, v in classes.items()
+                               if v["ms"] > 0},
+            "classes_launches_per_sweep": {k: v["launches"] for k, v in classes.items()}}
+
+
+def measured_traffic(cls, g, launches):
+    """DRAM bytes per launch of a kernel class from the committed ncu summary of this workload
+    (profiles/traffic.json: dram__bytes_read.sum + dram__bytes_write.sum over the class's
+    launches of one replayed sweep, with the hash of the kernel source it was taken on).  None
+    once that source has changed, or for another workload."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        rec = json.load(f)
+    e = rec.get(cls)
+    if not e or e.get("workload") != g.workload_name:
+        return None
+    h = hashlib.sha256()
+    for src in e["sources"]:
+        with open(os.path.join(ROOT, src), "rb") as fh:
+            h.update(fh.read())
+    if h.hexdigest()[:16] != e["source_sha16"]:
+        return None
+    return {"bytes_per_launch": e["dram_bytes_per_launch"], "source": e["profile"]}
+
+
+def golden_error(B, cfg, prec, stream, torch):
+    """<O> error against the stored oracle values of the workload's golden case (a smaller
+    lattice at the same D, chi and block, run for the golden's fixed schedule): the chosen
+    precision and the FP64 GPU path, max |d<O>| over the golden's observables."""
+    from paper_2301_05844_gb300 import inputs as I
+    name = cfg.get("golden")
+    if not name:
+        return None
+    with open(os.path.join(ROOT, "tests", "golden", name)) as f:
+        gd = json.load(f)
+    p = gd["params"]
+    T = I.uniform_noise_peps(p["L"], p["L"], p["d"], p["D"], seed=p["seed"], dtype=np.float32)
+    n = p["L"] * p["L"]
+    terms = [[(s, I.SIGMA_Z)] for s in range(n)] + [[(s, I.SIGMA_X)] for s in range(n)]
+    ref = np.array(gd["sz"] + gd["sx"])
+    out = {"workload": f"peps{p['L']}x{p['L']}_D{p['D']}_chi{p['chi']}", "observables": 2 * n,
+           "schedule": f"{p['sweeps']} sweeps, fit tol {p['fit_tol']} / {p['fit_max_sweeps']}, warm start",
+           "max_abs_dO": {}}
+    for pr in (prec, "fp64"):
+        g = B.Lattice(Lx=p["L"], Ly=p["L"], d=p["d"], D=p["D"], bx=p["block"], by=p["block"], chi=p["chi"],
+                      dtype=B.F32, prec=pr, fit_tol=p["fit_tol"], fit_max_sweeps=p["fit_max_sweeps"], seed=p["seed"],
+                      warm_start=int(p["warm_start"]), stream=stream)
+        g.set_tensors(T)
+        g.sweep(p["sweeps"])
+        v = g.expect(terms)
+        out["max_abs_dO"][pr] = float(np.max(np.abs(v.real - ref)))
+        g.close()
+    torch.cuda.synchronize()
+    return out
 
 
 def run_ours(args):
@@ -197,35 +326,29 @@ def run_ours(args):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # 256 MB > 129 MB L2
     cfg, terms = workload(args.config)
     prec = args.prec or cfg.get("prec", "tf32")
+    big = cfg["D"] >= 5  # the 224-message D=5 workload: FP64 arm and read-outs sized down
 
     g = make_lattice(B, cfg, prec, stream.cuda_stream)
+    g.workload_name = cfg["name"]
     g.set_tensors(cfg["tensors"])
     tune = None
     if prec != "fp64" and not args.no_autotune:
+        t0 = time.perf_counter()
         tb, ta, tk = g.autotune(3)
         tune = {"ms_per_sweep_default_tiles": round(tb, 4), "ms_per_sweep_tuned_tiles": round(ta, 4),
-                "steps_retiled": tk}
+                "steps_retiled": tk, "seconds": round(time.perf_counter() - t0, 1)}
     for _ in range(args.warmup):
         g.sweep(1)
     s0 = g.stats()
-    step_ms = []
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
     with Clocks(local) as clk:
         w0 = time.perf_counter()
-        for k in range(args.steps):
-            with torch.cuda.stream(stream):
-                flush.fill_(k & 0xFF)
-                ev[k][0].record(stream)
-            g.sweep(1)
-            ev[k][1].record(stream)
-        torch.cuda.synchronize()
+        step_ms = timed_sweeps(torch, g, stream, flush, args.steps)
         wall = time.perf_counter() - w0
     if dist:
         dist.barrier()
-    step_ms = [a.elapsed_time(b) for a, b in ev]
     dev_s = sum(step_ms) / 1e3
     s1 = g.stats()
     tmax = R.max_over_ranks(dev_s, device=dev)
@@ -233,91 +356,69 @@ def run_ours(args):
     flops = s1["flops"] - s0["flops"]
     qr_flops = s1["qr_flops"] - s0["qr_flops"]
     kernels = s1["kernels"] - s0["kernels"]
-    # fit sweeps each column's zip-up fit loop ran (device counters), over the timed sweeps
-    loops = s1["fits"] - s0["fits"]
-    fit_sweeps = (s1["fit_sweeps"] - s0["fit_sweeps"]) / loops if loops > 0 else None
-    vals = g.expect(terms) if not args.no_readout else None
+    fit_cols = fit_sweeps_per_column(s0, s1)
+    readout = None
+    vals = None
+    if not args.no_readout:
+        t0 = time.perf_counter()
+        vals = g.expect(terms)
+        readout = {"observables": len(terms), "seconds": time.perf_counter() - t0}
+    roofline = kernel_roofline(B, g, prec, torch, dev)
 
-    # kernel classes of one sweep (every fit stage active), replayed with events
-    classes = {}
-    for cls, name in ((0, "tcgen05_gemm"), (1, "fp64_contraction"), (2, "fp64_qr")):
-        ms, n, f, by = C.c_double(), C.c_longlong(), C.c_double(), C.c_double()
-        rc = B.lib().bbp_time_kernels(g.h, cls, 3, C.byref(ms), C.byref(n), C.byref(f), C.byref(by))
-        if rc == 0 and n.value > 0:
-            classes[name] = {"ms": ms.value, "launches": n.value, "flops": f.value, "bytes": by.value}
-    pk, src = peaks()
-    roofline = None
-    if classes:
-        dom = max(classes, key=lambda k: classes[k]["ms"])
-        c = classes[dom]
-        per_launch_s = c["ms"] / 1e3 / c["launches"]
-        ach = c["flops"] / c["launches"] / per_launch_s / 1e12
-        if dom == "tcgen05_gemm":
-            base = pk["bf16_tflops"]
-            peak = base if prec == "bf16" else base * NOMINAL_TF32_OVER_BF16
-            bound, note = "tensor", f"of {src} bf16 burst" + ("" if prec == "bf16" else " x nominal tf32/bf16")
-        else:
-            sms = torch.cuda.get_device_properties(dev).multi_processor_count
-            mhz = pk.get("sm_max_mhz", 2070.0)
-            peak = DFMA_PER_SM_CLK * 2 * sms * mhz * 1e6 / 1e12
-            bound, note = "alu", f"of derived FP64 DFMA peak ({DFMA_PER_SM_CLK} DFMA/clk/SM x {sms} SMs x {mhz:.0f} MHz)"
-        roofline = {"bound": bound, "kernel": dom, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                    "frac": ach / peak, "traffic": None, "peak_source": note,
-                    "classes_ms_per_sweep": {k: round(v["ms"], 4) for k, v in classes.items()},
-                    # TFLOP/s of each class over its replayed launches (split-TF32 GEMMs counted
-                    # over 3K, their MMA work)
-                    "classes_tflops": {k: round(v["flops"] / (v["ms"] / 1e3) / 1e12, 4) for k, v in classes.items()
-                                       if v["ms"] > 0},
-                    "classes_launches_per_sweep": {k: v["launches"] for k, v in classes.items()}}
-
-    # the plain FP64 GPU path on the same workload, same number of sweeps
+    # the plain FP64 GPU path on the same workload and stop rules (on the D=5 workload one
+    # warm-up and one timed sweep: an FP64 sweep there takes about a minute)
     fp64 = None
     if prec != "fp64" and not args.no_fp64:
         h = make_lattice(B, cfg, "fp64", stream.cuda_stream)
         h.set_tensors(cfg["tensors"])
-        for _ in range(args.warmup):
+        w64 = 1 if big else args.warmup
+        k64 = min(args.steps, args.fp64_steps) if big else args.steps
+        for _ in range(w64):
             h.sweep(1)
         torch.cuda.synchronize()
-        evs = []
-        for k in range(args.steps):
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            with torch.cuda.stream(stream):
-                flush.fill_(k & 0xFF)
-                a.record(stream)
-            h.sweep(1)
-            b.record(stream)
-            evs.append((a, b))
-        torch.cuda.synchronize()
-        t64 = sum(a.elapsed_time(b) for a, b in evs) / 1e3
-        v64 = h.expect(terms) if vals is not None else None
-        fp64 = {"sweeps_per_s": args.steps / t64, "speedup": (args.steps / dev_s) / (args.steps / t64),
-                "max_abs_dO": float(np.max(np.abs(vals - v64))) if vals is not None else None,
-                "observables": len(terms) if vals is not None else 0}
+        t0 = h.stats()
+        ms64 = timed_sweeps(torch, h, stream, flush, k64)
+        t64 = sum(ms64) / 1e3
+        fp64 = {"sweeps_per_s": k64 / t64, "speedup": (args.steps / dev_s) / (k64 / t64), "timed_sweeps": k64,
+                "warmup_sweeps": w64, "fit_sweeps_per_column": fit_sweeps_per_column(t0, h.stats())}
+        if vals is not None and not big:
+            v64 = h.expect(terms)
+            fp64["max_abs_dO"] = float(np.max(np.abs(vals - v64)))
+            fp64["observables"] = len(terms)
         h.close()
 
-    # end to end through the C ABI from host memory: upload, solve to tolerance, read out
+    oracle_err = golden_error(B, cfg, prec, stream.cuda_stream, torch) if not args.no_oracle_error else None
+
+    # end to end through the C ABI: the tensors copied from pinned host memory, the solve run
+    # to tolerance, the read-out copied back; the timed region holds all of it
     e2e = None
     if not args.no_e2e:
-        host = [np.ascontiguousarray(t) for t in cfg["tensors"]]
-        nbytes = sum(t.nbytes for t in host)
+        flat = np.concatenate([np.ascontiguousarray(t).reshape(-1) for t in cfg["tensors"]])
+        pinned = torch.empty(flat.nbytes, dtype=torch.uint8, pin_memory=True)
+        pinned.numpy()[:] = flat.view(np.uint8)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         e = make_lattice(B, cfg, prec, stream.cuda_stream)
-        e.set_tensors(host)
+        e.set_tensors(host_ptr=pinned.data_ptr())
         r, k, _ = e.sweep(0)
-        out = e.expect(terms)
+        out = e.expect(terms) if not args.no_readout else None
         torch.cuda.synchronize()
         te = time.perf_counter() - t0
-        e2e = {"value": k / te, "unit": "sweeps/s", "h2d_bytes_per_step": nbytes / max(k, 1),
-               "d2h_bytes_per_step": (8 * k + 16 * len(terms)) / max(k, 1), "sweeps_to_tol": k,
-               "final_residual": r, "solve_s": te, "includes": "create+plan+graph capture, upload, sweeps, read-out"}
+        e2e = {"value": k / te, "unit": "sweeps/s", "h2d_bytes_per_step": flat.nbytes / max(k, 1),
+               "d2h_bytes_per_step": (8 * k + (16 * len(terms) if out is not None else 0)) / max(k, 1),
+               "sweeps_to_tol": k, "final_residual": r, "solve_s": te, "host_memory": "pinned",
+               "includes": "create+plan+graph capture, upload, sweeps to tolerance, read-out"}
         e.close()
 
     cpu = None
     if rank == 0 and not args.no_cpu:
-        n, dt = oracle_sample(cfg, args.cpu_seconds, min(3, args.warmup))
-        cpu = {"value": n / dt, "unit": "sweeps/s", "cores": os.cpu_count(), "kind": "oracle",
-               "sample": f"{n} oracle sweeps of the same workload after {min(3, args.warmup)} warm-up sweeps ({dt:.1f} s)"}
+        o = oracle_lattice(cfg)
+        unit = oracle_units(cfg)
+        k, dt = oracle_steps(o, unit, seconds=args.cpu_seconds)
+        cpu = {"value": oracle_rate(cfg, o, unit, k, dt), "unit": "sweeps/s", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": (f"{k} oracle sweeps of the same workload ({dt:.1f} s)" if unit == "sweep" else
+                          f"{k} of the {len(o.msgs)} messages of the first oracle sweep of the same workload "
+                          f"(random fit starts, {dt:.1f} s), scaled to sweeps")}
 
     lat = sorted(step_ms)
     p50 = lat[len(lat) // 2]
@@ -325,19 +426,19 @@ def run_ours(args):
     if rank == 0:
         out = {"metric": METRIC, "value": value, "unit": "sweeps/s", "n_gpus": world, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": 1e3 * tmax / args.steps, "higher_is_better": True,
-               "scaling": "weak", "vs_baseline": None, "dtype": {"tf32": "tf32+f64qr", "bf16": "bf16+f64qr",
-                                                                "tf32x3": "3xtf32+f64qr", "fp64": "f64"}[prec],
+               "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[prec],
                "data": "synthetic", "config": {"workload": cfg["name"], "lattice": f"{cfg['Lx']}x{cfg['Ly']}",
                                               "d": cfg["d"], "D": cfg["D"], "chi": cfg["chi"],
                                               "block": f"{cfg['bx']}x{cfg['by']}",
                                               "messages": 2 * ((cfg["Lx"] // cfg["bx"] - 1) * (cfg["Ly"] // cfg["by"]) + (cfg["Ly"] // cfg["by"] - 1) * (cfg["Lx"] // cfg["bx"])) if cfg["boundary"] == "obc" else 4,
                                               "network": "single-layer" if cfg.get("single_layer") else "double-layer",
+                                              "fit_tol": FIT_TOL[prec], "fit_max_sweeps": 10,
                                               "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{world}"},
                "tflops": flops / dev_s / 1e12, "fp64_qr_gflops": qr_flops / dev_s / 1e9,
-               "gpu_launches": kernels, "fit_sweeps_per_column": fit_sweeps,
+               "gpu_launches": kernels, "fit_sweeps_per_column": fit_cols,
                "latency_ms": {"p50": p50, "p99": p99}, "wall_s": wall,
-               "fp64_path": fp64, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(),
-               "autotune": tune}
+               "fp64_path": fp64, "oracle_error": oracle_err, "readout": readout, "roofline": roofline,
+               "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(), "autotune": tune}
         print(json.dumps(out), flush=True)
     g.close()
     if dist:
@@ -455,14 +556,16 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", type=int, default=2)
-    ap.add_argument("--prec", default=None, choices=[None, "fp64", "tf32", "bf16", "tf32x3"])
-    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--config", type=int, default=4)
+    ap.add_argument("--prec", default=None, choices=[None, "fp64", "tf32", "bf16", "tf32x3", "bf16x3"])
+    ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-readout", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--no-oracle-error", action="store_true")
+    ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--serve", action="store_true")
     ap.add_argument("--requests", type=int, default=24)
     ap.add_argument("--seed", type=int, default=5)

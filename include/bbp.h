@@ -81,9 +81,9 @@ typedef struct {
     int max_sweeps;          /* cap on sweeps when running to tolerance (10) */
     int stop_relative;       /* 0: residual < tol (main text); 1: r_l / r_1 < tol (App. A) */
     double fit_tol;          /* zip-up fit: std/|mean| of -||Yt||^2 over a sweep (App. A: 1e-6);
-                                on the TF32 / BF16 / BF16X3 paths at least 3e-3 / 3e-2 / 3e-5,
-                                the noise of a loss computed in that precision (TF32X3 and
-                                FP64: as given) */
+                                on the TF32 / BF16 / split (TF32X3, BF16X3) paths at least
+                                3e-3 / 3e-2 / 3e-5, the noise of a loss computed with FP32
+                                accumulation of contractions in that precision (FP64: as given) */
     int fit_max_sweeps;      /* zip-up fit sweep cap (App. A: 10) */
     unsigned long long seed; /* counter-based generator key (fit initial states, init_mode 1) */
     int init_mode;           /* 0: identity-product messages; 1: random MPDO (App. A) */

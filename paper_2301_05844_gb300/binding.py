@@ -222,11 +222,14 @@ class Lattice:
         except Exception:
             pass
 
-    def set_tensors(self, tensors=None, device_ptr=None):
+    def set_tensors(self, tensors=None, device_ptr=None, host_ptr=None):
         """tensors: list of numpy arrays T[p,u,l,d,r] (E[u,l,d,r] on a single-layer network;
-        cast to the desc dtype), or device_ptr: address of the same data already on the GPU."""
+        cast to the desc dtype); or device_ptr / host_ptr: the address of the same data,
+        already in the desc dtype and concatenated, on the GPU / in (pinned) host memory."""
         if device_ptr is not None:
             return _check(lib().bbp_set_tensors(self.h, C.c_void_p(device_ptr), 1))
+        if host_ptr is not None:
+            return _check(lib().bbp_set_tensors(self.h, C.c_void_p(host_ptr), 0))
         flat = _flat_tensors(tensors, self.desc.dtype)
         self._host = flat
         return _check(lib().bbp_set_tensors(self.h, flat.ctypes.data_as(C.c_void_p), 0))

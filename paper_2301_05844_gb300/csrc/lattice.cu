@@ -407,13 +407,16 @@ int plan_column_sweeps(bbp_lattice* L, Program& pr, std::vector<ColumnSweep>& cs
 // Lower bound on the zip-up fit tolerance of a precision.  The stop rule compares
 // std/|mean| of a sweep's losses (App. A); a loss computed from plain TF32 / BF16
 // contractions carries relative noise near 1e-3 / 1e-2, below which the rule never fires,
-// so those paths raise the tolerance to 3e-3 / 3e-2.  The split paths carry FP32-level
-// (TF32X3) and 16-bit (BF16X3) operands, whose loss noise sits below the paper's 1e-6
-// (TF32X3) or near 1e-5 (BF16X3): no floor, and 3e-5.
+// so those paths raise the tolerance to 3e-3 / 3e-2.  The split paths (TF32X3, BF16X3)
+// accumulate products of long contractions in FP32 (K up to 3 x 2400 at D=5, chi=96), whose
+// rounding leaves relative loss noise of order 2^-24 sqrt(K), about 5e-6 there: both take
+// 3e-5 (at 1e-6, and for TF32X3 at 1e-5, some fits of the D=5, chi=96 lattices ran to the
+// sweep cap).
 double bbp::fit_tol_floor(int prec) {
     switch (prec) {
         case BBP_PREC_TF32: return 3e-3;
         case BBP_PREC_BF16: return 3e-2;
+        case BBP_PREC_TF32X3:
         case BBP_PREC_BF16X3: return 3e-5;
         default: return 0.0;
     }

@@ -121,7 +121,8 @@ def config(k: int) -> dict:
     2: 12x12 OBC, d=2, D=3, near-product (+0.05N), 3x3 blocks, chi=32, residual 1e-8; FP32-level
        contractions on TF32 tensor cores (split operands, "tf32x3").
     3: infinite 2x2 cell, d=2, D=4, complex64 N(0,1)/sqrt(D), 4x4 block, chi=64, BF16.
-    4: 32x32 OBC, d=2, D=5, U[0,1]+0.1N as float32, 4x4 blocks, chi=96, TF32.
+    4: 32x32 OBC, d=2, D=5, U[0,1]+0.1N as float32, 4x4 blocks, chi=96, split-BF16 contractions
+       ("bf16x3"), FP64 truncation.
     6: 20x20 OBC, d=2, D=4, U[0,1]+0.1N, 4x4 blocks (80 messages), chi=64, BF16 -- the
        tensor-core measurement workload (D=4, chi=64 contractions over >= 64 messages).
     7: the infinite classical 2D Ising model at beta = 0.6 as its own single-layer network
@@ -139,9 +140,10 @@ def config(k: int) -> dict:
         return dict(name="ipeps2x2_D4_chi64_bf16", Lx=2, Ly=2, d=2, D=4, bx=4, by=4, chi=64,
                     boundary="infinite", tensors=complex_normal_cell(2, 2, 2, 4, seed=3), prec="bf16")
     if k == 4:
-        return dict(name="peps32x32_D5_chi96_tf32", Lx=32, Ly=32, d=2, D=5, bx=4, by=4, chi=96,
+        # golden: the oracle's values on an 8x8 lattice at the same D, chi and blocks
+        return dict(name="peps32x32_D5_chi96", Lx=32, Ly=32, d=2, D=5, bx=4, by=4, chi=96,
                     boundary="obc", tensors=uniform_noise_peps(32, 32, 2, 5, seed=4, dtype=np.float32),
-                    prec="tf32")
+                    prec="bf16x3", golden="d5_chi96_8x8.json")
     if k == 6:
         # tensor-core measurement workload: D=4, chi=64 contractions batched over 80 messages
         return dict(name="peps20x20_D4_chi64_bf16", Lx=20, Ly=20, d=2, D=4, bx=4, by=4, chi=64,

@@ -1,5 +1,6 @@
 """bench.py's reference arm runs on the host: the FP64 oracle on the bench workload, one
-JSON line with the fields the benchmark contract names (a short run)."""
+JSON line with the fields the benchmark contract names (a short run: one step, which on the
+default D=5 workload is one message of a sweep, scaled to sweeps)."""
 import json
 import os
 import subprocess
@@ -22,4 +23,4 @@ def test_reference_arm_prints_one_json_line():
     assert d["higher_is_better"] is True and d["steps"] == 1 and d["warmup"] == 0
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
-    assert d["config"]["workload"] == "peps12x12_D3_chi32"
+    assert d["config"]["workload"] == "peps32x32_D5_chi96" and d["config"]["step"] == "message"

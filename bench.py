@@ -211,10 +211,17 @@ def timed_sweeps(torch, g, stream, flush, steps):
 
 
 def fit_sweeps_per_column(s0, s1):
-    """Fit sweeps the zip-up fit loops ran per column fit between two stats snapshots
-    (counted on the device)."""
+    """Fit sweeps the zip-up fits ran per column fit between two stats snapshots (counted
+    on the device)."""
     loops = s1["fits"] - s0["fits"]
     return (s1["fit_sweeps"] - s0["fit_sweeps"]) / loops if loops > 0 else None
+
+
+def loop_iters_per_sweep(s0, s1):
+    """Iterations the lockstep fit loops ran per message sweep (each loop runs until every fit
+    of its group has met the stop rule; the fits that have skip their work)."""
+    n = s1["sweeps"] - s0["sweeps"]
+    return (s1["fit_loop_iters"] - s0["fit_loop_iters"]) / n if n > 0 else None
 
 
 def kernel_roofline(B, g, prec, torch, dev):
@@ -332,13 +339,17 @@ def run_ours(args):
     g.workload_name = cfg["name"]
     g.set_tensors(cfg["tensors"])
     tune = None
-    if prec != "fp64" and not args.no_autotune:
+    if prec != "fp64" and not args.no_autotune and not big:  # at D=5 it retiles for ~1% in ~2 min
         t0 = time.perf_counter()
         tb, ta, tk = g.autotune(3)
         tune = {"ms_per_sweep_default_tiles": round(tb, 4), "ms_per_sweep_tuned_tiles": round(ta, 4),
                 "steps_retiled": tk, "seconds": round(time.perf_counter() - t0, 1)}
+    # warm-up sweeps 1..W, timed one by one (sweep 2 is the FP64 arm's reference on the D=5 workload)
+    warm_ms, warm_fit = [], []
     for _ in range(args.warmup):
-        g.sweep(1)
+        a = g.stats()
+        warm_ms += timed_sweeps(torch, g, stream, flush, 1)
+        warm_fit.append(fit_sweeps_per_column(a, g.stats()))
     s0 = g.stats()
     if dist:
         dist.barrier()
@@ -357,6 +368,7 @@ def run_ours(args):
     qr_flops = s1["qr_flops"] - s0["qr_flops"]
     kernels = s1["kernels"] - s0["kernels"]
     fit_cols = fit_sweeps_per_column(s0, s1)
+    loop_iters = loop_iters_per_sweep(s0, s1)
     readout = None
     vals = None
     if not args.no_readout:
@@ -365,22 +377,31 @@ def run_ours(args):
         readout = {"observables": len(terms), "seconds": time.perf_counter() - t0}
     roofline = kernel_roofline(B, g, prec, torch, dev)
 
-    # the plain FP64 GPU path on the same workload and stop rules (on the D=5 workload one
-    # warm-up and one timed sweep: an FP64 sweep there takes about a minute)
+    # the plain FP64 GPU path on the same workload and stop rules.  On the D=5 workload (an
+    # FP64 sweep takes over a minute) it times sweep 2 alone, against the same sweep of the
+    # chosen path (timed during its warm-up): both start from the same messages and draws.
     fp64 = None
     if prec != "fp64" and not args.no_fp64:
         h = make_lattice(B, cfg, "fp64", stream.cuda_stream)
         h.set_tensors(cfg["tensors"])
-        w64 = 1 if big else args.warmup
-        k64 = min(args.steps, args.fp64_steps) if big else args.steps
+        same = big and args.warmup >= 2
+        w64 = 1 if same else args.warmup
+        k64 = 1 if same else args.steps
         for _ in range(w64):
             h.sweep(1)
         torch.cuda.synchronize()
         t0 = h.stats()
         ms64 = timed_sweeps(torch, h, stream, flush, k64)
         t64 = sum(ms64) / 1e3
-        fp64 = {"sweeps_per_s": k64 / t64, "speedup": (args.steps / dev_s) / (k64 / t64), "timed_sweeps": k64,
-                "warmup_sweeps": w64, "fit_sweeps_per_column": fit_sweeps_per_column(t0, h.stats())}
+        t1 = h.stats()
+        ref_s = warm_ms[1] / 1e3 if same else dev_s / args.steps * k64
+        fp64 = {"sweeps_per_s": k64 / t64, "speedup": t64 / ref_s, "timed_sweeps": k64,
+                "compared_sweeps": "sweep 2 of both paths" if same else f"sweeps {args.warmup + 1}-{args.warmup + k64}",
+                "fit_sweeps_per_column": fit_sweeps_per_column(t0, t1),
+                "fit_loop_iters_per_sweep": loop_iters_per_sweep(t0, t1),
+                "tflops": (t1["flops"] - t0["flops"]) / t64 / 1e12}
+        if same:
+            fp64["chosen_path_sweep2"] = {"ms": warm_ms[1], "fit_sweeps_per_column": warm_fit[1]}
         if vals is not None and not big:
             v64 = h.expect(terms)
             fp64["max_abs_dO"] = float(np.max(np.abs(vals - v64)))
@@ -420,6 +441,13 @@ def run_ours(args):
                           f"{k} of the {len(o.msgs)} messages of the first oracle sweep of the same workload "
                           f"(random fit starts, {dt:.1f} s), scaled to sweeps")}
 
+    served = None
+    if rank == 0 and world == 1 and args.serve_requests > 0:
+        r = run_serve(args, requests=args.serve_requests, emit=False)
+        served = {k: r[k] for k in ("value", "unit", "latency_s", "alone_vs_mix", "sweeps", "makespan_s",
+                                    "served_vs_sequential", "saturated")}
+        served["config"] = {k: r["config"][k] for k in ("requests", "arrivals", "prec", "L", "D", "chi")}
+
     lat = sorted(step_ms)
     p50 = lat[len(lat) // 2]
     p99 = lat[min(len(lat) - 1, int(0.99 * len(lat)))]
@@ -435,10 +463,11 @@ def run_ours(args):
                                               "fit_tol": FIT_TOL[prec], "fit_max_sweeps": 10,
                                               "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{world}"},
                "tflops": flops / dev_s / 1e12, "fp64_qr_gflops": qr_flops / dev_s / 1e9,
-               "gpu_launches": kernels, "fit_sweeps_per_column": fit_cols,
+               "gpu_launches": kernels, "fit_sweeps_per_column": fit_cols, "fit_loop_iters_per_sweep": loop_iters,
                "latency_ms": {"p50": p50, "p99": p99}, "wall_s": wall,
                "fp64_path": fp64, "oracle_error": oracle_err, "readout": readout, "roofline": roofline,
-               "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(), "autotune": tune}
+               "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(), "autotune": tune,
+               "served_mix": served}
         print(json.dumps(out), flush=True)
     g.close()
     if dist:
@@ -448,8 +477,8 @@ def run_ours(args):
 def serve_mix(n, seed):
     """Seeded mix of whole solves: L in {6,...,24} (square, OBC), block b in {2,3,4}
     dividing L, D in {2,...,5}, chi in {16,32,64}, tensors U[0,1] + 0.1 N(0,1),
-    BF16 (residual tol 1e-5) or TF32 (tol 1e-6) contractions with FP64 truncation,
-    at most 50 sweeps; read-out <sz> on every site."""
+    split-BF16 (residual tol 1e-5) or split-TF32 (tol 1e-6) contractions with FP64
+    truncation, at most 50 sweeps; read-out <sz> on every site."""
     from paper_2301_05844_gb300 import inputs as I
     rng = np.random.default_rng(seed)
     reqs = []
@@ -458,24 +487,25 @@ def serve_mix(n, seed):
         b = int(rng.choice([x for x in (2, 3, 4) if L % x == 0]))
         D = int(rng.integers(2, 6))
         chi = int(rng.choice([16, 32, 64]))
-        prec = "bf16" if rng.random() < 0.5 else "tf32"
+        prec = "bf16x3" if rng.random() < 0.5 else "tf32x3"
         T = I.uniform_noise_peps(L, L, 2, D, seed=1000 + i)
-        kw = dict(Lx=L, Ly=L, d=2, D=D, bx=b, by=b, chi=chi, prec=prec, tol=1e-5 if prec == "bf16" else 1e-6,
+        kw = dict(Lx=L, Ly=L, d=2, D=D, bx=b, by=b, chi=chi, prec=prec, tol=1e-5 if prec == "bf16x3" else 1e-6,
                   max_sweeps=50, fit_tol=1e-6, fit_max_sweeps=10, seed=i + 1, warm_start=WARM)
         reqs.append((T, [[(s, I.SIGMA_Z)] for s in range(L * L)], kw))
     return reqs
 
 
-def run_serve(args):
+def run_serve(args, requests=None, emit=True):
     """Served mix: every request first solved alone (sequential capacity and the
     reference results), then all of them submitted to the request server with
-    Poisson arrivals at 0.8x the sequential capacity."""
+    Poisson arrivals at 0.8x the sequential capacity.  emit=False returns the record
+    instead of printing it (the compact mix of the default line)."""
     import threading
 
     import torch
     from paper_2301_05844_gb300 import binding as B
     torch.cuda.set_device(0)
-    reqs = serve_mix(args.requests, args.seed)
+    reqs = serve_mix(requests or args.requests, args.seed)
     # warm-up: module load and the first graph capture
     w = B.Lattice(**reqs[0][2])
     w.set_tensors(reqs[0][0])
@@ -534,7 +564,7 @@ def run_serve(args):
                       "L": sorted({kw["Lx"] for _, _, kw in reqs}), "D": sorted({kw["D"] for _, _, kw in reqs}),
                       "chi": sorted({kw["chi"] for _, _, kw in reqs}),
                       "block": sorted({kw["bx"] for _, _, kw in reqs}),
-                      "prec": {p_: sum(kw["prec"] == p_ for _, _, kw in reqs) for p_ in ("bf16", "tf32")},
+                      "prec": {p_: sum(kw["prec"] == p_ for _, _, kw in reqs) for p_ in ("bf16x3", "tf32x3")},
                       "arrivals": f"Poisson, rate 0.8 x sequential capacity = {lam:.3f} req/s",
                       "budget_gb": budget / (1 << 30), "max_active": args.max_active,
                       "largest_footprint_gb": max(feet) / 1e9},
@@ -547,6 +577,8 @@ def run_serve(args):
                          "vs_sequential": (sum(o["sweeps"] for o in bouts) / burst_s) /
                          (sum(a["sweeps"] for a in alone) / solo_s), "max_abs_dO_vs_alone": bdiff},
            "server_stats": st, "clocks": clk.summary()}
+    if not emit:
+        return out
     print(json.dumps(out), flush=True)
 
 
@@ -565,9 +597,10 @@ def main():
     ap.add_argument("--no-readout", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-oracle-error", action="store_true")
-    ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--serve", action="store_true")
     ap.add_argument("--requests", type=int, default=24)
+    ap.add_argument("--serve-requests", type=int, default=24,
+                    help="compact served mix added to the default line (0: none)")
     ap.add_argument("--seed", type=int, default=5)
     ap.add_argument("--serve-gb", type=float, default=64.0)
     ap.add_argument("--max-active", type=int, default=16)

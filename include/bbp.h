@@ -265,10 +265,14 @@ typedef struct {
     int sweeps;              /* message sweeps executed since set_tensors */
     double last_residual;
     double first_residual;
+    long long fit_loop_iters; /* fit sweeps the lockstep fit loops ran: each loop runs until every
+                                fit of its group has met the stop rule (or the cap), the fits
+                                that have met it skipping their work */
 } bbp_stats;
 
 /* Counters since bbp_set_tensors (flops are counted on the host from the planned
- * shapes; fit sweeps and loop iterations are read back from the device). */
+ * shapes, each fit's work times the fit sweeps it ran; fit sweeps and loop iterations
+ * are read back from the device). */
 int bbp_get_stats(bbp_lattice* lat, bbp_stats* out);
 
 /* ---- diagnostics ------------------------------------------------------------------

@@ -48,7 +48,7 @@ class Stats(C.Structure):
     _fields_ = [
         ("flops", C.c_double), ("qr_flops", C.c_double), ("kernels", C.c_longlong),
         ("fit_sweeps", C.c_longlong), ("fits", C.c_longlong), ("sweeps", C.c_int),
-        ("last_residual", C.c_double), ("first_residual", C.c_double),
+        ("last_residual", C.c_double), ("first_residual", C.c_double), ("fit_loop_iters", C.c_longlong),
     ]
 
 

@@ -247,14 +247,22 @@ void Program::gc_step(std::vector<GTask>& ts) {
         const int tiles = (int)(((M + tile - 1) / tile) * ((N + tile - 1) / tile));
         mt = std::max(mt, tiles);
         const double f = 2.0 * (double)M * (double)N * (double)K * (cplx ? 4.0 : 1.0);
-        if (t.active) gated_flops += f;
-        else static_flops += f;
+        count_flops(t.active, f, false);
         gc.push_back(t);
     }
     s.aux = mt;
     s.aux2 = small ? 1 : 0;
     steps.push_back(s);
     ts.clear();
+}
+
+void Program::count_flops(const int* active, double f, bool qr_step) {
+    if (!active) {
+        (qr_step ? static_qr_flops : static_flops) += f;
+        return;
+    }
+    (qr_step ? gated_qr_flops : gated_flops) += f;
+    (qr_step ? fit_qr_flops : fit_flops)[(uintptr_t)active] += f;
 }
 
 void Program::qr_step(std::vector<QRTask>& ts) {
@@ -269,8 +277,7 @@ void Program::qr_step(std::vector<QRTask>& ts) {
         mm = std::max(mm, t.m);
         mn = std::max(mn, (long long)t.m * t.n);
         const double f = (4.0 * t.m * (double)t.n * t.n - 4.0 / 3.0 * (double)t.n * t.n * t.n) * (cplx ? 4.0 : 1.0);
-        if (t.active) gated_qr_flops += f;
-        else static_qr_flops += f;
+        count_flops(t.active, f, true);
         qr.push_back(t);
     }
     s.aux = mm;
@@ -606,6 +613,8 @@ void Program::relocate(char* base, size_t split, char* base2) {
     for (auto& t : rnd) {
         RELOC(t.ptr); RELOC(t.active);
     }
+    if (chk_keys.empty())
+        for (auto& t : chk) chk_keys.push_back((uintptr_t)t.active);
     for (auto& t : chk) {
         RELOC(t.losses); RELOC(t.active); RELOC(t.counter);
     }
@@ -778,6 +787,10 @@ cudaError_t Program::reset_loop_totals(cudaStream_t st) const {
         cudaError_t e = cudaMemsetAsync((char*)p + offsetof(LoopDesc, total), 0, sizeof(int), st);
         if (e != cudaSuccess) return e;
     }
+    for (const auto& t : chk) {  // each fit's count of the fit sweeps it ran
+        cudaError_t e = cudaMemsetAsync(t.counter, 0, sizeof(int), st);
+        if (e != cudaSuccess) return e;
+    }
     return cudaSuccess;
 }
 
@@ -912,7 +925,8 @@ void Program::free_all(cudaStream_t st) {
 
 long long Program::kernel_count() const { return (long long)steps.size(); }
 
-cudaError_t Program::executed(long long runs, long long* launches, double* flops, double* qr_flops) const {
+cudaError_t Program::executed(long long runs, long long* launches, double* flops, double* qr_flops,
+                              long long* loop_iters) const {
     // steps outside loops run once per program run; a loop body runs `total` times
     long long n = 0;
     std::vector<int> totals(loop_ptr.size(), 0);
@@ -934,11 +948,25 @@ cudaError_t Program::executed(long long runs, long long* launches, double* flops
     }
     long long body_runs = 0;
     for (int t : totals) body_runs += t;
-    const double per_loop = loop_ptr.empty() ? 0.0 : (double)body_runs / (double)loop_ptr.size();
     if (launches) *launches = n;
-    // every loop body holds one fit sweep of its group; gated flops are summed over groups
-    if (flops) *flops = runs * static_flops + per_loop * gated_flops;
-    if (qr_flops) *qr_flops = runs * static_qr_flops + per_loop * gated_qr_flops;
+    if (loop_iters) *loop_iters = body_runs;
+    // a fit's gated work is done in the fit sweeps it ran while active (its device counter);
+    // the counters of the check tasks of one fit are the same word, read once
+    double fl = runs * static_flops, qfl = runs * static_qr_flops;
+    std::map<const int*, bool> seen;
+    for (size_t i = 0; i < chk.size() && i < chk_keys.size(); ++i) {
+        if (seen.count(chk[i].counter)) continue;
+        seen[chk[i].counter] = true;
+        int c = 0;
+        cudaError_t e = cudaMemcpy(&c, chk[i].counter, sizeof(int), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return e;
+        auto a = fit_flops.find(chk_keys[i]);
+        auto b = fit_qr_flops.find(chk_keys[i]);
+        if (a != fit_flops.end()) fl += c * a->second;
+        if (b != fit_qr_flops.end()) qfl += c * b->second;
+    }
+    if (flops) *flops = fl;
+    if (qr_flops) *qr_flops = qfl;
     return cudaSuccess;
 }
 

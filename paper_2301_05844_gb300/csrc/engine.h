@@ -2,6 +2,7 @@
 // program is one message sweep (or one read-out), replayed as a CUDA graph.
 #pragma once
 
+#include <map>
 #include <string>
 #include <vector>
 
@@ -72,6 +73,11 @@ struct Program {
     int max_qr_m = 0;
     size_t arena_used = 256;  // offset 0 stays unused so that 0 means "no buffer"
     double static_flops = 0, gated_flops = 0, static_qr_flops = 0, gated_qr_flops = 0;
+    // flops of one fit sweep of each fit, keyed by its active flag's arena offset (the value the
+    // task pointers hold before relocation), and that key for each check task
+    std::map<uintptr_t, double> fit_flops, fit_qr_flops;
+    std::vector<uintptr_t> chk_keys;
+    void count_flops(const int* active, double f, bool qr_step);
     cudaGraphExec_t exec = nullptr;
 
     std::vector<std::pair<size_t, size_t>> allocs;  // (byte offset, bytes) of every arena buffer
@@ -115,9 +121,11 @@ struct Program {
     // release the graph and the task descriptors (stream-ordered on st)
     void free_all(cudaStream_t st);
     long long kernel_count() const;
-    // launches and algorithmic flops actually executed over `runs` runs of the program
-    // (loop bodies counted by the iterations the devices ran)
-    cudaError_t executed(long long runs, long long* launches, double* flops, double* qr_flops) const;
+    // launches and algorithmic flops actually executed over `runs` runs of the program (loop
+    // bodies counted by the iterations the device ran; a fit's gated work by the fit sweeps it
+    // ran while active), and the iterations all fit loops ran
+    cudaError_t executed(long long runs, long long* launches, double* flops, double* qr_flops,
+                         long long* loop_iters = nullptr) const;
 };
 
 // warm: the random initial state is drawn only while the sweep counter is 0; later

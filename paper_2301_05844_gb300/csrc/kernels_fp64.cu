@@ -32,6 +32,9 @@ template <> __device__ __forceinline__ double2 zero<double2>() { return make_dou
 template <typename S> __device__ __forceinline__ S one();
 template <> __device__ __forceinline__ double one<double>() { return 1.0; }
 template <> __device__ __forceinline__ double2 one<double2>() { return make_double2(1.0, 0.0); }
+template <typename S> __device__ __forceinline__ S from_real(double x);
+template <> __device__ __forceinline__ double from_real<double>(double x) { return x; }
+template <> __device__ __forceinline__ double2 from_real<double2>(double x) { return make_double2(x, 0.0); }
 __device__ __forceinline__ double add(double a, double b) { return a + b; }
 __device__ __forceinline__ double2 add(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ double sub(double a, double b) { return a - b; }
@@ -304,7 +307,7 @@ cudaError_t launch_gcontract(const GTask* d_tasks, int ntasks, int max_tiles, bo
 }
 
 // ---------------------------------------------------------------- Householder QR / LQ
-// One CTA per task.  Column j: alpha = x_j, x' = x_{j+1..m-1}, nrm = sqrt(|alpha|^2 + ||x'||^2),
+// Column j: alpha = x_j, x' = x_{j+1..m-1}, nrm = sqrt(|alpha|^2 + ||x'||^2),
 // beta_j = -phase(alpha) nrm (no cancellation).  The reflector is kept in the scaled form
 // H_j = I - tau_j v_j v_j^H with v_j = (x - beta_j e_j) / (alpha - beta_j), so v_j[j] = 1,
 // |v_j[i]| <= 1 and tau_j = 1 + |alpha| / nrm in [1, 2]: nothing overflows however small the
@@ -312,153 +315,241 @@ cudaError_t launch_gcontract(const GTask* d_tasks, int ntasks, int max_tiles, bo
 // ~1e-154, which happens to columns beyond the numerical rank).  ||x'|| is accumulated
 // unscaled and recomputed relative to max |x'_i| when the sum is near underflow.  A column
 // with x' = 0 gets H_j = I and beta_j = alpha.
-// Q = H_0 ... H_{n-1} [I; 0], accumulated backwards; finally column j is multiplied
-// by phase(beta_j) so that R_jj = |beta_j| >= 0.
+// Q = H_0 ... H_{n-1} [I; 0]; finally column j is multiplied by phase(beta_j) so that
+// R_jj = |beta_j| >= 0.  (k_qr_wy and k_qr_cluster below.)
 constexpr int QR_MAXN = 512;
-// resident != 0: the working matrix W and Q live in dynamic shared memory (after u),
-// which holds (m + 2*m*n) scalars; otherwise they live in the task's global workspace.
-template <typename S>
-__global__ void __launch_bounds__(256) k_qr(const QRTask* __restrict__ tasks, int resident) {
+constexpr size_t QR_SMEM_LIMIT = 200 * 1024;
+
+// ---------------------------------------------------------------- blocked Householder QR
+// For matrices too large for the cluster QR's shared memory (the (chi K) x chi site matrices
+// at D=5, chi=96: 2400 x 96): one CTA per matrix, the matrix in the task's global workspace,
+// taken in panels of NB columns (LAPACK's blocked Householder QR, in compact WY form):
+//  * the panel (rows p0.., NB columns) is factored in shared memory with the reflectors
+//    described above (scaled form v_j[j] = 1, tau_j in [1, 2]);
+//  * its product H_p0 ... H_p0+nb-1 = I - V T V^H (T upper triangular, T_jj = tau_j,
+//    T[0:j, j] = -tau_j T[0:j, 0:j] V[:, 0:j]^H v_j) is applied to every trailing column c as
+//    c <- c - V (T^H (V^H c)), one column per warp in two passes with nb accumulators per
+//    lane: each trailing column crosses the memory system three times per panel instead of
+//    three times per column, and the FP64 units work on nb independent chains;
+//  * Q = H_0 ... H_{n-1} [I; 0] is accumulated backwards, panel by panel, in place: the
+//    panel's V is staged in shared memory, its columns of W are reset to e_k, and
+//    c <- c - V (T (V^H c)) is applied to the columns k >= p0 (rows < p0 stay zero).
+// Every reflector is the Householder reflector of its column (the one the unblocked order
+// would form), so the result is the same Q up to rounding.  W occupies the first m*n scalars
+// of the workspace, the panels' T the next n*NB.
+template <typename S, int NB>
+__global__ void __launch_bounds__(256) k_qr_wy(const QRTask* __restrict__ tasks) {
     const QRTask& t = tasks[blockIdx.x];
     if (t.active && *t.active == 0) return;
     extern __shared__ __align__(16) unsigned char qr_smem[];
-    // u: two buffers of m entries (the reflector of the current and of the previous column)
-    S* ubuf = (S*)qr_smem;
+    S* P = (S*)qr_smem;  // panel, column c at P + c*m (absolute row index)
     __shared__ S betas[QR_MAXN];
-    __shared__ double coefs[QR_MAXN];
+    __shared__ double taus[QR_MAXN];
+    __shared__ S Ts[NB * NB];  // T of the current panel, Ts[r + c*NB]
+    __shared__ S G[NB * NB];   // V^H V of the panel
     __shared__ double redd[32];
-    __shared__ double next_x2;  // ||x'||^2 of the next column, from the warp that updated it
     const int m = t.m, n = t.n, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    S* W = resident ? ubuf + 2 * m : (S*)t.work;
-    S* Q = W + (size_t)m * n;
+    S* W = (S*)t.work;
+    S* Tg = W + (size_t)m * n;
     const S* in = (const S*)t.in;
-    S* out = (S*)t.out;
     double ss = 0.0;
     for (long long idx = tid; idx < (long long)m * n; idx += 256) {
         const int i = (int)(idx % m), j = (int)(idx / m);
         const long long src = (long long)i * t.in_rs + (long long)j * t.in_cs;
-        S v;
-        if (t.in_float) v = from_float<S>(((const float*)t.in), src);
-        else v = in[src];
+        S v = t.in_float ? from_float<S>(((const float*)t.in), src) : in[src];
         if (t.conj_io) v = conjv(v);
         W[(size_t)j * m + i] = v;
         ss += abs2(v);
     }
     ss = block_sum(ss, redd);
     if (tid == 0 && t.loss) *t.loss = -ss;
-    bool fused = false;  // next_x2 holds the sub-diagonal norm of column j (uniform)
-    for (int j = 0; j < n; ++j) {
-        S* col = W + (size_t)j * m;
-        S* u = ubuf + (size_t)(j & 1) * m;
-        double xs2;
-        if (fused) {
-            xs2 = next_x2;
-        } else {
-            xs2 = 0.0;
+    __syncthreads();
+    // ---- factorization
+    for (int p0 = 0; p0 < n; p0 += NB) {
+        const int pw = min(NB, n - p0), rows = m - p0;
+        for (int idx = tid; idx < pw * rows; idx += 256) {
+            const int c = idx / rows, i = p0 + (idx - c * rows);
+            P[(size_t)c * m + i] = W[(size_t)(p0 + c) * m + i];
+        }
+        __syncthreads();
+        for (int c = 0; c < pw; ++c) {
+            const int j = p0 + c;
+            S* col = P + (size_t)c * m;
+            double xs2 = 0.0;
             for (int i = j + 1 + tid; i < m; i += 256) xs2 += abs2(col[i]);
             xs2 = block_sum(xs2, redd);
-        }
-        double xnorm = sqrt(xs2);
-        if (xs2 < 1e-280) {  // near underflow (uniform branch): rescale by max |x'_i|
-            double amax = 0.0;
-            for (int i = j + 1 + tid; i < m; i += 256) amax = fmax(amax, absv(col[i]));
-            amax = block_max(amax, redd);
-            double t2 = 0.0;
-            if (amax > 0.0)
-                for (int i = j + 1 + tid; i < m; i += 256) t2 += abs2(divr(col[i], amax));
-            t2 = block_sum(t2, redd);
-            xnorm = amax > 0.0 ? amax * sqrt(t2) : 0.0;
-        }
-        const S alpha = col[j];
-        const double aa = absv(alpha);
-        S beta = alpha;
-        double tau = 0.0;
-        if (xnorm > 0.0) {
-            const double nrm = hypot(aa, xnorm);
-            const S ph = aa > 0.0 ? divr(alpha, aa) : one<S>();
-            beta = scal(ph, -nrm);
-            tau = 1.0 + aa / nrm;
-            const double den = aa + nrm;  // |alpha - beta|
-            const S cph = conjv(ph);
-            if (den > 1e-290) {
-                const S sc = scal(cph, 1.0 / den);
-                for (int i = j + 1 + tid; i < m; i += 256) {
-                    const S v = mul(col[i], sc);
-                    u[i] = v;
-                    col[i] = v;  // rows below the diagonal: nobody else reads them in this step
-                }
-            } else {
-                for (int i = j + 1 + tid; i < m; i += 256) {
-                    const S v = divr(mul(col[i], cph), den);
-                    u[i] = v;
-                    col[i] = v;
-                }
+            double xnorm = sqrt(xs2);
+            if (xs2 < 1e-280) {  // near underflow (uniform branch): rescale by max |x'_i|
+                double amax = 0.0;
+                for (int i = j + 1 + tid; i < m; i += 256) amax = fmax(amax, absv(col[i]));
+                amax = block_max(amax, redd);
+                double t2 = 0.0;
+                if (amax > 0.0)
+                    for (int i = j + 1 + tid; i < m; i += 256) t2 += abs2(divr(col[i], amax));
+                t2 = block_sum(t2, redd);
+                xnorm = amax > 0.0 ? amax * sqrt(t2) : 0.0;
             }
-            if (tid == 0) u[j] = one<S>();
-        }
-        if (tid == 0) {
-            betas[j] = beta;
-            coefs[j] = tau;
-        }
-        __syncthreads();  // u complete; every thread has read alpha
-        fused = false;
-        if (tau != 0.0) {
-            if (tid == 0) col[j] = one<S>();
-            for (int k = j + 1 + warp; k < n; k += 8) {
-                S* ck = W + (size_t)k * m;
-                S dot = zero<S>();
-                for (int i = j + lane; i < m; i += 32) mac(dot, conjv(u[i]), ck[i]);
-                dot = warp_sum(dot);
-                const S f = scal(dot, -tau);
-                if (k == j + 1) {  // the next column: also its norm below the next diagonal
-                    double nx = 0.0;
-                    for (int i = j + lane; i < m; i += 32) {
-                        S c = ck[i];
-                        mac(c, u[i], f);
-                        ck[i] = c;
-                        if (i > k) nx += abs2(c);
-                    }
-                    nx = warp_sum(nx);
-                    if (lane == 0) next_x2 = nx;
+            const S alpha = col[j];
+            const double aa = absv(alpha);
+            S beta = alpha;
+            double tau = 0.0;
+            if (xnorm > 0.0) {
+                const double nrm = hypot(aa, xnorm);
+                const S ph = aa > 0.0 ? divr(alpha, aa) : one<S>();
+                beta = scal(ph, -nrm);
+                tau = 1.0 + aa / nrm;
+                const double den = aa + nrm;  // |alpha - beta|
+                const S cph = conjv(ph);
+                if (den > 1e-290) {
+                    const S sc = scal(cph, 1.0 / den);
+                    for (int i = j + 1 + tid; i < m; i += 256) col[i] = mul(col[i], sc);
                 } else {
-                    for (int i = j + lane; i < m; i += 32) mac(ck[i], u[i], f);
+                    for (int i = j + 1 + tid; i < m; i += 256) col[i] = divr(mul(col[i], cph), den);
                 }
             }
-            fused = j + 1 < n;
+            __syncthreads();  // every thread has read alpha
+            if (tid == 0) {
+                betas[j] = beta;
+                taus[j] = tau;
+                col[j] = one<S>();  // v_j[j] = 1 (with tau = 0 the reflector is the identity)
+            }
+            for (int i = p0 + tid; i < j; i += 256) col[i] = zero<S>();  // V is zero above its diagonal
+            __syncthreads();
+            if (tau != 0.0) {  // H_j on the panel's later columns, one warp each
+                for (int k = c + 1 + warp; k < pw; k += 8) {
+                    S* ck = P + (size_t)k * m;
+                    S d0 = zero<S>(), d1 = zero<S>();
+                    int i = j + lane;
+                    for (; i + 32 < m; i += 64) {
+                        mac(d0, conjv(col[i]), ck[i]);
+                        mac(d1, conjv(col[i + 32]), ck[i + 32]);
+                    }
+                    if (i < m) mac(d0, conjv(col[i]), ck[i]);
+                    const S f = scal(warp_sum(add(d0, d1)), -tau);
+                    for (int r = j + lane; r < m; r += 32) mac(ck[r], col[r], f);
+                }
+            }
             __syncthreads();
         }
-    }
-    for (long long idx = tid; idx < (long long)m * n; idx += 256) {
-        const int i = (int)(idx % m), k = (int)(idx / m);
-        Q[(size_t)k * m + i] = (i == k) ? one<S>() : zero<S>();
-    }
-    __syncthreads();
-    for (int j = n - 1; j >= 0; --j) {
-        const double coef = coefs[j];
-        if (coef == 0.0) continue;
-        const S* uj = W + (size_t)j * m;  // v_j with v_j[j] = 1
-        const S* v = uj;
-        if (!resident) {  // stage v_j in shared memory
-            S* u = ubuf + (size_t)(j & 1) * m;
-            for (int i = j + tid; i < m; i += 256) u[i] = uj[i];
-            __syncthreads();
-            v = u;
+        // T of the panel: G = V^H V (columns r < c), then T column by column
+        for (int pr = warp; pr < pw * pw; pr += 8) {
+            const int r = pr / pw, c = pr - r * pw;
+            if (r >= c) continue;
+            const S* vr = P + (size_t)r * m;
+            const S* vc = P + (size_t)c * m;
+            S d = zero<S>();
+            for (int i = p0 + c + lane; i < m; i += 32) mac(d, conjv(vr[i]), vc[i]);  // v_c is zero above row p0+c
+            d = warp_sum(d);
+            if (lane == 0) G[r + c * NB] = d;
         }
-        for (int k = j + warp; k < n; k += 8) {
-            S* qk = Q + (size_t)k * m;
-            S dot = zero<S>();
-            for (int i = j + lane; i < m; i += 32) mac(dot, conjv(v[i]), qk[i]);
-            dot = warp_sum(dot);
-            const S f = scal(dot, -coef);
-            for (int i = j + lane; i < m; i += 32) mac(qk[i], v[i], f);
+        __syncthreads();
+        if (tid == 0) {
+            for (int c = 0; c < pw; ++c) {
+                const double tc = taus[p0 + c];
+                for (int r = 0; r < c; ++r) {
+                    S acc = zero<S>();
+                    for (int q = r; q < c; ++q) mac(acc, Ts[r + q * NB], G[q + c * NB]);
+                    Ts[r + c * NB] = scal(acc, -tc);
+                }
+                Ts[c + c * NB] = from_real<S>(tc);
+                for (int r = c + 1; r < NB; ++r) Ts[r + c * NB] = zero<S>();
+            }
+            for (int c = pw; c < NB; ++c)
+                for (int r = 0; r < NB; ++r) Ts[r + c * NB] = zero<S>();
+        }
+        __syncthreads();
+        for (int idx = tid; idx < NB * NB; idx += 256) Tg[(size_t)p0 * NB + idx] = Ts[idx];
+        // trailing columns: c <- c - V (T^H (V^H c)), one column per warp
+        for (int k = p0 + pw + warp; k < n; k += 8) {
+            S* ck = W + (size_t)k * m;
+            S acc[NB];
+#pragma unroll
+            for (int r = 0; r < NB; ++r) acc[r] = zero<S>();
+            for (int i = p0 + lane; i < m; i += 32) {
+                const S x = ck[i];
+#pragma unroll
+                for (int r = 0; r < NB; ++r)
+                    if (r < pw) mac(acc[r], conjv(P[(size_t)r * m + i]), x);
+            }
+#pragma unroll
+            for (int r = 0; r < NB; ++r) acc[r] = warp_sum(acc[r]);
+            S wv[NB];
+#pragma unroll
+            for (int r = 0; r < NB; ++r) {
+                S a = zero<S>();
+#pragma unroll
+                for (int q = 0; q < NB; ++q)
+                    if (q <= r) mac(a, conjv(Ts[q + r * NB]), acc[q]);  // (T^H w)_r
+                wv[r] = scal(a, -1.0);
+            }
+            for (int i = p0 + lane; i < m; i += 32) {
+                S x = ck[i];
+#pragma unroll
+                for (int r = 0; r < NB; ++r)
+                    if (r < pw) mac(x, P[(size_t)r * m + i], wv[r]);
+                ck[i] = x;
+            }
+        }
+        // the panel's reflectors back to W (read again by the Q phase)
+        for (int idx = tid; idx < pw * rows; idx += 256) {
+            const int c = idx / rows, i = p0 + (idx - c * rows);
+            W[(size_t)(p0 + c) * m + i] = P[(size_t)c * m + i];
         }
         __syncthreads();
     }
+    // ---- Q, backwards over the panels, in place
+    for (int p0 = ((n - 1) / NB) * NB; p0 >= 0; p0 -= NB) {
+        const int pw = min(NB, n - p0), rows = m - p0;
+        for (int idx = tid; idx < pw * rows; idx += 256) {
+            const int c = idx / rows, i = p0 + (idx - c * rows);
+            P[(size_t)c * m + i] = W[(size_t)(p0 + c) * m + i];
+        }
+        for (int idx = tid; idx < NB * NB; idx += 256) Ts[idx] = Tg[(size_t)p0 * NB + idx];
+        __syncthreads();
+        for (int idx = tid; idx < pw * m; idx += 256) {  // columns p0.. of the panel start as e_k
+            const int c = idx / m, i = idx - c * m;
+            W[(size_t)(p0 + c) * m + i] = i == p0 + c ? one<S>() : zero<S>();
+        }
+        __syncthreads();
+        for (int k = p0 + warp; k < n; k += 8) {
+            S* ck = W + (size_t)k * m;
+            S acc[NB];
+#pragma unroll
+            for (int r = 0; r < NB; ++r) acc[r] = zero<S>();
+            for (int i = p0 + lane; i < m; i += 32) {
+                const S x = ck[i];
+#pragma unroll
+                for (int r = 0; r < NB; ++r)
+                    if (r < pw) mac(acc[r], conjv(P[(size_t)r * m + i]), x);
+            }
+#pragma unroll
+            for (int r = 0; r < NB; ++r) acc[r] = warp_sum(acc[r]);
+            S wv[NB];
+#pragma unroll
+            for (int r = 0; r < NB; ++r) {
+                S a = zero<S>();
+#pragma unroll
+                for (int q = 0; q < NB; ++q)
+                    if (q >= r && q < pw) mac(a, Ts[r + q * NB], acc[q]);  // (T w)_r
+                wv[r] = scal(a, -1.0);
+            }
+            for (int i = p0 + lane; i < m; i += 32) {
+                S x = ck[i];
+#pragma unroll
+                for (int r = 0; r < NB; ++r)
+                    if (r < pw) mac(x, P[(size_t)r * m + i], wv[r]);
+                ck[i] = x;
+            }
+        }
+        __syncthreads();
+    }
+    // ---- output: column k times phase(beta_k), so that R_kk = |beta_k| >= 0
+    S* out = (S*)t.out;
     for (long long idx = tid; idx < (long long)m * n; idx += 256) {
         const int i = (int)(idx % m), k = (int)(idx / m);
         const double bb = absv(betas[k]);
         const S ph = bb > 0.0 ? divr(betas[k], bb) : one<S>();
-        S v = mul(Q[(size_t)k * m + i], ph);
+        S v = mul(W[(size_t)k * m + i], ph);
         if (t.conj_io) v = conjv(v);
         out[(long long)i * t.out_rs + (long long)k * t.out_cs] = v;
         if (t.out2) {
@@ -469,7 +560,13 @@ __global__ void __launch_bounds__(256) k_qr(const QRTask* __restrict__ tasks, in
     }
 }
 
-constexpr size_t QR_SMEM_LIMIT = 200 * 1024;
+// Panel width of the blocked QR: the widest of 16, 8, 4, 2, 1 whose panel (nb x m scalars)
+// fits QR_SMEM_LIMIT.
+static int qr_wy_nb(int max_m, size_t ss) {
+    int nb = 16;
+    while (nb > 1 && (size_t)nb * max_m * ss > QR_SMEM_LIMIT) nb >>= 1;
+    return nb;
+}
 
 // The QR with one task spread over a thread-block cluster of C CTAs (1 <= C <= 8), W and Q
 // in shared memory.  On GB300 every warp-wide FP64 instruction occupies its SM sub-partition's
@@ -528,9 +625,6 @@ __device__ __forceinline__ double flip(double x, bool neg) {
 __device__ __forceinline__ double phase_of(double a, double aa) { return aa > 0.0 && a < 0.0 ? -1.0 : 1.0; }
 __device__ __forceinline__ double2 phase_of(double2 a, double aa) { return aa > 0.0 ? divr(a, aa) : one<double2>(); }
 __device__ __forceinline__ double apply_phase(double x, double ph) { return flip(x, ph < 0.0); }
-template <typename S> __device__ __forceinline__ S from_real(double x);
-template <> __device__ __forceinline__ double from_real<double>(double x) { return x; }
-template <> __device__ __forceinline__ double2 from_real<double2>(double x) { return make_double2(x, 0.0); }
 __device__ __forceinline__ double2 apply_phase(double2 x, double2 ph) { return mul(x, ph); }
 
 // 1/sqrt(s), s in [2^-100, 2^100]: the FP32 estimate y (relative error < 2^-21) refined by one
@@ -602,7 +696,7 @@ struct ChainScratch {
 };
 
 // Warps 0-3 of the CTA owning column nxt: if tau != 0, apply H_j (v_j in ub) to column c on
-// rows >= j; then turn c into the scaled reflector v_nxt in place (v_nxt[nxt] = 1; see k_qr
+// rows >= j; then turn c into the scaled reflector v_nxt in place (v_nxt[nxt] = 1; see above
 // for the scaled form) and record tau_nxt, beta_nxt.  Warp w takes the rows
 // base + 32 (4 t + w) + lane, base = j (nxt when there is no H_j).
 template <typename S>
@@ -859,41 +953,38 @@ static size_t qr_cluster_smem(int max_m, long long max_mn, int C, size_t ss) {
     return (2 * (size_t)max_m + 2 * cols) * ss + QR_MAXN * (16 + ss) + 16;
 }
 
-static size_t qr_smem_bytes(int max_m, long long max_mn, bool cplx, int* resident) {
-    const size_t ss = cplx ? sizeof(double2) : sizeof(double);
-    const size_t all = (2 * (size_t)max_m + 2 * (size_t)max_mn) * ss;  // u (two buffers), W, Q
-    *resident = all <= QR_SMEM_LIMIT ? 1 : 0;
-    return *resident ? all : 2 * (size_t)max_m * ss;
-}
-
 cudaError_t qr_prepare(int max_m, bool cplx) {
     static std::mutex mu;  // the request server reads out on a second thread
     std::lock_guard<std::mutex> guard(mu);
     // A kernel attribute applies to the current device only, so the state is kept per device.
-    // The limit only ever grows, so that a smaller request cannot break a larger user; it
-    // covers the shared-memory-resident form up to QR_SMEM_LIMIT as well.
     constexpr int kMaxDev = 64;
-    static size_t limits[kMaxDev][2] = {};
-    static bool cluster_sets[kMaxDev][2] = {};
+    static bool done[kMaxDev][2] = {};
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) return cudaErrorInvalidDevice;
-    size_t* limit = limits[dev];
-    bool* cluster_set = cluster_sets[dev];
-    if (!cluster_set[cplx ? 1 : 0]) {
-        cudaError_t e = cplx ? cudaFuncSetAttribute(k_qr_cluster<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                    (int)QR_CLUSTER_SMEM)
-                             : cudaFuncSetAttribute(k_qr_cluster<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                    (int)QR_CLUSTER_SMEM);
-        if (e != cudaSuccess) return e;
-        cluster_set[cplx ? 1 : 0] = true;
+    if (qr_wy_nb(max_m, cplx ? sizeof(double2) : sizeof(double)) * (size_t)max_m * (cplx ? 16 : 8) > QR_SMEM_LIMIT)
+        return cudaErrorInvalidValue;  // not even one column of this height fits shared memory
+    if (done[dev][cplx ? 1 : 0]) return cudaSuccess;
+    const int lim = (int)QR_SMEM_LIMIT;
+    cudaError_t e;
+    if (cplx) {
+        if ((e = cudaFuncSetAttribute(k_qr_cluster<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)QR_CLUSTER_SMEM)) != cudaSuccess) return e;
+        if ((e = cudaFuncSetAttribute(k_qr_wy<double2, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+        if ((e = cudaFuncSetAttribute(k_qr_wy<double2, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+        if ((e = cudaFuncSetAttribute(k_qr_wy<double2, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+        if ((e = cudaFuncSetAttribute(k_qr_wy<double2, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+        if ((e = cudaFuncSetAttribute(k_qr_wy<double2, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+    } else {
+        if ((e = cudaFuncSetAttribute(k_qr_cluster<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)QR_CLUSTER_SMEM)) != cudaSuccess) return e;
+        if ((e = cudaFuncSetAttribute(k_qr_wy<double, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+        if ((e = cudaFuncSetAttribute(k_qr_wy<double, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+        if ((e = cudaFuncSetAttribute(k_qr_wy<double, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+        if ((e = cudaFuncSetAttribute(k_qr_wy<double, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+        if ((e = cudaFuncSetAttribute(k_qr_wy<double, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
     }
-    const size_t ss = cplx ? sizeof(double2) : sizeof(double);
-    const size_t sm = std::max(2 * (size_t)max_m * ss, QR_SMEM_LIMIT);
-    if (sm <= limit[cplx ? 1 : 0]) return cudaSuccess;
-    cudaError_t e = cplx ? cudaFuncSetAttribute(k_qr<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)
-                         : cudaFuncSetAttribute(k_qr<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e == cudaSuccess) limit[cplx ? 1 : 0] = sm;
-    return e;
+    done[dev][cplx ? 1 : 0] = true;
+    return cudaSuccess;
 }
 
 bool qr_cluster_fits(int max_m, long long max_mn, bool cplx, int C) {
@@ -929,15 +1020,20 @@ cudaError_t launch_qr(const QRTask* d_tasks, int ntasks, int max_m, long long ma
         return cplx ? cudaLaunchKernelEx(&cfg, k_qr_cluster<double2>, d_tasks, C)
                     : cudaLaunchKernelEx(&cfg, k_qr_cluster<double>, d_tasks, C);
     }
-    // too large for the shared memory of a cluster: one CTA per task, W and Q in the task's
-    // global workspace
-    int resident = 0;
-    const size_t sm = qr_smem_bytes(max_m, max_mn, cplx, &resident);
-    if (cplx)
-        k_qr<double2><<<ntasks, 256, sm, s>>>(d_tasks, resident);
-    else
-        k_qr<double><<<ntasks, 256, sm, s>>>(d_tasks, resident);
-    return cudaGetLastError();
+    // too large for the shared memory of a cluster: one CTA per task, the blocked QR with the
+    // matrix in the task's global workspace and a panel of nb columns in shared memory
+    const int nb = qr_wy_nb(max_m, ssz);
+    const size_t sm = (size_t)nb * max_m * ssz;
+    if (sm > QR_SMEM_LIMIT) return cudaErrorInvalidValue;
+#define WY_CASE(NB_)                                                               \
+    if (nb == NB_) {                                                               \
+        if (cplx) k_qr_wy<double2, NB_><<<ntasks, 256, sm, s>>>(d_tasks);          \
+        else k_qr_wy<double, NB_><<<ntasks, 256, sm, s>>>(d_tasks);                \
+        return cudaGetLastError();                                                 \
+    }
+    WY_CASE(16) WY_CASE(8) WY_CASE(4) WY_CASE(2) WY_CASE(1)
+#undef WY_CASE
+    return cudaErrorInvalidValue;
 }
 
 // ---------------------------------------------------------------- random fill

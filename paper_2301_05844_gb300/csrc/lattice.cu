@@ -1203,6 +1203,7 @@ int bbp_autotune(bbp_lattice* L, int reps, double* ms_before, double* ms_after, 
             after += best / reps;
         }
     }
+    CKR(pr.reset_loop_totals(st));  // the timings ran no fit of the solve: statistics restart
     CKR(cudaStreamSynchronize(st));
     int te = 0;
     if (L->mixed) CKR(cudaMemcpy(&te, L->d_tcerr, sizeof(int), cudaMemcpyDeviceToHost));
@@ -1231,7 +1232,9 @@ int bbp_get_stats(bbp_lattice* L, bbp_stats* out) try {
     }
     long long launches = 0;
     double fl = 0, qfl = 0;
-    if (L->sweeps > 0) CKR(pr.executed(L->sweeps, &launches, &fl, &qfl));
+    long long iters = 0;
+    if (L->sweeps > 0) CKR(pr.executed(L->sweeps, &launches, &fl, &qfl, &iters));
+    out->fit_loop_iters = iters;
     out->fit_sweeps = fs;
     out->fits = fits * (long long)L->sweeps;
     out->flops = fl + L->readout_flops;

@@ -117,8 +117,7 @@ void add(Program& pr, const MixCtx& cx, TB& tb, size_t a_off, long long a_rows, 
     s.b_off = b_off; s.b_rows = b_rows; s.b_ld = b_ld;
     tb.ts.push_back(t);
     tb.sp.push_back(s);
-    if (active) pr.gated_flops += alg_flops;
-    else pr.static_flops += alg_flops;
+    pr.count_flops(active, alg_flops, false);
 }
 
 // site dims of fit f at site i

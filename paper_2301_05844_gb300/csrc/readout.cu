@@ -274,11 +274,11 @@ extern "C" int bbp_expect(bbp_lattice* L, const bbp_term* terms, int n_terms, do
             cs.push_back(s);
         }
     }
-    // The environment columns are fits like those of a sweep.  On a split-TF32 lattice they run
-    // on its tensor-core path (FP32-level contractions, FP64 QR, the same fit tolerance);
-    // TF32 / BF16 / split-BF16 lattices keep FP64 fits here, so that the read-out adds no error
-    // of its own at their precision.  The closings and the ratio N_O / N_I are FP64 in every case.
-    const bool tc_env = L->mixed && L->cx.x3 && L->cx.tck == 0;
+    // The environment columns are fits like those of a sweep.  On a split-precision lattice
+    // (TF32X3, BF16X3) they run on its tensor-core path (split contractions, FP64 QR, the same
+    // fit tolerance); plain TF32 / BF16 lattices keep FP64 fits here, so that the read-out adds
+    // no error of its own at their precision.  The closings and N_O / N_I are FP64 in every case.
+    const bool tc_env = L->mixed && L->cx.x3;
     if (tc_env) {
         pr.tc_kind = L->cx.tck;
         pr.tc_err = L->d_tcerr;

@@ -61,8 +61,8 @@ def test_infinite_complex_cell_truncating():
     sequence): FP64 to 1e-10, TF32X3 / BF16X3 to 1e-5, plain TF32 / BF16 to ten times their
     operands' unit roundoff; the oracle's sweeps use the fit tolerance each path raises
     1e-12 to (3e-5 / 3e-3 / 3e-2 for the split paths / TF32 / BF16), its read-out fits the
-    tolerance of the path's read-out fits (3e-5 on the tensor cores for TF32X3, else 1e-12
-    in FP64).  The
+    tolerance of the path's read-out fits (3e-5 on the tensor cores for the split paths, else
+    1e-12 in FP64).  The
     complex oracle's truncated fits start from complex draws and may settle in a different,
     equally valid truncated optimum: FP64 in the Hermitian basis stays within 1e-5 of it
     (measured 3.2e-6)."""
@@ -71,7 +71,7 @@ def test_infinite_complex_cell_truncating():
     terms = [[(5, SZ)], [(6, SX)], [(9, SY)], [(10, SPLUS)], [(5, SZ), (6, SZ)], [(5, SX), (9, SX)],
              [(6, SY), (10, SY)]]
     # (sweep, read-out) fit tolerance of each path when 1e-12 is asked for
-    floor = {"fp64": (1e-12, 1e-12), "tf32x3": (3e-5, 3e-5), "bf16x3": (3e-5, 1e-12), "tf32": (3e-3, 1e-12),
+    floor = {"fp64": (1e-12, 1e-12), "tf32x3": (3e-5, 3e-5), "bf16x3": (3e-5, 3e-5), "tf32": (3e-3, 1e-12),
              "bf16": (3e-2, 1e-12)}
     bound = {"fp64": 1e-10, "tf32x3": 1e-5, "bf16x3": 1e-5, "tf32": 10 * 2.0 ** -11, "bf16": 10 * 2.0 ** -8}
     ref = {}

@@ -17,8 +17,8 @@ SZ, SX = I.SIGMA_Z, I.SIGMA_X
 # bound on max |d<O>| against the oracle, and the fit-tolerance floor of the path
 BOUND = {"tf32x3": 1e-5, "bf16x3": 1e-5, "tf32": 10 * 2.0 ** -11, "bf16": 10 * 2.0 ** -8}
 FLOOR = {"tf32x3": 3e-5, "bf16x3": 3e-5, "tf32": 3e-3, "bf16": 3e-2}
-# the read-out's environment fits run on the tensor cores (with the floor) only for TF32X3
-RO_FLOOR = {"tf32x3": 3e-5, "bf16x3": 0.0, "tf32": 0.0, "bf16": 0.0}
+# the read-out's environment fits run on the tensor cores (with the floor) on the split paths
+RO_FLOOR = {"tf32x3": 3e-5, "bf16x3": 3e-5, "tf32": 0.0, "bf16": 0.0}
 
 
 def c2_terms():

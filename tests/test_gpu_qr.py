@@ -11,10 +11,12 @@ pytestmark = pytest.mark.gpu
 
 @pytest.mark.parametrize("cplx", [False, True])
 @pytest.mark.parametrize("m,n,batch", [(288, 32, 5), (81, 81, 2), (1000, 17, 3), (1024, 64, 2), (600, 512, 1),
-                                       (1, 1, 3), (16, 1, 4)])
+                                       (2400, 96, 3), (1500, 37, 2), (5000, 20, 2), (1, 1, 3), (16, 1, 4)])
 def test_qr_batched(cplx, m, n, batch):
-    """Shapes of the fits, the largest cluster shape (1024 x 64), the largest n (512: one
-    CTA per matrix, W in global memory) and the degenerate 1 x 1 and single-column cases."""
+    """Shapes of the fits, the largest cluster shape (1024 x 64), the blocked one-CTA QR of
+    matrices beyond a cluster's shared memory (the 2400 x 96 site matrices of D=5, chi=96;
+    panels of 16 / 8 / 4 columns, a last panel narrower than the others), the largest n
+    (512) and the degenerate 1 x 1 and single-column cases."""
     torch = pytest.importorskip("torch")
     rng = np.random.default_rng(m + n)
     A = rng.standard_normal((batch, m, n)) + (1j * rng.standard_normal((batch, m, n)) if cplx else 0)

@@ -154,8 +154,7 @@ def test_active_fit_stop_rule_split_paths(prec):
     the paths' 3e-5; the oracle at the same tolerances): <O> within 1e-5 of the oracle after 6
     sweeps."""
     cfg = I.config(2)
-    ro = {"tf32x3": 3e-5, "bf16x3": 1e-6}[prec]  # read-out fits: on the tensor cores for TF32X3 only
     g, o, gr, orr, gv, ov = run_both(cfg["tensors"], 12, 12, 2, 3, 3, 3, 32, c2_terms(), n_sweeps=6, fit_tol=1e-6,
                                      fit_max_sweeps=10, prec=prec, warm_start=True, oracle_fit_tol=3e-5,
-                                     oracle_readout_fit_tol=ro)
+                                     oracle_readout_fit_tol=3e-5)
     assert np.max(np.abs(gv - ov)) < TOLMIX, np.max(np.abs(gv - ov))

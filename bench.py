@@ -317,6 +317,34 @@ def golden_error(B, cfg, prec, stream, torch):
     return out
 
 
+def run_replay(args):
+    """For ncu captures: the configured workload (or the same recipe on an L x L lattice), one
+    sweep (untimed: its graph has conditional nodes, which ncu does not profile kernel by
+    kernel), then one kernel-class replay of each requested class (bbp_time_kernels: the
+    sweep's launches of that class, one by one, every fit stage active)."""
+    import torch
+    from paper_2301_05844_gb300 import binding as B
+    from paper_2301_05844_gb300 import inputs as I
+    cfg, _ = workload(args.config)
+    if args.lattice:
+        assert cfg["boundary"] == "obc" and not cfg.get("single_layer"), "--lattice: OBC PEPS workloads only"
+        L = args.lattice
+        cfg = dict(cfg, Lx=L, Ly=L, name=f"peps{L}x{L}_D{cfg['D']}_chi{cfg['chi']}",
+                   tensors=I.uniform_noise_peps(L, L, cfg["d"], cfg["D"], seed=args.config,
+                                                dtype=np.asarray(cfg["tensors"][0]).dtype))
+    prec = args.prec or cfg.get("prec", "tf32")
+    torch.cuda.set_device(0)
+    g = make_lattice(B, cfg, prec, None)
+    g.set_tensors(cfg["tensors"])
+    g.sweep(1)
+    for cls in [int(c) for c in args.replay.split(",")]:
+        ms, n, f, by = C.c_double(), C.c_longlong(), C.c_double(), C.c_double()
+        rc = B.lib().bbp_time_kernels(g.h, cls, 1, C.byref(ms), C.byref(n), C.byref(f), C.byref(by))
+        print(json.dumps({"workload": cfg["name"], "prec": prec, "class": cls, "rc": rc, "ms": ms.value,
+                          "launches": n.value, "flops": f.value, "bytes": by.value}), flush=True)
+    g.close()
+
+
 def run_ours(args):
     import torch
     from paper_2301_05844_gb300 import binding as B
@@ -604,8 +632,12 @@ def main():
     ap.add_argument("--seed", type=int, default=5)
     ap.add_argument("--serve-gb", type=float, default=64.0)
     ap.add_argument("--max-active", type=int, default=16)
+    ap.add_argument("--replay", default=None, help="kernel classes to replay once (for ncu), e.g. 0,2")
+    ap.add_argument("--lattice", type=int, default=0, help="with --replay: the workload's recipe on an L x L lattice")
     args = ap.parse_args()
-    if args.serve and args.impl == "ours":
+    if args.replay:
+        run_replay(args)
+    elif args.serve and args.impl == "ours":
         run_serve(args)
     elif args.impl == "reference":
         run_reference(args)

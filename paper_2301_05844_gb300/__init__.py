@@ -2,6 +2,6 @@
 
 The compute path is a CUDA library (``libbbp.so``, built from ``csrc/`` for sm_103a)
 behind the C ABI declared in ``include/bbp.h``; ``binding`` marshals arguments to it.
-Importing this package loads nothing; ``binding.load()`` opens the library and
+Importing this package loads nothing; ``binding.lib()`` opens the library and
 raises if it is missing.
 """

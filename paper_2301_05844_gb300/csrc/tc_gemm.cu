@@ -260,47 +260,58 @@ __device__ __forceinline__ void epilogue_dest(const float* tile, long long* roff
     // a split destination vectorises only if every segment start stays 16-byte aligned
     const bool segs_aligned = !x3 || ((kseg * esz) & 15) == 0;
     float x[8];
+    // Two passes per destination: 16-byte vectors where a group of VW elements is contiguous
+    // and aligned in the destination, then every other element with consecutive lanes on
+    // consecutive destination addresses (so that a warp's scalar stores share a few sectors:
+    // the site-update operands of D=5 have contiguous runs of K = 25 elements, and split rows
+    // whose segments are K apart, neither of which is 16-byte aligned).
     if (sn2 == 1) {
         const int G = (ncols + VW - 1) / VW;
+        auto is_vec = [&](int r, int c0) {
+            const long long o = roff[r] + coff[c0];
+            return segs_aligned && c0 + VW <= ncols && ((base + (uintptr_t)(o * esz)) & 15) == 0 &&
+                   coff[c0 + VW - 1] == coff[c0] + VW - 1;
+        };
         for (int it = tid; it < rows * G; it += 128) {
             const int r = it / G, c0 = (it - r * G) * VW;
+            if (!is_vec(r, c0)) continue;
             const long long o = roff[r] + coff[c0];
-            bool vec = segs_aligned && c0 + VW <= ncols && ((base + (uintptr_t)(o * esz)) & 15) == 0 &&
-                       coff[c0 + VW - 1] == coff[c0] + VW - 1;
-            if (vec) {
 #pragma unroll
-                for (int j = 0; j < 8; ++j)
-                    if (j < VW) x[j] = tile[r * P + c0 + j] * alpha;
-                if (x3) store_split_vec(out, o, kind, x, x3, kseg);
-                else store_vec(out, o, kind, x);
-            } else {
-                for (int j = 0; j < VW && c0 + j < ncols; ++j) {
-                    const float xv = tile[r * P + c0 + j] * alpha;
-                    if (x3) store_split1(out, roff[r] + coff[c0 + j], kind, xv, x3, kseg);
-                    else store_out(out, roff[r] + coff[c0 + j], kind, xv);
-                }
-            }
+            for (int j = 0; j < 8; ++j)
+                if (j < VW) x[j] = tile[r * P + c0 + j] * alpha;
+            if (x3) store_split_vec(out, o, kind, x, x3, kseg);
+            else store_vec(out, o, kind, x);
+        }
+        for (int it = tid; it < rows * ncols; it += 128) {  // lanes along a row
+            const int r = it / ncols, c = it - r * ncols;
+            if (is_vec(r, c - c % VW)) continue;
+            const float xv = tile[r * P + c] * alpha;
+            if (x3) store_split1(out, roff[r] + coff[c], kind, xv, x3, kseg);
+            else store_out(out, roff[r] + coff[c], kind, xv);
         }
     } else if (sm2 == 1) {
         const int G = (rows + VW - 1) / VW;
+        auto is_vec = [&](int r0, int c) {
+            const long long o = roff[r0] + coff[c];
+            return segs_aligned && r0 + VW <= rows && ((base + (uintptr_t)(o * esz)) & 15) == 0 &&
+                   roff[r0 + VW - 1] == roff[r0] + VW - 1;
+        };
         for (int it = tid; it < ncols * G; it += 128) {
             const int c = it / G, r0 = (it - c * G) * VW;
+            if (!is_vec(r0, c)) continue;
             const long long o = roff[r0] + coff[c];
-            bool vec = segs_aligned && r0 + VW <= rows && ((base + (uintptr_t)(o * esz)) & 15) == 0 &&
-                       roff[r0 + VW - 1] == roff[r0] + VW - 1;
-            if (vec) {
 #pragma unroll
-                for (int j = 0; j < 8; ++j)
-                    if (j < VW) x[j] = tile[(r0 + j) * P + c] * alpha;
-                if (x3) store_split_vec(out, o, kind, x, x3, kseg);
-                else store_vec(out, o, kind, x);
-            } else {
-                for (int j = 0; j < VW && r0 + j < rows; ++j) {
-                    const float xv = tile[(r0 + j) * P + c] * alpha;
-                    if (x3) store_split1(out, roff[r0 + j] + coff[c], kind, xv, x3, kseg);
-                    else store_out(out, roff[r0 + j] + coff[c], kind, xv);
-                }
-            }
+            for (int j = 0; j < 8; ++j)
+                if (j < VW) x[j] = tile[(r0 + j) * P + c] * alpha;
+            if (x3) store_split_vec(out, o, kind, x, x3, kseg);
+            else store_vec(out, o, kind, x);
+        }
+        for (int it = tid; it < rows * ncols; it += 128) {  // lanes down a column
+            const int c = it / rows, r = it - c * rows;
+            if (is_vec(r - r % VW, c)) continue;
+            const float xv = tile[r * P + c] * alpha;
+            if (x3) store_split1(out, roff[r] + coff[c], kind, xv, x3, kseg);
+            else store_out(out, roff[r] + coff[c], kind, xv);
         }
     } else {
         for (int it = tid; it < rows * ncols; it += 128) {
@@ -327,7 +338,9 @@ __global__ void __launch_bounds__(128, 1) k_tc_gemm(const TCTask* __restrict__ t
     __syncthreads();
     const int tilesM = (t.M + BM - 1) / BM, tilesN = (t.N + BN - 1) / BN;
     if ((int)blockIdx.x >= tilesM * tilesN) return;
-    const int m0 = (blockIdx.x % tilesM) * BM, n0 = (blockIdx.x / tilesM) * BN;
+    // the tiles of one row block are consecutive CTAs, so that its A rows are fetched from HBM
+    // once and read from L2 by the other column tiles (B, one tensor per task, stays in L2)
+    const int n0 = (blockIdx.x % tilesN) * BN, m0 = (blockIdx.x / tilesN) * BM;
     constexpr int EK = KBYTES / (KIND == 0 ? 4 : 2);  // elements of K per k-block
     const int nk = (t.K + EK - 1) / EK;
     constexpr uint32_t A_BYTES = BM * KBYTES, B_BYTES = BN * KBYTES;  // one k-block

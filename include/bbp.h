@@ -117,11 +117,16 @@ typedef struct {
                                 entries (init_mode 1), the phase reference of the normalisation
                                 is <1|m> (all-ones vector) instead of <I|m>, and a term's
                                 op_re[k] is the impurity tensor that replaces E at site[k]. */
-    int shift_x, shift_y;    /* INFINITE only (0 for OBC): the partition shifted by shift_x
-                                columns and shift_y rows, 0 <= shift < Lx (Ly), so that block
-                                site (r, c) is lattice site (r + shift_y, c + shift_x); the
+    int shift_x, shift_y;    /* the partition shifted by shift_x columns and shift_y rows (the
                                 paper covers every bond from a block centre by such shifted
-                                partitions (Sec. "The blockBP algorithm"). */
+                                partitions, Sec. "The blockBP algorithm").  INFINITE:
+                                0 <= shift < Lx (Ly), block site (r, c) is lattice site
+                                (r + shift_y, c + shift_x).  OBC: 0 <= shift < bx (by), block
+                                boundaries at columns shift_x, shift_x + bx, ... and rows
+                                shift_y, shift_y + by, ..., so the blocks on the lattice edges
+                                are narrower (the periodic embedding's blocks that straddle its
+                                seam, which split into two pieces joined only by bonds of
+                                dimension 1); the block index stays row-major over the blocks */
     int launch_mode;         /* 0: each sweep is one CUDA graph whose fit loops are conditional
                                 nodes that stop when the fits have met the stop rule; 1: the
                                 same kernels launched one by one on the stream, each fit loop
@@ -133,7 +138,8 @@ typedef struct {
  * buffers) and plan one sweep.  *out receives the handle.  Limits checked here:
  * Lx, Ly <= 4096; bx, by <= 16; D <= 16; d <= 64; 1 <= fit_max_sweeps <= 64;
  * init_mode, warm_start, hermitian_basis, single_layer and launch_mode 0 or 1; 0 <= shift_x < Lx and
- * 0 <= shift_y < Ly on infinite lattices, both 0 with OBC.  Errors: INVALID, OOM, CUDA. */
+ * 0 <= shift_y < Ly on infinite lattices, 0 <= shift_x < bx and 0 <= shift_y < by with OBC.
+ * Errors: INVALID, OOM, CUDA. */
 int bbp_create_lattice(const bbp_lattice_desc* desc, bbp_lattice** out);
 
 /* Device bytes a lattice with this desc would hold (arena plus task descriptors),
@@ -182,7 +188,18 @@ typedef struct {
  * doubles each (host memory; out_im may be NULL).  Errors: INVALID, STATE, CUDA. */
 int bbp_expect(bbp_lattice* lat, const bbp_term* terms, int n_terms, double* out_re, double* out_im);
 
-/* Reduced density matrix of nsite (1 or 2) sites, rho = Tr_rest |psi><psi| / <psi|psi>
+/* Read-out over several partitions of one OBC lattice (the same tensors run with different
+ * desc.shift_x / shift_y): blockBP's observables are accurate near a block's centre, and the
+ * paper covers every bond from a block centre by shifted partitions (Sec. "The blockBP
+ * algorithm").  Each term is read (bbp_expect) from the lattice in which its sites lie deepest
+ * inside one block: the smallest distance of its sites to that block's edges, a pair split
+ * between two blocks counting -1, the first lattice on a tie.  chosen (n_terms ints, may be
+ * NULL) receives that lattice's index per term.  Errors: INVALID (no lattice, a NULL one,
+ * lattices of different Lx, Ly or d, an infinite one, a bad term), and bbp_expect's. */
+int bbp_expect_centred(bbp_lattice* const* lats, int n_lats, const bbp_term* terms, int n_terms, double* out_re,
+                       double* out_im, int* chosen);
+
+/* Reduced density matrix of nsite (1 or 2) sites, rho = Tr_rest |psi><psi| / <psi|psi>/* Reduced density matrix of nsite (1 or 2) sites, rho = Tr_rest |psi><psi| / <psi|psi>
  * (the 2-local RDMs that the paper compares between methods by their trace distance
  * D(rho, sigma) = ||rho - sigma||_1 / 2, Sec. on the transverse Ising model).  Entry
  * (a, b) = <a|rho|b> is the read-out of the matrix unit |b><a| (a product of single-site

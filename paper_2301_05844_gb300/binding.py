@@ -203,6 +203,20 @@ class Server:
             pass
 
 
+def expect_centred(lattices, terms):
+    """<O> of every term from the partition (one of `lattices`, the same OBC lattice run with
+    different shifts) in which its sites lie deepest inside one block; returns (values,
+    index of the lattice each term was read from)."""
+    n = len(terms)
+    arr, keep = _term_array(terms)
+    hs = (C.c_void_p * len(lattices))(*[g.h.value for g in lattices])
+    out_re, out_im, chosen = np.zeros(n), np.zeros(n), np.zeros(max(n, 1), dtype=np.int32)
+    _check(lib().bbp_expect_centred(hs, len(lattices), arr, n, out_re.ctypes.data_as(C.POINTER(C.c_double)),
+                                    out_im.ctypes.data_as(C.POINTER(C.c_double)),
+                                    chosen.ctypes.data_as(C.POINTER(C.c_int))))
+    return out_re + 1j * out_im, chosen[:n]
+
+
 class Lattice:
     """Owning wrapper of a bbp_lattice handle."""
 

@@ -75,8 +75,20 @@ int bbp_lattice::neighbour(int blk, int dir) const {
 }
 
 void bbp_lattice::block_origin(int blk, int& r0, int& c0) const {
-    r0 = (blk / nbx) * desc.by;
-    c0 = (blk % nbx) * desc.bx;
+    r0 = ys[blk / nbx];
+    c0 = xs[blk % nbx];
+}
+
+void bbp_lattice::block_size(int blk, int& h, int& w) const {
+    const int R = blk / nbx, C = blk % nbx;
+    h = ys[R + 1] - ys[R];
+    w = xs[C + 1] - xs[C];
+}
+
+int bbp_lattice::block_of(int r, int c) const {
+    const int R = (int)(std::upper_bound(ys.begin(), ys.end(), r) - ys.begin()) - 1;
+    const int C = (int)(std::upper_bound(xs.begin(), xs.end(), c) - xs.begin()) - 1;
+    return R * nbx + C;
 }
 
 View3 bbp_lattice::msg_site(int it, int s, bool cur) const {
@@ -91,7 +103,9 @@ static View3 one3(size_t one_off) {
 }
 
 std::vector<View3> bbp_lattice::incoming(int blk, int dir) const {
-    const int nsite = (dir == DIR_LEFT || dir == DIR_RIGHT) ? desc.by : desc.bx;
+    int bh, bw;
+    block_size(blk, bh, bw);
+    const int nsite = (dir == DIR_LEFT || dir == DIR_RIGHT) ? bh : bw;
     std::vector<View3> v;
     const int nb = neighbour(blk, dir);
     if (nb < 0) {
@@ -436,8 +450,7 @@ static int plan_sweep(bbp_lattice* L) {
         ColumnSweep s;
         s.dir = I.dir;
         L->block_origin(I.block, s.r0, s.c0);
-        s.bh = L->desc.by;
-        s.bw = L->desc.bx;
+        L->block_size(I.block, s.bh, s.bw);
         s.fm = L->frame_msgs(I.dir, in);
         s.chi = L->desc.chi;
         s.keep = L->desc.warm_start != 0;  // per-column Y buffers persist across sweeps
@@ -587,9 +600,9 @@ static int validate(const bbp_lattice_desc* d) {
     if (d->warm_start != 0 && d->warm_start != 1) return fail(BBP_ERR_INVALID, "warm_start must be 0 or 1");
     if (d->single_layer != 0 && d->single_layer != 1) return fail(BBP_ERR_INVALID, "single_layer must be 0 or 1");
     if (d->launch_mode != 0 && d->launch_mode != 1) return fail(BBP_ERR_INVALID, "launch_mode must be 0 or 1");
-    if (d->boundary == BBP_OBC ? (d->shift_x != 0 || d->shift_y != 0)
+    if (d->boundary == BBP_OBC ? (d->shift_x < 0 || d->shift_x >= d->bx || d->shift_y < 0 || d->shift_y >= d->by)
                                : (d->shift_x < 0 || d->shift_x >= d->Lx || d->shift_y < 0 || d->shift_y >= d->Ly))
-        return fail(BBP_ERR_INVALID, "shifts: 0 <= shift < unit cell on infinite lattices, 0 with OBC");
+        return fail(BBP_ERR_INVALID, "shifts: 0 <= shift < unit cell on infinite lattices, < block side with OBC");
     if (d->single_layer && (d->d != 1 || (d->dtype != BBP_F64 && d->dtype != BBP_F32)))
         return fail(BBP_ERR_INVALID, "a single-layer network has d = 1 and real tensors");
     return BBP_OK;
@@ -614,9 +627,24 @@ int bbp::plan_lattice(const bbp_lattice_desc* desc, bbp_lattice** out) {
     L->cplx = in_cplx && !L->hb;
     L->ss = L->cplx ? 16 : 8;
     if (desc->boundary == BBP_OBC) {
-        L->nbx = desc->Lx / desc->bx;
-        L->nby = desc->Ly / desc->by;
+        // block boundaries every bx columns from shift_x (every by rows from shift_y): with a
+        // shift the blocks on the lattice edges are narrower (the shifted partition of the OBC
+        // lattice, whose blocks straddling the periodic embedding's seam split into two)
+        auto bounds = [](int L, int b, int sh) {
+            std::vector<int> v{0};
+            for (int x = sh; x < L; x += b)
+                if (x > 0) v.push_back(x);
+            v.push_back(L);
+            return v;
+        };
+        L->xs = bounds(desc->Lx, desc->bx, desc->shift_x);
+        L->ys = bounds(desc->Ly, desc->by, desc->shift_y);
+    } else {
+        L->xs = {0, desc->bx};
+        L->ys = {0, desc->by};
     }
+    L->nbx = (int)L->xs.size() - 1;
+    L->nby = (int)L->ys.size() - 1;
     L->nblocks = L->nbx * L->nby;
     L->ntens = desc->Lx * desc->Ly;
     Program& pr = L->sweep;
@@ -652,7 +680,9 @@ int bbp::plan_lattice(const bbp_lattice_desc* desc, bbp_lattice** out) {
             I.block = blk;
             I.dir = dir;
             I.msgid = 4 * blk + dir;
-            I.b = (dir == DIR_LEFT || dir == DIR_RIGHT) ? desc->by : desc->bx;
+            int bh, bw;
+            L->block_size(blk, bh, bw);
+            I.b = (dir == DIR_LEFT || dir == DIR_RIGHT) ? bh : bw;
             std::vector<int> ph(I.b, L->K);
             I.mb = bond_caps(ph, desc->chi);
             L->item_of[blk * 4 + dir] = (int)L->items.size();

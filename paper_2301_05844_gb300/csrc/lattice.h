@@ -64,6 +64,9 @@ struct bbp_lattice {
     int K = 1;          // leg dimension of the network: D^2 (double layer) or D (single layer)
     bool single = false;  // single-layer network: the tensors are used as they are
     int nbx = 1, nby = 1, nblocks = 1;
+    // block boundaries: block (R, C) holds rows ys[R] .. ys[R+1]-1 and columns xs[C] .. xs[C+1]-1
+    // (OBC: every bx columns from shift_x, every by rows from shift_y; infinite: the one block)
+    std::vector<int> xs, ys;
     int ntens = 0;
     std::vector<std::array<int, 4>> tdims;  // Du, Dl, Dd, Dr per distinct tensor
     std::vector<size_t> T_off, E_off;       // element offsets
@@ -104,6 +107,8 @@ struct bbp_lattice {
     std::array<int, 4> site_dims(int r, int c) const;
     int neighbour(int blk, int dir) const;
     void block_origin(int blk, int& r0, int& c0) const;
+    void block_size(int blk, int& h, int& w) const;
+    int block_of(int r, int c) const;  // OBC: the block holding lattice site (r, c)
     bbp::View3 msg_site(int item, int s, bool cur) const;
     std::vector<bbp::View3> incoming(int blk, int dir) const;  // message into blk from side dir
     bbp::View4 frame_E(int dir, int r0, int c0, int bh, int bw, int rf, int cf, int* tensor = nullptr) const;

@@ -88,26 +88,31 @@ extern "C" int bbp_expect(bbp_lattice* L, const bbp_term* terms, int n_terms, do
     std::map<int, int> region_of;
     auto get_region = [&](const std::vector<std::pair<int, int>>& rc, int& out) -> int {
         int rid, r0, c0, h, w;
+        bool horiz = false;
         std::vector<int> blks;
         if (!obc) {
             rid = 0; r0 = 0; c0 = 0; h = ds.by; w = ds.bx;
             blks = {0};
         } else {
-            for (auto& p : rc) blks.push_back((p.first / ds.by) * L->nbx + p.second / ds.bx);
+            for (auto& p : rc) blks.push_back(L->block_of(p.first, p.second));
             if (blks.size() == 1 || blks[0] == blks[1]) {
                 rid = blks[0];
                 L->block_origin(rid, r0, c0);
-                h = ds.by; w = ds.bx;
+                L->block_size(rid, h, w);
                 blks = {rid};
             } else {
                 const int dr = std::abs(rc[0].first - rc[1].first), dc = std::abs(rc[0].second - rc[1].second);
                 if (dr + dc != 1) return fail(BBP_ERR_INVALID, "a two-site term across blocks must be a nearest-neighbour pair");
                 const int a = std::min(blks[0], blks[1]), b = std::max(blks[0], blks[1]);
+                int ha, wa, hb, wb;
                 L->block_origin(a, r0, c0);
-                if (dc == 1) {
-                    rid = L->nblocks + 2 * a; h = ds.by; w = 2 * ds.bx;
+                L->block_size(a, ha, wa);
+                L->block_size(b, hb, wb);
+                horiz = dc == 1;
+                if (horiz) {
+                    rid = L->nblocks + 2 * a; h = ha; w = wa + wb;
                 } else {
-                    rid = L->nblocks + 2 * a + 1; h = 2 * ds.by; w = ds.bx;
+                    rid = L->nblocks + 2 * a + 1; h = ha + hb; w = wa;
                 }
                 blks = {a, b};
             }
@@ -127,7 +132,6 @@ extern "C" int bbp_expect(bbp_lattice* L, const bbp_term* terms, int n_terms, do
                 ia[dd] = L->incoming(blks[0], dd);
                 ib[dd] = L->incoming(blks[1], dd);
             }
-            const bool horiz = w > ds.bx;
             auto cat = [](std::vector<View3> x, const std::vector<View3>& y) {
                 x.insert(x.end(), y.begin(), y.end());
                 return x;
@@ -565,6 +569,71 @@ extern "C" int bbp_expect(bbp_lattice* L, const bbp_term* terms, int n_terms, do
     for (int t = 0; t < n_terms; ++t) {
         out_re[t] = res[2 * (size_t)t];
         if (out_im) out_im[t] = res[2 * (size_t)t + 1];
+    }
+    return BBP_OK;
+} catch (...) {
+    return abi_error();
+}
+
+// Read-out over several partitions of one lattice (Sec. "The blockBP algorithm": observables are
+// accurate near a block's centre, so every bond is read from a partition whose blocks hold it
+// away from their edges).  Each term goes to the lattice in which its sites lie deepest inside
+// one block: the smallest distance of any of its sites to that block's edges (a pair split
+// between two blocks scores -1), the first lattice on a tie; then one bbp_expect per lattice.
+extern "C" int bbp_expect_centred(bbp_lattice* const* lats, int n_lats, const bbp_term* terms, int n_terms,
+                                  double* out_re, double* out_im, int* chosen) try {
+    if (!lats || n_lats < 1) return fail(BBP_ERR_INVALID, "expect_centred: no lattices");
+    if (n_terms < 0 || (n_terms > 0 && (!terms || !out_re))) return fail(BBP_ERR_INVALID, "bad term arguments");
+    for (int k = 0; k < n_lats; ++k) {
+        if (!lats[k]) return fail(BBP_ERR_INVALID, "expect_centred: a lattice is NULL");
+        const bbp_lattice_desc& a = lats[k]->desc;
+        const bbp_lattice_desc& b = lats[0]->desc;
+        if (a.boundary != BBP_OBC || a.Lx != b.Lx || a.Ly != b.Ly || a.d != b.d)
+            return fail(BBP_ERR_INVALID, "expect_centred: OBC partitions of one lattice (same Lx, Ly, d) only");
+    }
+    const int Lx = lats[0]->desc.Lx, Ly = lats[0]->desc.Ly;
+    std::vector<int> pick(n_terms, 0);
+    for (int t = 0; t < n_terms; ++t) {
+        const bbp_term& T = terms[t];
+        if (T.nsite < 1 || T.nsite > 2) return fail(BBP_ERR_INVALID, "term must have 1 or 2 sites");
+        int best = -2;
+        for (int k = 0; k < n_lats; ++k) {
+            const bbp_lattice* L = lats[k];
+            int score = 1 << 30, blk0 = -1;
+            for (int q = 0; q < T.nsite; ++q) {
+                const int s = T.site[q];
+                if (s < 0 || s >= Lx * Ly) return fail(BBP_ERR_INVALID, "site out of range");
+                const int r = s / Lx, c = s % Lx, blk = L->block_of(r, c);
+                int r0, c0, h, w;
+                L->block_origin(blk, r0, c0);
+                L->block_size(blk, h, w);
+                const int dist = std::min(std::min(r - r0, r0 + h - 1 - r), std::min(c - c0, c0 + w - 1 - c));
+                if (q == 0) blk0 = blk;
+                score = blk != blk0 ? -1 : std::min(score, dist);
+            }
+            if (score > best) {
+                best = score;
+                pick[t] = k;
+            }
+        }
+        if (chosen) chosen[t] = pick[t];
+    }
+    for (int k = 0; k < n_lats; ++k) {
+        std::vector<bbp_term> sub;
+        std::vector<int> idx;
+        for (int t = 0; t < n_terms; ++t)
+            if (pick[t] == k) {
+                sub.push_back(terms[t]);
+                idx.push_back(t);
+            }
+        if (sub.empty()) continue;
+        std::vector<double> re(sub.size()), im(sub.size());
+        const int rc = bbp_expect(lats[k], sub.data(), (int)sub.size(), re.data(), im.data());
+        if (rc < 0) return rc;
+        for (size_t i = 0; i < idx.size(); ++i) {
+            out_re[idx[i]] = re[i];
+            if (out_im) out_im[idx[i]] = im[i];
+        }
     }
     return BBP_OK;
 } catch (...) {

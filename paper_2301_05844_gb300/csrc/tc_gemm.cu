@@ -19,6 +19,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <atomic>
 
 #include "bbp_internal.h"
 #include "tc_gemm.h"
@@ -43,6 +44,9 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
 }
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 // Non-blocking test of a phase (a satisfied mbarrier.try_wait measured ~280 cycles on this
 // GPU, a satisfied test_wait ~150; the waits below poll it in a bounded loop).
@@ -239,22 +243,37 @@ __device__ __forceinline__ void store_split_vec(void* out, long long o, int kind
     *(float4*)(f + o + 2 * kseg) = x3 == 1 ? Hf : Lf;
 }
 
+// The epilogue runs on the 256 threads of the eight epilogue warps (tid = 0..255); they
+// synchronise among themselves on named barrier 1.
+constexpr int EPI_THREADS = 256;
+__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+// the same barrier, returning whether every epilogue thread passed true
+__device__ __forceinline__ bool epi_all(bool v) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\t"
+        "bar.red.and.pred q, 1, 256, p;\n\tselp.u32 %0, 1, 0, q;\n\t}\n"
+        : "=r"(r)
+        : "r"((uint32_t)v)
+        : "memory");
+    return r != 0;
+}
+
 __device__ __forceinline__ void epilogue_dest(const float* tile, long long* roff, long long* coff, int rows, int ncols,
                                               int m0, int n0, int M2, int N2, long long sm1, long long sm2,
                                               long long sn1, long long sn2, int kind, float alpha, void* out, int x3,
-                                              long long kseg) {
+                                              long long kseg, int tid) {
     constexpr int P = EC + 1;
-    const int tid = threadIdx.x;
-    __syncthreads();  // the previous destination has finished with the offsets
-    for (int r = tid; r < rows; r += 128) {
+    epi_sync();  // the previous destination has finished with the offsets
+    for (int r = tid; r < rows; r += EPI_THREADS) {
         const int m = m0 + r, m1 = m / M2;
         roff[r] = (long long)m1 * sm1 + (long long)(m - m1 * M2) * sm2;
     }
-    for (int c = tid; c < ncols; c += 128) {
+    for (int c = tid; c < ncols; c += EPI_THREADS) {
         const int n = n0 + c, n1 = n / N2;
         coff[c] = (long long)n1 * sn1 + (long long)(n - n1 * N2) * sn2;
     }
-    __syncthreads();
+    epi_sync();
     const int esz = out_esz(kind), VW = 16 / esz;
     const uintptr_t base = (uintptr_t)out;
     // a split destination vectorises only if every segment start stays 16-byte aligned
@@ -272,7 +291,7 @@ __device__ __forceinline__ void epilogue_dest(const float* tile, long long* roff
             return segs_aligned && c0 + VW <= ncols && ((base + (uintptr_t)(o * esz)) & 15) == 0 &&
                    coff[c0 + VW - 1] == coff[c0] + VW - 1;
         };
-        for (int it = tid; it < rows * G; it += 128) {
+        for (int it = tid; it < rows * G; it += EPI_THREADS) {
             const int r = it / G, c0 = (it - r * G) * VW;
             if (!is_vec(r, c0)) continue;
             const long long o = roff[r] + coff[c0];
@@ -282,7 +301,7 @@ __device__ __forceinline__ void epilogue_dest(const float* tile, long long* roff
             if (x3) store_split_vec(out, o, kind, x, x3, kseg);
             else store_vec(out, o, kind, x);
         }
-        for (int it = tid; it < rows * ncols; it += 128) {  // lanes along a row
+        for (int it = tid; it < rows * ncols; it += EPI_THREADS) {  // lanes along a row
             const int r = it / ncols, c = it - r * ncols;
             if (is_vec(r, c - c % VW)) continue;
             const float xv = tile[r * P + c] * alpha;
@@ -296,7 +315,7 @@ __device__ __forceinline__ void epilogue_dest(const float* tile, long long* roff
             return segs_aligned && r0 + VW <= rows && ((base + (uintptr_t)(o * esz)) & 15) == 0 &&
                    roff[r0 + VW - 1] == roff[r0] + VW - 1;
         };
-        for (int it = tid; it < ncols * G; it += 128) {
+        for (int it = tid; it < ncols * G; it += EPI_THREADS) {
             const int c = it / G, r0 = (it - c * G) * VW;
             if (!is_vec(r0, c)) continue;
             const long long o = roff[r0] + coff[c];
@@ -306,7 +325,7 @@ __device__ __forceinline__ void epilogue_dest(const float* tile, long long* roff
             if (x3) store_split_vec(out, o, kind, x, x3, kseg);
             else store_vec(out, o, kind, x);
         }
-        for (int it = tid; it < rows * ncols; it += 128) {  // lanes down a column
+        for (int it = tid; it < rows * ncols; it += EPI_THREADS) {  // lanes down a column
             const int c = it / rows, r = it - c * rows;
             if (is_vec(r - r % VW, c)) continue;
             const float xv = tile[r * P + c] * alpha;
@@ -314,7 +333,7 @@ __device__ __forceinline__ void epilogue_dest(const float* tile, long long* roff
             else store_out(out, roff[r] + coff[c], kind, xv);
         }
     } else {
-        for (int it = tid; it < rows * ncols; it += 128) {
+        for (int it = tid; it < rows * ncols; it += EPI_THREADS) {
             const int c = it / rows, r = it - c * rows;
             const float xv = tile[r * P + c] * alpha;
             if (x3) store_split1(out, roff[r] + coff[c], kind, xv, x3, kseg);
@@ -323,37 +342,35 @@ __device__ __forceinline__ void epilogue_dest(const float* tile, long long* roff
     }
 }
 
-template <int KIND, int BN>
+constexpr int EPI_WARPS = EPI_THREADS / 32;      // warps 2..9, two per TMEM lane quarter
+constexpr int NTHREADS = 32 * (2 + EPI_WARPS);   // producer, MMA issuer, epilogue
+constexpr size_t EPI_BYTES = (size_t)BM * (EC + 1) * sizeof(float) + (size_t)(BM + EC) * sizeof(long long);
+
+// Persistent, warp-specialised grouped GEMM.  The work items of a launch are the tiles of all
+// its tasks (task = item / max_tiles, tile = item % max_tiles; tiles a task does not have are
+// skipped, and so are the tasks whose active flag is 0); CTA b takes items b, b + G, b + 2G, ...
+// Warp 0 (one lane) streams the k-blocks of its items through a ring of stages with TMA, warp 1
+// (one lane) issues the MMAs of item j into TMEM accumulator j & 1, and warps 2-9 drain the
+// other accumulator meanwhile (two warps per quarter of the TMEM lanes, alternate 16-column
+// groups): the epilogue of one tile runs under the loads and MMAs of the next.  The tiles of one row block are consecutive items (their A rows reach L2 once).
 // stall != 0 (self-test of the bounded waits only): the producer issues no copy, so the
 // first wait on a full stage never succeeds and must end by its bound.
-__global__ void __launch_bounds__(128, 1) k_tc_gemm(const TCTask* __restrict__ tasks, int* err, int stages, int ksub,
-                                                    int stall) {
-    // The task descriptor is copied to shared memory in one coalesced read (its fields are
-    // otherwise fetched from global memory one dependent load at a time); the TMA copies use
-    // the tensor maps at their global address.
-    __shared__ TCTask t;
-    const TCTask* gt = tasks + blockIdx.y;
-    for (int w = threadIdx.x; w < (int)(sizeof(TCTask) / 4); w += 128)
-        ((uint32_t*)&t)[w] = ((const uint32_t*)gt)[w];
-    __syncthreads();
-    const int tilesM = (t.M + BM - 1) / BM, tilesN = (t.N + BN - 1) / BN;
-    if ((int)blockIdx.x >= tilesM * tilesN) return;
-    // the tiles of one row block are consecutive CTAs, so that its A rows are fetched from HBM
-    // once and read from L2 by the other column tiles (B, one tensor per task, stays in L2)
-    const int n0 = (blockIdx.x % tilesN) * BN, m0 = (blockIdx.x / tilesN) * BM;
+template <int KIND, int BN>
+__global__ void __launch_bounds__(NTHREADS, 1) k_tc_gemm(const TCTask* __restrict__ tasks, int ntasks, int max_tiles,
+                                                         int* err, int stages, int ksub, int stall) {
     constexpr int EK = KBYTES / (KIND == 0 ? 4 : 2);  // elements of K per k-block
-    const int nk = (t.K + EK - 1) / EK;
     constexpr uint32_t A_BYTES = BM * KBYTES, B_BYTES = BN * KBYTES;  // one k-block
-    // a ring stage holds ksub k-blocks: one full/empty barrier round trip per stage (two
-    // halve the round trips, one keeps rings small enough for two CTAs per SM)
+    constexpr uint32_t TCOLS = 2 * (BN < 32 ? 32 : BN);               // two accumulators
     const uint32_t A_STAGE = A_BYTES * ksub, B_STAGE = B_BYTES * ksub;
-    const int nst = (nk + ksub - 1) / ksub;
 
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     unsigned char* sA = smem;
     unsigned char* sB = smem + stages * A_STAGE;
-    __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES], accum;
+    float* tile = (float*)(sB + stages * B_STAGE);  // epilogue staging, its own region
+    long long* roff = (long long*)(tile + BM * (EC + 1));
+    long long* coff = roff + BM;
+    __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES], tfull[2], tempty[2], mma_done;
     __shared__ uint32_t tmem_base;
     __shared__ int issued;
 
@@ -363,141 +380,203 @@ __global__ void __launch_bounds__(128, 1) k_tc_gemm(const TCTask* __restrict__ t
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
-        mbar_init(&accum, 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&tfull[b], 1);
+            mbar_init(&tempty[b], EPI_WARPS);
+        }
+        mbar_init(&mma_done, 1);
         issued = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        prefetch_map(&gt->map_a);
-        prefetch_map(&gt->map_b);
     }
-    if (warp == 0) tmem_alloc(&tmem_base, BN < 32 ? 32 : BN);
+    if (warp == 0) tmem_alloc(&tmem_base, TCOLS);
     fence_before();
     __syncthreads();
     fence_after();
     const uint32_t tmem = tmem_base;
-    // Everything above reads only the static task descriptor, so it may overlap the previous
-    // kernel (programmatic dependent launch); the active flag and the operands are its output.
+    // Everything above reads no earlier kernel's output, so it may overlap the previous kernel
+    // (programmatic dependent launch); the active flags and the operands are its output.
     grid_dependency_wait();
-    if (t.active && *t.active == 0) {
-        if (warp == 0) tmem_dealloc(tmem, BN < 32 ? 32 : BN);
-        return;
-    }
+    const int nitems = ntasks * max_tiles;
+    // item -> (task, m0, n0), or false if the item is empty (same answer in every role)
+    auto item = [&](int w, const TCTask*& t, int& m0, int& n0) {
+        t = tasks + w / max_tiles;
+        const int tl = w % max_tiles;
+        const int tilesM = (t->M + BM - 1) / BM, tilesN = (t->N + BN - 1) / BN;
+        if (tl >= tilesM * tilesN) return false;
+        if (t->active && *t->active == 0) return false;
+        n0 = (tl % tilesN) * BN;
+        m0 = (tl / tilesN) * BM;
+        return true;
+    };
 
-    if (warp == 0 && lane == 0) {
-        // TMA producer: stage ks holds k-blocks ks*ksub .. (the last stage may hold fewer)
-        for (int ks = 0; ks < (stall ? 0 : nst); ++ks) {
-            const int s = ks % stages, r = ks / stages;
-            if (r > 0 && !mbar_wait(&empty[s], (r - 1) & 1, err)) break;
-            const int na = min(ksub, nk - ks * ksub);
-            mbar_expect_tx(&full[s], (uint32_t)na * (A_BYTES + B_BYTES));
-            for (int a = 0; a < na; ++a) {
-                const int kb = ks * ksub + a;
-                tma_load_2d(sA + s * A_STAGE + a * A_BYTES, &gt->map_a, &full[s], kb * EK, m0);
-                tma_load_2d(sB + s * B_STAGE + a * B_BYTES, &gt->map_b, &full[s], kb * EK, n0);
+    if (warp == 0) {
+        if (lane == 0) {
+            // TMA producer: stage gks holds k-blocks of one item (the last stage may hold fewer)
+            int gks = 0;
+            bool ok = true;
+            for (int w = blockIdx.x; w < nitems && ok && !stall; w += gridDim.x) {
+                const TCTask* t;
+                int m0, n0;
+                if (!item(w, t, m0, n0)) continue;
+                prefetch_map(&t->map_a);
+                prefetch_map(&t->map_b);
+                const int nk = (t->K + EK - 1) / EK, nst = (nk + ksub - 1) / ksub;
+                for (int ks = 0; ks < nst; ++ks, ++gks) {
+                    const int s = gks % stages, r = gks / stages;
+                    if (r > 0 && !mbar_wait(&empty[s], (r - 1) & 1, err)) {
+                        ok = false;
+                        break;
+                    }
+                    const int na = min(ksub, nk - ks * ksub);
+                    mbar_expect_tx(&full[s], (uint32_t)na * (A_BYTES + B_BYTES));
+                    for (int a = 0; a < na; ++a) {
+                        const int kb = ks * ksub + a;
+                        tma_load_2d(sA + s * A_STAGE + a * A_BYTES, &t->map_a, &full[s], kb * EK, m0);
+                        tma_load_2d(sB + s * B_STAGE + a * B_BYTES, &t->map_b, &full[s], kb * EK, n0);
+                    }
+                    issued = gks + 1;
+                }
             }
-            issued = ks + 1;
         }
-    } else if (warp == 1 && lane == 0) {
-        // MMA issuer
-        constexpr uint32_t ID = idesc(KIND, BN);
-        bool ok = true;
-        for (int ks = 0; ks < nst && ok; ++ks) {
-            const int s = ks % stages, r = ks / stages;
-            ok = mbar_wait(&full[s], r & 1, err);
-            if (!ok) break;
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // MMA issuer: item j into accumulator j & 1, once the epilogue has emptied it
+            constexpr uint32_t ID = idesc(KIND, BN);
+            int gks = 0, j = 0;
+            bool ok = true;
+            for (int w = blockIdx.x; w < nitems && ok; w += gridDim.x) {
+                const TCTask* t;
+                int m0, n0;
+                if (!item(w, t, m0, n0)) continue;
+                const int b = j & 1, u = j >> 1;
+                if (u > 0 && !mbar_wait(&tempty[b], (u - 1) & 1, err)) break;
+                fence_after();
+                const uint32_t acc = tmem + (uint32_t)(b * (TCOLS / 2));
+                const int nk = (t->K + EK - 1) / EK, nst = (nk + ksub - 1) / ksub;
+                for (int ks = 0; ks < nst; ++ks, ++gks) {
+                    const int s = gks % stages, r = gks / stages;
+                    if (!mbar_wait(&full[s], r & 1, err)) {
+                        ok = false;
+                        break;
+                    }
+                    fence_after();
+                    const int na = min(ksub, nk - ks * ksub);
+                    for (int a = 0; a < na; ++a) {
+                        const int kb = ks * ksub + a;
+                        const uint32_t a0 = smem_u32(sA + s * A_STAGE + a * A_BYTES);
+                        const uint32_t b0 = smem_u32(sB + s * B_STAGE + a * B_BYTES);
+#pragma unroll
+                        for (int k = 0; k < KBYTES / 32; ++k)  // 32 bytes of K per instruction
+                            umma<KIND>(acc, sdesc(a0 + 32 * k), sdesc(b0 + 32 * k), ID, (kb | k) ? 1u : 0u);
+                    }
+                    umma_commit(&empty[s]);
+                }
+                if (!ok) break;
+                umma_commit(&tfull[b]);
+                ++j;
+            }
+            umma_commit(&mma_done);  // completes once every MMA issued above has
+        }
+    } else {
+        // epilogue: item j from accumulator j & 1, 64 columns at a time through shared memory
+        const int etid = threadIdx.x - 64;            // 0..255
+        const int quad = warp & 3;                    // TMEM lanes 32 quad .. 32 quad + 31
+        const int half = (warp - 2) >> 2;             // this warp's 16-column groups: c / 16 = half mod 2
+        const int row = quad * 32 + lane;
+        int j = 0;
+        for (int w = blockIdx.x; w < nitems; w += gridDim.x) {
+            const TCTask* t;
+            int m0, n0;
+            if (!item(w, t, m0, n0)) continue;
+            const int b = j & 1, u = j >> 1;
+            if (w + (int)gridDim.x >= nitems) launch_dependents();  // the last item of this CTA
+            // one decision for all four warps, so that none is left at a barrier
+            if (!epi_all(mbar_wait(&tfull[b], u & 1, err))) break;
             fence_after();
-            const int na = min(ksub, nk - ks * ksub);
-            for (int a = 0; a < na; ++a) {
-                const int kb = ks * ksub + a;
-                const uint32_t a0 = smem_u32(sA + s * A_STAGE + a * A_BYTES), b0 = smem_u32(sB + s * B_STAGE + a * B_BYTES);
+            const uint32_t acc = tmem + (uint32_t)(b * (TCOLS / 2)) + ((uint32_t)(quad * 32) << 16);
+            const int ncols = min(BN, t->N - n0), rows = min(BM, t->M - m0);
+#pragma unroll 1
+            for (int c0 = 0; c0 < ncols; c0 += EC) {
+                const int cn = min(EC, ncols - c0);
+                const int nchunk = (cn + 15) & ~15;  // tcgen05.ld is warp-collective: uniform bound
+                epi_sync();                          // the previous chunk has been written out
+#pragma unroll 1
+                for (int c = 16 * half; c < nchunk; c += 32) {
+                    uint32_t v[16];
+                    tmem_ld16(acc + (uint32_t)(c0 + c), v);
 #pragma unroll
-                for (int k = 0; k < KBYTES / 32; ++k)  // 32 bytes of K per instruction, K order as in one stage per k-block
-                    umma<KIND>(tmem, sdesc(a0 + 32 * k), sdesc(b0 + 32 * k), ID, (kb | k) ? 1u : 0u);
+                    for (int q = 0; q < 16; ++q)
+                        if (c + q < EC) tile[row * (EC + 1) + c + q] = __uint_as_float(v[q]);
+                }
+                if (c0 + EC >= ncols) {  // every column of this accumulator has been read
+                    fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&tempty[b]);
+                }
+                for (int dst = 0; dst < (t->C2 ? 2 : 1); ++dst) {
+                    void* out = dst ? t->C2 : t->C;
+                    const long long sm1 = dst ? t->d_m1 : t->c_m1, sm2 = dst ? t->d_m2 : t->c_m2;
+                    const long long sn1 = dst ? t->d_n1 : t->c_n1, sn2 = dst ? t->d_n2 : t->c_n2;
+                    const int x3 = (t->x3 >> (2 * dst)) & 3;
+                    epilogue_dest(tile, roff, coff, rows, cn, m0, n0 + c0, t->M2, t->N2, sm1, sm2, sn1, sn2,
+                                  t->out_kind, t->alpha, out, x3, dst ? t->kseg2 : t->kseg, etid);
+                }
             }
-            umma_commit(&empty[s]);
+            ++j;
         }
-        umma_commit(&accum);
     }
-    __syncwarp();
-    // epilogue: every warp waits for the accumulator, stages its 32 rows in shared memory
-    // (the operand ring is free: every issued copy was consumed by a finished MMA)
-    const bool ready = mbar_wait(&accum, 0, err);
-    launch_dependents();  // the next kernel may start its prologue during this epilogue
-    fence_after();
-    const int all_ready = __syncthreads_and(ready ? 1 : 0);
-    if (all_ready) {
-        const int ncols = min(BN, t.N - n0), rows = min(BM, t.M - m0);
-        float* tile = (float*)smem;
-        long long* roff = (long long*)(tile + BM * (EC + 1));
-        long long* coff = roff + BM;
-        const int row = warp * 32 + lane;
-#pragma unroll 1
-        for (int c0 = 0; c0 < ncols; c0 += EC) {
-            const int cn = min(EC, ncols - c0);
-            const int nchunk = (cn + 15) & ~15;  // tcgen05.ld is warp-collective: uniform bound
-            __syncthreads();                     // the previous chunk has been written out
-#pragma unroll 1
-            for (int c = 0; c < nchunk; c += 16) {
-                uint32_t v[16];
-                tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c0 + c), v);
-#pragma unroll
-                for (int j = 0; j < 16; ++j)
-                    if (c + j < EC) tile[row * (EC + 1) + c + j] = __uint_as_float(v[j]);
-            }
-            for (int dst = 0; dst < (t.C2 ? 2 : 1); ++dst) {
-                void* out = dst ? t.C2 : t.C;
-                const long long sm1 = dst ? t.d_m1 : t.c_m1, sm2 = dst ? t.d_m2 : t.c_m2;
-                const long long sn1 = dst ? t.d_n1 : t.c_n1, sn2 = dst ? t.d_n2 : t.c_n2;
-                const int x3 = (t.x3 >> (2 * dst)) & 3;
-                epilogue_dest(tile, roff, coff, rows, cn, m0, n0 + c0, t.M2, t.N2, sm1, sm2, sn1, sn2, t.out_kind,
-                              t.alpha, out, x3, dst ? t.kseg2 : t.kseg);
-            }
-        }
+    __syncthreads();
+    // drain after a failed wait (here or in another CTA): the MMAs issued must have finished
+    // before TMEM is released, and the producer's copies must have landed before the CTA exits
+    // (its shared memory may be given to the next CTA).  mma_done is committed after the MMA
+    // loop in every case; these waits ignore the error word and have their own bound.
+    if (threadIdx.x == 0 && *(volatile int*)err) {
+        mbar_wait_own(&mma_done, 0);
+        const int n_issued = issued;
+        for (int g = (n_issued > stages ? n_issued - stages : 0); g < n_issued; ++g)
+            mbar_wait_own(&full[g % stages], (g / stages) & 1);
     }
     fence_before();
     __syncthreads();
-    // drain: the MMAs issued must have finished before TMEM is released, and the producer's
-    // copies must have landed before shared memory is.  On success the MMA warp already waited
-    // for every issued copy and the epilogue for every MMA, so only a pipeline that stopped on
-    // a timed-out wait (here or in another CTA) can still have work in flight.  The MMA warp
-    // commits the accumulator barrier after its loop in every case, so it completes once the
-    // MMAs issued before it have; these waits ignore the error word.
-    if (!all_ready && threadIdx.x == 0) {
-        mbar_wait_own(&accum, 0);
-        const int n_issued = issued;
-        for (int kb = (n_issued > stages ? n_issued - stages : 0); kb < n_issued; ++kb)
-            mbar_wait_own(&full[kb % stages], (kb / stages) & 1);
-    }
-    __syncthreads();
-    if (warp == 0) tmem_dealloc(tmem, BN < 32 ? 32 : BN);
+    if (warp == 0) tmem_dealloc(tmem, TCOLS);
 }
 
 }  // namespace tc
 
 // Dynamic shared memory: the operand ring, or the staged epilogue tile and its offsets
 // if that is larger, plus 1 KB for the 1024-byte alignment of the swizzled ring.
+// Dynamic shared memory: the operand ring and the epilogue's staging tile with its offsets,
+// plus 1 KB for the 1024-byte alignment of the swizzled ring.
 static size_t tc_smem(int stages, int bn, int ksub) {
     const size_t ring = (size_t)stages * (tc::BM + bn) * tc::KBYTES * ksub;
-    const size_t tile = (size_t)tc::BM * (tc::EC + 1) * sizeof(float) + (size_t)(tc::BM + tc::EC) * sizeof(long long);
-    return std::max(ring, tile) + 1024;
+    return ring + tc::EPI_BYTES + 1024;
 }
 
-// Deepest ring (stages of ksub k-blocks) that fits the 227 KB of shared memory a CTA may hold
-// (2 KB kept for the static barriers and the task): for ksub = 1, 8 stages for BN <= 64, 7 for
-// 128, 4 for 256; for ksub = 2, 5 / 4 / 3 / 2 for BN = 32 / 64 / 128 / 256.
-
-// Default ring depth: up to 4 stages within ~96 KB of shared memory (so that two CTAs share an
-// SM and one's epilogue overlaps the other's loads and MMAs), at least 2, at most the stages
-// the K extent needs.
-int tc_default_stages(int bn, int kblocks) {  // one k-block per stage
-    const int per = (tc::BM + bn) * tc::KBYTES;
-    const int depth = std::max(2, std::min(4, (96 * 1024) / per));
-    return std::max(1, std::min(std::min(kblocks, depth), tc_max_stages(bn, 1)));
-}
+// Deepest ring (stages of ksub k-blocks) that fits, next to the epilogue's staging tile, the
+// 227 KB of shared memory a CTA may hold (2 KB kept for the static barriers).
 int tc_max_stages(int bn, int ksub) {
     if (ksub < 1 || ksub > tc::KSUB_MAX) return 0;
     const size_t per = (size_t)(tc::BM + bn) * tc::KBYTES * ksub;
-    const size_t cap = 232448 - 2048 - 1024;
+    const size_t cap = 232448 - 2048 - 1024 - tc::EPI_BYTES;
     return std::max(1, std::min(tc::STAGES, (int)(cap / per)));
+}
+
+// Default ring depth (one k-block per stage): up to 4 stages, at least 2, at most the stages
+// the K extent needs and the shared memory holds.
+int tc_default_stages(int bn, int kblocks) {
+    return std::max(1, std::min(std::min(kblocks, 4), tc_max_stages(bn, 1)));
+}
+
+static int tc_sm_count() {
+    static std::atomic<int> cached{0};  // read by the server's worker and read-out threads
+    int n = cached.load(std::memory_order_relaxed);
+    if (n == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) n = 1;
+        cached.store(n, std::memory_order_relaxed);
+    }
+    return n;
 }
 
 cudaError_t tc_prepare() {
@@ -533,21 +612,25 @@ cudaError_t launch_tc_gemm(const TCTask* d_tasks, int ntasks, int kind, int bn, 
     if (ksub < 1) ksub = 1;
     if (stages < 1 || stages > tc_max_stages(bn, ksub)) return cudaErrorInvalidValue;
     const size_t smem = tc_smem(stages, bn, ksub);
-    dim3 grid(max_tiles, ntasks);
+    // persistent CTAs: as many as fit on the GPU at once, never more than the work items
+    const long long items = (long long)ntasks * max_tiles;
+    const int per_sm = std::max(1, std::min(4, (int)((233472 - 2048) / (smem + 2048))));
+    const int grid = (int)std::max(1LL, std::min(items, (long long)tc_sm_count() * per_sm));
     // programmatic dependent launch: the kernel waits (griddepcontrol.wait) before it reads
     // anything an earlier kernel wrote
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.gridDim = grid;
-    cfg.blockDim = dim3(128);
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(tc::NTHREADS);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-#define TC_CASE(K_, N_)                                                              \
-    if (kind == K_ && bn == N_) return cudaLaunchKernelEx(&cfg, tc::k_tc_gemm<K_, N_>, d_tasks, err, stages, ksub, stall);
+#define TC_CASE(K_, N_)                                                                                        \
+    if (kind == K_ && bn == N_)                                                                                \
+        return cudaLaunchKernelEx(&cfg, tc::k_tc_gemm<K_, N_>, d_tasks, ntasks, max_tiles, err, stages, ksub, stall);
     TC_CASE(0, 32) TC_CASE(0, 64) TC_CASE(0, 128) TC_CASE(0, 256)
     TC_CASE(1, 32) TC_CASE(1, 64) TC_CASE(1, 128) TC_CASE(1, 256)
 #undef TC_CASE

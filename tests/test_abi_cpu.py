@@ -138,12 +138,16 @@ def test_random_descriptions_plan_within_bounds(libpath):
 
 
 def test_shifted_partition_descriptions(libpath):
-    """Shifted partitions exist on infinite lattices only, with 0 <= shift < unit cell."""
+    """Shifted partitions: on infinite lattices 0 <= shift < unit cell (same footprint); with
+    OBC 0 <= shift < block side, the blocks on the lattice edges narrower (a 4x4 lattice in
+    2x2 blocks shifted by (1, 1) has 3 x 3 blocks and 24 messages instead of 8)."""
     from paper_2301_05844_gb300 import binding as B
     cell = dict(Lx=2, Ly=2, d=2, D=2, bx=4, by=4, chi=4, boundary="infinite")
     assert B.footprint(shift=(1, 1), **cell) == B.footprint(**cell)
-    for bad in (dict(cell, shift=(2, 0)), dict(cell, shift=(0, -1)),
-                dict(Lx=4, Ly=4, d=2, D=2, bx=2, by=2, chi=4, shift=(1, 0))):
+    obc = dict(Lx=4, Ly=4, d=2, D=2, bx=2, by=2, chi=4)
+    assert B.footprint(shift=(1, 1), **obc) > B.footprint(shift=(1, 0), **obc) > B.footprint(**obc)
+    for bad in (dict(cell, shift=(2, 0)), dict(cell, shift=(0, -1)), dict(obc, shift=(2, 0)),
+                dict(obc, shift=(0, -1))):
         with pytest.raises(B.BBPError) as e:
             B.footprint(**bad)
         assert e.value.code == B.ERR_INVALID

@@ -279,11 +279,37 @@ __device__ __forceinline__ void epilogue_dest(const float* tile, long long* roff
     // a split destination vectorises only if every segment start stays 16-byte aligned
     const bool segs_aligned = !x3 || ((kseg * esz) & 15) == 0;
     float x[8];
-    // Two passes per destination: 16-byte vectors where a group of VW elements is contiguous
-    // and aligned in the destination, then every other element with consecutive lanes on
-    // consecutive destination addresses (so that a warp's scalar stores share a few sectors:
-    // the site-update operands of D=5 have contiguous runs of K = 25 elements, and split rows
-    // whose segments are K apart, neither of which is 16-byte aligned).
+    // A split destination whose segments are not 16-byte aligned takes no vector at all (the
+    // site-update operands of D=5: split rows whose segments are K = 625 apart): one pass of
+    // scalar stores, each warp on one row (one column) at a time with its lanes on consecutive
+    // destination addresses, no per-element index arithmetic beyond the two offsets.
+    if (!segs_aligned && (sn2 == 1 || sm2 == 1)) {
+        const int wq = tid >> 5, ln = tid & 31;
+        constexpr int NW = EPI_THREADS / 32;
+        if (sn2 == 1) {
+            for (int r = wq; r < rows; r += NW) {
+                const long long ro = roff[r];
+                for (int c = ln; c < ncols; c += 32) {
+                    const float xv = tile[r * P + c] * alpha;
+                    if (x3) store_split1(out, ro + coff[c], kind, xv, x3, kseg);
+                    else store_out(out, ro + coff[c], kind, xv);
+                }
+            }
+        } else {
+            for (int c = wq; c < ncols; c += NW) {
+                const long long co = coff[c];
+                for (int r = ln; r < rows; r += 32) {
+                    const float xv = tile[r * P + c] * alpha;
+                    if (x3) store_split1(out, roff[r] + co, kind, xv, x3, kseg);
+                    else store_out(out, roff[r] + co, kind, xv);
+                }
+            }
+        }
+        return;
+    }
+    // Otherwise two passes: 16-byte vectors where a group of VW elements is contiguous and
+    // aligned in the destination, then every other element with consecutive lanes on
+    // consecutive destination addresses (so that a warp's scalar stores share a few sectors).
     if (sn2 == 1) {
         const int G = (ncols + VW - 1) / VW;
         auto is_vec = [&](int r, int c0) {

@@ -122,13 +122,16 @@ class Clocks:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def make_lattice(B, cfg, prec, stream):
+KEEP_FP64 = 0  # --keep-fp64: FP64 QR/LQ and read-out closings on the tensor-core paths too
+
+
+def make_lattice(B, cfg, prec, stream, launch_mode=0):
     dtype = {np.dtype(np.float64): B.F64, np.dtype(np.float32): B.F32, np.dtype(np.complex64): B.C64,
              np.dtype(np.complex128): B.C128}[np.asarray(cfg["tensors"][0]).dtype]
     g = B.Lattice(Lx=cfg["Lx"], Ly=cfg["Ly"], d=cfg["d"], D=cfg["D"], bx=cfg["bx"], by=cfg["by"], chi=cfg["chi"],
                   boundary=cfg["boundary"], dtype=dtype, prec=prec, tol=cfg.get("tol", 1e-8), max_sweeps=50,
                   fit_tol=FIT_TOL[prec], fit_max_sweeps=10, seed=1, warm_start=WARM, stream=stream,
-                  single_layer=cfg.get("single_layer", 0))
+                  single_layer=cfg.get("single_layer", 0), launch_mode=launch_mode, keep_fp64=KEEP_FP64)
     return g
 
 
@@ -307,7 +310,7 @@ def golden_error(B, cfg, prec, stream, torch):
     for pr in (prec, "fp64"):
         g = B.Lattice(Lx=p["L"], Ly=p["L"], d=p["d"], D=p["D"], bx=p["block"], by=p["block"], chi=p["chi"],
                       dtype=B.F32, prec=pr, fit_tol=p["fit_tol"], fit_max_sweeps=p["fit_max_sweeps"], seed=p["seed"],
-                      warm_start=int(p["warm_start"]), stream=stream)
+                      warm_start=int(p["warm_start"]), stream=stream, keep_fp64=KEEP_FP64)
         g.set_tensors(T)
         g.sweep(p["sweeps"])
         v = g.expect(terms)
@@ -334,9 +337,34 @@ def run_replay(args):
                                                 dtype=np.asarray(cfg["tensors"][0]).dtype))
     prec = args.prec or cfg.get("prec", "tf32")
     torch.cuda.set_device(0)
+    if args.replay == "readout":
+        g = make_lattice(B, cfg, prec, None, launch_mode=1)
+        g.set_tensors(cfg["tensors"])
+        g.sweep(2)
+        n = cfg["Lx"] * cfg["Ly"]
+        terms = [[(s_, I.SIGMA_Z)] for s_ in range(n)] + [[(s_, I.SIGMA_X)] for s_ in range(n)]
+        torch.cuda.synchronize()
+        torch.cuda.profiler.start()  # for `ncu --profile-from-start off`: the read-out's launches only
+        t0 = time.perf_counter()
+        g.expect(terms)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+        print(json.dumps({"workload": cfg["name"], "prec": prec, "readout_s": time.perf_counter() - t0,
+                          "observables": len(terms)}), flush=True)
+        g.close()
+        return
     g = make_lattice(B, cfg, prec, None)
     g.set_tensors(cfg["tensors"])
     g.sweep(1)
+    if args.replay == "steps":
+        # every launch of the sweep timed on its own, with its work and the tile width
+        rows = g.time_steps(reps=3)
+        for r in rows:
+            r["tflops"] = r["flops"] / max(r["ms"], 1e-9) / 1e9
+            r["gbs"] = r["bytes"] / max(r["ms"], 1e-9) / 1e6
+            print(json.dumps({"workload": cfg["name"], "prec": prec, **r}), flush=True)
+        g.close()
+        return
     for cls in [int(c) for c in args.replay.split(",")]:
         ms, n, f, by = C.c_double(), C.c_longlong(), C.c_double(), C.c_double()
         rc = B.lib().bbp_time_kernels(g.h, cls, 1, C.byref(ms), C.byref(n), C.byref(f), C.byref(by))
@@ -625,6 +653,8 @@ def main():
     ap.add_argument("--no-readout", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-oracle-error", action="store_true")
+    ap.add_argument("--keep-fp64", action="store_true",
+                    help="tensor-core paths: QR/LQ truncations and read-out closings in FP64 arithmetic (default FP32)")
     ap.add_argument("--serve", action="store_true")
     ap.add_argument("--requests", type=int, default=24)
     ap.add_argument("--serve-requests", type=int, default=24,
@@ -632,9 +662,13 @@ def main():
     ap.add_argument("--seed", type=int, default=5)
     ap.add_argument("--serve-gb", type=float, default=64.0)
     ap.add_argument("--max-active", type=int, default=16)
-    ap.add_argument("--replay", default=None, help="kernel classes to replay once (for ncu), e.g. 0,2")
+    ap.add_argument("--replay", default=None, help="kernel classes to replay once (for ncu), e.g. 0,2; 'readout': "
+                                                   "one read-out of every site's <sz>, <sx> with every kernel launched on its own; "
+                                                   "'steps': every launch of a sweep timed on its own (one JSON line each)")
     ap.add_argument("--lattice", type=int, default=0, help="with --replay: the workload's recipe on an L x L lattice")
     args = ap.parse_args()
+    global KEEP_FP64
+    KEEP_FP64 = int(args.keep_fp64)
     if args.replay:
         run_replay(args)
     elif args.serve and args.impl == "ours":

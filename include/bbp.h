@@ -51,12 +51,14 @@ typedef enum { BBP_OBC = 0, BBP_INFINITE = 1 } bbp_boundary;
 typedef enum { BBP_F64 = 0, BBP_C128 = 1, BBP_F32 = 2, BBP_C64 = 3 } bbp_dtype;
 /* Arithmetic of the contractions.  FP64: every step in FP64 on the GPU.  TF32 and
  * BF16: the site-update contractions on tensor cores with FP32 accumulation, while
- * the QR/LQ truncation, message normalisation, residual and read-out ratios stay FP64.
+ * the message normalisation, residual and read-out ratios stay FP64.
  * TF32X3: as TF32, but every operand is split into a TF32 high part and a TF32 low part
  * (the rounding remainder) and each product is A_hi B_hi + A_lo B_hi + A_hi B_lo, all in
  * one FP32 accumulator: FP32-level contraction accuracy at three times the MMA work.
  * BF16X3: the same split with BF16 parts (hi = bf16(x), lo = bf16(x - hi)): operands carry
- * 16 significant bits, at three BF16 MMAs per product (1.5 times the TF32 MMA time). */
+ * 16 significant bits, at three BF16 MMAs per product (1.5 times the TF32 MMA time).
+ * On the four tensor-core paths the QR/LQ truncations and the read-out closings run in FP32
+ * arithmetic unless desc->keep_fp64 is set. */
 typedef enum {
     BBP_PREC_FP64 = 0,
     BBP_PREC_TF32 = 1,
@@ -132,12 +134,20 @@ typedef struct {
                                 same kernels launched one by one on the stream, each fit loop
                                 run to fit_max_sweeps with the converged fits skipped (same
                                 results; lets a kernel profiler see every launch) */
+    int keep_fp64;           /* TF32 / BF16 / TF32X3 / BF16X3 paths: 0 runs the stages outside
+                                the tensor cores in FP32 arithmetic: the QR/LQ truncations
+                                (their input is already an FP32 contraction result; Q is
+                                still stored in FP64 and the fit loss summed in FP64) and the
+                                read-out closings (FP64 operands rounded to FP32, FP32
+                                accumulation, FP64 results, every environment of a strip
+                                rescaled by a power of two so that nothing overflows); 1 keeps
+                                FP64 arithmetic there.  The FP64 path always uses FP64. */
 } bbp_lattice_desc;
 
 /* Validate desc, allocate the device arena (double layer, message store, work
  * buffers) and plan one sweep.  *out receives the handle.  Limits checked here:
  * Lx, Ly <= 4096; bx, by <= 16; D <= 16; d <= 64; 1 <= fit_max_sweeps <= 64;
- * init_mode, warm_start, hermitian_basis, single_layer and launch_mode 0 or 1; 0 <= shift_x < Lx and
+ * init_mode, warm_start, hermitian_basis, single_layer, launch_mode and keep_fp64 0 or 1; 0 <= shift_x < Lx and
  * 0 <= shift_y < Ly on infinite lattices, 0 <= shift_x < bx and 0 <= shift_y < by with OBC.
  * Errors: INVALID, OOM, CUDA. */
 int bbp_create_lattice(const bbp_lattice_desc* desc, bbp_lattice** out);
@@ -317,6 +327,14 @@ int bbp_selftest_gemm_timeout(void);
 int bbp_selftest_scalar(long long n, const double* x, double* rsqrt_ours, double* rcp_ours, double* rsqrt_cuda,
                         double* rcp_cuda);
 
+/* Not a step of the method: the self-test of the FP32-arithmetic blocked Householder QR that
+ * the tensor-core paths use for the truncation of App. A (Q with diag(R) >= 0).  A holds
+ * batch row-major m x n FP32 matrices on the host; Q receives their thin Q factors (FP64,
+ * same layout) and loss (may be NULL) -||A_b||^2.  Every task's 2 m n workspace is followed by
+ * guard words; *workspace_intact is 1 if the QR left them unchanged.  Errors: INVALID, OOM,
+ * CUDA. */
+int bbp_selftest_qr_fp32(int batch, int m, int n, const float* A, double* Q, double* loss, int* workspace_intact);
+
 /* Kernel-class timing of one planned sweep, for roofline measurements: replays, on
  * the handle's stream and bracketed by CUDA events, only the launches of one class
  * (0: tensor-core GEMM steps, 1: FP64 strided contractions, 2: FP64 QR/LQ),
@@ -327,6 +345,24 @@ int bbp_selftest_scalar(long long n, const double* x, double* rsqrt_ours, double
  * least (operands read once, results written once).  Errors: INVALID, STATE, CUDA. */
 int bbp_time_kernels(bbp_lattice* lat, int kernel_class, int reps, double* ms, long long* launches,
                      double* flops, double* bytes);
+
+/* One row of bbp_time_steps: a launch of the planned sweep, in program order. */
+typedef struct {
+    int index;               /* step index in the sweep program */
+    int kernel_class;        /* 0 tensor-core GEMM, 1 FP64 strided contraction, 2 QR/LQ */
+    int tasks;               /* task descriptors (independent problems) in the launch */
+    int tile_n;              /* tensor-core steps: tile width BN; otherwise 0 */
+    long long max_m, max_n, max_k;  /* largest task dimensions (QR: m, n; K 0) */
+    double flops, bytes;     /* algorithmic work of the launch, as bbp_time_kernels counts it */
+    double ms;               /* device milliseconds per launch */
+} bbp_step_time;
+
+/* Per-launch timing of one planned sweep: every launch of classes 0-2 replayed on its own
+ * (reps times after one warm-up, CUDA events on the handle's stream, every fit stage active;
+ * a fit loop's body appears once), in program order.  Writes min(cap, launches) rows to out
+ * (may be NULL with cap 0) and the number of such launches to *n_steps.  Like
+ * bbp_time_kernels it writes only work buffers.  Errors: INVALID, STATE, CUDA, TIMEOUT. */
+int bbp_time_steps(bbp_lattice* lat, int reps, int cap, bbp_step_time* out, int* n_steps);
 
 /* Launch-shape autotuner (the batching pattern's tiles chosen per workload rather than by a
  * fixed rule).  Must run after bbp_set_tensors and before the first bbp_sweep.  It times,

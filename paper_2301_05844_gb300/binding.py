@@ -33,7 +33,15 @@ class Desc(C.Structure):
         ("stop_relative", C.c_int), ("fit_tol", C.c_double), ("fit_max_sweeps", C.c_int),
         ("seed", C.c_ulonglong), ("init_mode", C.c_int), ("warm_start", C.c_int),
         ("hermitian_basis", C.c_int), ("stream", C.c_void_p), ("single_layer", C.c_int),
-        ("shift_x", C.c_int), ("shift_y", C.c_int), ("launch_mode", C.c_int),
+        ("shift_x", C.c_int), ("shift_y", C.c_int), ("launch_mode", C.c_int), ("keep_fp64", C.c_int),
+    ]
+
+
+class StepTime(C.Structure):
+    _fields_ = [
+        ("index", C.c_int), ("kernel_class", C.c_int), ("tasks", C.c_int), ("tile_n", C.c_int),
+        ("max_m", C.c_longlong), ("max_n", C.c_longlong), ("max_k", C.c_longlong),
+        ("flops", C.c_double), ("bytes", C.c_double), ("ms", C.c_double),
     ]
 
 
@@ -83,6 +91,7 @@ def lib():
     L.bbp_qr_batched_noalloc.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, P, P, P, P]
     L.bbp_lattice_footprint.argtypes = [C.POINTER(Desc), C.POINTER(C.c_size_t)]
     L.bbp_autotune.argtypes = [P, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_int)]
+    L.bbp_time_steps.argtypes = [P, C.c_int, C.c_int, C.POINTER(StepTime), C.POINTER(C.c_int)]
     L.bbp_server_create.argtypes = [C.c_size_t, C.c_int, C.POINTER(P)]
     L.bbp_server_submit.argtypes = [P, C.POINTER(Desc), P, C.POINTER(Term), C.c_int, C.POINTER(C.c_longlong)]
     L.bbp_server_poll.argtypes = [P, C.c_longlong, C.POINTER(C.c_int), C.POINTER(C.c_double),
@@ -111,11 +120,11 @@ def _check(rc):
 
 def make_desc(Lx, Ly, d, D, bx, by, chi, boundary="obc", chi_exp=0, dtype=F64, prec="fp64", tol=1e-5,
               max_sweeps=10, stop_relative=0, fit_tol=1e-6, fit_max_sweeps=10, seed=0, init_mode=0, warm_start=0,
-              hermitian_basis=0, stream=None, single_layer=0, shift=(0, 0), launch_mode=0):
+              hermitian_basis=0, stream=None, single_layer=0, shift=(0, 0), launch_mode=0, keep_fp64=0):
     return Desc(Lx, Ly, OBC if boundary == "obc" else INFINITE, d, D, bx, by, chi, chi_exp, dtype,
                 _PREC[prec] if isinstance(prec, str) else prec, tol, max_sweeps, stop_relative, fit_tol,
                 fit_max_sweeps, seed, init_mode, int(warm_start), int(hermitian_basis), stream, int(single_layer),
-                int(shift[0]), int(shift[1]), int(launch_mode))
+                int(shift[0]), int(shift[1]), int(launch_mode), int(keep_fp64))
 
 
 def _term_array(terms):
@@ -299,6 +308,14 @@ class Lattice:
         the Hermitian basis)."""
         d = self.desc
         return d.dtype in (C128, C64) and d.prec == PREC_FP64 and not d.hermitian_basis
+
+    def time_steps(self, reps=3):
+        """Every launch of the planned sweep timed on its own (bbp_time_steps): a list of dicts."""
+        n = C.c_int()
+        _check(lib().bbp_time_steps(self.h, reps, 0, None, C.byref(n)))
+        rows = (StepTime * max(n.value, 1))()
+        _check(lib().bbp_time_steps(self.h, reps, n.value, rows, C.byref(n)))
+        return [{f: getattr(r, f) for f, _ in StepTime._fields_} for r in rows[:n.value]]
 
     def autotune(self, reps=3):
         """Choose the tensor-core tile shapes of the planned sweep by timing them (before

@@ -43,7 +43,8 @@ struct QRTask {
     int m, n;
     long long in_rs, in_cs, out_rs, out_cs;
     int conj_io;
-    int in_float;    // 1: input is FP32 (mixed path), 0: the FP64 scalar type
+    int in_float;    // 0: input in the FP64 scalar type; 1: FP32 input (mixed path), FP64
+                     // arithmetic; 2: FP32 input and FP32 arithmetic (see QR_F32)
     void* out2;      // optional second copy of Q in a low-precision operand layout:
                      // element (i, k) at (i / out2_M2) * out2_rs + (i % out2_M2) * out2_rs2 + k * out2_cs
     long long out2_rs, out2_cs, out2_rs2;
@@ -144,6 +145,20 @@ struct DLTask {
 // leg m (read-out of a horizontal pair):
 //   out[(u1 u2)][l1][(d1 d2)][r2] = sum_m A[u1][l1][d1][m] B[u2][m][d2][r2]
 // with A, B given as strided 4-leg views (u, l, d, r); out is contiguous.
+// Inner product (step aux 0): *out = 2^(*ea + *eb) sum_x A[x] B[x] over n scalars of the
+// program's scalar type, no conjugation (a null exponent pointer reads as 0).
+// Power-of-two normalisation (step aux 1): A (n scalars) is multiplied in place by 2^-e,
+// 2^(e-1) <= max |component| < 2^e (e = 0 for a zero or non-finite buffer), and the int
+// *out becomes e + *ea.  B and eb are unused.
+struct DotTask {
+    const void* A;
+    const void* B;
+    void* out;
+    long long n;
+    const int* ea;
+    const int* eb;
+};
+
 struct FuseTask {
     const void* A;
     const void* B;
@@ -183,13 +198,17 @@ struct RatioTask {
 };
 
 // Launchers (kernels.cu).  cplx selects double2 (complex) over double.
-// small != 0: 16x16 output tiles, one output per thread (steps whose outputs have a
-// dimension of at most 16); max_tiles counts tiles of the chosen size.
-cudaError_t launch_gcontract(const GTask* d_tasks, int ntasks, int max_tiles, bool cplx, cudaStream_t s, int small);
+// mode bit 0: 16x16 output tiles, one output per thread (steps whose outputs have a
+// dimension of at most 16); max_tiles counts tiles of the chosen size.  mode | GC_F32: FP64
+// operands and results, FP32 arithmetic.
+constexpr int GC_F32 = 1 << 8;
+cudaError_t launch_gcontract(const GTask* d_tasks, int ntasks, int max_tiles, bool cplx, cudaStream_t s, int mode);
 cudaError_t qr_prepare(int max_m, bool cplx);  // sets the dynamic shared memory limit once
 // max_mn: largest m*n of the launch; small problems keep their matrices in shared memory.
-// cluster > 0: spread each task over that many CTAs (if its matrices fit; else the smallest
-// larger C that fits); 0: the built-in rule.  The result does not depend on it.
+// cluster (low byte) > 0: spread each task over that many CTAs (if its matrices fit; else the
+// smallest larger C that fits); 0: the built-in rule.  The result does not depend on it.
+// cluster | QR_F32: every task has in_float == 2 and is factored in FP32 arithmetic.
+constexpr int QR_F32 = 1 << 8;
 cudaError_t launch_qr(const QRTask* d_tasks, int ntasks, int max_m, long long max_mn, bool cplx, cudaStream_t s,
                       int cluster = 0);
 // whether one QR of the given maximal shape fits a cluster of C CTAs
@@ -203,6 +222,7 @@ cudaError_t launch_check(const CheckTask* d_tasks, int ntasks, double tol, LoopD
 cudaError_t launch_scale(const ScaleTask* d_tasks, int ntasks, bool cplx, int* status, cudaStream_t s);
 cudaError_t launch_assemble(const AssembleTask* d_tasks, int ntasks, bool cplx, cudaStream_t s);
 cudaError_t launch_normalise(const NormTask* d_tasks, int ntasks, bool cplx, cudaStream_t s);
+cudaError_t launch_dot(const DotTask* d_tasks, int ntasks, bool cplx, cudaStream_t s, int normalise);
 cudaError_t launch_mean(const double* in, int n, double* out, cudaStream_t s);
 cudaError_t launch_double_layer(const DLTask* d_tasks, int ntasks, long long max_out, bool cplx, cudaStream_t s);
 // complex T and O (Hermitian), real E in the Hermitian basis of every merged leg

@@ -17,6 +17,7 @@
 #include <cstddef>
 #include <complex>
 #include <new>
+#include <stdexcept>
 #include <string>
 #include <type_traits>
 #include <vector>
@@ -155,6 +156,18 @@ std::string Program::validate() const {
         c.range(t.corner0, 1, ss, "corner", i);
         c.range(t.corner1, 1, ss, "corner", i);
     }
+    for (const Step& s : steps) {
+        if (s.kind != ST_DOT) continue;
+        for (int k = 0; k < s.count; ++k) {
+            const size_t i = s.first + k;
+            const DotTask& t = dots[i];
+            c.range(t.A, t.n, ss, "dot A", i);
+            if (s.aux == 0) c.range(t.B, t.n, ss, "dot B", i);
+            c.range(t.out, 1, s.aux == 0 ? ss : 4, "dot out", i);
+            c.range(t.ea, 1, 4, "dot exponent", i);
+            if (s.aux == 0) c.range(t.eb, 1, 4, "dot exponent", i);
+        }
+    }
     for (size_t i = 0; i < nrm.size(); ++i) {
         const NormTask& t = nrm[i];
         c.range(t.site0, t.size0, ss, "norm site0", i);
@@ -251,7 +264,7 @@ void Program::gc_step(std::vector<GTask>& ts) {
         gc.push_back(t);
     }
     s.aux = mt;
-    s.aux2 = small ? 1 : 0;
+    s.aux2 = (small ? 1 : 0) | (gc_f32 ? GC_F32 : 0);
     steps.push_back(s);
     ts.clear();
 }
@@ -273,7 +286,9 @@ void Program::qr_step(std::vector<QRTask>& ts) {
     s.count = (int)ts.size();
     int mm = 1;
     long long mn = 1;
+    int f32 = 0;
     for (auto& t : ts) {
+        f32 += t.in_float == 2;
         mm = std::max(mm, t.m);
         mn = std::max(mn, (long long)t.m * t.n);
         const double f = (4.0 * t.m * (double)t.n * t.n - 4.0 / 3.0 * (double)t.n * t.n * t.n) * (cplx ? 4.0 : 1.0);
@@ -282,7 +297,25 @@ void Program::qr_step(std::vector<QRTask>& ts) {
     }
     s.aux = mm;
     s.n = mn;
+    // FP32-arithmetic tasks form steps of their own (the planner never mixes the two)
+    if (f32 != 0 && f32 != (int)ts.size()) throw std::logic_error("QR step mixes FP32 and FP64 arithmetic");
+    s.aux2 = f32 ? QR_F32 : 0;
     max_qr_m = std::max(max_qr_m, mm);
+    steps.push_back(s);
+    ts.clear();
+}
+
+void Program::dot_step(std::vector<DotTask>& ts, bool normalise) {
+    if (ts.empty()) return;
+    Step s;
+    s.kind = ST_DOT;
+    s.first = dots.size();
+    s.count = (int)ts.size();
+    s.aux = normalise ? 1 : 0;
+    for (auto& t : ts) {
+        if (!normalise) count_flops(nullptr, 2.0 * (double)t.n * (cplx ? 4.0 : 1.0), false);
+        dots.push_back(t);
+    }
     steps.push_back(s);
     ts.clear();
 }
@@ -636,6 +669,9 @@ void Program::relocate(char* base, size_t split, char* base2) {
     for (auto& t : dl) {
         RELOC(t.T); RELOC(t.E); RELOC(t.O);
     }
+    for (auto& t : dots) {
+        RELOC(t.A); RELOC(t.B); RELOC(t.out); RELOC(t.ea); RELOC(t.eb);
+    }
     for (auto& t : tcs) {
         RELOC(t.C); RELOC(t.C2); RELOC(t.active);
     }
@@ -706,6 +742,7 @@ cudaError_t Program::upload_tasks(cudaStream_t st) {
     if ((e = upload(nrm, &d_nrm, st)) != cudaSuccess) return e;
     if ((e = upload(fus, &d_fus, st)) != cudaSuccess) return e;
     if ((e = upload(dl, &d_dl, st)) != cudaSuccess) return e;
+    if ((e = upload(dots, &d_dot, st)) != cudaSuccess) return e;
     if ((e = upload(tcs, &d_tcs, st)) != cudaSuccess) return e;
     if ((e = upload(rel, &d_rel, st)) != cudaSuccess) return e;
     if (!tcs.empty()) {
@@ -737,6 +774,7 @@ cudaError_t Program::launch_step(const Step& s, cudaStream_t st, const int* swee
         case ST_TC: return launch_tc_gemm(d_tcs + s.first, s.count, s.aux2 & 0xFF, s.aux, (int)s.n, (s.aux2 >> 8) & 0xFF, tc_err, st,
                                           (s.aux2 >> 16) & 0xFF);
         case ST_REL: return launch_relayout(d_rel + s.first, s.count, s.n, st);
+        case ST_DOT: return launch_dot(d_dot + s.first, s.count, cplx, st, s.aux);
         case ST_LOOP_BEGIN: return launch_set_int((int*)s.p0, 1, 0, st);  // iteration counter = 0
         case ST_LOOP_END: return cudaSuccess;
         default: return cudaErrorInvalidValue;
@@ -861,47 +899,77 @@ static int step_class(int kind) {
     return 3;
 }
 
+int Program::step_class_of(const Step& s) const { return step_class(s.kind); }
+
+void Program::step_work(const Step& s, double* flops, double* bytes, long long* max_m, long long* max_n,
+                        long long* max_k) const {
+    double f = 0, b = 0;
+    long long mm = 0, mn = 0, mk = 0;
+    const int ss = cplx ? 16 : 8;
+    switch (s.kind) {
+        case ST_GC:
+            for (int i = 0; i < s.count; ++i) {
+                const GTask& t = gc[s.first + i];
+                const double M = (double)t.M1 * t.M2, N = (double)t.N1 * t.N2, K = (double)t.K1 * t.K2;
+                f += 2.0 * M * N * K * (cplx ? 4.0 : 1.0);
+                b += (M * K + K * N + M * N) * ss;
+                mm = std::max(mm, (long long)M); mn = std::max(mn, (long long)N); mk = std::max(mk, (long long)K);
+            }
+            break;
+        case ST_QR:
+            for (int i = 0; i < s.count; ++i) {
+                const QRTask& t = qr[s.first + i];
+                f += (4.0 * t.m * (double)t.n * t.n - 4.0 / 3.0 * (double)t.n * t.n * t.n) * (cplx ? 4.0 : 1.0);
+                b += 2.0 * t.m * (double)t.n * ss;
+                mm = std::max(mm, (long long)t.m); mn = std::max(mn, (long long)t.n);
+            }
+            break;
+        case ST_TC:
+            for (int i = 0; i < s.count; ++i) {
+                const TCTask& t = tcs[s.first + i];
+                const TCSpec& sp = tcspec[s.first + i];
+                const int esz = sp.kind == 0 ? 4 : 2, osz = t.out_kind == 2 ? 2 : t.out_kind == 3 ? 8 : 4;
+                f += 2.0 * (double)t.M * t.N * t.K;
+                b += ((double)t.M * t.K + (double)t.N * t.K) * esz + (double)t.M * t.N * osz * (t.C2 ? 2 : 1);
+                mm = std::max(mm, (long long)t.M); mn = std::max(mn, (long long)t.N); mk = std::max(mk, (long long)t.K);
+            }
+            break;
+        default:
+            break;
+    }
+    if (flops) *flops = f;
+    if (bytes) *bytes = b;
+    if (max_m) *max_m = mm;
+    if (max_n) *max_n = mn;
+    if (max_k) *max_k = mk;
+}
+
 cudaError_t Program::launch_class(cudaStream_t st, const int* sweep_ctr, unsigned long long seed, int cls,
                                   long long* launches, double* flops, double* bytes) const {
     long long n = 0;
     double f = 0, b = 0;
-    const int ss = cplx ? 16 : 8;
     for (const Step& s : steps) {
         if (step_class(s.kind) != cls) continue;  // loop bodies count once: one fit sweep
         cudaError_t e = cudaSuccess;
         switch (s.kind) {
             case ST_GC:
                 e = launch_gcontract(d_gc + s.first, s.count, s.aux, cplx, st, s.aux2);
-                for (int i = 0; i < s.count; ++i) {
-                    const GTask& t = gc[s.first + i];
-                    const double M = (double)t.M1 * t.M2, N = (double)t.N1 * t.N2, K = (double)t.K1 * t.K2;
-                    f += 2.0 * M * N * K * (cplx ? 4.0 : 1.0);
-                    b += (M * K + K * N + M * N) * ss;
-                }
                 break;
             case ST_QR:
                 e = launch_qr(d_qr + s.first, s.count, s.aux, s.n, cplx, st, s.aux2);
-                for (int i = 0; i < s.count; ++i) {
-                    const QRTask& t = qr[s.first + i];
-                    f += (4.0 * t.m * (double)t.n * t.n - 4.0 / 3.0 * (double)t.n * t.n * t.n) * (cplx ? 4.0 : 1.0);
-                    b += 2.0 * t.m * (double)t.n * ss;
-                }
                 break;
             case ST_TC:
                 e = launch_tc_gemm(d_tcs + s.first, s.count, s.aux2 & 0xFF, s.aux, (int)s.n, (s.aux2 >> 8) & 0xFF, tc_err, st,
                                    (s.aux2 >> 16) & 0xFF);
-                for (int i = 0; i < s.count; ++i) {
-                    const TCTask& t = tcs[s.first + i];
-                    const TCSpec& sp = tcspec[s.first + i];
-                    const int esz = sp.kind == 0 ? 4 : 2, osz = t.out_kind == 2 ? 2 : t.out_kind == 3 ? 8 : 4;
-                    f += 2.0 * (double)t.M * t.N * t.K;
-                    b += ((double)t.M * t.K + (double)t.N * t.K) * esz + (double)t.M * t.N * osz * (t.C2 ? 2 : 1);
-                }
                 break;
             default:
                 break;
         }
         if (e != cudaSuccess) return e;
+        double sf = 0, sb = 0;
+        step_work(s, &sf, &sb, nullptr, nullptr, nullptr);
+        f += sf;
+        b += sb;
         ++n;
     }
     if (launches) *launches = n;
@@ -916,9 +984,9 @@ void Program::free_all(cudaStream_t st) {
     if (exec) cudaGraphExecDestroy(exec);
     exec = nullptr;
     for (void* p : {(void*)d_gc, (void*)d_qr, (void*)d_rnd, (void*)d_chk, (void*)d_scl, (void*)d_asm, (void*)d_nrm,
-                    (void*)d_fus, (void*)d_dl, (void*)d_tcs, (void*)d_rel})
+                    (void*)d_fus, (void*)d_dl, (void*)d_tcs, (void*)d_rel, (void*)d_dot})
         if (p) cudaFreeAsync(p, st);
-    d_tcs = nullptr; d_rel = nullptr;
+    d_tcs = nullptr; d_rel = nullptr; d_dot = nullptr;
     d_gc = nullptr; d_qr = nullptr; d_rnd = nullptr; d_chk = nullptr;
     d_scl = nullptr; d_asm = nullptr; d_nrm = nullptr; d_fus = nullptr; d_dl = nullptr;
 }

@@ -58,6 +58,7 @@ struct Program {
     std::vector<NormTask> nrm;
     std::vector<FuseTask> fus;
     std::vector<DLTask> dl;
+    std::vector<DotTask> dots;
     GTask* d_gc = nullptr;
     QRTask* d_qr = nullptr;
     RandTask* d_rnd = nullptr;
@@ -67,6 +68,7 @@ struct Program {
     NormTask* d_nrm = nullptr;
     FuseTask* d_fus = nullptr;
     DLTask* d_dl = nullptr;
+    DotTask* d_dot = nullptr;
     long long dl_max_out = 1;
     int* status = nullptr;  // device error word (relocated separately)
     double fit_tol = 0.0;
@@ -90,6 +92,9 @@ struct Program {
     std::string validate() const;
     void gc_step(std::vector<GTask>& ts);
     void qr_step(std::vector<QRTask>& ts);
+    // inner products (normalise = false) or power-of-two normalisations (true), see DotTask
+    void dot_step(std::vector<DotTask>& ts, bool normalise = false);
+    bool gc_f32 = false;  // contraction steps added from now on run in FP32 arithmetic
     void simple(int kind, void* p0, void* p1, long long n, int aux);
     void relocate(char* base, size_t split = (size_t)-1, char* base2 = nullptr);
     void tc_step(std::vector<TCTask>& ts, std::vector<TCSpec>& sp, int kind);
@@ -115,6 +120,11 @@ struct Program {
     cudaError_t build_graph(cudaStream_t st, const int* sweep_ctr, unsigned long long seed);
     // set every fit's active flag (so that a replay runs every gated stage)
     cudaError_t reset_active(cudaStream_t st) const;
+    // class of a step (0 tensor-core GEMM, 1 FP64 contraction, 2 QR/LQ, 3 other) and its
+    // algorithmic work: flops, bytes (operands once, results once), largest task dimensions
+    int step_class_of(const Step& s) const;
+    void step_work(const Step& s, double* flops, double* bytes, long long* max_m, long long* max_n,
+                   long long* max_k) const;
     // launch only the steps of one class (see bbp_time_kernels); returns launches
     cudaError_t launch_class(cudaStream_t st, const int* sweep_ctr, unsigned long long seed, int cls,
                              long long* launches, double* flops, double* bytes) const;
@@ -134,8 +144,8 @@ void emit_fits(Program& pr, int ss, std::vector<FitSpec*>& fits, int max_sweeps,
                bool rand_uses_sweep);
 void emit_overlaps(Program& pr, int ss, std::vector<OverlapSpec>& ov);
 
-// Tensor-core (TF32 / BF16) variant of emit_fits: same stages, same generator
-// streams and the same FP64 QR/LQ, with every contraction on tcgen05.
+// Tensor-core (TF32 / BF16) variant of emit_fits: same stages and generator streams, with
+// every contraction on tcgen05 and the QR/LQ in FP32 (or FP64, MixCtx::qr_f32) arithmetic.
 struct MixCtx {
     int ss = 8;      // canonical (FP64) scalar bytes
     int esz = 4;     // low-precision element bytes
@@ -144,6 +154,7 @@ struct MixCtx {
     int tck = 0;     // tensor-core kind: 0 TF32, 1 BF16
     int tco = 1;     // tensor-core epilogue kind of low-precision results
     bool x3 = false; // split TF32 operands: every K-major row holds three K-segments
+    bool qr_f32 = true;  // QR/LQ truncations in FP32 arithmetic (QRTask::in_float = 2)
 };
 void emit_fits_mixed(Program& pr, const MixCtx& cx, std::vector<FitSpec*>& fits, int max_sweeps, double fit_tol,
                      bool warm, bool rand_uses_sweep);

@@ -11,6 +11,7 @@
 #include <algorithm>
 #include <atomic>
 #include <mutex>
+#include <type_traits>
 
 #include "bbp_internal.h"
 
@@ -57,6 +58,41 @@ __device__ __forceinline__ double shfl_idx(double v, int l) { return __shfl_sync
 __device__ __forceinline__ double2 shfl_idx(double2 v, int l) {
     return make_double2(__shfl_sync(0xffffffffu, v.x, l), __shfl_sync(0xffffffffu, v.y, l));
 }
+// FP32 / complex-FP32 counterparts of the helpers above (the FP32-arithmetic QR of the
+// reduced-precision paths)
+__device__ __forceinline__ float conjv(float a) { return a; }
+__device__ __forceinline__ float2 conjv(float2 a) { return make_float2(a.x, -a.y); }
+__device__ __forceinline__ void mac(float& c, float a, float b) { c = fmaf(a, b, c); }
+__device__ __forceinline__ void mac(float2& c, float2 a, float2 b) {
+    c.x = fmaf(a.x, b.x, fmaf(-a.y, b.y, c.x));
+    c.y = fmaf(a.x, b.y, fmaf(a.y, b.x, c.y));
+}
+__device__ __forceinline__ float abs2(float a) { return a * a; }
+__device__ __forceinline__ float abs2(float2 a) { return a.x * a.x + a.y * a.y; }
+template <> __device__ __forceinline__ float zero<float>() { return 0.0f; }
+template <> __device__ __forceinline__ float2 zero<float2>() { return make_float2(0.0f, 0.0f); }
+template <> __device__ __forceinline__ float one<float>() { return 1.0f; }
+template <> __device__ __forceinline__ float2 one<float2>() { return make_float2(1.0f, 0.0f); }
+template <> __device__ __forceinline__ float from_real<float>(double x) { return (float)x; }
+template <> __device__ __forceinline__ float2 from_real<float2>(double x) { return make_float2((float)x, 0.0f); }
+__device__ __forceinline__ float add(float a, float b) { return a + b; }
+__device__ __forceinline__ float2 add(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float mul(float a, float b) { return a * b; }
+__device__ __forceinline__ float2 mul(float2 a, float2 b) { return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+__device__ __forceinline__ float scal(float a, float s) { return a * s; }
+__device__ __forceinline__ float2 scal(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+__device__ __forceinline__ float divr(float a, float d) { return a / d; }
+__device__ __forceinline__ float2 divr(float2 a, float d) { return make_float2(a.x / d, a.y / d); }
+__device__ __forceinline__ float absv(float a) { return fabsf(a); }
+__device__ __forceinline__ float absv(float2 a) { return hypotf(a.x, a.y); }
+__device__ __forceinline__ float shfl_down(float v, int o) { return __shfl_down_sync(0xffffffffu, v, o); }
+__device__ __forceinline__ float2 shfl_down(float2 v, int o) {
+    return make_float2(__shfl_down_sync(0xffffffffu, v.x, o), __shfl_down_sync(0xffffffffu, v.y, o));
+}
+__device__ __forceinline__ float shfl_idx(float v, int l) { return __shfl_sync(0xffffffffu, v, l); }
+__device__ __forceinline__ float2 shfl_idx(float2 v, int l) {
+    return make_float2(__shfl_sync(0xffffffffu, v.x, l), __shfl_sync(0xffffffffu, v.y, l));
+}
 template <typename S>
 __device__ __forceinline__ S warp_sum(S v) {
     for (int o = 16; o > 0; o >>= 1) v = add(v, shfl_down(v, o));
@@ -101,6 +137,71 @@ __device__ double block_max(double v, double* red) {
     return t;
 }
 
+__device__ float block_max(float v, float* red) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_down_sync(0xffffffffu, v, o));
+    __syncthreads();
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    float t = 0.0f;
+    if (threadIdx.x < 32) {
+        t = (lane < (int)(blockDim.x >> 5)) ? red[lane] : 0.0f;
+        for (int o = 16; o > 0; o >>= 1) t = fmaxf(t, __shfl_down_sync(0xffffffffu, t, o));
+        if (lane == 0) red[0] = t;
+    }
+    __syncthreads();
+    t = red[0];
+    __syncthreads();
+    return t;
+}
+// Real type of a scalar type, its FP64 counterpart, and the thresholds of the Householder
+// step: a squared norm below tiny2 is recomputed relative to the largest entry (its squares
+// would lose bits to underflow), and a divisor below tiny_div is divided by instead of
+// multiplied by its reciprocal (which would overflow).
+template <typename S> struct ScalarTraits;
+template <> struct ScalarTraits<double> {
+    using R = double;
+    using Wide = double;
+    static __device__ __forceinline__ double tiny2() { return 1e-280; }
+    static __device__ __forceinline__ double tiny_div() { return 1e-290; }
+};
+template <> struct ScalarTraits<double2> {
+    using R = double;
+    using Wide = double2;
+    static __device__ __forceinline__ double tiny2() { return 1e-280; }
+    static __device__ __forceinline__ double tiny_div() { return 1e-290; }
+};
+template <> struct ScalarTraits<float> {
+    using R = float;
+    using Wide = double;
+    static __device__ __forceinline__ float tiny2() { return 1e-30f; }
+    static __device__ __forceinline__ float tiny_div() { return 1e-36f; }
+};
+template <> struct ScalarTraits<float2> {
+    using R = float;
+    using Wide = double2;
+    static __device__ __forceinline__ float tiny2() { return 1e-30f; }
+    static __device__ __forceinline__ float tiny_div() { return 1e-36f; }
+};
+__device__ __forceinline__ double sqrt_r(double x) { return sqrt(x); }
+__device__ __forceinline__ float sqrt_r(float x) { return sqrtf(x); }
+__device__ __forceinline__ double hypot_r(double a, double b) { return hypot(a, b); }
+__device__ __forceinline__ double max_r(double a, double b) { return fmax(a, b); }
+__device__ __forceinline__ float max_r(float a, float b) { return fmaxf(a, b); }
+__device__ __forceinline__ float max_component(float a) { return fabsf(a); }
+__device__ __forceinline__ float max_component(float2 a) { return fmaxf(fabsf(a.x), fabsf(a.y)); }
+__device__ __forceinline__ float hypot_r(float a, float b) { return hypotf(a, b); }
+__device__ __forceinline__ double widen(double a) { return a; }
+__device__ __forceinline__ double2 widen(double2 a) { return a; }
+__device__ __forceinline__ double widen(float a) { return (double)a; }
+__device__ __forceinline__ double2 widen(float2 a) { return make_double2((double)a.x, (double)a.y); }
+template <typename Cm> __device__ __forceinline__ Cm narrow(double a);
+template <typename Cm> __device__ __forceinline__ Cm narrow(double2 a);
+template <> __device__ __forceinline__ double narrow<double>(double a) { return a; }
+template <> __device__ __forceinline__ double2 narrow<double2>(double2 a) { return a; }
+template <> __device__ __forceinline__ float narrow<float>(double a) { return (float)a; }
+template <> __device__ __forceinline__ float2 narrow<float2>(double2 a) { return make_float2((float)a.x, (float)a.y); }
+
 // ---------------------------------------------------------------- SplitMix64
 __host__ __device__ __forceinline__ uint64_t sm64(uint64_t z) {
     z += 0x9E3779B97F4A7C15ull;
@@ -121,6 +222,23 @@ template <typename S> __device__ __forceinline__ S from_float(const float* p, lo
 template <> __device__ __forceinline__ double from_float<double>(const float* p, long long i) { return (double)p[i]; }
 template <> __device__ __forceinline__ double2 from_float<double2>(const float* p, long long i) {
     return make_double2((double)p[2 * i], (double)p[2 * i + 1]);
+}
+template <> __device__ __forceinline__ float from_float<float>(const float* p, long long i) { return p[i]; }
+template <> __device__ __forceinline__ float2 from_float<float2>(const float* p, long long i) {
+    return make_float2(p[2 * i], p[2 * i + 1]);
+}
+// element i of an FP64 (complex-FP64) array in the scalar type S
+template <typename S> __device__ __forceinline__ S from_double(const void* p, long long i);
+template <> __device__ __forceinline__ double from_double<double>(const void* p, long long i) { return ((const double*)p)[i]; }
+template <> __device__ __forceinline__ double2 from_double<double2>(const void* p, long long i) {
+    return ((const double2*)p)[i];
+}
+template <> __device__ __forceinline__ float from_double<float>(const void* p, long long i) {
+    return (float)((const double*)p)[i];
+}
+template <> __device__ __forceinline__ float2 from_double<float2>(const void* p, long long i) {
+    const double2 v = ((const double2*)p)[i];
+    return make_float2((float)v.x, (float)v.y);
 }
 __device__ __forceinline__ float tf32_round(float x) {
     uint32_t r;
@@ -179,7 +297,10 @@ __device__ __forceinline__ double load_kind(const void* p, long long i, int kind
 
 // ---------------------------------------------------------------- generic contraction
 // 64x64 output tile per CTA, K in chunks of 16, 256 threads each owning 4x4 outputs.
-template <typename S>
+// Cm is the arithmetic type: S itself, or float / float2 for FP64 operands contracted in FP32
+// arithmetic (each operand rounded to FP32 as it is staged, FP32 accumulation, the result
+// widened to FP64 when stored).
+template <typename S, typename Cm = S>
 __global__ void __launch_bounds__(256) k_gcontract(const GTask* __restrict__ tasks) {
     const GTask& t = tasks[blockIdx.y];
     if (t.active && *t.active == 0) return;
@@ -188,8 +309,8 @@ __global__ void __launch_bounds__(256) k_gcontract(const GTask* __restrict__ tas
     const int tile = blockIdx.x;
     if (tile >= tilesM * tilesN) return;
     const int m0 = (tile % tilesM) << 6, n0 = (tile / tilesM) << 6;
-    __shared__ S As[16][65];
-    __shared__ S Bs[16][65];
+    __shared__ Cm As[16][65];
+    __shared__ Cm Bs[16][65];
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     const S* __restrict__ Ap = (const S*)t.A;
     const S* __restrict__ Bp = (const S*)t.B;
@@ -198,11 +319,11 @@ __global__ void __launch_bounds__(256) k_gcontract(const GTask* __restrict__ tas
     const bool av = am < M, bv = bn < N;
     const long long aoff = av ? (long long)(am / t.M2) * t.a_m1 + (long long)(am % t.M2) * t.a_m2 : 0;
     const long long boff = bv ? (long long)(bn / t.N2) * t.b_n1 + (long long)(bn % t.N2) * t.b_n2 : 0;
-    S acc[4][4];
+    Cm acc[4][4];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = zero<S>();
+        for (int j = 0; j < 4; ++j) acc[i][j] = zero<Cm>();
     for (int k0 = 0; k0 < Kd; k0 += 16) {
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
@@ -216,13 +337,13 @@ __global__ void __launch_bounds__(256) k_gcontract(const GTask* __restrict__ tas
                 }
                 if (bv) b = Bp[boff + (long long)k1 * t.b_k1 + (long long)k2 * t.b_k2];
             }
-            As[kk][lmn] = a;
-            Bs[kk][lmn] = b;
+            As[kk][lmn] = narrow<Cm>(a);
+            Bs[kk][lmn] = narrow<Cm>(b);
         }
         __syncthreads();
 #pragma unroll
         for (int kk = 0; kk < 16; ++kk) {
-            S a[4], b[4];
+            Cm a[4], b[4];
 #pragma unroll
             for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
 #pragma unroll
@@ -245,7 +366,8 @@ __global__ void __launch_bounds__(256) k_gcontract(const GTask* __restrict__ tas
             const int n = n0 + tx + 16 * j;
             if (n >= N) continue;
             const long long o = mo + (long long)(n / t.N2) * t.c_n1 + (long long)(n % t.N2) * t.c_n2;
-            Cp[o] = t.accumulate ? add(Cp[o], acc[i][j]) : acc[i][j];
+            const S r = widen(acc[i][j]);
+            Cp[o] = t.accumulate ? add(Cp[o], r) : r;
         }
     }
 }
@@ -254,8 +376,8 @@ __global__ void __launch_bounds__(256) k_gcontract(const GTask* __restrict__ tas
 // output tile per CTA, one output per thread, operands read through the cache.  A 64x64 tile
 // would spend most of its FP64 instructions on padding, and each warp-wide FP64 instruction
 // costs the same however few lanes do useful work.  The K sum runs in four interleaved partial
-// sums (four independent FP64 chains instead of one), added in a fixed order.
-template <typename S>
+// sums (four independent FP64 chains instead of one), added in a fixed order.  Cm as above.
+template <typename S, typename Cm = S>
 __global__ void __launch_bounds__(256) k_gcontract_small(const GTask* __restrict__ tasks) {
     const GTask& t = tasks[blockIdx.y];
     if (t.active && *t.active == 0) return;
@@ -269,30 +391,44 @@ __global__ void __launch_bounds__(256) k_gcontract_small(const GTask* __restrict
     const S* __restrict__ Bp = (const S*)t.B;
     const long long aoff = (long long)(m / t.M2) * t.a_m1 + (long long)(m % t.M2) * t.a_m2;
     const long long boff = (long long)(n / t.N2) * t.b_n1 + (long long)(n % t.N2) * t.b_n2;
-    S p[4];
+    Cm p[4];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) p[q] = zero<S>();
+    for (int q = 0; q < 4; ++q) p[q] = zero<Cm>();
     int k1 = 0, k2 = 0;  // k = k1 * K2 + k2
 #pragma unroll 4
     for (int k = 0; k < Kd; ++k) {
         S a = Ap[aoff + (long long)k1 * t.a_k1 + (long long)k2 * t.a_k2];
         if (t.conjA) a = conjv(a);
-        mac(p[k & 3], a, Bp[boff + (long long)k1 * t.b_k1 + (long long)k2 * t.b_k2]);
+        mac(p[k & 3], narrow<Cm>(a), narrow<Cm>(Bp[boff + (long long)k1 * t.b_k1 + (long long)k2 * t.b_k2]));
         if (++k2 == t.K2) {
             k2 = 0;
             ++k1;
         }
     }
-    const S r = add(add(p[0], p[1]), add(p[2], p[3]));
+    const S r = widen(add(add(p[0], p[1]), add(p[2], p[3])));
     S* __restrict__ Cp = (S*)t.C;
     const long long o = (long long)(m / t.M2) * t.c_m1 + (long long)(m % t.M2) * t.c_m2 +
                         (long long)(n / t.N2) * t.c_n1 + (long long)(n % t.N2) * t.c_n2;
     Cp[o] = t.accumulate ? add(Cp[o], r) : r;
 }
 
-cudaError_t launch_gcontract(const GTask* d_tasks, int ntasks, int max_tiles, bool cplx, cudaStream_t s, int small) {
+cudaError_t launch_gcontract(const GTask* d_tasks, int ntasks, int max_tiles, bool cplx, cudaStream_t s, int mode) {
     if (ntasks <= 0) return cudaSuccess;
     dim3 grid(max_tiles, ntasks);
+    const bool small = mode & 1;
+    if (mode & GC_F32) {
+        if (small) {
+            if (cplx)
+                k_gcontract_small<double2, float2><<<grid, 256, 0, s>>>(d_tasks);
+            else
+                k_gcontract_small<double, float><<<grid, 256, 0, s>>>(d_tasks);
+        } else if (cplx) {
+            k_gcontract<double2, float2><<<grid, 256, 0, s>>>(d_tasks);
+        } else {
+            k_gcontract<double, float><<<grid, 256, 0, s>>>(d_tasks);
+        }
+        return cudaGetLastError();
+    }
     if (small) {
         if (cplx)
             k_gcontract_small<double2><<<grid, 256, 0, s>>>(d_tasks);
@@ -320,6 +456,94 @@ cudaError_t launch_gcontract(const GTask* d_tasks, int ntasks, int max_tiles, bo
 constexpr int QR_MAXN = 512;
 constexpr size_t QR_SMEM_LIMIT = 200 * 1024;
 
+// T of the compact-WY form of a panel (H_p0 ... H_p0+pw-1 = I - V T V^H, T upper triangular,
+// T_jj = tau_j, T[0:j, j] = -tau_j T[0:j, 0:j] V[:, 0:j]^H v_j) from its reflectors in P:
+// G = V^H V by the warps, then T column by column by thread 0.  The factorization and the Q
+// phase both call it on the same reflectors, so both see the same T.
+template <typename S, int NB>
+__device__ __forceinline__ void panel_T(const S* P, int m, int p0, int pw, const typename ScalarTraits<S>::R* taus,
+                                        S* G, S* Ts) {
+    using R = typename ScalarTraits<S>::R;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int pr = warp; pr < pw * pw; pr += 8) {
+        const int r = pr / pw, c = pr - r * pw;
+        if (r >= c) continue;
+        const S* vr = P + (size_t)r * m;
+        const S* vc = P + (size_t)c * m;
+        S d = zero<S>();
+        for (int i = p0 + c + lane; i < m; i += 32) mac(d, conjv(vr[i]), vc[i]);  // v_c is zero above row p0+c
+        d = warp_sum(d);
+        if (lane == 0) G[r + c * NB] = d;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        for (int c = 0; c < pw; ++c) {
+            const R tc = taus[p0 + c];
+            for (int r = 0; r < c; ++r) {
+                S acc = zero<S>();
+                for (int q = r; q < c; ++q) mac(acc, Ts[r + q * NB], G[q + c * NB]);
+                Ts[r + c * NB] = scal(acc, -tc);
+            }
+            Ts[c + c * NB] = from_real<S>(tc);
+            for (int r = c + 1; r < NB; ++r) Ts[r + c * NB] = zero<S>();
+        }
+        for (int c = pw; c < NB; ++c)
+            for (int r = 0; r < NB; ++r) Ts[r + c * NB] = zero<S>();
+    }
+    __syncthreads();
+}
+
+// acc[r] += sum conj(P[r*m + i]) c[i] over the lane's rows i = p0 + lane + 32 j (V^H c for a
+// panel of pw reflectors), the column read four rows at a time so that four loads are in
+// flight (it lives in global memory); each acc[r] still adds its terms in row order.
+template <typename S, int NB>
+__device__ __forceinline__ void panel_dot(S (&acc)[NB], const S* c, const S* P, int m, int p0, int pw, int lane) {
+    int i = p0 + lane;
+    for (; i + 96 < m; i += 128) {
+        const S x0 = c[i], x1 = c[i + 32], x2 = c[i + 64], x3 = c[i + 96];
+#pragma unroll
+        for (int r = 0; r < NB; ++r)
+            if (r < pw) {
+                const S* pr = P + (size_t)r * m + i;
+                mac(acc[r], conjv(pr[0]), x0);
+                mac(acc[r], conjv(pr[32]), x1);
+                mac(acc[r], conjv(pr[64]), x2);
+                mac(acc[r], conjv(pr[96]), x3);
+            }
+    }
+    for (; i < m; i += 32) {
+        const S x = c[i];
+#pragma unroll
+        for (int r = 0; r < NB; ++r)
+            if (r < pw) mac(acc[r], conjv(P[(size_t)r * m + i]), x);
+    }
+}
+// c[i] += sum_r P[r*m + i] w[r] over the lane's rows (c <- c + V w), four rows at a time; each
+// element adds its terms in the order r = 0, 1, ...
+template <typename S, int NB>
+__device__ __forceinline__ void panel_update(S* c, const S* P, const S (&w)[NB], int m, int p0, int pw, int lane) {
+    int i = p0 + lane;
+    for (; i + 96 < m; i += 128) {
+        S x[4] = {c[i], c[i + 32], c[i + 64], c[i + 96]};
+#pragma unroll
+        for (int r = 0; r < NB; ++r)
+            if (r < pw) {
+                const S* pr = P + (size_t)r * m + i;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) mac(x[q], pr[32 * q], w[r]);
+            }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) c[i + 32 * q] = x[q];
+    }
+    for (; i < m; i += 32) {
+        S x = c[i];
+#pragma unroll
+        for (int r = 0; r < NB; ++r)
+            if (r < pw) mac(x, P[(size_t)r * m + i], w[r]);
+        c[i] = x;
+    }
+}
+
 // ---------------------------------------------------------------- blocked Householder QR
 // For matrices too large for the cluster QR's shared memory (the (chi K) x chi site matrices
 // at D=5, chi=96: 2400 x 96): one CTA per matrix, the matrix in the task's global workspace,
@@ -336,30 +560,70 @@ constexpr size_t QR_SMEM_LIMIT = 200 * 1024;
 //    c <- c - V (T (V^H c)) is applied to the columns k >= p0 (rows < p0 stay zero).
 // Every reflector is the Householder reflector of its column (the one the unblocked order
 // would form), so the result is the same Q up to rounding.  W occupies the first m*n scalars
-// of the workspace, the panels' T the next n*NB.
+// of the workspace; each panel's T is formed again in the Q phase rather than stored.
+// S = float / float2 is the same algorithm in FP32 arithmetic, for the reduced-precision paths
+// (tasks with in_float == 2, whose input is already an FP32 contraction result): on GB300 an
+// FP32 instruction issues at 64 times the FP64 rate, and a single-CTA FP64 QR of a 2400 x 96
+// site matrix is bound by exactly that rate.  Q is still written in FP64 (and the low-precision
+// copy), and the loss is still summed in FP64.
 template <typename S, int NB>
 __global__ void __launch_bounds__(256) k_qr_wy(const QRTask* __restrict__ tasks) {
+    using R = typename ScalarTraits<S>::R;
+    using SW = typename ScalarTraits<S>::Wide;
     const QRTask& t = tasks[blockIdx.x];
     if (t.active && *t.active == 0) return;
     extern __shared__ __align__(16) unsigned char qr_smem[];
     S* P = (S*)qr_smem;  // panel, column c at P + c*m (absolute row index)
     __shared__ S betas[QR_MAXN];
-    __shared__ double taus[QR_MAXN];
+    __shared__ R taus[QR_MAXN];
     __shared__ S Ts[NB * NB];  // T of the current panel, Ts[r + c*NB]
     __shared__ S G[NB * NB];   // V^H V of the panel
     __shared__ double redd[32];
+    __shared__ R redr[32];
     const int m = t.m, n = t.n, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     S* W = (S*)t.work;
-    S* Tg = W + (size_t)m * n;
-    const S* in = (const S*)t.in;
-    double ss = 0.0;
-    for (long long idx = tid; idx < (long long)m * n; idx += 256) {
-        const int i = (int)(idx % m), j = (int)(idx / m);
-        const long long src = (long long)i * t.in_rs + (long long)j * t.in_cs;
-        S v = t.in_float ? from_float<S>(((const float*)t.in), src) : in[src];
-        if (t.conj_io) v = conjv(v);
-        W[(size_t)j * m + i] = v;
-        ss += abs2(v);
+    double ss = 0.0;  // the loss -||in||^2, summed in FP64
+    if constexpr (std::is_same<R, double>::value) {
+        for (long long idx = tid; idx < (long long)m * n; idx += 256) {
+            const int i = (int)(idx % m), j = (int)(idx / m);
+            const long long src = (long long)i * t.in_rs + (long long)j * t.in_cs;
+            S v = t.in_float ? from_float<S>(((const float*)t.in), src) : from_double<S>(t.in, src);
+            if (t.conj_io) v = conjv(v);
+            W[(size_t)j * m + i] = v;
+            ss += abs2(v);
+        }
+    } else {
+        // FP32 arithmetic: the matrix is scaled by 2^-e (exact), 2^(e-1) <= max |component| <
+        // 2^e, so that no sum of squares overflows or underflows wholesale; Q does not change
+        // and the loss is scaled back by 4^e.  Squares are summed in FP32 in runs of 16, the
+        // runs in FP64.
+        R amax = R(0);
+        for (long long idx = tid; idx < (long long)m * n; idx += 256) {
+            const int i = (int)(idx % m), j = (int)(idx / m);
+            const long long src = (long long)i * t.in_rs + (long long)j * t.in_cs;
+            S v = t.in_float ? from_float<S>(((const float*)t.in), src) : from_double<S>(t.in, src);
+            if (t.conj_io) v = conjv(v);
+            W[(size_t)j * m + i] = v;
+            amax = max_r(amax, max_component(v));
+        }
+        amax = block_max(amax, redr);
+        int e = 0;
+        if (amax > R(0) && amax <= 3.4e38f) frexpf(amax, &e);
+        const R sc = ldexpf(1.0f, -e);
+        R part = R(0);
+        int cnt = 0;
+        for (long long idx = tid; idx < (long long)m * n; idx += 256) {
+            const int i = (int)(idx % m), j = (int)(idx / m);
+            const S v = scal(W[(size_t)j * m + i], sc);
+            W[(size_t)j * m + i] = v;
+            part += abs2(v);
+            if (++cnt == 16) {
+                ss += (double)part;
+                part = R(0);
+                cnt = 0;
+            }
+        }
+        ss = ldexp(ss + (double)part, 2 * e);
     }
     ss = block_sum(ss, redd);
     if (tid == 0 && t.loss) *t.loss = -ss;
@@ -375,33 +639,33 @@ __global__ void __launch_bounds__(256) k_qr_wy(const QRTask* __restrict__ tasks)
         for (int c = 0; c < pw; ++c) {
             const int j = p0 + c;
             S* col = P + (size_t)c * m;
-            double xs2 = 0.0;
+            R xs2 = R(0);
             for (int i = j + 1 + tid; i < m; i += 256) xs2 += abs2(col[i]);
-            xs2 = block_sum(xs2, redd);
-            double xnorm = sqrt(xs2);
-            if (xs2 < 1e-280) {  // near underflow (uniform branch): rescale by max |x'_i|
-                double amax = 0.0;
-                for (int i = j + 1 + tid; i < m; i += 256) amax = fmax(amax, absv(col[i]));
-                amax = block_max(amax, redd);
-                double t2 = 0.0;
-                if (amax > 0.0)
+            xs2 = block_sum(xs2, redr);
+            R xnorm = sqrt_r(xs2);
+            if (xs2 < ScalarTraits<S>::tiny2()) {  // near underflow (uniform branch): rescale by max |x'_i|
+                R amax = R(0);
+                for (int i = j + 1 + tid; i < m; i += 256) amax = max_r(amax, absv(col[i]));
+                amax = block_max(amax, redr);
+                R t2 = R(0);
+                if (amax > R(0))
                     for (int i = j + 1 + tid; i < m; i += 256) t2 += abs2(divr(col[i], amax));
-                t2 = block_sum(t2, redd);
-                xnorm = amax > 0.0 ? amax * sqrt(t2) : 0.0;
+                t2 = block_sum(t2, redr);
+                xnorm = amax > R(0) ? amax * sqrt_r(t2) : R(0);
             }
             const S alpha = col[j];
-            const double aa = absv(alpha);
+            const R aa = absv(alpha);
             S beta = alpha;
-            double tau = 0.0;
-            if (xnorm > 0.0) {
-                const double nrm = hypot(aa, xnorm);
-                const S ph = aa > 0.0 ? divr(alpha, aa) : one<S>();
+            R tau = R(0);
+            if (xnorm > R(0)) {
+                const R nrm = hypot_r(aa, xnorm);
+                const S ph = aa > R(0) ? divr(alpha, aa) : one<S>();
                 beta = scal(ph, -nrm);
-                tau = 1.0 + aa / nrm;
-                const double den = aa + nrm;  // |alpha - beta|
+                tau = R(1) + aa / nrm;
+                const R den = aa + nrm;  // |alpha - beta|
                 const S cph = conjv(ph);
-                if (den > 1e-290) {
-                    const S sc = scal(cph, 1.0 / den);
+                if (den > ScalarTraits<S>::tiny_div()) {
+                    const S sc = scal(cph, R(1) / den);
                     for (int i = j + 1 + tid; i < m; i += 256) col[i] = mul(col[i], sc);
                 } else {
                     for (int i = j + 1 + tid; i < m; i += 256) col[i] = divr(mul(col[i], cph), den);
@@ -415,7 +679,7 @@ __global__ void __launch_bounds__(256) k_qr_wy(const QRTask* __restrict__ tasks)
             }
             for (int i = p0 + tid; i < j; i += 256) col[i] = zero<S>();  // V is zero above its diagonal
             __syncthreads();
-            if (tau != 0.0) {  // H_j on the panel's later columns, one warp each
+            if (tau != R(0)) {  // H_j on the panel's later columns, one warp each
                 for (int k = c + 1 + warp; k < pw; k += 8) {
                     S* ck = P + (size_t)k * m;
                     S d0 = zero<S>(), d1 = zero<S>();
@@ -431,46 +695,15 @@ __global__ void __launch_bounds__(256) k_qr_wy(const QRTask* __restrict__ tasks)
             }
             __syncthreads();
         }
-        // T of the panel: G = V^H V (columns r < c), then T column by column
-        for (int pr = warp; pr < pw * pw; pr += 8) {
-            const int r = pr / pw, c = pr - r * pw;
-            if (r >= c) continue;
-            const S* vr = P + (size_t)r * m;
-            const S* vc = P + (size_t)c * m;
-            S d = zero<S>();
-            for (int i = p0 + c + lane; i < m; i += 32) mac(d, conjv(vr[i]), vc[i]);  // v_c is zero above row p0+c
-            d = warp_sum(d);
-            if (lane == 0) G[r + c * NB] = d;
-        }
-        __syncthreads();
-        if (tid == 0) {
-            for (int c = 0; c < pw; ++c) {
-                const double tc = taus[p0 + c];
-                for (int r = 0; r < c; ++r) {
-                    S acc = zero<S>();
-                    for (int q = r; q < c; ++q) mac(acc, Ts[r + q * NB], G[q + c * NB]);
-                    Ts[r + c * NB] = scal(acc, -tc);
-                }
-                Ts[c + c * NB] = from_real<S>(tc);
-                for (int r = c + 1; r < NB; ++r) Ts[r + c * NB] = zero<S>();
-            }
-            for (int c = pw; c < NB; ++c)
-                for (int r = 0; r < NB; ++r) Ts[r + c * NB] = zero<S>();
-        }
-        __syncthreads();
-        for (int idx = tid; idx < NB * NB; idx += 256) Tg[(size_t)p0 * NB + idx] = Ts[idx];
+        // T of the panel (recomputed by the Q phase from the same reflectors)
+        panel_T<S, NB>(P, m, p0, pw, taus, G, Ts);
         // trailing columns: c <- c - V (T^H (V^H c)), one column per warp
         for (int k = p0 + pw + warp; k < n; k += 8) {
             S* ck = W + (size_t)k * m;
             S acc[NB];
 #pragma unroll
             for (int r = 0; r < NB; ++r) acc[r] = zero<S>();
-            for (int i = p0 + lane; i < m; i += 32) {
-                const S x = ck[i];
-#pragma unroll
-                for (int r = 0; r < NB; ++r)
-                    if (r < pw) mac(acc[r], conjv(P[(size_t)r * m + i]), x);
-            }
+            panel_dot<S, NB>(acc, ck, P, m, p0, pw, lane);
 #pragma unroll
             for (int r = 0; r < NB; ++r) acc[r] = warp_sum(acc[r]);
             S wv[NB];
@@ -480,15 +713,9 @@ __global__ void __launch_bounds__(256) k_qr_wy(const QRTask* __restrict__ tasks)
 #pragma unroll
                 for (int q = 0; q < NB; ++q)
                     if (q <= r) mac(a, conjv(Ts[q + r * NB]), acc[q]);  // (T^H w)_r
-                wv[r] = scal(a, -1.0);
+                wv[r] = scal(a, R(-1));
             }
-            for (int i = p0 + lane; i < m; i += 32) {
-                S x = ck[i];
-#pragma unroll
-                for (int r = 0; r < NB; ++r)
-                    if (r < pw) mac(x, P[(size_t)r * m + i], wv[r]);
-                ck[i] = x;
-            }
+            panel_update<S, NB>(ck, P, wv, m, p0, pw, lane);
         }
         // the panel's reflectors back to W (read again by the Q phase)
         for (int idx = tid; idx < pw * rows; idx += 256) {
@@ -504,8 +731,8 @@ __global__ void __launch_bounds__(256) k_qr_wy(const QRTask* __restrict__ tasks)
             const int c = idx / rows, i = p0 + (idx - c * rows);
             P[(size_t)c * m + i] = W[(size_t)(p0 + c) * m + i];
         }
-        for (int idx = tid; idx < NB * NB; idx += 256) Ts[idx] = Tg[(size_t)p0 * NB + idx];
         __syncthreads();
+        panel_T<S, NB>(P, m, p0, pw, taus, G, Ts);
         for (int idx = tid; idx < pw * m; idx += 256) {  // columns p0.. of the panel start as e_k
             const int c = idx / m, i = idx - c * m;
             W[(size_t)(p0 + c) * m + i] = i == p0 + c ? one<S>() : zero<S>();
@@ -516,12 +743,7 @@ __global__ void __launch_bounds__(256) k_qr_wy(const QRTask* __restrict__ tasks)
             S acc[NB];
 #pragma unroll
             for (int r = 0; r < NB; ++r) acc[r] = zero<S>();
-            for (int i = p0 + lane; i < m; i += 32) {
-                const S x = ck[i];
-#pragma unroll
-                for (int r = 0; r < NB; ++r)
-                    if (r < pw) mac(acc[r], conjv(P[(size_t)r * m + i]), x);
-            }
+            panel_dot<S, NB>(acc, ck, P, m, p0, pw, lane);
 #pragma unroll
             for (int r = 0; r < NB; ++r) acc[r] = warp_sum(acc[r]);
             S wv[NB];
@@ -531,26 +753,21 @@ __global__ void __launch_bounds__(256) k_qr_wy(const QRTask* __restrict__ tasks)
 #pragma unroll
                 for (int q = 0; q < NB; ++q)
                     if (q >= r && q < pw) mac(a, Ts[r + q * NB], acc[q]);  // (T w)_r
-                wv[r] = scal(a, -1.0);
+                wv[r] = scal(a, R(-1));
             }
-            for (int i = p0 + lane; i < m; i += 32) {
-                S x = ck[i];
-#pragma unroll
-                for (int r = 0; r < NB; ++r)
-                    if (r < pw) mac(x, P[(size_t)r * m + i], wv[r]);
-                ck[i] = x;
-            }
+            panel_update<S, NB>(ck, P, wv, m, p0, pw, lane);
         }
         __syncthreads();
     }
     // ---- output: column k times phase(beta_k), so that R_kk = |beta_k| >= 0
-    S* out = (S*)t.out;
+    SW* out = (SW*)t.out;  // FP64 (complex-FP64) in every arithmetic
     for (long long idx = tid; idx < (long long)m * n; idx += 256) {
         const int i = (int)(idx % m), k = (int)(idx / m);
-        const double bb = absv(betas[k]);
-        const S ph = bb > 0.0 ? divr(betas[k], bb) : one<S>();
-        S v = mul(W[(size_t)k * m + i], ph);
-        if (t.conj_io) v = conjv(v);
+        const R bb = absv(betas[k]);
+        const S ph = bb > R(0) ? divr(betas[k], bb) : one<S>();
+        S vs = mul(W[(size_t)k * m + i], ph);
+        if (t.conj_io) vs = conjv(vs);
+        const SW v = widen(vs);
         out[(long long)i * t.out_rs + (long long)k * t.out_cs] = v;
         if (t.out2) {
             const int M2 = t.out2_M2 > 1 ? t.out2_M2 : 1, i1 = i / M2;
@@ -966,6 +1183,20 @@ cudaError_t qr_prepare(int max_m, bool cplx) {
     if (done[dev][cplx ? 1 : 0]) return cudaSuccess;
     const int lim = (int)QR_SMEM_LIMIT;
     cudaError_t e;
+    // the FP32-arithmetic blocked QR (reduced-precision paths)
+    if (cplx) {
+        if ((e = cudaFuncSetAttribute(k_qr_wy<float2, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+        if ((e = cudaFuncSetAttribute(k_qr_wy<float2, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+        if ((e = cudaFuncSetAttribute(k_qr_wy<float2, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+        if ((e = cudaFuncSetAttribute(k_qr_wy<float2, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+        if ((e = cudaFuncSetAttribute(k_qr_wy<float2, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+    } else {
+        if ((e = cudaFuncSetAttribute(k_qr_wy<float, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+        if ((e = cudaFuncSetAttribute(k_qr_wy<float, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+        if ((e = cudaFuncSetAttribute(k_qr_wy<float, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+        if ((e = cudaFuncSetAttribute(k_qr_wy<float, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+        if ((e = cudaFuncSetAttribute(k_qr_wy<float, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+    }
     if (cplx) {
         if ((e = cudaFuncSetAttribute(k_qr_cluster<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)QR_CLUSTER_SMEM)) != cudaSuccess) return e;
@@ -994,6 +1225,23 @@ bool qr_cluster_fits(int max_m, long long max_mn, bool cplx, int C) {
 cudaError_t launch_qr(const QRTask* d_tasks, int ntasks, int max_m, long long max_mn, bool cplx, cudaStream_t s,
                       int cluster) {
     if (ntasks <= 0) return cudaSuccess;
+    if (cluster & QR_F32) {
+        // FP32 arithmetic: the blocked QR, one CTA per task, whatever the size
+        const size_t fsz = cplx ? sizeof(float2) : sizeof(float);
+        const int nb = qr_wy_nb(max_m, fsz);
+        const size_t sm = (size_t)nb * max_m * fsz;
+        if (sm > QR_SMEM_LIMIT) return cudaErrorInvalidValue;
+#define WY_CASE(NB_)                                                               \
+        if (nb == NB_) {                                                           \
+            if (cplx) k_qr_wy<float2, NB_><<<ntasks, 256, sm, s>>>(d_tasks);       \
+            else k_qr_wy<float, NB_><<<ntasks, 256, sm, s>>>(d_tasks);             \
+            return cudaGetLastError();                                             \
+        }
+        WY_CASE(16) WY_CASE(8) WY_CASE(4) WY_CASE(2) WY_CASE(1)
+#undef WY_CASE
+        return cudaErrorInvalidValue;
+    }
+    cluster &= 0xFF;
     // Spread each task over C CTAs so that the launch covers the SMs (with at least two
     // columns per CTA), and over more CTAs if its matrix does not fit one CTA's shared memory.
     // cluster > 0 asks for that C (the autotuner's choice; the result is the same for every C).
@@ -1399,6 +1647,73 @@ __global__ void k_msg_init(const MsgInitTask* __restrict__ tasks, int ntasks) {
 cudaError_t launch_msg_init(const MsgInitTask* d_tasks, int ntasks, cudaStream_t s) {
     if (ntasks <= 0) return cudaSuccess;
     k_msg_init<<<(ntasks + 63) / 64, 64, 0, s>>>(d_tasks, ntasks);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- inner products
+// *out = 2^(ea + eb) sum_x A[x] B[x] over n scalars, no conjugation (the last contraction of a
+// read-out closing): one CTA per task, four partial sums per thread, the block's sums added
+// in a fixed order (the result does not depend on timing).
+__device__ __forceinline__ int exp_or_zero(const int* e) { return e ? *e : 0; }
+__device__ __forceinline__ double scale2(double v, int e) { return ldexp(v, e); }
+__device__ __forceinline__ double2 scale2(double2 v, int e) { return make_double2(ldexp(v.x, e), ldexp(v.y, e)); }
+template <typename S>
+__global__ void __launch_bounds__(256) k_dot(const DotTask* __restrict__ tasks) {
+    const DotTask& t = tasks[blockIdx.x];
+    __shared__ S red[32];
+    const S* __restrict__ a = (const S*)t.A;
+    const S* __restrict__ b = (const S*)t.B;
+    S p[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) p[q] = zero<S>();
+    long long i = threadIdx.x;
+    for (; i + 768 < t.n; i += 1024) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) mac(p[q], a[i + 256 * q], b[i + 256 * q]);
+    }
+    for (; i < t.n; i += 256) mac(p[0], a[i], b[i]);
+    const S v = block_sum(add(add(p[0], p[1]), add(p[2], p[3])), red);
+    if (threadIdx.x == 0) *(S*)t.out = scale2(v, exp_or_zero(t.ea) + exp_or_zero(t.eb));
+}
+
+// Power-of-two normalisation of a buffer of n doubles (2n for complex scalars): the largest
+// magnitude is found on the bit patterns (for finite doubles the order of |x| is the integer
+// order of the bits without the sign), and the scaling by 2^-e is exact.
+__global__ void __launch_bounds__(256) k_pow2norm(const DotTask* __restrict__ tasks, int cplx) {
+    const DotTask& t = tasks[blockIdx.x];
+    __shared__ unsigned long long red[8];
+    double* x = (double*)t.A;
+    const long long n = t.n * (cplx ? 2 : 1);
+    unsigned long long m = 0;
+    for (long long i = threadIdx.x; i < n; i += 256) {
+        const unsigned long long u = (unsigned long long)__double_as_longlong(x[i]) & 0x7FFFFFFFFFFFFFFFull;
+        m = u > m ? u : m;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long v = __shfl_xor_sync(0xffffffffu, m, o);
+        m = v > m ? v : m;
+    }
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    __syncthreads();
+    m = red[0];
+    for (int w = 1; w < 8; ++w) m = red[w] > m ? red[w] : m;
+    int e = 0;
+    if (m != 0 && m < 0x7FF0000000000000ull) frexp(__longlong_as_double((long long)m), &e);
+    if (e != 0) {
+        const double sc = ldexp(1.0, -e);
+        for (long long i = threadIdx.x; i < n; i += 256) x[i] *= sc;
+    }
+    if (threadIdx.x == 0) *(int*)t.out = e + exp_or_zero(t.ea);
+}
+
+cudaError_t launch_dot(const DotTask* d_tasks, int ntasks, bool cplx, cudaStream_t s, int normalise) {
+    if (ntasks <= 0) return cudaSuccess;
+    if (normalise)
+        k_pow2norm<<<ntasks, 256, 0, s>>>(d_tasks, cplx ? 1 : 0);
+    else if (cplx)
+        k_dot<double2><<<ntasks, 256, 0, s>>>(d_tasks);
+    else
+        k_dot<double><<<ntasks, 256, 0, s>>>(d_tasks);
     return cudaGetLastError();
 }
 

@@ -600,6 +600,7 @@ static int validate(const bbp_lattice_desc* d) {
     if (d->warm_start != 0 && d->warm_start != 1) return fail(BBP_ERR_INVALID, "warm_start must be 0 or 1");
     if (d->single_layer != 0 && d->single_layer != 1) return fail(BBP_ERR_INVALID, "single_layer must be 0 or 1");
     if (d->launch_mode != 0 && d->launch_mode != 1) return fail(BBP_ERR_INVALID, "launch_mode must be 0 or 1");
+    if (d->keep_fp64 != 0 && d->keep_fp64 != 1) return fail(BBP_ERR_INVALID, "keep_fp64 must be 0 or 1");
     if (d->boundary == BBP_OBC ? (d->shift_x < 0 || d->shift_x >= d->bx || d->shift_y < 0 || d->shift_y >= d->by)
                                : (d->shift_x < 0 || d->shift_x >= d->Lx || d->shift_y < 0 || d->shift_y >= d->Ly))
         return fail(BBP_ERR_INVALID, "shifts: 0 <= shift < unit cell on infinite lattices, < block side with OBC");
@@ -711,6 +712,7 @@ int bbp::plan_lattice(const bbp_lattice_desc* desc, bbp_lattice** out) {
         cx.pe = 16 / cx.esz;
         cx.lpk = cx.tck == 0 ? 4 : 3;
         cx.tco = cx.tck == 0 ? 1 : 2;
+        cx.qr_f32 = desc->keep_fp64 == 0;
         pr.tc_kind = cx.tck;
         L->one_lp = pr.arena_alloc(16);
         L->one_lp_b = cx.x3 ? pr.arena_alloc(16) : L->one_lp;
@@ -1161,6 +1163,45 @@ static cudaError_t time_step(bbp_lattice* L, size_t si, int reps, cudaEvent_t a,
     return e;
 }
 
+int bbp_time_steps(bbp_lattice* L, int reps, int cap, bbp_step_time* out, int* n_steps) try {
+    if (!L) return fail(BBP_ERR_INVALID, "lattice is NULL");
+    if (reps < 1 || cap < 0 || (cap > 0 && !out) || !n_steps) return fail(BBP_ERR_INVALID, "bad arguments");
+    if (!L->has_tensors) return fail(BBP_ERR_STATE, "bbp_set_tensors has not been called");
+    Program& pr = L->sweep;
+    EventPair ev;
+    CKR(cudaEventCreate(&ev.a));
+    CKR(cudaEventCreate(&ev.b));
+    CKR(pr.reset_active(L->stream));
+    int n = 0;
+    for (size_t si = 0; si < pr.steps.size(); ++si) {
+        const Step& s = pr.steps[si];
+        const int cls = pr.step_class_of(s);
+        if (cls > 2) continue;
+        if (n < cap) {
+            bbp_step_time& r = out[n];
+            r = bbp_step_time{};
+            r.index = (int)si;
+            r.kernel_class = cls;
+            r.tasks = s.count;
+            r.tile_n = s.kind == ST_TC ? s.aux : 0;
+            pr.step_work(s, &r.flops, &r.bytes, &r.max_m, &r.max_n, &r.max_k);
+            float t = 0.0f;
+            CKR(time_step(L, si, reps, ev.a, ev.b, &t));
+            r.ms = t / reps;
+        }
+        ++n;
+    }
+    *n_steps = n;
+    if (L->mixed) {
+        int te = 0;
+        CKR(cudaMemcpy(&te, L->d_tcerr, sizeof(int), cudaMemcpyDeviceToHost));
+        if (te) return fail(BBP_ERR_TIMEOUT, "a tensor-core pipeline wait exceeded its bound");
+    }
+    return BBP_OK;
+} catch (...) {
+    return abi_error();
+}
+
 int bbp_autotune(bbp_lattice* L, int reps, double* ms_before, double* ms_after, int* steps_changed) try {
     if (!L) return fail(BBP_ERR_INVALID, "lattice is NULL");
     if (reps < 1) return fail(BBP_ERR_INVALID, "reps must be >= 1");
@@ -1212,7 +1253,7 @@ int bbp_autotune(bbp_lattice* L, int reps, double* ms_before, double* ms_after, 
             if (best_bn != bn0 || best_d != d0 || best_k != k0) ++changed;
             before += (t0 >= 0.0f ? t0 : best) / reps;
             after += best / reps;
-        } else if (s0.kind == ST_QR && qr_cluster_fits(s0.aux, s0.n, pr.cplx, 1)) {
+        } else if (s0.kind == ST_QR && !(s0.aux2 & QR_F32) && qr_cluster_fits(s0.aux, s0.n, pr.cplx, 1)) {
             // QR/LQ: cluster size (0: the built-in rule); the result is the same for every C
             int best_c = 0;
             float best = -1.0f, t0 = -1.0f;

@@ -199,7 +199,7 @@ QRTask qr_mixed(const MixCtx& cx, const FitSpec& f, int i, bool lq, size_t loss_
     const long long y = f.ybond[i], y2 = f.ybond[i + 1], q = f.O[i].q;
     QRTask t{};
     t.in = P(f.mx.Ytf);
-    t.in_float = 1;
+    t.in_float = cx.qr_f32 ? 2 : 1;
     t.out = P(f.Y[i] * (size_t)cx.ss);
     t.work = P(f.qrw * (size_t)cx.ss);
     t.loss = (double*)P(loss_byte);

@@ -77,7 +77,7 @@ struct FitSpec {
 
 enum StepKind {
     ST_GC = 0, ST_QR, ST_RAND, ST_SETACT, ST_CHECK, ST_SCALE, ST_ASM, ST_NORM, ST_MEAN, ST_COPY, ST_INC, ST_FUSE, ST_DL,
-    ST_TC, ST_REL,
+    ST_TC, ST_REL, ST_DOT,
     ST_LOOP_BEGIN,  // p0: LoopDesc; aux: max iterations; the body runs until the matching ST_LOOP_END
     ST_LOOP_END
 };

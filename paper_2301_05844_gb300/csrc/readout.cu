@@ -6,10 +6,12 @@
 // crosses a block edge) gets its left and right environment columns L_c, R_c from
 // the same lockstep zip-up fits as the sweep, and each term is the exact
 // top-to-bottom closing L_c . column(s) . R_c with E^O at the operator sites;
-// <O> = N_O / N_I is formed in FP64.
+// <O> = N_O / N_I is formed in FP64.  The closings of one column strip share its top
+// and bottom environments, so a term costs the rows that carry its operators.
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <complex>
 #include <cstring>
 #include <map>
@@ -308,7 +310,44 @@ extern "C" int bbp_expect(bbp_lattice* L, const bbp_term* terms, int n_terms, do
         return contiguous3(f.Y[i], f.ybond[i], f.O[i].q, f.ybond[i + 1]);
     };
 
-    // lane scratch sizing
+    // ---- closings, shared per column strip
+    // A strip is one (region, first column, columns) group of closings.  Its top environments
+    // T_i (rows 0..i-1 contracted; open legs: left env bond a, the strip's vertical leg(s) w,
+    // right env bond b, stored [a][w][b]) and bottom environments G_i (rows i..h+1, the same
+    // legs) are formed once; a closing with operators on rows i0..i1 contracts T_i0, those rows
+    // with E^O at its operator sites, and G_(i1+1) (an inner product), and the strip's
+    // N_I = <T_(h+1), G_(h+1)>.  These are the sums of the top-to-bottom closing L_c . column(s)
+    // . R_c, in another order.
+    struct Strip {
+        int region = 0, col = 0, ncols = 1, norm = -1;
+        std::vector<int> clos;
+        std::vector<size_t> T, G;    // element offsets of T_i (i = 1..h+1) and G_i (i = 2..h+1)
+        std::vector<size_t> eT, eG;  // byte offsets of their power-of-two exponents (FP32 closings)
+        size_t chain = 0;            // their scalars
+    };
+    std::vector<Strip> strips;
+    {
+        std::map<std::tuple<int, int, int>, int> sid;
+        for (size_t ci = 0; ci < closings.size(); ++ci) {
+            const Closing& C = closings[ci];
+            const auto key = std::make_tuple(C.region, C.col, C.ncols);
+            auto it = sid.find(key);
+            int k = 0;
+            if (it == sid.end()) {
+                k = (int)strips.size();
+                sid[key] = k;
+                Strip S;
+                S.region = C.region; S.col = C.col; S.ncols = C.ncols;
+                strips.push_back(S);
+            } else {
+                k = it->second;
+            }
+            if (C.pos.empty())
+                strips[k].norm = (int)ci;
+            else
+                strips[k].clos.push_back((int)ci);
+        }
+    }
     const int K4max = L->K * L->K * L->K * L->K;
     const size_t nclos = closings.size();
     const size_t results = elem_alloc(nclos);
@@ -317,11 +356,6 @@ extern "C" int bbp_expect(bbp_lattice* L, const bbp_term* terms, int n_terms, do
     const size_t ratio_tasks = pr.arena_alloc((size_t)n_terms * sizeof(RatioTask));
     const size_t ratio_out = pr.arena_alloc((size_t)n_terms * 2 * sizeof(double));
     const size_t ratio_status = pr.arena_alloc(sizeof(int));
-    struct Lane {
-        size_t F[2], G1, G2, EO[2], O12;
-    };
-    // per-closing maxima of the row intermediates
-    size_t fmax = 1, g1max = 1, g2max = 1, o12max = 1;
     auto row_op = [&](const Region& R, int c, int i, size_t eo_off, bool use_eo) -> Op4 {
         if (i == 0) return op_from_top(R.in[DIR_UP][c]);
         if (i == R.h + 1) return op_from_bottom(R.in[DIR_DOWN][c]);
@@ -331,31 +365,89 @@ extern "C" int bbp_expect(bbp_lattice* L, const bbp_term* terms, int n_terms, do
         if (L->single) return op_contig(off, dd[0], dd[1], dd[2], dd[3]);
         return op_contig(off, dd[0] * dd[0], dd[1] * dd[1], dd[2] * dd[2], dd[3] * dd[3]);
     };
-    for (auto& C : closings) {
-        const Region& R = regions[C.region];
-        size_t fa = 1, fw = 1, fb = 1;
+    // leg dimensions of strip row i: (u, l, d, r) of its (fused) operator
+    auto row_dims = [&](const Strip& S, int i) -> std::array<long long, 4> {
+        const Region& R = regions[S.region];
+        Op4 o = row_op(R, S.col, i, 0, false);
+        if (S.ncols == 2) {
+            const Op4 o2 = row_op(R, S.col + 1, i, 0, false);
+            o.u *= o2.u; o.d *= o2.d; o.r = o2.r;
+        }
+        return {o.u, o.l, o.d, o.r};
+    };
+    // scratch maxima over every strip row (the chains and the closings use the same rows)
+    size_t fmax = 1, s1max = 1, s2max = 1, o12max = 1;
+    for (auto& S : strips) {
+        const Region& R = regions[S.region];
         for (int i = 0; i < R.h + 2; ++i) {
-            const View3 Lv = env_site(R, true, C.col, i), Rv = env_site(R, false, C.col + C.ncols - 1, i);
-            Op4 o = row_op(R, C.col, i, 0, false);
-            if (C.ncols == 2) {
-                Op4 o2 = row_op(R, C.col + 1, i, 0, false);
-                o12max = std::max(o12max, (size_t)o.u * o2.u * o.l * o.d * o2.d * o2.r);
-                o.u *= o2.u; o.d *= o2.d; o.r = o2.r;
+            const View3 Lv = env_site(R, true, S.col, i), Rv = env_site(R, false, S.col + S.ncols - 1, i);
+            const auto od = row_dims(S, i);
+            const size_t u = od[0], s = Lv.k, v = od[2], t2 = od[3], A = Lv.a, Ap = Lv.b, B = Rv.a, Bp = Rv.b;
+            if (od[1] != Lv.k || t2 != (size_t)Rv.k) return fail(BBP_ERR_INVALID, "internal: closing leg mismatch");
+            if (i + 1 < R.h + 2) {
+                const View3 Ln = env_site(R, true, S.col, i + 1), Rn = env_site(R, false, S.col + S.ncols - 1, i + 1);
+                if (Ln.a != Lv.b || Rn.a != Rv.b || row_dims(S, i + 1)[0] != od[2])
+                    return fail(BBP_ERR_INVALID, "internal: closing rows do not chain");
             }
-            const size_t s = Lv.k, Ap = Lv.b, v = o.d, t2 = o.r, Bp = Rv.b;
-            g1max = std::max(g1max, fw * fb * s * Ap);
-            g2max = std::max(g2max, fb * Ap * v * t2);
-            fa = Ap; fw = v; fb = Bp;
-            fmax = std::max(fmax, fa * fw * fb);
+            if (S.ncols == 2) {
+                const Op4 o = row_op(R, S.col, i, 0, false), o2 = row_op(R, S.col + 1, i, 0, false);
+                o12max = std::max(o12max, (size_t)o.u * o2.u * o.l * o.d * o2.d * o2.r);
+            }
+            fmax = std::max({fmax, A * u * B, Ap * v * Bp});
+            s1max = std::max({s1max, u * B * s * Ap, v * Bp * s * A});     // G1 (down), X1 (up)
+            s2max = std::max({s2max, B * Ap * v * t2, Bp * A * u * t2});   // G2 (down), X2 (up)
+            if (i >= 1) S.chain += A * u * B;                              // T_i, i = 1..h+1
+            if (i >= 2) S.chain += A * u * B;                              // G_i, i = 2..h+1
         }
     }
-    const size_t lane_elems = 2 * fmax + g1max + g2max + (L->single ? 0 : 2 * (size_t)K4max) + o12max;
-    const size_t budget = (size_t)4 << 30;
-    size_t nlanes = std::max<size_t>(1, std::min(nclos, budget / std::max<size_t>(1, lane_elems * ss)));
+    struct Lane {
+        size_t F[2], S1, S2, EO[2], O12;
+    };
+    const size_t lane_elems = 2 * fmax + s1max + s2max + (L->single ? 0 : 2 * (size_t)K4max) + o12max;
+    // device memory for the read-out's scratch: up to a quarter of what is free (at least 1 GB,
+    // at most 16 GB), half of it for lanes, half for the strips' environments
+    size_t mem_free = 0, mem_total = 0;
+    CKR(cudaMemGetInfo(&mem_free, &mem_total));
+    const size_t budget = std::max<size_t>((size_t)1 << 30, std::min<size_t>((size_t)16 << 30, mem_free / 4));
+    const size_t nlanes =
+        std::max<size_t>(2, std::min<size_t>(std::max<size_t>(2, nclos), budget / 2 / std::max<size_t>(1, lane_elems * ss)));
+    const size_t chain_budget = budget / 2 / (size_t)ss;
+    // waves of strips: two lanes per strip for its chains, environments within the budget
+    std::vector<std::vector<int>> waves;
+    size_t chain_cap = 1;
+    {
+        std::vector<int> cur;
+        size_t tot = 0;
+        for (int k = 0; k < (int)strips.size(); ++k) {
+            if (!cur.empty() && (2 * (cur.size() + 1) > nlanes || tot + strips[k].chain > chain_budget)) {
+                waves.push_back(cur);
+                cur.clear();
+                tot = 0;
+            }
+            cur.push_back(k);
+            tot += strips[k].chain;
+            chain_cap = std::max(chain_cap, tot);
+        }
+        if (!cur.empty()) waves.push_back(cur);
+    }
+    const size_t chain_base = elem_alloc(chain_cap);
+    // Closings in FP32 arithmetic (tensor-core lattices unless keep_fp64): every environment is
+    // rescaled by a power of two after it is formed (exact), its exponent kept on the device
+    // and restored in the FP64 inner products, so that no FP32 intermediate overflows however
+    // many rows a strip has.
+    const bool f32c = L->mixed && !ds.keep_fp64;
+    size_t exp_cap = 1;
+    for (const auto& wave : waves) {
+        size_t e = 0;
+        for (int k : wave) e += 2 * (size_t)(regions[strips[k].region].h + 2);
+        exp_cap = std::max(exp_cap, e);
+    }
+    const size_t exp_base = pr.arena_alloc(exp_cap * sizeof(int));
+    auto eptr = [&](size_t byte_off) { return (const int*)P(byte_off); };
     std::vector<Lane> lanes(nlanes);
     for (auto& ln : lanes) {
         ln.F[0] = elem_alloc(fmax); ln.F[1] = elem_alloc(fmax);
-        ln.G1 = elem_alloc(g1max); ln.G2 = elem_alloc(g2max);
+        ln.S1 = elem_alloc(s1max); ln.S2 = elem_alloc(s2max);
         if (!L->single) {
             ln.EO[0] = elem_alloc(K4max);
             ln.EO[1] = elem_alloc(K4max);
@@ -391,126 +483,274 @@ extern "C" int bbp_expect(bbp_lattice* L, const bbp_term* terms, int n_terms, do
             opoff[ci][k] = elem_alloc(L->cplx ? v.size() / 2 : v.size());
             uploads.push_back({opoff[ci][k], v});
         }
-    for (size_t w0 = 0; w0 < nclos; w0 += nlanes) {
-        const size_t w1 = std::min(nclos, w0 + nlanes);
-        // E^O for the operator sites of this wave
-        std::vector<DLTask> dts;
-        long long dlmax = 1;
-        for (size_t ci = w0; ci < w1; ++ci) {
-            const Closing& C = closings[ci];
-            const Region& R = regions[C.region];
-            const Lane& ln = lanes[ci - w0];
-            if (L->single) continue;  // the impurity tensor is E^O itself
-            for (size_t k = 0; k < C.pos.size(); ++k) {
-                const int r = R.r0 + C.pos[k].first, c = R.c0 + C.pos[k].second;
-                const auto dd = L->site_dims(r, c);
-                DLTask t{};
-                t.T = P(L->T_off[L->tensor_index(r, c)] * ss);
-                t.E = P(ln.EO[k] * ss);
-                t.O = P(opoff[ci][k] * ss);
-                t.d = d; t.Du = dd[0]; t.Dl = dd[1]; t.Dd = dd[2]; t.Dr = dd[3];
-                t.hb = L->hb ? 1 : 0;
-                dts.push_back(t);
-                dlmax = std::max(dlmax, (long long)dd[0] * dd[0] * dd[1] * dd[1] * dd[2] * dd[2] * dd[3] * dd[3]);
+
+    // strip row i's operator, E^O at the sites listed in subs (local (row, col), offset); a
+    // column pair is fused into o12 first
+    bool leg_error = false;
+    auto strip_op = [&](const Strip& S, int i, const std::vector<std::pair<std::pair<int, int>, size_t>>& subs,
+                        size_t o12, std::vector<FuseTask>& ft, long long& fmx) -> Op4 {
+        const Region& R = regions[S.region];
+        auto op_at = [&](int c) {
+            for (auto& sb : subs)
+                if (sb.first.first == i - 1 && sb.first.second == c) return row_op(R, c, i, sb.second, true);
+            return row_op(R, c, i, 0, false);
+        };
+        Op4 o = op_at(S.col);
+        if (S.ncols == 2) {
+            const Op4 o2 = op_at(S.col + 1);
+            FuseTask f{};
+            f.A = P(o.off * ss); f.B = P(o2.off * ss); f.out = P(o12 * ss);
+            f.u1 = o.u; f.l1 = o.l; f.d1 = o.d; f.m = o.r; f.u2 = o2.u; f.d2 = o2.d; f.r2 = o2.r;
+            f.a_u = o.su; f.a_l = o.sl; f.a_d = o.sd; f.a_r = o.sr;
+            f.b_u = o2.su; f.b_l = o2.sl; f.b_d = o2.sd; f.b_r = o2.sr;
+            if (o.r != o2.l) leg_error = true;
+            ft.push_back(f);
+            fmx = std::max(fmx, (long long)o.u * o2.u * o.l * o.d * o2.d * o2.r);
+            o = op_contig(o12, o.u * o2.u, o.l, o.d * o2.d, o2.r);
+        }
+        return o;
+    };
+    // one row downwards: Fout[Ap][v][Bp] = sum Fin[A][W][B] L[A][s][Ap] O[W][s][v][t2] R[B][t2][Bp]
+    // through G1[W][B][s][Ap] and G2[B][Ap][v][t2]
+    auto row_down = [&](size_t Fin, size_t Fout, const View3& Lv, const Op4& o, const View3& Rv, const Lane& ln,
+                        std::vector<GTask>& g1, std::vector<GTask>& g2, std::vector<GTask>& g3) {
+        const long long A_ = Lv.a, Wd = o.u, B_ = Rv.a, s = Lv.k, Ap = Lv.b, v = o.d, t2 = o.r, Bp = Rv.b;
+        GTask a{};
+        a.A = P(Fin * ss); a.B = P(Lv.off * ss); a.C = P(ln.S1 * ss);
+        a.M1 = (int)Wd; a.M2 = (int)B_; a.K1 = 1; a.K2 = (int)A_; a.N1 = (int)s; a.N2 = (int)Ap;
+        a.a_m1 = B_; a.a_m2 = 1; a.a_k2 = Wd * B_;
+        a.b_k2 = Lv.sa; a.b_n1 = Lv.sk; a.b_n2 = Lv.sb;
+        a.c_m1 = B_ * s * Ap; a.c_m2 = s * Ap; a.c_n1 = Ap; a.c_n2 = 1;
+        g1.push_back(a);
+        GTask b{};
+        b.A = P(ln.S1 * ss); b.B = P(o.off * ss); b.C = P(ln.S2 * ss);
+        b.M1 = (int)B_; b.M2 = (int)Ap; b.K1 = (int)Wd; b.K2 = (int)s; b.N1 = (int)v; b.N2 = (int)t2;
+        b.a_m1 = s * Ap; b.a_m2 = 1; b.a_k1 = B_ * s * Ap; b.a_k2 = Ap;
+        b.b_k1 = o.su; b.b_k2 = o.sl; b.b_n1 = o.sd; b.b_n2 = o.sr;
+        b.c_m1 = Ap * v * t2; b.c_m2 = v * t2; b.c_n1 = t2; b.c_n2 = 1;
+        g2.push_back(b);
+        GTask c{};
+        c.A = P(ln.S2 * ss); c.B = P(Rv.off * ss); c.C = P(Fout * ss);
+        c.M1 = (int)Ap; c.M2 = (int)v; c.K1 = (int)B_; c.K2 = (int)t2; c.N1 = 1; c.N2 = (int)Bp;
+        c.a_m1 = v * t2; c.a_m2 = t2; c.a_k1 = Ap * v * t2; c.a_k2 = 1;
+        c.b_k1 = Rv.sa; c.b_k2 = Rv.sk; c.b_n2 = Rv.sb;
+        c.c_m1 = v * Bp; c.c_m2 = Bp; c.c_n2 = 1;
+        g3.push_back(c);
+    };
+    // one row upwards: Gout[A][W][B] = sum L[A][s][Ap] O[W][s][v][t2] R[B][t2][Bp] Gin[Ap][v][Bp]
+    // through X1[v][Bp][s][A] and X2[Bp][A][W][t2] (row_down with the roles of the legs swapped)
+    auto row_up = [&](size_t Gin, size_t Gout, const View3& Lv, const Op4& o, const View3& Rv, const Lane& ln,
+                      std::vector<GTask>& g1, std::vector<GTask>& g2, std::vector<GTask>& g3) {
+        const long long A_ = Lv.a, Wd = o.u, B_ = Rv.a, s = Lv.k, Ap = Lv.b, v = o.d, t2 = o.r, Bp = Rv.b;
+        GTask a{};
+        a.A = P(Gin * ss); a.B = P(Lv.off * ss); a.C = P(ln.S1 * ss);
+        a.M1 = (int)v; a.M2 = (int)Bp; a.K1 = 1; a.K2 = (int)Ap; a.N1 = (int)s; a.N2 = (int)A_;
+        a.a_m1 = Bp; a.a_m2 = 1; a.a_k2 = v * Bp;
+        a.b_k2 = Lv.sb; a.b_n1 = Lv.sk; a.b_n2 = Lv.sa;
+        a.c_m1 = Bp * s * A_; a.c_m2 = s * A_; a.c_n1 = A_; a.c_n2 = 1;
+        g1.push_back(a);
+        GTask b{};
+        b.A = P(ln.S1 * ss); b.B = P(o.off * ss); b.C = P(ln.S2 * ss);
+        b.M1 = (int)Bp; b.M2 = (int)A_; b.K1 = (int)v; b.K2 = (int)s; b.N1 = (int)Wd; b.N2 = (int)t2;
+        b.a_m1 = s * A_; b.a_m2 = 1; b.a_k1 = Bp * s * A_; b.a_k2 = A_;
+        b.b_k1 = o.sd; b.b_k2 = o.sl; b.b_n1 = o.su; b.b_n2 = o.sr;
+        b.c_m1 = A_ * Wd * t2; b.c_m2 = Wd * t2; b.c_n1 = t2; b.c_n2 = 1;
+        g2.push_back(b);
+        GTask c{};
+        c.A = P(ln.S2 * ss); c.B = P(Rv.off * ss); c.C = P(Gout * ss);
+        c.M1 = (int)A_; c.M2 = (int)Wd; c.K1 = (int)Bp; c.K2 = (int)t2; c.N1 = 1; c.N2 = (int)B_;
+        c.a_m1 = Wd * t2; c.a_m2 = t2; c.a_k1 = A_ * Wd * t2; c.a_k2 = 1;
+        c.b_k1 = Rv.sb; c.b_k2 = Rv.sk; c.b_n2 = Rv.sa;
+        c.c_m1 = Wd * B_; c.c_m2 = B_; c.c_n2 = 1;
+        g3.push_back(c);
+    };
+    auto fuse_step = [&](std::vector<FuseTask>& ft, long long fmx) {
+        if (ft.empty()) return;
+        Step s;
+        s.kind = ST_FUSE;
+        s.first = pr.fus.size();
+        s.count = (int)ft.size();
+        s.n = fmx;
+        pr.fus.insert(pr.fus.end(), ft.begin(), ft.end());
+        pr.steps.push_back(s);
+        ft.clear();
+    };
+    auto env_scalars = [&](const Strip& S, int i) {  // scalars of T_i / G_i
+        const Region& R = regions[S.region];
+        const View3 Lv = env_site(R, true, S.col, i), Rv = env_site(R, false, S.col + S.ncols - 1, i);
+        return (size_t)Lv.a * (size_t)row_dims(S, i)[0] * (size_t)Rv.a;
+    };
+
+    pr.gc_f32 = f32c;
+    for (const auto& wave : waves) {
+        // environments of this wave's strips, in the shared chain slab
+        size_t at = chain_base, eat = exp_base;
+        int hmax = 0;
+        for (int k : wave) {
+            Strip& S = strips[k];
+            const int h = regions[S.region].h;
+            hmax = std::max(hmax, h);
+            S.T.assign(h + 2, 0);
+            S.G.assign(h + 2, 0);
+            S.eT.assign(h + 2, 0);
+            S.eG.assign(h + 2, 0);
+            for (int i = 0; i < h + 2; ++i) {
+                S.eT[i] = eat + (size_t)i * sizeof(int);
+                S.eG[i] = eat + (size_t)(h + 2 + i) * sizeof(int);
+            }
+            eat += 2 * (size_t)(h + 2) * sizeof(int);
+            for (int i = 1; i <= h + 1; ++i) {
+                S.T[i] = at;
+                at += env_scalars(S, i);
+            }
+            for (int i = 2; i <= h + 1; ++i) {
+                S.G[i] = at;
+                at += env_scalars(S, i);
             }
         }
-        if (!dts.empty()) {
-            Step s;
-            s.kind = ST_DL;
-            s.first = pr.dl.size();
-            s.count = (int)dts.size();
-            s.n = dlmax;
-            s.aux2 = L->hb ? 1 : 0;
-            pr.dl.insert(pr.dl.end(), dts.begin(), dts.end());
-            pr.steps.push_back(s);
-        }
-        int hmax = 0;
-        for (size_t ci = w0; ci < w1; ++ci) hmax = std::max(hmax, regions[closings[ci].region].h);
-        std::vector<size_t> fa(w1 - w0, 1), fw(w1 - w0, 1), fb(w1 - w0, 1);
-        for (int i = 0; i < hmax + 2; ++i) {
+        // the chains: step j takes top row j and bottom row h+1-j of every strip
+        for (int j = 0; j <= hmax + 1; ++j) {
             std::vector<FuseTask> ft;
             long long fmx = 1;
-            std::vector<Op4> ops(w1 - w0);
-            std::vector<bool> live(w1 - w0, false);
-            for (size_t ci = w0; ci < w1; ++ci) {
-                const Closing& C = closings[ci];
-                const Region& R = regions[C.region];
-                if (i >= R.h + 2) continue;
-                live[ci - w0] = true;
-                const Lane& ln = lanes[ci - w0];
-                auto op_at = [&](int c) {
-                    for (size_t k = 0; k < C.pos.size(); ++k)
-                        if (C.pos[k].first == i - 1 && C.pos[k].second == c)
-                            return row_op(R, c, i, L->single ? opoff[ci][k] : ln.EO[k], true);
-                    return row_op(R, c, i, 0, false);
-                };
-                Op4 o = op_at(C.col);
-                if (C.ncols == 2) {
-                    Op4 o2 = op_at(C.col + 1);
-                    FuseTask f{};
-                    f.A = P(o.off * ss); f.B = P(o2.off * ss); f.out = P(ln.O12 * ss);
-                    f.u1 = o.u; f.l1 = o.l; f.d1 = o.d; f.m = o.r; f.u2 = o2.u; f.d2 = o2.d; f.r2 = o2.r;
-                    f.a_u = o.su; f.a_l = o.sl; f.a_d = o.sd; f.a_r = o.sr;
-                    f.b_u = o2.su; f.b_l = o2.sl; f.b_d = o2.sd; f.b_r = o2.sr;
-                    if (o.r != o2.l) return fail(BBP_ERR_INVALID, "internal: column pair leg mismatch");
-                    ft.push_back(f);
-                    fmx = std::max(fmx, (long long)o.u * o2.u * o.l * o.d * o2.d * o2.r);
-                    o = op_contig(ln.O12, o.u * o2.u, o.l, o.d * o2.d, o2.r);
-                }
-                ops[ci - w0] = o;
-            }
-            if (!ft.empty()) {
-                Step s;
-                s.kind = ST_FUSE;
-                s.first = pr.fus.size();
-                s.count = (int)ft.size();
-                s.n = fmx;
-                pr.fus.insert(pr.fus.end(), ft.begin(), ft.end());
-                pr.steps.push_back(s);
-            }
             std::vector<GTask> g1, g2, g3;
-            for (size_t ci = w0; ci < w1; ++ci) {
-                if (!live[ci - w0]) continue;
-                const Closing& C = closings[ci];
-                const Region& R = regions[C.region];
-                const Lane& ln = lanes[ci - w0];
-                const size_t j = ci - w0;
-                const View3 Lv = env_site(R, true, C.col, i), Rv = env_site(R, false, C.col + C.ncols - 1, i);
-                const Op4& o = ops[j];
-                const size_t Fin = i == 0 ? L->one_off : ln.F[i % 2];
-                const bool last = i == R.h + 1;
-                const size_t Fout = last ? results + ci : ln.F[(i + 1) % 2];
-                const long long A_ = fa[j], Wd = fw[j], B_ = fb[j], s = Lv.k, Ap = Lv.b, v = o.d, t2 = o.r, Bp = Rv.b;
-                if (Lv.a != A_ || Rv.a != B_ || o.u != Wd || o.l != s || Rv.k != t2)
-                    return fail(BBP_ERR_INVALID, "internal: closing leg mismatch");
-                GTask a{};
-                a.A = P(Fin * ss); a.B = P(Lv.off * ss); a.C = P(ln.G1 * ss);
-                a.M1 = (int)Wd; a.M2 = (int)B_; a.K1 = 1; a.K2 = (int)A_; a.N1 = (int)s; a.N2 = (int)Ap;
-                a.a_m1 = B_; a.a_m2 = 1; a.a_k2 = Wd * B_;
-                a.b_k2 = Lv.sa; a.b_n1 = Lv.sk; a.b_n2 = Lv.sb;
-                a.c_m1 = B_ * s * Ap; a.c_m2 = s * Ap; a.c_n1 = Ap; a.c_n2 = 1;
-                g1.push_back(a);
-                GTask b{};
-                b.A = P(ln.G1 * ss); b.B = P(o.off * ss); b.C = P(ln.G2 * ss);
-                b.M1 = (int)B_; b.M2 = (int)Ap; b.K1 = (int)Wd; b.K2 = (int)s; b.N1 = (int)v; b.N2 = (int)t2;
-                b.a_m1 = s * Ap; b.a_m2 = 1; b.a_k1 = B_ * s * Ap; b.a_k2 = Ap;
-                b.b_k1 = o.su; b.b_k2 = o.sl; b.b_n1 = o.sd; b.b_n2 = o.sr;
-                b.c_m1 = Ap * v * t2; b.c_m2 = v * t2; b.c_n1 = t2; b.c_n2 = 1;
-                g2.push_back(b);
-                GTask c{};
-                c.A = P(ln.G2 * ss); c.B = P(Rv.off * ss); c.C = P(Fout * ss);
-                c.M1 = (int)Ap; c.M2 = (int)v; c.K1 = (int)B_; c.K2 = (int)t2; c.N1 = 1; c.N2 = (int)Bp;
-                c.a_m1 = v * t2; c.a_m2 = t2; c.a_k1 = Ap * v * t2; c.a_k2 = 1;
-                c.b_k1 = Rv.sa; c.b_k2 = Rv.sk; c.b_n2 = Rv.sb;
-                c.c_m1 = v * Bp; c.c_m2 = Bp; c.c_n2 = 1;
-                g3.push_back(c);
-                fa[j] = Ap; fw[j] = v; fb[j] = Bp;
+            std::vector<DotTask> p2;
+            for (size_t q = 0; q < wave.size(); ++q) {
+                const Strip& S = strips[wave[q]];
+                const Region& R = regions[S.region];
+                const int h = R.h;
+                const Lane& top = lanes[2 * q];
+                const Lane& bot = lanes[2 * q + 1];
+                if (j <= h) {
+                    const Op4 o = strip_op(S, j, {}, top.O12, ft, fmx);
+                    row_down(j == 0 ? L->one_off : S.T[j], S.T[j + 1], env_site(R, true, S.col, j),
+                             o, env_site(R, false, S.col + S.ncols - 1, j), top, g1, g2, g3);
+                    DotTask t{};
+                    t.A = P(S.T[j + 1] * ss); t.out = P(S.eT[j + 1]); t.n = (long long)env_scalars(S, j + 1);
+                    t.ea = j == 0 ? nullptr : eptr(S.eT[j]);
+                    p2.push_back(t);
+                }
+                const int ib = h + 1 - j;
+                if (ib >= 2) {
+                    const Op4 o = strip_op(S, ib, {}, bot.O12, ft, fmx);
+                    row_up(ib == h + 1 ? L->one_off : S.G[ib + 1], S.G[ib], env_site(R, true, S.col, ib), o,
+                           env_site(R, false, S.col + S.ncols - 1, ib), bot, g1, g2, g3);
+                    DotTask t{};
+                    t.A = P(S.G[ib] * ss); t.out = P(S.eG[ib]); t.n = (long long)env_scalars(S, ib);
+                    t.ea = ib == h + 1 ? nullptr : eptr(S.eG[ib + 1]);
+                    p2.push_back(t);
+                }
             }
+            fuse_step(ft, fmx);
             pr.gc_step(g1);
             pr.gc_step(g2);
             pr.gc_step(g3);
+            if (f32c) pr.dot_step(p2, true);
+        }
+        // the strips' norms, then their closings, nlanes at a time
+        std::vector<DotTask> dts;
+        std::vector<int> cl;
+        for (int k : wave) {
+            const Strip& S = strips[k];
+            const int h = regions[S.region].h;
+            DotTask t{};
+            t.A = P(S.T[h + 1] * ss); t.B = P(S.G[h + 1] * ss); t.out = P((results + S.norm) * ss);
+            t.n = (long long)env_scalars(S, h + 1);
+            if (f32c) {
+                t.ea = eptr(S.eT[h + 1]);
+                t.eb = eptr(S.eG[h + 1]);
+            }
+            dts.push_back(t);
+            cl.insert(cl.end(), S.clos.begin(), S.clos.end());
+        }
+        pr.dot_step(dts);
+        std::vector<int> strip_of(nclos, -1);
+        for (int k : wave)
+            for (int ci : strips[k].clos) strip_of[ci] = k;
+        for (size_t w0 = 0; w0 < cl.size(); w0 += nlanes) {
+            const size_t w1 = std::min(cl.size(), w0 + nlanes);
+            // E^O for the operator sites of these closings
+            std::vector<DLTask> dlt;
+            long long dlmax = 1;
+            std::vector<int> i0(w1 - w0), i1(w1 - w0);
+            int nrows = 0;
+            for (size_t q = w0; q < w1; ++q) {
+                const int ci = cl[q];
+                const Closing& C = closings[ci];
+                const Region& R = regions[C.region];
+                const Lane& ln = lanes[q - w0];
+                i0[q - w0] = 1 << 30;
+                i1[q - w0] = -1;
+                for (size_t k = 0; k < C.pos.size(); ++k) {
+                    i0[q - w0] = std::min(i0[q - w0], C.pos[k].first + 1);
+                    i1[q - w0] = std::max(i1[q - w0], C.pos[k].first + 1);
+                    if (L->single) continue;  // the impurity tensor is E^O itself
+                    const int r = R.r0 + C.pos[k].first, c = R.c0 + C.pos[k].second;
+                    const auto dd = L->site_dims(r, c);
+                    DLTask t{};
+                    t.T = P(L->T_off[L->tensor_index(r, c)] * ss);
+                    t.E = P(ln.EO[k] * ss);
+                    t.O = P(opoff[ci][k] * ss);
+                    t.d = d; t.Du = dd[0]; t.Dl = dd[1]; t.Dd = dd[2]; t.Dr = dd[3];
+                    t.hb = L->hb ? 1 : 0;
+                    dlt.push_back(t);
+                    dlmax = std::max(dlmax, (long long)dd[0] * dd[0] * dd[1] * dd[1] * dd[2] * dd[2] * dd[3] * dd[3]);
+                }
+                nrows = std::max(nrows, i1[q - w0] - i0[q - w0] + 1);
+            }
+            if (!dlt.empty()) {
+                Step s;
+                s.kind = ST_DL;
+                s.first = pr.dl.size();
+                s.count = (int)dlt.size();
+                s.n = dlmax;
+                s.aux2 = L->hb ? 1 : 0;
+                pr.dl.insert(pr.dl.end(), dlt.begin(), dlt.end());
+                pr.steps.push_back(s);
+            }
+            for (int rr = 0; rr < nrows; ++rr) {
+                std::vector<FuseTask> ft;
+                long long fmx = 1;
+                std::vector<GTask> g1, g2, g3;
+                for (size_t q = w0; q < w1; ++q) {
+                    const int i = i0[q - w0] + rr;
+                    if (i > i1[q - w0]) continue;
+                    const int ci = cl[q];
+                    const Closing& C = closings[ci];
+                    const Strip& S = strips[strip_of[ci]];
+                    const Region& R = regions[S.region];
+                    const Lane& ln = lanes[q - w0];
+                    std::vector<std::pair<std::pair<int, int>, size_t>> subs;
+                    for (size_t k = 0; k < C.pos.size(); ++k)
+                        subs.push_back({C.pos[k], L->single ? opoff[ci][k] : ln.EO[k]});
+                    const Op4 o = strip_op(S, i, subs, ln.O12, ft, fmx);
+                    row_down(rr == 0 ? S.T[i] : ln.F[(rr - 1) % 2], ln.F[rr % 2], env_site(R, true, S.col, i), o,
+                             env_site(R, false, S.col + S.ncols - 1, i), ln, g1, g2, g3);
+                }
+                fuse_step(ft, fmx);
+                pr.gc_step(g1);
+                pr.gc_step(g2);
+                pr.gc_step(g3);
+            }
+            // N_O = <F after the closing's last row, G below it>
+            for (size_t q = w0; q < w1; ++q) {
+                const int ci = cl[q];
+                const Strip& S = strips[strip_of[ci]];
+                const int last = i1[q - w0], nr = last - i0[q - w0] + 1;
+                DotTask t{};
+                t.A = P(lanes[q - w0].F[(nr - 1) % 2] * ss);
+                t.B = P(S.G[last + 1] * ss);
+                t.out = P((results + ci) * ss);
+                t.n = (long long)env_scalars(S, last + 1);
+                if (f32c) {
+                    t.ea = eptr(S.eT[i0[q - w0]]);
+                    t.eb = eptr(S.eG[last + 1]);
+                }
+                dts.push_back(t);
+            }
+            pr.dot_step(dts);
         }
     }
+    if (leg_error) return fail(BBP_ERR_INVALID, "internal: column pair leg mismatch");
 
     // ---- check, allocate, relocate, upload, run
     pr.parent = &L->sweep;
@@ -541,9 +781,10 @@ extern "C" int bbp_expect(bbp_lattice* L, const bbp_term* terms, int n_terms, do
         const size_t bytes = u.second.size() * sizeof(double);
         CKR(cudaMemcpyAsync(ro + (u.first * ss - split), u.second.data(), bytes, cudaMemcpyHostToDevice, st));
     }
-    if (!pr.loop_descs.empty()) {
+    if (!pr.loop_descs.empty() && ds.launch_mode == 0) {
         // one graph: each fit loop is a conditional WHILE node that stops when its fits
         // have converged, instead of launching every loop body its maximum number of times
+        // (launch_mode 1: the kernels one by one, as for the sweep)
         CKR(pr.build_graph(st, nullptr, ds.seed));
         CKR(cudaGraphLaunch(pr.exec, st));
     } else {

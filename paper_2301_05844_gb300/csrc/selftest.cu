@@ -100,6 +100,59 @@ extern "C" int bbp_selftest_scalar(long long n, const double* x, double* rsqrt_o
     return abi_error();
 }
 
+extern "C" int bbp_selftest_qr_fp32(int batch, int m, int n, const float* A, double* Q, double* loss,
+                                    int* workspace_intact) try {
+    if (batch < 1 || n < 1 || m < n || n > 512 || !A || !Q || !workspace_intact)
+        return fail(BBP_ERR_INVALID, "selftest_qr_fp32: need batch >= 1, 1 <= n <= m, n <= 512, non-NULL arrays");
+    const size_t mat = (size_t)m * n;
+    const size_t guard = 512;                    // doubles after each task's 2 m n workspace
+    const size_t per = 2 * mat + guard;
+    const double pattern = -0x1.5p+77;            // a value no QR writes
+    std::vector<QRTask> ts(batch);
+    char* d = nullptr;
+    const size_t in_b = (size_t)batch * mat * sizeof(float), out_b = (size_t)batch * mat * sizeof(double);
+    const size_t work_b = (size_t)batch * per * sizeof(double), loss_b = (size_t)batch * sizeof(double);
+    cudaError_t e = cudaMalloc((void**)&d, in_b + out_b + work_b + loss_b + batch * sizeof(QRTask) + 1024);
+    if (e) return fail(BBP_ERR_OOM, std::string("selftest_qr_fp32: ") + cudaGetErrorString(e));
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    char* d_in = d;
+    char* d_out = d + al(in_b);
+    double* d_work = (double*)(d_out + al(out_b));
+    double* d_loss = (double*)((char*)d_work + al(work_b));
+    QRTask* d_ts = (QRTask*)((char*)d_loss + al(loss_b));
+    std::vector<double> wk((size_t)batch * per, pattern);
+    for (int b = 0; b < batch; ++b) {
+        QRTask& t = ts[b];
+        t = QRTask{};
+        t.in = d_in + b * mat * sizeof(float);
+        t.in_float = 2;
+        t.out = d_out + b * mat * sizeof(double);
+        t.work = d_work + b * per;
+        t.loss = d_loss + b;
+        t.m = m;
+        t.n = n;
+        t.in_rs = n; t.in_cs = 1; t.out_rs = n; t.out_cs = 1;
+    }
+    e = cudaMemcpy(d_in, A, in_b, cudaMemcpyHostToDevice);
+    if (!e) e = cudaMemcpy(d_work, wk.data(), wk.size() * sizeof(double), cudaMemcpyHostToDevice);
+    if (!e) e = cudaMemcpy(d_ts, ts.data(), ts.size() * sizeof(QRTask), cudaMemcpyHostToDevice);
+    if (!e) e = qr_prepare(m, false);
+    if (!e) e = launch_qr(d_ts, batch, m, (long long)mat, false, 0, QR_F32);
+    if (!e) e = cudaDeviceSynchronize();
+    if (!e) e = cudaMemcpy(Q, d_out, out_b, cudaMemcpyDeviceToHost);
+    if (!e && loss) e = cudaMemcpy(loss, d_loss, loss_b, cudaMemcpyDeviceToHost);
+    if (!e) e = cudaMemcpy(wk.data(), d_work, wk.size() * sizeof(double), cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e) return fail(BBP_ERR_CUDA, std::string("selftest_qr_fp32: ") + cudaGetErrorString(e));
+    int ok = 1;
+    for (int b = 0; b < batch; ++b)
+        for (size_t i = 2 * mat; i < per; ++i) ok &= wk[(size_t)b * per + i] == pattern;
+    *workspace_intact = ok;
+    return BBP_OK;
+} catch (...) {
+    return abi_error();
+}
+
 extern "C" int bbp_selftest_rng(unsigned long long seed, unsigned long long stream, long long n, double* out) try {
     if (n < 0 || (n > 0 && !out)) return fail(BBP_ERR_INVALID, "selftest_rng: bad arguments");
     for (long long i = 0; i < n; ++i) out[i] = bbp::uniform_pm1(seed, stream, (uint64_t)i);

@@ -8,7 +8,8 @@ from paper_2301_05844_gb300 import binding as B
 
 def run_both(T, Lx, Ly, d, D, bx, by, chi, terms, n_sweeps, boundary="obc", chi_exp=0, fit_tol=0.0,
              fit_max_sweeps=2, seed=7, init_mode=0, dtype=None, prec="fp64", warm_start=False, hermitian_basis=0,
-             single_layer=False, shift=(0, 0), oracle_hb=False, oracle_fit_tol=None, oracle_readout_fit_tol=None):
+             single_layer=False, shift=(0, 0), oracle_hb=False, oracle_fit_tol=None, oracle_readout_fit_tol=None,
+             keep_fp64=0):
     """oracle_hb: run the oracle in its Hermitian-basis option (the basis of the library's
     real-arithmetic paths for complex tensors).  oracle_fit_tol / oracle_readout_fit_tol: the
     fit tolerance of the oracle's message sweeps / read-out fits (default: fit_tol), set to
@@ -18,7 +19,8 @@ def run_both(T, Lx, Ly, d, D, bx, by, chi, terms, n_sweeps, boundary="obc", chi_
         dtype = B.C128 if cplx else B.F64
     g = B.Lattice(Lx=Lx, Ly=Ly, d=d, D=D, bx=bx, by=by, chi=chi, boundary=boundary, chi_exp=chi_exp, dtype=dtype,
                   prec=prec, fit_tol=fit_tol, fit_max_sweeps=fit_max_sweeps, seed=seed, init_mode=init_mode,
-                  warm_start=warm_start, hermitian_basis=hermitian_basis, single_layer=int(single_layer), shift=shift)
+                  warm_start=warm_start, hermitian_basis=hermitian_basis, single_layer=int(single_layer), shift=shift,
+                  keep_fp64=keep_fp64)
     g.set_tensors(T)
     o = ob.Lattice(Lx, Ly, d, D, bx, by, [np.asarray(t) for t in T], boundary=boundary, chi=chi, chi_exp=chi_exp,
                    fit_tol=fit_tol if oracle_fit_tol is None else oracle_fit_tol, fit_max_sweeps=fit_max_sweeps,

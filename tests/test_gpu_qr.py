@@ -66,3 +66,40 @@ def test_qr_rank_deficient_and_tiny_columns(cplx):
     Qn, Rn = np.linalg.qr(A[0][:, :4])
     ph = np.diag(Rn) / np.abs(np.diag(Rn))
     assert np.allclose(Q[:, :4], Qn * ph[None, :], atol=1e-12)
+
+
+@pytest.mark.parametrize("m,n,batch,scale", [(9, 9, 3, 1.0), (12, 9, 2, 1.0), (108, 12, 4, 1.0), (27, 27, 2, 1.0),
+                                             (1, 1, 2, 1.0), (33, 17, 2, 1.0), (300, 64, 2, 1.0),
+                                             (2400, 96, 2, 1.0), (1500, 37, 1, 1.0), (108, 12, 2, 1e25),
+                                             (300, 64, 1, 1e-25)])
+def test_qr_fp32_arithmetic(m, n, batch, scale):
+    """The FP32-arithmetic blocked QR of the tensor-core paths: on small matrices (one panel
+    wider than the matrix, square ones) as well as the 2400 x 96 site matrices.  Q against
+    the FP64 QR of the same FP32 input with the same sign rule (well-conditioned Gaussian
+    matrices: the FP32 factorisation's error is a few units of 2^-24 times a modest growth
+    factor), orthonormality, Q R = A with R = Q^T A upper triangular and diag(R) >= 0, the
+    loss in FP64, and no write past a task's 2 m n workspace.  Scaled by 1e25 (squares beyond
+    the FP32 range) and 1e-25 (squares below it), Q is the same."""
+    import ctypes as C
+    rng = np.random.default_rng(3 * m + n)
+    A = (scale * rng.standard_normal((batch, m, n))).astype(np.float32)
+    Q = np.zeros((batch, m, n))
+    loss = np.zeros(batch)
+    intact = C.c_int(0)
+    L = B.lib()
+    L.bbp_selftest_qr_fp32.argtypes = [C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
+                                       C.POINTER(C.c_int)]
+    assert L.bbp_selftest_qr_fp32(batch, m, n, A.ctypes.data, Q.ctypes.data, loss.ctypes.data, C.byref(intact)) == 0
+    assert intact.value == 1
+    tol = 2e-5 * np.sqrt(m)
+    for b in range(batch):
+        Ad = A[b].astype(np.float64)
+        Qn, Rn = np.linalg.qr(Ad)
+        Qn = Qn * np.where(np.diag(Rn) < 0, -1.0, 1.0)[None, :]
+        assert np.max(np.abs(Q[b] - Qn)) < tol
+        assert np.max(np.abs(Q[b].T @ Q[b] - np.eye(n))) < tol
+        R = Q[b].T @ Ad
+        assert np.max(np.abs(np.tril(R, -1))) < tol * np.max(np.abs(Ad))
+        assert np.all(np.diag(R) > -tol)
+        assert np.max(np.abs(Q[b] @ np.triu(R) - Ad)) < tol * np.max(np.abs(Ad))
+    assert np.allclose(loss, -np.sum(A.astype(np.float64) ** 2, axis=(1, 2)), rtol=1e-6)

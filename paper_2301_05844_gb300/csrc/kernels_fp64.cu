@@ -195,6 +195,18 @@ __device__ __forceinline__ double widen(double a) { return a; }
 __device__ __forceinline__ double2 widen(double2 a) { return a; }
 __device__ __forceinline__ double widen(float a) { return (double)a; }
 __device__ __forceinline__ double2 widen(float2 a) { return make_double2((double)a.x, (double)a.y); }
+// (h, l) <- h + c exactly as the pair h + l (Knuth's TwoSum; l collects the rounding errors)
+__device__ __forceinline__ void two_sum_into(float& h, float& l, float c) {
+    const float s = h + c, bp = s - h;
+    l += (h - (s - bp)) + (c - bp);
+    h = s;
+}
+__device__ __forceinline__ void two_sum_into(float2& h, float2& l, float2 c) {
+    two_sum_into(h.x, l.x, c.x);
+    two_sum_into(h.y, l.y, c.y);
+}
+__device__ __forceinline__ void two_sum_into(double&, double&, double) {}
+__device__ __forceinline__ void two_sum_into(double2&, double2&, double2) {}
 template <typename Cm> __device__ __forceinline__ Cm narrow(double a);
 template <typename Cm> __device__ __forceinline__ Cm narrow(double2 a);
 template <> __device__ __forceinline__ double narrow<double>(double a) { return a; }
@@ -298,8 +310,9 @@ __device__ __forceinline__ double load_kind(const void* p, long long i, int kind
 // ---------------------------------------------------------------- generic contraction
 // 64x64 output tile per CTA, K in chunks of 16, 256 threads each owning 4x4 outputs.
 // Cm is the arithmetic type: S itself, or float / float2 for FP64 operands contracted in FP32
-// arithmetic (each operand rounded to FP32 as it is staged, FP32 accumulation, the result
-// widened to FP64 when stored).
+// arithmetic: each operand rounded to FP32 as it is staged, each chunk of 16 products summed in
+// FP32 and the chunks added into an unevaluated FP32 pair (hi, lo) by Knuth's TwoSum, so that
+// the accumulation error does not grow with K; the result hi + lo is formed in FP64.
 template <typename S, typename Cm = S>
 __global__ void __launch_bounds__(256) k_gcontract(const GTask* __restrict__ tasks) {
     const GTask& t = tasks[blockIdx.y];
@@ -319,11 +332,12 @@ __global__ void __launch_bounds__(256) k_gcontract(const GTask* __restrict__ tas
     const bool av = am < M, bv = bn < N;
     const long long aoff = av ? (long long)(am / t.M2) * t.a_m1 + (long long)(am % t.M2) * t.a_m2 : 0;
     const long long boff = bv ? (long long)(bn / t.N2) * t.b_n1 + (long long)(bn % t.N2) * t.b_n2 : 0;
-    Cm acc[4][4];
+    constexpr bool kComp = !std::is_same<S, Cm>::value;
+    Cm acc[4][4], hi[4][4], lo[4][4];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = zero<Cm>();
+        for (int j = 0; j < 4; ++j) acc[i][j] = hi[i][j] = lo[i][j] = zero<Cm>();
     for (int k0 = 0; k0 < Kd; k0 += 16) {
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
@@ -354,6 +368,15 @@ __global__ void __launch_bounds__(256) k_gcontract(const GTask* __restrict__ tas
                 for (int j = 0; j < 4; ++j) mac(acc[i][j], a[i], b[j]);
         }
         __syncthreads();
+        if constexpr (kComp) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    two_sum_into(hi[i][j], lo[i][j], acc[i][j]);
+                    acc[i][j] = zero<Cm>();
+                }
+        }
     }
     S* __restrict__ Cp = (S*)t.C;
 #pragma unroll
@@ -366,7 +389,9 @@ __global__ void __launch_bounds__(256) k_gcontract(const GTask* __restrict__ tas
             const int n = n0 + tx + 16 * j;
             if (n >= N) continue;
             const long long o = mo + (long long)(n / t.N2) * t.c_n1 + (long long)(n % t.N2) * t.c_n2;
-            const S r = widen(acc[i][j]);
+            S r;
+            if constexpr (kComp) r = add(widen(hi[i][j]), widen(lo[i][j]));
+            else r = widen(acc[i][j]);
             Cp[o] = t.accumulate ? add(Cp[o], r) : r;
         }
     }
@@ -455,17 +480,18 @@ cudaError_t launch_gcontract(const GTask* d_tasks, int ntasks, int max_tiles, bo
 // R_jj = |beta_j| >= 0.  (k_qr_wy and k_qr_cluster below.)
 constexpr int QR_MAXN = 512;
 constexpr size_t QR_SMEM_LIMIT = 200 * 1024;
+constexpr size_t QR32_SMEM_LIMIT = 100 * 1024;  // FP32 blocked QR: two CTAs per SM
 
 // T of the compact-WY form of a panel (H_p0 ... H_p0+pw-1 = I - V T V^H, T upper triangular,
 // T_jj = tau_j, T[0:j, j] = -tau_j T[0:j, 0:j] V[:, 0:j]^H v_j) from its reflectors in P:
 // G = V^H V by the warps, then T column by column by thread 0.  The factorization and the Q
 // phase both call it on the same reflectors, so both see the same T.
-template <typename S, int NB>
+template <typename S, int NB, int NT>
 __device__ __forceinline__ void panel_T(const S* P, int m, int p0, int pw, const typename ScalarTraits<S>::R* taus,
                                         S* G, S* Ts) {
     using R = typename ScalarTraits<S>::R;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    for (int pr = warp; pr < pw * pw; pr += 8) {
+    for (int pr = warp; pr < pw * pw; pr += NT / 32) {
         const int r = pr / pw, c = pr - r * pw;
         if (r >= c) continue;
         const S* vr = P + (size_t)r * m;
@@ -566,8 +592,8 @@ __device__ __forceinline__ void panel_update(S* c, const S* P, const S (&w)[NB],
 // FP32 instruction issues at 64 times the FP64 rate, and a single-CTA FP64 QR of a 2400 x 96
 // site matrix is bound by exactly that rate.  Q is still written in FP64 (and the low-precision
 // copy), and the loss is still summed in FP64.
-template <typename S, int NB>
-__global__ void __launch_bounds__(256) k_qr_wy(const QRTask* __restrict__ tasks) {
+template <typename S, int NB, int NT>
+__global__ void __launch_bounds__(NT, NT == 512 ? 2 : 1) k_qr_wy(const QRTask* __restrict__ tasks) {
     using R = typename ScalarTraits<S>::R;
     using SW = typename ScalarTraits<S>::Wide;
     const QRTask& t = tasks[blockIdx.x];
@@ -584,7 +610,7 @@ __global__ void __launch_bounds__(256) k_qr_wy(const QRTask* __restrict__ tasks)
     S* W = (S*)t.work;
     double ss = 0.0;  // the loss -||in||^2, summed in FP64
     if constexpr (std::is_same<R, double>::value) {
-        for (long long idx = tid; idx < (long long)m * n; idx += 256) {
+        for (long long idx = tid; idx < (long long)m * n; idx += NT) {
             const int i = (int)(idx % m), j = (int)(idx / m);
             const long long src = (long long)i * t.in_rs + (long long)j * t.in_cs;
             S v = t.in_float ? from_float<S>(((const float*)t.in), src) : from_double<S>(t.in, src);
@@ -598,7 +624,7 @@ __global__ void __launch_bounds__(256) k_qr_wy(const QRTask* __restrict__ tasks)
         // and the loss is scaled back by 4^e.  Squares are summed in FP32 in runs of 16, the
         // runs in FP64.
         R amax = R(0);
-        for (long long idx = tid; idx < (long long)m * n; idx += 256) {
+        for (long long idx = tid; idx < (long long)m * n; idx += NT) {
             const int i = (int)(idx % m), j = (int)(idx / m);
             const long long src = (long long)i * t.in_rs + (long long)j * t.in_cs;
             S v = t.in_float ? from_float<S>(((const float*)t.in), src) : from_double<S>(t.in, src);
@@ -612,7 +638,7 @@ __global__ void __launch_bounds__(256) k_qr_wy(const QRTask* __restrict__ tasks)
         const R sc = ldexpf(1.0f, -e);
         R part = R(0);
         int cnt = 0;
-        for (long long idx = tid; idx < (long long)m * n; idx += 256) {
+        for (long long idx = tid; idx < (long long)m * n; idx += NT) {
             const int i = (int)(idx % m), j = (int)(idx / m);
             const S v = scal(W[(size_t)j * m + i], sc);
             W[(size_t)j * m + i] = v;
@@ -631,7 +657,7 @@ __global__ void __launch_bounds__(256) k_qr_wy(const QRTask* __restrict__ tasks)
     // ---- factorization
     for (int p0 = 0; p0 < n; p0 += NB) {
         const int pw = min(NB, n - p0), rows = m - p0;
-        for (int idx = tid; idx < pw * rows; idx += 256) {
+        for (int idx = tid; idx < pw * rows; idx += NT) {
             const int c = idx / rows, i = p0 + (idx - c * rows);
             P[(size_t)c * m + i] = W[(size_t)(p0 + c) * m + i];
         }
@@ -640,16 +666,16 @@ __global__ void __launch_bounds__(256) k_qr_wy(const QRTask* __restrict__ tasks)
             const int j = p0 + c;
             S* col = P + (size_t)c * m;
             R xs2 = R(0);
-            for (int i = j + 1 + tid; i < m; i += 256) xs2 += abs2(col[i]);
+            for (int i = j + 1 + tid; i < m; i += NT) xs2 += abs2(col[i]);
             xs2 = block_sum(xs2, redr);
             R xnorm = sqrt_r(xs2);
             if (xs2 < ScalarTraits<S>::tiny2()) {  // near underflow (uniform branch): rescale by max |x'_i|
                 R amax = R(0);
-                for (int i = j + 1 + tid; i < m; i += 256) amax = max_r(amax, absv(col[i]));
+                for (int i = j + 1 + tid; i < m; i += NT) amax = max_r(amax, absv(col[i]));
                 amax = block_max(amax, redr);
                 R t2 = R(0);
                 if (amax > R(0))
-                    for (int i = j + 1 + tid; i < m; i += 256) t2 += abs2(divr(col[i], amax));
+                    for (int i = j + 1 + tid; i < m; i += NT) t2 += abs2(divr(col[i], amax));
                 t2 = block_sum(t2, redr);
                 xnorm = amax > R(0) ? amax * sqrt_r(t2) : R(0);
             }
@@ -666,9 +692,9 @@ __global__ void __launch_bounds__(256) k_qr_wy(const QRTask* __restrict__ tasks)
                 const S cph = conjv(ph);
                 if (den > ScalarTraits<S>::tiny_div()) {
                     const S sc = scal(cph, R(1) / den);
-                    for (int i = j + 1 + tid; i < m; i += 256) col[i] = mul(col[i], sc);
+                    for (int i = j + 1 + tid; i < m; i += NT) col[i] = mul(col[i], sc);
                 } else {
-                    for (int i = j + 1 + tid; i < m; i += 256) col[i] = divr(mul(col[i], cph), den);
+                    for (int i = j + 1 + tid; i < m; i += NT) col[i] = divr(mul(col[i], cph), den);
                 }
             }
             __syncthreads();  // every thread has read alpha
@@ -677,10 +703,10 @@ __global__ void __launch_bounds__(256) k_qr_wy(const QRTask* __restrict__ tasks)
                 taus[j] = tau;
                 col[j] = one<S>();  // v_j[j] = 1 (with tau = 0 the reflector is the identity)
             }
-            for (int i = p0 + tid; i < j; i += 256) col[i] = zero<S>();  // V is zero above its diagonal
+            for (int i = p0 + tid; i < j; i += NT) col[i] = zero<S>();  // V is zero above its diagonal
             __syncthreads();
             if (tau != R(0)) {  // H_j on the panel's later columns, one warp each
-                for (int k = c + 1 + warp; k < pw; k += 8) {
+                for (int k = c + 1 + warp; k < pw; k += NT / 32) {
                     S* ck = P + (size_t)k * m;
                     S d0 = zero<S>(), d1 = zero<S>();
                     int i = j + lane;
@@ -696,9 +722,9 @@ __global__ void __launch_bounds__(256) k_qr_wy(const QRTask* __restrict__ tasks)
             __syncthreads();
         }
         // T of the panel (recomputed by the Q phase from the same reflectors)
-        panel_T<S, NB>(P, m, p0, pw, taus, G, Ts);
+        panel_T<S, NB, NT>(P, m, p0, pw, taus, G, Ts);
         // trailing columns: c <- c - V (T^H (V^H c)), one column per warp
-        for (int k = p0 + pw + warp; k < n; k += 8) {
+        for (int k = p0 + pw + warp; k < n; k += NT / 32) {
             S* ck = W + (size_t)k * m;
             S acc[NB];
 #pragma unroll
@@ -718,7 +744,7 @@ __global__ void __launch_bounds__(256) k_qr_wy(const QRTask* __restrict__ tasks)
             panel_update<S, NB>(ck, P, wv, m, p0, pw, lane);
         }
         // the panel's reflectors back to W (read again by the Q phase)
-        for (int idx = tid; idx < pw * rows; idx += 256) {
+        for (int idx = tid; idx < pw * rows; idx += NT) {
             const int c = idx / rows, i = p0 + (idx - c * rows);
             W[(size_t)(p0 + c) * m + i] = P[(size_t)c * m + i];
         }
@@ -727,18 +753,18 @@ __global__ void __launch_bounds__(256) k_qr_wy(const QRTask* __restrict__ tasks)
     // ---- Q, backwards over the panels, in place
     for (int p0 = ((n - 1) / NB) * NB; p0 >= 0; p0 -= NB) {
         const int pw = min(NB, n - p0), rows = m - p0;
-        for (int idx = tid; idx < pw * rows; idx += 256) {
+        for (int idx = tid; idx < pw * rows; idx += NT) {
             const int c = idx / rows, i = p0 + (idx - c * rows);
             P[(size_t)c * m + i] = W[(size_t)(p0 + c) * m + i];
         }
         __syncthreads();
-        panel_T<S, NB>(P, m, p0, pw, taus, G, Ts);
-        for (int idx = tid; idx < pw * m; idx += 256) {  // columns p0.. of the panel start as e_k
+        panel_T<S, NB, NT>(P, m, p0, pw, taus, G, Ts);
+        for (int idx = tid; idx < pw * m; idx += NT) {  // columns p0.. of the panel start as e_k
             const int c = idx / m, i = idx - c * m;
             W[(size_t)(p0 + c) * m + i] = i == p0 + c ? one<S>() : zero<S>();
         }
         __syncthreads();
-        for (int k = p0 + warp; k < n; k += 8) {
+        for (int k = p0 + warp; k < n; k += NT / 32) {
             S* ck = W + (size_t)k * m;
             S acc[NB];
 #pragma unroll
@@ -761,7 +787,7 @@ __global__ void __launch_bounds__(256) k_qr_wy(const QRTask* __restrict__ tasks)
     }
     // ---- output: column k times phase(beta_k), so that R_kk = |beta_k| >= 0
     SW* out = (SW*)t.out;  // FP64 (complex-FP64) in every arithmetic
-    for (long long idx = tid; idx < (long long)m * n; idx += 256) {
+    for (long long idx = tid; idx < (long long)m * n; idx += NT) {
         const int i = (int)(idx % m), k = (int)(idx / m);
         const R bb = absv(betas[k]);
         const S ph = bb > R(0) ? divr(betas[k], bb) : one<S>();
@@ -1183,36 +1209,35 @@ cudaError_t qr_prepare(int max_m, bool cplx) {
     if (done[dev][cplx ? 1 : 0]) return cudaSuccess;
     const int lim = (int)QR_SMEM_LIMIT;
     cudaError_t e;
-    // the FP32-arithmetic blocked QR (reduced-precision paths)
+    // the FP32-arithmetic blocked QR (reduced-precision paths): 512 threads, two CTAs per SM
+    const int lim32 = (int)QR32_SMEM_LIMIT;
     if (cplx) {
-        if ((e = cudaFuncSetAttribute(k_qr_wy<float2, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
-        if ((e = cudaFuncSetAttribute(k_qr_wy<float2, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
-        if ((e = cudaFuncSetAttribute(k_qr_wy<float2, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
-        if ((e = cudaFuncSetAttribute(k_qr_wy<float2, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
-        if ((e = cudaFuncSetAttribute(k_qr_wy<float2, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+        if ((e = cudaFuncSetAttribute(k_qr_wy<float2, 1, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim32))) return e;
+        if ((e = cudaFuncSetAttribute(k_qr_wy<float2, 2, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim32))) return e;
+        if ((e = cudaFuncSetAttribute(k_qr_wy<float2, 4, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim32))) return e;
+        if ((e = cudaFuncSetAttribute(k_qr_wy<float2, 8, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim32))) return e;
     } else {
-        if ((e = cudaFuncSetAttribute(k_qr_wy<float, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
-        if ((e = cudaFuncSetAttribute(k_qr_wy<float, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
-        if ((e = cudaFuncSetAttribute(k_qr_wy<float, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
-        if ((e = cudaFuncSetAttribute(k_qr_wy<float, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
-        if ((e = cudaFuncSetAttribute(k_qr_wy<float, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+        if ((e = cudaFuncSetAttribute(k_qr_wy<float, 1, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim32))) return e;
+        if ((e = cudaFuncSetAttribute(k_qr_wy<float, 2, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim32))) return e;
+        if ((e = cudaFuncSetAttribute(k_qr_wy<float, 4, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim32))) return e;
+        if ((e = cudaFuncSetAttribute(k_qr_wy<float, 8, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim32))) return e;
     }
     if (cplx) {
         if ((e = cudaFuncSetAttribute(k_qr_cluster<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)QR_CLUSTER_SMEM)) != cudaSuccess) return e;
-        if ((e = cudaFuncSetAttribute(k_qr_wy<double2, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
-        if ((e = cudaFuncSetAttribute(k_qr_wy<double2, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
-        if ((e = cudaFuncSetAttribute(k_qr_wy<double2, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
-        if ((e = cudaFuncSetAttribute(k_qr_wy<double2, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
-        if ((e = cudaFuncSetAttribute(k_qr_wy<double2, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+        if ((e = cudaFuncSetAttribute(k_qr_wy<double2, 1, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+        if ((e = cudaFuncSetAttribute(k_qr_wy<double2, 2, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+        if ((e = cudaFuncSetAttribute(k_qr_wy<double2, 4, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+        if ((e = cudaFuncSetAttribute(k_qr_wy<double2, 8, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+        if ((e = cudaFuncSetAttribute(k_qr_wy<double2, 16, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
     } else {
         if ((e = cudaFuncSetAttribute(k_qr_cluster<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)QR_CLUSTER_SMEM)) != cudaSuccess) return e;
-        if ((e = cudaFuncSetAttribute(k_qr_wy<double, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
-        if ((e = cudaFuncSetAttribute(k_qr_wy<double, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
-        if ((e = cudaFuncSetAttribute(k_qr_wy<double, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
-        if ((e = cudaFuncSetAttribute(k_qr_wy<double, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
-        if ((e = cudaFuncSetAttribute(k_qr_wy<double, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+        if ((e = cudaFuncSetAttribute(k_qr_wy<double, 1, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+        if ((e = cudaFuncSetAttribute(k_qr_wy<double, 2, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+        if ((e = cudaFuncSetAttribute(k_qr_wy<double, 4, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+        if ((e = cudaFuncSetAttribute(k_qr_wy<double, 8, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+        if ((e = cudaFuncSetAttribute(k_qr_wy<double, 16, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
     }
     done[dev][cplx ? 1 : 0] = true;
     return cudaSuccess;
@@ -1226,18 +1251,21 @@ cudaError_t launch_qr(const QRTask* d_tasks, int ntasks, int max_m, long long ma
                       int cluster) {
     if (ntasks <= 0) return cudaSuccess;
     if (cluster & QR_F32) {
-        // FP32 arithmetic: the blocked QR, one CTA per task, whatever the size
+        // FP32 arithmetic: the blocked QR, one CTA of 512 threads per task, whatever the size,
+        // panels of up to 8 columns so that two CTAs share an SM (the one-CTA QR is bound by
+        // latency, not by a unit's throughput)
         const size_t fsz = cplx ? sizeof(float2) : sizeof(float);
-        const int nb = qr_wy_nb(max_m, fsz);
+        int nb = 8;
+        while (nb > 1 && (size_t)nb * max_m * fsz > QR32_SMEM_LIMIT) nb >>= 1;
         const size_t sm = (size_t)nb * max_m * fsz;
-        if (sm > QR_SMEM_LIMIT) return cudaErrorInvalidValue;
+        if (sm > QR32_SMEM_LIMIT) return cudaErrorInvalidValue;
 #define WY_CASE(NB_)                                                               \
         if (nb == NB_) {                                                           \
-            if (cplx) k_qr_wy<float2, NB_><<<ntasks, 256, sm, s>>>(d_tasks);       \
-            else k_qr_wy<float, NB_><<<ntasks, 256, sm, s>>>(d_tasks);             \
+            if (cplx) k_qr_wy<float2, NB_, 512><<<ntasks, 512, sm, s>>>(d_tasks);  \
+            else k_qr_wy<float, NB_, 512><<<ntasks, 512, sm, s>>>(d_tasks);        \
             return cudaGetLastError();                                             \
         }
-        WY_CASE(16) WY_CASE(8) WY_CASE(4) WY_CASE(2) WY_CASE(1)
+        WY_CASE(8) WY_CASE(4) WY_CASE(2) WY_CASE(1)
 #undef WY_CASE
         return cudaErrorInvalidValue;
     }
@@ -1275,8 +1303,8 @@ cudaError_t launch_qr(const QRTask* d_tasks, int ntasks, int max_m, long long ma
     if (sm > QR_SMEM_LIMIT) return cudaErrorInvalidValue;
 #define WY_CASE(NB_)                                                               \
     if (nb == NB_) {                                                               \
-        if (cplx) k_qr_wy<double2, NB_><<<ntasks, 256, sm, s>>>(d_tasks);          \
-        else k_qr_wy<double, NB_><<<ntasks, 256, sm, s>>>(d_tasks);                \
+        if (cplx) k_qr_wy<double2, NB_, 256><<<ntasks, 256, sm, s>>>(d_tasks);          \
+        else k_qr_wy<double, NB_, 256><<<ntasks, 256, sm, s>>>(d_tasks);                \
         return cudaGetLastError();                                                 \
     }
     WY_CASE(16) WY_CASE(8) WY_CASE(4) WY_CASE(2) WY_CASE(1)

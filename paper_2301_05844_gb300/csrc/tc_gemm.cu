@@ -279,11 +279,18 @@ __device__ __forceinline__ void epilogue_dest(const float* tile, long long* roff
     // a split destination vectorises only if every segment start stays 16-byte aligned
     const bool segs_aligned = !x3 || ((kseg * esz) & 15) == 0;
     float x[8];
-    // A split destination whose segments are not 16-byte aligned takes no vector at all (the
-    // site-update operands of D=5: split rows whose segments are K = 625 apart): one pass of
-    // scalar stores, each warp on one row (one column) at a time with its lanes on consecutive
-    // destination addresses, no per-element index arithmetic beyond the two offsets.
-    if (!segs_aligned && (sn2 == 1 || sm2 == 1)) {
+    // fully regular destinations (below): every group of VW rows (columns) is one vector
+    const bool al = (base & 15) == 0 && segs_aligned;
+    const bool vec_m = al && sm2 == 1 && M2 % VW == 0 && m0 % VW == 0 && sm1 % VW == 0 && sn1 % VW == 0 && sn2 % VW == 0;
+    const bool vec_n = !vec_m && al && sn2 == 1 && N2 % VW == 0 && n0 % VW == 0 && sn1 % VW == 0 && sm1 % VW == 0 &&
+                       sm2 % VW == 0;
+    // A destination whose contiguous runs cannot line up with vectors (split segments not
+    // 16-byte aligned: the site-update operands of D=5, whose segments are K = 625 apart; or a
+    // run length that is no multiple of the vector width, such as q = 25) takes no vector at
+    // all: one pass of scalar stores, each warp on one row (one column) at a time with its
+    // lanes on consecutive destination addresses, no per-element test or index division.
+    if (!vec_m && !vec_n && (!segs_aligned || (sn2 == 1 && N2 % VW) || (sm2 == 1 && M2 % VW)) &&
+        (sn2 == 1 || sm2 == 1)) {
         const int wq = tid >> 5, ln = tid & 31;
         constexpr int NW = EPI_THREADS / 32;
         if (sn2 == 1) {
@@ -304,6 +311,48 @@ __device__ __forceinline__ void epilogue_dest(const float* tile, long long* roff
                     else store_out(out, roff[r] + co, kind, xv);
                 }
             }
+        }
+        return;
+    }
+    // Fully regular destinations: contiguous along m2 (or n2) in runs that are whole multiples
+    // of the vector width, every run start and segment 16-byte aligned.  Then every group of VW
+    // rows (columns) of the chunk is one vector: a single pass, no per-group test; lanes run
+    // along the contiguous direction (consecutive 16-byte stores), a ragged tail in scalars.
+    if (vec_m) {
+        const int G = rows / VW;
+        for (int it = tid; it < ncols * G; it += EPI_THREADS) {
+            const int c = it / G, r0 = (it - c * G) * VW;
+            const long long o = roff[r0] + coff[c];
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                if (j < VW) x[j] = tile[(r0 + j) * P + c] * alpha;
+            if (x3) store_split_vec(out, o, kind, x, x3, kseg);
+            else store_vec(out, o, kind, x);
+        }
+        for (int it = tid; it < ncols * (rows - G * VW); it += EPI_THREADS) {
+            const int c = it / (rows - G * VW), r = G * VW + it % (rows - G * VW);
+            const float xv = tile[r * P + c] * alpha;
+            if (x3) store_split1(out, roff[r] + coff[c], kind, xv, x3, kseg);
+            else store_out(out, roff[r] + coff[c], kind, xv);
+        }
+        return;
+    }
+    if (vec_n) {
+        const int G = ncols / VW;
+        for (int it = tid; it < rows * G; it += EPI_THREADS) {
+            const int r = it / G, c0 = (it - r * G) * VW;
+            const long long o = roff[r] + coff[c0];
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                if (j < VW) x[j] = tile[r * P + c0 + j] * alpha;
+            if (x3) store_split_vec(out, o, kind, x, x3, kseg);
+            else store_vec(out, o, kind, x);
+        }
+        for (int it = tid; it < rows * (ncols - G * VW); it += EPI_THREADS) {
+            const int r = it / (ncols - G * VW), c = G * VW + it % (ncols - G * VW);
+            const float xv = tile[r * P + c] * alpha;
+            if (x3) store_split1(out, roff[r] + coff[c], kind, xv, x3, kseg);
+            else store_out(out, roff[r] + coff[c], kind, xv);
         }
         return;
     }

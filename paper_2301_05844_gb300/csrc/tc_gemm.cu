@@ -123,15 +123,15 @@ __device__ __forceinline__ void umma_commit(uint64_t* bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                  : "memory");
 }
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* r) {
+__device__ __forceinline__ void tmem_ld16_issue(uint32_t taddr, uint32_t* r) {
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
           "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
         : "r"(taddr)
         : "memory");
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 // Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart.
 __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
@@ -190,6 +190,11 @@ __device__ __forceinline__ void store_vec(void* out, long long o, int kind, cons
 }
 
 constexpr int EC = 64;  // epilogue chunk (columns)
+// Staged rows are skewed by one slot per 32 rows: row r lives at slot r + r / 32 (pitch EC + 1),
+// so that the 16 lanes reading rows 8l + j of one column (a vector down a column) hit 16
+// different banks, while row-wise and lane-per-row accesses stay conflict-free.
+constexpr int TROWS = BM + BM / 32;
+__device__ __forceinline__ int trow(int r) { return r + (r >> 5); }
 
 // Split destination (x3 = 1: A rows [hi|lo|hi], 2: B rows [hi|hi|lo], segments kseg
 // elements apart): hi = r(x), lo = r(x - hi), r the rounding of the element kind (TF32 for
@@ -297,7 +302,7 @@ __device__ __forceinline__ void epilogue_dest(const float* tile, long long* roff
             for (int r = wq; r < rows; r += NW) {
                 const long long ro = roff[r];
                 for (int c = ln; c < ncols; c += 32) {
-                    const float xv = tile[r * P + c] * alpha;
+                    const float xv = tile[trow(r) * P + c] * alpha;
                     if (x3) store_split1(out, ro + coff[c], kind, xv, x3, kseg);
                     else store_out(out, ro + coff[c], kind, xv);
                 }
@@ -306,7 +311,7 @@ __device__ __forceinline__ void epilogue_dest(const float* tile, long long* roff
             for (int c = wq; c < ncols; c += NW) {
                 const long long co = coff[c];
                 for (int r = ln; r < rows; r += 32) {
-                    const float xv = tile[r * P + c] * alpha;
+                    const float xv = tile[trow(r) * P + c] * alpha;
                     if (x3) store_split1(out, roff[r] + co, kind, xv, x3, kseg);
                     else store_out(out, roff[r] + co, kind, xv);
                 }
@@ -325,13 +330,13 @@ __device__ __forceinline__ void epilogue_dest(const float* tile, long long* roff
             const long long o = roff[r0] + coff[c];
 #pragma unroll
             for (int j = 0; j < 8; ++j)
-                if (j < VW) x[j] = tile[(r0 + j) * P + c] * alpha;
+                if (j < VW) x[j] = tile[trow(r0 + j) * P + c] * alpha;
             if (x3) store_split_vec(out, o, kind, x, x3, kseg);
             else store_vec(out, o, kind, x);
         }
         for (int it = tid; it < ncols * (rows - G * VW); it += EPI_THREADS) {
             const int c = it / (rows - G * VW), r = G * VW + it % (rows - G * VW);
-            const float xv = tile[r * P + c] * alpha;
+            const float xv = tile[trow(r) * P + c] * alpha;
             if (x3) store_split1(out, roff[r] + coff[c], kind, xv, x3, kseg);
             else store_out(out, roff[r] + coff[c], kind, xv);
         }
@@ -344,13 +349,13 @@ __device__ __forceinline__ void epilogue_dest(const float* tile, long long* roff
             const long long o = roff[r] + coff[c0];
 #pragma unroll
             for (int j = 0; j < 8; ++j)
-                if (j < VW) x[j] = tile[r * P + c0 + j] * alpha;
+                if (j < VW) x[j] = tile[trow(r) * P + c0 + j] * alpha;
             if (x3) store_split_vec(out, o, kind, x, x3, kseg);
             else store_vec(out, o, kind, x);
         }
         for (int it = tid; it < rows * (ncols - G * VW); it += EPI_THREADS) {
             const int r = it / (ncols - G * VW), c = G * VW + it % (ncols - G * VW);
-            const float xv = tile[r * P + c] * alpha;
+            const float xv = tile[trow(r) * P + c] * alpha;
             if (x3) store_split1(out, roff[r] + coff[c], kind, xv, x3, kseg);
             else store_out(out, roff[r] + coff[c], kind, xv);
         }
@@ -372,14 +377,14 @@ __device__ __forceinline__ void epilogue_dest(const float* tile, long long* roff
             const long long o = roff[r] + coff[c0];
 #pragma unroll
             for (int j = 0; j < 8; ++j)
-                if (j < VW) x[j] = tile[r * P + c0 + j] * alpha;
+                if (j < VW) x[j] = tile[trow(r) * P + c0 + j] * alpha;
             if (x3) store_split_vec(out, o, kind, x, x3, kseg);
             else store_vec(out, o, kind, x);
         }
         for (int it = tid; it < rows * ncols; it += EPI_THREADS) {  // lanes along a row
             const int r = it / ncols, c = it - r * ncols;
             if (is_vec(r, c - c % VW)) continue;
-            const float xv = tile[r * P + c] * alpha;
+            const float xv = tile[trow(r) * P + c] * alpha;
             if (x3) store_split1(out, roff[r] + coff[c], kind, xv, x3, kseg);
             else store_out(out, roff[r] + coff[c], kind, xv);
         }
@@ -396,21 +401,21 @@ __device__ __forceinline__ void epilogue_dest(const float* tile, long long* roff
             const long long o = roff[r0] + coff[c];
 #pragma unroll
             for (int j = 0; j < 8; ++j)
-                if (j < VW) x[j] = tile[(r0 + j) * P + c] * alpha;
+                if (j < VW) x[j] = tile[trow(r0 + j) * P + c] * alpha;
             if (x3) store_split_vec(out, o, kind, x, x3, kseg);
             else store_vec(out, o, kind, x);
         }
         for (int it = tid; it < rows * ncols; it += EPI_THREADS) {  // lanes down a column
             const int c = it / rows, r = it - c * rows;
             if (is_vec(r - r % VW, c)) continue;
-            const float xv = tile[r * P + c] * alpha;
+            const float xv = tile[trow(r) * P + c] * alpha;
             if (x3) store_split1(out, roff[r] + coff[c], kind, xv, x3, kseg);
             else store_out(out, roff[r] + coff[c], kind, xv);
         }
     } else {
         for (int it = tid; it < rows * ncols; it += EPI_THREADS) {
             const int c = it / rows, r = it - c * rows;
-            const float xv = tile[r * P + c] * alpha;
+            const float xv = tile[trow(r) * P + c] * alpha;
             if (x3) store_split1(out, roff[r] + coff[c], kind, xv, x3, kseg);
             else store_out(out, roff[r] + coff[c], kind, xv);
         }
@@ -419,7 +424,7 @@ __device__ __forceinline__ void epilogue_dest(const float* tile, long long* roff
 
 constexpr int EPI_WARPS = EPI_THREADS / 32;      // warps 2..9, two per TMEM lane quarter
 constexpr int NTHREADS = 32 * (2 + EPI_WARPS);   // producer, MMA issuer, epilogue
-constexpr size_t EPI_BYTES = (size_t)BM * (EC + 1) * sizeof(float) + (size_t)(BM + EC) * sizeof(long long);
+constexpr size_t EPI_BYTES = (size_t)TROWS * (EC + 1) * sizeof(float) + (size_t)(BM + EC) * sizeof(long long);
 
 // Persistent, warp-specialised grouped GEMM.  The work items of a launch are the tiles of all
 // its tasks (task = item / max_tiles, tile = item % max_tiles; tiles a task does not have are
@@ -443,7 +448,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc_gemm(const TCTask* __restric
     unsigned char* sA = smem;
     unsigned char* sB = smem + stages * A_STAGE;
     float* tile = (float*)(sB + stages * B_STAGE);  // epilogue staging, its own region
-    long long* roff = (long long*)(tile + BM * (EC + 1));
+    long long* roff = (long long*)(tile + TROWS * (EC + 1));
     long long* coff = roff + BM;
     __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES], tfull[2], tempty[2], mma_done;
     __shared__ uint32_t tmem_base;
@@ -575,13 +580,23 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc_gemm(const TCTask* __restric
                 const int cn = min(EC, ncols - c0);
                 const int nchunk = (cn + 15) & ~15;  // tcgen05.ld is warp-collective: uniform bound
                 epi_sync();                          // the previous chunk has been written out
-#pragma unroll 1
-                for (int c = 16 * half; c < nchunk; c += 32) {
-                    uint32_t v[16];
-                    tmem_ld16(acc + (uint32_t)(c0 + c), v);
+                {
+                    // this warp's two 16-column groups of the chunk: both loads issued, one wait
+                    const int c = 16 * half;
+                    uint32_t v[16], w[16];
+                    const bool two = c + 32 < nchunk;  // uniform: nchunk is
+                    if (c < nchunk) tmem_ld16_issue(acc + (uint32_t)(c0 + c), v);
+                    if (two) tmem_ld16_issue(acc + (uint32_t)(c0 + c + 32), w);
+                    tmem_wait_ld();
+                    float* trw = tile + trow(row) * (EC + 1);
+                    if (c < nchunk) {
 #pragma unroll
-                    for (int q = 0; q < 16; ++q)
-                        if (c + q < EC) tile[row * (EC + 1) + c + q] = __uint_as_float(v[q]);
+                        for (int q = 0; q < 16; ++q) trw[c + q] = __uint_as_float(v[q]);
+                    }
+                    if (two) {
+#pragma unroll
+                        for (int q = 0; q < 16; ++q) trw[c + 32 + q] = __uint_as_float(w[q]);
+                    }
                 }
                 if (c0 + EC >= ncols) {  // every column of this accumulator has been read
                     fence_before();

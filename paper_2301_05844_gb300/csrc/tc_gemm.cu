@@ -248,18 +248,20 @@ __device__ __forceinline__ void store_split_vec(void* out, long long o, int kind
     *(float4*)(f + o + 2 * kseg) = x3 == 1 ? Hf : Lf;
 }
 
-// The epilogue runs on the 256 threads of the eight epilogue warps (tid = 0..255); they
-// synchronise among themselves on named barrier 1.
-constexpr int EPI_THREADS = 256;
-__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+// The epilogue runs on the 384 threads of twelve epilogue warps (tid = 0..383): eight of them
+// drain the TMEM accumulator into the staged tile (two per quarter of the TMEM lanes), all
+// twelve write the staged tile out.  They synchronise among themselves on named barrier 1.
+constexpr int EPI_THREADS = 384;
+constexpr int DRAIN_WARPS = 8;
+__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, %0;" ::"n"(EPI_THREADS) : "memory"); }
 // the same barrier, returning whether every epilogue thread passed true
 __device__ __forceinline__ bool epi_all(bool v) {
     uint32_t r;
     asm volatile(
         "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\t"
-        "bar.red.and.pred q, 1, 256, p;\n\tselp.u32 %0, 1, 0, q;\n\t}\n"
+        "bar.red.and.pred q, 1, %2, p;\n\tselp.u32 %0, 1, 0, q;\n\t}\n"
         : "=r"(r)
-        : "r"((uint32_t)v)
+        : "r"((uint32_t)v), "n"(EPI_THREADS)
         : "memory");
     return r != 0;
 }
@@ -422,7 +424,7 @@ __device__ __forceinline__ void epilogue_dest(const float* tile, long long* roff
     }
 }
 
-constexpr int EPI_WARPS = EPI_THREADS / 32;      // warps 2..9, two per TMEM lane quarter
+constexpr int EPI_WARPS = EPI_THREADS / 32;      // warps 2..13; 2..9 drain TMEM, two per lane quarter
 constexpr int NTHREADS = 32 * (2 + EPI_WARPS);   // producer, MMA issuer, epilogue
 constexpr size_t EPI_BYTES = (size_t)TROWS * (EC + 1) * sizeof(float) + (size_t)(BM + EC) * sizeof(long long);
 
@@ -444,7 +446,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc_gemm(const TCTask* __restric
     const uint32_t A_STAGE = A_BYTES * ksub, B_STAGE = B_BYTES * ksub;
 
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    // aligned to 1024 bytes by pointer arithmetic on the shared array (an integer round trip
+    // would turn every access through these pointers into a generic one)
+    unsigned char* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
     unsigned char* sA = smem;
     unsigned char* sB = smem + stages * A_STAGE;
     float* tile = (float*)(sB + stages * B_STAGE);  // epilogue staging, its own region
@@ -462,7 +466,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc_gemm(const TCTask* __restric
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&tfull[b], 1);
-            mbar_init(&tempty[b], EPI_WARPS);
+            mbar_init(&tempty[b], DRAIN_WARPS);
         }
         mbar_init(&mma_done, 1);
         issued = 0;
@@ -559,7 +563,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc_gemm(const TCTask* __restric
         }
     } else {
         // epilogue: item j from accumulator j & 1, 64 columns at a time through shared memory
-        const int etid = threadIdx.x - 64;            // 0..255
+        const int etid = threadIdx.x - 64;            // 0..EPI_THREADS-1
+        const bool drains = warp < 2 + DRAIN_WARPS;   // warps 2..9 read the accumulator
         const int quad = warp & 3;                    // TMEM lanes 32 quad .. 32 quad + 31
         const int half = (warp - 2) >> 2;             // this warp's 16-column groups: c / 16 = half mod 2
         const int row = quad * 32 + lane;
@@ -570,7 +575,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc_gemm(const TCTask* __restric
             if (!item(w, t, m0, n0)) continue;
             const int b = j & 1, u = j >> 1;
             if (w + (int)gridDim.x >= nitems) launch_dependents();  // the last item of this CTA
-            // one decision for all four warps, so that none is left at a barrier
+            // one decision for all epilogue warps, so that none is left at a barrier
             if (!epi_all(mbar_wait(&tfull[b], u & 1, err))) break;
             fence_after();
             const uint32_t acc = tmem + (uint32_t)(b * (TCOLS / 2)) + ((uint32_t)(quad * 32) << 16);
@@ -580,7 +585,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc_gemm(const TCTask* __restric
                 const int cn = min(EC, ncols - c0);
                 const int nchunk = (cn + 15) & ~15;  // tcgen05.ld is warp-collective: uniform bound
                 epi_sync();                          // the previous chunk has been written out
-                {
+                if (drains) {
                     // this warp's two 16-column groups of the chunk: both loads issued, one wait
                     const int c = 16 * half;
                     uint32_t v[16], w[16];
@@ -598,7 +603,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc_gemm(const TCTask* __restric
                         for (int q = 0; q < 16; ++q) trw[c + 32 + q] = __uint_as_float(w[q]);
                     }
                 }
-                if (c0 + EC >= ncols) {  // every column of this accumulator has been read
+                if (drains && c0 + EC >= ncols) {  // every column of this accumulator has been read
                     fence_before();
                     __syncwarp();
                     if (lane == 0) mbar_arrive(&tempty[b]);

@@ -50,7 +50,7 @@ struct QRTask {
     long long out2_rs, out2_cs, out2_rs2;
     int out2_kind;   // element kind of out2 (see RelayoutTask)
     int out2_M2;     // >= 1
-    int out2_x3;     // split TF32 operand rows (see RelayoutTask)
+    int out2_x3;     // split operand (see RelayoutTask); out2_kseg = elements between its planes
     long long out2_kseg;
 };
 
@@ -64,8 +64,8 @@ struct RelayoutTask {
     long long ss[4];
     long long ds[4];
     int src_kind, dst_kind;
-    int x3;          // split TF32 operand (see store_split): 0 no, 1 A rows [hi|lo|hi], 2 B rows [hi|hi|lo]
-    long long kseg;  // K extent: distance between the three segments of a split row
+    int x3;          // split operand (see store_split): 0 no; else hi at the destination, lo kseg further
+    long long kseg;  // elements from the hi plane to the lo plane
 };
 
 // Fill n scalars (2n doubles if complex) with the counter-based uniforms in [-1,1).

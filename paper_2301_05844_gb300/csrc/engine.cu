@@ -131,7 +131,7 @@ std::string Program::validate() const {
         if (t.out2) {
             const int M2 = t.out2_M2 > 1 ? t.out2_M2 : 1;
             const long long ext = (long long)((t.m - 1) / M2) * t.out2_rs + (long long)(std::min(M2, t.m) - 1) * t.out2_rs2 +
-                                  (long long)(t.n - 1) * t.out2_cs + 1 + (t.out2_x3 ? 2 * t.out2_kseg : 0);
+                                  (long long)(t.n - 1) * t.out2_cs + 1 + (t.out2_x3 ? t.out2_kseg : 0);
             c.range(t.out2, ext, t.out2_kind == 0 ? 8 : t.out2_kind == 3 ? 2 : 4, "QR out2", i);
         }
         c.range(t.loss, 1, 8, "QR loss", i);
@@ -206,10 +206,12 @@ std::string Program::validate() const {
         if ((sp.a_ld * esz) % 16 || (sp.b_ld * esz) % 16 || sp.K > sp.a_ld || sp.K > sp.b_ld)
             return "tensor-core operand rows not padded to 16 bytes in task " + std::to_string(i);
         if (t.M != sp.a_rows || t.N != sp.b_rows || t.M % t.M2 || t.N % t.N2) return "tensor-core shape mismatch " + std::to_string(i);
-        c.range(P(sp.a_off), (sp.a_rows - 1) * sp.a_ld + sp.K, esz, "TC A", i);
-        c.range(P(sp.b_off), (sp.b_rows - 1) * sp.b_ld + sp.K, esz, "TC B", i);
+        if (t.nseg == 3 && (!sp.a_pl || !sp.b_pl || (sp.a_pl * esz) % 16 || (sp.b_pl * esz) % 16))
+            return "split tensor-core operand without an aligned second plane in task " + std::to_string(i);
+        c.range(P(sp.a_off), (sp.a_rows - 1) * sp.a_ld + sp.K + sp.a_pl, esz, "TC A", i);
+        c.range(P(sp.b_off), (sp.b_rows - 1) * sp.b_ld + sp.K + sp.b_pl, esz, "TC B", i);
         const int osz = t.out_kind == 2 ? 2 : t.out_kind == 3 ? 8 : 4;
-        const long long xc = (t.x3 & 3) ? 2 * t.kseg : 0, xd = ((t.x3 >> 2) & 3) ? 2 * t.kseg2 : 0;  // split segments
+        const long long xc = (t.x3 & 3) ? t.kseg : 0, xd = ((t.x3 >> 2) & 3) ? t.kseg2 : 0;  // split: second plane
         c.range(t.C, ext2(t.M / t.M2, t.c_m1, t.M2, t.c_m2) + ext2(t.N / t.N2, t.c_n1, t.N2, t.c_n2) + 1 + xc, osz, "TC C", i);
         if (t.C2) c.range(t.C2, ext2(t.M / t.M2, t.d_m1, t.M2, t.d_m2) + ext2(t.N / t.N2, t.d_n1, t.N2, t.d_n2) + 1 + xd, osz, "TC C2", i);
         c.range(t.active, 1, 4, "TC active", i);
@@ -223,7 +225,7 @@ std::string Program::validate() const {
         }
         auto ksz = [](int k) { return k == 0 ? 8 : k == 3 ? 2 : 4; };
         c.range(t.src, se, ksz(t.src_kind), "relayout src", i);
-        c.range(t.dst, de + (t.x3 ? 2 * t.kseg : 0), ksz(t.dst_kind), "relayout dst", i);
+        c.range(t.dst, de + (t.x3 ? t.kseg : 0), ksz(t.dst_kind), "relayout dst", i);
     }
     for (size_t i = 0; i < steps.size(); ++i) {
         const Step& s = steps[i];
@@ -303,6 +305,19 @@ void Program::qr_step(std::vector<QRTask>& ts) {
     max_qr_m = std::max(max_qr_m, mm);
     steps.push_back(s);
     ts.clear();
+}
+
+size_t Program::lp_alloc(size_t elems, int esz, bool split) {
+    const size_t off = arena_alloc((split ? 2 : 1) * elems * (size_t)esz);
+    if (split) planes[off] = (long long)elems;
+    return off;
+}
+
+long long Program::plane_of(size_t byte_off) const {
+    auto it = planes.find(byte_off);
+    if (it != planes.end()) return it->second;
+    if (parent && byte_off < split) return parent->plane_of(byte_off);  // the lattice's own buffers
+    throw std::logic_error("internal: split operand without a second plane");
 }
 
 void Program::dot_step(std::vector<DotTask>& ts, bool normalise) {
@@ -691,11 +706,20 @@ void Program::relocate(char* base, size_t split, char* base2) {
 cudaError_t Program::encode_maps(char* base, size_t split, char* base2) {
     for (size_t i = 0; i < tcs.size(); ++i) {
         const TCSpec& sp = tcspec[i];
+        const int esz = sp.kind == 0 ? 4 : 2;
         cudaError_t e = tc_make_map(&tcs[i].map_a, reloc_ptr(sp.a_off, base, split, base2), sp.kind, sp.a_rows, sp.K,
                                     sp.a_ld, 128);
         if (e != cudaSuccess) return e;
         e = tc_make_map(&tcs[i].map_b, reloc_ptr(sp.b_off, base, split, base2), sp.kind, sp.b_rows, sp.K, sp.b_ld, sp.bn);
         if (e != cudaSuccess) return e;
+        if (tcs[i].nseg == 3) {  // the lo planes
+            e = tc_make_map(&tcs[i].map_a2, reloc_ptr(sp.a_off, base, split, base2) + sp.a_pl * esz, sp.kind, sp.a_rows,
+                            sp.K, sp.a_ld, 128);
+            if (e != cudaSuccess) return e;
+            e = tc_make_map(&tcs[i].map_b2, reloc_ptr(sp.b_off, base, split, base2) + sp.b_pl * esz, sp.kind, sp.b_rows,
+                            sp.K, sp.b_ld, sp.bn);
+            if (e != cudaSuccess) return e;
+        }
     }
     return cudaSuccess;
 }
@@ -711,6 +735,11 @@ cudaError_t Program::tc_retile(size_t si, int bn, int depth, char* base, size_t 
         cudaError_t e = tc_make_map(&tcs[k].map_b, reloc_ptr(sp.b_off, base, split, base2), sp.kind, sp.b_rows, sp.K,
                                     sp.b_ld, bn);
         if (e != cudaSuccess) return e;
+        if (tcs[k].nseg == 3) {
+            e = tc_make_map(&tcs[k].map_b2, reloc_ptr(sp.b_off, base, split, base2) + sp.b_pl * (sp.kind == 0 ? 4 : 2),
+                            sp.kind, sp.b_rows, sp.K, sp.b_ld, bn);
+            if (e != cudaSuccess) return e;
+        }
         tiles = std::max(tiles, ((tcs[k].M + 127) / 128) * ((tcs[k].N + bn - 1) / bn));
     }
     s.aux = bn;
@@ -929,9 +958,14 @@ void Program::step_work(const Step& s, double* flops, double* bytes, long long* 
                 const TCTask& t = tcs[s.first + i];
                 const TCSpec& sp = tcspec[s.first + i];
                 const int esz = sp.kind == 0 ? 4 : 2, osz = t.out_kind == 2 ? 2 : t.out_kind == 3 ? 8 : 4;
-                f += 2.0 * (double)t.M * t.N * t.K;
-                b += ((double)t.M * t.K + (double)t.N * t.K) * esz + (double)t.M * t.N * osz * (t.C2 ? 2 : 1);
-                mm = std::max(mm, (long long)t.M); mn = std::max(mn, (long long)t.N); mk = std::max(mk, (long long)t.K);
+                // split operands: three K-segments of MMA work over two planes of each operand;
+                // a split result is written as two planes
+                const int nseg = t.nseg == 3 ? 3 : 1, planes_in = nseg == 3 ? 2 : 1;
+                const int parts = (t.x3 & 3 ? 2 : 1) + (t.C2 ? ((t.x3 >> 2) & 3 ? 2 : 1) : 0);
+                f += 2.0 * (double)t.M * t.N * t.K * nseg;
+                b += ((double)t.M * t.K + (double)t.N * t.K) * esz * planes_in + (double)t.M * t.N * osz * parts;
+                mm = std::max(mm, (long long)t.M); mn = std::max(mn, (long long)t.N);
+                mk = std::max(mk, (long long)t.K * nseg);
             }
             break;
         default:

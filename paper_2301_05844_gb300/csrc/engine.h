@@ -36,6 +36,7 @@ struct OverlapSpec {
 struct TCSpec {
     size_t a_off = 0, b_off = 0;          // byte offsets
     long long a_rows = 1, b_rows = 1, K = 1, a_ld = 1, b_ld = 1;
+    long long a_pl = 0, b_pl = 0;         // split operands: elements from the hi plane to the lo plane
     int kind = 0, bn = 32;
 };
 
@@ -87,6 +88,11 @@ struct Program {
     size_t split = (size_t)-1;
 
     size_t arena_alloc(size_t bytes);
+    // Low-precision operand buffer of `elems` elements of esz bytes; a split operand (hi and lo
+    // planes) takes two planes of that size and is recorded in `planes`.
+    std::map<size_t, long long> planes;  // byte offset of a split buffer -> elements per plane
+    size_t lp_alloc(size_t elems, int esz, bool split);
+    long long plane_of(size_t byte_off) const;
     // Check, before any launch, that every operand range of every task lies inside one
     // arena buffer.  Returns an empty string or a description of the first violation.
     std::string validate() const;

@@ -271,9 +271,9 @@ __device__ __forceinline__ void store_kind(void* p, long long i, int kind, doubl
     store_kind(p, 2 * i + 1, kind, v.y);
 }
 // Split operand (x3 != 0; kind 4 TF32, kind 3 BF16): hi = r(v), lo = r(v - hi), r the rounding
-// of the kind applied to the FP32 rounding of v, written to the three K-segments of the row,
-// kseg elements apart: [hi|lo|hi] for an A operand (x3 = 1), [hi|hi|lo] for a B operand
-// (x3 = 2), so that a GEMM over 3K forms A_hi B_hi + A_lo B_hi + A_hi B_lo.
+// of the kind applied to the FP32 rounding of v; hi goes to the first plane, lo kseg elements
+// further (the second plane).  A consumer GEMM reads them as the K-segments (hi, lo, hi) of an A
+// operand or (hi, hi, lo) of a B operand, forming A_hi B_hi + A_lo B_hi + A_hi B_lo.
 __device__ __forceinline__ void store_split(void* p, long long i, int kind, double v, int x3, long long kseg) {
     if (!x3) {
         store_kind(p, i, kind, v);
@@ -285,15 +285,13 @@ __device__ __forceinline__ void store_split(void* p, long long i, int kind, doub
         const __nv_bfloat16 lb = __float2bfloat16_rn(f32 - __bfloat162float(hb));  // f32 - hi is exact
         __nv_bfloat16* b = (__nv_bfloat16*)p;
         b[i] = hb;
-        b[i + kseg] = x3 == 1 ? lb : hb;
-        b[i + 2 * kseg] = x3 == 1 ? hb : lb;
+        b[i + kseg] = lb;
         return;
     }
     const float hi = tf32_round(f32), lo = tf32_round(f32 - hi);  // f32 - hi is exact
     float* f = (float*)p;
     f[i] = hi;
-    f[i + kseg] = x3 == 1 ? lo : hi;
-    f[i + 2 * kseg] = x3 == 1 ? hi : lo;
+    f[i + kseg] = lo;
 }
 __device__ __forceinline__ void store_split(void* p, long long i, int kind, double2 v, int x3, long long kseg) {
     store_split(p, 2 * i, kind, v.x, x3, kseg);

@@ -202,7 +202,7 @@ int plan_column_sweeps(bbp_lattice* L, Program& pr, std::vector<ColumnSweep>& cs
     const int ss = L->ss;
     const MixCtx& cx = L->cx;
     auto pad = [&](long long x) { return padded(cx, x); };
-    auto lp_alloc = [&](size_t elems) { return pr.arena_alloc(elems * (size_t)cx.esz); };
+    auto lp_alloc = [&](size_t elems) { return pr.lp_alloc(elems, cx.esz, cx.x3); };
     auto elem_alloc = [&](size_t elems) { return pr.arena_alloc(elems * (size_t)ss) / (size_t)ss; };
     for (auto& s : cs) {
         const int H = (s.dir == DIR_LEFT || s.dir == DIR_RIGHT) ? s.bh : s.bw;
@@ -372,12 +372,12 @@ int plan_column_sweeps(bbp_lattice* L, Program& pr, std::vector<ColumnSweep>& cs
                 r.d[0] = v.b; r.d[1] = v.k; r.d[2] = v.a; r.d[3] = 1;
                 r.ss[0] = v.sb; r.ss[1] = v.sk; r.ss[2] = v.sa;
                 r.ds[0] = (long long)v.k * pad(v.a); r.ds[1] = pad(v.a); r.ds[2] = 1;
-                r.x3 = cx.x3 ? 2 : 0; r.kseg = v.a;
+                r.x3 = cx.x3 ? 1 : 0; r.kseg = cx.x3 ? pr.plane_of(dst) : 0;
             } else {  // XR[x][p][pad x2]  (A operand of K2r)
                 r.d[0] = v.a; r.d[1] = v.k; r.d[2] = v.b; r.d[3] = 1;
                 r.ss[0] = v.sa; r.ss[1] = v.sk; r.ss[2] = v.sb;
                 r.ds[0] = (long long)v.k * pad(v.b); r.ds[1] = pad(v.b); r.ds[2] = 1;
-                r.x3 = cx.x3 ? 1 : 0; r.kseg = v.b;
+                r.x3 = cx.x3 ? 1 : 0; r.kseg = cx.x3 ? pr.plane_of(dst) : 0;
             }
             rt.push_back(r);
         };
@@ -391,12 +391,12 @@ int plan_column_sweeps(bbp_lattice* L, Program& pr, std::vector<ColumnSweep>& cs
                 r.d[0] = o.w2; r.d[1] = o.q; r.d[2] = o.w; r.d[3] = o.p;
                 r.ss[0] = o.sw2; r.ss[1] = o.sq; r.ss[2] = o.sw; r.ss[3] = o.sp;
                 r.ds[0] = (long long)o.q * pad((long long)o.w * o.p); r.ds[1] = pad((long long)o.w * o.p); r.ds[2] = o.p; r.ds[3] = 1;
-                r.x3 = cx.x3 ? 2 : 0; r.kseg = (long long)o.w * o.p;  // B operand of K3
+                r.x3 = cx.x3 ? 1 : 0; r.kseg = cx.x3 ? pr.plane_of(dst) : 0;  // B operand of K3
             } else {  // OR[w][q][pad(p w2)]
                 r.d[0] = o.w; r.d[1] = o.q; r.d[2] = o.p; r.d[3] = o.w2;
                 r.ss[0] = o.sw; r.ss[1] = o.sq; r.ss[2] = o.sp; r.ss[3] = o.sw2;
                 r.ds[0] = (long long)o.q * pad((long long)o.p * o.w2); r.ds[1] = pad((long long)o.p * o.w2); r.ds[2] = o.w2; r.ds[3] = 1;
-                r.x3 = cx.x3 ? 2 : 0; r.kseg = (long long)o.p * o.w2;  // B operand of K3r
+                r.x3 = cx.x3 ? 1 : 0; r.kseg = cx.x3 ? pr.plane_of(dst) : 0;  // B operand of K3r
             }
             rt.push_back(r);
         };
@@ -714,16 +714,17 @@ int bbp::plan_lattice(const bbp_lattice_desc* desc, bbp_lattice** out) {
         cx.tco = cx.tck == 0 ? 1 : 2;
         cx.qr_f32 = desc->keep_fp64 == 0;
         pr.tc_kind = cx.tck;
-        L->one_lp = pr.arena_alloc(16);
-        L->one_lp_b = cx.x3 ? pr.arena_alloc(16) : L->one_lp;
+        // the constant 1 as a K = 1 operand row (16 bytes; a split one has a zero lo plane)
+        L->one_lp = pr.lp_alloc(16 / cx.esz, cx.esz, cx.x3);
+        L->one_lp_b = L->one_lp;
         const size_t errw = pr.arena_alloc(sizeof(int));
         L->d_tcerr = (int*)(uintptr_t)errw;
         for (int t = 0; t < L->ntens; ++t) {
             std::array<size_t, 4> el{}, er{};
             for (int dir = 0; dir < 4; ++dir) {
                 const View4 o = L->E_view(t, dir);
-                el[dir] = pr.arena_alloc((size_t)o.q * o.w2 * padded(cx, (long long)o.w * o.p) * cx.esz);
-                er[dir] = pr.arena_alloc((size_t)o.w * o.q * padded(cx, (long long)o.p * o.w2) * cx.esz);
+                el[dir] = pr.lp_alloc((size_t)o.q * o.w2 * padded(cx, (long long)o.w * o.p), cx.esz, cx.x3);
+                er[dir] = pr.lp_alloc((size_t)o.w * o.q * padded(cx, (long long)o.p * o.w2), cx.esz, cx.x3);
             }
             L->EL_off.push_back(el);
             L->ER_off.push_back(er);
@@ -810,19 +811,13 @@ int bbp_create_lattice(const bbp_lattice_desc* desc, bbp_lattice** out) try {
         e = cudaMemcpyAsync(base + L->one_off * L->ss, one, L->ss, cudaMemcpyHostToDevice, L->stream);
     }
     if (e == cudaSuccess && L->mixed) {
+        // the constant 1 as a K = 1 operand row; a split operand's lo plane stays zero (the
+        // arena was cleared above)
         static const float one_f[4] = {1.0f, 0.0f, 0.0f, 0.0f};
         static const unsigned short one_b[8] = {0x3F80, 0, 0, 0, 0, 0, 0, 0};
-        // split rows of the constant 1 (K = 1): A [hi|lo|hi] = [1|0|1], B [hi|hi|lo] = [1|1|0]
-        static const float one_xa[4] = {1.0f, 0.0f, 1.0f, 0.0f}, one_xb[4] = {1.0f, 1.0f, 0.0f, 0.0f};
-        static const unsigned short one_bxa[8] = {0x3F80, 0, 0x3F80, 0, 0, 0, 0, 0};
-        static const unsigned short one_bxb[8] = {0x3F80, 0x3F80, 0, 0, 0, 0, 0, 0};
         const bool bf = L->cx.tck == 1;
-        const void* src = L->cx.x3 ? (bf ? (const void*)one_bxa : (const void*)one_xa)
-                                   : (bf ? (const void*)one_b : (const void*)one_f);
-        e = cudaMemcpyAsync(base + L->one_lp, src, 16, cudaMemcpyHostToDevice, L->stream);
-        if (e == cudaSuccess && L->cx.x3)
-            e = cudaMemcpyAsync(base + L->one_lp_b, bf ? (const void*)one_bxb : (const void*)one_xb, 16,
-                                cudaMemcpyHostToDevice, L->stream);
+        e = cudaMemcpyAsync(base + L->one_lp, bf ? (const void*)one_b : (const void*)one_f, 16, cudaMemcpyHostToDevice,
+                            L->stream);
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(L->stream);
     if (e != cudaSuccess) {
@@ -936,14 +931,14 @@ int bbp_set_tensors(bbp_lattice* L, const void* data, int on_device) try {
                         r.d[0] = o.w2; r.d[1] = o.q; r.d[2] = o.w; r.d[3] = o.p;
                         r.ss[0] = o.sw2; r.ss[1] = o.sq; r.ss[2] = o.sw; r.ss[3] = o.sp;
                         r.ds[0] = (long long)o.q * wp; r.ds[1] = wp; r.ds[2] = o.p; r.ds[3] = 1;
-                        r.x3 = cx.x3 ? 2 : 0; r.kseg = (long long)o.w * o.p;  // B operand of K3
+                        r.x3 = cx.x3 ? 1 : 0; r.kseg = cx.x3 ? L->sweep.plane_of(L->EL_off[t][dir]) : 0;
                     } else {
                         r.dst = base + L->ER_off[t][dir];
                         const long long pw = padded(cx, (long long)o.p * o.w2);
                         r.d[0] = o.w; r.d[1] = o.q; r.d[2] = o.p; r.d[3] = o.w2;
                         r.ss[0] = o.sw; r.ss[1] = o.sq; r.ss[2] = o.sp; r.ss[3] = o.sw2;
                         r.ds[0] = (long long)o.q * pw; r.ds[1] = pw; r.ds[2] = o.w2; r.ds[3] = 1;
-                        r.x3 = cx.x3 ? 2 : 0; r.kseg = (long long)o.p * o.w2;  // B operand of K3r
+                        r.x3 = cx.x3 ? 1 : 0; r.kseg = cx.x3 ? L->sweep.plane_of(L->ER_off[t][dir]) : 0;
                     }
                     mx = std::max(mx, (long long)o.w * o.p * o.q * o.w2);
                     rt.push_back(r);
@@ -1224,7 +1219,7 @@ int bbp_autotune(bbp_lattice* L, int reps, double* ms_before, double* ms_after, 
             int nmax = 1, kmax = 1;
             for (int i = 0; i < s0.count; ++i) {
                 nmax = std::max(nmax, pr.tcs[s0.first + i].N);
-                kmax = std::max(kmax, (pr.tcs[s0.first + i].K + ek - 1) / ek);
+                kmax = std::max(kmax, (pr.tcs[s0.first + i].K + ek - 1) / ek * (pr.tcs[s0.first + i].nseg == 3 ? 3 : 1));
             }
             const int bn0 = s0.aux, d0 = (s0.aux2 >> 8) & 0xFF, k0 = std::max(1, (s0.aux2 >> 16) & 0xFF);
             int best_bn = bn0, best_d = d0, best_k = k0;

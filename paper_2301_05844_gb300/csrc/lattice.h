@@ -80,7 +80,8 @@ struct bbp_lattice {
     bbp::MixCtx cx;
     std::vector<std::array<size_t, 4>> EL_off, ER_off;  // per tensor and frame direction (bytes)
     size_t one_lp = 0;                      // low-precision constant 1 (bytes), A-operand form
-    size_t one_lp_b = 0;                    // the same as a B operand (differs for split TF32 rows)
+    size_t one_lp_b = 0;                    // the same as a B operand (the same buffer: a split operand's
+                                            // planes serve either role)
     int* d_tcerr = nullptr;
     char* arena = nullptr;
     size_t arena_bytes = 0;

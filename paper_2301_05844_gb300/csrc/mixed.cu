@@ -1,9 +1,10 @@
 // Tensor-core (TF32 / BF16) zip-up fit: the stages of App. A's fit with every
 // contraction of Eq. (update) and of the A/B recurrences on the tcgen05 GEMM, FP32
-// accumulation in TMEM, and the QR/LQ truncation, normalisation and generator in
-// FP64 exactly as on the FP64 path.
+// accumulation in TMEM, the QR/LQ truncation in FP32 (or FP64) arithmetic, and the
+// normalisation and generator in FP64 exactly as on the FP64 path.
 //
-// Operand layouts (low precision, every row padded to 16 bytes):
+// Operand layouts (low precision, every row padded to 16 bytes; a split operand is two such
+// planes, hi and lo, one plane apart):
 //   X   : XL[x2][p][pad x]        XR[x][p][pad x2]
 //   O   : OL[w2][q][pad(w p)]     OR[w][q][pad(p w2)]
 //   env : ER[y][w][pad x]         EK[y][pad(w x)]      (A and B envs, both forms)
@@ -23,12 +24,9 @@
 
 namespace bbp {
 
-// Row pitch of a K-major operand with K = x: three K-segments per row for split TF32
-// operands, padded to 16 bytes.
-long long padded(const MixCtx& cx, long long x) {
-    const long long k = cx.x3 ? 3 * x : x;
-    return (k + cx.pe - 1) / cx.pe * cx.pe;
-}
+// Row pitch of a K-major operand with K = x, padded to 16 bytes (a split operand has two
+// planes of such rows, hi and lo).
+long long padded(const MixCtx& cx, long long x) { return (x + cx.pe - 1) / cx.pe * cx.pe; }
 
 void Program::tc_step(std::vector<TCTask>& ts, std::vector<TCSpec>& sp, int kind) {
     if (ts.empty()) return;
@@ -41,7 +39,7 @@ void Program::tc_step(std::vector<TCTask>& ts, std::vector<TCSpec>& sp, int kind
         sp[i].bn = bn;
         sp[i].kind = kind;
         tiles = std::max(tiles, ((ts[i].M + 127) / 128) * ((ts[i].N + bn - 1) / bn));
-        kmax = std::max(kmax, (ts[i].K + ek - 1) / ek);
+        kmax = std::max(kmax, (ts[i].K + ek - 1) / ek * (ts[i].nseg == 3 ? 3 : 1));
     }
     Step s;
     s.kind = ST_TC;
@@ -78,8 +76,9 @@ struct TB {  // tasks of one tensor-core step
     std::vector<TCSpec> sp;
 };
 
-// Role of a low-precision destination in its consumer GEMM (split TF32 rows: A [hi|lo|hi],
-// B [hi|hi|lo]); the segment length is the consumer's K.
+// A low-precision destination that is a split operand (hi and lo planes) of a later GEMM; the
+// consumer decides the K-segment order (A: hi, lo, hi; B: hi, hi, lo), so either role reads the
+// same two planes.  The argument is the consumer's K (documentation of the shape only).
 constexpr int ROLE_A = 1, ROLE_B = 2;
 struct Dst {
     int role = 0;
@@ -88,20 +87,20 @@ struct Dst {
 
 // C = A B^T with A (a_rows x K, leading dim a_ld) and B (b_rows x K, b_ld), both K-major;
 // result element (m, n), m = m1*M2 + m2, n = n1*N2 + n2, goes to C (and C2).  With split
-// TF32 operands the GEMM runs over the three K-segments of every row (3K).
+// operands the GEMM runs three K-segments over the hi and lo planes of A and B.
 void add(Program& pr, const MixCtx& cx, TB& tb, size_t a_off, long long a_rows, long long K, long long a_ld,
          size_t b_off, long long b_rows, long long b_ld, int M2, int N2, void* C, long long cm1, long long cm2,
          long long cn1, long long cn2, void* C2, long long dm1, long long dm2, long long dn1, long long dn2,
          int out_kind, const int* active, double alg_flops, Dst dc = Dst(), Dst dd = Dst()) {
-    if (cx.x3) K *= 3;
     TCTask t{};
     t.M = (int)a_rows;
     t.N = (int)b_rows;
     t.K = (int)K;
-    if (cx.x3) {
-        t.x3 = dc.role | (dd.role << 2);
-        t.kseg = dc.kseg;
-        t.kseg2 = dd.kseg;
+    t.nseg = cx.x3 ? 3 : 1;
+    if (cx.x3) {  // split destinations: hi plane, lo plane one plane further
+        t.x3 = (dc.role ? 1 : 0) | ((dd.role ? 1 : 0) << 2);
+        t.kseg = dc.role ? pr.plane_of((size_t)C) : 0;
+        t.kseg2 = dd.role ? pr.plane_of((size_t)C2) : 0;
     }
     t.M2 = M2;
     t.N2 = N2;
@@ -115,6 +114,10 @@ void add(Program& pr, const MixCtx& cx, TB& tb, size_t a_off, long long a_rows, 
     TCSpec s;
     s.a_off = a_off; s.a_rows = a_rows; s.K = K; s.a_ld = a_ld;
     s.b_off = b_off; s.b_rows = b_rows; s.b_ld = b_ld;
+    if (cx.x3) {
+        s.a_pl = pr.plane_of(a_off);
+        s.b_pl = pr.plane_of(b_off);
+    }
     tb.ts.push_back(t);
     tb.sp.push_back(s);
     pr.count_flops(active, alg_flops, false);
@@ -195,7 +198,8 @@ void rl(Program& pr, const MixCtx& cx, TB& tb, const FitSpec& f, int i, int stag
     }
 }
 
-QRTask qr_mixed(const MixCtx& cx, const FitSpec& f, int i, bool lq, size_t loss_byte, const int* act) {
+QRTask qr_mixed(const Program& pr, const MixCtx& cx, const FitSpec& f, int i, bool lq, size_t loss_byte,
+                const int* act) {
     const long long y = f.ybond[i], y2 = f.ybond[i + 1], q = f.O[i].q;
     QRTask t{};
     t.in = P(f.mx.Ytf);
@@ -210,14 +214,14 @@ QRTask qr_mixed(const MixCtx& cx, const FitSpec& f, int i, bool lq, size_t loss_
         t.in_rs = y2; t.in_cs = 1; t.out_rs = y2; t.out_cs = 1; t.conj_io = 0;
         t.out2 = P(f.mx.YT[i]);
         t.out2_M2 = 1; t.out2_rs = 1; t.out2_rs2 = 0; t.out2_cs = padded(cx, y * q);   // YT[y2][pad(y q)]
-        t.out2_x3 = cx.x3 ? ROLE_A : 0; t.out2_kseg = y * q;
+        t.out2_x3 = cx.x3 ? 1 : 0; t.out2_kseg = cx.x3 ? pr.plane_of(f.mx.YT[i]) : 0;
     } else {
         t.m = (int)(q * y2); t.n = (int)y;
         t.in_rs = 1; t.in_cs = q * y2; t.out_rs = 1; t.out_cs = q * y2; t.conj_io = 1;
         t.out2 = P(f.mx.YS[i]);
         // row i = (q, y2) of the LQ matrix goes to YS[y][pad(y2 q)]
         t.out2_M2 = (int)y2; t.out2_rs = 1; t.out2_rs2 = q; t.out2_cs = padded(cx, q * y2);
-        t.out2_x3 = cx.x3 ? ROLE_A : 0; t.out2_kseg = q * y2;
+        t.out2_x3 = cx.x3 ? 1 : 0; t.out2_kseg = cx.x3 ? pr.plane_of(f.mx.YS[i]) : 0;
     }
     return t;
 }
@@ -259,8 +263,8 @@ void emit_fits_mixed(Program& pr, const MixCtx& cx, std::vector<FitSpec*>& fits,
                 r.d[0] = (int)y; r.d[1] = (int)q; r.d[2] = (int)y2; r.d[3] = 1;
                 r.ss[0] = q * y2; r.ss[1] = y2; r.ss[2] = 1;
                 r.ds[0] = padded(cx, q * y2); r.ds[1] = 1; r.ds[2] = q;  // YS[y][pad(y2 q)]
-                r.x3 = cx.x3 ? ROLE_A : 0;
-                r.kseg = q * y2;
+                r.x3 = cx.x3 ? 1 : 0;
+                r.kseg = cx.x3 ? pr.plane_of(f->mx.YS[i]) : 0;
                 r.src_kind = 0;
                 r.dst_kind = cx.lpk;
                 rl_.push_back(r);
@@ -294,7 +298,7 @@ void emit_fits_mixed(Program& pr, const MixCtx& cx, std::vector<FitSpec*>& fits,
             for (auto* f : fits)
                 if (k <= f->n() - 2) {
                     const int nu = 2 * (f->n() - 1);
-                    qt.push_back(qr_mixed(cx, *f, k, false, f->losses + (size_t)k * sizeof(double),
+                    qt.push_back(qr_mixed(pr, cx, *f, k, false, f->losses + (size_t)k * sizeof(double),
                                           (const int*)P(f->active)));
                 }
             pr.qr_step(qt);
@@ -314,7 +318,7 @@ void emit_fits_mixed(Program& pr, const MixCtx& cx, std::vector<FitSpec*>& fits,
                 const int i = f->n() - 1 - k;
                 if (i >= 1) {
                     const int nu = 2 * (f->n() - 1);
-                    qt.push_back(qr_mixed(cx, *f, i, true,
+                    qt.push_back(qr_mixed(pr, cx, *f, i, true,
                                           f->losses + (size_t)((f->n() - 1) + k) * sizeof(double),
                                           (const int*)P(f->active)));
                 }

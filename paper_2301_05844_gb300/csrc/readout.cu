@@ -263,6 +263,8 @@ extern "C" int bbp_expect(bbp_lattice* L, const bbp_term* terms, int n_terms, do
     pr.cplx = L->cplx;
     const size_t split = (L->arena_bytes + 255) & ~(size_t)255;
     pr.arena_used = split;
+    pr.parent = &L->sweep;  // buffers below `split` are the lattice's
+    pr.split = split;
     auto elem_alloc = [&](size_t elems) { return pr.arena_alloc(elems * (size_t)ss) / (size_t)ss; };
     std::vector<ColumnSweep> cs;
     for (auto& R : regions) {

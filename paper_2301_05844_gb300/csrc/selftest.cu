@@ -46,6 +46,7 @@ static int selftest_gemm(int M, int N, int K, int prec, const float* A, const fl
     if (!e) e = tc_make_map(&t.map_a, da, kind, M, K, ld, 128);
     if (!e) e = tc_make_map(&t.map_b, db, kind, N, K, ld, bn);
     t.M = M; t.N = N; t.K = K; t.M2 = M; t.N2 = N; t.out_kind = 0;
+    t.nseg = 1;
     t.c_m1 = 0; t.c_m2 = N; t.c_n1 = 0; t.c_n2 = 1;
     t.C = dc; t.C2 = nullptr; t.active = nullptr; t.alpha = 1.0f;
     if (!e) e = cudaMemcpy(dt, &t, sizeof(t), cudaMemcpyHostToDevice);

@@ -196,29 +196,26 @@ constexpr int EC = 64;  // epilogue chunk (columns)
 constexpr int TROWS = BM + BM / 32;
 __device__ __forceinline__ int trow(int r) { return r + (r >> 5); }
 
-// Split destination (x3 = 1: A rows [hi|lo|hi], 2: B rows [hi|hi|lo], segments kseg
-// elements apart): hi = r(x), lo = r(x - hi), r the rounding of the element kind (TF32 for
-// kind 1, BF16 for kind 2); x - hi is exact in FP32 for both.
-__device__ __forceinline__ void store_split1(void* out, long long o, int kind, float x, int x3, long long kseg) {
+// Split destination (x3 != 0): two planes kseg elements apart, hi = r(x) in the first and
+// lo = r(x - hi) in the second, r the rounding of the element kind (TF32 for kind 1, BF16 for
+// kind 2); x - hi is exact in FP32 for both.  A consumer GEMM reads the planes of an A operand
+// in the K-segment order (hi, lo, hi) and those of a B operand as (hi, hi, lo).
+__device__ __forceinline__ void store_split1(void* out, long long o, int kind, float x, long long kseg) {
     if (kind == 2) {
         const __nv_bfloat16 hb = __float2bfloat16_rn(x);
         const __nv_bfloat16 lb = __float2bfloat16_rn(x - __bfloat162float(hb));
         __nv_bfloat16* b = (__nv_bfloat16*)out;
         b[o] = hb;
-        b[o + kseg] = x3 == 1 ? lb : hb;
-        b[o + 2 * kseg] = x3 == 1 ? hb : lb;
+        b[o + kseg] = lb;
         return;
     }
     float* f = (float*)out;
     const float hi = round_tf32(x), lo = round_tf32(x - hi);
     f[o] = hi;
-    f[o + kseg] = x3 == 1 ? lo : hi;
-    f[o + 2 * kseg] = x3 == 1 ? hi : lo;
+    f[o + kseg] = lo;
 }
-// 16 bytes per segment: 4 TF32 elements (kind 1) or 8 BF16 elements (kind 2)
-__device__ __forceinline__ void store_split_vec(void* out, long long o, int kind, const float* x, int x3,
-                                                long long kseg) {
-    uint4 H, Lo;
+// 16 bytes per plane: 4 TF32 elements (kind 1) or 8 BF16 elements (kind 2)
+__device__ __forceinline__ void store_split_vec(void* out, long long o, int kind, const float* x, long long kseg) {
     if (kind == 2) {
         __nv_bfloat162 h[4], l[4];
 #pragma unroll
@@ -227,12 +224,9 @@ __device__ __forceinline__ void store_split_vec(void* out, long long o, int kind
             const float2 hf = __bfloat1622float2(h[j]);
             l[j] = __floats2bfloat162_rn(x[2 * j] - hf.x, x[2 * j + 1] - hf.y);
         }
-        H = *(const uint4*)h;
-        Lo = *(const uint4*)l;
         __nv_bfloat16* b = (__nv_bfloat16*)out;
-        *(uint4*)(b + o) = H;
-        *(uint4*)(b + o + kseg) = x3 == 1 ? Lo : H;
-        *(uint4*)(b + o + 2 * kseg) = x3 == 1 ? H : Lo;
+        *(uint4*)(b + o) = *(const uint4*)h;
+        *(uint4*)(b + o + kseg) = *(const uint4*)l;
         return;
     }
     float hi[4], lo[4];
@@ -242,16 +236,15 @@ __device__ __forceinline__ void store_split_vec(void* out, long long o, int kind
         lo[j] = round_tf32(x[j] - hi[j]);
     }
     float* f = (float*)out;
-    const float4 Hf = make_float4(hi[0], hi[1], hi[2], hi[3]), Lf = make_float4(lo[0], lo[1], lo[2], lo[3]);
-    *(float4*)(f + o) = Hf;
-    *(float4*)(f + o + kseg) = x3 == 1 ? Lf : Hf;
-    *(float4*)(f + o + 2 * kseg) = x3 == 1 ? Hf : Lf;
+    *(float4*)(f + o) = make_float4(hi[0], hi[1], hi[2], hi[3]);
+    *(float4*)(f + o + kseg) = make_float4(lo[0], lo[1], lo[2], lo[3]);
 }
 
-// The epilogue runs on the 384 threads of twelve epilogue warps (tid = 0..383): eight of them
-// drain the TMEM accumulator into the staged tile (two per quarter of the TMEM lanes), all
-// twelve write the staged tile out.  They synchronise among themselves on named barrier 1.
-constexpr int EPI_THREADS = 384;
+// The epilogue runs on the EPI_THREADS threads of EPI_THREADS / 32 epilogue warps: eight of
+// them drain the TMEM accumulator into the staged tile (two per quarter of the TMEM lanes), all
+// of them write the staged tile out (the stores are latency-bound, so more warps hide more of
+// it).  They synchronise among themselves on named barrier 1.
+constexpr int EPI_THREADS = 512;
 constexpr int DRAIN_WARPS = 8;
 __device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, %0;" ::"n"(EPI_THREADS) : "memory"); }
 // the same barrier, returning whether every epilogue thread passed true
@@ -283,7 +276,7 @@ __device__ __forceinline__ void epilogue_dest(const float* tile, long long* roff
     epi_sync();
     const int esz = out_esz(kind), VW = 16 / esz;
     const uintptr_t base = (uintptr_t)out;
-    // a split destination vectorises only if every segment start stays 16-byte aligned
+    // a split destination vectorises only if its second plane starts 16-byte aligned as well
     const bool segs_aligned = !x3 || ((kseg * esz) & 15) == 0;
     float x[8];
     // fully regular destinations (below): every group of VW rows (columns) is one vector
@@ -305,7 +298,7 @@ __device__ __forceinline__ void epilogue_dest(const float* tile, long long* roff
                 const long long ro = roff[r];
                 for (int c = ln; c < ncols; c += 32) {
                     const float xv = tile[trow(r) * P + c] * alpha;
-                    if (x3) store_split1(out, ro + coff[c], kind, xv, x3, kseg);
+                    if (x3) store_split1(out, ro + coff[c], kind, xv, kseg);
                     else store_out(out, ro + coff[c], kind, xv);
                 }
             }
@@ -314,7 +307,7 @@ __device__ __forceinline__ void epilogue_dest(const float* tile, long long* roff
                 const long long co = coff[c];
                 for (int r = ln; r < rows; r += 32) {
                     const float xv = tile[trow(r) * P + c] * alpha;
-                    if (x3) store_split1(out, roff[r] + co, kind, xv, x3, kseg);
+                    if (x3) store_split1(out, roff[r] + co, kind, xv, kseg);
                     else store_out(out, roff[r] + co, kind, xv);
                 }
             }
@@ -333,13 +326,13 @@ __device__ __forceinline__ void epilogue_dest(const float* tile, long long* roff
 #pragma unroll
             for (int j = 0; j < 8; ++j)
                 if (j < VW) x[j] = tile[trow(r0 + j) * P + c] * alpha;
-            if (x3) store_split_vec(out, o, kind, x, x3, kseg);
+            if (x3) store_split_vec(out, o, kind, x, kseg);
             else store_vec(out, o, kind, x);
         }
         for (int it = tid; it < ncols * (rows - G * VW); it += EPI_THREADS) {
             const int c = it / (rows - G * VW), r = G * VW + it % (rows - G * VW);
             const float xv = tile[trow(r) * P + c] * alpha;
-            if (x3) store_split1(out, roff[r] + coff[c], kind, xv, x3, kseg);
+            if (x3) store_split1(out, roff[r] + coff[c], kind, xv, kseg);
             else store_out(out, roff[r] + coff[c], kind, xv);
         }
         return;
@@ -352,13 +345,13 @@ __device__ __forceinline__ void epilogue_dest(const float* tile, long long* roff
 #pragma unroll
             for (int j = 0; j < 8; ++j)
                 if (j < VW) x[j] = tile[trow(r) * P + c0 + j] * alpha;
-            if (x3) store_split_vec(out, o, kind, x, x3, kseg);
+            if (x3) store_split_vec(out, o, kind, x, kseg);
             else store_vec(out, o, kind, x);
         }
         for (int it = tid; it < rows * (ncols - G * VW); it += EPI_THREADS) {
             const int r = it / (ncols - G * VW), c = G * VW + it % (ncols - G * VW);
             const float xv = tile[trow(r) * P + c] * alpha;
-            if (x3) store_split1(out, roff[r] + coff[c], kind, xv, x3, kseg);
+            if (x3) store_split1(out, roff[r] + coff[c], kind, xv, kseg);
             else store_out(out, roff[r] + coff[c], kind, xv);
         }
         return;
@@ -380,14 +373,14 @@ __device__ __forceinline__ void epilogue_dest(const float* tile, long long* roff
 #pragma unroll
             for (int j = 0; j < 8; ++j)
                 if (j < VW) x[j] = tile[trow(r) * P + c0 + j] * alpha;
-            if (x3) store_split_vec(out, o, kind, x, x3, kseg);
+            if (x3) store_split_vec(out, o, kind, x, kseg);
             else store_vec(out, o, kind, x);
         }
         for (int it = tid; it < rows * ncols; it += EPI_THREADS) {  // lanes along a row
             const int r = it / ncols, c = it - r * ncols;
             if (is_vec(r, c - c % VW)) continue;
             const float xv = tile[trow(r) * P + c] * alpha;
-            if (x3) store_split1(out, roff[r] + coff[c], kind, xv, x3, kseg);
+            if (x3) store_split1(out, roff[r] + coff[c], kind, xv, kseg);
             else store_out(out, roff[r] + coff[c], kind, xv);
         }
     } else if (sm2 == 1) {
@@ -404,27 +397,27 @@ __device__ __forceinline__ void epilogue_dest(const float* tile, long long* roff
 #pragma unroll
             for (int j = 0; j < 8; ++j)
                 if (j < VW) x[j] = tile[trow(r0 + j) * P + c] * alpha;
-            if (x3) store_split_vec(out, o, kind, x, x3, kseg);
+            if (x3) store_split_vec(out, o, kind, x, kseg);
             else store_vec(out, o, kind, x);
         }
         for (int it = tid; it < rows * ncols; it += EPI_THREADS) {  // lanes down a column
             const int c = it / rows, r = it - c * rows;
             if (is_vec(r - r % VW, c)) continue;
             const float xv = tile[trow(r) * P + c] * alpha;
-            if (x3) store_split1(out, roff[r] + coff[c], kind, xv, x3, kseg);
+            if (x3) store_split1(out, roff[r] + coff[c], kind, xv, kseg);
             else store_out(out, roff[r] + coff[c], kind, xv);
         }
     } else {
         for (int it = tid; it < rows * ncols; it += EPI_THREADS) {
             const int c = it / rows, r = it - c * rows;
             const float xv = tile[trow(r) * P + c] * alpha;
-            if (x3) store_split1(out, roff[r] + coff[c], kind, xv, x3, kseg);
+            if (x3) store_split1(out, roff[r] + coff[c], kind, xv, kseg);
             else store_out(out, roff[r] + coff[c], kind, xv);
         }
     }
 }
 
-constexpr int EPI_WARPS = EPI_THREADS / 32;      // warps 2..13; 2..9 drain TMEM, two per lane quarter
+constexpr int EPI_WARPS = EPI_THREADS / 32;      // warps 2..; 2..9 drain TMEM, two per lane quarter
 constexpr int NTHREADS = 32 * (2 + EPI_WARPS);   // producer, MMA issuer, epilogue
 constexpr size_t EPI_BYTES = (size_t)TROWS * (EC + 1) * sizeof(float) + (size_t)(BM + EC) * sizeof(long long);
 
@@ -504,7 +497,13 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc_gemm(const TCTask* __restric
                 if (!item(w, t, m0, n0)) continue;
                 prefetch_map(&t->map_a);
                 prefetch_map(&t->map_b);
-                const int nk = (t->K + EK - 1) / EK, nst = (nk + ksub - 1) / ksub;
+                const int nk1 = (t->K + EK - 1) / EK;  // k-blocks of one K-segment
+                const int nseg = t->nseg == 3 ? 3 : 1;
+                if (nseg == 3) {
+                    prefetch_map(&t->map_a2);
+                    prefetch_map(&t->map_b2);
+                }
+                const int nk = nk1 * nseg, nst = (nk + ksub - 1) / ksub;
                 for (int ks = 0; ks < nst; ++ks, ++gks) {
                     const int s = gks % stages, r = gks / stages;
                     if (r > 0 && !mbar_wait(&empty[s], (r - 1) & 1, err)) {
@@ -514,9 +513,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc_gemm(const TCTask* __restric
                     const int na = min(ksub, nk - ks * ksub);
                     mbar_expect_tx(&full[s], (uint32_t)na * (A_BYTES + B_BYTES));
                     for (int a = 0; a < na; ++a) {
-                        const int kb = ks * ksub + a;
-                        tma_load_2d(sA + s * A_STAGE + a * A_BYTES, &t->map_a, &full[s], kb * EK, m0);
-                        tma_load_2d(sB + s * B_STAGE + a * B_BYTES, &t->map_b, &full[s], kb * EK, n0);
+                        // split operands: segment 0 = (A hi, B hi), 1 = (A lo, B hi), 2 = (A hi, B lo);
+                        // a segment's last k-block reads past K, which the maps fill with zeros
+                        const int kb = ks * ksub + a, seg = kb / nk1, kk = kb - seg * nk1;
+                        tma_load_2d(sA + s * A_STAGE + a * A_BYTES, seg == 1 ? &t->map_a2 : &t->map_a, &full[s], kk * EK, m0);
+                        tma_load_2d(sB + s * B_STAGE + a * B_BYTES, seg == 2 ? &t->map_b2 : &t->map_b, &full[s], kk * EK, n0);
                     }
                     issued = gks + 1;
                 }
@@ -536,7 +537,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc_gemm(const TCTask* __restric
                 if (u > 0 && !mbar_wait(&tempty[b], (u - 1) & 1, err)) break;
                 fence_after();
                 const uint32_t acc = tmem + (uint32_t)(b * (TCOLS / 2));
-                const int nk = (t->K + EK - 1) / EK, nst = (nk + ksub - 1) / ksub;
+                const int nk = ((t->K + EK - 1) / EK) * (t->nseg == 3 ? 3 : 1), nst = (nk + ksub - 1) / ksub;
                 for (int ks = 0; ks < nst; ++ks, ++gks) {
                     const int s = gks % stages, r = gks / stages;
                     if (!mbar_wait(&full[s], r & 1, err)) {

@@ -6,17 +6,21 @@
 
 namespace bbp {
 
-// C[m][n] = alpha * sum_k A[m][k] B[n][k]; A and B are read by TMA through the two
-// tensor maps (K innermost, rows outer, 128-byte swizzle, zero fill past the edges).
+// C[m][n] = alpha * sum_k A[m][k] B[n][k]; A and B are read by TMA through the tensor maps
+// (K innermost, rows outer, 128-byte swizzle, zero fill past the edges).  nseg = 3: split
+// operands, each stored as two planes (hi, lo) with a map per plane; the GEMM runs three
+// K-segments of K each, (A hi, B hi), (A lo, B hi), (A hi, B lo), accumulating
+// A_hi B_hi + A_lo B_hi + A_hi B_lo.  Otherwise one segment through map_a, map_b.
 // The result is written through the two-level map
 //   C[(m/M2)*c_m1 + (m%M2)*c_m2 + (n/N2)*c_n1 + (n%N2)*c_n2]
 // and, if C2 is set, also to C2 through (d_*).  out_kind: 0 FP32, 1 FP32 rounded to
-// TF32, 2 BF16, 3 FP64.  x3 (bits 0-1 for C, 2-3 for C2): the destination is a split TF32
-// operand whose rows hold K-segments [hi|lo|hi] (1, A operand) or [hi|hi|lo] (2, B
-// operand) kseg (kseg2) elements apart; the element offset is that of the first segment.
+// TF32, 2 BF16, 3 FP64.  x3 (bits 0-1 for C, 2-3 for C2): the destination is a split
+// operand, hi in the first plane and lo kseg (kseg2) elements further.
 struct TCTask {
     CUtensorMap map_a;
     CUtensorMap map_b;
+    CUtensorMap map_a2;  // second (lo) planes of split operands
+    CUtensorMap map_b2;
     int M, N, K, M2, N2, out_kind;
     long long c_m1, c_m2, c_n1, c_n2;
     long long d_m1, d_m2, d_n1, d_n2;
@@ -26,6 +30,7 @@ struct TCTask {
     float alpha;
     int x3;
     long long kseg, kseg2;
+    int nseg;  // 3 for split operands, otherwise 1
 };
 
 cudaError_t tc_prepare();

@@ -435,6 +435,103 @@ __global__ void __launch_bounds__(256) k_gcontract_small(const GTask* __restrict
     Cp[o] = t.accumulate ? add(Cp[o], r) : r;
 }
 
+// FP32-arithmetic contraction of real FP64 operands with a wider tile (the read-out closings
+// of tensor-core lattices): 128 x 64 outputs per CTA, K in chunks of 16, 256 threads each
+// owning 8 rows x 4 columns.  The staged operands are K-major in shared memory ([k][m], [k][n])
+// so that each thread reads its 8 A values and 4 B values as 16-byte vectors; the loaders walk
+// m (n) fastest and keep their (k1, k2) indices incrementally (no division per element).
+// Each chunk's 16 products are summed in FP32 and added into an unevaluated FP32 pair
+// (hi, lo) by TwoSum, as in k_gcontract; the result hi + lo is formed in FP64.
+__global__ void __launch_bounds__(256) k_gcontract_f32w(const GTask* __restrict__ tasks) {
+    const GTask& t = tasks[blockIdx.y];
+    if (t.active && *t.active == 0) return;
+    const int M = t.M1 * t.M2, N = t.N1 * t.N2, Kd = t.K1 * t.K2;
+    const int tilesM = (M + 127) >> 7, tilesN = (N + 63) >> 6;
+    const int tile = blockIdx.x;
+    if (tile >= tilesM * tilesN) return;
+    const int m0 = (tile % tilesM) << 7, n0 = (tile / tilesM) << 6;
+    __shared__ __align__(16) float As[16][128];
+    __shared__ __align__(16) float Bs[16][64];
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const double* __restrict__ Ap = (const double*)t.A;
+    const double* __restrict__ Bp = (const double*)t.B;
+    // A loader: row m0 + (tid & 127), k = lk + 2j (j = 0..7); B loader: column n0 + (tid & 63), k = lkb + 4j (j = 0..3)
+    const int am = m0 + (tid & 127), lk = tid >> 7;
+    const int bn = n0 + (tid & 63), lkb = tid >> 6;
+    const bool av = am < M, bv = bn < N;
+    const long long aoff = av ? (long long)(am / t.M2) * t.a_m1 + (long long)(am % t.M2) * t.a_m2 : 0;
+    const long long boff = bv ? (long long)(bn / t.N2) * t.b_n1 + (long long)(bn % t.N2) * t.b_n2 : 0;
+    int ak1 = lk / t.K2, ak2 = lk - ak1 * t.K2;     // (k1, k2) of this thread's next A element
+    int bk1 = lkb / t.K2, bk2 = lkb - bk1 * t.K2;  // and of its next B element
+    float acc[8][4], hi[8][4], lo[8][4];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = hi[i][j] = lo[i][j] = 0.0f;
+    for (int k0 = 0; k0 < Kd; k0 += 16) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int kk = lk + 2 * j;
+            float a = 0.0f;
+            if (av && k0 + kk < Kd) a = (float)Ap[aoff + (long long)ak1 * t.a_k1 + (long long)ak2 * t.a_k2];
+            As[kk][tid & 127] = a;
+            ak2 += 2;
+            while (ak2 >= t.K2) {
+                ak2 -= t.K2;
+                ++ak1;
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int kk = lkb + 4 * j;
+            float b = 0.0f;
+            if (bv && k0 + kk < Kd) b = (float)Bp[boff + (long long)bk1 * t.b_k1 + (long long)bk2 * t.b_k2];
+            Bs[kk][tid & 63] = b;
+            bk2 += 4;
+            while (bk2 >= t.K2) {
+                bk2 -= t.K2;
+                ++bk1;
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < 16; ++kk) {
+            const float4 a0 = *(const float4*)&As[kk][ty * 8];
+            const float4 a1 = *(const float4*)&As[kk][ty * 8 + 4];
+            const float4 b4 = *(const float4*)&Bs[kk][tx * 4];
+            const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+            const float b[4] = {b4.x, b4.y, b4.z, b4.w};
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                two_sum_into(hi[i][j], lo[i][j], acc[i][j]);
+                acc[i][j] = 0.0f;
+            }
+    }
+    double* __restrict__ Cp = (double*)t.C;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int m = m0 + ty * 8 + i;
+        if (m >= M) continue;
+        const long long mo = (long long)(m / t.M2) * t.c_m1 + (long long)(m % t.M2) * t.c_m2;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int n = n0 + tx * 4 + j;
+            if (n >= N) continue;
+            const long long o = mo + (long long)(n / t.N2) * t.c_n1 + (long long)(n % t.N2) * t.c_n2;
+            const double r = (double)hi[i][j] + (double)lo[i][j];
+            Cp[o] = t.accumulate ? Cp[o] + r : r;
+        }
+    }
+}
+
 cudaError_t launch_gcontract(const GTask* d_tasks, int ntasks, int max_tiles, bool cplx, cudaStream_t s, int mode) {
     if (ntasks <= 0) return cudaSuccess;
     dim3 grid(max_tiles, ntasks);
@@ -448,7 +545,8 @@ cudaError_t launch_gcontract(const GTask* d_tasks, int ntasks, int max_tiles, bo
         } else if (cplx) {
             k_gcontract<double2, float2><<<grid, 256, 0, s>>>(d_tasks);
         } else {
-            k_gcontract<double, float><<<grid, 256, 0, s>>>(d_tasks);
+            // 128 x 64 tiles: at most as many as the 64 x 64 tiles max_tiles counts
+            k_gcontract_f32w<<<grid, 256, 0, s>>>(d_tasks);
         }
         return cudaGetLastError();
     }

@@ -344,13 +344,17 @@ def run_replay(args):
         n = cfg["Lx"] * cfg["Ly"]
         terms = [[(s_, I.SIGMA_Z)] for s_ in range(n)] + [[(s_, I.SIGMA_X)] for s_ in range(n)]
         torch.cuda.synchronize()
+        s0 = g.stats()
         torch.cuda.profiler.start()  # for `ncu --profile-from-start off`: the read-out's launches only
         t0 = time.perf_counter()
         g.expect(terms)
         torch.cuda.synchronize()
         torch.cuda.profiler.stop()
-        print(json.dumps({"workload": cfg["name"], "prec": prec, "readout_s": time.perf_counter() - t0,
-                          "observables": len(terms)}), flush=True)
+        t1 = time.perf_counter()
+        s1 = g.stats()
+        print(json.dumps({"workload": cfg["name"], "prec": prec, "readout_s": t1 - t0,
+                          "observables": len(terms), "readout_gflop": (s1["flops"] - s0["flops"]) / 1e9,
+                          "readout_kernels": s1["kernels"] - s0["kernels"]}), flush=True)
         g.close()
         return
     g = make_lattice(B, cfg, prec, None)
@@ -653,6 +657,9 @@ def main():
     ap.add_argument("--no-readout", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-oracle-error", action="store_true")
+    ap.add_argument("--warm-start", type=int, default=None, choices=[0, 1, 2],
+                    help="fit warm start of the solve (default: the workload's; 2 also warm-starts the "
+                         "read-out's environment columns)")
     ap.add_argument("--keep-fp64", action="store_true",
                     help="tensor-core paths: QR/LQ truncations and read-out closings in FP64 arithmetic (default FP32)")
     ap.add_argument("--serve", action="store_true")
@@ -667,8 +674,10 @@ def main():
                                                    "'steps': every launch of a sweep timed on its own (one JSON line each)")
     ap.add_argument("--lattice", type=int, default=0, help="with --replay: the workload's recipe on an L x L lattice")
     args = ap.parse_args()
-    global KEEP_FP64
+    global KEEP_FP64, WARM
     KEEP_FP64 = int(args.keep_fp64)
+    if args.warm_start is not None:
+        WARM = args.warm_start
     if args.replay:
         run_replay(args)
     elif args.serve and args.impl == "ours":

@@ -91,7 +91,10 @@ typedef struct {
     int init_mode;           /* 0: identity-product messages; 1: random MPDO (App. A) */
     int warm_start;          /* 0: every zip-up fit starts from a random state (App. A);
                                 1: from the second sweep on, each fit starts from its own
-                                result of the previous sweep */
+                                result of the previous sweep; 2: as 1, and when chi_exp = chi
+                                the read-out's environment columns of a one-block region (the
+                                fits the sweep runs for that block's left and right messages)
+                                start from the sweep's last fits in the same frame */
     int hermitian_basis;     /* complex tensors only.  0: complex arithmetic on the FP64 path;
                                 1: Hermitian basis on the FP64 path too.  The TF32 / BF16
                                 paths always use it.  In the Hermitian basis every merged
@@ -148,7 +151,7 @@ typedef struct {
 /* Validate desc, allocate the device arena (double layer, message store, work
  * buffers) and plan one sweep.  *out receives the handle.  Limits checked here:
  * Lx, Ly <= 4096; bx, by <= 16; D <= 16; d <= 64; 1 <= fit_max_sweeps <= 64;
- * init_mode, warm_start, hermitian_basis, single_layer, launch_mode and keep_fp64 0 or 1; 0 <= shift_x < Lx and
+ * init_mode, hermitian_basis, single_layer, launch_mode and keep_fp64 0 or 1; warm_start 0..2; 0 <= shift_x < Lx and
  * 0 <= shift_y < Ly on infinite lattices, 0 <= shift_x < bx and 0 <= shift_y < by with OBC.
  * Errors: INVALID, OOM, CUDA. */
 int bbp_create_lattice(const bbp_lattice_desc* desc, bbp_lattice** out);

@@ -515,7 +515,7 @@ class Lattice:
     fit_max_sweeps: int = 10
     seed: int = 0
     init_mode: int = 0
-    warm_start: bool = False
+    warm_start: int = 0  # 0 cold; 1 sweeps warm-started; 2 also the read-out (reading 8)
     single_layer: bool = False
     shift: tuple = (0, 0)
     hermitian_basis: bool = False
@@ -759,12 +759,20 @@ class Lattice:
         m_in = self.region_incoming(blocks, horizontal=horizontal)
         tol = self.fit_tol if self.readout_fit_tol is None else self.readout_fit_tol
         opts = FitOpts(self.chi_exp, tol, self.fit_max_sweeps)
+        # Warm read-out (option warm_start = 2, reading 8): with chi_exp = chi, the environment
+        # columns of a one-block region in the LEFT (RIGHT) frame are the fits the sweep runs for
+        # that block's LEFT (RIGHT) message; each column's fit starts from a copy of the sweep's
+        # last one.
+        warm = {LEFT: None, RIGHT: None}
+        if self.warm_start == 2 and self.chi_exp == self.chi and len(blocks) == 1:
+            for dr in (LEFT, RIGHT):
+                warm[dr] = {c: [x.copy() for x in Y] for c, Y in self.warm.get((blocks[0], dr), {}).items()}
         Ef, mT, mR, mB = frame(grid, m_in, LEFT)
         keptR = column_sweep(Ef, mT, mR, mB, opts, self.seed,
-                             lambda c, i: stream_id(1, rid, 0, c, i), self.dtype, keep=True)
+                             lambda c, i: stream_id(1, rid, 0, c, i), self.dtype, keep=True, warm=warm[LEFT])
         Ef, mT, mR, mB = frame(grid, m_in, RIGHT)
         keptL = column_sweep(Ef, mT, mR, mB, opts, self.seed,
-                             lambda c, i: stream_id(1, rid, 1, c, i), self.dtype, keep=True)
+                             lambda c, i: stream_id(1, rid, 1, c, i), self.dtype, keep=True, warm=warm[RIGHT])
         Renv = {c: keptR[c + 1] for c in range(w)}
         Lenv = {c: keptL[w - c] for c in range(w)}
         return grid, m_in, Lenv, Renv

@@ -26,7 +26,18 @@ struct GTask {
     int conjA;       // complex: use conj(A)
     int accumulate;  // 1: C += result, 0: C = result
     const int* active;  // task skipped when *active == 0 (nullptr: always runs)
-    int pad;
+    // layer_d > 0: a layered pair contraction (steps with mode GC_LAYER, real operands) over
+    // layer_d physical values instead of the product above.  For every pair (m1, m2) the task
+    // reads a matrix over two contracted double legs,
+    //   X[(k1 k1')][(k2 k2')] = A[m1 a_m1 + m2 a_m2 + (k1 K1 + k1') a_k1 + (k2 K2 + k2') a_k2],
+    // and writes
+    //   Y[(n1 n1')][(n2 n2')] = sum_p sum_{k1 k2 k1' k2'} Tk_p[k1 k2 n1 n2] X[(k1 k1')][(k2 k2')] Tb_p[k1' k2' n1' n2']
+    // to C[m1 c_m1 + m2 c_m2 + (n1 N1 + n1') c_n1 + (n2 N2 + n2') c_n2]: the contraction of X
+    // with the double layer E = sum_p Tk_p (x) Tb_p, without forming E.  Tk_p[k1 k2 n1 n2] is
+    // B[p vol + k1 b_k1 + k2 b_k2 + n1 b_n1 + n2 b_n2] (vol = K1 K2 N1 N2), Tb the same view
+    // tb_off elements from B (0: the same tensor).  K1 K2 and N1 N2 are at most 32.
+    int layer_d;
+    long long tb_off;
 };
 
 // Householder QR of an m x n matrix (m >= n) read with element (i, j) at
@@ -74,8 +85,9 @@ struct RandTask {
     long long n;
     unsigned long long stream;
     int* active;  // if set, the fit's active flag is reset to 1
-    int warm;     // 1: leave the buffer as it is once the sweep counter is > 0 (warm start)
+    int warm;     // 1: leave the buffer as it is once *warm_ctr > 0 (warm start)
     int pad;
+    const int* warm_ctr;  // the lattice's sweep counter (warm tasks)
 };
 
 // One zip-up fit's convergence check after a sweep (App. A stop rule).
@@ -202,7 +214,16 @@ struct RatioTask {
 // dimension of at most 16); max_tiles counts tiles of the chosen size.  mode | GC_F32: FP64
 // operands and results, FP32 arithmetic.
 constexpr int GC_F32 = 1 << 8;
-cudaError_t launch_gcontract(const GTask* d_tasks, int ntasks, int max_tiles, bool cplx, cudaStream_t s, int mode);
+// mode | GC_LAYER: layered pair contractions (GTask::layer_d > 0); max_tiles counts CTAs of
+// LAYER_APT_F32 (with GC_F32) or LAYER_APT_F64 pairs, smem_bytes is the largest dynamic shared
+// memory of the step's tasks (layer_smem_bytes).
+constexpr int GC_LAYER = 1 << 9;
+constexpr int LAYER_APT_F32 = 8, LAYER_APT_F64 = 4;   // pairs (consecutive m2) per CTA
+constexpr size_t LAYER_SMEM_MAX = 160 * 1024;
+size_t layer_smem_bytes(int d, int UL, int DR, bool f32);
+cudaError_t layer_prepare();  // sets the dynamic shared memory limit of the layered kernels once
+cudaError_t launch_gcontract(const GTask* d_tasks, int ntasks, int max_tiles, bool cplx, cudaStream_t s, int mode,
+                             long long smem_bytes = 0);
 cudaError_t qr_prepare(int max_m, bool cplx);  // sets the dynamic shared memory limit once
 // max_mn: largest m*n of the launch; small problems keep their matrices in shared memory.
 // cluster (low byte) > 0: spread each task over that many CTAs (if its matrices fit; else the

@@ -117,10 +117,36 @@ std::string Program::validate() const {
     for (size_t i = 0; i < gc.size(); ++i) {
         const GTask& t = gc[i];
         if (t.M1 < 1 || t.M2 < 1 || t.N1 < 1 || t.N2 < 1 || t.K1 < 1 || t.K2 < 1) return "empty contraction " + std::to_string(i);
+        if (t.layer_d > 0) {
+            const int UL = t.K1 * t.K2, DR = t.N1 * t.N2;
+            if (cplx || UL > 32 || DR > 32 || layer_smem_bytes(t.layer_d, UL, DR, false) > LAYER_SMEM_MAX ||
+                layer_smem_bytes(t.layer_d, UL, DR, true) > LAYER_SMEM_MAX)
+                return "layered contraction out of range in task " + std::to_string(i);
+            const long long vol = (long long)UL * DR;
+            c.range(t.A, ext2(t.M1, t.a_m1, t.M2, t.a_m2) + ext2((long long)t.K1 * t.K1, t.a_k1, (long long)t.K2 * t.K2, t.a_k2) + 1,
+                    ss, "layered A", i);
+            const long long text = (t.layer_d - 1) * vol + ext2(t.K1, t.b_k1, t.K2, t.b_k2) + ext2(t.N1, t.b_n1, t.N2, t.b_n2) + 1;
+            c.range(t.B, text, ss, "layered Tk", i);
+            c.range((const char*)t.B + t.tb_off * ss, text, ss, "layered Tb", i);
+            // one offset from the ket to the bra survives relocation only inside one region
+            const size_t kb = (size_t)(uintptr_t)t.B, bb = kb + (size_t)(t.tb_off * ss);
+            if (parent && t.tb_off != 0 && ((kb < split) != (bb < split)))
+                return "layered tensors of task " + std::to_string(i) + " lie in different buffers";
+            c.range(t.C, ext2(t.M1, t.c_m1, t.M2, t.c_m2) + ext2((long long)t.N1 * t.N1, t.c_n1, (long long)t.N2 * t.N2, t.c_n2) + 1,
+                    ss, "layered C", i);
+            c.range(t.active, 1, 4, "active", i);
+            continue;
+        }
         c.range(t.A, ext2(t.M1, t.a_m1, t.M2, t.a_m2) + ext2(t.K1, t.a_k1, t.K2, t.a_k2) + 1, ss, "A", i);
         c.range(t.B, ext2(t.K1, t.b_k1, t.K2, t.b_k2) + ext2(t.N1, t.b_n1, t.N2, t.b_n2) + 1, ss, "B", i);
         c.range(t.C, ext2(t.M1, t.c_m1, t.M2, t.c_m2) + ext2(t.N1, t.c_n1, t.N2, t.c_n2) + 1, ss, "C", i);
         c.range(t.active, 1, 4, "active", i);
+    }
+    for (const Step& st : steps) {
+        if (st.kind != ST_GC) continue;
+        for (int k = 0; k < st.count; ++k)
+            if ((gc[st.first + k].layer_d > 0) != ((st.aux2 & GC_LAYER) != 0))
+                return "contraction step mixes layered and plain tasks";
     }
     for (size_t i = 0; i < qr.size(); ++i) {
         const QRTask& t = qr[i];
@@ -140,6 +166,7 @@ std::string Program::validate() const {
     for (size_t i = 0; i < rnd.size(); ++i) {
         c.range(rnd[i].ptr, rnd[i].n, ss, "rand", i);
         c.range(rnd[i].active, 1, 4, "rand active", i);
+        c.range(rnd[i].warm_ctr, 1, 4, "rand warm counter", i);
     }
     for (size_t i = 0; i < chk.size(); ++i) {
         c.range(chk[i].losses, chk[i].count, 8, "losses", i);
@@ -267,6 +294,30 @@ void Program::gc_step(std::vector<GTask>& ts) {
     }
     s.aux = mt;
     s.aux2 = (small ? 1 : 0) | (gc_f32 ? GC_F32 : 0);
+    steps.push_back(s);
+    ts.clear();
+}
+
+void Program::layer_step(std::vector<GTask>& ts) {
+    if (ts.empty()) return;
+    Step s;
+    s.kind = ST_GC;
+    s.first = gc.size();
+    s.count = (int)ts.size();
+    int mt = 1;
+    long long smem = 0;
+    const int apt = gc_f32 ? LAYER_APT_F32 : LAYER_APT_F64;
+    for (auto& t : ts) {
+        const int UL = t.K1 * t.K2, DR = t.N1 * t.N2;
+        mt = std::max(mt, t.M1 * ((t.M2 + apt - 1) / apt));
+        smem = std::max(smem, (long long)layer_smem_bytes(t.layer_d, UL, DR, gc_f32));
+        const double f = 2.0 * t.layer_d * UL * DR * (double)(UL + DR) * t.M1 * t.M2;
+        count_flops(t.active, f, false);
+        gc.push_back(t);
+    }
+    s.aux = mt;
+    s.aux2 = GC_LAYER | (gc_f32 ? GC_F32 : 0);
+    s.n = smem;
     steps.push_back(s);
     ts.clear();
 }
@@ -490,7 +541,8 @@ void emit_fits(Program& pr, int ss, std::vector<FitSpec*>& fits, int max_sweeps,
                 t.n = (long long)f->ybond[i] * f->O[i].q * f->ybond[i + 1];
                 t.stream = f->stream + (uint64_t)i;
                 t.active = i == 0 ? (int*)P(f->active) : nullptr;
-                t.warm = warm ? 1 : 0;
+                t.warm = (warm || f->warm) ? 1 : 0;
+                t.warm_ctr = t.warm ? (const int*)P(pr.warm_ctr_off) : nullptr;
                 rt.push_back(t);
             }
         Step s;
@@ -659,7 +711,7 @@ void Program::relocate(char* base, size_t split, char* base2) {
         RELOC(t.in); RELOC(t.out); RELOC(t.work); RELOC(t.loss); RELOC(t.active);
     }
     for (auto& t : rnd) {
-        RELOC(t.ptr); RELOC(t.active);
+        RELOC(t.ptr); RELOC(t.active); RELOC(t.warm_ctr);
     }
     if (chk_keys.empty())
         for (auto& t : chk) chk_keys.push_back((uintptr_t)t.active);
@@ -780,12 +832,17 @@ cudaError_t Program::upload_tasks(cudaStream_t st) {
     if (max_qr_m > 0) {
         if ((e = qr_prepare(max_qr_m, cplx)) != cudaSuccess) return e;
     }
+    for (const Step& s : steps)
+        if (s.kind == ST_GC && (s.aux2 & GC_LAYER)) {
+            if ((e = layer_prepare()) != cudaSuccess) return e;
+            break;
+        }
     return cudaSuccess;
 }
 
 cudaError_t Program::launch_step(const Step& s, cudaStream_t st, const int* sweep_ctr, unsigned long long seed) const {
     switch (s.kind) {
-        case ST_GC: return launch_gcontract(d_gc + s.first, s.count, s.aux, cplx, st, s.aux2);
+        case ST_GC: return launch_gcontract(d_gc + s.first, s.count, s.aux, cplx, st, s.aux2, s.n);
         case ST_QR: return launch_qr(d_qr + s.first, s.count, s.aux, s.n, cplx, st, s.aux2);
         case ST_RAND: return launch_rand(d_rnd + s.first, s.count, seed, s.aux ? sweep_ctr : nullptr, cplx, st);
         case ST_SETACT: return launch_set_int((int*)s.p0, (int)s.n, s.aux, st);
@@ -940,6 +997,12 @@ void Program::step_work(const Step& s, double* flops, double* bytes, long long* 
             for (int i = 0; i < s.count; ++i) {
                 const GTask& t = gc[s.first + i];
                 const double M = (double)t.M1 * t.M2, N = (double)t.N1 * t.N2, K = (double)t.K1 * t.K2;
+                if (t.layer_d > 0) {  // pairs: an input matrix K^2 in, an output N^2 out
+                    f += 2.0 * t.layer_d * K * N * (K + N) * M;
+                    b += M * (K * K + N * N) * ss;
+                    mm = std::max(mm, (long long)M); mn = std::max(mn, (long long)(N * N)); mk = std::max(mk, (long long)(K * K));
+                    continue;
+                }
                 f += 2.0 * M * N * K * (cplx ? 4.0 : 1.0);
                 b += (M * K + K * N + M * N) * ss;
                 mm = std::max(mm, (long long)M); mn = std::max(mn, (long long)N); mk = std::max(mk, (long long)K);
@@ -987,7 +1050,7 @@ cudaError_t Program::launch_class(cudaStream_t st, const int* sweep_ctr, unsigne
         cudaError_t e = cudaSuccess;
         switch (s.kind) {
             case ST_GC:
-                e = launch_gcontract(d_gc + s.first, s.count, s.aux, cplx, st, s.aux2);
+                e = launch_gcontract(d_gc + s.first, s.count, s.aux, cplx, st, s.aux2, s.n);
                 break;
             case ST_QR:
                 e = launch_qr(d_qr + s.first, s.count, s.aux, s.n, cplx, st, s.aux2);

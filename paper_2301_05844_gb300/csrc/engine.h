@@ -74,6 +74,7 @@ struct Program {
     int* status = nullptr;  // device error word (relocated separately)
     double fit_tol = 0.0;
     int max_qr_m = 0;
+    size_t warm_ctr_off = 0;  // byte offset of the lattice's sweep counter (warm-started fits)
     size_t arena_used = 256;  // offset 0 stays unused so that 0 means "no buffer"
     double static_flops = 0, gated_flops = 0, static_qr_flops = 0, gated_qr_flops = 0;
     // flops of one fit sweep of each fit, keyed by its active flag's arena offset (the value the
@@ -97,6 +98,7 @@ struct Program {
     // arena buffer.  Returns an empty string or a description of the first violation.
     std::string validate() const;
     void gc_step(std::vector<GTask>& ts);
+    void layer_step(std::vector<GTask>& ts);  // layered pair contractions (GTask::layer_d > 0)
     void qr_step(std::vector<QRTask>& ts);
     // inner products (normalise = false) or power-of-two normalisations (true), see DotTask
     void dot_step(std::vector<DotTask>& ts, bool normalise = false);

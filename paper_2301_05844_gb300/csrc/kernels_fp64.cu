@@ -532,10 +532,194 @@ __global__ void __launch_bounds__(256) k_gcontract_f32w(const GTask* __restrict_
     }
 }
 
-cudaError_t launch_gcontract(const GTask* d_tasks, int ntasks, int max_tiles, bool cplx, cudaStream_t s, int mode) {
+// Layered pair contraction (GTask::layer_d > 0; read-out rows of real double-layer lattices):
+// per pair, Z_p = X' Tb_p and Y' = sum_p Tk_p^T Z_p, where X' is the [(k1 k2)][(k1' k2')]
+// matrix of the pair's input and Tk_p, Tb_p the [(k1 k2)][(n1 n2)] matrices of the two
+// tensors: 2 d UL DR (UL + DR) flops per pair (UL = K1 K2, DR = N1 N2) where the contraction
+// with the double layer E costs 2 UL^2 DR^2.  A CTA takes one m1 and APT consecutive m2 (the
+// input's unit-stride index at every call site, so that the loads are contiguous runs); both
+// tensors, the APT input matrices, the Z_p and the staged outputs sit in shared memory in the
+// arithmetic type Cm (float: the operands are rounded to FP32 as in k_gcontract<double, float>).
+// Shared layout (elements of Cm): Ts [2][d][UL][DRp] | Xs [APT][UL][ULs] (reused for the output
+// tile [APT][DR*DR]) | Zs [APT][d][UL][DRp]; DRp = DR rounded up to 4 (vector reads), ULs = UL
+// made odd (conflict-free row reads).
+__host__ __device__ inline int layer_drp(int DR) { return (DR + 3) & ~3; }
+__host__ __device__ inline int layer_uls(int UL) { return UL | 1; }
+__host__ __device__ inline long long layer_round4(long long x) { return (x + 3) & ~3LL; }
+
+__device__ inline void lds4(const float* p, float (&v)[4]) {
+    const float4 q = *(const float4*)p;
+    v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+}
+__device__ inline void lds4(const double* p, double (&v)[4]) {
+    const double2 a = *(const double2*)p, b = *(const double2*)(p + 2);
+    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+
+template <typename Cm, int APT>
+__global__ void __launch_bounds__(256) k_layer_pair(const GTask* __restrict__ tasks) {
+    const GTask& t = tasks[blockIdx.y];
+    if (t.active && *t.active == 0) return;
+    const int d = t.layer_d, K1 = t.K1, K2 = t.K2, N1 = t.N1, N2 = t.N2;
+    const int UL = K1 * K2, DR = N1 * N2, DRp = layer_drp(DR), ULs = layer_uls(UL);
+    const int tilesM2 = (t.M2 + APT - 1) / APT;
+    if ((int)blockIdx.x >= t.M1 * tilesM2) return;
+    const int m1 = blockIdx.x / tilesM2, m20 = (blockIdx.x % tilesM2) * APT;
+    extern __shared__ __align__(16) unsigned char layer_smem[];
+    Cm* Ts = (Cm*)layer_smem;
+    const long long tsz = layer_round4(2LL * d * UL * DRp);
+    Cm* Xs = Ts + tsz;
+    const long long xin = (long long)APT * UL * ULs, xout = (long long)APT * DR * DR;
+    const long long xsz = layer_round4(xin > xout ? xin : xout);
+    Cm* Zs = Xs + xsz;
+    const double* __restrict__ A = (const double*)t.A;
+    const double* __restrict__ B = (const double*)t.B;
+    const long long vol = (long long)UL * DR;
+    const int tid = threadIdx.x;
+    // both tensors, [side][p][(k1 k2)][(n1 n2)], pad columns zero
+    for (int e = tid; e < 2 * d * UL * DRp; e += 256) {
+        const int dr = e % DRp, r = e / DRp, ul = r % UL, r2 = r / UL, p = r2 % d, side = r2 / d;
+        Cm v = Cm(0);
+        if (dr < DR) {
+            const int k1 = ul / K2, k2 = ul % K2, n1 = dr / N2, n2 = dr % N2;
+            v = (Cm)B[(side ? t.tb_off : 0) + p * vol + k1 * t.b_k1 + k2 * t.b_k2 + n1 * t.b_n1 + n2 * t.b_n2];
+        }
+        Ts[e] = v;
+    }
+    // the APT input matrices, [ap][(k1 k2)][(k1' k2')]; ap fastest in the loads
+    for (int e = tid; e < APT * UL * UL; e += 256) {
+        const int ap = e % APT, r = e / APT, ulp = r % UL, ul = r / UL;
+        const int k1 = ul / K2, k2 = ul % K2, k1p = ulp / K2, k2p = ulp % K2;
+        const int m2 = m20 + ap;
+        Cm v = Cm(0);
+        if (m2 < t.M2)
+            v = (Cm)A[m1 * t.a_m1 + m2 * t.a_m2 + (long long)(k1 * K1 + k1p) * t.a_k1 + (long long)(k2 * K2 + k2p) * t.a_k2];
+        Xs[(ap * UL + ul) * ULs + ulp] = v;
+    }
+    __syncthreads();
+    const Cm* Tk = Ts;
+    const Cm* Tb = Ts + (long long)d * UL * DRp;
+    // Z_p[(k1 k2)][(n1' n2')] = sum_{(k1' k2')} X'[(k1 k2)][(k1' k2')] Tb_p[(k1' k2')][(n1' n2')]
+    for (int w = tid; w < APT * d * UL; w += 256) {
+        const int ul = w % UL, r = w / UL, ap = r % APT, p = r / APT;
+        Cm acc[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) acc[j] = Cm(0);
+        const Cm* xr = Xs + (ap * UL + ul) * ULs;
+        const Cm* tb = Tb + (long long)p * UL * DRp;
+        for (int k = 0; k < UL; ++k) {
+            const Cm x = xr[k];
+            const Cm* row = tb + k * DRp;
+#pragma unroll
+            for (int j4 = 0; j4 < 8; ++j4)
+                if (4 * j4 < DR) {
+                    Cm v[4];
+                    lds4(row + 4 * j4, v);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) acc[4 * j4 + q] = fma(x, v[q], acc[4 * j4 + q]);
+                }
+        }
+        Cm* zr = Zs + (((long long)ap * d + p) * UL + ul) * DRp;
+#pragma unroll
+        for (int j4 = 0; j4 < 8; ++j4)
+            if (4 * j4 < DRp) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) zr[4 * j4 + q] = acc[4 * j4 + q];
+            }
+    }
+    __syncthreads();
+    // Y[(n1 n1')][(n2 n2')] = sum_p sum_{(k1 k2)} Tk_p[(k1 k2)][(n1 n2)] Z_p[(k1 k2)][(n1' n2')],
+    // staged as [ap][(n1 n1')][(n2 n2')] over the input matrices
+    Cm* Os = Xs;
+    for (int w = tid; w < APT * DR; w += 256) {
+        const int dr = w % DR, ap = w / DR;
+        Cm acc[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) acc[j] = Cm(0);
+        for (int p = 0; p < d; ++p) {
+            const Cm* tk = Tk + (long long)p * UL * DRp + dr;
+            const Cm* zb = Zs + ((long long)ap * d + p) * UL * DRp;
+            for (int k = 0; k < UL; ++k) {
+                const Cm a = tk[k * DRp];
+                const Cm* row = zb + k * DRp;
+#pragma unroll
+                for (int j4 = 0; j4 < 8; ++j4)
+                    if (4 * j4 < DR) {
+                        Cm v[4];
+                        lds4(row + 4 * j4, v);
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) acc[4 * j4 + q] = fma(a, v[q], acc[4 * j4 + q]);
+                    }
+            }
+        }
+        // the pad columns of Z are zero, so acc[j >= DR] is never stored
+        const int n1 = dr / N2, n2 = dr % N2;
+        Cm* orow = Os + (long long)ap * DR * DR;
+        int n1p = 0, n2p = 0;
+#pragma unroll
+        for (int j = 0; j < 32; ++j)
+            if (j < DR) {
+                orow[(n1 * N1 + n1p) * (N2 * N2) + n2 * N2 + n2p] = acc[j];
+                if (++n2p == N2) {
+                    n2p = 0;
+                    ++n1p;
+                }
+            }
+    }
+    __syncthreads();
+    double* __restrict__ C = (double*)t.C;
+    const int DR2 = DR * DR, N22 = N2 * N2;
+    for (int e = tid; e < APT * DR2; e += 256) {
+        const int ap = e / DR2, rem = e % DR2, i1 = rem / N22, i2 = rem % N22;
+        const int m2 = m20 + ap;
+        if (m2 >= t.M2) continue;
+        const long long o = m1 * t.c_m1 + m2 * t.c_m2 + i1 * t.c_n1 + i2 * t.c_n2;
+        const double r = (double)Os[e];
+        C[o] = t.accumulate ? C[o] + r : r;
+    }
+}
+
+size_t layer_smem_bytes(int d, int UL, int DR, bool f32) {
+    const int apt = f32 ? LAYER_APT_F32 : LAYER_APT_F64;
+    const long long DRp = layer_drp(DR), ULs = layer_uls(UL);
+    const long long el = layer_round4(2LL * d * UL * DRp) +
+                         layer_round4(std::max((long long)apt * UL * ULs, (long long)apt * DR * DR)) +
+                         (long long)apt * d * UL * DRp;
+    return (size_t)el * (f32 ? sizeof(float) : sizeof(double));
+}
+
+cudaError_t layer_prepare() {
+    static std::mutex mu;
+    std::lock_guard<std::mutex> guard(mu);
+    constexpr int kMaxDev = 64;
+    static bool done[kMaxDev] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) return cudaErrorInvalidDevice;
+    if (done[dev]) return cudaSuccess;
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(k_layer_pair<float, LAYER_APT_F32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)LAYER_SMEM_MAX)))
+        return e;
+    if ((e = cudaFuncSetAttribute(k_layer_pair<double, LAYER_APT_F64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)LAYER_SMEM_MAX)))
+        return e;
+    done[dev] = true;
+    return cudaSuccess;
+}
+
+cudaError_t launch_gcontract(const GTask* d_tasks, int ntasks, int max_tiles, bool cplx, cudaStream_t s, int mode,
+                             long long smem_bytes) {
     if (ntasks <= 0) return cudaSuccess;
     dim3 grid(max_tiles, ntasks);
     const bool small = mode & 1;
+    if (mode & GC_LAYER) {
+        if (cplx || smem_bytes <= 0 || smem_bytes > (long long)LAYER_SMEM_MAX) return cudaErrorInvalidValue;
+        if (mode & GC_F32)
+            k_layer_pair<float, LAYER_APT_F32><<<grid, 256, (size_t)smem_bytes, s>>>(d_tasks);
+        else
+            k_layer_pair<double, LAYER_APT_F64><<<grid, 256, (size_t)smem_bytes, s>>>(d_tasks);
+        return cudaGetLastError();
+    }
     if (mode & GC_F32) {
         if (small) {
             if (cplx)
@@ -1416,7 +1600,7 @@ __global__ void k_rand(const RandTask* __restrict__ tasks, unsigned long long se
     const long long cnt = cplx ? 2 * t.n : t.n;
     double* p = (double*)t.ptr;
     if (t.active && blockIdx.x == 0 && threadIdx.x == 0) *t.active = 1;
-    if (t.warm && sweep_ctr && *sweep_ctr > 0) return;
+    if (t.warm && t.warm_ctr && *t.warm_ctr > 0) return;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < cnt; i += (long long)gridDim.x * blockDim.x)
         p[i] = u_pm1(key, (uint64_t)i);
 }

@@ -282,6 +282,11 @@ int plan_column_sweeps(bbp_lattice* L, Program& pr, std::vector<ColumnSweep>& cs
             f.active = active;
             f.counter = pr.arena_alloc(sizeof(int));
             f.stream = stream_id(s.tag, s.outer, s.msg, (uint64_t)c, 0);
+            if (s.warm_from) {
+                const FitSpec& g = (*s.warm_from)[c];
+                if (g.ybond != f.ybond || g.n() != f.n()) return fail(BBP_ERR_INVALID, "internal: warm source shape");
+                f.warm = true;
+            }
         }
         if (!mixed) continue;
         // low-precision operand buffers, sized for every column of this sweep
@@ -351,10 +356,31 @@ int plan_column_sweeps(bbp_lattice* L, Program& pr, std::vector<ColumnSweep>& cs
     for (auto& s : cs) Wmax = std::max(Wmax, s.W);
     for (int k = 0; k < Wmax; ++k) {
         std::vector<FitSpec*> group;
+        std::vector<RelayoutTask> warm_copy;  // FP64 copies of the warm sources' fitted MPS
         for (auto& s : cs) {
             const int c = s.W - 1 - k;
-            if (c >= 0) group.push_back(&s.fits[c]);
+            if (c < 0) continue;
+            group.push_back(&s.fits[c]);
+            if (!s.warm_from) continue;
+            const FitSpec& g = (*s.warm_from)[c];
+            const FitSpec& f = s.fits[c];
+            for (int i = 0; i < f.n(); ++i) {
+                RelayoutTask r{};
+                r.src = P(g.Y[i] * (size_t)ss);
+                r.dst = P(f.Y[i] * (size_t)ss);
+                r.src_kind = 0;
+                r.dst_kind = 0;
+                r.d[0] = f.ybond[i] * f.O[i].q * f.ybond[i + 1];
+                r.d[1] = r.d[2] = r.d[3] = 1;
+                r.ss[0] = 1;
+                r.ds[0] = 1;
+                if (L->cplx) {  // complex scalars as pairs of doubles
+                    r.d[0] *= 2;
+                }
+                warm_copy.push_back(r);
+            }
         }
+        pr.rel_step(warm_copy);
         if (!mixed) {
             emit_fits(pr, ss, group, max_sweeps, fit_tol, warm, rand_uses_sweep);
             continue;
@@ -441,6 +467,9 @@ static int plan_sweep(bbp_lattice* L) {
     Program& pr = L->sweep;
     pr.cplx = L->cplx;
     const int ss = L->ss;
+    // the sweep counter first: warm-started fits read it
+    const size_t sweepctr = pr.arena_alloc(sizeof(int));
+    pr.warm_ctr_off = sweepctr;
     // the column sweep of every item
     std::vector<ColumnSweep> cs;
     for (int it = 0; it < (int)L->items.size(); ++it) {
@@ -535,7 +564,6 @@ static int plan_sweep(bbp_lattice* L) {
     const size_t resid = pr.arena_alloc(sizeof(double) * std::max<size_t>(1, L->items.size()));
     const size_t residual = pr.arena_alloc(sizeof(double));
     const size_t status = pr.arena_alloc(sizeof(int));
-    const size_t sweepctr = pr.arena_alloc(sizeof(int));
     for (int it = 0; it < (int)nt.size(); ++it) {
         nt[it].resid = (double*)P(resid + (size_t)it * sizeof(double));
         nt[it].status = (int*)P(status);
@@ -597,7 +625,7 @@ static int validate(const bbp_lattice_desc* d) {
     if (d->Lx > 4096 || d->Ly > 4096) return fail(BBP_ERR_INVALID, "lattice sides are limited to 4096 sites");
     if (d->D > 16 || d->d > 64) return fail(BBP_ERR_INVALID, "D or d too large");
     if (d->init_mode != 0 && d->init_mode != 1) return fail(BBP_ERR_INVALID, "init_mode must be 0 or 1");
-    if (d->warm_start != 0 && d->warm_start != 1) return fail(BBP_ERR_INVALID, "warm_start must be 0 or 1");
+    if (d->warm_start < 0 || d->warm_start > 2) return fail(BBP_ERR_INVALID, "warm_start must be 0, 1 or 2");
     if (d->single_layer != 0 && d->single_layer != 1) return fail(BBP_ERR_INVALID, "single_layer must be 0 or 1");
     if (d->launch_mode != 0 && d->launch_mode != 1) return fail(BBP_ERR_INVALID, "launch_mode must be 0 or 1");
     if (d->keep_fp64 != 0 && d->keep_fp64 != 1) return fail(BBP_ERR_INVALID, "keep_fp64 must be 0 or 1");

@@ -38,6 +38,10 @@ struct ColumnSweep {
     uint64_t tag = 0, outer = 0, msg = 0;  // generator stream fields
     int H = 0, W = 0;
     std::vector<FitSpec> fits;
+    // Warm start from another column sweep's fits of the same shapes (the read-out's environment
+    // columns of a block from the sweep's fits of that block's message in the same frame): each
+    // column's fit starts from a copy of that sweep's fitted MPS once the sweep counter is > 0.
+    const std::vector<FitSpec>* warm_from = nullptr;
 };
 
 // Words read back after every sweep (pinned host memory).

@@ -243,7 +243,8 @@ void emit_fits_mixed(Program& pr, const MixCtx& cx, std::vector<FitSpec*>& fits,
                 t.n = (long long)f->ybond[i] * f->O[i].q * f->ybond[i + 1];
                 t.stream = f->stream + (uint64_t)i;
                 t.active = i == 0 ? (int*)P(f->active) : nullptr;
-                t.warm = warm ? 1 : 0;
+                t.warm = (warm || f->warm) ? 1 : 0;
+                t.warm_ctr = t.warm ? (const int*)P(pr.warm_ctr_off) : nullptr;
                 rt.push_back(t);
             }
         Step s;

@@ -71,6 +71,7 @@ struct FitSpec {
     size_t losses = 0, active = 0, counter = 0;  // byte offsets: doubles, int flag, int counter
     uint64_t stream = 0;      // generator stream of site 0 (site i adds i)
     bool mixed = false;
+    bool warm = false;        // start from Y as it is once the sweep counter is > 0
     MixBufs mx;
     int n() const { return (int)X.size(); }
 };

@@ -265,6 +265,7 @@ extern "C" int bbp_expect(bbp_lattice* L, const bbp_term* terms, int n_terms, do
     pr.arena_used = split;
     pr.parent = &L->sweep;  // buffers below `split` are the lattice's
     pr.split = split;
+    pr.warm_ctr_off = L->sweep.warm_ctr_off;
     auto elem_alloc = [&](size_t elems) { return pr.arena_alloc(elems * (size_t)ss) / (size_t)ss; };
     std::vector<ColumnSweep> cs;
     for (auto& R : regions) {
@@ -278,6 +279,13 @@ extern "C" int bbp_expect(bbp_lattice* L, const bbp_term* terms, int n_terms, do
             s.tag = 1;
             s.outer = (uint64_t)R.rid;
             s.msg = (uint64_t)side;
+            // Warm read-out (desc->warm_start = 2, chi_exp = chi): a one-block region's
+            // environment columns in this frame are the fits the sweep runs for the block's
+            // message in the same direction; they start from that sweep's last fitted MPS of
+            // each column.
+            if (ds.warm_start == 2 && ds.chi_exp == ds.chi && R.blocks.size() == 1)
+                for (const auto& I : L->items)
+                    if (I.block == R.blocks[0] && I.dir == s.dir) s.warm_from = &I.fits;
             (side == 0 ? R.sweepL : R.sweepR) = (int)cs.size();
             cs.push_back(s);
         }
@@ -378,7 +386,26 @@ extern "C" int bbp_expect(bbp_lattice* L, const bbp_term* terms, int n_terms, do
         return {o.u, o.l, o.d, o.r};
     };
     // scratch maxima over every strip row (the chains and the closings use the same rows)
-    size_t fmax = 1, s1max = 1, s2max = 1, o12max = 1;
+    // Layered rows (real double-layer lattices): a site row contracts the ket tensor T (or O T at
+    // an operator site) and the bra tensor T one after the other instead of the double-layer
+    // E = sum_p (O T)_p T_p; the same sums in another order, with about a fifth of the flops of
+    // the E contraction at D = 5.
+    const bool layered = !L->cplx && !L->single && !L->hb;
+    // a site row of a one-column strip takes the layered route when both of its pair
+    // contractions (down: legs u, l against d, r; up: d, l against u, r) fit the kernel
+    auto layered_site = [&](const Strip& S, int i) {
+        if (!layered || S.ncols != 1 || i < 1 || i > regions[S.region].h) return false;
+        const Region& R = regions[S.region];
+        const auto dd = L->site_dims(R.r0 + i - 1, R.c0 + S.col);
+        const int ULd = dd[0] * dd[1], DRd = dd[2] * dd[3], ULu = dd[2] * dd[1], DRu = dd[0] * dd[3];
+        if (ULd > 32 || DRd > 32 || ULu > 32 || DRu > 32) return false;
+        for (bool f : {false, true})
+            if (layer_smem_bytes(d, ULd, DRd, f) > LAYER_SMEM_MAX || layer_smem_bytes(d, ULu, DRu, f) > LAYER_SMEM_MAX)
+                return false;
+        return true;
+    };
+    bool any_layered = false;
+    size_t fmax = 1, s1max = 1, s2max = 1, o12max = 1, tomax = 1;
     for (auto& S : strips) {
         const Region& R = regions[S.region];
         for (int i = 0; i < R.h + 2; ++i) {
@@ -396,6 +423,11 @@ extern "C" int bbp_expect(bbp_lattice* L, const bbp_term* terms, int n_terms, do
                 o12max = std::max(o12max, (size_t)o.u * o2.u * o.l * o.d * o2.d * o2.r);
             }
             fmax = std::max({fmax, A * u * B, Ap * v * Bp});
+            if (layered_site(S, i)) {  // O T and T of an operator site in this row
+                const auto dd = L->site_dims(R.r0 + i - 1, R.c0 + S.col);
+                tomax = std::max(tomax, 2 * (size_t)d * dd[0] * dd[1] * dd[2] * dd[3]);
+                any_layered = true;
+            }
             s1max = std::max({s1max, u * B * s * Ap, v * Bp * s * A});     // G1 (down), X1 (up)
             s2max = std::max({s2max, B * Ap * v * t2, Bp * A * u * t2});   // G2 (down), X2 (up)
             if (i >= 1) S.chain += A * u * B;                              // T_i, i = 1..h+1
@@ -403,9 +435,10 @@ extern "C" int bbp_expect(bbp_lattice* L, const bbp_term* terms, int n_terms, do
         }
     }
     struct Lane {
-        size_t F[2], S1, S2, EO[2], O12;
+        size_t F[2], S1, S2, EO[2], O12, TO[2];
     };
-    const size_t lane_elems = 2 * fmax + s1max + s2max + (L->single ? 0 : 2 * (size_t)K4max) + o12max;
+    const size_t lane_elems = 2 * fmax + s1max + s2max + (L->single ? 0 : 2 * (size_t)K4max) + o12max +
+                              (any_layered ? 2 * tomax : 0);
     // device memory for the read-out's scratch: up to a quarter of what is free (at least 1 GB,
     // at most 16 GB), half of it for lanes, half for the strips' environments
     size_t mem_free = 0, mem_total = 0;
@@ -455,6 +488,10 @@ extern "C" int bbp_expect(bbp_lattice* L, const bbp_term* terms, int n_terms, do
             ln.EO[1] = elem_alloc(K4max);
         }
         ln.O12 = elem_alloc(o12max);
+        if (any_layered) {
+            ln.TO[0] = elem_alloc(tomax);
+            ln.TO[1] = elem_alloc(tomax);
+        }
     }
     // operators (impurity tensors) of every closing, each in its own slab: uploaded once
     // before the read-out runs, whichever wave of lanes uses them
@@ -485,6 +522,20 @@ extern "C" int bbp_expect(bbp_lattice* L, const bbp_term* terms, int n_terms, do
             opoff[ci][k] = elem_alloc(L->cplx ? v.size() / 2 : v.size());
             uploads.push_back({opoff[ci][k], v});
         }
+    // layered operator rows: [O; 1], so that one contraction writes O T and a copy of T side by
+    // side in the lane (the layered kernel finds the bra tensor at a fixed offset from the ket,
+    // and the read-out's buffers and the lattice's are placed independently)
+    std::vector<std::array<size_t, 2>> opaug(nclos, std::array<size_t, 2>{0, 0});
+    if (any_layered)
+        for (size_t ci = 0; ci < nclos; ++ci)
+            for (size_t k = 0; k < closings[ci].pos.size(); ++k) {
+                std::vector<double> v = closings[ci].ops[k];
+                if (v.size() != (size_t)d * d) continue;  // real d x d operators only
+                v.resize(2 * (size_t)d * d, 0.0);
+                for (int p = 0; p < d; ++p) v[(size_t)(d + p) * d + p] = 1.0;
+                opaug[ci][k] = elem_alloc(v.size());
+                uploads.push_back({opaug[ci][k], v});
+            }
 
     // strip row i's operator, E^O at the sites listed in subs (local (row, col), offset); a
     // column pair is fused into o12 first
@@ -566,6 +617,78 @@ extern "C" int bbp_expect(bbp_lattice* L, const bbp_term* terms, int n_terms, do
         c.c_m1 = Wd * B_; c.c_m2 = B_; c.c_n2 = 1;
         g3.push_back(c);
     };
+    // Layered rows: g1 and g3 as in row_down / row_up, and between them one layered pair
+    // contraction (GTask::layer_d) with the ket tensor tk (T, or O T at an operator site) and
+    // the bra tensor T in place of the contraction with E.  Downwards the pairs are (B, Ap),
+    // the contracted double legs (u u'), (l l') of G1 and the free ones (d d'), (r r') of G2;
+    // upwards the pairs are (Bp, A), contracted (d d'), (l l') of X1, free (u u'), (r r') of X2.
+    auto row_down_layered = [&](size_t Fin, size_t Fout, const View3& Lv, const View3& Rv, size_t tk, size_t tb,
+                                const std::array<int, 4>& dd, const Lane& ln, std::vector<GTask>& g1,
+                                std::vector<GTask>& g2, std::vector<GTask>& g3) {
+        const long long Du = dd[0], Dl = dd[1], Dd = dd[2], Dr = dd[3], DdDr = Dd * Dr;
+        const long long A_ = Lv.a, Wd = Du * Du, B_ = Rv.a, sK = Lv.k, Ap = Lv.b, v = Dd * Dd, t2 = Rv.k, Bp = Rv.b;
+        GTask a{};
+        a.A = P(Fin * ss); a.B = P(Lv.off * ss); a.C = P(ln.S1 * ss);
+        a.M1 = (int)Wd; a.M2 = (int)B_; a.K1 = 1; a.K2 = (int)A_; a.N1 = (int)sK; a.N2 = (int)Ap;
+        a.a_m1 = B_; a.a_m2 = 1; a.a_k2 = Wd * B_;
+        a.b_k2 = Lv.sa; a.b_n1 = Lv.sk; a.b_n2 = Lv.sb;
+        a.c_m1 = B_ * sK * Ap; a.c_m2 = sK * Ap; a.c_n1 = Ap; a.c_n2 = 1;
+        g1.push_back(a);
+        GTask t{};
+        t.A = P(ln.S1 * ss); t.B = P(tk * ss); t.C = P(ln.S2 * ss);
+        t.layer_d = d;
+        t.tb_off = (long long)tb - (long long)tk;
+        t.M1 = (int)B_; t.M2 = (int)Ap; t.K1 = (int)Du; t.K2 = (int)Dl; t.N1 = (int)Dd; t.N2 = (int)Dr;
+        t.a_m1 = sK * Ap; t.a_m2 = 1; t.a_k1 = B_ * sK * Ap; t.a_k2 = Ap;       // G1[W][B][s][Ap]
+        t.b_k1 = Dl * DdDr; t.b_k2 = DdDr; t.b_n1 = Dr; t.b_n2 = 1;              // T[p][u][l][d][r]
+        t.c_m1 = Ap * v * t2; t.c_m2 = v * t2; t.c_n1 = t2; t.c_n2 = 1;          // G2[B][Ap][v][t2]
+        g2.push_back(t);
+        GTask c{};
+        c.A = P(ln.S2 * ss); c.B = P(Rv.off * ss); c.C = P(Fout * ss);
+        c.M1 = (int)Ap; c.M2 = (int)v; c.K1 = (int)B_; c.K2 = (int)t2; c.N1 = 1; c.N2 = (int)Bp;
+        c.a_m1 = v * t2; c.a_m2 = t2; c.a_k1 = Ap * v * t2; c.a_k2 = 1;
+        c.b_k1 = Rv.sa; c.b_k2 = Rv.sk; c.b_n2 = Rv.sb;
+        c.c_m1 = v * Bp; c.c_m2 = Bp; c.c_n2 = 1;
+        g3.push_back(c);
+    };
+    auto row_up_layered = [&](size_t Gin, size_t Gout, const View3& Lv, const View3& Rv, size_t tk, size_t tb,
+                              const std::array<int, 4>& dd, const Lane& ln, std::vector<GTask>& g1,
+                              std::vector<GTask>& g2, std::vector<GTask>& g3) {
+        const long long Du = dd[0], Dl = dd[1], Dd = dd[2], Dr = dd[3], DdDr = Dd * Dr;
+        const long long A_ = Lv.a, Wd = Du * Du, B_ = Rv.a, sK = Lv.k, Ap = Lv.b, v = Dd * Dd, t2 = Rv.k, Bp = Rv.b;
+        GTask a{};
+        a.A = P(Gin * ss); a.B = P(Lv.off * ss); a.C = P(ln.S1 * ss);
+        a.M1 = (int)v; a.M2 = (int)Bp; a.K1 = 1; a.K2 = (int)Ap; a.N1 = (int)sK; a.N2 = (int)A_;
+        a.a_m1 = Bp; a.a_m2 = 1; a.a_k2 = v * Bp;
+        a.b_k2 = Lv.sb; a.b_n1 = Lv.sk; a.b_n2 = Lv.sa;
+        a.c_m1 = Bp * sK * A_; a.c_m2 = sK * A_; a.c_n1 = A_; a.c_n2 = 1;
+        g1.push_back(a);
+        GTask t{};
+        t.A = P(ln.S1 * ss); t.B = P(tk * ss); t.C = P(ln.S2 * ss);
+        t.layer_d = d;
+        t.tb_off = (long long)tb - (long long)tk;
+        t.M1 = (int)Bp; t.M2 = (int)A_; t.K1 = (int)Dd; t.K2 = (int)Dl; t.N1 = (int)Du; t.N2 = (int)Dr;
+        t.a_m1 = sK * A_; t.a_m2 = 1; t.a_k1 = Bp * sK * A_; t.a_k2 = A_;       // X1[v][Bp][s][A]
+        t.b_k1 = Dr; t.b_k2 = DdDr; t.b_n1 = Dl * DdDr; t.b_n2 = 1;            // T[p][u][l][d][r]
+        t.c_m1 = A_ * Wd * t2; t.c_m2 = Wd * t2; t.c_n1 = t2; t.c_n2 = 1;        // X2[Bp][A][W][t2]
+        g2.push_back(t);
+        GTask c{};
+        c.A = P(ln.S2 * ss); c.B = P(Rv.off * ss); c.C = P(Gout * ss);
+        c.M1 = (int)A_; c.M2 = (int)Wd; c.K1 = (int)Bp; c.K2 = (int)t2; c.N1 = 1; c.N2 = (int)B_;
+        c.a_m1 = Wd * t2; c.a_m2 = t2; c.a_k1 = A_ * Wd * t2; c.a_k2 = 1;
+        c.b_k1 = Rv.sb; c.b_k2 = Rv.sk; c.b_n2 = Rv.sa;
+        c.c_m1 = Wd * B_; c.c_m2 = B_; c.c_n2 = 1;
+        g3.push_back(c);
+    };
+    auto is_layered = [&](const Strip& S, int i) { return layered_site(S, i); };
+    auto site_T = [&](const Strip& S, int i) {
+        const Region& R = regions[S.region];
+        return L->T_off[L->tensor_index(R.r0 + i - 1, R.c0 + S.col)];
+    };
+    auto site_dd = [&](const Strip& S, int i) {
+        const Region& R = regions[S.region];
+        return L->site_dims(R.r0 + i - 1, R.c0 + S.col);
+    };
     auto fuse_step = [&](std::vector<FuseTask>& ft, long long fmx) {
         if (ft.empty()) return;
         Step s;
@@ -614,7 +737,7 @@ extern "C" int bbp_expect(bbp_lattice* L, const bbp_term* terms, int n_terms, do
         for (int j = 0; j <= hmax + 1; ++j) {
             std::vector<FuseTask> ft;
             long long fmx = 1;
-            std::vector<GTask> g1, g2, g3;
+            std::vector<GTask> g1, g2, g2l, g3;
             std::vector<DotTask> p2;
             for (size_t q = 0; q < wave.size(); ++q) {
                 const Strip& S = strips[wave[q]];
@@ -623,9 +746,15 @@ extern "C" int bbp_expect(bbp_lattice* L, const bbp_term* terms, int n_terms, do
                 const Lane& top = lanes[2 * q];
                 const Lane& bot = lanes[2 * q + 1];
                 if (j <= h) {
-                    const Op4 o = strip_op(S, j, {}, top.O12, ft, fmx);
-                    row_down(j == 0 ? L->one_off : S.T[j], S.T[j + 1], env_site(R, true, S.col, j),
-                             o, env_site(R, false, S.col + S.ncols - 1, j), top, g1, g2, g3);
+                    if (is_layered(S, j)) {
+                        row_down_layered(S.T[j], S.T[j + 1], env_site(R, true, S.col, j),
+                                         env_site(R, false, S.col, j), site_T(S, j), site_T(S, j), site_dd(S, j),
+                                         top, g1, g2l, g3);
+                    } else {
+                        const Op4 o = strip_op(S, j, {}, top.O12, ft, fmx);
+                        row_down(j == 0 ? L->one_off : S.T[j], S.T[j + 1], env_site(R, true, S.col, j),
+                                 o, env_site(R, false, S.col + S.ncols - 1, j), top, g1, g2, g3);
+                    }
                     DotTask t{};
                     t.A = P(S.T[j + 1] * ss); t.out = P(S.eT[j + 1]); t.n = (long long)env_scalars(S, j + 1);
                     t.ea = j == 0 ? nullptr : eptr(S.eT[j]);
@@ -633,9 +762,15 @@ extern "C" int bbp_expect(bbp_lattice* L, const bbp_term* terms, int n_terms, do
                 }
                 const int ib = h + 1 - j;
                 if (ib >= 2) {
-                    const Op4 o = strip_op(S, ib, {}, bot.O12, ft, fmx);
-                    row_up(ib == h + 1 ? L->one_off : S.G[ib + 1], S.G[ib], env_site(R, true, S.col, ib), o,
-                           env_site(R, false, S.col + S.ncols - 1, ib), bot, g1, g2, g3);
+                    if (is_layered(S, ib)) {
+                        row_up_layered(S.G[ib + 1], S.G[ib], env_site(R, true, S.col, ib),
+                                       env_site(R, false, S.col, ib), site_T(S, ib), site_T(S, ib), site_dd(S, ib),
+                                       bot, g1, g2l, g3);
+                    } else {
+                        const Op4 o = strip_op(S, ib, {}, bot.O12, ft, fmx);
+                        row_up(ib == h + 1 ? L->one_off : S.G[ib + 1], S.G[ib], env_site(R, true, S.col, ib), o,
+                               env_site(R, false, S.col + S.ncols - 1, ib), bot, g1, g2, g3);
+                    }
                     DotTask t{};
                     t.A = P(S.G[ib] * ss); t.out = P(S.eG[ib]); t.n = (long long)env_scalars(S, ib);
                     t.ea = ib == h + 1 ? nullptr : eptr(S.eG[ib + 1]);
@@ -645,6 +780,7 @@ extern "C" int bbp_expect(bbp_lattice* L, const bbp_term* terms, int n_terms, do
             fuse_step(ft, fmx);
             pr.gc_step(g1);
             pr.gc_step(g2);
+            pr.layer_step(g2l);
             pr.gc_step(g3);
             if (f32c) pr.dot_step(p2, true);
         }
@@ -672,6 +808,7 @@ extern "C" int bbp_expect(bbp_lattice* L, const bbp_term* terms, int n_terms, do
             const size_t w1 = std::min(cl.size(), w0 + nlanes);
             // E^O for the operator sites of these closings
             std::vector<DLTask> dlt;
+            std::vector<GTask> otk;
             long long dlmax = 1;
             std::vector<int> i0(w1 - w0), i1(w1 - w0);
             int nrows = 0;
@@ -688,6 +825,19 @@ extern "C" int bbp_expect(bbp_lattice* L, const bbp_term* terms, int n_terms, do
                     if (L->single) continue;  // the impurity tensor is E^O itself
                     const int r = R.r0 + C.pos[k].first, c = R.c0 + C.pos[k].second;
                     const auto dd = L->site_dims(r, c);
+                    if (is_layered(strips[strip_of[ci]], C.pos[k].first + 1)) {
+                        // layered row: the ket tensor O T and the bra tensor T,
+                        //   TO[p'][x] = sum_p [O; 1][p'][p] T[p][x], p' < 2d
+                        const long long vol = (long long)dd[0] * dd[1] * dd[2] * dd[3];
+                        if (!opaug[ci][k]) return fail(BBP_ERR_INVALID, "internal: layered operator missing");
+                        GTask t{};
+                        t.A = P(opaug[ci][k] * ss); t.B = P(L->T_off[L->tensor_index(r, c)] * ss);
+                        t.C = P(ln.TO[k] * ss);
+                        t.M1 = 1; t.M2 = 2 * d; t.K1 = 1; t.K2 = d; t.N1 = 1; t.N2 = (int)vol;
+                        t.a_m2 = d; t.a_k2 = 1; t.b_k2 = vol; t.b_n2 = 1; t.c_m2 = vol; t.c_n2 = 1;
+                        otk.push_back(t);
+                        continue;
+                    }
                     DLTask t{};
                     t.T = P(L->T_off[L->tensor_index(r, c)] * ss);
                     t.E = P(ln.EO[k] * ss);
@@ -709,10 +859,11 @@ extern "C" int bbp_expect(bbp_lattice* L, const bbp_term* terms, int n_terms, do
                 pr.dl.insert(pr.dl.end(), dlt.begin(), dlt.end());
                 pr.steps.push_back(s);
             }
+            pr.gc_step(otk);
             for (int rr = 0; rr < nrows; ++rr) {
                 std::vector<FuseTask> ft;
                 long long fmx = 1;
-                std::vector<GTask> g1, g2, g3;
+                std::vector<GTask> g1, g2, g2l, g3;
                 for (size_t q = w0; q < w1; ++q) {
                     const int i = i0[q - w0] + rr;
                     if (i > i1[q - w0]) continue;
@@ -721,16 +872,31 @@ extern "C" int bbp_expect(bbp_lattice* L, const bbp_term* terms, int n_terms, do
                     const Strip& S = strips[strip_of[ci]];
                     const Region& R = regions[S.region];
                     const Lane& ln = lanes[q - w0];
+                    const size_t Fin = rr == 0 ? S.T[i] : ln.F[(rr - 1) % 2];
+                    if (is_layered(S, i)) {
+                        size_t tk = site_T(S, i), tb = tk;
+                        for (size_t k = 0; k < C.pos.size(); ++k)
+                            if (C.pos[k].first == i - 1 && C.pos[k].second == S.col) {
+                                const auto dd = site_dd(S, i);
+                                tk = ln.TO[k];
+                                tb = tk + (size_t)d * dd[0] * dd[1] * dd[2] * dd[3];
+                                break;
+                            }
+                        row_down_layered(Fin, ln.F[rr % 2], env_site(R, true, S.col, i), env_site(R, false, S.col, i),
+                                         tk, tb, site_dd(S, i), ln, g1, g2l, g3);
+                        continue;
+                    }
                     std::vector<std::pair<std::pair<int, int>, size_t>> subs;
                     for (size_t k = 0; k < C.pos.size(); ++k)
                         subs.push_back({C.pos[k], L->single ? opoff[ci][k] : ln.EO[k]});
                     const Op4 o = strip_op(S, i, subs, ln.O12, ft, fmx);
-                    row_down(rr == 0 ? S.T[i] : ln.F[(rr - 1) % 2], ln.F[rr % 2], env_site(R, true, S.col, i), o,
+                    row_down(Fin, ln.F[rr % 2], env_site(R, true, S.col, i), o,
                              env_site(R, false, S.col + S.ncols - 1, i), ln, g1, g2, g3);
                 }
                 fuse_step(ft, fmx);
                 pr.gc_step(g1);
                 pr.gc_step(g2);
+                pr.layer_step(g2l);
                 pr.gc_step(g3);
             }
             // N_O = <F after the closing's last row, G below it>

@@ -133,6 +133,35 @@ def test_warm_start_parity(chi):
     assert close(gv, ov)
 
 
+@pytest.mark.parametrize("chi", [16, 6])
+def test_warm_start_readout_parity(chi):
+    """Warm read-out (warm_start = 2) with chi_exp = chi: the read-out's environment columns of every one-block
+    region start from the sweep's last fits in the same frame, on both sides (blocks at the
+    lattice edge have no message toward it and start cold); same <O>."""
+    cfg = I.config(1)
+    terms = I.standard_terms(4, 4)
+    g, o, gr, orr, gv, ov = run_both(cfg["tensors"], 4, 4, 2, 2, 2, 2, chi, terms, n_sweeps=4, warm_start=2,
+                                     fit_max_sweeps=2, chi_exp=chi)
+    assert close(gr, orr, 1e-9), (gr, orr)
+    assert close(gv, ov)
+
+
+def test_warm_start_readout_truncating_6x6():
+    """6x6 OBC, D=3, 3x3 blocks, chi = chi_exp = 12 (truncating), warm read-out, one fit sweep per
+    fit, six sweeps (the messages converge to a residual of ~1e-14, while a read-out fit started
+    cold stays unconverged: warm and cold read-outs differ by 1.0e-7 here): interior frames'
+    environment columns start from the sweep's fits; frames at the lattice edge and cross-block
+    pairs (merged regions) start cold.  With one fit sweep per fit the fits never converge, so
+    the roundoff of the two sides' QRs at the truncation stays in their results; the bound is
+    1e-8, ten times below the warm/cold difference it has to resolve."""
+    T = I.uniform_noise_peps(6, 6, 2, 3, seed=5)
+    terms = [[(7, SZ)], [(14, SX)], [(7, SZ), (8, SZ)], [(2, SX), (3, SX)], [(14, SZ), (20, SZ)], [(21, SZ)]]
+    g, o, gr, orr, gv, ov = run_both(T, 6, 6, 2, 3, 3, 3, 12, terms, n_sweeps=6, warm_start=2, fit_max_sweeps=1,
+                                     chi_exp=12)
+    assert close(gr, orr, 1e-9)
+    assert np.max(np.abs(gv - ov)) < 1e-8, (np.max(np.abs(gv - ov)), 1 - message_fidelity(g, o))
+
+
 def test_bonds_above_the_numerical_rank():
     """chi = 64 > the rank that the column MPS can carry next to an open edge: the fits
     meet QR columns beyond the numerical rank (tiny norms) and must still match the

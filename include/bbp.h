@@ -142,9 +142,11 @@ typedef struct {
                                 (their input is already an FP32 contraction result; Q is
                                 still stored in FP64 and the fit loss summed in FP64) and the
                                 read-out closings (FP64 operands rounded to FP32, FP32
-                                accumulation compensated by TwoSum, FP64 results, every
-                                environment of a strip rescaled by a power of two so that
-                                nothing overflows); 1 keeps
+                                accumulation compensated by TwoSum over the environment bonds,
+                                plain FP32 sums of at most d D^2 terms in the layered site
+                                rows of real lattices, FP64 results, every environment of a
+                                strip rescaled by a power of two so that nothing overflows);
+                                1 keeps
                                 FP64 arithmetic there.  The FP64 path always uses FP64. */
 } bbp_lattice_desc;
 

@@ -303,6 +303,21 @@ def test_warm_start_reaches_the_same_fixed_point():
     assert np.max(np.abs(vals[0] - vals[1])) < 1e-10
 
 
+def test_warm_readout_environments_change_nothing_at_full_rank():
+    """warm_start = 2 also starts the read-out's environment columns of one-block regions
+    from the sweep's last fits (chi_exp = chi).  Where those fits are exact (full rank) the
+    starting point cannot move <O>: warm_start 2 agrees with 0 on every observable, one-block
+    and two-block (cross-edge pair) regions alike."""
+    T = I.uniform_noise_peps(4, 4, 2, 2, seed=5)
+    terms = I.standard_terms(4, 4)
+    vals = []
+    for warm in (0, 2):
+        lat = ob.Lattice(4, 4, 2, 2, 2, 2, T, chi=16, chi_exp=16, fit_tol=1e-12, fit_max_sweeps=6, warm_start=warm)
+        lat.run(n_sweeps=6)
+        vals.append(lat.expect(terms))
+    assert np.max(np.abs(vals[0] - vals[1])) < 1e-10
+
+
 def _onsager(beta):
     """Spontaneous magnetisation of the 2D square-lattice Ising model (Onsager, Yang):
     (1 - sinh(2 beta)^-4)^(1/8) below the critical temperature, 0 above it."""

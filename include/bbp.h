@@ -341,6 +341,17 @@ int bbp_selftest_scalar(long long n, const double* x, double* rsqrt_ours, double
  * CUDA. */
 int bbp_selftest_qr_fp32(int batch, int m, int n, const float* A, double* Q, double* loss, int* workspace_intact);
 
+/* Not a step of the method: the self-test of the layered pair contraction that the read-out
+ * uses on the site rows of real double-layer lattices (App. A read-out closings, contracted
+ * with the ket and bra tensors in turn instead of E = sum_p Tk_p (x) Tb_p):
+ *   Y[m1][m2][(n1 n1')][(n2 n2')] = sum_p sum_{k1 k2 k1' k2'} Tk[p][k1][k2][n1][n2]
+ *                                   X[(k1 k1')][m1][(k2 k2')][m2] Tb[p][k1'][k2'][n1'][n2'],
+ * merged indices ket-major (k1 K1 + k1').  All arrays on the host, FP64, C order; f32 != 0
+ * runs the FP32-arithmetic instance (tensor-core lattices).  Requires K1 K2 <= 32 and
+ * N1 N2 <= 32 (and the shared memory that d and these imply).  Errors: INVALID, OOM, CUDA. */
+int bbp_selftest_layer(int f32, int d, int K1, int K2, int N1, int N2, int M1, int M2, const double* X,
+                       const double* Tk, const double* Tb, double* Y);
+
 /* Kernel-class timing of one planned sweep, for roofline measurements: replays, on
  * the handle's stream and bracketed by CUDA events, only the launches of one class
  * (0: tensor-core GEMM steps, 1: FP64 strided contractions, 2: FP64 QR/LQ),

@@ -154,6 +154,53 @@ extern "C" int bbp_selftest_qr_fp32(int batch, int m, int n, const float* A, dou
     return abi_error();
 }
 
+// Layered pair contraction (the read-out's layered site rows) on host arrays: X in the
+// layout of a downward row's first intermediate, [(k1 k1')][m1][(k2 k2')][m2], Tk and Tb as
+// [p][k1][k2][n1][n2] (placed side by side on the device, the bra at a fixed offset from
+// the ket, as the read-out places O T and T), Y as [m1][m2][(n1 n1')][(n2 n2')].
+extern "C" int bbp_selftest_layer(int f32, int d, int K1, int K2, int N1, int N2, int M1, int M2, const double* X,
+                                  const double* Tk, const double* Tb, double* Y) try {
+    if (d < 1 || K1 < 1 || K2 < 1 || N1 < 1 || N2 < 1 || M1 < 1 || M2 < 1 || !X || !Tk || !Tb || !Y)
+        return fail(BBP_ERR_INVALID, "selftest_layer: bad arguments");
+    const int UL = K1 * K2, DR = N1 * N2;
+    const size_t smem = layer_smem_bytes(d, UL, DR, f32 != 0);
+    if (UL > 32 || DR > 32 || smem > LAYER_SMEM_MAX) return fail(BBP_ERR_INVALID, "selftest_layer: shape beyond the kernel");
+    const long long K1q = (long long)K1 * K1, K2q = (long long)K2 * K2, vol = (long long)UL * DR;
+    const size_t nx = (size_t)(K1q * M1 * K2q * M2), nt = (size_t)(d * vol), ny = (size_t)M1 * M2 * DR * DR;
+    GTask t{};
+    t.layer_d = d;
+    t.tb_off = (long long)nt;
+    t.M1 = M1; t.M2 = M2; t.K1 = K1; t.K2 = K2; t.N1 = N1; t.N2 = N2;
+    t.a_k1 = (long long)M1 * K2q * M2; t.a_m1 = K2q * M2; t.a_k2 = M2; t.a_m2 = 1;
+    t.b_k1 = (long long)K2 * DR; t.b_k2 = DR; t.b_n1 = N2; t.b_n2 = 1;
+    t.c_m1 = (long long)M2 * DR * DR; t.c_m2 = (long long)DR * DR; t.c_n1 = (long long)N2 * N2; t.c_n2 = 1;
+    auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    const size_t xb = nx * 8, tb = 2 * nt * 8, yb = ny * 8;
+    char* dmem = nullptr;
+    cudaError_t e = cudaMalloc((void**)&dmem, al(xb) + al(tb) + al(yb) + al(sizeof(GTask)));
+    if (e) return fail(BBP_ERR_OOM, std::string("selftest_layer: ") + cudaGetErrorString(e));
+    double* dx = (double*)dmem;
+    double* dt = (double*)(dmem + al(xb));
+    double* dy = (double*)(dmem + al(xb) + al(tb));
+    GTask* dtask = (GTask*)(dmem + al(xb) + al(tb) + al(yb));
+    t.A = dx; t.B = dt; t.C = dy;
+    e = cudaMemcpy(dx, X, xb, cudaMemcpyHostToDevice);
+    if (!e) e = cudaMemcpy(dt, Tk, nt * 8, cudaMemcpyHostToDevice);
+    if (!e) e = cudaMemcpy(dt + nt, Tb, nt * 8, cudaMemcpyHostToDevice);
+    if (!e) e = cudaMemcpy(dtask, &t, sizeof(GTask), cudaMemcpyHostToDevice);
+    if (!e) e = layer_prepare();
+    const int apt = f32 ? LAYER_APT_F32 : LAYER_APT_F64;
+    const int tiles = M1 * ((M2 + apt - 1) / apt);
+    if (!e) e = launch_gcontract(dtask, 1, tiles, false, 0, GC_LAYER | (f32 ? GC_F32 : 0), (long long)smem);
+    if (!e) e = cudaDeviceSynchronize();
+    if (!e) e = cudaMemcpy(Y, dy, yb, cudaMemcpyDeviceToHost);
+    cudaFree(dmem);
+    if (e) return fail(BBP_ERR_CUDA, std::string("selftest_layer: ") + cudaGetErrorString(e));
+    return BBP_OK;
+} catch (...) {
+    return abi_error();
+}
+
 extern "C" int bbp_selftest_rng(unsigned long long seed, unsigned long long stream, long long n, double* out) try {
     if (n < 0 || (n > 0 && !out)) return fail(BBP_ERR_INVALID, "selftest_rng: bad arguments");
     for (long long i = 0; i < n; ++i) out[i] = bbp::uniform_pm1(seed, stream, (uint64_t)i);

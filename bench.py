@@ -139,7 +139,7 @@ def oracle_lattice(cfg):
     from oracle import blockbp as ob
     return ob.Lattice(cfg["Lx"], cfg["Ly"], cfg["d"], cfg["D"], cfg["bx"], cfg["by"],
                       [np.asarray(t) for t in cfg["tensors"]], boundary=cfg["boundary"], chi=cfg["chi"],
-                      fit_tol=1e-6, fit_max_sweeps=10, seed=1, warm_start=bool(WARM),
+                      fit_tol=1e-6, fit_max_sweeps=10, seed=1, warm_start=int(WARM),
                       single_layer=bool(cfg.get("single_layer", 0)))
 
 

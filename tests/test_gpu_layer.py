@@ -18,6 +18,8 @@ SHAPES = [  # d, K1, K2, N1, N2, M1, M2
     (1, 1, 4, 4, 1, 1, 5),
     (2, 4, 8, 8, 4, 2, 9),
     (4, 2, 2, 3, 3, 2, 7),
+    (2, 1, 1, 1, 32, 1, 3),
+    (1, 32, 1, 1, 1, 2, 3),
 ]
 
 
